@@ -1,0 +1,91 @@
+/*
+ * amg_oracle.h -- plain FP64 CPU oracle of the sparsified-AMG hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this code; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code with the CUDA path.
+ *
+ * It follows, in order and notation, Bienz, Falgout, Gropp, Olson, Schroder,
+ * "Reducing Parallel Communication in Algebraic Multigrid through
+ * Sparsification" (arXiv:1512.04629):
+ *   Algorithm 1 (amg_setup), Algorithm 2 (amg_solve, the V-cycle),
+ *   Algorithm 3 (sparsify: minimal pattern M, drop test, symmetric N) with the
+ *   diagonal-lumping loop of Algorithm 3b, Algorithm 4 (Sparse Galerkin),
+ *   Algorithm 5 (adaptive_solve) and PCG (Section 5.5 / Section 6).
+ * Where the paper leaves a choice open (strength formula, PMIS details, direct
+ * interpolation, stop rule, ell1-Jacobi, the garbled lines of Algorithms 4 and
+ * 5) the reading taken is stated at the function that implements it.
+ *
+ * Floating point: every sum runs sequentially in increasing column order and
+ * the file is compiled with -ffp-contract=off, so each result is the plain
+ * IEEE-754 double evaluation of the formula as written.
+ *
+ * Parity status: every function here is pinned by a CPU test against closed
+ * forms, dense brute force or the paper's worked example (Example 1); the
+ * iteration counts of PCG are pinned only through those parts ("parity
+ * unpinned" against the paper, whose convergence plots are not printed).
+ */
+#ifndef AMG_ORACLE_H
+#define AMG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CSR matrix: nrows x ncols, int32 indices, columns increasing in each row. */
+typedef struct {
+    int32_t nrows, ncols, nnz;
+    int32_t *rowptr; /* nrows + 1 */
+    int32_t *col;    /* nnz */
+    double *val;     /* nnz */
+} orc_csr;
+
+typedef struct {
+    int32_t iterations;   /* number of products with A_0 p */
+    int32_t status;       /* 0 converged, 4 not converged, 6 breakdown */
+    int32_t resets;       /* adaptive: number of reintroductions (PCG restarts) */
+    int32_t replacements; /* residual replacements after a failed true-residual check */
+    double final_relres;  /* ||b - A x|| / ||b|| at exit (true residual) */
+    double conv_factor;   /* (||r_end|| / ||r_0||)^(1 / iterations) */
+} orc_info;
+
+typedef struct orc_hier orc_hier;
+
+/* ---- building blocks (Section 2, Algorithm 1) ---- */
+void orc_strength(const orc_csr *A, double theta, uint8_t *strong);
+int orc_pmis(const orc_csr *A, const uint8_t *strong, uint64_t seed, int32_t level, int8_t *cf);
+orc_csr *orc_direct_interp(const orc_csr *A, const uint8_t *strong, const int8_t *cf);
+orc_csr *orc_transpose(const orc_csr *M);
+orc_csr *orc_spgemm(const orc_csr *A, const orc_csr *B);
+int orc_minimal_pattern(const orc_csr *Ac, const orc_csr *AP, const int8_t *cf, uint8_t *inM);
+orc_csr *orc_sparsify_diag(const orc_csr *Ac, const uint8_t *inM, double gamma, uint8_t *keep);
+void orc_l1_diag(const orc_csr *A, double *d);
+int orc_cholesky(int32_t n, double *a);
+void orc_chol_solve(int32_t n, const double *L, const double *b, double *x);
+void orc_spmv(const orc_csr *A, const double *x, double *y);
+double orc_uniform_weight(uint64_t seed, int32_t level, int64_t i);
+int orc_gamma_schedule(double *gamma, int32_t nlev, int32_t s, double gamma_min, int32_t *changed);
+
+/* ---- hierarchy (Algorithms 1, 2, 4, 5) ---- */
+orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
+                    uint64_t seed, int32_t *status);
+int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma);
+int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed);
+int orc_vcycle(orc_hier *h, const double *b, double *x);
+int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info);
+int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                       int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info);
+void orc_free(orc_hier *h);
+void orc_csr_free(orc_csr *m);
+
+/* accessors for the tests (borrowed pointers, valid until orc_free) */
+int32_t orc_num_levels(const orc_hier *h);
+const orc_csr *orc_level_matrix(const orc_hier *h, int32_t l, int32_t which);
+const void *orc_level_array(const orc_hier *h, int32_t l, int32_t which);
+double orc_level_gamma(const orc_hier *h, int32_t l);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
