@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the sparsified-AMG PCG solver on GB300.
+
+Workload (BASELINE config 2): 3D 7-point Poisson on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760), right-hand side uniform[-1, 1) from seed 1,
+x0 = 0.  One step = the whole hot path on inputs already resident in HBM:
+GPU setup (strength, PMIS, direct interpolation, Galerkin SpGEMM), Sparse
+Galerkin sparsification with diagonal lumping at gamma = 0.1 on levels >= 1,
+ell1 diagonals, coarse Cholesky, then PCG with one V(1,1) per iteration to
+||b - A x|| / ||b|| <= 1e-8, FP64.  value = solves per second over all ranks.
+
+Also reported: the roofline of the dominant solve-phase kernel (algorithmic
+bytes / CUDA-event time vs the measured HBM peak), the same metric end to end
+through the C ABI with host buffers, the CPU oracle on the host cores, and
+the Galerkin / gamma / adaptive arms of config 2 measured outside the timed
+region.  `--impl reference` times the CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 solve & V-cycle HBM GB/s, sparse vs Galerkin; serving p99"
+UNIT = "solves/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--grid", type=int, default=128)
+    p.add_argument("--gamma", type=float, default=0.1)
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--no-arms", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(args):
+    n = args.grid ** 3
+    return {
+        "workload": f"3D 7-point Poisson {args.grid}^3 (n={n}), Sparse Galerkin gamma={args.gamma} on levels>=1, "
+                    f"PCG + V(1,1) l1-Jacobi to {args.tol:g}, FP64; step = GPU setup + sparsify + solve",
+        "grid": args.grid, "n": n, "gamma": args.gamma, "tol": args.tol, "precision": "fp64",
+        "theta": 0.25, "coarsening": "PMIS", "interpolation": "direct",
+        "l2_policy": "inputs larger than L2 (A = 175 MB FP64 CSR at 128^3)",
+        "parallelism": "replicas",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-launch DRAM bytes of kernels captured with ncu (profiles/)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            key, rows, nnz, b = line.split()[:4]
+            out[key] = (int(rows), int(nnz), float(b))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+def oracle_step(A, b, gamma, tol):
+    import oracle
+
+    t0 = time.perf_counter()
+    h = oracle.Hierarchy(A)
+    h.sparsify([0.0, gamma])
+    x, info = h.pcg(b, tol=tol)
+    dt = time.perf_counter() - t0
+    assert info.status == 0, info
+    return dt, info
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import amg_inputs as gen
+    import oracle
+
+    oracle.build()
+    A = gen.poisson3d_7pt(args.grid)
+    b = gen.rhs_uniform(A.n, 1)
+    budget = 200.0 / max(1, args.steps + args.warmup)  # seconds per step
+    # one untimed full-size step sizes the sample: full size if it fits the
+    # per-step budget, else the largest sub-grid that does (value scaled by n)
+    t_full, _ = oracle_step(A, b, args.gamma, args.tol)
+    N, As, bs, scale = args.grid, A, b, 1.0
+    if t_full > budget:
+        N = max(16, int(args.grid * (budget / t_full) ** (1.0 / 3.0)))
+        As = gen.poisson3d_7pt(N)
+        bs = gen.rhs_uniform(As.n, 1)
+        scale = As.n / A.n
+    for _ in range(max(0, args.warmup - (1 if scale == 1.0 else 0))):
+        oracle_step(As, bs, args.gamma, args.tol)
+    times = []
+    its = None
+    for _ in range(args.steps):
+        dt, info = oracle_step(As, bs, args.gamma, args.tol)
+        times.append(dt)
+        its = info.iterations
+    total = sum(times)
+    value = args.steps / total * scale
+    sample = (f"full workload ({args.grid}^3) per step" if scale == 1.0 else
+              f"{N}^3 sub-grid per step (n={As.n}), value scaled by n ratio {scale:.4f} (AMG cost is O(n))")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args), "iterations": its,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+KIND_NAMES = {0: "relax_pre_residual", 1: "restrict", 2: "prolong", 3: "relax_post", 4: "coarse_solve",
+              5: "pcg_Ap_dot", 6: "pcg_vector"}
+
+
+def collect_timing(h, nlev):
+    rows = []
+    for kind in range(7):
+        for l in range(nlev):
+            n, ms, by = h.timing_get(kind, l)
+            if n:
+                rows.append({"kind": KIND_NAMES[kind], "level": l, "launches": n, "ms": ms, "bytes": by})
+    return rows
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+    from paper_1512_04629_gb300 import build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    amg.lib()
+
+    A = gen.poisson3d_7pt(args.grid)
+    b = gen.rhs_uniform(A.n, 1)
+    rp = torch.from_numpy(A.rowptr).cuda()
+    ci = torch.from_numpy(A.col).cuda()
+    va = torch.from_numpy(A.val).cuda()
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    A_dev = amg.amg.csr_struct(rp, ci, va)
+    gamma = [0.0, args.gamma]
+    torch.cuda.synchronize()
+
+    def step(timing=False):
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma)
+        if timing:
+            h.timing_enable(True)
+        x, info = h.solve(bd, xd, tol=args.tol)
+        return h, info
+
+    for _ in range(args.warmup):
+        h, info = step()
+        assert info.status == 0, info.as_dict()
+        del h
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timings = {}
+    its = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = amg.kernel_launches()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        h, info = step(timing=True)
+        its.append(info.iterations)
+        assert info.status == 0 and info.final_relres <= args.tol, info.as_dict()
+        for r in collect_timing(h, h.num_levels):
+            key = (r["kind"], r["level"])
+            t = timings.setdefault(key, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+            t["launches"] += r["launches"]
+            t["ms"] += r["ms"]
+            t["bytes"] += r["bytes"]
+        last_h = h
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = amg.kernel_launches() - launches0
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = world * args.steps / elapsed
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # hierarchy shape of the timed configuration
+    levels = []
+    for l in range(last_h.num_levels):
+        st = last_h.level_stats(l)
+        levels.append({"n": st["n"], "nnz_galerkin": st["nnz_galerkin"], "nnz_operator": st["nnz_operator"],
+                       "spmv": amg.SPMV_NAMES.get(st["spmv_variant"], "?"), "bytes_per_cycle": st["bytes_per_cycle"]})
+
+    # roofline of the dominant solve-phase kernel
+    peak, peak_kind = measured_peak()
+    dom_key = max(timings, key=lambda k: timings[k]["ms"])
+    dom = timings[dom_key]
+    per_launch_bytes = dom["bytes"] / dom["launches"]
+    avg_ms = dom["ms"] / dom["launches"]
+    achieved = per_launch_bytes / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    tr = ncu_traffic().get(f"{dom_key[0]}_L{dom_key[1]}")
+    if tr is not None:
+        rows_cap, nnz_cap, bytes_cap = tr
+        n_dom = levels[dom_key[1]]["n"]
+        traffic = bytes_cap * (n_dom / rows_cap) if rows_cap else None
+    roofline = {"kernel": f"{dom_key[0]} level {dom_key[1]}", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
+                "launches": dom["launches"]}
+    vcycle_ms = sum(v["ms"] for k, v in timings.items() if k[0] not in ("pcg_Ap_dot", "pcg_vector"))
+    vcycle_bytes = sum(v["bytes"] for k, v in timings.items() if k[0] not in ("pcg_Ap_dot", "pcg_vector"))
+    kernels = sorted(({"kernel": f"{k[0]} L{k[1]}", "launches": v["launches"], "ms": round(v["ms"], 4),
+                       "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
+                      for k, v in timings.items()), key=lambda r: -r["ms"])[:12]
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hp = [torch.from_numpy(a).pin_memory() for a in (A.rowptr, A.col, A.val, b)]
+        xh = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+        A_host = amg.amg.csr_struct(hp[0].numpy(), hp[1].numpy(), hp[2].numpy())
+        bh = hp[3].numpy()
+        xn = xh.numpy()
+        ke = max(1, min(args.steps, 5))
+        h = amg.Hierarchy.setup(A_host, gamma=gamma)
+        h.solve(bh, xn, tol=args.tol)
+        del h
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            h = amg.Hierarchy.setup(A_host, gamma=gamma)
+            _, info = h.solve(bh, xn, tol=args.tol)
+            assert info.status == 0
+            del h
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = A.rowptr.nbytes + A.col.nbytes + A.val.nbytes + b.nbytes
+        e2e = {"value": ke / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(xn.nbytes),
+               "steps": ke}
+
+    # config 2 arms (outside the timed region): solve-only time to 1e-8 per hierarchy
+    arms = None
+    if not args.no_arms:
+        arms = {}
+        for name, g, adaptive in [("galerkin", 0.0, False), ("gamma_0.01", 0.01, False), ("gamma_0.1", 0.1, False),
+                                  ("gamma_1.0", 1.0, False), ("adaptive_from_1.0", 1.0, True)]:
+            t0 = time.perf_counter()
+            h = amg.Hierarchy.setup(A_dev, gamma=[0.0, g] if g > 0 else None)
+            torch.cuda.synchronize()
+            setup_ms = 1e3 * (time.perf_counter() - t0)
+            sol = []
+            for rep in range(3):
+                if adaptive and rep > 0:
+                    h.sparsify([0.0, g])
+                h.timing_reset()
+                h.timing_enable(rep == 2)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, info = h.solve(bd, xd, tol=args.tol, adaptive=adaptive)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sol.append(e0.elapsed_time(e1))
+            rows = collect_timing(h, h.num_levels)
+            vms = sum(r["ms"] for r in rows if r["kind"] not in ("pcg_Ap_dot", "pcg_vector"))
+            vby = sum(r["bytes"] for r in rows if r["kind"] not in ("pcg_Ap_dot", "pcg_vector"))
+            oc = sum(h.level_stats(l)["nnz_operator"] for l in range(h.num_levels)) / A.nnz
+            arms[name] = {"solve_ms_median": statistics.median(sol[1:]) if not adaptive else sol[0],
+                          "setup_ms": setup_ms, "iterations": info.iterations, "resets": info.resets,
+                          "conv_factor": info.conv_factor, "final_relres": info.final_relres,
+                          "operator_complexity": oc,
+                          "vcycle_GBps": vby / (vms * 1e-3) / 1e9 if vms > 0 else None,
+                          "nnz_per_level": [h.level_stats(l)["nnz_operator"] for l in range(h.num_levels)]}
+            del h
+
+    cpu = None
+    if not args.no_cpu:
+        dt, info = oracle_step(A, b, args.gamma, args.tol)
+        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full step ({args.grid}^3 setup + sparsify + PCG, {info.iterations} its) on one host core"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+        "iterations": statistics.median(its), "levels": levels,
+        "roofline": roofline, "vcycle_GBps": vcycle_bytes / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms else None,
+        "top_kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,267 @@
+/*
+ * amg.h -- C ABI of the GB300 sparsified algebraic-multigrid library (libamg.so).
+ *
+ * The library solves SPD systems A x = b (Bienz, Falgout, Gropp, Olson,
+ * Schroder, "Reducing Parallel Communication in Algebraic Multigrid through
+ * Sparsification", arXiv:1512.04629, Section 1) with preconditioned CG whose
+ * preconditioner is one AMG V-cycle (Algorithm 2) over a classical Galerkin
+ * hierarchy (Algorithm 1) whose coarse operators are thinned by Sparse
+ * Galerkin sparsification with diagonal lumping (Algorithm 4 with the loop of
+ * Algorithm 3b), and whose dropped entries can be reintroduced when
+ * convergence is slow (Algorithm 5).  Every step runs in the library's own
+ * CUDA kernels on one GPU (sm_103a).
+ *
+ * Conventions shared by every call:
+ *  - Matrices are CSR with int32 row pointers and column indices, columns
+ *    strictly increasing within a row, the diagonal stored, fewer than 2^31
+ *    stored entries, FP64 values.
+ *  - Pointers are host pointers unless an argument or struct field says they
+ *    are device pointers.  "Device pointer" means memory of the current CUDA
+ *    device (e.g. the data pointer of a CUDA torch tensor).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device work of a call is ordered on that stream; a call that
+ *    returns host data synchronises it.
+ *  - The caller owns every buffer it passes; the library only reads inputs
+ *    and writes outputs during the call and keeps no pointer to them.  The
+ *    library owns every hierarchy, its device memory, and every server.
+ *  - No C++ exception crosses the ABI.  Every call returns an amg_status; on
+ *    failure amg_last_error() holds a thread-local message.  Invalid input is
+ *    rejected with AMG_ERR_INVALID before any kernel is launched.
+ *  - A hierarchy may be used by one thread at a time (the server serialises
+ *    its own use).
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_ERR_INVALID = 1,   /* bad argument or matrix; nothing was launched */
+    AMG_ERR_OOM = 2,       /* device or host allocation failed */
+    AMG_ERR_CUDA = 3,      /* a CUDA call failed; see amg_last_error() */
+    AMG_NOT_CONVERGED = 4, /* max_it reached; x and info are still filled */
+    AMG_DIVERGED = 5,      /* residual grew by 1e3 over a check window */
+    AMG_BREAKDOWN = 6,     /* CG lost positive definiteness (rho or p.Ap <= 0) */
+    AMG_TIMEOUT = 7,       /* a wait ran past its time limit */
+    AMG_REJECTED = 8       /* admission refused (server: memory budget / queue) */
+} amg_status;
+
+/* A square (or, with ncols > 0, rectangular) CSR matrix, caller-owned and
+ * read-only.  on_device != 0: rowptr, col, val are device pointers. */
+typedef struct {
+    int64_t n;             /* rows */
+    int64_t nnz;           /* stored entries = rowptr[n] */
+    const int32_t *rowptr; /* n + 1 */
+    const int32_t *col;    /* nnz, increasing within each row */
+    const double *val;     /* nnz */
+    int on_device;
+    int64_t ncols;         /* 0 means ncols = n */
+} amg_csr;
+
+enum { AMG_METHOD_SPARSE = 0, AMG_METHOD_HYBRID = 1 };
+enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_FP32_BF16 = 2 };
+/* SpMV kernel variants: CSR with T threads per row, or SELL-32 slices. */
+enum {
+    AMG_SPMV_AUTO = -1,
+    AMG_SPMV_CSR2 = 1, AMG_SPMV_CSR4 = 2, AMG_SPMV_CSR8 = 3, AMG_SPMV_CSR16 = 4,
+    AMG_SPMV_CSR32 = 5, AMG_SPMV_SELL32 = 6
+};
+
+typedef struct {
+    double theta;        /* strength threshold (classical rule), default 0.25 */
+    int max_size;        /* stop coarsening at n <= max_size, default 100 */
+    int max_levels;      /* default 25 */
+    uint64_t seed;       /* PMIS random weights, default 0 */
+    int method;          /* AMG_METHOD_SPARSE (default) or AMG_METHOD_HYBRID */
+    int precision;       /* AMG_PREC_*: storage/arithmetic of the V-cycle */
+    int k_check;         /* Algorithm 5: PCG steps between checks, default 3 */
+    int s_levels;        /* Algorithm 5: levels updated per step, default 1 */
+    double gamma_min;    /* Algorithm 5: smaller tolerances become 0, default 0.01 */
+    double rho_max;      /* Algorithm 5: reintroduce above this factor, default 0.5 */
+    int level_offset;    /* PMIS level index of the first level, default 0 */
+    int spmv_variant;    /* AMG_SPMV_AUTO (autotuned per level) or forced */
+    int use_graph;       /* capture the PCG iteration in a CUDA graph, default 1 */
+    int check_every;     /* PCG iterations between host stop tests, default 1 */
+} amg_options;
+
+typedef struct {
+    int iterations;      /* products with A_0 (CG steps) */
+    int status;          /* amg_status of the solve */
+    int resets;          /* adaptive: reintroductions (PCG restarts) */
+    int replacements;    /* true-residual replacements */
+    double final_relres; /* ||b - A x||_2 / ||b||_2, FP64, at exit */
+    double conv_factor;  /* (||r_end|| / ||r_0||)^(1/iterations) */
+    double solve_ms;     /* wall time of the call (host clock) */
+} amg_solve_info;
+
+typedef struct {
+    int64_t n;              /* rows of A_l */
+    int64_t nnz_galerkin;   /* stored entries of the Galerkin A_l */
+    int64_t nnz_operator;   /* stored entries of the relaxed operator Ahat_l */
+    int64_t nnz_p;          /* entries of P_l (0 on the coarsest level) */
+    int64_t n_coarse;       /* columns of P_l */
+    double gamma;           /* drop tolerance of the level */
+    int spmv_variant;       /* AMG_SPMV_* used by the level's relaxation */
+    int value_bytes;        /* bytes per stored value in the cycle (8, 4, 2) */
+    double bytes_per_cycle; /* algorithmic HBM bytes of the level per V(1,1) cycle */
+} amg_level_info;
+
+typedef struct amg_hierarchy amg_hierarchy;
+typedef struct amg_server amg_server;
+
+/* Fill *opt with the defaults listed above. */
+void amg_options_default(amg_options *opt);
+
+/*
+ * amg_setup -- Algorithm 1 (Galerkin hierarchy: classical strength, PMIS
+ * C/F splitting, direct interpolation, A_{l+1} = P_l^T A_l P_l), then
+ * Algorithm 4 (Sparse Galerkin sparsify with diagonal lumping, Algorithm 3b)
+ * with gamma_per_level, then the ell1-Jacobi diagonals and the coarsest-level
+ * Cholesky factor.  gamma_per_level[l] applies to level l; levels past
+ * n_gamma - 1 use the last value; gamma_per_level[0] must be 0 (level 0 is
+ * never sparsified); n_gamma = 0 (or NULL) means no sparsification.  `theta`
+ * overrides opt->theta.  A is copied (host or device); the hierarchy, owned
+ * by the library, is returned in *out and freed with amg_free.
+ * Errors: AMG_ERR_INVALID for a non-square, unsorted, non-symmetric-pattern
+ * matrix, a missing or non-positive diagonal, non-finite values or bad
+ * options; AMG_ERR_OOM; AMG_ERR_CUDA.
+ */
+amg_status amg_setup(const amg_csr *A, double theta, const double *gamma_per_level, int n_gamma,
+                     const amg_options *opt, void *stream, amg_hierarchy **out);
+
+/*
+ * amg_hierarchy_assemble -- build a hierarchy from given Galerkin operators
+ * A_0..A_{L-1}, interpolations P_0..P_{L-2} (ncols = n_{l+1}), C/F markers
+ * cf_0..cf_{L-2} (1 = C, -1 = F, host int8) and minimal-pattern flags
+ * inM_1..inM_{L-1} (host uint8 per stored entry of A_l; inM[0] is ignored),
+ * e.g. a hierarchy saved earlier or built by another code.  Then as
+ * amg_setup: sparsify, ell1 diagonals, Cholesky.  Errors as amg_setup.
+ */
+amg_status amg_hierarchy_assemble(int levels, const amg_csr *A, const amg_csr *P,
+                                  const int8_t *const *cf, const uint8_t *const *inM,
+                                  const double *gamma_per_level, int n_gamma,
+                                  const amg_options *opt, void *stream, amg_hierarchy **out);
+
+/* amg_sparsify -- re-run Algorithm 4 on the retained Galerkin operators with
+ * new drop tolerances (same gamma convention as amg_setup). */
+amg_status amg_sparsify(amg_hierarchy *h, const double *gamma_per_level, int n_gamma);
+
+/* amg_reintroduce -- one drop-tolerance update of Algorithm 5: from the
+ * finest level l >= 1 with gamma_l > 0, on s_levels levels, gamma <- gamma/10
+ * (0 below gamma_min), and those levels are re-sparsified from the retained
+ * Galerkin A_l.  *levels_changed (may be NULL) receives the number of levels
+ * changed (0: every gamma is already 0). */
+amg_status amg_reintroduce(amg_hierarchy *h, int s_levels, int *levels_changed);
+
+/*
+ * amg_solve -- PCG (FP64 recurrences, x0 = 0) preconditioned by one V(1,1)
+ * cycle (Algorithm 2) to ||b - A_0 x|| / ||b|| <= tol, at most max_it steps.
+ * adaptive != 0 runs Algorithm 5 around it (k_check, s_levels, gamma_min,
+ * rho_max from the options given at setup).  b and x are n-vectors, both host
+ * or both device: on_device says which.  In the FP32 precision modes the
+ * outer loop is flexible CG.  Returns the solve status (also in info->status).
+ */
+amg_status amg_solve(amg_hierarchy *h, const double *b, double *x, double tol, int max_it,
+                     int adaptive, int on_device, void *stream, amg_solve_info *info);
+
+/*
+ * amg_solve_batch -- k independent solves sharing one hierarchy; B and X are
+ * row-major n x k (column j = right-hand side j), host or device per
+ * on_device.  The V-cycle runs as a multi-right-hand-side SpMM; each column
+ * keeps its own CG scalars and stops on its own.  info_k has k entries.
+ */
+amg_status amg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double tol,
+                           int max_it, int on_device, void *stream, amg_solve_info *info_k);
+
+/* amg_precond_apply -- z = M r, one V(1,1) cycle; r, z: device n-vectors. */
+amg_status amg_precond_apply(amg_hierarchy *h, const double *r, double *z, void *stream);
+
+/* amg_num_levels / amg_level_stats -- hierarchy shape and per-level figures. */
+int amg_num_levels(const amg_hierarchy *h);
+amg_status amg_level_stats(const amg_hierarchy *h, int level, amg_level_info *out);
+
+/*
+ * amg_level_export -- copy one matrix of a level to host buffers.
+ * which: 0 Galerkin A_l, 1 relaxed operator Ahat_l, 2 P_l, 3 R_l = P_l^T.
+ * With rowptr == NULL only *nrows, *ncols, *nnz are returned (size query);
+ * otherwise rowptr (nrows+1), col and val (nnz) are filled.
+ */
+amg_status amg_level_export(const amg_hierarchy *h, int level, int which, int32_t *rowptr,
+                            int32_t *col, double *val, int64_t *nrows, int64_t *ncols,
+                            int64_t *nnz);
+
+/*
+ * amg_level_array -- copy a per-level array to a host buffer `out`:
+ * which 0: cf (int8, n; 1 = C, -1 = F), 1: keep mask (uint8 per entry of A_l),
+ * 2: inM (uint8 per entry of A_l), 3: ell1 diagonal (double, n),
+ * 4: strength flags (uint8 per entry of A_l).  *count receives the length.
+ */
+amg_status amg_level_array(const amg_hierarchy *h, int level, int which, void *out,
+                           int64_t *count);
+
+/* Per-kernel timing with CUDA events on the solve stream (off by default).
+ * amg_timing_get returns, for kernel class `kind` (0 fused pre-smooth +
+ * residual, 1 restrict, 2 prolong, 3 post-smooth, 4 coarse solve, 5 PCG
+ * A p + dot, 6 PCG vector update) on `level`, the number of timed launches,
+ * their total milliseconds and their algorithmic bytes. */
+amg_status amg_timing_enable(amg_hierarchy *h, int on);
+amg_status amg_timing_get(const amg_hierarchy *h, int kind, int level, int64_t *launches,
+                          double *total_ms, double *bytes);
+amg_status amg_timing_reset(amg_hierarchy *h);
+
+/* Save / load the Galerkin hierarchy, C/F markers, minimal-pattern flags and
+ * drop tolerances to a file (little-endian binary, documented in DESIGN). */
+amg_status amg_hierarchy_save(const amg_hierarchy *h, const char *path);
+amg_status amg_hierarchy_load(const char *path, const amg_options *opt, void *stream,
+                              amg_hierarchy **out);
+
+void amg_free(amg_hierarchy *h);
+const char *amg_status_str(amg_status s);
+const char *amg_last_error(void);
+
+/* Number of CUDA kernels this process has launched through the library so
+ * far (a diagnostic counter, e.g. to count the launches of one solve). */
+int64_t amg_kernel_launches(void);
+
+/* Device memory the library currently holds for hierarchies (bytes). */
+int64_t amg_device_bytes(const amg_hierarchy *h);
+
+/*
+ * Serving: a host thread owns a queue of solve requests against registered
+ * hierarchies.  Requests on one hierarchy are solved together as columns of
+ * one multi-right-hand-side solve; new requests join the running batch at the
+ * next iteration boundary when a column slot and device memory are free
+ * (continuous batching).  Each column's CG scalars are its own, so a result
+ * does not depend on what else is in the batch.
+ */
+typedef struct {
+    int max_batch;          /* column slots per hierarchy, default 32 */
+    int64_t hbm_budget;     /* bytes the server may allocate for batches; 0 = free HBM */
+    int max_queue;          /* pending requests before submits are rejected, default 4096 */
+    int max_it;             /* per request, default 500 */
+} amg_server_opts;
+
+void amg_server_opts_default(amg_server_opts *o);
+amg_status amg_server_create(const amg_server_opts *o, amg_server **out);
+/* The hierarchy stays owned by the caller and must outlive the server. */
+amg_status amg_server_register(amg_server *s, amg_hierarchy *h, int *hid);
+/* b: host n-vector, copied at submit.  Returns a ticket. */
+amg_status amg_server_submit(amg_server *s, int hid, const double *b, double tol,
+                             uint64_t *ticket);
+/* Waits up to timeout_ms for the ticket; x: host n-vector.  AMG_TIMEOUT if
+ * not finished in time (the request stays queued and can be waited again). */
+amg_status amg_server_wait(amg_server *s, uint64_t ticket, double *x, int timeout_ms,
+                           amg_solve_info *info);
+/* Stops the worker after the running batches finish; frees the server. */
+void amg_server_destroy(amg_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,110 @@
+// common.cuh -- internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/amg.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------------------
+// errors: internal code throws amg::Error; the C ABI turns it into a status.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+    amg_status status;
+    Error(amg_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+void set_last_error(const std::string &msg);
+
+// number of kernels the library has launched (diagnostic counter)
+void count_launch();
+
+#define AMG_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            if (e_ == cudaErrorMemoryAllocation) {                                         \
+                cudaGetLastError();                                                        \
+                throw ::amg::Error(AMG_ERR_OOM, std::string("device allocation: ") +      \
+                                                     cudaGetErrorString(e_));              \
+            }                                                                              \
+            throw ::amg::Error(AMG_ERR_CUDA, std::string(#call) + ": " +                   \
+                                                 cudaGetErrorString(e_) + " at " +         \
+                                                 __FILE__ + ":" + std::to_string(__LINE__)); \
+        }                                                                                  \
+    } while (0)
+
+#define AMG_CHECK_LAUNCH() AMG_CUDA(cudaGetLastError())
+
+inline void require(bool ok, const std::string &msg) {
+    if (!ok) throw Error(AMG_ERR_INVALID, msg);
+}
+
+// ---------------------------------------------------------------------------
+// device buffers (RAII); every persistent allocation of the library goes
+// through DevBuf so amg_device_bytes can account for it.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t b) { alloc(b); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : ptr(o.ptr), bytes(o.bytes) { o.ptr = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            ptr = o.ptr; bytes = o.bytes;
+            o.ptr = nullptr; o.bytes = 0;
+        }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t b);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// A CSR matrix resident on the device (library-owned).
+struct DevCSR {
+    int32_t nrows = 0, ncols = 0;
+    int64_t nnz = 0;
+    DevBuf rowptr, col, val;  // int32[nrows+1], int32[nnz(+pad)], double[nnz(+pad)]
+    const int32_t *rp() const { return rowptr.as<int32_t>(); }
+    const int32_t *ci() const { return col.as<int32_t>(); }
+    const double *v() const { return val.as<double>(); }
+    int32_t *rp() { return rowptr.as<int32_t>(); }
+    int32_t *ci() { return col.as<int32_t>(); }
+    double *v() { return val.as<double>(); }
+    size_t bytes() const { return rowptr.bytes + col.bytes + val.bytes; }
+    // allocate with `pad` spare entries so vector loads past the last row stay in bounds
+    void allocate(int32_t r, int32_t c, int64_t z);
+};
+
+constexpr int64_t kPad = 16;  // spare entries at the end of every CSR array
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+// exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
+int64_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+template <typename T> T read_scalar(const T *dptr, cudaStream_t s) {
+    T v;
+    AMG_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    return v;
+}
+
+}  // namespace amg

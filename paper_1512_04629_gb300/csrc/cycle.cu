@@ -1,0 +1,526 @@
+// cycle.cu -- V-cycle and PCG kernels.
+//
+// Every kernel here is a streaming pass over a sparse matrix or a few
+// vectors, so HBM bandwidth bounds it.  Two SpMV layouts serve all of them:
+//  * vector-CSR: a group of T lanes (T = 2..32) owns a row; each lane loads
+//    16-byte vectors of values and column indices (2 FP64 / 4 FP32 / 8 BF16
+//    entries) read through the non-coherent path, masks the entries outside
+//    its row, gathers x, and the group reduces with xor shuffles;
+//  * SELL-32: one thread per row, 32-row slices stored column-major so each
+//    warp load is one contiguous 128/256-byte segment.
+// Reductions for PCG are deterministic: fixed grid, per-block partials, and
+// the last block to arrive sums them in block order.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "cycle_ops.cuh"
+
+namespace amg {
+namespace cyc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT, typename XT> __device__ __forceinline__ XT cvt(VT v) { return (XT)v; }
+template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+// 16-byte vector loads of V consecutive entries
+template <typename VT> struct Vec;
+template <> struct Vec<double> {
+    static constexpr int V = 2;
+    __device__ __forceinline__ static void load(const double *v, const int32_t *c, int64_t q, double (&vv)[2], int32_t (&cc)[2]) {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(v + q));
+        int2 b = __ldg(reinterpret_cast<const int2 *>(c + q));
+        vv[0] = a.x; vv[1] = a.y; cc[0] = b.x; cc[1] = b.y;
+    }
+};
+template <> struct Vec<float> {
+    static constexpr int V = 4;
+    __device__ __forceinline__ static void load(const float *v, const int32_t *c, int64_t q, float (&vv)[4], int32_t (&cc)[4]) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(v + q));
+        int4 b = __ldg(reinterpret_cast<const int4 *>(c + q));
+        vv[0] = a.x; vv[1] = a.y; vv[2] = a.z; vv[3] = a.w;
+        cc[0] = b.x; cc[1] = b.y; cc[2] = b.z; cc[3] = b.w;
+    }
+};
+template <> struct Vec<__nv_bfloat16> {
+    static constexpr int V = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *v, const int32_t *c, int64_t q,
+                                                __nv_bfloat16 (&vv)[8], int32_t (&cc)[8]) {
+        uint4 a = __ldg(reinterpret_cast<const uint4 *>(v + q));
+        int4 b0 = __ldg(reinterpret_cast<const int4 *>(c + q));
+        int4 b1 = __ldg(reinterpret_cast<const int4 *>(c + q + 4));
+        const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&a);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) vv[u] = h[u];
+        cc[0] = b0.x; cc[1] = b0.y; cc[2] = b0.z; cc[3] = b0.w;
+        cc[4] = b1.x; cc[5] = b1.y; cc[6] = b1.z; cc[7] = b1.w;
+    }
+};
+
+// sum over one CSR row by a group of T lanes (all lanes get the sum)
+template <typename VT, typename XT, int T, class G>
+__device__ __forceinline__ XT csr_row_sum(int32_t p0, int32_t p1, int t, const int32_t *__restrict__ ci,
+                                          const VT *__restrict__ v, G gather) {
+    constexpr int V = Vec<VT>::V;
+    XT acc = XT(0);
+    for (int32_t q = (p0 & ~(V - 1)) + t * V; q < p1; q += T * V) {
+        VT vv[V];
+        int32_t cc[V];
+        Vec<VT>::load(v, ci, q, vv, cc);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            int32_t e = q + u;
+            if (e >= p0 && e < p1) acc += cvt<VT, XT>(vv[u]) * gather(cc[u]);
+        }
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, T);
+    return acc;
+}
+
+template <typename VT, typename XT, class G>
+__device__ __forceinline__ XT sell_row_sum(int32_t i, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
+                                           const int32_t *__restrict__ sci, const VT *__restrict__ sv, G gather) {
+    int32_t s = i >> 5, lane = i & 31;
+    int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
+    XT acc = XT(0);
+#pragma unroll 4
+    for (int32_t k = 0; k < w; ++k) {
+        int32_t p = off + k * 32;
+        acc += cvt<VT, XT>(__ldg(sv + p)) * gather(__ldg(sci + p));
+    }
+    return acc;
+}
+
+enum Op { kPre = 0, kPost = 1, kSpmv = 2, kSpmvAdd = 3 };
+
+template <typename VT, typename XT, int T, int OP>
+__global__ void __launch_bounds__(kThreads)
+csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const VT *__restrict__ v,
+              const XT *__restrict__ b, const XT *__restrict__ dinv, const XT *__restrict__ x,
+              XT *__restrict__ o1, XT *__restrict__ o2) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t i = (int32_t)(g / T);
+    int t = (int)(g % T);
+    int32_t p0 = 0, p1 = 0;
+    if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+    XT s;
+    if (OP == kPre) s = csr_row_sum<VT, XT, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = csr_row_sum<VT, XT, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+    if (i >= n || t != 0) return;
+    if (OP == kPre) {
+        XT bi = b[i];
+        o1[i] = bi * dinv[i];
+        o2[i] = bi - s;
+    } else if (OP == kPost) {
+        o1[i] = x[i] + dinv[i] * (b[i] - s);
+    } else if (OP == kSpmv) {
+        o1[i] = s;
+    } else {
+        o1[i] += s;
+    }
+}
+
+template <typename VT, typename XT, int OP>
+__global__ void __launch_bounds__(kThreads)
+sell_op_kernel(int32_t n, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw, const int32_t *__restrict__ sci,
+               const VT *__restrict__ sv, const XT *__restrict__ b, const XT *__restrict__ dinv,
+               const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    XT s;
+    if (OP == kPre) s = sell_row_sum<VT, XT>(i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT>(i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) {
+        XT bi = b[i];
+        o1[i] = bi * dinv[i];
+        o2[i] = bi - s;
+    } else if (OP == kPost) {
+        o1[i] = x[i] + dinv[i] * (b[i] - s);
+    } else if (OP == kSpmv) {
+        o1[i] = s;
+    } else {
+        o1[i] += s;
+    }
+}
+
+template <typename VT, typename XT, int OP>
+void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, XT *o1, XT *o2, cudaStream_t s) {
+    int32_t n = A.nrows;
+    if (n == 0) return;
+    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+        { sell_op_kernel<VT, XT, OP><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.soff, A.sw, A.sci, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    } else {
+        int T = threads_per_row(A.variant);
+        int blocks = div_up((int64_t)n * T, kThreads);
+        switch (T) {
+            case 2: { csr_op_kernel<VT, XT, 2, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 4: { csr_op_kernel<VT, XT, 4, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 8: { csr_op_kernel<VT, XT, 8, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 16: { csr_op_kernel<VT, XT, 16, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            default: { csr_op_kernel<VT, XT, 32, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+        }
+    }
+    AMG_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// deterministic block reduction with last-block finish
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV]) {
+    __shared__ double sh[NV][kThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][w] = x;
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = lane < kThreads / 32 ? sh[k][lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            v[k] = x;
+        }
+    }
+    __syncthreads();
+}
+
+// Every block adds its partials; the last block to arrive reduces all of
+// them in block order and returns true (thread 0 holds the totals).
+template <int NV>
+__device__ bool reduce_and_finish(double (&v)[NV], Reduce red) {
+    block_reduce<NV>(v);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red.partials[k * kMaxReduceBlocks + blockIdx.x] = v[k];
+        __threadfence();
+        unsigned prev = atomicAdd(red.counter, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double t[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        t[k] = 0.0;
+        for (int bI = threadIdx.x; bI < (int)gridDim.x; bI += kThreads)
+            t[k] += ((volatile double *)red.partials)[k * kMaxReduceBlocks + bI];
+    }
+    block_reduce<NV>(t);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = t[k];
+        *red.counter = 0u;
+    }
+    return true;
+}
+
+int reduce_blocks(int64_t n, int per_thread = 1) {
+    int64_t b = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+    if (b < 1) b = 1;
+    if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// PCG kernels (FP64)
+// ---------------------------------------------------------------------------
+__global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double *__restrict__ p,
+                                const PcgScalars *sc, int first) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    p[i] = first ? z[i] : z[i] + sc->beta * p[i];
+}
+
+// q = A p (vector-CSR, T lanes per row) and p . q
+template <int T>
+__global__ void __launch_bounds__(kThreads)
+ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+          const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    double part[1] = {0.0};
+    int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T; g += stride) {
+        int32_t i = (int32_t)(g / T);
+        int t = (int)(g % T);
+        int32_t p0 = 0, p1 = 0;
+        if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(p + j); });
+        if (i < n && t == 0) {
+            q[i] = s;
+            part[0] += p[i] * s;
+        }
+    }
+    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
+        sc->pq = part[0];
+        sc->alpha = sc->rho / part[0];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
+                 double *__restrict__ r, PcgScalars *sc, Reduce red) {
+    double alpha = sc->alpha;
+    double part[1] = {0.0};
+    for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+        x[i] += alpha * p[i];
+        double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        part[0] += ri * ri;
+    }
+    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) sc->rr = part[0];
+}
+
+__global__ void __launch_bounds__(kThreads)
+rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ q,
+          PcgScalars *sc, Reduce red, int first) {
+    double part[2] = {0.0, 0.0};
+    for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+        double zi = z[i];
+        part[0] += r[i] * zi;
+        if (!first) part[1] += zi * q[i];
+    }
+    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) {
+        double rho_new = part[0];
+        if (!first) {
+            sc->zq = part[1];
+            sc->beta = sc->flexible ? (-sc->alpha * part[1]) / sc->rho : rho_new / sc->rho;
+        } else {
+            sc->beta = 0.0;
+        }
+        sc->rho = rho_new;
+    }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kThreads)
+resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+             const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ t_out,
+             PcgScalars *sc, Reduce red) {
+    double part[1] = {0.0};
+    int64_t stride = (int64_t)gridDim.x * kThreads;
+    for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T; g += stride) {
+        int32_t i = (int32_t)(g / T);
+        int t = (int)(g % T);
+        int32_t p0 = 0, p1 = 0;
+        if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        if (i < n && t == 0) {
+            double e = b[i] - s;
+            t_out[i] = e;
+            part[0] += e * e;
+        }
+    }
+    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) sc->tt = part[0];
+}
+
+// ---------------------------------------------------------------------------
+// coarse solve: x = inv b, one warp per row
+// ---------------------------------------------------------------------------
+template <typename XT>
+__global__ void coarse_kernel(int32_t n, const double *__restrict__ inv, const XT *__restrict__ b, XT *__restrict__ x) {
+    int lane = threadIdx.x & 31;
+    int32_t row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (row >= n) return;
+    double s = 0.0;
+    for (int32_t j = lane; j < n; j += 32) s += inv[(size_t)row * n + j] * (double)b[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = (XT)s;
+}
+
+// ---------------------------------------------------------------------------
+// conversions and SELL construction
+// ---------------------------------------------------------------------------
+template <typename VT>
+__global__ void convert_kernel(const double *src, VT *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (VT)src[i];
+}
+template <>
+__global__ void convert_kernel<__nv_bfloat16>(const double *src, __nv_bfloat16 *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __double2bfloat16(src[i]);
+}
+
+template <typename XT>
+__global__ void to_f64_kernel(const XT *src, double *dst, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+__global__ void slice_width_kernel(int32_t n, const int32_t *rp, int32_t *sw) {
+    int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t nsl = (n + 31) / 32;
+    if (s >= nsl) return;
+    int32_t w = 0;
+    for (int32_t i = s * 32; i < min(n, s * 32 + 32); ++i) w = max(w, rp[i + 1] - rp[i]);
+    sw[s] = w;
+}
+
+__global__ void slice_size_kernel(int32_t nsl, const int32_t *sw, int32_t *sz) {
+    int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < nsl) sz[s] = sw[s] * 32;
+}
+
+template <typename VT>
+__global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v,
+                                 const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t nsl = (n + 31) / 32;
+    if (i >= nsl * 32) return;
+    int32_t s = i >> 5, lane = i & 31;
+    int32_t off = soff[s] + lane, w = sw[s];
+    int32_t p0 = i < n ? rp[i] : 0, len = i < n ? rp[i + 1] - p0 : 0;
+    int32_t self = i < n ? i : 0;
+    for (int32_t k = 0; k < w; ++k) {
+        int32_t p = off + k * 32;
+        if (k < len) { sci[p] = ci[p0 + k]; sv[p] = v[p0 + k]; }
+        else { sci[p] = self; sv[p] = VT(0); }
+    }
+}
+
+}  // namespace
+
+int threads_per_row(int variant) {
+    switch (variant) {
+        case AMG_SPMV_CSR2: return 2;
+        case AMG_SPMV_CSR4: return 4;
+        case AMG_SPMV_CSR8: return 8;
+        case AMG_SPMV_CSR16: return 16;
+        case AMG_SPMV_CSR32: return 32;
+        default: return 4;
+    }
+}
+
+template <typename VT, typename XT>
+void pre_smooth_residual(const CycMat<VT> &A, const XT *b, const XT *dinv, XT *x, XT *r, cudaStream_t s) {
+    dispatch_op<VT, XT, kPre>(A, b, dinv, nullptr, x, r, s);
+}
+template <typename VT, typename XT>
+void post_smooth(const CycMat<VT> &A, const XT *x, const XT *b, const XT *dinv, XT *xo, cudaStream_t s) {
+    dispatch_op<VT, XT, kPost>(A, b, dinv, x, xo, nullptr, s);
+}
+template <typename VT, typename XT>
+void spmv(const CycMat<VT> &A, const XT *x, XT *y, bool accumulate, cudaStream_t s) {
+    if (accumulate) dispatch_op<VT, XT, kSpmvAdd>(A, nullptr, nullptr, x, y, nullptr, s);
+    else dispatch_op<VT, XT, kSpmv>(A, nullptr, nullptr, x, y, nullptr, s);
+}
+
+template <typename XT>
+void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t s) {
+    if (n == 0) return;
+    { coarse_kernel<XT><<<div_up(n, 8), 256, 0, s>>>(n, inv, b, x); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, bool first, cudaStream_t s) {
+    { p_update_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, z, p, sc, first ? 1 : 0); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+template <int T>
+static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    int blocks = reduce_blocks((int64_t)A.nrows * T, 4);
+    { ap_kernel<T><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, p, q, sc, red); ::amg::count_launch(); }
+}
+
+void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    switch (threads_per_row(A.variant == AMG_SPMV_SELL32 ? AMG_SPMV_CSR4 : A.variant)) {
+        case 2: launch_ap<2>(A, p, q, sc, red, s); break;
+        case 4: launch_ap<4>(A, p, q, sc, red, s); break;
+        case 8: launch_ap<8>(A, p, q, sc, red, s); break;
+        case 16: launch_ap<16>(A, p, q, sc, red, s); break;
+        default: launch_ap<32>(A, p, q, sc, red, s); break;
+    }
+    AMG_CHECK_LAUNCH();
+}
+
+void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
+                   Reduce red, cudaStream_t s) {
+    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
+            bool first, cudaStream_t s) {
+    { rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, r, z, q, sc, red, first ? 1 : 0); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
+                   Reduce red, cudaStream_t s) {
+    int blocks = reduce_blocks((int64_t)A.nrows * 4, 4);
+    { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+template <typename VT> void convert_values(const double *src, VT *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    { convert_kernel<VT><<<div_up(n, kThreads), kThreads, 0, s>>>(src, dst, n); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+template <typename XT> void convert_vec_from_f64(const double *src, XT *dst, int64_t n, cudaStream_t s) {
+    convert_values<XT>(src, dst, n, s);
+}
+template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    { to_f64_kernel<XT><<<div_up(n, kThreads), kThreads, 0, s>>>(src, dst, n); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *soff, int32_t *sw, cudaStream_t s) {
+    int32_t nsl = (n + 31) / 32;
+    if (nsl == 0) return 0;
+    DevBuf sz(sizeof(int32_t) * (nsl + 1));
+    { slice_width_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(n, rp, sw); ::amg::count_launch(); }
+    { slice_size_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(nsl, sw, sz.as<int32_t>()); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+    return exclusive_scan_i32(sz.as<int32_t>(), soff, nsl, s);
+}
+
+template <typename VT>
+void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *soff,
+               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s) {
+    int32_t nsl = (n + 31) / 32;
+    if (nsl == 0) return;
+    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, soff, sw, sci, sv); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+// explicit instantiations
+#define AMG_INST(VT, XT)                                                                                  \
+    template void pre_smooth_residual<VT, XT>(const CycMat<VT> &, const XT *, const XT *, XT *, XT *, cudaStream_t); \
+    template void post_smooth<VT, XT>(const CycMat<VT> &, const XT *, const XT *, const XT *, XT *, cudaStream_t); \
+    template void spmv<VT, XT>(const CycMat<VT> &, const XT *, XT *, bool, cudaStream_t);
+AMG_INST(double, double)
+AMG_INST(float, float)
+AMG_INST(__nv_bfloat16, float)
+#undef AMG_INST
+template void coarse_solve<double>(int32_t, const double *, const double *, double *, cudaStream_t);
+template void coarse_solve<float>(int32_t, const double *, const float *, float *, cudaStream_t);
+template void convert_values<float>(const double *, float *, int64_t, cudaStream_t);
+template void convert_values<__nv_bfloat16>(const double *, __nv_bfloat16 *, int64_t, cudaStream_t);
+template void convert_vec_from_f64<float>(const double *, float *, int64_t, cudaStream_t);
+template void convert_vec_to_f64<float>(const float *, double *, int64_t, cudaStream_t);
+template void sell_fill<double>(int32_t, const int32_t *, const int32_t *, const double *, const int32_t *,
+                                const int32_t *, int32_t *, double *, cudaStream_t);
+template void sell_fill<float>(int32_t, const int32_t *, const int32_t *, const float *, const int32_t *,
+                               const int32_t *, int32_t *, float *, cudaStream_t);
+template void sell_fill<__nv_bfloat16>(int32_t, const int32_t *, const int32_t *, const __nv_bfloat16 *,
+                                       const int32_t *, const int32_t *, int32_t *, __nv_bfloat16 *, cudaStream_t);
+
+}  // namespace cyc
+}  // namespace amg

@@ -1,0 +1,78 @@
+// cycle_ops.cuh -- solve-phase kernels (cycle.cu): SpMV-based relaxation,
+// restriction, interpolation, coarse solve, PCG vector kernels.
+#pragma once
+#include "common.cuh"
+
+namespace amg {
+
+// A matrix as the cycle kernels read it: CSR in value type VT, plus an
+// optional SELL-32 copy (slices of 32 rows, column-major inside a slice).
+template <typename VT> struct CycMat {
+    int32_t nrows = 0, ncols = 0;
+    int64_t nnz = 0;
+    const int32_t *rp = nullptr, *ci = nullptr;
+    const VT *v = nullptr;
+    int32_t nslices = 0;
+    const int32_t *soff = nullptr, *sw = nullptr, *sci = nullptr;
+    const VT *sv = nullptr;
+    int variant = AMG_SPMV_CSR4;
+};
+
+// Device-side scalars of one PCG run.
+struct PcgScalars {
+    double rho;      // r . z
+    double pq;       // p . A p
+    double alpha, beta;
+    double rr;       // r . r after the update
+    double zq;       // z . q (flexible CG)
+    double tt;       // ||b - A x||^2 of the last true-residual check
+    int flexible;
+    int pad;
+};
+
+// Deterministic reduction workspace: per-block partials + arrival counter.
+struct Reduce {
+    double *partials = nullptr;  // 2 * kMaxReduceBlocks
+    unsigned *counter = nullptr;
+};
+constexpr int kMaxReduceBlocks = 1024;
+
+namespace cyc {
+
+int threads_per_row(int variant);
+
+// relaxation and transfers (XT = vector type, VT = matrix value type)
+template <typename VT, typename XT>
+void pre_smooth_residual(const CycMat<VT> &A, const XT *b, const XT *dinv, XT *x, XT *r, cudaStream_t s);
+template <typename VT, typename XT>
+void post_smooth(const CycMat<VT> &A, const XT *x, const XT *b, const XT *dinv, XT *xo, cudaStream_t s);
+template <typename VT, typename XT>
+void spmv(const CycMat<VT> &A, const XT *x, XT *y, bool accumulate, cudaStream_t s);
+
+// coarsest level: x = inv * b (dense, FP64 inverse)
+template <typename XT>
+void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t s);
+
+// PCG (FP64)
+void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, bool first, cudaStream_t s);
+void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s);
+void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
+                   Reduce red, cudaStream_t s);
+void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
+            bool first, cudaStream_t s);
+// t = b - A x, sc->tt = ||t||^2; if `replace`, r = t
+void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
+                   Reduce red, cudaStream_t s);
+
+// precision conversion and SELL construction
+template <typename VT> void convert_values(const double *src, VT *dst, int64_t n, cudaStream_t s);
+template <typename XT> void convert_vec_from_f64(const double *src, XT *dst, int64_t n, cudaStream_t s);
+template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64_t n, cudaStream_t s);
+// slice widths and offsets; returns padded entry count
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *soff, int32_t *sw, cudaStream_t s);
+template <typename VT>
+void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *soff,
+               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s);
+
+}  // namespace cyc
+}  // namespace amg

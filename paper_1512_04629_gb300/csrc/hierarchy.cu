@@ -1,0 +1,579 @@
+// hierarchy.cu -- setup driver (Algorithm 1), Sparse Galerkin sparsify
+// (Algorithm 4 with Algorithm 3b), cycle preparation and autotuning, the
+// V-cycle (Algorithm 2), PCG and the adaptive solve (Algorithm 5).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "cycle_ops.cuh"
+#include "hierarchy.cuh"
+#include "setup_ops.cuh"
+
+namespace amg {
+
+Hierarchy::~Hierarchy() {
+    if (g_update) cudaGraphExecDestroy(g_update);
+    if (g_precond) cudaGraphExecDestroy(g_precond);
+    for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : event_pool) cudaEventDestroy(e);
+    if (h_scal) cudaFreeHost(h_scal);
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 (sparsify off): strength, PMIS, direct interpolation, Galerkin
+// product, and the minimal-pattern flags of each coarse operator.
+// Stop: n_l <= max_size, max_levels reached, or |C| = 0 or |C| > 0.9 n_l.
+// ---------------------------------------------------------------------------
+static void init_level_maps(Level &V, cudaStream_t s) {
+    V.diagpos.alloc(sizeof(int32_t) * (V.A.nrows + 1));
+    V.tpos.alloc(sizeof(int32_t) * (V.A.nnz + 1));
+    setup::validate(V.A, V.diagpos.as<int32_t>(), s);
+    setup::transpose_positions(V.A, V.tpos.as<int32_t>(), s);
+    V.keep.alloc(V.A.nnz + kPad);
+}
+
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
+    (void)A0in;
+    const amg_options &o = h.opt;
+    for (int l = 0;; ++l) {
+        Level &V = *h.lev[l];
+        if (l == 0) init_level_maps(V, s);
+        int32_t n = V.A.nrows;
+        if (n <= o.max_size || l + 1 >= o.max_levels) break;
+        V.strong.alloc(V.A.nnz + kPad);
+        V.cf.alloc(n + kPad);
+        setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s);
+        int64_t nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed,
+                                 o.level_offset + l, V.cf.as<int8_t>(), s);
+        if (nc == 0 || (double)nc > 0.9 * (double)n) {
+            V.strong.release();
+            V.cf.release();
+            break;
+        }
+        V.cmap.alloc(sizeof(int32_t) * (n + 1));
+        V.cpts.alloc(sizeof(int32_t) * (nc + 1));
+        setup::coarse_map(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
+        setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
+                             (int32_t)nc, V.P, s);
+        setup::transpose(V.P, V.R, s);
+        DevCSR AP;
+        setup::spgemm(V.A, V.P, AP, s);
+        auto C = std::make_unique<Level>();
+        setup::spgemm(V.R, AP, C->A, s);
+        init_level_maps(*C, s);
+        C->inM.alloc(C->A.nnz + kPad);
+        setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+        h.lev.push_back(std::move(C));
+    }
+}
+
+// Levels given by the caller (amg_hierarchy_assemble / load).
+void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &P,
+                     const std::vector<std::vector<int8_t>> &cf,
+                     const std::vector<std::vector<uint8_t>> &inM, cudaStream_t s) {
+    int L = (int)A.size();
+    for (int l = 0; l < L; ++l) {
+        auto V = std::make_unique<Level>();
+        V->A = std::move(A[l]);
+        init_level_maps(*V, s);
+        if (l + 1 < L) {
+            require(P[l].nrows == V->A.nrows && P[l].ncols == A[l + 1].nrows,
+                    "assemble: P_l must be n_l x n_{l+1}");
+            V->P = std::move(P[l]);
+            setup::transpose(V->P, V->R, s);
+            require((int64_t)cf[l].size() == V->A.nrows, "assemble: cf_l has the wrong length");
+            V->cf.alloc(V->A.nrows + kPad);
+            AMG_CUDA(cudaMemcpyAsync(V->cf.ptr, cf[l].data(), cf[l].size(), cudaMemcpyHostToDevice, s));
+        }
+        if (l > 0) {
+            require((int64_t)inM[l].size() == V->A.nnz, "assemble: inM_l has the wrong length");
+            V->inM.alloc(V->A.nnz + kPad);
+            AMG_CUDA(cudaMemcpyAsync(V->inM.ptr, inM[l].data(), inM[l].size(), cudaMemcpyHostToDevice, s));
+        }
+        h.lev.push_back(std::move(V));
+    }
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 4 (Sparse Galerkin), Algorithm 3 / 3b per level
+// ---------------------------------------------------------------------------
+void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
+    Level &V = *h.lev[l];
+    if (l == 0 || V.gamma == 0.0) {
+        V.H = DevCSR();
+        V.h_alias = true;
+        AMG_CUDA(cudaMemsetAsync(V.keep.ptr, 1, V.A.nnz, s));
+        return;
+    }
+    DevCSR H;
+    setup::sparsify(V.A, V.inM.as<uint8_t>(), V.tpos.as<int32_t>(), V.diagpos.as<int32_t>(), V.gamma,
+                    V.keep.as<uint8_t>(), H, s);
+    V.H = std::move(H);
+    V.h_alias = false;
+}
+
+void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s) {
+    for (int l = 0; l < h.nlev(); ++l) {
+        double g = 0.0;
+        if (l > 0 && n_gamma > 0 && gamma) g = gamma[std::min(l, n_gamma - 1)];
+        h.lev[l]->gamma = g;
+        resparsify_level(h, l, s);
+    }
+}
+
+// Algorithm 5 drop-tolerance update (finest level >= 1 with gamma > 0, s
+// levels, gamma/10 or 0 below gamma_min) and re-sparsify from the retained
+// Galerkin operators.  Returns the number of levels changed.
+int reintroduce(Hierarchy &h, int s_levels, cudaStream_t s) {
+    int L = h.nlev();
+    int lstart = -1;
+    for (int l = 1; l < L; ++l)
+        if (h.lev[l]->gamma > 0.0) { lstart = l; break; }
+    if (lstart < 0) return 0;
+    std::vector<int> changed;
+    for (int l = lstart; l < lstart + s_levels && l < L; ++l) {
+        double g = h.lev[l]->gamma / 10.0;
+        h.lev[l]->gamma = (g >= h.opt.gamma_min * (1.0 - 1e-12)) ? g : 0.0;
+        resparsify_level(h, l, s);
+        changed.push_back(l);
+    }
+    prepare_cycle(h, s, changed);
+    return (int)changed.size();
+}
+
+// ---------------------------------------------------------------------------
+// cycle preparation: ell1 diagonals, precision copies, SELL, autotuning
+// ---------------------------------------------------------------------------
+static int heuristic_variant(const DevCSR &M) {
+    double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
+    if (mean <= 3.0) return AMG_SPMV_CSR2;
+    if (mean <= 8.0) return AMG_SPMV_CSR4;
+    if (mean <= 20.0) return AMG_SPMV_CSR8;
+    if (mean <= 48.0) return AMG_SPMV_CSR16;
+    return AMG_SPMV_CSR32;
+}
+
+template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
+    const DevCSR &M = V.op();
+    int32_t nsl = (M.nrows + 31) / 32;
+    V.soff.alloc(sizeof(int32_t) * (nsl + 1));
+    V.sw.alloc(sizeof(int32_t) * (nsl + 1));
+    V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), V.soff.as<int32_t>(), V.sw.as<int32_t>(), s);
+    V.sci.alloc(sizeof(int32_t) * (V.sell_entries + kPad));
+    V.sv.alloc(sizeof(VT) * (V.sell_entries + kPad));
+    CycMat<VT> m = op_mat<VT>(V);
+    cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), m.v, V.soff.as<int32_t>(), V.sw.as<int32_t>(),
+                       V.sci.as<int32_t>(), V.sv.as<VT>(), s);
+}
+
+static void free_sell(Level &V) {
+    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release();
+    V.sell_entries = 0;
+}
+
+// time the post-smoothing kernel of one level under each variant; keep the fastest
+template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Level &V, cudaStream_t s) {
+    const int cands[] = {AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16, AMG_SPMV_CSR32, AMG_SPMV_SELL32};
+    cudaEvent_t e0, e1;
+    AMG_CUDA(cudaEventCreate(&e0));
+    AMG_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_v = V.variant;
+    const XT *dinv = sizeof(XT) == 8 ? reinterpret_cast<const XT *>(V.dinv.ptr) : V.dinv32.as<XT>();
+    for (int c : cands) {
+        V.variant = c;
+        CycMat<VT> m = op_mat<VT>(V);
+        cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);  // warm-up
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            AMG_CUDA(cudaEventRecord(e0, s));
+            cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);
+            AMG_CUDA(cudaEventRecord(e1, s));
+            AMG_CUDA(cudaEventSynchronize(e1));
+            float ms;
+            AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            tmin = std::min(tmin, ms);
+        }
+        if (tmin < best * 0.98f) { best = tmin; best_v = c; }
+    }
+    V.variant = best_v;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)h;
+}
+
+template <typename T> static void alloc_zero(DevBuf &b, int64_t n, cudaStream_t s) {
+    b.alloc(sizeof(T) * (size_t)(n + kPad));
+    AMG_CUDA(cudaMemsetAsync(b.ptr, 0, b.bytes, s));
+}
+
+static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
+    Level &V = *h.lev[l];
+    const DevCSR &M = V.op();
+    int32_t n = V.n();
+    int prec = h.opt.precision;
+    V.l1.alloc(sizeof(double) * (n + kPad));
+    V.dinv.alloc(sizeof(double) * (n + kPad));
+    setup::l1_diag(M, V.l1.as<double>(), V.dinv.as<double>(), s);
+    V.vbytes = prec == AMG_PREC_FP64 ? 8 : (prec == AMG_PREC_FP32_BF16 && l >= 2 ? 2 : 4);
+    V.hv32.release();
+    V.hv16.release();
+    V.dinv32.release();
+    free_sell(V);
+    bool has_p = l + 1 < h.nlev();
+    if (prec == AMG_PREC_FP64) {
+        alloc_zero<double>(V.b, n, s); alloc_zero<double>(V.x, n, s);
+        alloc_zero<double>(V.r, n, s); alloc_zero<double>(V.xo, n, s);
+    } else {
+        alloc_zero<float>(V.b, n, s); alloc_zero<float>(V.x, n, s);
+        alloc_zero<float>(V.r, n, s); alloc_zero<float>(V.xo, n, s);
+        V.dinv32.alloc(sizeof(float) * (n + kPad));
+        cyc::convert_values<float>(V.dinv.as<double>(), V.dinv32.as<float>(), n, s);
+        if (V.vbytes == 4) {
+            V.hv32.alloc(sizeof(float) * (M.nnz + kPad));
+            AMG_CUDA(cudaMemsetAsync(V.hv32.ptr, 0, V.hv32.bytes, s));
+            cyc::convert_values<float>(M.v(), V.hv32.as<float>(), M.nnz, s);
+        } else {
+            V.hv16.alloc(sizeof(__nv_bfloat16) * (M.nnz + kPad));
+            AMG_CUDA(cudaMemsetAsync(V.hv16.ptr, 0, V.hv16.bytes, s));
+            cyc::convert_values<__nv_bfloat16>(M.v(), V.hv16.as<__nv_bfloat16>(), M.nnz, s);
+        }
+        if (has_p && !V.pv32.ptr) {
+            V.pv32.alloc(sizeof(float) * (V.P.nnz + kPad));
+            V.rv32.alloc(sizeof(float) * (V.R.nnz + kPad));
+            AMG_CUDA(cudaMemsetAsync(V.pv32.ptr, 0, V.pv32.bytes, s));
+            AMG_CUDA(cudaMemsetAsync(V.rv32.ptr, 0, V.rv32.bytes, s));
+            cyc::convert_values<float>(V.P.v(), V.pv32.as<float>(), V.P.nnz, s);
+            cyc::convert_values<float>(V.R.v(), V.rv32.as<float>(), V.R.nnz, s);
+        }
+    }
+    if (has_p) {
+        V.variant_p = heuristic_variant(V.P);
+        V.variant_r = heuristic_variant(V.R);
+    }
+    // relaxation SpMV variant
+    int forced = h.opt.spmv_variant;
+    bool tune = forced == AMG_SPMV_AUTO && M.nnz >= 20000 && has_p;
+    V.variant = forced == AMG_SPMV_AUTO ? heuristic_variant(M) : forced;
+    if (tune || V.variant == AMG_SPMV_SELL32) {
+        if (V.vbytes == 8) build_sell<double>(V, s);
+        else if (V.vbytes == 4) build_sell<float>(V, s);
+        else build_sell<__nv_bfloat16>(V, s);
+    }
+    if (tune) {
+        if (V.vbytes == 8) autotune_level<double, double>(h, V, s);
+        else if (V.vbytes == 4) autotune_level<float, float>(h, V, s);
+        else autotune_level<__nv_bfloat16, float>(h, V, s);
+        if (V.variant != AMG_SPMV_SELL32) free_sell(V);
+    }
+    if (l == h.nlev() - 1) {
+        h.coarse_n = n;
+        h.coarse_inv.alloc(sizeof(double) * ((size_t)n * n + kPad));
+        setup::cholesky_inverse(M, h.coarse_inv.as<double>(), s);
+    }
+}
+
+void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
+    for (int l : levels) prepare_level(h, l, s);
+    h.graph_dirty = true;
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+void ensure_workspace(Hierarchy &h, cudaStream_t s) {
+    int64_t n = h.lev[0]->n();
+    if (h.ws_n == n) return;
+    alloc_zero<double>(h.pb, n, s); alloc_zero<double>(h.px, n, s);
+    alloc_zero<double>(h.pr, n, s); alloc_zero<double>(h.pz, n, s);
+    alloc_zero<double>(h.pp, n, s); alloc_zero<double>(h.pq, n, s);
+    alloc_zero<double>(h.pt, n, s);
+    if (h.opt.precision != AMG_PREC_FP64) {
+        alloc_zero<float>(h.r32, n, s);
+        alloc_zero<float>(h.z32, n, s);
+    }
+    h.scal.alloc(sizeof(PcgScalars));
+    AMG_CUDA(cudaMemsetAsync(h.scal.ptr, 0, sizeof(PcgScalars), s));
+    h.partials.alloc(sizeof(double) * 4 * kMaxReduceBlocks);
+    h.counter.alloc(sizeof(unsigned) * 4);
+    AMG_CUDA(cudaMemsetAsync(h.counter.ptr, 0, h.counter.bytes, s));
+    if (!h.h_scal) AMG_CUDA(cudaMallocHost(&h.h_scal, sizeof(PcgScalars)));
+    h.ws_n = n;
+}
+
+// ---------------------------------------------------------------------------
+// algorithmic bytes (compulsory HBM traffic) per kernel launch
+// ---------------------------------------------------------------------------
+static double bytes_pre(int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + 4.0 * n * xb; }
+static double bytes_post(int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + 4.0 * n * xb; }
+static double bytes_restrict(int64_t nc, int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (nc + 1) + (double)(n + nc) * xb; }
+static double bytes_prolong(int64_t n, int64_t nc, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + (double)(nc + 2 * n) * xb; }
+
+double level_cycle_bytes(const Hierarchy &h, int l) {
+    const Level &V = *h.lev[l];
+    int xb = h.opt.precision == AMG_PREC_FP64 ? 8 : 4;
+    int64_t n = V.n(), nnz = V.op().nnz;
+    if (l == h.nlev() - 1) return (double)n * n * 8 + 2.0 * n * xb;
+    double b = bytes_pre(n, nnz, V.vbytes, xb) + bytes_post(n, nnz, V.vbytes, xb);
+    b += bytes_restrict(V.R.nrows, n, V.R.nnz, xb, xb) + bytes_prolong(n, V.P.ncols, V.P.nnz, xb, xb);
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel timing with events on the launching stream
+// ---------------------------------------------------------------------------
+static cudaEvent_t get_event(Hierarchy &h) {
+    if (!h.event_pool.empty()) {
+        cudaEvent_t e = h.event_pool.back();
+        h.event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    AMG_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+template <class F> static void timed(Hierarchy &h, int kind, int level, double bytes, cudaStream_t s, F &&f) {
+    if (!h.timing) { f(); return; }
+    PendingEvent pe{kind, level, bytes, get_event(h), get_event(h)};
+    AMG_CUDA(cudaEventRecord(pe.a, s));
+    f();
+    AMG_CUDA(cudaEventRecord(pe.b, s));
+    h.pending.push_back(pe);
+}
+
+void timing_collect(Hierarchy &h) {
+    for (auto &pe : h.pending) {
+        AMG_CUDA(cudaEventSynchronize(pe.b));
+        float ms = 0.f;
+        AMG_CUDA(cudaEventElapsedTime(&ms, pe.a, pe.b));
+        if (pe.kind >= 0 && pe.kind < kTimingKinds && pe.level >= 0 && pe.level < kMaxLevels) {
+            Timing &t = h.timers[pe.kind][pe.level];
+            t.launches++;
+            t.ms += ms;
+            t.bytes += pe.bytes;
+        }
+        h.event_pool.push_back(pe.a);
+        h.event_pool.push_back(pe.b);
+    }
+    h.pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2: V(1,1) on the residual equation, zero initial guess per level
+// ---------------------------------------------------------------------------
+template <typename XT>
+static void relax_pre(Hierarchy &h, int l, const XT *b, cudaStream_t s) {
+    Level &V = *h.lev[l];
+    int xb = sizeof(XT);
+    timed(h, 0, l, bytes_pre(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
+        if constexpr (sizeof(XT) == 8) {
+            cyc::pre_smooth_residual<double, double>(op_mat<double>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+        } else {
+            if (V.vbytes == 2)
+                cyc::pre_smooth_residual<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+            else
+                cyc::pre_smooth_residual<float, float>(op_mat<float>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+        }
+    });
+}
+
+template <typename XT>
+static void relax_post(Hierarchy &h, int l, const XT *b, XT *out, cudaStream_t s) {
+    Level &V = *h.lev[l];
+    int xb = sizeof(XT);
+    timed(h, 3, l, bytes_post(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
+        if constexpr (sizeof(XT) == 8) {
+            cyc::post_smooth<double, double>(op_mat<double>(V), V.x.as<XT>(), b, dinv_of<XT>(V), out, s);
+        } else {
+            if (V.vbytes == 2)
+                cyc::post_smooth<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), V.x.as<XT>(), b, dinv_of<XT>(V), out, s);
+            else
+                cyc::post_smooth<float, float>(op_mat<float>(V), V.x.as<XT>(), b, dinv_of<XT>(V), out, s);
+        }
+    });
+}
+
+template <typename XT>
+static void vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s) {
+    int L = h.nlev();
+    int xb = sizeof(XT);
+    if (L == 1) {
+        timed(h, 4, 0, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,
+              [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), b0, z0, s); });
+        return;
+    }
+    for (int l = 0; l + 1 < L; ++l) {
+        Level &V = *h.lev[l];
+        const XT *b = l == 0 ? b0 : V.b.as<XT>();
+        relax_pre<XT>(h, l, b, s);
+        Level &C = *h.lev[l + 1];
+        timed(h, 1, l, bytes_restrict(V.R.nrows, V.n(), V.R.nnz, xb, xb), s,
+              [&] { cyc::spmv<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), C.b.as<XT>(), false, s); });
+    }
+    Level &Cl = *h.lev[L - 1];
+    timed(h, 4, L - 1, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,
+          [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), Cl.b.as<XT>(), Cl.xo.as<XT>(), s); });
+    for (int l = L - 2; l >= 0; --l) {
+        Level &V = *h.lev[l];
+        Level &C = *h.lev[l + 1];
+        timed(h, 2, l, bytes_prolong(V.n(), V.P.ncols, V.P.nnz, xb, xb), s,
+              [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
+        const XT *b = l == 0 ? b0 : V.b.as<XT>();
+        relax_post<XT>(h, l, b, l == 0 ? z0 : V.xo.as<XT>(), s);
+    }
+}
+
+void vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s) {
+    if (h.opt.precision == AMG_PREC_FP64) {
+        vcycle_impl<double>(h, r, z, s);
+    } else {
+        int64_t n = h.lev[0]->n();
+        cyc::convert_vec_from_f64<float>(r, h.r32.as<float>(), n, s);
+        vcycle_impl<float>(h, h.r32.as<float>(), h.z32.as<float>(), s);
+        cyc::convert_vec_to_f64<float>(h.z32.as<float>(), z, n, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG (FP64 recurrences; flexible CG when the cycle is FP32)
+// ---------------------------------------------------------------------------
+namespace {
+struct Run {
+    int steps = 0, replacements = 0;
+    bool converged = false, breakdown = false;
+    double rnorm = 0.0;
+};
+
+CycMat<double> a0_mat(Hierarchy &h) {
+    Level &V = *h.lev[0];
+    CycMat<double> m = make_mat<double>(V.A, V.A.v());
+    m.variant = V.variant == AMG_SPMV_SELL32 ? heuristic_variant(V.A) : V.variant;
+    if (V.vbytes != 8) m.variant = heuristic_variant(V.A);
+    return m;
+}
+
+void read_scalars(Hierarchy &h, cudaStream_t s) {
+    AMG_CUDA(cudaMemcpyAsync(h.h_scal, h.dscal(), sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+double true_resnorm(Hierarchy &h, const double *b, const double *x, cudaStream_t s) {
+    CycMat<double> A0 = a0_mat(h);
+    cyc::true_residual(A0, b, x, h.pt.as<double>(), h.dscal(), h.reduce(), s);
+    read_scalars(h, s);
+    return std::sqrt(h.h_scal->tt);
+}
+
+// r = b - A x, z = M r, rho = r.z, p = 0 (beta = 0); returns ||r||
+double pcg_start(Hierarchy &h, const double *b, const double *x, cudaStream_t s) {
+    int64_t n = h.lev[0]->n();
+    double rn = true_resnorm(h, b, x, s);
+    AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
+    cyc::pcg_rz((int32_t)n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), true, s);
+    AMG_CUDA(cudaMemsetAsync(h.pp.ptr, 0, sizeof(double) * n, s));
+    return rn;
+}
+
+void pcg_iterate(Hierarchy &h, const double *b, double *x, double bnorm, double tol, int max_steps,
+                 double rnorm_now, cudaStream_t s, Run &run) {
+    int32_t n = h.lev[0]->n();
+    CycMat<double> A0 = a0_mat(h);
+    run = Run();
+    run.rnorm = rnorm_now;
+    if (rnorm_now <= tol * bnorm) { run.converged = true; return; }
+    double ap_bytes = (double)A0.nnz * 12 + 4.0 * (n + 1) + 16.0 * n;
+    while (run.steps < max_steps) {
+        timed(h, 6, 0, 24.0 * n, s, [&] { cyc::pcg_p_update(n, h.pz.as<double>(), h.pp.as<double>(), h.dscal(), false, s); });
+        timed(h, 5, 0, ap_bytes, s, [&] { cyc::pcg_ap(A0, h.pp.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s); });
+        timed(h, 6, 0, 48.0 * n, s, [&] {
+            cyc::pcg_xr_update(n, h.pp.as<double>(), h.pq.as<double>(), x, h.pr.as<double>(), h.dscal(), h.reduce(), s);
+        });
+        run.steps++;
+        read_scalars(h, s);
+        const PcgScalars &sc = *h.h_scal;
+        if (!(sc.pq > 0.0) || !(sc.rho > 0.0) || !std::isfinite(sc.rr)) { run.breakdown = true; return; }
+        run.rnorm = std::sqrt(sc.rr);
+        if (run.rnorm <= tol * bnorm) {
+            double tn = true_resnorm(h, b, x, s);
+            run.rnorm = tn;
+            if (tn <= tol * bnorm) { run.converged = true; return; }
+            AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            run.replacements++;
+        }
+        vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
+        timed(h, 6, 0, 24.0 * n, s, [&] {
+            cyc::pcg_rz(n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), false, s);
+        });
+    }
+}
+}  // namespace
+
+amg_status solve(Hierarchy &h, const double *b, double *x, double tol, int max_it, bool adaptive,
+                 cudaStream_t s, amg_solve_info *info) {
+    ensure_workspace(h, s);
+    int64_t n = h.lev[0]->n();
+    std::memset(info, 0, sizeof(*info));
+    PcgScalars init{};
+    init.flexible = h.opt.precision != AMG_PREC_FP64;
+    AMG_CUDA(cudaMemcpyAsync(h.dscal(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    double bnorm = true_resnorm(h, b, x, s);
+    if (bnorm == 0.0) { info->status = AMG_OK; return AMG_OK; }
+    amg_status st = AMG_OK;
+    if (!adaptive) {
+        double r0 = pcg_start(h, b, x, s);
+        Run run;
+        pcg_iterate(h, b, x, bnorm, tol, max_it, r0, s, run);
+        info->iterations = run.steps;
+        info->replacements = run.replacements;
+        info->conv_factor = run.steps > 0 ? std::pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
+        st = run.converged ? AMG_OK : (run.breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+    } else {
+        // Algorithm 5: check every k steps; reintroduce on slow convergence
+        int k = std::max(1, h.opt.k_check), sl = std::max(1, h.opt.s_levels);
+        DevBuf xs(sizeof(double) * (n + kPad));
+        double rstart = bnorm;
+        double rnow = pcg_start(h, b, x, s);
+        int total = 0;
+        bool converged = false, breakdown = false;
+        while (total < max_it) {
+            AMG_CUDA(cudaMemcpyAsync(xs.ptr, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            Run run;
+            pcg_iterate(h, b, x, bnorm, tol, std::min(k, max_it - total), rnow, s, run);
+            total += run.steps;
+            info->replacements += run.replacements;
+            double rend = true_resnorm(h, b, x, s);
+            if (run.converged || rend <= tol * bnorm) { converged = true; break; }
+            breakdown = run.breakdown;
+            rnow = run.rnorm;
+            double factor = run.steps > 0 ? std::pow(rend / rstart, 1.0 / run.steps) : 1.0;
+            if (factor > h.opt.rho_max || breakdown) {
+                int cnt = reintroduce(h, sl, s);
+                if (cnt == 0 && breakdown) break;
+                if (cnt > 0) {
+                    info->resets++;
+                    breakdown = false;
+                    if (rend > rstart) {
+                        AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                        rend = rstart;
+                    }
+                    rnow = pcg_start(h, b, x, s);
+                }
+            }
+            rstart = rend;
+        }
+        info->iterations = total;
+        st = converged ? AMG_OK : (breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+    }
+    double fin = true_resnorm(h, b, x, s);
+    info->final_relres = fin / bnorm;
+    if (adaptive) info->conv_factor = info->iterations > 0 ? std::pow(info->final_relres, 1.0 / info->iterations) : 0.0;
+    info->status = st;
+    timing_collect(h);
+    return st;
+}
+
+}  // namespace amg

@@ -1,0 +1,200 @@
+// hierarchy.cuh -- the device-resident AMG hierarchy and its drivers.
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include <map>
+
+#include "batch_ops.cuh"
+#include "common.cuh"
+#include "cycle_ops.cuh"
+
+namespace amg {
+
+// One level l of the hierarchy.  A is the retained Galerkin operator
+// (Algorithm 4 keeps it so Algorithm 5 can reintroduce entries); H is the
+// relaxed operator Ahat_l (an alias of A where nothing is dropped).
+struct Level {
+    DevCSR A;
+    DevBuf diagpos, tpos;  // int32 per row / per entry of A
+    DevBuf strong;         // uint8 per entry of A (levels that were coarsened)
+    DevBuf inM, keep;      // uint8 per entry of A
+    DevBuf cf;             // int8 per row (coarsened levels)
+    DevBuf cmap, cpts;     // int32
+    DevCSR P, R;           // interpolation and restriction (not on the coarsest level)
+    DevCSR H;              // sparsified operator when it differs from A
+    bool h_alias = true;
+    double gamma = 0.0;
+    DevBuf l1, dinv;       // FP64 ell1 diagonal and its inverse
+
+    // cycle representation (precision-dependent copies)
+    int vbytes = 8;        // bytes per value of the relaxed operator in the cycle
+    DevBuf hv32, hv16;     // FP32 / BF16 values of the relaxed operator
+    DevBuf pv32, rv32;     // FP32 values of P and R
+    DevBuf dinv32;
+    DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
+    int64_t sell_entries = 0;
+    int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
+
+    // work vectors in the cycle precision (b, x, r, post-smoothed output)
+    DevBuf b, x, r, xo;
+
+    const DevCSR &op() const { return h_alias ? A : H; }
+    int32_t n() const { return A.nrows; }
+};
+
+struct Timing {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+constexpr int kTimingKinds = 8;
+constexpr int kMaxLevels = 64;
+
+struct PendingEvent {
+    int kind, level;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+// Workspace of a K-column (multi-right-hand-side) solve: per-level cycle
+// vectors (n_l x K, cycle precision), FP64 PCG blocks (n_0 x K) and the
+// per-column scalars.
+struct BatchWS {
+    int K = 0;
+    std::vector<DevBuf> b, x, r, xo;
+    DevBuf B, X, R, Z, P, Q, T;
+    DevBuf R32, Z32;
+    DevBuf sc_buf, partials, counter, mask;
+    bat::ColScalars sc{};
+    double *h_d = nullptr;  // pinned: rho, pq, alpha, beta, rr, zq, tt (K each)
+    int *h_i = nullptr;     // pinned: active, start, mask (K each)
+    ~BatchWS();
+    double *h_rho() { return h_d; }
+    double *h_pq() { return h_d + K; }
+    double *h_rr() { return h_d + 4 * K; }
+    double *h_tt() { return h_d + 6 * K; }
+    int *h_active() { return h_i; }
+    int *h_start() { return h_i + K; }
+    int *h_mask() { return h_i + 2 * K; }
+};
+
+struct Hierarchy {
+    amg_options opt{};
+    int device = 0;
+    std::vector<std::unique_ptr<Level>> lev;
+    DevBuf coarse_inv;  // FP64 dense inverse of the coarsest relaxed operator
+    int32_t coarse_n = 0;
+
+    // FP64 PCG workspace
+    DevBuf pb, px, pr, pz, pp, pq, pt;
+    DevBuf scal;          // PcgScalars
+    DevBuf partials, counter;
+    PcgScalars *h_scal = nullptr;  // pinned
+    DevBuf z32, r32;      // FP32 V-cycle input/output in the FP32 modes
+    int64_t ws_n = -1;
+
+    // per-kernel timing
+    bool timing = false;
+    Timing timers[kTimingKinds][kMaxLevels];
+    std::vector<PendingEvent> pending;
+    std::vector<cudaEvent_t> event_pool;
+
+    // CUDA graphs of the PCG iteration halves (captured per stream)
+    cudaGraphExec_t g_update = nullptr, g_precond = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    bool graph_dirty = true;
+
+    std::map<int, std::unique_ptr<BatchWS>> batch;
+
+    ~Hierarchy();
+    int nlev() const { return (int)lev.size(); }
+    Reduce reduce() { return Reduce{partials.as<double>(), counter.as<unsigned>()}; }
+    PcgScalars *dscal() { return scal.as<PcgScalars>(); }
+};
+
+// views of a level in the cycle precision
+template <typename VT> inline CycMat<VT> make_mat(const DevCSR &M, const VT *vals) {
+    CycMat<VT> m;
+    m.nrows = M.nrows;
+    m.ncols = M.ncols;
+    m.nnz = M.nnz;
+    m.rp = M.rp();
+    m.ci = M.ci();
+    m.v = vals;
+    return m;
+}
+
+template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
+    const DevCSR &M = V.op();
+    const VT *vals;
+    if constexpr (sizeof(VT) == 8) vals = reinterpret_cast<const VT *>(M.v());
+    else if constexpr (sizeof(VT) == 4) vals = V.hv32.as<VT>();
+    else vals = V.hv16.as<VT>();
+    CycMat<VT> m = make_mat<VT>(M, vals);
+    if (V.sv.ptr) {
+        m.nslices = (M.nrows + 31) / 32;
+        m.soff = V.soff.as<int32_t>();
+        m.sw = V.sw.as<int32_t>();
+        m.sci = V.sci.as<int32_t>();
+        m.sv = V.sv.as<VT>();
+    }
+    m.variant = V.variant;
+    return m;
+}
+
+template <typename XT> inline CycMat<XT> p_mat(const Level &V) {
+    const XT *vals;
+    if constexpr (sizeof(XT) == 8) vals = reinterpret_cast<const XT *>(V.P.v());
+    else vals = V.pv32.as<XT>();
+    CycMat<XT> m = make_mat<XT>(V.P, vals);
+    m.variant = V.variant_p;
+    return m;
+}
+
+template <typename XT> inline CycMat<XT> r_mat(const Level &V) {
+    const XT *vals;
+    if constexpr (sizeof(XT) == 8) vals = reinterpret_cast<const XT *>(V.R.v());
+    else vals = V.rv32.as<XT>();
+    CycMat<XT> m = make_mat<XT>(V.R, vals);
+    m.variant = V.variant_r;
+    return m;
+}
+
+template <typename XT> inline const XT *dinv_of(const Level &V) {
+    if constexpr (sizeof(XT) == 8) return reinterpret_cast<const XT *>(V.dinv.ptr);
+    else return V.dinv32.as<XT>();
+}
+
+// drivers (hierarchy.cu)
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s);
+void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &P,
+                     const std::vector<std::vector<int8_t>> &cf,
+                     const std::vector<std::vector<uint8_t>> &inM, cudaStream_t s);
+void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s);
+void resparsify_level(Hierarchy &h, int l, cudaStream_t s);
+void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels);
+void ensure_workspace(Hierarchy &h, cudaStream_t s);
+int reintroduce(Hierarchy &h, int s_levels, cudaStream_t s);
+void vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s);
+amg_status solve(Hierarchy &h, const double *b_dev, double *x_dev, double tol, int max_it, bool adaptive,
+                 cudaStream_t s, amg_solve_info *info);
+void timing_collect(Hierarchy &h);
+
+// multi-right-hand-side solves (batch_driver.cu)
+BatchWS &batch_workspace(Hierarchy &h, int K, cudaStream_t s);
+void batch_vcycle(Hierarchy &h, BatchWS &w, cudaStream_t s);
+void batch_iteration(Hierarchy &h, BatchWS &w, cudaStream_t s);  // async; scalars copied to w.h_d
+void batch_true_residual(Hierarchy &h, BatchWS &w, cudaStream_t s);  // async; tt copied to w.h_d
+void batch_push_flags(BatchWS &w, cudaStream_t s);
+amg_status solve_batch(Hierarchy &h, int k, const double *B, double *X, bool on_device, double tol, int max_it,
+                       cudaStream_t s, amg_solve_info *infos);
+double level_cycle_bytes(const Hierarchy &h, int l);
+
+}  // namespace amg
+
+// the opaque handle of the C ABI
+struct amg_hierarchy {
+    amg::Hierarchy h;
+};

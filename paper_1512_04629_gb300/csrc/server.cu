@@ -1,0 +1,456 @@
+// server.cu -- continuous-batching solve server (amg_server_*).
+//
+// One worker thread owns the device work.  Each registered hierarchy has a
+// K-column batch (K = batch width >= max_batch) on its own stream.  Between
+// two iterations the worker admits queued requests into free columns (the
+// batch workspace is allocated on first use, within the memory budget, and
+// released when the hierarchy goes idle), launches one PCG iteration on every
+// hierarchy with work -- so different hierarchies' batches overlap on the
+// device -- then polls the streams' completion events with a time limit and
+// retires converged columns.  A column's arithmetic does not depend on the
+// other columns, so a request's result is the same alone and in any mix.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+
+#include "batch_ops.cuh"
+#include "hierarchy.cuh"
+
+namespace amg {
+void set_last_error(const std::string &msg);
+}
+
+using namespace amg;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    int hid = 0;
+    std::vector<double> b, x;
+    double tol = 1e-8;
+    double bnorm = 0.0;
+    amg_solve_info info{};
+    int status = AMG_NOT_CONVERGED;
+    bool done = false;
+    Clock::time_point submitted;
+};
+
+struct Slot {
+    Request *req = nullptr;
+    int its = 0, reps = 0;
+    double rnorm = 0.0;
+};
+
+struct HState {
+    Hierarchy *h = nullptr;
+    int32_t n = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    BatchWS *ws = nullptr;
+    int64_t ws_bytes = 0;
+    std::vector<Slot> slots;
+    std::deque<Request *> queue;
+    DevBuf dstage;          // n doubles: admission / retirement staging
+    double *hstage = nullptr;  // pinned n doubles
+    bool launched = false;
+};
+
+constexpr double kWaitLimitSeconds = 120.0;
+
+}  // namespace
+
+struct amg_server {
+    amg_server_opts opt{};
+    int K = 8;
+    std::vector<std::unique_ptr<HState>> hs;
+    std::mutex mu;
+    std::condition_variable cv_done, cv_work;
+    std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::thread worker;
+    bool stop = false;
+    int64_t queued = 0;
+    uint64_t next_ticket = 1;
+    int64_t budget = 0, in_use = 0;
+    int device = 0;
+    std::string fatal;
+};
+
+namespace {
+
+int64_t batch_bytes(const Hierarchy &h, int K) {
+    int64_t xb = h.opt.precision == AMG_PREC_FP64 ? 8 : 4;
+    int64_t cyc = 0;
+    for (int l = 0; l < h.nlev(); ++l) cyc += 4 * xb * (int64_t)h.lev[l]->n() * K;
+    int64_t n0 = h.lev[0]->n();
+    int64_t pcg = 7 * 8 * n0 * K + (xb == 4 ? 2 * 4 * n0 * K : 0);
+    return cyc + pcg + (1 << 20);
+}
+
+// polls the stream's completion event; false on time-out
+bool wait_event(cudaEvent_t ev, double limit_s) {
+    auto t0 = Clock::now();
+    while (true) {
+        cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return true;
+        if (e != cudaErrorNotReady) throw Error(AMG_ERR_CUDA, std::string("stream failed: ") + cudaGetErrorString(e));
+        if (std::chrono::duration<double>(Clock::now() - t0).count() > limit_s) return false;
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
+    Slot &sl = H.slots[c];
+    Request *r = sl.req;
+    BatchWS &w = *H.ws;
+    // X column -> host
+    bat::gather_column(H.n, w.K, c, w.X.as<double>(), H.dstage.as<double>(), H.stream);
+    AMG_CUDA(cudaMemcpyAsync(H.hstage, H.dstage.ptr, sizeof(double) * H.n, cudaMemcpyDeviceToHost, H.stream));
+    AMG_CUDA(cudaStreamSynchronize(H.stream));
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->x.assign(H.hstage, H.hstage + H.n);
+    r->status = status;
+    r->info.iterations = sl.its;
+    r->info.replacements = sl.reps;
+    r->info.status = status;
+    r->info.final_relres = r->bnorm > 0 ? std::sqrt(tt) / r->bnorm : 0.0;
+    r->info.conv_factor = sl.its > 0 && r->bnorm > 0 ? std::pow(sl.rnorm / r->bnorm, 1.0 / sl.its) : 0.0;
+    r->info.solve_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->submitted).count();
+    r->done = true;
+    sl = Slot();
+    w.h_active()[c] = 0;
+    S->cv_done.notify_all();
+}
+
+// admit queued requests into free columns of one hierarchy (worker thread)
+bool admit(amg_server *S, HState &H) {
+    std::vector<std::pair<int, Request *>> adm;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (H.queue.empty()) return false;
+        if (!H.ws) {
+            int64_t need = batch_bytes(*H.h, S->K);
+            if (S->in_use + need > S->budget) return false;  // wait for memory
+            H.ws_bytes = need;
+            S->in_use += need;
+        }
+        for (int c = 0; c < S->K && !H.queue.empty(); ++c) {
+            if (H.slots[c].req) continue;
+            adm.push_back({c, H.queue.front()});
+            H.queue.pop_front();
+            S->queued--;
+        }
+    }
+    if (!H.ws) {
+        try {
+            H.ws = &batch_workspace(*H.h, S->K, H.stream);
+        } catch (const Error &e) {
+            if (e.status != AMG_ERR_OOM) throw;
+            std::lock_guard<std::mutex> lk(S->mu);  // no memory now: requeue in order
+            for (auto it = adm.rbegin(); it != adm.rend(); ++it) H.queue.push_front(it->second);
+            S->queued += (int64_t)adm.size();
+            S->in_use -= H.ws_bytes;
+            H.ws_bytes = 0;
+            return false;
+        }
+        for (int c = 0; c < S->K; ++c) H.ws->h_active()[c] = 0;
+    }
+    BatchWS &w = *H.ws;
+    // only the columns admitted now restart (beta = 0); running columns go on
+    for (int c = 0; c < S->K; ++c) w.h_start()[c] = 0;
+    for (auto &a : adm) {
+        int c = a.first;
+        Request *r = a.second;
+        std::memcpy(H.hstage, r->b.data(), sizeof(double) * H.n);
+        AMG_CUDA(cudaMemcpyAsync(H.dstage.ptr, H.hstage, sizeof(double) * H.n, cudaMemcpyHostToDevice, H.stream));
+        bat::scatter_column(H.n, w.K, c, H.dstage.as<double>(), w.B.as<double>(), H.stream);
+        bat::scatter_column(H.n, w.K, c, H.dstage.as<double>(), w.R.as<double>(), H.stream);
+        bat::zero_column(H.n, w.K, c, w.X.as<double>(), H.stream);
+        bat::zero_column(H.n, w.K, c, w.P.as<double>(), H.stream);
+        bat::zero_column(H.n, w.K, c, w.Q.as<double>(), H.stream);
+        AMG_CUDA(cudaStreamSynchronize(H.stream));  // staging buffers are reused
+        H.slots[c].req = r;
+        H.slots[c].its = H.slots[c].reps = 0;
+        H.slots[c].rnorm = r->bnorm;
+        w.h_active()[c] = 1;
+        w.h_start()[c] = 1;
+    }
+    if (!adm.empty()) batch_push_flags(w, H.stream);
+    return !adm.empty();
+}
+
+void release_if_idle(amg_server *S, HState &H) {
+    if (!H.ws) return;
+    for (auto &sl : H.slots)
+        if (sl.req) return;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!H.queue.empty()) return;
+    H.h->batch.erase(S->K);
+    H.ws = nullptr;
+    S->in_use -= H.ws_bytes;
+    H.ws_bytes = 0;
+}
+
+void fail_all(amg_server *S, const std::string &msg) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->fatal = msg;
+    for (auto &kv : S->reqs) {
+        Request *r = kv.second.get();
+        if (!r->done) {
+            r->done = true;
+            r->status = AMG_ERR_CUDA;
+            r->info.status = AMG_ERR_CUDA;
+        }
+    }
+    for (auto &H : S->hs) {
+        H->queue.clear();
+        for (auto &sl : H->slots) sl = Slot();
+    }
+    S->queued = 0;
+    S->cv_done.notify_all();
+}
+
+void worker_loop(amg_server *S) {
+    cudaSetDevice(S->device);
+    try {
+        while (true) {
+            {
+                std::unique_lock<std::mutex> lk(S->mu);
+                bool busy = S->queued > 0;
+                for (auto &H : S->hs)
+                    for (auto &sl : H->slots) busy |= sl.req != nullptr;
+                if (S->stop && !busy) break;
+                if (!busy) {
+                    S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                    continue;
+                }
+            }
+            for (auto &H : S->hs) admit(S, *H);
+            // one iteration on every hierarchy with live columns, all launched before any wait
+            for (auto &H : S->hs) {
+                H->launched = false;
+                if (!H->ws) continue;
+                bool live = false;
+                for (auto &sl : H->slots) live |= sl.req != nullptr;
+                if (!live) continue;
+                batch_iteration(*H->h, *H->ws, H->stream);
+                AMG_CUDA(cudaEventRecord(H->done_ev, H->stream));
+                H->launched = true;
+            }
+            for (auto &H : S->hs) {
+                if (!H->launched) continue;
+                if (!wait_event(H->done_ev, kWaitLimitSeconds)) throw Error(AMG_TIMEOUT, "batch iteration timed out");
+                BatchWS &w = *H->ws;
+                bool candidate = false, changed = false;
+                for (int c = 0; c < S->K; ++c) {
+                    Slot &sl = H->slots[c];
+                    if (!sl.req || !w.h_active()[c]) continue;
+                    sl.its++;
+                    double pq = w.h_pq()[c], rho = w.h_rho()[c], rr = w.h_rr()[c];
+                    w.h_mask()[c] = 0;
+                    if (!(pq > 0.0) || !(rho > 0.0) || !std::isfinite(rr)) {
+                        finish_request(S, *H, c, AMG_BREAKDOWN, rr);
+                        changed = true;
+                        continue;
+                    }
+                    sl.rnorm = std::sqrt(rr);
+                    if (sl.rnorm <= sl.req->tol * sl.req->bnorm) { w.h_mask()[c] = 1; candidate = true; }
+                    else if (sl.its >= S->opt.max_it) {
+                        batch_true_residual(*H->h, w, H->stream);
+                        AMG_CUDA(cudaStreamSynchronize(H->stream));
+                        finish_request(S, *H, c, AMG_NOT_CONVERGED, w.h_tt()[c]);
+                        changed = true;
+                    }
+                }
+                if (candidate) {
+                    batch_true_residual(*H->h, w, H->stream);
+                    AMG_CUDA(cudaEventRecord(H->done_ev, H->stream));
+                    if (!wait_event(H->done_ev, kWaitLimitSeconds)) throw Error(AMG_TIMEOUT, "residual check timed out");
+                    bool replace = false;
+                    for (int c = 0; c < S->K; ++c) {
+                        Slot &sl = H->slots[c];
+                        if (!sl.req || !w.h_mask()[c]) continue;
+                        double tn = std::sqrt(w.h_tt()[c]);
+                        sl.rnorm = tn;
+                        if (tn <= sl.req->tol * sl.req->bnorm) {
+                            w.h_mask()[c] = 0;
+                            finish_request(S, *H, c, AMG_OK, w.h_tt()[c]);
+                            changed = true;
+                        } else {
+                            sl.reps++;
+                            replace = true;
+                        }
+                    }
+                    if (replace) {
+                        AMG_CUDA(cudaMemcpyAsync(w.mask.ptr, w.h_mask(), sizeof(int) * w.K, cudaMemcpyHostToDevice, H->stream));
+                        bat::copy_masked_columns(H->n, w.K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), H->stream);
+                    }
+                    for (int c = 0; c < S->K; ++c) w.h_mask()[c] = 0;
+                }
+                if (changed) {
+                    for (int c = 0; c < S->K; ++c) w.h_start()[c] = 0;
+                    batch_push_flags(w, H->stream);
+                }
+                release_if_idle(S, *H);
+            }
+        }
+    } catch (const std::exception &e) {
+        fail_all(S, e.what());
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void amg_server_opts_default(amg_server_opts *o) {
+    if (!o) return;
+    o->max_batch = 32;
+    o->hbm_budget = 0;
+    o->max_queue = 4096;
+    o->max_it = 500;
+}
+
+amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
+    try {
+        set_last_error("");
+        if (!out) { set_last_error("out is NULL"); return AMG_ERR_INVALID; }
+        *out = nullptr;
+        amg_server_opts opt;
+        if (o) opt = *o; else amg_server_opts_default(&opt);
+        if (opt.max_batch < 1 || opt.max_batch > 64 || opt.max_queue < 1 || opt.max_it < 1 || opt.hbm_budget < 0) {
+            set_last_error("server options out of range (max_batch 1..64, max_queue >= 1, max_it >= 1)");
+            return AMG_ERR_INVALID;
+        }
+        auto S = std::make_unique<amg_server>();
+        S->opt = opt;
+        S->K = bat::batch_width(opt.max_batch);
+        AMG_CUDA(cudaGetDevice(&S->device));
+        if (opt.hbm_budget > 0) {
+            S->budget = opt.hbm_budget;
+        } else {
+            size_t fr = 0, tot = 0;
+            AMG_CUDA(cudaMemGetInfo(&fr, &tot));
+            S->budget = (int64_t)(fr * 0.9);
+        }
+        S->worker = std::thread(worker_loop, S.get());
+        *out = S.release();
+        return AMG_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return AMG_ERR_CUDA;
+    }
+}
+
+amg_status amg_server_register(amg_server *S, amg_hierarchy *h, int *hid) {
+    try {
+        set_last_error("");
+        if (!S || !h || !hid) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
+        auto H = std::make_unique<HState>();
+        H->h = &h->h;
+        H->n = h->h.lev[0]->n();
+        H->slots.resize(S->K);
+        AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
+        AMG_CUDA(cudaEventCreateWithFlags(&H->done_ev, cudaEventDisableTiming));
+        H->dstage.alloc(sizeof(double) * (H->n + kPad));
+        AMG_CUDA(cudaMallocHost(&H->hstage, sizeof(double) * (H->n + kPad)));
+        ensure_workspace(h->h, H->stream);
+        AMG_CUDA(cudaStreamSynchronize(H->stream));
+        std::lock_guard<std::mutex> lk(S->mu);
+        *hid = (int)S->hs.size();
+        S->hs.push_back(std::move(H));
+        return AMG_OK;
+    } catch (const Error &e) {
+        set_last_error(e.what());
+        return e.status;
+    } catch (const std::exception &e) {
+        set_last_error(e.what());
+        return AMG_ERR_CUDA;
+    }
+}
+
+amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol, uint64_t *ticket) {
+    set_last_error("");
+    if (!S || !b || !ticket) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
+    if (!(tol > 0.0) || !std::isfinite(tol)) { set_last_error("tol must be > 0"); return AMG_ERR_INVALID; }
+    auto r = std::make_unique<Request>();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (hid < 0 || hid >= (int)S->hs.size()) { set_last_error("unknown hierarchy id"); return AMG_ERR_INVALID; }
+        if (!S->fatal.empty()) { set_last_error("server failed: " + S->fatal); return AMG_ERR_CUDA; }
+        if (S->queued >= S->opt.max_queue) { set_last_error("queue full"); return AMG_REJECTED; }
+    }
+    int32_t n = S->hs[hid]->n;
+    r->b.assign(b, b + n);
+    double s2 = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!std::isfinite(b[i])) { set_last_error("b has a non-finite value"); return AMG_ERR_INVALID; }
+        s2 += b[i] * b[i];
+    }
+    r->bnorm = std::sqrt(s2);
+    r->tol = tol;
+    r->hid = hid;
+    r->submitted = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->ticket = S->next_ticket++;
+    *ticket = r->ticket;
+    Request *rp = r.get();
+    if (r->bnorm == 0.0) {  // x = 0 solves it
+        r->x.assign(n, 0.0);
+        r->done = true;
+        r->status = AMG_OK;
+        S->reqs[rp->ticket] = std::move(r);
+        return AMG_OK;
+    }
+    S->reqs[rp->ticket] = std::move(r);
+    S->hs[hid]->queue.push_back(rp);
+    S->queued++;
+    S->cv_work.notify_all();
+    return AMG_OK;
+}
+
+amg_status amg_server_wait(amg_server *S, uint64_t ticket, double *x, int timeout_ms, amg_solve_info *info) {
+    set_last_error("");
+    if (!S || !x) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) { set_last_error("unknown ticket"); return AMG_ERR_INVALID; }
+    Request *r = it->second.get();
+    bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] { return r->done; });
+    if (!ok) { set_last_error("request not finished within the time limit"); return AMG_TIMEOUT; }
+    std::memcpy(x, r->x.data(), sizeof(double) * r->x.size());
+    if (info) *info = r->info;
+    amg_status st = (amg_status)r->status;
+    if (st == AMG_ERR_CUDA) set_last_error("server failed: " + S->fatal);
+    S->reqs.erase(it);
+    return st;
+}
+
+void amg_server_destroy(amg_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    for (auto &H : S->hs) {
+        if (H->ws) H->h->batch.erase(S->K);
+        if (H->stream) cudaStreamDestroy(H->stream);
+        if (H->done_ev) cudaEventDestroy(H->done_ev);
+        if (H->hstage) cudaFreeHost(H->hstage);
+    }
+    delete S;
+}
+
+}  // extern "C"

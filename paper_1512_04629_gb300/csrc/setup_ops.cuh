@@ -1,0 +1,45 @@
+// setup_ops.cuh -- host entry points of the setup kernels (setup.cu).
+#pragma once
+#include "common.cuh"
+
+namespace amg {
+namespace setup {
+
+// Checks sortedness, column range, finite values, a stored positive diagonal;
+// writes the diagonal position of every row.  Throws AMG_ERR_INVALID.
+void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s);
+// Position of the mirrored entry (j,i) for every stored (i,j); throws
+// AMG_ERR_INVALID if the pattern is not symmetric.
+void transpose_positions(const DevCSR &A, int32_t *tpos, cudaStream_t s);
+// Classical strength flags (one byte per stored entry).
+void strength(const DevCSR &A, double theta, uint8_t *strong, cudaStream_t s);
+// PMIS C/F splitting; cf[i] = 1 (C) / -1 (F); returns |C|.
+int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64_t seed,
+             int32_t level, int8_t *cf, cudaStream_t s);
+// Coarse numbering: cmap[i] for C points, cpts[c] = fine index of coarse point c.
+void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s);
+// Direct interpolation P (n x nc).
+void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, const int32_t *cmap,
+                   int32_t nc, DevCSR &P, cudaStream_t s);
+// R = P^T with sorted rows.
+void transpose(const DevCSR &P, DevCSR &R, cudaStream_t s);
+// C = A B (structural, deterministic, sorted rows).
+void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &C, cudaStream_t s);
+// Minimal-pattern flags of Ac's entries from the C rows of AP.
+void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, uint8_t *inM,
+                     cudaStream_t s);
+// Hybrid variant: pattern of Phat^T Ahat P (+ transpose) with Ahat the
+// sparsified fine operator.  Recomputes AP from Ahat.
+// Sparsify with diagonal lumping; fills keep[] and Ahat; returns nnz(Ahat).
+int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const int32_t *diagpos,
+                 double gamma, uint8_t *keep, DevCSR &Ahat, cudaStream_t s);
+// Copy of A (Ahat = A when gamma = 0) with keep[] = 1.
+void copy_all(const DevCSR &A, uint8_t *keep, DevCSR &Ahat, cudaStream_t s);
+// ell1 diagonal d_i = sum_j |a_ij| and its inverse.
+void l1_diag(const DevCSR &A, double *d, double *dinv, cudaStream_t s);
+// Dense inverse of the SPD coarsest operator through its Cholesky factor.
+// Throws AMG_BREAKDOWN if a pivot is not positive.
+void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s);
+
+}  // namespace setup
+}  // namespace amg

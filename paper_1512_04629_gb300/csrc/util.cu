@@ -1,0 +1,157 @@
+// util.cu -- device buffers, thread-local error text, exclusive scans.
+#include <atomic>
+#include <string>
+
+#include "common.cuh"
+
+namespace amg {
+
+static thread_local std::string g_last_error;
+std::atomic<int64_t> g_device_bytes{0};
+
+std::atomic<int64_t> g_launches{0};
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+const char *last_error_cstr() { return g_last_error.c_str(); }
+
+void DevBuf::alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&ptr, b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+        throw Error(e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(b) + "): " + cudaGetErrorString(e));
+    }
+    bytes = b;
+    g_device_bytes += (int64_t)b;
+}
+
+void DevBuf::release() {
+    if (ptr) {
+        cudaFree(ptr);
+        g_device_bytes -= (int64_t)bytes;
+    }
+    ptr = nullptr;
+    bytes = 0;
+}
+
+void DevCSR::allocate(int32_t r, int32_t c, int64_t z) {
+    nrows = r;
+    ncols = c;
+    nnz = z;
+    rowptr.alloc(sizeof(int32_t) * ((size_t)r + 1));
+    col.alloc(sizeof(int32_t) * (size_t)(z + kPad));
+    val.alloc(sizeof(double) * (size_t)(z + kPad));
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan: out[i] = sum_{k<i} in[k], out[n] = total (three passes:
+// per-tile sums, a single-block scan of the tile sums, tile-local scans)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kScanThreads = 256, kScanItems = 4, kTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T *total) {
+    __shared__ T warp_sums[kScanThreads / 32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T s = lane < kScanThreads / 32 ? warp_sums[lane] : T(0);
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < kScanThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    T base = w > 0 ? warp_sums[w - 1] : T(0);
+    *total = warp_sums[kScanThreads / 32 - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+template <typename TI>
+__global__ void tile_sum_kernel(const TI *in, int64_t n, int64_t *sums) {
+    int64_t base = (int64_t)blockIdx.x * kTile;
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) s += (int64_t)in[i];
+    }
+    int64_t tot;
+    block_exclusive_scan<int64_t>(s, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void scan_sums_kernel(int64_t *sums, int64_t m, int64_t *total) {
+    int64_t carry = 0;
+    for (int64_t b = 0; b < m; b += kScanThreads) {
+        int64_t i = b + threadIdx.x;
+        int64_t v = i < m ? sums[i] : 0;
+        int64_t tot;
+        int64_t ex = block_exclusive_scan<int64_t>(v, &tot);
+        if (i < m) sums[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+template <typename TI, typename TO>
+__global__ void tile_scan_kernel(const TI *in, int64_t n, const int64_t *sums, TO *out) {
+    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        v[k] = i < n ? (int64_t)in[i] : 0;
+        s += v[k];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan<int64_t>(s, &tot) + sums[blockIdx.x];
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = (TO)ex;
+        ex += v[k];
+    }
+}
+
+template <typename TI, typename TO>
+int64_t scan_impl(const TI *in, TO *out, int64_t n, cudaStream_t s) {
+    int64_t tiles = (n + kTile - 1) / kTile;
+    DevBuf sums(sizeof(int64_t) * (tiles + 1)), total(sizeof(int64_t));
+    if (n > 0) {
+        { tile_sum_kernel<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()); ::amg::count_launch(); }
+        { scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums.as<int64_t>(), tiles, total.as<int64_t>()); ::amg::count_launch(); }
+        { tile_scan_kernel<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>(), out); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+    } else {
+        AMG_CUDA(cudaMemsetAsync(total.ptr, 0, sizeof(int64_t), s));
+    }
+    int64_t t = read_scalar(total.as<int64_t>(), s);
+    if (sizeof(TO) == 4 && t >= ((int64_t)1 << 31))
+        throw Error(AMG_ERR_INVALID, "scan: total exceeds the int32 index range");
+    TO tt = (TO)t;
+    AMG_CUDA(cudaMemcpyAsync(out + n, &tt, sizeof(TO), cudaMemcpyHostToDevice, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    return t;
+}
+}  // namespace
+
+int64_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s) {
+    return scan_impl<int32_t, int32_t>(in, out, n, s);
+}
+int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+    return scan_impl<int64_t, int64_t>(in, out, n, s);
+}
+
+}  // namespace amg

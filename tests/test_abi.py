@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every function include/amg.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "amg.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(amg_[a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1512_04629_gb300 import build
+
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["amg_setup", "amg_sparsify", "amg_reintroduce", "amg_solve", "amg_solve_batch",
+                     "amg_level_stats", "amg_hierarchy_save", "amg_hierarchy_load", "amg_free",
+                     "amg_status_str", "amg_last_error", "amg_server_create", "amg_server_register",
+                     "amg_server_submit", "amg_server_wait", "amg_server_destroy"]:
+        assert required in names, required
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.amg_status_str.restype = ctypes.c_char_p
+    assert lib.amg_status_str(0) == b"AMG_OK"
+    assert lib.amg_status_str(8) == b"AMG_REJECTED"
+
+
+def test_binding_signatures_cover_header():
+    from paper_1512_04629_gb300 import amg
+
+    assert set(declared_functions()) == set(amg.SIGNATURES)
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    from paper_1512_04629_gb300 import amg
+
+    monkeypatch.setattr(amg, "_lib", None)
+    monkeypatch.setattr(amg, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        amg.lib()

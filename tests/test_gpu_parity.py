@@ -1,0 +1,246 @@
+"""GPU path vs the CPU oracle, through the C ABI (libamg.so).
+
+Integer work (strength flags, C/F split, kept-entry masks, patterns, per-level
+sizes) must match bit for bit.  FP64 setup values (P, Galerkin A_l, Ahat_l)
+must match to 1e-12 relative (the kernels accumulate in the oracle's order,
+so they are in fact expected to be identical).  Solutions must reach the
+1e-8 relative residual and match the oracle's iteration count within one.
+"""
+import numpy as np
+import pytest
+
+import amg_inputs as gen
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    from paper_1512_04629_gb300 import build
+
+    build.build()
+    import paper_1512_04629_gb300 as m
+
+    return m
+
+
+def _same_csr(got, ref, rtol=1e-12, what=""):
+    assert got.nrows == ref.nrows and got.ncols == ref.ncols, what
+    np.testing.assert_array_equal(got.rowptr, ref.rowptr, err_msg=what + " rowptr")
+    np.testing.assert_array_equal(got.col, ref.col, err_msg=what + " col")
+    scale = max(np.abs(ref.val).max() if ref.nnz else 1.0, 1e-300)
+    np.testing.assert_allclose(got.val, ref.val, rtol=0, atol=rtol * scale, err_msg=what + " val")
+
+
+CASES = {
+    "2d5_64": lambda: gen.poisson2d_5pt(64),
+    "2d5_37": lambda: gen.poisson2d_5pt(37),
+    "3d7_20": lambda: gen.poisson3d_7pt(20),
+    "3d27_11": lambda: gen.poisson3d_27pt(11),
+    "fv7_15": lambda: gen.fv7_lognormal(15, seed=3),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_setup_end_to_end_matches_oracle(amg, case):
+    A = CASES[case]()
+    ref = oracle.Hierarchy(A)
+    h = amg.Hierarchy.setup(A)
+    assert h.num_levels == ref.num_levels
+    for l in range(h.num_levels):
+        _same_csr(h.export(l, "A"), ref.matrix(l, "A"), what=f"A_{l}")
+        if l + 1 < h.num_levels:
+            np.testing.assert_array_equal(h.level_array(l, "strong"), ref.strong(l), err_msg=f"S_{l}")
+            np.testing.assert_array_equal(h.level_array(l, "cf"), ref.cf(l), err_msg=f"cf_{l}")
+            _same_csr(h.export(l, "P"), ref.matrix(l, "P"), what=f"P_{l}")
+            _same_csr(h.export(l, "R"), ref.matrix(l, "R"), what=f"R_{l}")
+        if l > 0:
+            np.testing.assert_array_equal(h.level_array(l, "inM"), ref.inM(l), err_msg=f"inM_{l}")
+        np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14)
+
+
+@pytest.mark.parametrize("gamma", [0.01, 0.1, 1.0])
+@pytest.mark.parametrize("case", ["2d5_64", "3d7_20", "fv7_15"])
+def test_sparsify_end_to_end_matches_oracle(amg, case, gamma):
+    A = CASES[case]()
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, gamma])
+    h = amg.Hierarchy.setup(A, gamma=[0.0, gamma])
+    for l in range(1, h.num_levels):
+        np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l), err_msg=f"keep_{l}")
+        _same_csr(h.export(l, "Ahat"), ref.matrix(l, "Ahat"), what=f"Ahat_{l}")
+        np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14)
+    # re-sparsify in place and reintroduce back to Galerkin
+    h.sparsify([0.0, 1.0])
+    ref.sparsify([0.0, 1.0])
+    for l in range(1, h.num_levels):
+        np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l))
+    for _ in range(20):
+        c1 = h.reintroduce(1)
+        c2, _ = ref.reintroduce(1)
+        assert c1 == c2
+        for l in range(1, h.num_levels):
+            np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l))
+        if c1 == 0:
+            break
+    for l in range(h.num_levels):
+        np.testing.assert_array_equal(h.export(l, "Ahat").val, h.export(l, "A").val)
+
+
+def test_per_level_on_oracle_matrices(amg):
+    """Given the oracle's own A_l, the GPU's strength/PMIS/interpolation/RAP
+    reproduce the oracle's level l (PMIS seeded with the level index)."""
+    A = gen.poisson3d_7pt(22)
+    ref = oracle.Hierarchy(A)
+    for l in range(ref.num_levels - 1):
+        Al = ref.matrix(l, "A")
+        h = amg.Hierarchy.setup(Al, max_levels=2, max_size=1, level_offset=l)
+        assert h.num_levels == 2
+        np.testing.assert_array_equal(h.level_array(0, "cf"), ref.cf(l))
+        _same_csr(h.export(0, "P"), ref.matrix(l, "P"), what=f"P_{l}")
+        _same_csr(h.export(1, "A"), ref.matrix(l + 1, "A"), what=f"A_{l + 1}")
+        np.testing.assert_array_equal(h.level_array(1, "inM"), ref.inM(l + 1))
+
+
+def _assemble_oracle(amg, ref, gamma=None, **opts):
+    L = ref.num_levels
+    As = [ref.matrix(l, "A") for l in range(L)]
+    Ps = [ref.matrix(l, "P") for l in range(L - 1)]
+    cfs = [ref.cf(l) for l in range(L - 1)]
+    inMs = [None] + [ref.inM(l) for l in range(1, L)]
+    return amg.Hierarchy.assemble(As, Ps, cfs, inMs, gamma=gamma, **opts)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.1, 1.0])
+def test_sparsify_on_oracle_galerkin(amg, gamma):
+    """Kept-entry pattern is bit-exact when given the oracle's Galerkin A_l."""
+    A = gen.poisson3d_7pt(24)
+    ref = oracle.Hierarchy(A)
+    h = _assemble_oracle(amg, ref, gamma=[0.0, gamma])
+    ref.sparsify([0.0, gamma])
+    for l in range(1, ref.num_levels):
+        np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l))
+        _same_csr(h.export(l, "Ahat"), ref.matrix(l, "Ahat"), what=f"Ahat_{l}")
+        st = h.level_stats(l)
+        assert st["nnz_operator"] == ref.matrix(l, "Ahat").nnz
+
+
+@pytest.mark.parametrize("variant", [-1, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("gamma", [0.0, 0.1])
+def test_vcycle_matches_oracle(amg, variant, gamma):
+    A = gen.poisson3d_7pt(23)  # n = 12167: ragged against 32-row slices and 256-thread blocks
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, gamma])
+    h = _assemble_oracle(amg, ref, gamma=[0.0, gamma], spmv_variant=variant)
+    for seed in (5, 6):
+        r = gen.rhs_uniform(A.n, seed)
+        z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        h.precond_apply(torch.from_numpy(r).cuda(), z)
+        zr = ref.vcycle(r)
+        np.testing.assert_allclose(z.cpu().numpy(), zr, rtol=1e-12, atol=1e-12 * np.abs(zr).max())
+
+
+@pytest.mark.parametrize("case,gamma", [("2d5_64", 0.0), ("3d7_20", 0.1), ("3d7_20", 1.0),
+                                        ("fv7_15", 0.1), ("3d27_11", 0.1)])
+def test_pcg_matches_oracle(amg, case, gamma):
+    A = CASES[case]()
+    b = gen.rhs_uniform(A.n, 1)
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, gamma])
+    xr, ir = ref.pcg(b, tol=1e-8)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, gamma])
+    for on_dev in (False, True):
+        bb = torch.from_numpy(b).cuda() if on_dev else b
+        x, info = h.solve(bb, tol=1e-8)
+        x = x.cpu().numpy() if on_dev else x
+        assert info.status == 0 and info.final_relres <= 1e-8
+        assert abs(info.iterations - ir.iterations) <= 1, (info.iterations, ir.iterations)
+        assert abs(info.conv_factor - ir.conv_factor) < 0.02
+        resid = b - A.to_scipy() @ x
+        assert np.linalg.norm(resid) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+        assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_adaptive_matches_oracle(amg):
+    A = gen.poisson3d_7pt(24)
+    b = gen.rhs_uniform(A.n, 1)
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, 1.0])
+    xr, ir = ref.adaptive_solve(b, rho_max=0.3, s=1, k=3)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0], rho_max=0.3, s_levels=1, k_check=3)
+    x, info = h.solve(b, tol=1e-8, adaptive=True)
+    assert info.status == 0 and info.final_relres <= 1e-8
+    assert info.resets == ir.resets
+    assert abs(info.iterations - ir.iterations) <= 1
+    for l in range(h.num_levels):
+        assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_reaches_fp64_tolerance(amg, prec):
+    A = gen.poisson3d_27pt(14)
+    b = gen.rhs_uniform(A.n, 2)
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, 0.1])
+    xr, ir = ref.pcg(b, tol=1e-8)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=prec)
+    x, info = h.solve(b, tol=1e-8)
+    assert info.status == 0 and info.final_relres <= 1e-8
+    assert info.iterations <= ir.iterations + 3
+    assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_single_level_and_zero_rhs(amg):
+    A = gen.poisson2d_5pt(9)
+    h = amg.Hierarchy.setup(A, max_size=1000)
+    assert h.num_levels == 1
+    b = gen.rhs_uniform(A.n, 0)
+    x, info = h.solve(b)
+    assert info.iterations == 1 and info.status == 0
+    x, info = h.solve(np.zeros(A.n))
+    assert info.iterations == 0 and not x.any()
+
+
+def test_tiny_matrix(amg):
+    import scipy.sparse as sp
+
+    A = sp.csr_matrix(np.array([[2.0]]))
+    h = amg.Hierarchy.setup(A)
+    x, info = h.solve(np.array([3.0]))
+    assert info.status == 0 and abs(x[0] - 1.5) < 1e-14
+
+
+def test_invalid_inputs_rejected(amg):
+    import scipy.sparse as sp
+
+    good = gen.poisson2d_5pt(6).to_scipy()
+
+    def expect_invalid(M, **kw):
+        with pytest.raises(amg.AmgError) as e:
+            amg.Hierarchy.setup(M, **kw)
+        assert e.value.status == 1
+
+    bad = good.copy()
+    bad.data[bad.indptr[3]] = np.nan
+    expect_invalid(bad)
+    d = good.toarray()
+    d[4, 4] = -1.0
+    expect_invalid(sp.csr_matrix(d))
+    d = good.toarray()
+    d[0, 5] = -0.5  # breaks pattern symmetry
+    expect_invalid(sp.csr_matrix(d))
+    d = good.toarray()
+    d[2, 2] = 0.0
+    m = sp.csr_matrix(d)
+    m.eliminate_zeros()
+    expect_invalid(m)  # missing diagonal
+    unsorted = good.copy()
+    r0 = slice(unsorted.indptr[7], unsorted.indptr[8])
+    unsorted.indices[r0] = unsorted.indices[r0][::-1].copy()
+    unsorted.data[r0] = unsorted.data[r0][::-1].copy()
+    expect_invalid(unsorted)
+    expect_invalid(good, gamma=[0.5, 0.1])  # gamma_0 must be 0
+    expect_invalid(sp.csr_matrix(np.ones((2, 3))))
