@@ -23,12 +23,14 @@ template <typename VT, typename XT> __device__ __forceinline__ XT cvt(VT v) { re
 // groups of one warp own different rows and run different trip counts, so
 // their shuffles name only their own lanes
 template <int G> __device__ __forceinline__ unsigned group_mask() {
-    if (G == 32) return 0xffffffffu;
-    unsigned lane = threadIdx.x & 31u;
-    return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
 }
 template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ double cvt<__nv_bfloat16, double>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
 enum Op { kPre = 0, kPost = 1, kSpmv = 2, kSpmvAdd = 3 };
 

@@ -22,9 +22,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename VT, typename XT> __device__ __forceinline__ XT cvt(VT v) { return (XT)v; }
 template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) {
@@ -240,10 +237,10 @@ int reduce_blocks(int64_t n, int per_thread = 1) {
 // PCG kernels (FP64)
 // ---------------------------------------------------------------------------
 __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double *__restrict__ p,
-                                const PcgScalars *sc, int first) {
+                                const PcgScalars *sc) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    p[i] = first ? z[i] : z[i] + sc->beta * p[i];
+    p[i] = z[i] + sc->beta * p[i];
 }
 
 // q = A p (vector-CSR, T lanes per row) and p . q
@@ -266,13 +263,16 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
     }
     if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
         sc->pq = part[0];
-        sc->alpha = sc->rho / part[0];
+        bool ok = part[0] > 0.0 && sc->rho > 0.0;
+        if (!ok) sc->breakdown = 1;
+        sc->alpha = ok ? sc->rho / part[0] : 0.0;
     }
 }
 
 __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
-                 double *__restrict__ r, PcgScalars *sc, Reduce red) {
+                 double *__restrict__ r, PcgScalars *sc, Reduce red, cudaGraphConditionalHandle handle,
+                 int use_handle) {
     double alpha = sc->alpha;
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -281,12 +281,21 @@ xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restri
         r[i] = ri;
         part[0] += ri * ri;
     }
-    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) sc->rr = part[0];
+    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
+        sc->rr = part[0];
+        int its = sc->its + 1;
+        sc->its = its;
+        if (use_handle) {
+            bool go = part[0] > sc->thresh2 && its < sc->max_its && !sc->breakdown && isfinite(part[0]);
+            cudaGraphSetConditional(handle, go ? 1u : 0u);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads)
 rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ q,
-          PcgScalars *sc, Reduce red, int first) {
+          PcgScalars *sc, Reduce red) {
+    int first = sc->start;
     double part[2] = {0.0, 0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         double zi = z[i];
@@ -302,6 +311,7 @@ rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z,
             sc->beta = 0.0;
         }
         sc->rho = rho_new;
+        sc->start = 0;
     }
 }
 
@@ -426,8 +436,8 @@ void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t
     AMG_CHECK_LAUNCH();
 }
 
-void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, bool first, cudaStream_t s) {
-    { p_update_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, z, p, sc, first ? 1 : 0); ::amg::count_launch(); }
+void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, cudaStream_t s) {
+    { p_update_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, z, p, sc); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -449,14 +459,14 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 }
 
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
-                   Reduce red, cudaStream_t s) {
-    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red); ::amg::count_launch(); }
+                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s) {
+    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
-            bool first, cudaStream_t s) {
-    { rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, r, z, q, sc, red, first ? 1 : 0); ::amg::count_launch(); }
+            cudaStream_t s) {
+    { rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, r, z, q, sc, red); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 

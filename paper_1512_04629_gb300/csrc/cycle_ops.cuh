@@ -26,7 +26,12 @@ struct PcgScalars {
     double rr;       // r . r after the update
     double zq;       // z . q (flexible CG)
     double tt;       // ||b - A x||^2 of the last true-residual check
+    double thresh2;  // (tol ||b||)^2: the recurrence stop test
     int flexible;
+    int start;       // 1: next r.z starts a (re)started run (beta = 0)
+    int its;         // CG steps taken
+    int max_its;     // the graph loop stops at this count
+    int breakdown;   // p.Ap <= 0 or r.z <= 0 was met
     int pad;
 };
 
@@ -54,12 +59,14 @@ template <typename XT>
 void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t s);
 
 // PCG (FP64)
-void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, bool first, cudaStream_t s);
+void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, cudaStream_t s);
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s);
+// x += alpha p, r -= alpha q, rr, its += 1; with a graph handle, the WHILE
+// condition is set to continue while rr > thresh2, its < max_its, no breakdown
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
-                   Reduce red, cudaStream_t s);
+                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s);
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
-            bool first, cudaStream_t s);
+            cudaStream_t s);
 // t = b - A x, sc->tt = ||t||^2; if `replace`, r = t
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s);

@@ -16,6 +16,7 @@ namespace amg {
 Hierarchy::~Hierarchy() {
     if (g_update) cudaGraphExecDestroy(g_update);
     if (g_precond) cudaGraphExecDestroy(g_precond);
+    if (graph_stream) cudaStreamDestroy(graph_stream);
     for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : event_pool) cudaEventDestroy(e);
     if (h_scal) cudaFreeHost(h_scal);
@@ -438,6 +439,13 @@ void vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // PCG (FP64 recurrences; flexible CG when the cycle is FP32)
+//
+// One CG step is the body [z = M r; rho, beta; p = z + beta p; q = A_0 p,
+// alpha; x += alpha p, r -= alpha q, rr].  With graphs on (and per-kernel
+// timing off) the body is captured once into the child graph of a CUDA WHILE
+// node whose condition the last kernel sets on the device -- the whole run up
+// to the recurrence stop test is one graph launch.  The host then confirms
+// convergence with the true residual, exactly as in the eager path.
 // ---------------------------------------------------------------------------
 namespace {
 struct Run {
@@ -459,6 +467,11 @@ void read_scalars(Hierarchy &h, cudaStream_t s) {
     AMG_CUDA(cudaStreamSynchronize(s));
 }
 
+// the device is idle here (every caller synchronised after its last launch)
+void write_scalars(Hierarchy &h, cudaStream_t s) {
+    AMG_CUDA(cudaMemcpyAsync(h.dscal(), h.h_scal, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+}
+
 double true_resnorm(Hierarchy &h, const double *b, const double *x, cudaStream_t s) {
     CycMat<double> A0 = a0_mat(h);
     cyc::true_residual(A0, b, x, h.pt.as<double>(), h.dscal(), h.reduce(), s);
@@ -466,67 +479,140 @@ double true_resnorm(Hierarchy &h, const double *b, const double *x, cudaStream_t
     return std::sqrt(h.h_scal->tt);
 }
 
-// r = b - A x, z = M r, rho = r.z, p = 0 (beta = 0); returns ||r||
+// r = b - A x, p = 0, start = 1 (the next body sets beta = 0); returns ||r||
 double pcg_start(Hierarchy &h, const double *b, const double *x, cudaStream_t s) {
     int64_t n = h.lev[0]->n();
     double rn = true_resnorm(h, b, x, s);
     AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
-    cyc::pcg_rz((int32_t)n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), true, s);
     AMG_CUDA(cudaMemsetAsync(h.pp.ptr, 0, sizeof(double) * n, s));
+    h.h_scal->start = 1;
+    h.h_scal->breakdown = 0;
+    write_scalars(h, s);
     return rn;
 }
 
-void pcg_iterate(Hierarchy &h, const double *b, double *x, double bnorm, double tol, int max_steps,
-                 double rnorm_now, cudaStream_t s, Run &run) {
+// one CG step on the internal x (h.px)
+void pcg_body(Hierarchy &h, cudaStream_t s, cudaGraphConditionalHandle handle, bool use_handle) {
     int32_t n = h.lev[0]->n();
     CycMat<double> A0 = a0_mat(h);
+    double ap_bytes = (double)A0.nnz * 12 + 4.0 * (n + 1) + 16.0 * n;
+    vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
+    timed(h, 6, 0, 24.0 * n, s, [&] {
+        cyc::pcg_rz(n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s);
+    });
+    timed(h, 6, 0, 24.0 * n, s, [&] { cyc::pcg_p_update(n, h.pz.as<double>(), h.pp.as<double>(), h.dscal(), s); });
+    timed(h, 5, 0, ap_bytes, s, [&] { cyc::pcg_ap(A0, h.pp.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s); });
+    timed(h, 6, 0, 48.0 * n, s, [&] {
+        cyc::pcg_xr_update(n, h.pp.as<double>(), h.pq.as<double>(), h.px.as<double>(), h.pr.as<double>(), h.dscal(),
+                           h.reduce(), handle, use_handle, s);
+    });
+}
+
+void destroy_graph(Hierarchy &h) {
+    if (h.g_update) cudaGraphExecDestroy(h.g_update);
+    h.g_update = nullptr;
+}
+
+void ensure_graph(Hierarchy &h) {
+    if (h.g_update && !h.graph_dirty) return;
+    destroy_graph(h);
+    if (!h.graph_stream) AMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    AMG_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle handle;
+    AMG_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        AMG_CUDA(e);
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    AMG_CUDA(cudaStreamBeginCaptureToGraph(h.graph_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    bool was = h.timing;
+    h.timing = false;
+    try {
+        pcg_body(h, h.graph_stream, handle, true);
+    } catch (...) {
+        cudaGraph_t junk;
+        cudaStreamEndCapture(h.graph_stream, &junk);
+        h.timing = was;
+        cudaGraphDestroy(g);
+        throw;
+    }
+    h.timing = was;
+    cudaGraph_t captured;
+    AMG_CUDA(cudaStreamEndCapture(h.graph_stream, &captured));
+    e = cudaGraphInstantiate(&h.g_update, g, 0);
+    cudaGraphDestroy(g);
+    AMG_CUDA(e);
+    h.graph_dirty = false;
+}
+
+// Runs up to max_steps CG steps (stopping at the recurrence test, then
+// confirming with the true residual; a failed confirmation replaces r).
+void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int max_steps, double rnorm_now,
+                 cudaStream_t s, Run &run) {
     run = Run();
     run.rnorm = rnorm_now;
     if (rnorm_now <= tol * bnorm) { run.converged = true; return; }
-    double ap_bytes = (double)A0.nnz * 12 + 4.0 * (n + 1) + 16.0 * n;
+    bool graph = h.opt.use_graph && !h.timing;
+    if (graph) ensure_graph(h);
+    double thresh2 = (tol * bnorm) * (tol * bnorm);
+    int32_t n = h.lev[0]->n();
     while (run.steps < max_steps) {
-        timed(h, 6, 0, 24.0 * n, s, [&] { cyc::pcg_p_update(n, h.pz.as<double>(), h.pp.as<double>(), h.dscal(), false, s); });
-        timed(h, 5, 0, ap_bytes, s, [&] { cyc::pcg_ap(A0, h.pp.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s); });
-        timed(h, 6, 0, 48.0 * n, s, [&] {
-            cyc::pcg_xr_update(n, h.pp.as<double>(), h.pq.as<double>(), x, h.pr.as<double>(), h.dscal(), h.reduce(), s);
-        });
-        run.steps++;
-        read_scalars(h, s);
-        const PcgScalars &sc = *h.h_scal;
-        if (!(sc.pq > 0.0) || !(sc.rho > 0.0) || !std::isfinite(sc.rr)) { run.breakdown = true; return; }
-        run.rnorm = std::sqrt(sc.rr);
-        if (run.rnorm <= tol * bnorm) {
-            double tn = true_resnorm(h, b, x, s);
-            run.rnorm = tn;
-            if (tn <= tol * bnorm) { run.converged = true; return; }
-            AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            run.replacements++;
+        h.h_scal->its = 0;
+        h.h_scal->max_its = max_steps - run.steps;
+        h.h_scal->thresh2 = thresh2;
+        write_scalars(h, s);
+        if (graph) {
+            AMG_CUDA(cudaGraphLaunch(h.g_update, s));
+            read_scalars(h, s);
+        } else {
+            while (true) {
+                pcg_body(h, s, cudaGraphConditionalHandle{}, false);
+                read_scalars(h, s);
+                const PcgScalars &c = *h.h_scal;
+                if (!(c.rr > c.thresh2 && c.its < c.max_its && !c.breakdown && std::isfinite(c.rr))) break;
+            }
         }
-        vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
-        timed(h, 6, 0, 24.0 * n, s, [&] {
-            cyc::pcg_rz(n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), false, s);
-        });
+        const PcgScalars &sc = *h.h_scal;
+        run.steps += sc.its;
+        if (sc.breakdown || !std::isfinite(sc.rr)) { run.breakdown = true; return; }
+        run.rnorm = std::sqrt(sc.rr);
+        if (sc.rr > thresh2) return;  // step budget used up
+        double tn = true_resnorm(h, b, h.px.as<double>(), s);
+        run.rnorm = tn;
+        if (tn <= tol * bnorm) { run.converged = true; return; }
+        AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        run.replacements++;
     }
 }
 }  // namespace
 
-amg_status solve(Hierarchy &h, const double *b, double *x, double tol, int max_it, bool adaptive,
+amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int max_it, bool adaptive,
                  cudaStream_t s, amg_solve_info *info) {
     ensure_workspace(h, s);
     int64_t n = h.lev[0]->n();
+    double *x = h.px.as<double>();
     std::memset(info, 0, sizeof(*info));
-    PcgScalars init{};
-    init.flexible = h.opt.precision != AMG_PREC_FP64;
-    AMG_CUDA(cudaMemcpyAsync(h.dscal(), &init, sizeof(init), cudaMemcpyHostToDevice, s));
+    std::memset(h.h_scal, 0, sizeof(PcgScalars));
+    h.h_scal->flexible = h.opt.precision != AMG_PREC_FP64;
+    write_scalars(h, s);
     AMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     double bnorm = true_resnorm(h, b, x, s);
-    if (bnorm == 0.0) { info->status = AMG_OK; return AMG_OK; }
     amg_status st = AMG_OK;
-    if (!adaptive) {
+    if (bnorm == 0.0) {
+        info->status = AMG_OK;
+    } else if (!adaptive) {
         double r0 = pcg_start(h, b, x, s);
         Run run;
-        pcg_iterate(h, b, x, bnorm, tol, max_it, r0, s, run);
+        pcg_iterate(h, b, bnorm, tol, max_it, r0, s, run);
         info->iterations = run.steps;
         info->replacements = run.replacements;
         info->conv_factor = run.steps > 0 ? std::pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
@@ -542,7 +628,7 @@ amg_status solve(Hierarchy &h, const double *b, double *x, double tol, int max_i
         while (total < max_it) {
             AMG_CUDA(cudaMemcpyAsync(xs.ptr, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             Run run;
-            pcg_iterate(h, b, x, bnorm, tol, std::min(k, max_it - total), rnow, s, run);
+            pcg_iterate(h, b, bnorm, tol, std::min(k, max_it - total), rnow, s, run);
             total += run.steps;
             info->replacements += run.replacements;
             double rend = true_resnorm(h, b, x, s);
@@ -568,10 +654,13 @@ amg_status solve(Hierarchy &h, const double *b, double *x, double tol, int max_i
         info->iterations = total;
         st = converged ? AMG_OK : (breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
     }
-    double fin = true_resnorm(h, b, x, s);
-    info->final_relres = fin / bnorm;
-    if (adaptive) info->conv_factor = info->iterations > 0 ? std::pow(info->final_relres, 1.0 / info->iterations) : 0.0;
+    if (bnorm > 0.0) {
+        double fin = true_resnorm(h, b, x, s);
+        info->final_relres = fin / bnorm;
+        if (adaptive) info->conv_factor = info->iterations > 0 ? std::pow(info->final_relres, 1.0 / info->iterations) : 0.0;
+    }
     info->status = st;
+    if (x_out != x) AMG_CUDA(cudaMemcpyAsync(x_out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     timing_collect(h);
     return st;
 }
