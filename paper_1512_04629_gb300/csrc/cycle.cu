@@ -194,29 +194,47 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Every block adds its partials; the last block to arrive reduces all of
-// them in block order and returns true (thread 0 holds the totals).
+// Every block adds its partials; the last block of each group of 256 blocks
+// sums the group's partials (one load per thread), and the last group to
+// finish sums the group partials.  Fixed groups and fixed trees: the result
+// does not depend on arrival order.  Returns true in the single block that
+// holds the totals (thread 0's v).
 template <int NV>
 __device__ bool reduce_and_finish(double (&v)[NV], Reduce red) {
     block_reduce<NV>(v);
     __shared__ bool last;
+    const int g = blockIdx.x >> 8;
+    const int gsize = min(256, (int)gridDim.x - g * 256);
+    const int ngroups = ((int)gridDim.x + 255) >> 8;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) red.partials[k * kMaxReduceBlocks + blockIdx.x] = v[k];
         __threadfence();
-        unsigned prev = atomicAdd(red.counter, 1u);
-        last = (prev == gridDim.x - 1);
+        unsigned prev = atomicAdd(red.counter + 1 + g, 1u);
+        last = (prev == (unsigned)gsize - 1);
     }
     __syncthreads();
     if (!last) return false;
     __threadfence();
     double t[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        t[k] = 0.0;
-        for (int bI = threadIdx.x; bI < (int)gridDim.x; bI += kThreads)
-            t[k] += ((volatile double *)red.partials)[k * kMaxReduceBlocks + bI];
+    for (int k = 0; k < NV; ++k)
+        t[k] = (int)threadIdx.x < gsize ? ((volatile double *)red.partials)[k * kMaxReduceBlocks + g * 256 + threadIdx.x] : 0.0;
+    block_reduce<NV>(t);
+    if (threadIdx.x == 0) {
+        red.counter[1 + g] = 0u;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red.gpartials[k * 256 + g] = t[k];
+        __threadfence();
+        unsigned prev = atomicAdd(red.counter, 1u);
+        last = (prev == (unsigned)ngroups - 1);
     }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        t[k] = (int)threadIdx.x < ngroups ? ((volatile double *)red.gpartials)[k * 256 + threadIdx.x] : 0.0;
     block_reduce<NV>(t);
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -232,6 +250,7 @@ int reduce_blocks(int64_t n, int per_thread = 1) {
     if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
     return (int)b;
 }
+static_assert(kThreads == 256, "two-level reduction assumes groups of 256 blocks and 256 threads");
 
 // ---------------------------------------------------------------------------
 // PCG kernels (FP64)
@@ -241,6 +260,25 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     p[i] = z[i] + sc->beta * p[i];
+}
+
+// q = A p (SELL-32, one thread per row) and p . q
+__global__ void __launch_bounds__(kThreads)
+ap_sell_kernel(int32_t n, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw, const int32_t *__restrict__ sci,
+               const double *__restrict__ sv, const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc,
+               Reduce red) {
+    double part[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+        double s = sell_row_sum<double, double>((int32_t)i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
+        q[i] = s;
+        part[0] += p[i] * s;
+    }
+    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
+        sc->pq = part[0];
+        bool ok = part[0] > 0.0 && sc->rho > 0.0;
+        if (!ok) sc->breakdown = 1;
+        sc->alpha = ok ? sc->rho / part[0] : 0.0;
+    }
 }
 
 // q = A p (vector-CSR, T lanes per row) and p . q
@@ -443,11 +481,16 @@ void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, c
 
 template <int T>
 static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
-    int blocks = reduce_blocks((int64_t)A.nrows * T, 4);
+    int blocks = reduce_blocks((int64_t)A.nrows * T, 1);
     { ap_kernel<T><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, p, q, sc, red); ::amg::count_launch(); }
 }
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+        { ap_sell_kernel<<<reduce_blocks(A.nrows, 1), kThreads, 0, s>>>(A.nrows, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     switch (threads_per_row(A.variant == AMG_SPMV_SELL32 ? AMG_SPMV_CSR4 : A.variant)) {
         case 2: launch_ap<2>(A, p, q, sc, red, s); break;
         case 4: launch_ap<4>(A, p, q, sc, red, s); break;
@@ -472,7 +515,7 @@ void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgSca
 
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s) {
-    int blocks = reduce_blocks((int64_t)A.nrows * 4, 4);
+    int blocks = reduce_blocks((int64_t)A.nrows * 4, 1);
     { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }

@@ -37,10 +37,11 @@ struct PcgScalars {
 
 // Deterministic reduction workspace: per-block partials + arrival counter.
 struct Reduce {
-    double *partials = nullptr;  // 2 * kMaxReduceBlocks
-    unsigned *counter = nullptr;
+    double *partials = nullptr;   // 4 * kMaxReduceBlocks (per block)
+    unsigned *counter = nullptr;  // [0]: groups done; [1 + g]: blocks done in group g (257 used)
+    double *gpartials = nullptr;  // 4 * 256 (per group of 256 blocks)
 };
-constexpr int kMaxReduceBlocks = 1024;
+constexpr int kMaxReduceBlocks = 65536;
 
 namespace cyc {
 

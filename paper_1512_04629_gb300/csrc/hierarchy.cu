@@ -5,6 +5,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "cycle_ops.cuh"
@@ -175,9 +177,37 @@ static void free_sell(Level &V) {
     V.sell_entries = 0;
 }
 
-// time the post-smoothing kernel of one level under each variant; keep the fastest
+// Autotuner: time the post-smoothing kernel of one level under each plausible
+// variant (vector-CSR with T lanes covering between a quarter and four times
+// the mean row, and SELL-32), keep the fastest.  Decisions are cached per
+// (rows, entries, value bytes) so setting up the same operator shape again
+// costs no trials.
+struct TuneKey {
+    int64_t n, nnz;
+    int vbytes;
+    bool operator<(const TuneKey &o) const {
+        return n != o.n ? n < o.n : (nnz != o.nnz ? nnz < o.nnz : vbytes < o.vbytes);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune_cache;
+
+static std::vector<int> tune_candidates(const DevCSR &M, int vbytes) {
+    double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
+    int V = 16 / vbytes;  // entries per 16-byte load
+    std::vector<int> c;
+    const int vars[] = {AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16, AMG_SPMV_CSR32};
+    for (int v : vars) {
+        double cover = (double)cyc::threads_per_row(v) * V;
+        if (cover >= mean / 4.0 && cover <= std::max(4.0 * mean, (double)V * 2)) c.push_back(v);
+    }
+    if (c.empty()) c.push_back(AMG_SPMV_CSR4);
+    c.push_back(AMG_SPMV_SELL32);
+    return c;
+}
+
 template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Level &V, cudaStream_t s) {
-    const int cands[] = {AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16, AMG_SPMV_CSR32, AMG_SPMV_SELL32};
+    const std::vector<int> cands = tune_candidates(V.op(), V.vbytes);
     cudaEvent_t e0, e1;
     AMG_CUDA(cudaEventCreate(&e0));
     AMG_CUDA(cudaEventCreate(&e1));
@@ -189,7 +219,7 @@ template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Lev
         CycMat<VT> m = op_mat<VT>(V);
         cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);  // warm-up
         float tmin = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 2; ++rep) {
             AMG_CUDA(cudaEventRecord(e0, s));
             cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);
             AMG_CUDA(cudaEventRecord(e1, s));
@@ -259,6 +289,15 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     int forced = h.opt.spmv_variant;
     bool tune = forced == AMG_SPMV_AUTO && M.nnz >= 20000 && has_p;
     V.variant = forced == AMG_SPMV_AUTO ? heuristic_variant(M) : forced;
+    TuneKey key{M.nrows, M.nnz, V.vbytes};
+    if (tune) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            V.variant = it->second;
+            tune = false;
+        }
+    }
     if (tune || V.variant == AMG_SPMV_SELL32) {
         if (V.vbytes == 8) build_sell<double>(V, s);
         else if (V.vbytes == 4) build_sell<float>(V, s);
@@ -269,6 +308,8 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
         else if (V.vbytes == 4) autotune_level<float, float>(h, V, s);
         else autotune_level<__nv_bfloat16, float>(h, V, s);
         if (V.variant != AMG_SPMV_SELL32) free_sell(V);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = V.variant;
     }
     if (l == h.nlev() - 1) {
         h.coarse_n = n;
@@ -296,8 +337,8 @@ void ensure_workspace(Hierarchy &h, cudaStream_t s) {
     }
     h.scal.alloc(sizeof(PcgScalars));
     AMG_CUDA(cudaMemsetAsync(h.scal.ptr, 0, sizeof(PcgScalars), s));
-    h.partials.alloc(sizeof(double) * 4 * kMaxReduceBlocks);
-    h.counter.alloc(sizeof(unsigned) * 4);
+    h.partials.alloc(sizeof(double) * (4 * kMaxReduceBlocks + 4 * 256));
+    h.counter.alloc(sizeof(unsigned) * 512);
     AMG_CUDA(cudaMemsetAsync(h.counter.ptr, 0, h.counter.bytes, s));
     if (!h.h_scal) AMG_CUDA(cudaMallocHost(&h.h_scal, sizeof(PcgScalars)));
     h.ws_n = n;
@@ -454,11 +495,17 @@ struct Run {
     double rnorm = 0.0;
 };
 
+// A_0 in FP64 for the outer PCG: shares level 0's SELL copy when the cycle is
+// FP64 and the autotuner chose SELL there
 CycMat<double> a0_mat(Hierarchy &h) {
     Level &V = *h.lev[0];
+    if (V.vbytes == 8) {
+        CycMat<double> m = op_mat<double>(V);
+        if (m.variant == AMG_SPMV_SELL32 && !m.sv) m.variant = heuristic_variant(V.A);
+        return m;
+    }
     CycMat<double> m = make_mat<double>(V.A, V.A.v());
-    m.variant = V.variant == AMG_SPMV_SELL32 ? heuristic_variant(V.A) : V.variant;
-    if (V.vbytes != 8) m.variant = heuristic_variant(V.A);
+    m.variant = heuristic_variant(V.A);
     return m;
 }
 

@@ -110,7 +110,9 @@ struct Hierarchy {
 
     ~Hierarchy();
     int nlev() const { return (int)lev.size(); }
-    Reduce reduce() { return Reduce{partials.as<double>(), counter.as<unsigned>()}; }
+    Reduce reduce() {
+        return Reduce{partials.as<double>(), counter.as<unsigned>(), partials.as<double>() + 4 * kMaxReduceBlocks};
+    }
     PcgScalars *dscal() { return scal.as<PcgScalars>(); }
 };
 

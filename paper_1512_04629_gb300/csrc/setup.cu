@@ -277,15 +277,24 @@ struct RowTables {
     int32_t *rank;  // hs slots: position of the key in the sorted list
     int32_t *list;  // umax: distinct columns
     double *acc;    // umax: accumulators
-    int32_t hs;     // power of two
+    int32_t hs;     // table capacity (power of two)
     int32_t umax;   // power of two >= distinct count
 };
+
+// slots used for one row: the smallest power of two >= 2 ub (at least 64),
+// capped by the table capacity -- load factor <= 1/2 since u <= ub
+__device__ __forceinline__ int32_t row_slots(int64_t ub, int32_t cap) {
+    int32_t h = 64;
+    while (h < cap && (int64_t)h < 2 * ub) h <<= 1;
+    return h;
+}
 
 // Inserts every product column of row i; returns the number of distinct columns.
 template <int NT>
 __device__ int32_t row_insert(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
-                              const int32_t *brp, const int32_t *bci, const RowTables &t,
-                              int32_t *counter) {
+                              const int32_t *brp, const int32_t *bci, RowTables &t,
+                              int32_t *counter, int64_t ub) {
+    t.hs = row_slots(ub, t.umax * 2);
     for (int32_t s = lane; s < t.hs; s += NT) t.keys[s] = -1;
     if (lane == 0) *counter = 0;
     gsync<NT>();
@@ -319,9 +328,9 @@ __device__ __forceinline__ int32_t row_lookup(const RowTables &t, int32_t j) {
 template <int NT>
 __device__ void row_numeric(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
                             const double *av, const int32_t *brp, const int32_t *bci,
-                            const double *bv, const RowTables &t, int32_t *counter,
-                            const int32_t *crp, int32_t *cci, double *cv) {
-    int32_t u = row_insert<NT>(i, lane, arp, aci, brp, bci, t, counter);
+                            const double *bv, RowTables &t, int32_t *counter,
+                            const int32_t *crp, int32_t *cci, double *cv, int64_t ub) {
+    int32_t u = row_insert<NT>(i, lane, arp, aci, brp, bci, t, counter, ub);
     // compact the distinct keys, pad to a power of two, bitonic sort
     if (lane == 0) *counter = 0;
     gsync<NT>();
@@ -388,19 +397,29 @@ __global__ void spgemm_ub_kernel(int32_t n, const int32_t *arp, const int32_t *a
 constexpr int kWarpHS = 1024, kWarpUmax = 512, kWarpsPerBlock = 4;
 constexpr int kBlockHS = 8192, kBlockUmax = 4096, kBlockThreads = 256;
 
+// rows -> three bins by upper bound; one global atomic per bin per block
 __global__ void bin_rows_kernel(int32_t n, const int64_t *ub, int32_t *bins, int32_t *bin_count) {
+    __shared__ int32_t local[3], base[3];
+    if (threadIdx.x < 3) local[threadIdx.x] = 0;
+    __syncthreads();
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int b = ub[i] <= kWarpUmax ? 0 : (ub[i] <= kBlockUmax ? 1 : 2);
-    int32_t pos = atomicAdd(&bin_count[b], 1);
-    bins[(int64_t)b * n + pos] = i;
+    int b = -1;
+    int32_t my = 0;
+    if (i < n) {
+        b = ub[i] <= kWarpUmax ? 0 : (ub[i] <= kBlockUmax ? 1 : 2);
+        my = atomicAdd(&local[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) base[threadIdx.x] = local[threadIdx.x] ? atomicAdd(&bin_count[threadIdx.x], local[threadIdx.x]) : 0;
+    __syncthreads();
+    if (b >= 0) bins[(int64_t)b * n + base[b] + my] = i;
 }
 
 template <bool NUMERIC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 spgemm_warp_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                    const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
-                   int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv) {
+                   int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv, const int64_t *ub) {
     extern __shared__ __align__(16) unsigned char smem[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *base = smem + (size_t)w * (kWarpHS * 8 + kWarpUmax * 12 + 16);
@@ -410,14 +429,14 @@ spgemm_warp_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const
     t.rank = t.keys + kWarpHS;
     t.list = t.rank + kWarpHS;
     t.hs = kWarpHS;
-    t.umax = kWarpUmax;
+    t.umax = kWarpUmax;  // capacity: hs is chosen per row
     int32_t *counter = t.list + kWarpUmax;
     for (int32_t r = blockIdx.x * kWarpsPerBlock + w; r < nrows; r += gridDim.x * kWarpsPerBlock) {
         int32_t i = rows[r];
         if (NUMERIC) {
-            row_numeric<32>(i, lane, arp, aci, av, brp, bci, bv, t, counter, crp, cci, cv);
+            row_numeric<32>(i, lane, arp, aci, av, brp, bci, bv, t, counter, crp, cci, cv, ub[i]);
         } else {
-            int32_t u = row_insert<32>(i, lane, arp, aci, brp, bci, t, counter);
+            int32_t u = row_insert<32>(i, lane, arp, aci, brp, bci, t, counter, ub[i]);
             if (lane == 0) cnt[i] = u;
         }
     }
@@ -427,7 +446,7 @@ template <bool NUMERIC>
 __global__ void __launch_bounds__(kBlockThreads)
 spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                     const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
-                    int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv,
+                    int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv, const int64_t *ub,
                     unsigned char *gscratch, int32_t ghs, int32_t gumax) {
     extern __shared__ __align__(16) unsigned char smem[];
     RowTables t;
@@ -450,9 +469,9 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
         int32_t i = rows[r];
         if (NUMERIC) {
             row_numeric<kBlockThreads>(i, threadIdx.x, arp, aci, av, brp, bci, bv, t, &counter,
-                                       crp, cci, cv);
+                                       crp, cci, cv, ub[i]);
         } else {
-            int32_t u = row_insert<kBlockThreads>(i, threadIdx.x, arp, aci, brp, bci, t, &counter);
+            int32_t u = row_insert<kBlockThreads>(i, threadIdx.x, arp, aci, brp, bci, t, &counter, ub[i]);
             if (threadIdx.x == 0) cnt[i] = u;
         }
     }
@@ -806,31 +825,31 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
             int blocks = std::min(div_up(nb[0], kWarpsPerBlock), 152 * 16);
             if (numeric)
                 { spgemm_warp_kernel<true><<<blocks, kWarpsPerBlock * 32, warp_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v()); ::amg::count_launch(); }
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(), ub.as<int64_t>()); ::amg::count_launch(); }
             else
                 { spgemm_warp_kernel<false><<<blocks, kWarpsPerBlock * 32, warp_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr); ::amg::count_launch(); }
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr, ub.as<int64_t>()); ::amg::count_launch(); }
         }
         if (nb[1] > 0) {
             int blocks = std::min(nb[1], 152 * 4);
             if (numeric)
                 { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
                     rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
-                    nullptr, 0, 0); ::amg::count_launch(); }
+                    ub.as<int64_t>(), nullptr, 0, 0); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
                     rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
-                    nullptr, 0, 0); ::amg::count_launch(); }
+                    ub.as<int64_t>(), nullptr, 0, 0); ::amg::count_launch(); }
         }
         if (nb[2] > 0) {
             if (numeric)
                 { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
                     rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
-                    gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
+                    ub.as<int64_t>(), gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
                     rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
-                    gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
+                    ub.as<int64_t>(), gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
         }
         AMG_CHECK_LAUNCH();
     };

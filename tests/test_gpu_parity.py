@@ -143,15 +143,16 @@ def test_vcycle_matches_oracle(amg, variant, gamma):
         np.testing.assert_allclose(z.cpu().numpy(), zr, rtol=1e-12, atol=1e-12 * np.abs(zr).max())
 
 
+@pytest.mark.parametrize("use_graph", [1, 0])
 @pytest.mark.parametrize("case,gamma", [("2d5_64", 0.0), ("3d7_20", 0.1), ("3d7_20", 1.0),
                                         ("fv7_15", 0.1), ("3d27_11", 0.1)])
-def test_pcg_matches_oracle(amg, case, gamma):
+def test_pcg_matches_oracle(amg, case, gamma, use_graph):
     A = CASES[case]()
     b = gen.rhs_uniform(A.n, 1)
     ref = oracle.Hierarchy(A)
     ref.sparsify([0.0, gamma])
     xr, ir = ref.pcg(b, tol=1e-8)
-    h = amg.Hierarchy.setup(A, gamma=[0.0, gamma])
+    h = amg.Hierarchy.setup(A, gamma=[0.0, gamma], use_graph=use_graph)
     for on_dev in (False, True):
         bb = torch.from_numpy(b).cuda() if on_dev else b
         x, info = h.solve(bb, tol=1e-8)
@@ -164,13 +165,14 @@ def test_pcg_matches_oracle(amg, case, gamma):
         assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
 
 
-def test_adaptive_matches_oracle(amg):
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_adaptive_matches_oracle(amg, use_graph):
     A = gen.poisson3d_7pt(24)
     b = gen.rhs_uniform(A.n, 1)
     ref = oracle.Hierarchy(A)
     ref.sparsify([0.0, 1.0])
     xr, ir = ref.adaptive_solve(b, rho_max=0.3, s=1, k=3)
-    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0], rho_max=0.3, s_levels=1, k_check=3)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0], rho_max=0.3, s_levels=1, k_check=3, use_graph=use_graph)
     x, info = h.solve(b, tol=1e-8, adaptive=True)
     assert info.status == 0 and info.final_relres <= 1e-8
     assert info.resets == ir.resets
@@ -191,6 +193,23 @@ def test_mixed_precision_reaches_fp64_tolerance(amg, prec):
     assert info.status == 0 and info.final_relres <= 1e-8
     assert info.iterations <= ir.iterations + 3
     assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
+def test_timing_counters(amg):
+    """Per-kernel event timing accumulates launches and bytes on every level."""
+    A = gen.poisson3d_7pt(20)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 0.1])
+    h.timing_enable(True)
+    x, info = h.solve(gen.rhs_uniform(A.n, 1))
+    assert info.status == 0
+    for kind in (amg.K_PRE, amg.K_POST, amg.K_RESTRICT, amg.K_PROLONG):
+        for l in range(h.num_levels - 1):
+            n, ms, by = h.timing_get(kind, l)
+            assert n == info.iterations and ms > 0 and by > 0
+    n, ms, by = h.timing_get(amg.K_AP, 0)
+    assert n == info.iterations
+    h.timing_reset()
+    assert h.timing_get(amg.K_PRE, 0)[0] == 0
 
 
 def test_single_level_and_zero_rhs(amg):
