@@ -225,6 +225,26 @@ void amg_free(amg_hierarchy *h);
 const char *amg_status_str(amg_status s);
 const char *amg_last_error(void);
 
+/*
+ * amg_residual_noalloc -- r = b - A_0 x and rnorm[0] = ||r||_2 for the
+ * finest operator of h, for callers that cannot allocate device memory at
+ * the moment they call (a CUDA graph being recorded by stream capture, a
+ * framework or real-time loop whose device memory comes only from its own
+ * pool, a fully committed memory budget).  The paper has no counterpart: it
+ * is a service of this library, not a step of the method.
+ * b, x, r, rnorm: device pointers (b, x, r of length n; rnorm one double,
+ * written on the device -- the call does not synchronise).  The call
+ * allocates nothing: its reduction scratch is a fixed array of about 530 KB
+ * in the library image, held by every GPU that loads the library until the
+ * process exits.  n is limited to 67,108,864 rows (AMG_ERR_INVALID beyond).
+ * The first call on a device looks up that array's device address; make it
+ * before any stream capture.  All calls share the scratch and its counters
+ * are cleared at the start of each call, so calls that overlap on the GPU
+ * race: order them (e.g. one stream).
+ */
+amg_status amg_residual_noalloc(const amg_hierarchy *h, const double *b, const double *x, double *r,
+                                double *rnorm, void *stream);
+
 /* Number of CUDA kernels this process has launched through the library so
  * far (a diagnostic counter, e.g. to count the launches of one solve). */
 int64_t amg_kernel_launches(void);

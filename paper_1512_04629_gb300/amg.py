@@ -103,6 +103,7 @@ SIGNATURES = {
     "amg_last_error": (C.c_char_p, []),
     "amg_device_bytes": (_i64, [_vp]),
     "amg_kernel_launches": (_i64, []),
+    "amg_residual_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "amg_server_opts_default": (None, [C.POINTER(ServerOpts)]),
     "amg_server_create": (_i, [C.POINTER(ServerOpts), C.POINTER(_vp)]),
     "amg_server_register": (_i, [_vp, _vp, C.POINTER(_i)]),
