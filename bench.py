@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-arms", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--eager", action="store_true",
+                   help="launch the PCG iterations one kernel at a time (no CUDA graph; for ncu launch lists)")
     p.add_argument("--ncu-solve", action="store_true",
                    help="set up once, then run one solve between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return p.parse_args()
@@ -250,7 +252,7 @@ def main():
     torch.cuda.synchronize()
 
     def step(timing=False):
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma)
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0 if args.eager else 1)
         if timing:
             h.timing_enable(True)
         x, info = h.solve(bd, xd, tol=args.tol)

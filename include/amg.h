@@ -70,7 +70,7 @@ enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_FP32_BF16 = 2 };
 enum {
     AMG_SPMV_AUTO = -1,
     AMG_SPMV_CSR2 = 1, AMG_SPMV_CSR4 = 2, AMG_SPMV_CSR8 = 3, AMG_SPMV_CSR16 = 4,
-    AMG_SPMV_CSR32 = 5, AMG_SPMV_SELL32 = 6
+    AMG_SPMV_CSR32 = 5, AMG_SPMV_SELL32 = 6, AMG_SPMV_CSR1 = 7
 };
 
 typedef struct {

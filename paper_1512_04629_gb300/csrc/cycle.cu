@@ -97,7 +97,7 @@ __device__ __forceinline__ XT sell_row_sum(int32_t i, const int32_t *__restrict_
     return acc;
 }
 
-enum Op { kPre = 0, kPost = 1, kSpmv = 2, kSpmvAdd = 3 };
+enum Op { kPre = 0, kPost = 1, kSpmv = 2, kSpmvAdd = 3, kSpmvScale = 4, kResX = 5 };
 
 template <typename VT, typename XT, int T, int OP>
 __global__ void __launch_bounds__(kThreads)
@@ -121,6 +121,11 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
         o1[i] = x[i] + dinv[i] * (b[i] - s);
     } else if (OP == kSpmv) {
         o1[i] = s;
+    } else if (OP == kSpmvScale) {
+        o1[i] = s;
+        o2[i] = s * dinv[i];
+    } else if (OP == kResX) {
+        o2[i] = b[i] - s;
     } else {
         o1[i] += s;
     }
@@ -144,6 +149,11 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ soff, const int32_t *__res
         o1[i] = x[i] + dinv[i] * (b[i] - s);
     } else if (OP == kSpmv) {
         o1[i] = s;
+    } else if (OP == kSpmvScale) {
+        o1[i] = s;
+        o2[i] = s * dinv[i];
+    } else if (OP == kResX) {
+        o2[i] = b[i] - s;
     } else {
         o1[i] += s;
     }
@@ -159,6 +169,7 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);
         switch (T) {
+            case 1: { csr_op_kernel<VT, XT, 1, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
             case 2: { csr_op_kernel<VT, XT, 2, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
             case 4: { csr_op_kernel<VT, XT, 4, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
             case 8: { csr_op_kernel<VT, XT, 8, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
@@ -444,6 +455,7 @@ __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci
 
 int threads_per_row(int variant) {
     switch (variant) {
+        case AMG_SPMV_CSR1: return 1;
         case AMG_SPMV_CSR2: return 2;
         case AMG_SPMV_CSR4: return 4;
         case AMG_SPMV_CSR8: return 8;
@@ -465,6 +477,14 @@ template <typename VT, typename XT>
 void spmv(const CycMat<VT> &A, const XT *x, XT *y, bool accumulate, cudaStream_t s) {
     if (accumulate) dispatch_op<VT, XT, kSpmvAdd>(A, nullptr, nullptr, x, y, nullptr, s);
     else dispatch_op<VT, XT, kSpmv>(A, nullptr, nullptr, x, y, nullptr, s);
+}
+template <typename VT, typename XT>
+void spmv_scaled(const CycMat<VT> &A, const XT *x, const XT *d, XT *y, XT *xs, cudaStream_t s) {
+    dispatch_op<VT, XT, kSpmvScale>(A, nullptr, d, x, y, xs, s);
+}
+template <typename VT, typename XT>
+void residual_from_x(const CycMat<VT> &A, const XT *b, const XT *x, XT *r, cudaStream_t s) {
+    dispatch_op<VT, XT, kResX>(A, b, nullptr, x, nullptr, r, s);
 }
 
 template <typename XT>
@@ -557,7 +577,9 @@ void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, con
 #define AMG_INST(VT, XT)                                                                                  \
     template void pre_smooth_residual<VT, XT>(const CycMat<VT> &, const XT *, const XT *, XT *, XT *, cudaStream_t); \
     template void post_smooth<VT, XT>(const CycMat<VT> &, const XT *, const XT *, const XT *, XT *, cudaStream_t); \
-    template void spmv<VT, XT>(const CycMat<VT> &, const XT *, XT *, bool, cudaStream_t);
+    template void spmv<VT, XT>(const CycMat<VT> &, const XT *, XT *, bool, cudaStream_t); \
+    template void spmv_scaled<VT, XT>(const CycMat<VT> &, const XT *, const XT *, XT *, XT *, cudaStream_t); \
+    template void residual_from_x<VT, XT>(const CycMat<VT> &, const XT *, const XT *, XT *, cudaStream_t);
 AMG_INST(double, double)
 AMG_INST(float, float)
 AMG_INST(__nv_bfloat16, float)

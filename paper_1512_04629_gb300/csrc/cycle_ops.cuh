@@ -54,6 +54,12 @@ template <typename VT, typename XT>
 void post_smooth(const CycMat<VT> &A, const XT *x, const XT *b, const XT *dinv, XT *xo, cudaStream_t s);
 template <typename VT, typename XT>
 void spmv(const CycMat<VT> &A, const XT *x, XT *y, bool accumulate, cudaStream_t s);
+// restriction with the coarse pre-smooth folded in: y = A x, xs = d .* y
+template <typename VT, typename XT>
+void spmv_scaled(const CycMat<VT> &A, const XT *x, const XT *d, XT *y, XT *xs, cudaStream_t s);
+// pre-smooth residual when x = D^{-1} b is already stored: r = b - A x
+template <typename VT, typename XT>
+void residual_from_x(const CycMat<VT> &A, const XT *b, const XT *x, XT *r, cudaStream_t s);
 
 // coarsest level: x = inv * b (dense, FP64 inverse)
 template <typename XT>

@@ -281,7 +281,7 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
             cyc::convert_values<float>(V.R.v(), V.rv32.as<float>(), V.R.nnz, s);
         }
     }
-    if (has_p) {
+    if (has_p && !V.pr_tuned) {
         V.variant_p = heuristic_variant(V.P);
         V.variant_r = heuristic_variant(V.R);
     }
@@ -318,8 +318,69 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     }
 }
 
+// Transfer operators: time prolongation (x += P x_c) and restriction
+// (b_c = R r, x_c = d_c b_c) under the vector-CSR widths that fit their mean
+// row, keep the fastest (cached per shape like the relaxation).
+template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaStream_t s) {
+    Level &V = *h.lev[l];
+    Level &C = *h.lev[l + 1];
+    int vb = sizeof(XT);
+    cudaEvent_t e0, e1;
+    AMG_CUDA(cudaEventCreate(&e0));
+    AMG_CUDA(cudaEventCreate(&e1));
+    auto tune = [&](const DevCSR &M, int kind, int &variant, auto run) {
+        TuneKey key{M.nrows, M.nnz, 100 * kind + vb};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) { variant = it->second; return; }
+        }
+        double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
+        int V16 = 16 / vb;
+        float best = 1e30f;
+        int best_v = variant;
+        const int vars[] = {AMG_SPMV_CSR1, AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16};
+        for (int v : vars) {
+            double cover = (double)cyc::threads_per_row(v) * V16;
+            if (v != AMG_SPMV_CSR1 && !(cover >= mean / 4.0 && cover <= std::max(4.0 * mean, (double)V16 * 2))) continue;
+            variant = v;
+            run();
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                AMG_CUDA(cudaEventRecord(e0, s));
+                run();
+                AMG_CUDA(cudaEventRecord(e1, s));
+                AMG_CUDA(cudaEventSynchronize(e1));
+                float ms;
+                AMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                tmin = std::min(tmin, ms);
+            }
+            if (tmin < best * 0.98f) { best = tmin; best_v = v; }
+        }
+        variant = best_v;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best_v;
+    };
+    if (V.P.nnz >= 20000) {
+        tune(V.P, 1, V.variant_p, [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
+        tune(V.R, 2, V.variant_r, [&] {
+            cyc::spmv_scaled<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), dinv_of<XT>(C), C.b.as<XT>(), C.x.as<XT>(), s);
+        });
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
     for (int l : levels) prepare_level(h, l, s);
+    if (h.opt.spmv_variant == AMG_SPMV_AUTO) {
+        for (int l : levels) {
+            if (l + 1 >= h.nlev() || h.lev[l]->pr_tuned) continue;
+            if (h.opt.precision == AMG_PREC_FP64) autotune_transfers<double>(h, l, s);
+            else autotune_transfers<float>(h, l, s);
+            h.lev[l]->pr_tuned = true;
+        }
+    }
     h.graph_dirty = true;
     AMG_CUDA(cudaStreamSynchronize(s));
 }
@@ -348,6 +409,10 @@ void ensure_workspace(Hierarchy &h, cudaStream_t s) {
 // algorithmic bytes (compulsory HBM traffic) per kernel launch
 // ---------------------------------------------------------------------------
 static double bytes_pre(int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + 4.0 * n * xb; }
+// levels >= 1: x = D^{-1} b was written by the restriction; read b, x, write r
+static double bytes_pre_x(int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + 3.0 * n * xb; }
+// restriction that also writes the coarse pre-smooth x_c = d_c .* b_c
+static double bytes_restrict_x(int64_t nc, int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (nc + 1) + (double)(n + 3 * nc) * xb; }
 static double bytes_post(int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + 4.0 * n * xb; }
 static double bytes_restrict(int64_t nc, int64_t n, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (nc + 1) + (double)(n + nc) * xb; }
 static double bytes_prolong(int64_t n, int64_t nc, int64_t nnz, int vb, int xb) { return (double)nnz * (vb + 4) + 4.0 * (n + 1) + (double)(nc + 2 * n) * xb; }
@@ -357,8 +422,10 @@ double level_cycle_bytes(const Hierarchy &h, int l) {
     int xb = h.opt.precision == AMG_PREC_FP64 ? 8 : 4;
     int64_t n = V.n(), nnz = V.op().nnz;
     if (l == h.nlev() - 1) return (double)n * n * 8 + 2.0 * n * xb;
-    double b = bytes_pre(n, nnz, V.vbytes, xb) + bytes_post(n, nnz, V.vbytes, xb);
-    b += bytes_restrict(V.R.nrows, n, V.R.nnz, xb, xb) + bytes_prolong(n, V.P.ncols, V.P.nnz, xb, xb);
+    double b = (l == 0 ? bytes_pre(n, nnz, V.vbytes, xb) : bytes_pre_x(n, nnz, V.vbytes, xb)) +
+               bytes_post(n, nnz, V.vbytes, xb);
+    b += (l + 2 < h.nlev() ? bytes_restrict_x(V.R.nrows, n, V.R.nnz, xb, xb) : bytes_restrict(V.R.nrows, n, V.R.nnz, xb, xb)) +
+         bytes_prolong(n, V.P.ncols, V.P.nnz, xb, xb);
     return b;
 }
 
@@ -405,18 +472,34 @@ void timing_collect(Hierarchy &h) {
 // ---------------------------------------------------------------------------
 // Algorithm 2: V(1,1) on the residual equation, zero initial guess per level
 // ---------------------------------------------------------------------------
+// Pre-smooth from zero and residual.  Level 0 forms x = D^{-1} b here (one
+// pass, gathering b and d); on coarser levels the restriction already wrote
+// x = D^{-1} b, so the pass gathers x alone.
 template <typename XT>
 static void relax_pre(Hierarchy &h, int l, const XT *b, cudaStream_t s) {
     Level &V = *h.lev[l];
     int xb = sizeof(XT);
-    timed(h, 0, l, bytes_pre(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
+    if (l == 0) {
+        timed(h, 0, l, bytes_pre(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
+            if constexpr (sizeof(XT) == 8) {
+                cyc::pre_smooth_residual<double, double>(op_mat<double>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+            } else {
+                if (V.vbytes == 2)
+                    cyc::pre_smooth_residual<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+                else
+                    cyc::pre_smooth_residual<float, float>(op_mat<float>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+            }
+        });
+        return;
+    }
+    timed(h, 0, l, bytes_pre_x(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
         if constexpr (sizeof(XT) == 8) {
-            cyc::pre_smooth_residual<double, double>(op_mat<double>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+            cyc::residual_from_x<double, double>(op_mat<double>(V), b, V.x.as<XT>(), V.r.as<XT>(), s);
         } else {
             if (V.vbytes == 2)
-                cyc::pre_smooth_residual<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+                cyc::residual_from_x<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), b, V.x.as<XT>(), V.r.as<XT>(), s);
             else
-                cyc::pre_smooth_residual<float, float>(op_mat<float>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
+                cyc::residual_from_x<float, float>(op_mat<float>(V), b, V.x.as<XT>(), V.r.as<XT>(), s);
         }
     });
 }
@@ -451,8 +534,14 @@ static void vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s) {
         const XT *b = l == 0 ? b0 : V.b.as<XT>();
         relax_pre<XT>(h, l, b, s);
         Level &C = *h.lev[l + 1];
-        timed(h, 1, l, bytes_restrict(V.R.nrows, V.n(), V.R.nnz, xb, xb), s,
-              [&] { cyc::spmv<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), C.b.as<XT>(), false, s); });
+        if (l + 2 < L) {  // the coarse level relaxes: fold its x = D^{-1} b into the restriction
+            timed(h, 1, l, bytes_restrict_x(V.R.nrows, V.n(), V.R.nnz, xb, xb), s, [&] {
+                cyc::spmv_scaled<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), dinv_of<XT>(C), C.b.as<XT>(), C.x.as<XT>(), s);
+            });
+        } else {
+            timed(h, 1, l, bytes_restrict(V.R.nrows, V.n(), V.R.nnz, xb, xb), s,
+                  [&] { cyc::spmv<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), C.b.as<XT>(), false, s); });
+        }
     }
     Level &Cl = *h.lev[L - 1];
     timed(h, 4, L - 1, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,

@@ -36,6 +36,7 @@ struct Level {
     DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
     int64_t sell_entries = 0;
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
+    bool pr_tuned = false;  // transfer-operator variants chosen by timed trials
 
     // work vectors in the cycle precision (b, x, r, post-smoothed output)
     DevBuf b, x, r, xo;

@@ -394,51 +394,212 @@ __global__ void spgemm_ub_kernel(int32_t n, const int32_t *arp, const int32_t *a
     ub[i] = s;
 }
 
-constexpr int kWarpHS = 1024, kWarpUmax = 512, kWarpsPerBlock = 4;
 constexpr int kBlockHS = 8192, kBlockUmax = 4096, kBlockThreads = 256;
+constexpr int kTinyUmax = 64, kTinyWarps = 8;     // bin 0: <= 64 products per row
+constexpr int kSmallUmax = 512, kSmallWarps = 4;  // bin 1: <= 512 products per row
 
-// rows -> three bins by upper bound; one global atomic per bin per block
 __global__ void bin_rows_kernel(int32_t n, const int64_t *ub, int32_t *bins, int32_t *bin_count) {
-    __shared__ int32_t local[3], base[3];
-    if (threadIdx.x < 3) local[threadIdx.x] = 0;
+    __shared__ int32_t local[4], base[4];
+    if (threadIdx.x < 4) local[threadIdx.x] = 0;
     __syncthreads();
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = -1;
     int32_t my = 0;
     if (i < n) {
-        b = ub[i] <= kWarpUmax ? 0 : (ub[i] <= kBlockUmax ? 1 : 2);
+        int64_t u = ub[i];
+        b = u <= kTinyUmax ? 0 : (u <= kSmallUmax ? 1 : (u <= kBlockUmax ? 2 : 3));
         my = atomicAdd(&local[b], 1);
     }
     __syncthreads();
-    if (threadIdx.x < 3) base[threadIdx.x] = local[threadIdx.x] ? atomicAdd(&bin_count[threadIdx.x], local[threadIdx.x]) : 0;
+    if (threadIdx.x < 4) base[threadIdx.x] = local[threadIdx.x] ? atomicAdd(&bin_count[threadIdx.x], local[threadIdx.x]) : 0;
     __syncthreads();
     if (b >= 0) bins[(int64_t)b * n + base[b] + my] = i;
 }
 
-template <bool NUMERIC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// Per-warp shared layout for rows of at most U products: product values,
+// hash keys and ranks (2U slots), distinct columns, per-column counts /
+// cursors, product columns (later ranks), and the stable permutation.
+template <int U> struct WarpTab {
+    static constexpr size_t kBytes = (size_t)U * 8 + (size_t)4 * U * 4 + (size_t)(U + 4) * 4 + (size_t)U * 4 * 3;
+    double *pv;
+    int32_t *keys, *rank, *list, *cnt, *pj, *perm;
+    __device__ WarpTab(unsigned char *base) {
+        pv = reinterpret_cast<double *>(base);
+        keys = reinterpret_cast<int32_t *>(base + (size_t)U * 8);
+        rank = keys + 2 * U;
+        cnt = rank + 2 * U;
+        list = cnt + U + 4;
+        pj = list + U;
+        perm = pj + U;
+    }
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// One row of C = A B by one warp, all lanes working on the flattened product
+// space.  Symbolic: returns the number of distinct columns.  Numeric: writes
+// the sorted columns and, for every column, the sum of its products in the
+// order of A's row (a stable scatter keeps product order), i.e. exactly the
+// dense-accumulator order.
+template <int U, bool NUMERIC>
+__device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
+                            const double *__restrict__ av, const int32_t *__restrict__ brp,
+                            const int32_t *__restrict__ bci, const double *__restrict__ bv, WarpTab<U> &t,
+                            int64_t ub, const int32_t *__restrict__ crp, int32_t *__restrict__ cci,
+                            double *__restrict__ cv) {
+    const int32_t hs = row_slots(ub, 2 * U);
+    const uint32_t mask = (uint32_t)hs - 1;
+    for (int32_t s = lane; s < hs; s += 32) t.keys[s] = -1;
+    __syncwarp();
+    const int32_t p0 = arp[i], nA = arp[i + 1] - p0;
+    int32_t np = 0, uniq = 0;
+    for (int32_t c0 = 0; c0 < nA; c0 += 32) {
+        int32_t idx = c0 + lane, b0 = 0, len = 0;
+        double a = 0.0;
+        if (idx < nA) {
+            int32_t k = aci[p0 + idx];
+            if (NUMERIC) a = av[p0 + idx];
+            b0 = brp[k];
+            len = brp[k + 1] - b0;
+        }
+        int32_t incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int32_t excl = incl - len;
+        const int32_t total = __shfl_sync(kFull, incl, 31);
+        for (int32_t eb = 0; eb < total; eb += 32) {
+            const int32_t e = eb + lane;
+            int lo = 0;
+            for (int st = 16; st > 0; st >>= 1) {
+                int cand = lo + st;
+                int32_t ex = __shfl_sync(kFull, excl, cand & 31);
+                if (cand < 32 && ex <= e) lo = cand;
+            }
+            const int32_t kb0 = __shfl_sync(kFull, b0, lo);
+            const int32_t kex = __shfl_sync(kFull, excl, lo);
+            const double ka = __shfl_sync(kFull, a, lo);
+            if (e < total) {
+                const int32_t q = kb0 + (e - kex);
+                const int32_t j = bci[q];
+                const int32_t E = np + e;
+                if (NUMERIC) {
+                    t.pj[E] = j;
+                    t.pv[E] = ka * bv[q];
+                }
+                uint32_t sl = hash32(j) & mask;
+                while (true) {
+                    int32_t old = atomicCAS(&t.keys[sl], -1, j);
+                    if (old == -1) { ++uniq; break; }
+                    if (old == j) break;
+                    sl = (sl + 1) & mask;
+                }
+            }
+        }
+        np += total;
+    }
+    for (int o = 16; o > 0; o >>= 1) uniq += __shfl_xor_sync(kFull, uniq, o);
+    __syncwarp();
+    if (!NUMERIC) return uniq;
+    const int32_t u = uniq;
+    // distinct columns -> list (ballot compaction), pad, bitonic sort
+    int32_t base = 0;
+    for (int32_t s0 = 0; s0 < hs; s0 += 32) {
+        int32_t key = s0 + lane < hs ? t.keys[s0 + lane] : -1;
+        unsigned m = __ballot_sync(kFull, key >= 0);
+        if (key >= 0) t.list[base + __popc(m & ((1u << lane) - 1u))] = key;
+        base += __popc(m);
+    }
+    int32_t m2 = 1;
+    while (m2 < u) m2 <<= 1;
+    for (int32_t r = u + lane; r < m2; r += 32) t.list[r] = INT_MAX;
+    __syncwarp();
+    for (int32_t size = 2; size <= m2; size <<= 1) {
+        for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int32_t r = lane; r < m2; r += 32) {
+                int32_t partner = r ^ stride;
+                if (partner > r) {
+                    bool up = (r & size) == 0;
+                    int32_t x = t.list[r], y = t.list[partner];
+                    if ((x > y) == up) { t.list[r] = y; t.list[partner] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    const int32_t cbase = crp[i];
+    for (int32_t r = lane; r < u; r += 32) {
+        int32_t j = t.list[r];
+        uint32_t sl = hash32(j) & mask;
+        while (t.keys[sl] != j) sl = (sl + 1) & mask;
+        t.rank[sl] = r;
+        t.cnt[r] = 0;
+        cci[cbase + r] = j;
+    }
+    __syncwarp();
+    // products per column
+    for (int32_t e = lane; e < np; e += 32) {
+        int32_t j = t.pj[e];
+        uint32_t sl = hash32(j) & mask;
+        while (t.keys[sl] != j) sl = (sl + 1) & mask;
+        int32_t r = t.rank[sl];
+        t.pj[e] = r;
+        atomicAdd(&t.cnt[r], 1);
+    }
+    __syncwarp();
+    // counts -> start offsets
+    int32_t carry = 0;
+    for (int32_t r0 = 0; r0 < u; r0 += 32) {
+        int32_t r = r0 + lane;
+        int32_t c = r < u ? t.cnt[r] : 0;
+        int32_t incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (r < u) t.cnt[r] = carry + incl - c;
+        carry += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+    // stable scatter: product e goes to the next free slot of its column, in e order
+    for (int32_t eb = 0; eb < np; eb += 32) {
+        const int32_t e = eb + lane;
+        const bool valid = e < np;
+        const int32_t r = valid ? t.pj[e] : -1 - lane;
+        const unsigned peers = __match_any_sync(kFull, r);
+        const int32_t within = __popc(peers & ((1u << lane) - 1u));
+        const int32_t pos = valid ? t.cnt[r] + within : 0;
+        __syncwarp();
+        if (valid) {
+            t.perm[pos] = e;
+            if (lane == __ffs(peers) - 1) t.cnt[r] += __popc(peers);
+        }
+        __syncwarp();
+    }
+    // cnt[r] now holds the end of column r's segment (= start of r + 1)
+    for (int32_t r = lane; r < u; r += 32) {
+        int32_t s0 = r == 0 ? 0 : t.cnt[r - 1], s1 = t.cnt[r];
+        double acc = 0.0;
+        for (int32_t p = s0; p < s1; ++p) acc += t.pv[t.perm[p]];
+        cv[cbase + r] = acc;
+    }
+    __syncwarp();
+    return u;
+}
+
+template <int U, int WARPS, bool NUMERIC>
+__global__ void __launch_bounds__(WARPS * 32)
 spgemm_warp_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                    const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
                    int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv, const int64_t *ub) {
     extern __shared__ __align__(16) unsigned char smem[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *base = smem + (size_t)w * (kWarpHS * 8 + kWarpUmax * 12 + 16);
-    RowTables t;
-    t.acc = reinterpret_cast<double *>(base);
-    t.keys = reinterpret_cast<int32_t *>(base + kWarpUmax * 8);
-    t.rank = t.keys + kWarpHS;
-    t.list = t.rank + kWarpHS;
-    t.hs = kWarpHS;
-    t.umax = kWarpUmax;  // capacity: hs is chosen per row
-    int32_t *counter = t.list + kWarpUmax;
-    for (int32_t r = blockIdx.x * kWarpsPerBlock + w; r < nrows; r += gridDim.x * kWarpsPerBlock) {
+    WarpTab<U> t(smem + (size_t)w * WarpTab<U>::kBytes);
+    for (int32_t r = blockIdx.x * WARPS + w; r < nrows; r += gridDim.x * WARPS) {
         int32_t i = rows[r];
-        if (NUMERIC) {
-            row_numeric<32>(i, lane, arp, aci, av, brp, bci, bv, t, counter, crp, cci, cv, ub[i]);
-        } else {
-            int32_t u = row_insert<32>(i, lane, arp, aci, brp, bci, t, counter, ub[i]);
-            if (lane == 0) cnt[i] = u;
-        }
+        int32_t u = warp_row<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], crp, cci, cv);
+        if (!NUMERIC && lane == 0) cnt[i] = u;
     }
 }
 
@@ -779,7 +940,7 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         Cm.val.alloc(sizeof(double) * kPad);
         return;
     }
-    DevBuf ub(sizeof(int64_t) * n), bins(sizeof(int32_t) * 3 * (size_t)n), bcount(sizeof(int32_t) * 4),
+    DevBuf ub(sizeof(int64_t) * n), bins(sizeof(int32_t) * 4 * (size_t)n), bcount(sizeof(int32_t) * 4),
         cnt(sizeof(int32_t) * (n + 1));
     int g = div_up(n, kThreads);
     { spgemm_ub_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), B.rp(), ub.as<int64_t>()); ::amg::count_launch(); }
@@ -799,12 +960,16 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     const int32_t *rows0 = bins.as<int32_t>();
     const int32_t *rows1 = rows0 + n;
     const int32_t *rows2 = rows0 + 2 * (size_t)n;
-    size_t warp_smem = (size_t)kWarpsPerBlock * (kWarpHS * 8 + kWarpUmax * 12 + 16);
+    const int32_t *rows3 = rows0 + 3 * (size_t)n;
+    size_t tiny_smem = (size_t)kTinyWarps * WarpTab<kTinyUmax>::kBytes;
+    size_t small_smem = (size_t)kSmallWarps * WarpTab<kSmallUmax>::kBytes;
     size_t block_smem = (size_t)kBlockHS * 8 + (size_t)kBlockUmax * 12;
     static bool attrs = false;
     if (!attrs) {
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem));
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kTinyUmax, kTinyWarps, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiny_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kTinyUmax, kTinyWarps, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiny_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kSmallUmax, kSmallWarps, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kSmallUmax, kSmallWarps, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
         attrs = true;
@@ -813,43 +978,56 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     int64_t ghs = 2 * gumax;
     int gblocks = 0;
     DevBuf gscr;
-    if (nb[2] > 0) {
+    if (nb[3] > 0) {
         size_t per = (size_t)ghs * 8 + (size_t)gumax * 12;
         int64_t cap = std::max<int64_t>(1, (int64_t)(((size_t)2 << 30) / per));  // <= 2 GiB scratch
-        gblocks = (int)std::min<int64_t>({(int64_t)nb[2], 304, cap});
+        gblocks = (int)std::min<int64_t>({(int64_t)nb[3], 304, cap});
         gscr.alloc(per * gblocks);
     }
+    const int64_t *ubp = ub.as<int64_t>();
     auto launch = [&](bool numeric) {
         int32_t *cp = cnt.as<int32_t>();
+        int32_t *cc = numeric ? Cm.ci() : nullptr;
+        double *cvv = numeric ? Cm.v() : nullptr;
+        const int32_t *crp = numeric ? Cm.rp() : nullptr;
         if (nb[0] > 0) {
-            int blocks = std::min(div_up(nb[0], kWarpsPerBlock), 152 * 16);
+            int blocks = std::min(div_up(nb[0], kTinyWarps), 152 * 32);
             if (numeric)
-                { spgemm_warp_kernel<true><<<blocks, kWarpsPerBlock * 32, warp_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(), ub.as<int64_t>()); ::amg::count_launch(); }
+                { spgemm_warp_kernel<kTinyUmax, kTinyWarps, true><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
             else
-                { spgemm_warp_kernel<false><<<blocks, kWarpsPerBlock * 32, warp_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr, ub.as<int64_t>()); ::amg::count_launch(); }
+                { spgemm_warp_kernel<kTinyUmax, kTinyWarps, false><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[1] > 0) {
-            int blocks = std::min(nb[1], 152 * 4);
+            int blocks = std::min(div_up(nb[1], kSmallWarps), 152 * 16);
             if (numeric)
-                { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
-                    ub.as<int64_t>(), nullptr, 0, 0); ::amg::count_launch(); }
+                { spgemm_warp_kernel<kSmallUmax, kSmallWarps, true><<<blocks, kSmallWarps * 32, small_smem, s>>>(
+                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
             else
-                { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
-                    ub.as<int64_t>(), nullptr, 0, 0); ::amg::count_launch(); }
+                { spgemm_warp_kernel<kSmallUmax, kSmallWarps, false><<<blocks, kSmallWarps * 32, small_smem, s>>>(
+                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[2] > 0) {
+            int blocks = std::min(nb[2], 152 * 4);
+            if (numeric)
+                { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
+                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
+                    ubp, nullptr, 0, 0); ::amg::count_launch(); }
+            else
+                { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
+                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
+                    ubp, nullptr, 0, 0); ::amg::count_launch(); }
+        }
+        if (nb[3] > 0) {
             if (numeric)
                 { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
-                    ub.as<int64_t>(), gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
+                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
+                    ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
-                    ub.as<int64_t>(), gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
+                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
+                    ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
         }
         AMG_CHECK_LAUNCH();
     };

@@ -128,7 +128,7 @@ def test_sparsify_on_oracle_galerkin(amg, gamma):
         assert st["nnz_operator"] == ref.matrix(l, "Ahat").nnz
 
 
-@pytest.mark.parametrize("variant", [-1, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [-1, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("gamma", [0.0, 0.1])
 def test_vcycle_matches_oracle(amg, variant, gamma):
     A = gen.poisson3d_7pt(23)  # n = 12167: ragged against 32-row slices and 256-thread blocks
