@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--no-arms", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                   help="c2 (default, the bench line): 3D 7-pt 128^3; c3: 27-pt 192^3 precision arms; "
+                        "c4: lognormal FV 160^3 batched k in {1,8,32,64}; c5: serving stream")
+    p.add_argument("--serve-seconds", type=float, default=20.0)
     p.add_argument("--eager", action="store_true",
                    help="launch the PCG iterations one kernel at a time (no CUDA graph; for ncu launch lists)")
     p.add_argument("--ncu-solve", action="store_true",
@@ -213,10 +217,155 @@ def collect_timing(h, nlev):
     return rows
 
 
+# ---------------------------------------------------------------------------
+# other workloads (measured one line each; not the default bench line)
+# ---------------------------------------------------------------------------
+def _events_ms(fn, reps=3):
+    import torch
+
+    times, out = [], None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times), out
+
+
+def run_c3(args):
+    """27-point 192^3: FP64 vs FP32 vs FP32+BF16 cycles, Galerkin and gamma 0.1."""
+    import numpy as np
+    import torch
+
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    N = 192 if args.grid == 128 else args.grid
+    A = gen.poisson3d_27pt(N)
+    b = gen.rhs_uniform(A.n, 2)
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+    A_dev = amg.amg.csr_struct(rp, ci, va)
+    bd = torch.from_numpy(b).cuda()
+    res, xref = {}, None
+    for g in (0.0, 0.1):
+        for prec, pname in ((0, "fp64"), (1, "fp32"), (2, "fp32_bf16")):
+            t0 = time.perf_counter()
+            h = amg.Hierarchy.setup(A_dev, gamma=[0.0, g] if g else None, precision=prec)
+            torch.cuda.synchronize()
+            setup_ms = 1e3 * (time.perf_counter() - t0)
+            xd = torch.zeros_like(bd)
+            ms, (x, info) = _events_ms(lambda: h.solve(bd, xd, tol=args.tol))
+            if prec == 0 and g == 0.0:
+                xref = x.clone()
+            err = float(torch.linalg.norm(x - xref) / torch.linalg.norm(xref))
+            res[f"gamma{g}_{pname}"] = {"solve_ms": ms, "setup_ms": setup_ms, "iterations": info.iterations,
+                                       "final_relres": info.final_relres, "rel_err_vs_fp64_galerkin": err,
+                                       "levels": h.num_levels,
+                                       "nnz_per_level": [h.level_stats(l)["nnz_operator"] for l in range(h.num_levels)],
+                                       "value_bytes": [h.level_stats(l)["value_bytes"] for l in range(h.num_levels)]}
+            del h
+    print(json.dumps({"workload": f"c3: 3D 27-point {N}^3 (n={A.n}, nnz={A.nnz}) precision arms", "unit": "ms",
+                      "arms": res}))
+
+
+def run_c4(args):
+    """Lognormal FV 160^3, FP32 cycle, gamma 0.1: batched solves for k in {1,8,32,64}."""
+    import numpy as np
+    import torch
+
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    N = 160 if args.grid == 128 else args.grid
+    A = gen.fv7_lognormal(N, seed=3)
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+    A_dev = amg.amg.csr_struct(rp, ci, va)
+    out = {}
+    h64 = amg.Hierarchy.setup(A_dev, gamma=[0.0, 0.1], precision=0)
+    b0 = torch.from_numpy(gen.rhs_uniform(A.n, 0)).cuda()
+    ms64, (_, i64) = _events_ms(lambda: h64.solve(b0, tol=args.tol))
+    out["fp64_single"] = {"solve_ms": ms64, "solves_per_s": 1e3 / ms64, "iterations": i64.iterations}
+    del h64
+    h = amg.Hierarchy.setup(A_dev, gamma=[0.0, 0.1], precision=1)
+    for k in (1, 8, 32, 64):
+        B = torch.from_numpy(np.stack([gen.rhs_uniform(A.n, c) for c in range(k)], axis=1)).cuda().contiguous()
+        if k == 1:
+            bb = B[:, 0].contiguous()
+            ms, (_, inf) = _events_ms(lambda: h.solve(bb, tol=args.tol))
+            its, ok = [inf.iterations], inf.status == 0 and inf.final_relres <= args.tol
+        else:
+            ms, (_, infos) = _events_ms(lambda: h.solve_batch(B, tol=args.tol), reps=2)
+            its = [i.iterations for i in infos]
+            ok = all(i.status == 0 and i.final_relres <= args.tol for i in infos)
+        out[f"fp32_k{k}"] = {"ms": ms, "solves_per_s": k * 1e3 / ms, "iterations_max": max(its),
+                             "iterations_min": min(its), "all_converged": ok}
+        del B
+    print(json.dumps({"workload": f"c4: lognormal FV 7-pt {N}^3 (n={A.n}), gamma 0.1, FP32 cycle / FP64 outer",
+                      "arms": out}))
+
+
+def run_c5(args):
+    """Serving: 8 resident hierarchies, Poisson arrivals at 200/s, continuous batching."""
+    import numpy as np
+
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    kinds = [("2d5", 256), ("2d5", 512), ("2d5", 1024), ("2d5", 2048),
+             ("3d7", 32), ("3d7", 64), ("3d7", 96), ("3d7", 128)]
+    hs, ns = [], []
+    for kind, N in kinds:
+        A = gen.generate(kind, N)
+        hs.append(amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=1))
+        ns.append(A.n)
+    srv = amg.Server(max_batch=32)
+    ids = [srv.register(h) for h in hs]
+    rng = np.random.default_rng(5)
+    rate, T = 200.0, args.serve_seconds
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * T * 1.5)))
+    arrivals = arrivals[arrivals < T]
+    picks = rng.integers(0, len(hs), size=len(arrivals))
+    tickets = []
+    t0 = time.perf_counter()
+    for r, (ta, hid) in enumerate(zip(arrivals, picks)):
+        b = gen.rhs_uniform(ns[hid], 10_000 + r)
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append((srv.submit(ids[hid], b), hid))
+    lat, its, bad = [], [], 0
+    for t, hid in tickets:
+        st, x, info = srv.wait(t, ids[hid], timeout_ms=600000)
+        if st != 0 or info.final_relres > args.tol:
+            bad += 1
+        lat.append(info.solve_ms)
+        its.append(info.iterations)
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    print(json.dumps({"workload": "c5: serving 8 hierarchies (2D 256^2..2048^2, 3D 32^3..128^3, gamma 0.1, FP32 cycle), "
+                                  f"Poisson arrivals {rate:g}/s for {T:g} s, max_batch 32",
+                      "requests": len(tickets), "failed": bad, "solves_per_s": len(tickets) / wall,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "max_ms": float(lat.max()), "iterations_median": float(np.median(its))}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "c2":
+        import torch
+
+        from paper_1512_04629_gb300 import build
+
+        build.build()
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
         return
     import numpy as np
     import torch
@@ -259,7 +408,7 @@ def main():
         return h, info
 
     if args.ncu_solve:
-        h, info = step()
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
         h.solve(bd, xd, tol=args.tol)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()

@@ -16,6 +16,7 @@
 namespace amg {
 
 BatchWS::~BatchWS() {
+    if (graph) cudaGraphExecDestroy(graph);
     if (h_d) cudaFreeHost(h_d);
     if (h_i) cudaFreeHost(h_i);
 }
@@ -127,7 +128,7 @@ static CycMat<double> a0(Hierarchy &h) {
 // One CG step for every active column: Z = M R; rho, beta; P = Z + beta P;
 // Q = A P, alpha; X += alpha P, R -= alpha Q, rr.  Scalars are copied to the
 // pinned host mirror; the caller synchronises the stream before reading.
-void batch_iteration(Hierarchy &h, BatchWS &w, cudaStream_t s) {
+static void batch_iteration_body(Hierarchy &h, BatchWS &w, cudaStream_t s) {
     int32_t n = h.lev[0]->n();
     int K = w.K;
     int flexible = h.opt.precision != AMG_PREC_FP64;
@@ -139,6 +140,38 @@ void batch_iteration(Hierarchy &h, BatchWS &w, cudaStream_t s) {
     bat::xr_update(n, K, w.P.as<double>(), w.Q.as<double>(), w.X.as<double>(), w.R.as<double>(), w.sc,
                    w.partials.as<double>(), w.counter.as<unsigned>(), s);
     AMG_CUDA(cudaMemcpyAsync(w.h_d, w.sc_buf.ptr, sizeof(double) * 6 * K, cudaMemcpyDeviceToHost, s));
+}
+
+// The iteration is captured once per (workspace, hierarchy version) and then
+// launched as one graph: ~4 L + 8 kernels and a copy per launch.
+void batch_iteration(Hierarchy &h, BatchWS &w, cudaStream_t s) {
+    if (!h.opt.use_graph) {
+        batch_iteration_body(h, w, s);
+        return;
+    }
+    if (!w.graph || w.graph_version != h.version) {
+        if (w.graph) cudaGraphExecDestroy(w.graph);
+        w.graph = nullptr;
+        cudaStream_t cs;
+        AMG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        AMG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        try {
+            batch_iteration_body(h, w, cs);
+        } catch (...) {
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        AMG_CUDA(cudaStreamEndCapture(cs, &g));
+        cudaError_t e = cudaGraphInstantiate(&w.graph, g, 0);
+        cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
+        AMG_CUDA(e);
+        w.graph_version = h.version;
+    }
+    AMG_CUDA(cudaGraphLaunch(w.graph, s));
 }
 
 // T = B - A X and tt per column
@@ -172,10 +205,10 @@ amg_status solve_batch(Hierarchy &h, int k, const double *B, double *X, bool on_
     BatchWS &w = batch_workspace(h, K, s);
     int32_t n = h.lev[0]->n();
     // stage B (n x k, caller layout) into the n x K block
-    DevBuf staged;
+    TmpBuf staged;
     const double *Bk = B;
     if (!on_device) {
-        staged.alloc(sizeof(double) * (size_t)n * k);
+        staged.alloc(sizeof(double) * (size_t)n * k, s);
         AMG_CUDA(cudaMemcpyAsync(staged.ptr, B, sizeof(double) * (size_t)n * k, cudaMemcpyHostToDevice, s));
         Bk = staged.as<double>();
     }

@@ -100,7 +100,7 @@ void check_options(const amg_options &o) {
     require(o.precision >= AMG_PREC_FP64 && o.precision <= AMG_PREC_FP32_BF16, "unknown precision");
     require(o.k_check >= 1 && o.s_levels >= 1, "k_check and s_levels must be >= 1");
     require(o.gamma_min >= 0.0 && std::isfinite(o.rho_max), "bad gamma_min / rho_max");
-    require(o.spmv_variant == AMG_SPMV_AUTO || (o.spmv_variant >= AMG_SPMV_CSR2 && o.spmv_variant <= AMG_SPMV_SELL32),
+    require(o.spmv_variant == AMG_SPMV_AUTO || (o.spmv_variant >= AMG_SPMV_CSR2 && o.spmv_variant <= AMG_SPMV_CSR1),
             "unknown spmv_variant");
     require(o.check_every >= 1, "check_every must be >= 1");
 }

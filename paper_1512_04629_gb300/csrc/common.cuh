@@ -73,6 +73,23 @@ struct DevBuf {
     template <typename T> T *as() const { return static_cast<T *>(ptr); }
 };
 
+// A temporary device buffer with stream-ordered lifetime: allocated with
+// cudaMallocAsync and returned with cudaFreeAsync on the stream that uses it,
+// so freeing never waits for the device (the pool keeps the memory).
+struct TmpBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    TmpBuf() = default;
+    TmpBuf(size_t b, cudaStream_t s) { alloc(b, s); }
+    TmpBuf(const TmpBuf &) = delete;
+    TmpBuf &operator=(const TmpBuf &) = delete;
+    ~TmpBuf() { release(); }
+    void alloc(size_t b, cudaStream_t s);
+    void release();
+    template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
 // A CSR matrix resident on the device (library-owned).
 struct DevCSR {
     int32_t nrows = 0, ncols = 0;

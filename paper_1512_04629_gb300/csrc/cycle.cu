@@ -83,10 +83,11 @@ __device__ __forceinline__ XT csr_row_sum(int32_t p0, int32_t p1, int t, const i
     return acc;
 }
 
+// sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32)
 template <typename VT, typename XT, class G>
-__device__ __forceinline__ XT sell_row_sum(int32_t i, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
+__device__ __forceinline__ XT sell_row_sum(int32_t pos, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                                            const int32_t *__restrict__ sci, const VT *__restrict__ sv, G gather) {
-    int32_t s = i >> 5, lane = i & 31;
+    int32_t s = pos >> 5, lane = pos & 31;
     int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
     XT acc = XT(0);
 #pragma unroll 4
@@ -133,14 +134,15 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
 
 template <typename VT, typename XT, int OP>
 __global__ void __launch_bounds__(kThreads)
-sell_op_kernel(int32_t n, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw, const int32_t *__restrict__ sci,
-               const VT *__restrict__ sv, const XT *__restrict__ b, const XT *__restrict__ dinv,
-               const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
+               const int32_t *__restrict__ sci, const VT *__restrict__ sv, const XT *__restrict__ b,
+               const XT *__restrict__ dinv, const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
+    int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    const int32_t i = perm ? __ldg(perm + pos) : pos;
     XT s;
-    if (OP == kPre) s = sell_row_sum<VT, XT>(i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT>(i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) s = sell_row_sum<VT, XT>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -164,7 +166,7 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
     int32_t n = A.nrows;
     if (n == 0) return;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        { sell_op_kernel<VT, XT, OP><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.soff, A.sw, A.sci, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        { sell_op_kernel<VT, XT, OP><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
     } else {
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);
@@ -275,12 +277,13 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
 
 // q = A p (SELL-32, one thread per row) and p . q
 __global__ void __launch_bounds__(kThreads)
-ap_sell_kernel(int32_t n, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw, const int32_t *__restrict__ sci,
-               const double *__restrict__ sv, const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc,
-               Reduce red) {
+ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
+               const int32_t *__restrict__ sci, const double *__restrict__ sv, const double *__restrict__ p,
+               double *__restrict__ q, PcgScalars *sc, Reduce red) {
     double part[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
-        double s = sell_row_sum<double, double>((int32_t)i, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
+    for (int64_t pos = (int64_t)blockIdx.x * kThreads + threadIdx.x; pos < n; pos += (int64_t)gridDim.x * kThreads) {
+        const int32_t i = perm ? __ldg(perm + pos) : (int32_t)pos;
+        double s = sell_row_sum<double, double>((int32_t)pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
         q[i] = s;
         part[0] += p[i] * s;
     }
@@ -321,13 +324,14 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
 __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
                  double *__restrict__ r, PcgScalars *sc, Reduce red, cudaGraphConditionalHandle handle,
-                 int use_handle) {
+                 int use_handle, const double *__restrict__ dinv0, double *__restrict__ x0) {
     double alpha = sc->alpha;
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         x[i] += alpha * p[i];
         double ri = r[i] - alpha * q[i];
         r[i] = ri;
+        if (x0) x0[i] = ri * dinv0[i];  // the next cycle's level-0 pre-smooth from zero
         part[0] += ri * ri;
     }
     if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
@@ -386,6 +390,88 @@ resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restric
     if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) sc->tt = part[0];
 }
 
+// finish of r.z / z.q: beta and rho (start: beta = 0)
+__device__ __forceinline__ void finish_rz(PcgScalars *sc, double rz, double zq) {
+    if (!sc->start) {
+        sc->zq = zq;
+        sc->beta = sc->flexible ? (-sc->alpha * zq) / sc->rho : rz / sc->rho;
+    } else {
+        sc->beta = 0.0;
+    }
+    sc->rho = rz;
+    sc->start = 0;
+}
+
+// level-0 post-smoothing z = x + d (b - A x) with r.z and z.q (r = b)
+template <int T>
+__global__ void __launch_bounds__(kThreads)
+post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+                   const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
+                   double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t i = (int32_t)(g / T);
+    int t = (int)(g % T);
+    int32_t p0 = 0, p1 = 0;
+    if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+    double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+    double part[2] = {0.0, 0.0};
+    if (i < n && t == 0) {
+        double bi = b[i];
+        double zi = x[i] + dinv[i] * (bi - s);
+        z[i] = zi;
+        part[0] = bi * zi;
+        part[1] = zi * q[i];
+    }
+    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
+                    const int32_t *__restrict__ sw, const int32_t *__restrict__ sci, const double *__restrict__ sv,
+                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
+                    double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
+    double part[2] = {0.0, 0.0};
+    if (pos < n) {
+        const int32_t i = perm ? __ldg(perm + pos) : pos;
+        double s = sell_row_sum<double, double>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
+        double bi = b[i];
+        double zi = x[i] + dinv[i] * (bi - s);
+        z[i] = zi;
+        part[0] = bi * zi;
+        part[1] = zi * q[i];
+    }
+    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+}
+
+__global__ void __launch_bounds__(kThreads)
+to_f64_rz_kernel(int32_t n, const float *__restrict__ z32, double *__restrict__ z, const double *__restrict__ r,
+                 const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    double part[2] = {0.0, 0.0};
+    for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+        double zi = (double)z32[i];
+        z[i] = zi;
+        part[0] += r[i] * zi;
+        part[1] += zi * q[i];
+    }
+    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+}
+
+template <typename XT>
+__global__ void scale_kernel(int64_t n, const XT *__restrict__ a, const XT *__restrict__ d, XT *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] * d[i];
+}
+
+__global__ void to_f32_scaled_kernel(int64_t n, const double *__restrict__ src, const float *__restrict__ d,
+                                     float *__restrict__ dst, float *__restrict__ xdst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = (float)src[i];
+    dst[i] = v;
+    xdst[i] = v * d[i];
+}
+
 // ---------------------------------------------------------------------------
 // coarse solve: x = inv b, one warp per row
 // ---------------------------------------------------------------------------
@@ -420,12 +506,44 @@ __global__ void to_f64_kernel(const XT *src, double *dst, int64_t n) {
     if (i < n) dst[i] = (double)src[i];
 }
 
-__global__ void slice_width_kernel(int32_t n, const int32_t *rp, int32_t *sw) {
+// rows sorted by length (descending, then index) inside windows of
+// kSellSigma rows: one block sorts one window with a bitonic network
+__global__ void __launch_bounds__(512) sell_sort_kernel(int32_t n, const int32_t *rp, int32_t *perm) {
+    __shared__ unsigned long long key[kSellSigma];
+    int32_t w0 = blockIdx.x * kSellSigma;
+    for (int t = threadIdx.x; t < kSellSigma; t += blockDim.x) {
+        int32_t i = w0 + t;
+        key[t] = i < n ? ((unsigned long long)(0x7fffffff - (rp[i + 1] - rp[i])) << 32) | (unsigned)i : ~0ull;
+    }
+    __syncthreads();
+    for (int size = 2; size <= kSellSigma; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < kSellSigma; t += blockDim.x) {
+                int partner = t ^ stride;
+                if (partner > t) {
+                    bool up = (t & size) == 0;
+                    unsigned long long a = key[t], c = key[partner];
+                    if ((a > c) == up) { key[t] = c; key[partner] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < kSellSigma; t += blockDim.x) {
+        int32_t i = w0 + t;
+        if (i < n) perm[i] = (int32_t)(key[t] & 0xffffffffu);
+    }
+}
+
+__global__ void slice_width_kernel(int32_t n, const int32_t *rp, const int32_t *perm, int32_t *sw) {
     int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t nsl = (n + 31) / 32;
     if (s >= nsl) return;
     int32_t w = 0;
-    for (int32_t i = s * 32; i < min(n, s * 32 + 32); ++i) w = max(w, rp[i + 1] - rp[i]);
+    for (int32_t pos = s * 32; pos < min(n, s * 32 + 32); ++pos) {
+        int32_t i = perm ? perm[pos] : pos;
+        w = max(w, rp[i + 1] - rp[i]);
+    }
     sw[s] = w;
 }
 
@@ -435,15 +553,16 @@ __global__ void slice_size_kernel(int32_t nsl, const int32_t *sw, int32_t *sz) {
 }
 
 template <typename VT>
-__global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v,
+__global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
                                  const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t nsl = (n + 31) / 32;
-    if (i >= nsl * 32) return;
-    int32_t s = i >> 5, lane = i & 31;
+    if (pos >= nsl * 32) return;
+    int32_t s = pos >> 5, lane = pos & 31;
     int32_t off = soff[s] + lane, w = sw[s];
-    int32_t p0 = i < n ? rp[i] : 0, len = i < n ? rp[i + 1] - p0 : 0;
-    int32_t self = i < n ? i : 0;
+    int32_t i = pos < n ? (perm ? perm[pos] : pos) : -1;
+    int32_t p0 = i >= 0 ? rp[i] : 0, len = i >= 0 ? rp[i + 1] - p0 : 0;
+    int32_t self = i >= 0 ? i : 0;
     for (int32_t k = 0; k < w; ++k) {
         int32_t p = off + k * 32;
         if (k < len) { sci[p] = ci[p0 + k]; sv[p] = v[p0 + k]; }
@@ -507,7 +626,7 @@ static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgSc
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        { ap_sell_kernel<<<reduce_blocks(A.nrows, 1), kThreads, 0, s>>>(A.nrows, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        { ap_sell_kernel<<<reduce_blocks(A.nrows, 1), kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
         AMG_CHECK_LAUNCH();
         return;
     }
@@ -522,8 +641,55 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 }
 
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
-                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s) {
-    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
+                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
+                   double *x0, cudaStream_t s) {
+    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red, handle, use_handle ? 1 : 0, dinv0, x0); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, const double *dinv, double *z,
+                    const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    int32_t n = A.nrows;
+    if (n == 0) return false;
+    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+        int blocks = div_up(n, kThreads);
+        if (blocks > kMaxReduceBlocks) return false;
+        { post_rz_sell_kernel<<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+        return true;
+    }
+    int T = threads_per_row(A.variant);
+    int64_t blocks = ((int64_t)n * T + kThreads - 1) / kThreads;
+    if (blocks > kMaxReduceBlocks) return false;
+    switch (T) {
+        case 1: { post_rz_csr_kernel<1><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 2: { post_rz_csr_kernel<2><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 4: { post_rz_csr_kernel<4><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 8: { post_rz_csr_kernel<8><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 16: { post_rz_csr_kernel<16><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        default: { post_rz_csr_kernel<32><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+    }
+    AMG_CHECK_LAUNCH();
+    return true;
+}
+
+void to_f64_rz(int32_t n, const float *z32, double *z, const double *r, const double *q, PcgScalars *sc, Reduce red,
+               cudaStream_t s) {
+    { to_f64_rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, z32, z, r, q, sc, red); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+template <typename XT> void scale(int64_t n, const XT *a, const XT *d, XT *out, cudaStream_t s) {
+    if (n <= 0) return;
+    { scale_kernel<XT><<<div_up(n, kThreads), kThreads, 0, s>>>(n, a, d, out); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+template void scale<double>(int64_t, const double *, const double *, double *, cudaStream_t);
+template void scale<float>(int64_t, const float *, const float *, float *, cudaStream_t);
+
+void to_f32_scaled(int64_t n, const double *src, const float *d, float *dst, float *xdst, cudaStream_t s) {
+    if (n <= 0) return;
+    { to_f32_scaled_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, src, d, dst, xdst); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -554,22 +720,23 @@ template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64
     AMG_CHECK_LAUNCH();
 }
 
-int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *soff, int32_t *sw, cudaStream_t s) {
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s) {
     int32_t nsl = (n + 31) / 32;
     if (nsl == 0) return 0;
-    DevBuf sz(sizeof(int32_t) * (nsl + 1));
-    { slice_width_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(n, rp, sw); ::amg::count_launch(); }
+    TmpBuf sz(sizeof(int32_t) * (nsl + 1), s);
+    if (perm) { sell_sort_kernel<<<div_up(n, kSellSigma), 512, 0, s>>>(n, rp, perm); ::amg::count_launch(); }
+    { slice_width_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(n, rp, perm, sw); ::amg::count_launch(); }
     { slice_size_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(nsl, sw, sz.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     return exclusive_scan_i32(sz.as<int32_t>(), soff, nsl, s);
 }
 
 template <typename VT>
-void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *soff,
+void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm, const int32_t *soff,
                const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s) {
     int32_t nsl = (n + 31) / 32;
     if (nsl == 0) return;
-    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, soff, sw, sci, sv); ::amg::count_launch(); }
+    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, perm, soff, sw, sci, sv); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -591,11 +758,12 @@ template void convert_values<__nv_bfloat16>(const double *, __nv_bfloat16 *, int
 template void convert_vec_from_f64<float>(const double *, float *, int64_t, cudaStream_t);
 template void convert_vec_to_f64<float>(const float *, double *, int64_t, cudaStream_t);
 template void sell_fill<double>(int32_t, const int32_t *, const int32_t *, const double *, const int32_t *,
-                                const int32_t *, int32_t *, double *, cudaStream_t);
+                                const int32_t *, const int32_t *, int32_t *, double *, cudaStream_t);
 template void sell_fill<float>(int32_t, const int32_t *, const int32_t *, const float *, const int32_t *,
-                               const int32_t *, int32_t *, float *, cudaStream_t);
+                               const int32_t *, const int32_t *, int32_t *, float *, cudaStream_t);
 template void sell_fill<__nv_bfloat16>(int32_t, const int32_t *, const int32_t *, const __nv_bfloat16 *,
-                                       const int32_t *, const int32_t *, int32_t *, __nv_bfloat16 *, cudaStream_t);
+                                       const int32_t *, const int32_t *, const int32_t *, int32_t *, __nv_bfloat16 *,
+                                       cudaStream_t);
 
 }  // namespace cyc
 }  // namespace amg

@@ -14,6 +14,7 @@ template <typename VT> struct CycMat {
     const VT *v = nullptr;
     int32_t nslices = 0;
     const int32_t *soff = nullptr, *sw = nullptr, *sci = nullptr;
+    const int32_t *perm = nullptr;  // SELL position -> row (null: identity)
     const VT *sv = nullptr;
     int variant = AMG_SPMV_CSR4;
 };
@@ -71,7 +72,20 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 // x += alpha p, r -= alpha q, rr, its += 1; with a graph handle, the WHILE
 // condition is set to continue while rr > thresh2, its < max_its, no breakdown
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
-                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, cudaStream_t s);
+                   Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
+                   double *x0, cudaStream_t s);
+// level-0 post-smoothing that also forms rho = r.z and z.q (and beta): z is
+// the output, r = b the cycle input.  Returns false (nothing launched) when
+// the grid would exceed the reduction capacity.
+bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, const double *dinv, double *z,
+                    const double *q, PcgScalars *sc, Reduce red, cudaStream_t s);
+// z = (double) z32 and rho = r.z, z.q (FP32 cycles)
+void to_f64_rz(int32_t n, const float *z32, double *z, const double *r, const double *q, PcgScalars *sc, Reduce red,
+               cudaStream_t s);
+// out = a .* d (pre-smooth from zero)
+template <typename XT> void scale(int64_t n, const XT *a, const XT *d, XT *out, cudaStream_t s);
+// dst = (float) src and xdst = dst .* d (FP32 cycle input with its pre-smooth)
+void to_f32_scaled(int64_t n, const double *src, const float *d, float *dst, float *xdst, cudaStream_t s);
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
             cudaStream_t s);
 // t = b - A x, sc->tt = ||t||^2; if `replace`, r = t
@@ -82,11 +96,14 @@ void true_residual(const CycMat<double> &A, const double *b, const double *x, do
 template <typename VT> void convert_values(const double *src, VT *dst, int64_t n, cudaStream_t s);
 template <typename XT> void convert_vec_from_f64(const double *src, XT *dst, int64_t n, cudaStream_t s);
 template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64_t n, cudaStream_t s);
-// slice widths and offsets; returns padded entry count
-int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *soff, int32_t *sw, cudaStream_t s);
+// SELL-32 layout: slice widths and offsets, optionally over rows sorted by
+// length (descending) inside windows of kSellSigma rows (perm: position ->
+// row); returns the padded entry count
+constexpr int kSellSigma = 1024;
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s);
 template <typename VT>
-void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *soff,
-               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s);
+void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
+               const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s);
 
 }  // namespace cyc
 }  // namespace amg

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -159,21 +161,30 @@ static int heuristic_variant(const DevCSR &M) {
     return AMG_SPMV_CSR32;
 }
 
+// SELL-32 copy of the relaxed operator.  If slices of consecutive rows would
+// pad the matrix by more than 3%, rows are sorted by length inside windows of
+// kSellSigma rows (SELL-C-sigma) and kernels write through the permutation.
 template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
     const DevCSR &M = V.op();
     int32_t nsl = (M.nrows + 31) / 32;
     V.soff.alloc(sizeof(int32_t) * (nsl + 1));
     V.sw.alloc(sizeof(int32_t) * (nsl + 1));
-    V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), V.soff.as<int32_t>(), V.sw.as<int32_t>(), s);
+    V.sperm.release();
+    V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, V.soff.as<int32_t>(), V.sw.as<int32_t>(), s);
+    if ((double)V.sell_entries > 1.03 * (double)M.nnz) {
+        V.sperm.alloc(sizeof(int32_t) * (M.nrows + kPad));
+        V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), V.sperm.as<int32_t>(), V.soff.as<int32_t>(),
+                                          V.sw.as<int32_t>(), s);
+    }
     V.sci.alloc(sizeof(int32_t) * (V.sell_entries + kPad));
     V.sv.alloc(sizeof(VT) * (V.sell_entries + kPad));
     CycMat<VT> m = op_mat<VT>(V);
-    cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), m.v, V.soff.as<int32_t>(), V.sw.as<int32_t>(),
-                       V.sci.as<int32_t>(), V.sv.as<VT>(), s);
+    cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), m.v, V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
+                       V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sci.as<int32_t>(), V.sv.as<VT>(), s);
 }
 
 static void free_sell(Level &V) {
-    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release();
+    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release(); V.sperm.release();
     V.sell_entries = 0;
 }
 
@@ -191,6 +202,32 @@ struct TuneKey {
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, int> g_tune_cache;
+static bool g_tune_loaded = false;
+
+// Decisions persist across processes when AMG_TUNE_CACHE names a file: it is
+// read on first use and every new decision is appended ("n nnz kind variant").
+static void tune_cache_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("AMG_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    long long n, z;
+    int kind, var;
+    while (std::fscanf(f, "%lld %lld %d %d", &n, &z, &kind, &var) == 4) g_tune_cache[TuneKey{n, z, kind}] = var;
+    std::fclose(f);
+}
+
+static void tune_cache_store_locked(const TuneKey &k, int variant) {
+    g_tune_cache[k] = variant;
+    const char *path = std::getenv("AMG_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (std::FILE *f = std::fopen(path, "a")) {
+        std::fprintf(f, "%lld %lld %d %d\n", (long long)k.n, (long long)k.nnz, k.vbytes, variant);
+        std::fclose(f);
+    }
+}
 
 static std::vector<int> tune_candidates(const DevCSR &M, int vbytes) {
     double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
@@ -292,6 +329,7 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     TuneKey key{M.nrows, M.nnz, V.vbytes};
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_cache_load_locked();
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             V.variant = it->second;
@@ -309,7 +347,7 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
         else autotune_level<__nv_bfloat16, float>(h, V, s);
         if (V.variant != AMG_SPMV_SELL32) free_sell(V);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = V.variant;
+        tune_cache_store_locked(key, V.variant);
     }
     if (l == h.nlev() - 1) {
         h.coarse_n = n;
@@ -332,6 +370,7 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
         TuneKey key{M.nrows, M.nnz, 100 * kind + vb};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_cache_load_locked();
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) { variant = it->second; return; }
         }
@@ -359,7 +398,7 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
         }
         variant = best_v;
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = best_v;
+        tune_cache_store_locked(key, best_v);
     };
     if (V.P.nnz >= 20000) {
         tune(V.P, 1, V.variant_p, [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
@@ -382,6 +421,7 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
         }
     }
     h.graph_dirty = true;
+    h.version++;
     AMG_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -476,10 +516,10 @@ void timing_collect(Hierarchy &h) {
 // pass, gathering b and d); on coarser levels the restriction already wrote
 // x = D^{-1} b, so the pass gathers x alone.
 template <typename XT>
-static void relax_pre(Hierarchy &h, int l, const XT *b, cudaStream_t s) {
+static void relax_pre(Hierarchy &h, int l, const XT *b, cudaStream_t s, bool x_ready) {
     Level &V = *h.lev[l];
     int xb = sizeof(XT);
-    if (l == 0) {
+    if (!x_ready) {
         timed(h, 0, l, bytes_pre(V.n(), V.op().nnz, V.vbytes, xb), s, [&] {
             if constexpr (sizeof(XT) == 8) {
                 cyc::pre_smooth_residual<double, double>(op_mat<double>(V), b, dinv_of<XT>(V), V.x.as<XT>(), V.r.as<XT>(), s);
@@ -521,18 +561,19 @@ static void relax_post(Hierarchy &h, int l, const XT *b, XT *out, cudaStream_t s
 }
 
 template <typename XT>
-static void vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s) {
+static bool vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s, const CycleCtl &ctl) {
     int L = h.nlev();
     int xb = sizeof(XT);
+    bool fused = false;
     if (L == 1) {
         timed(h, 4, 0, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,
               [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), b0, z0, s); });
-        return;
+        return false;
     }
     for (int l = 0; l + 1 < L; ++l) {
         Level &V = *h.lev[l];
         const XT *b = l == 0 ? b0 : V.b.as<XT>();
-        relax_pre<XT>(h, l, b, s);
+        relax_pre<XT>(h, l, b, s, l > 0 || ctl.x0_ready);
         Level &C = *h.lev[l + 1];
         if (l + 2 < L) {  // the coarse level relaxes: fold its x = D^{-1} b into the restriction
             timed(h, 1, l, bytes_restrict_x(V.R.nrows, V.n(), V.R.nnz, xb, xb), s, [&] {
@@ -552,19 +593,41 @@ static void vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s) {
         timed(h, 2, l, bytes_prolong(V.n(), V.P.ncols, V.P.nnz, xb, xb), s,
               [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
         const XT *b = l == 0 ? b0 : V.b.as<XT>();
+        if constexpr (sizeof(XT) == 8) {
+            if (l == 0 && ctl.fuse_rz && V.vbytes == 8) {
+                timed(h, 3, 0, bytes_post(V.n(), V.op().nnz, V.vbytes, xb) + 8.0 * V.n(), s, [&] {
+                    fused = cyc::post_smooth_rz(op_mat<double>(V), V.x.as<double>(), b, dinv_of<double>(V), z0, ctl.q,
+                                                h.dscal(), h.reduce(), s);
+                });
+                if (fused) continue;
+            }
+        }
         relax_post<XT>(h, l, b, l == 0 ? z0 : V.xo.as<XT>(), s);
     }
+    return fused;
 }
 
-void vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s) {
-    if (h.opt.precision == AMG_PREC_FP64) {
-        vcycle_impl<double>(h, r, z, s);
+bool vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s, const CycleCtl &ctl) {
+    if (h.opt.precision == AMG_PREC_FP64) return vcycle_impl<double>(h, r, z, s, ctl);
+    int64_t n = h.lev[0]->n();
+    Level &V0 = *h.lev[0];
+    CycleCtl c32 = ctl;
+    if (h.nlev() > 1) {
+        // FP32 input and its level-0 pre-smooth in one pass
+        cyc::to_f32_scaled(n, r, V0.dinv32.as<float>(), h.r32.as<float>(), V0.x.as<float>(), s);
+        c32.x0_ready = true;
     } else {
-        int64_t n = h.lev[0]->n();
         cyc::convert_vec_from_f64<float>(r, h.r32.as<float>(), n, s);
-        vcycle_impl<float>(h, h.r32.as<float>(), h.z32.as<float>(), s);
-        cyc::convert_vec_to_f64<float>(h.z32.as<float>(), z, n, s);
     }
+    vcycle_impl<float>(h, h.r32.as<float>(), h.z32.as<float>(), s, c32);
+    if (ctl.fuse_rz) {
+        timed(h, 6, 0, 28.0 * n, s, [&] {
+            cyc::to_f64_rz((int32_t)n, h.z32.as<float>(), z, r, ctl.q, h.dscal(), h.reduce(), s);
+        });
+        return true;
+    }
+    cyc::convert_vec_to_f64<float>(h.z32.as<float>(), z, n, s);
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -615,11 +678,20 @@ double true_resnorm(Hierarchy &h, const double *b, const double *x, cudaStream_t
     return std::sqrt(h.h_scal->tt);
 }
 
+// In FP64 the level-0 pre-smooth x0 = D0^-1 r of the next cycle is written by
+// the x, r update; after r is set any other way it is formed here.
+void refresh_x0(Hierarchy &h, cudaStream_t s) {
+    if (h.opt.precision != AMG_PREC_FP64 || h.nlev() < 2) return;
+    Level &V0 = *h.lev[0];
+    cyc::scale<double>(V0.n(), h.pr.as<double>(), V0.dinv.as<double>(), V0.x.as<double>(), s);
+}
+
 // r = b - A x, p = 0, start = 1 (the next body sets beta = 0); returns ||r||
 double pcg_start(Hierarchy &h, const double *b, const double *x, cudaStream_t s) {
     int64_t n = h.lev[0]->n();
     double rn = true_resnorm(h, b, x, s);
     AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    refresh_x0(h, s);
     AMG_CUDA(cudaMemsetAsync(h.pp.ptr, 0, sizeof(double) * n, s));
     h.h_scal->start = 1;
     h.h_scal->breakdown = 0;
@@ -632,15 +704,23 @@ void pcg_body(Hierarchy &h, cudaStream_t s, cudaGraphConditionalHandle handle, b
     int32_t n = h.lev[0]->n();
     CycMat<double> A0 = a0_mat(h);
     double ap_bytes = (double)A0.nnz * 12 + 4.0 * (n + 1) + 16.0 * n;
-    vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
-    timed(h, 6, 0, 24.0 * n, s, [&] {
-        cyc::pcg_rz(n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s);
-    });
+    CycleCtl ctl;
+    ctl.x0_ready = true;  // pcg_start / replacement / the previous x, r update formed it
+    ctl.fuse_rz = true;
+    ctl.q = h.pq.as<double>();
+    bool fused = vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s, ctl);
+    if (!fused)
+        timed(h, 6, 0, 24.0 * n, s, [&] {
+            cyc::pcg_rz(n, h.pr.as<double>(), h.pz.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s);
+        });
     timed(h, 6, 0, 24.0 * n, s, [&] { cyc::pcg_p_update(n, h.pz.as<double>(), h.pp.as<double>(), h.dscal(), s); });
     timed(h, 5, 0, ap_bytes, s, [&] { cyc::pcg_ap(A0, h.pp.as<double>(), h.pq.as<double>(), h.dscal(), h.reduce(), s); });
-    timed(h, 6, 0, 48.0 * n, s, [&] {
+    bool fp64 = h.opt.precision == AMG_PREC_FP64 && h.nlev() > 1;
+    Level &V0 = *h.lev[0];
+    timed(h, 6, 0, fp64 ? 64.0 * n : 48.0 * n, s, [&] {
         cyc::pcg_xr_update(n, h.pp.as<double>(), h.pq.as<double>(), h.px.as<double>(), h.pr.as<double>(), h.dscal(),
-                           h.reduce(), handle, use_handle, s);
+                           h.reduce(), handle, use_handle, fp64 ? V0.dinv.as<double>() : nullptr,
+                           fp64 ? V0.x.as<double>() : nullptr, s);
     });
 }
 
@@ -726,6 +806,7 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
         run.rnorm = tn;
         if (tn <= tol * bnorm) { run.converged = true; return; }
         AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        refresh_x0(h, s);
         run.replacements++;
     }
 }
@@ -756,7 +837,7 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
     } else {
         // Algorithm 5: check every k steps; reintroduce on slow convergence
         int k = std::max(1, h.opt.k_check), sl = std::max(1, h.opt.s_levels);
-        DevBuf xs(sizeof(double) * (n + kPad));
+        TmpBuf xs(sizeof(double) * (n + kPad), s);
         double rstart = bnorm;
         double rnow = pcg_start(h, b, x, s);
         int total = 0;

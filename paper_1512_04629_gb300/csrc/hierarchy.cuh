@@ -34,6 +34,7 @@ struct Level {
     DevBuf pv32, rv32;     // FP32 values of P and R
     DevBuf dinv32;
     DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
+    DevBuf sperm;              // SELL position -> row when rows are length-sorted
     int64_t sell_entries = 0;
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
     bool pr_tuned = false;  // transfer-operator variants chosen by timed trials
@@ -71,6 +72,8 @@ struct BatchWS {
     bat::ColScalars sc{};
     double *h_d = nullptr;  // pinned: rho, pq, alpha, beta, rr, zq, tt (K each)
     int *h_i = nullptr;     // pinned: active, start, mask (K each)
+    cudaGraphExec_t graph = nullptr;  // one captured iteration
+    int graph_version = -1;
     ~BatchWS();
     double *h_rho() { return h_d; }
     double *h_pq() { return h_d + K; }
@@ -106,6 +109,7 @@ struct Hierarchy {
     cudaGraphExec_t g_update = nullptr, g_precond = nullptr;
     cudaStream_t graph_stream = nullptr;
     bool graph_dirty = true;
+    int version = 0;  // bumped whenever the cycle's buffers or operators change
 
     std::map<int, std::unique_ptr<BatchWS>> batch;
 
@@ -142,6 +146,7 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
         m.sw = V.sw.as<int32_t>();
         m.sci = V.sci.as<int32_t>();
         m.sv = V.sv.as<VT>();
+        m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
     }
     m.variant = V.variant;
     return m;
@@ -180,7 +185,15 @@ void resparsify_level(Hierarchy &h, int l, cudaStream_t s);
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels);
 void ensure_workspace(Hierarchy &h, cudaStream_t s);
 int reintroduce(Hierarchy &h, int s_levels, cudaStream_t s);
-void vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s);
+// V-cycle options: x0_ready -- level 0's x already holds D0^-1 r (FP64);
+// fuse_rz -- the last pass also forms rho = r.z and z.q (q given) and beta.
+struct CycleCtl {
+    bool x0_ready = false;
+    bool fuse_rz = false;
+    const double *q = nullptr;
+};
+// z = M r; returns true when rho / beta were formed in the cycle (fuse_rz)
+bool vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s, const CycleCtl &ctl = CycleCtl());
 amg_status solve(Hierarchy &h, const double *b_dev, double *x_dev, double tol, int max_it, bool adaptive,
                  cudaStream_t s, amg_solve_info *info);
 void timing_collect(Hierarchy &h);

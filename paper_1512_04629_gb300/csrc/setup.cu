@@ -798,7 +798,7 @@ __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
 // host entry points
 // ===========================================================================
 void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s) {
-    DevBuf err(sizeof(int));
+    TmpBuf err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
     if (A.nrows > 0)
         { validate_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(
@@ -817,7 +817,7 @@ void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s) {
 }
 
 void transpose_positions(const DevCSR &A, int32_t *tpos, cudaStream_t s) {
-    DevBuf err(sizeof(int));
+    TmpBuf err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
     if (A.nrows > 0)
         { tpos_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(A.nrows, A.rp(), A.ci(), tpos,
@@ -838,7 +838,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
              int32_t level, int8_t *cf, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return 0;
-    DevBuf w(sizeof(double) * n), newc(n), cnt(sizeof(int));
+    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int), s);
     int g = div_up(n, kThreads);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));
     { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
@@ -858,7 +858,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         if (next >= undecided) throw Error(AMG_ERR_CUDA, "PMIS made no progress");
         undecided = next;
     }
-    DevBuf flag(sizeof(int32_t) * n), scan(sizeof(int32_t) * (n + 1));
+    TmpBuf flag(sizeof(int32_t) * n, s), scan(sizeof(int32_t) * (n + 1), s);
     { is_c_kernel<<<g, kThreads, 0, s>>>(n, cf, flag.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     return exclusive_scan_i32(flag.as<int32_t>(), scan.as<int32_t>(), n, s);
@@ -866,7 +866,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
 
 void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s) {
     if (n == 0) return;
-    DevBuf flag(sizeof(int32_t) * n);
+    TmpBuf flag(sizeof(int32_t) * n, s);
     int g = div_up(n, kThreads);
     { is_c_kernel<<<g, kThreads, 0, s>>>(n, cf, flag.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
@@ -879,7 +879,7 @@ void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaS
 void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, const int32_t *cmap,
                    int32_t nc, DevCSR &P, cudaStream_t s) {
     int32_t n = A.nrows;
-    DevBuf cnt(sizeof(int32_t) * (n + 1));
+    TmpBuf cnt(sizeof(int32_t) * (n + 1), s);
     P.rowptr.alloc(sizeof(int32_t) * (n + 1));
     int g = div_up(n, kThreads);
     if (n > 0) { interp_count_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, cnt.as<int32_t>()); ::amg::count_launch(); }
@@ -900,7 +900,7 @@ void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, con
 
 void transpose(const DevCSR &M, DevCSR &T, cudaStream_t s) {
     int32_t m = M.ncols;
-    DevBuf cnt(sizeof(int32_t) * (m + 1)), fill(sizeof(int32_t) * (m + 1));
+    TmpBuf cnt(sizeof(int32_t) * (m + 1), s), fill(sizeof(int32_t) * (m + 1), s);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     if (M.nnz > 0) { col_count_kernel<<<div_up(M.nnz, kThreads), kThreads, 0, s>>>(M.nnz, M.ci(), cnt.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
@@ -940,8 +940,8 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         Cm.val.alloc(sizeof(double) * kPad);
         return;
     }
-    DevBuf ub(sizeof(int64_t) * n), bins(sizeof(int32_t) * 4 * (size_t)n), bcount(sizeof(int32_t) * 4),
-        cnt(sizeof(int32_t) * (n + 1));
+    TmpBuf ub(sizeof(int64_t) * n, s), bins(sizeof(int32_t) * 4 * (size_t)n, s), bcount(sizeof(int32_t) * 4, s),
+        cnt(sizeof(int32_t) * (n + 1), s);
     int g = div_up(n, kThreads);
     { spgemm_ub_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), B.rp(), ub.as<int64_t>()); ::amg::count_launch(); }
     AMG_CUDA(cudaMemsetAsync(bcount.ptr, 0, bcount.bytes, s));
@@ -977,12 +977,12 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     int64_t gumax = next_pow2(std::max<int64_t>(max_ub, 1));
     int64_t ghs = 2 * gumax;
     int gblocks = 0;
-    DevBuf gscr;
+    TmpBuf gscr;
     if (nb[3] > 0) {
         size_t per = (size_t)ghs * 8 + (size_t)gumax * 12;
         int64_t cap = std::max<int64_t>(1, (int64_t)(((size_t)2 << 30) / per));  // <= 2 GiB scratch
         gblocks = (int)std::min<int64_t>({(int64_t)nb[3], 304, cap});
-        gscr.alloc(per * gblocks);
+        gscr.alloc(per * gblocks, s);
     }
     const int64_t *ubp = ub.as<int64_t>();
     auto launch = [&](bool numeric) {
@@ -1053,7 +1053,7 @@ void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, ui
 int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const int32_t *diagpos,
                  double gamma, uint8_t *keep, DevCSR &H, cudaStream_t s) {
     int32_t n = A.nrows;
-    DevBuf rowmax(sizeof(double) * (n + 1)), flag(A.nnz + 1), guard(n + 1), cnt(sizeof(int32_t) * (n + 1));
+    TmpBuf rowmax(sizeof(double) * (n + 1), s), flag(A.nnz + 1, s), guard(n + 1, s), cnt(sizeof(int32_t) * (n + 1), s);
     int g = div_up(n, kThreads);
     if (n > 0) {
         { sparsify_flag_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), inM, gamma,
@@ -1105,7 +1105,7 @@ void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
     require(n <= 8192, "coarsest level too large for the dense direct solve (n > 8192)");
-    DevBuf a(sizeof(double) * (size_t)n * n), linv(sizeof(double) * (size_t)n * n), err(sizeof(int));
+    TmpBuf a(sizeof(double) * (size_t)n * n, s), linv(sizeof(double) * (size_t)n * n, s), err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
     { densify_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), a.as<double>()); ::amg::count_launch(); }
     { cholesky_kernel<<<1, 1024, 0, s>>>(n, a.as<double>(), err.as<int>()); ::amg::count_launch(); }

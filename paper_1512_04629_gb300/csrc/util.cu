@@ -38,6 +38,43 @@ void DevBuf::release() {
     bytes = 0;
 }
 
+// the default pool keeps freed blocks (no release back to the driver) so
+// stream-ordered temporaries are recycled without synchronisation
+static void keep_pool_warm() {
+    static thread_local int done_for = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (done_for == dev) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done_for = dev;
+}
+
+void TmpBuf::alloc(size_t b, cudaStream_t s) {
+    release();
+    keep_pool_warm();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMallocAsync(&ptr, b, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+        throw Error(e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA,
+                    std::string("cudaMallocAsync(") + std::to_string(b) + "): " + cudaGetErrorString(e));
+    }
+    bytes = b;
+    stream = s;
+}
+
+void TmpBuf::release() {
+    if (ptr) cudaFreeAsync(ptr, stream);
+    ptr = nullptr;
+    bytes = 0;
+}
+
 void DevCSR::allocate(int32_t r, int32_t c, int64_t z) {
     nrows = r;
     ncols = c;
@@ -128,7 +165,7 @@ __global__ void tile_scan_kernel(const TI *in, int64_t n, const int64_t *sums, T
 template <typename TI, typename TO>
 int64_t scan_impl(const TI *in, TO *out, int64_t n, cudaStream_t s) {
     int64_t tiles = (n + kTile - 1) / kTile;
-    DevBuf sums(sizeof(int64_t) * (tiles + 1)), total(sizeof(int64_t));
+    TmpBuf sums(sizeof(int64_t) * (tiles + 1), s), total(sizeof(int64_t), s);
     if (n > 0) {
         { tile_sum_kernel<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()); ::amg::count_launch(); }
         { scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums.as<int64_t>(), tiles, total.as<int64_t>()); ::amg::count_launch(); }
