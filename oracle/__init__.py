@@ -81,6 +81,7 @@ def _load():
         lib.orc_setup.restype = vp
         lib.orc_sparsify.argtypes = [vp, vp, C.c_int32]
         lib.orc_reintroduce.argtypes = [vp, C.c_int32, C.c_double, vp]
+        lib.orc_sparsify_method.argtypes = [vp, vp, C.c_int32, C.c_int32]
         lib.orc_vcycle.argtypes = [vp, vp, vp]
         lib.orc_pcg.argtypes = [vp, vp, vp, C.c_double, C.c_int32, P(_Info)]
         lib.orc_adaptive_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
@@ -332,9 +333,10 @@ class Hierarchy:
     def gamma(self, level) -> float:
         return self._lib.orc_level_gamma(self._h, level)
 
-    def sparsify(self, gamma):
+    def sparsify(self, gamma, method: int = 0):
+        """method 0: Sparse Galerkin; 1: Hybrid Galerkin."""
         g = np.ascontiguousarray(gamma, dtype=np.float64)
-        st = self._lib.orc_sparsify(self._h, _ptr(g), len(g))
+        st = self._lib.orc_sparsify_method(self._h, _ptr(g), len(g), method)
         if st:
             raise RuntimeError(f"orc_sparsify status {st}")
 

@@ -607,6 +607,7 @@ typedef struct {
 
 struct orc_hier {
     int32_t nlev;
+    int32_t method; /* 0 Sparse Galerkin, 1 Hybrid Galerkin (set by orc_sparsify_method) */
     orc_level lev[64];
     double *chol; /* dense Cholesky factor of Ahat of the coarsest level */
 };
@@ -730,15 +731,44 @@ oom:
     return NULL;
 }
 
-/* (Re)build Ahat_l from the retained A_l at the level's gamma. */
-static int resparsify_level(orc_hier *h, int32_t l) {
+/* Minimal pattern of level l for Hybrid Galerkin (Section 3, Algorithm 4,
+ * hybrid line): M = edges(Phat^T Ahat P + P^T Ahat Phat) with Ahat the
+ * sparsified operator of level l-1 (for l = 1, Ahat_0 = A_0). */
+static int hybrid_pattern(orc_hier *h, int32_t l, uint8_t *inM) {
+    orc_level *F = &h->lev[l - 1];
+    orc_csr *AP = orc_spgemm(F->Ahat, F->P);
+    if (!AP) return ORC_OOM;
+    int st = orc_minimal_pattern(h->lev[l].A, AP, F->cf, inM);
+    orc_csr_free(AP);
+    return st;
+}
+
+/* (Re)build Ahat_l from the retained A_l at the level's gamma; method 1
+ * (Hybrid) takes M from the current Ahat_{l-1}. */
+static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method);
+static int resparsify_level(orc_hier *h, int32_t l) { return resparsify_level_m(h, l, 0); }
+
+static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method) {
     orc_level *L = &h->lev[l];
     if (L->Ahat != L->A) orc_csr_free(L->Ahat);
     L->Ahat = L->A;
     if (l == 0 || L->gamma == 0.0) {
         for (int32_t p = 0; p < L->A->nnz; ++p) L->keep[p] = 1;
     } else {
-        orc_csr *H = orc_sparsify_diag(L->A, L->inM, L->gamma, L->keep);
+        const uint8_t *inM = L->inM;
+        uint8_t *hyb = NULL;
+        if (method == 1) {
+            hyb = (uint8_t *)malloc((size_t)(L->A->nnz > 0 ? L->A->nnz : 1));
+            if (!hyb) return ORC_OOM;
+            int st = hybrid_pattern(h, l, hyb);
+            if (st != ORC_OK) {
+                free(hyb);
+                return st;
+            }
+            inM = hyb;
+        }
+        orc_csr *H = orc_sparsify_diag(L->A, inM, L->gamma, L->keep);
+        free(hyb);
         if (!H) return ORC_OOM;
         L->Ahat = H;
     }
@@ -751,20 +781,27 @@ static int resparsify_level(orc_hier *h, int32_t l) {
 /* S_{l-1}, gamma_l) for l = 1 .. L-1 (reading of the garbled indices: the  */
 /* loop writes Ahat_l; Ahat_0 = A_0).  gamma[l] applies to level l, levels  */
 /* past ngamma - 1 use gamma[ngamma - 1]; gamma[0] must be 0.               */
-int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma) {
-    if (ngamma < 1 || gamma[0] != 0.0) return ORC_INVALID;
+int orc_sparsify_method(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method) {
+    if (ngamma < 1 || gamma[0] != 0.0 || method < 0 || method > 1) return ORC_INVALID;
     for (int32_t l = 0; l < ngamma; ++l)
         if (!(gamma[l] >= 0.0) || !isfinite(gamma[l])) return ORC_INVALID;
-    for (int32_t l = 1; l < h->nlev; ++l) {
+    h->method = method;
+    for (int32_t l = 1; l < h->nlev; ++l) {  /* in order: Hybrid reads Ahat_{l-1} */
         h->lev[l].gamma = gamma[l < ngamma ? l : ngamma - 1];
-        int st = resparsify_level(h, l);
+        int st = resparsify_level_m(h, l, method);
         if (st != ORC_OK) return st;
     }
     return ORC_OK;
 }
 
+int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma) {
+    return orc_sparsify_method(h, gamma, ngamma, 0);
+}
+
 /* One reintroduction step of Algorithm 5: new gammas on s levels, then    */
 /* re-sparsify those levels from the retained Galerkin A_l.               */
+/* Algorithm 5 re-sparsifies only the levels whose gamma changed; with the
+ * Hybrid method their M comes from the current Ahat_{l-1}. */
 int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed) {
     double g[64];
     for (int32_t l = 0; l < h->nlev; ++l) g[l] = h->lev[l].gamma;
@@ -772,7 +809,7 @@ int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed) 
     for (int32_t l = 0; l < h->nlev; ++l) {
         if (!changed[l]) continue;
         h->lev[l].gamma = g[l];
-        int st = resparsify_level(h, l);
+        int st = resparsify_level_m(h, l, h->method);
         if (st != ORC_OK) return -st;
     }
     return cnt;

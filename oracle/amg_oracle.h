@@ -71,6 +71,9 @@ int orc_gamma_schedule(double *gamma, int32_t nlev, int32_t s, double gamma_min,
 orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
                     uint64_t seed, int32_t *status);
 int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma);
+/* method 0: Sparse Galerkin (M from the Galerkin A_{l-1}); 1: Hybrid Galerkin
+ * (M from the sparsified Ahat_{l-1}, levels processed in order). */
+int orc_sparsify_method(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method);
 int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed);
 int orc_vcycle(orc_hier *h, const double *b, double *x);
 int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info);

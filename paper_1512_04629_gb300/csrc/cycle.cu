@@ -207,54 +207,86 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Every block adds its partials; the last block of each group of 256 blocks
-// sums the group's partials (one load per thread), and the last group to
-// finish sums the group partials.  Fixed groups and fixed trees: the result
-// does not depend on arrival order.  Returns true in the single block that
-// holds the totals (thread 0's v).
+// Every block reduces its values (fixed tree) and thread 0 stores the block
+// partial; a one-block finisher kernel launched next sums the partials in
+// block order.  No atomics and no fences on the producers' critical path.
 template <int NV>
-__device__ bool reduce_and_finish(double (&v)[NV], Reduce red) {
+__device__ __forceinline__ void block_partials(double (&v)[NV], Reduce red) {
     block_reduce<NV>(v);
-    __shared__ bool last;
-    const int g = blockIdx.x >> 8;
-    const int gsize = min(256, (int)gridDim.x - g * 256);
-    const int ngroups = ((int)gridDim.x + 255) >> 8;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) red.partials[k * kMaxReduceBlocks + blockIdx.x] = v[k];
-        __threadfence();
-        unsigned prev = atomicAdd(red.counter + 1 + g, 1u);
-        last = (prev == (unsigned)gsize - 1);
     }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
+}
+
+enum Fin { kFinAp = 0, kFinXr = 1, kFinRz = 2, kFinTt = 3 };
+
+constexpr int kFinThreads = 1024;
+
+// finish of r.z / z.q: beta and rho (start: beta = 0)
+__device__ __forceinline__ void finish_rz(PcgScalars *sc, double rz, double zq) {
+    if (!sc->start) {
+        sc->zq = zq;
+        sc->beta = sc->flexible ? (-sc->alpha * zq) / sc->rho : rz / sc->rho;
+    } else {
+        sc->beta = 0.0;
+    }
+    sc->rho = rz;
+    sc->start = 0;
+}
+
+template <int NV, int FIN>
+__global__ void __launch_bounds__(kFinThreads)
+finish_kernel(int nblocks, Reduce red, PcgScalars *sc, cudaGraphConditionalHandle handle, int use_handle) {
+    __shared__ double sh[NV][kFinThreads / 32];
     double t[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        t[k] = (int)threadIdx.x < gsize ? ((volatile double *)red.partials)[k * kMaxReduceBlocks + g * 256 + threadIdx.x] : 0.0;
-    block_reduce<NV>(t);
-    if (threadIdx.x == 0) {
-        red.counter[1 + g] = 0u;
+    for (int k = 0; k < NV; ++k) t[k] = 0.0;
+#pragma unroll 8
+    for (int b = threadIdx.x; b < nblocks; b += kFinThreads) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red.gpartials[k * 256 + g] = t[k];
-        __threadfence();
-        unsigned prev = atomicAdd(red.counter, 1u);
-        last = (prev == (unsigned)ngroups - 1);
+        for (int k = 0; k < NV; ++k) t[k] += red.partials[k * kMaxReduceBlocks + b];
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = t[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][w] = x;
     }
     __syncthreads();
-    if (!last) return false;
-    __threadfence();
+    if (w != 0) return;
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-        t[k] = (int)threadIdx.x < ngroups ? ((volatile double *)red.gpartials)[k * 256 + threadIdx.x] : 0.0;
-    block_reduce<NV>(t);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = t[k];
-        *red.counter = 0u;
+    for (int k = 0; k < NV; ++k) {
+        double x = sh[k][lane];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        t[k] = x;
     }
-    return true;
+    if (lane != 0) return;
+    if (FIN == kFinAp) {
+        sc->pq = t[0];
+        bool ok = t[0] > 0.0 && sc->rho > 0.0;
+        if (!ok) sc->breakdown = 1;
+        sc->alpha = ok ? sc->rho / t[0] : 0.0;
+    } else if (FIN == kFinXr) {
+        sc->rr = t[0];
+        int its = sc->its + 1;
+        sc->its = its;
+        if (use_handle) {
+            bool go = t[0] > sc->thresh2 && its < sc->max_its && !sc->breakdown && isfinite(t[0]);
+            cudaGraphSetConditional(handle, go ? 1u : 0u);
+        }
+    } else if (FIN == kFinRz) {
+        finish_rz(sc, t[0], NV > 1 ? t[NV - 1] : 0.0);
+    } else {
+        sc->tt = t[0];
+    }
+}
+
+template <int NV, int FIN>
+void launch_finish(int nblocks, Reduce red, PcgScalars *sc, cudaStream_t s,
+                   cudaGraphConditionalHandle handle = cudaGraphConditionalHandle{}, bool use_handle = false) {
+    { finish_kernel<NV, FIN><<<1, kFinThreads, 0, s>>>(nblocks, red, sc, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
 }
 
 int reduce_blocks(int64_t n, int per_thread = 1) {
@@ -287,12 +319,7 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         q[i] = s;
         part[0] += p[i] * s;
     }
-    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
-        sc->pq = part[0];
-        bool ok = part[0] > 0.0 && sc->rho > 0.0;
-        if (!ok) sc->breakdown = 1;
-        sc->alpha = ok ? sc->rho / part[0] : 0.0;
-    }
+    block_partials<1>(part, red);
 }
 
 // q = A p (vector-CSR, T lanes per row) and p . q
@@ -313,18 +340,13 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
             part[0] += p[i] * s;
         }
     }
-    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
-        sc->pq = part[0];
-        bool ok = part[0] > 0.0 && sc->rho > 0.0;
-        if (!ok) sc->breakdown = 1;
-        sc->alpha = ok ? sc->rho / part[0] : 0.0;
-    }
+    block_partials<1>(part, red);
 }
 
 __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
-                 double *__restrict__ r, PcgScalars *sc, Reduce red, cudaGraphConditionalHandle handle,
-                 int use_handle, const double *__restrict__ dinv0, double *__restrict__ x0) {
+                 double *__restrict__ r, const PcgScalars *sc, Reduce red, const double *__restrict__ dinv0,
+                 double *__restrict__ x0) {
     double alpha = sc->alpha;
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -334,15 +356,7 @@ xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restri
         if (x0) x0[i] = ri * dinv0[i];  // the next cycle's level-0 pre-smooth from zero
         part[0] += ri * ri;
     }
-    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) {
-        sc->rr = part[0];
-        int its = sc->its + 1;
-        sc->its = its;
-        if (use_handle) {
-            bool go = part[0] > sc->thresh2 && its < sc->max_its && !sc->breakdown && isfinite(part[0]);
-            cudaGraphSetConditional(handle, go ? 1u : 0u);
-        }
-    }
+    block_partials<1>(part, red);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -355,17 +369,7 @@ rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z,
         part[0] += r[i] * zi;
         if (!first) part[1] += zi * q[i];
     }
-    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) {
-        double rho_new = part[0];
-        if (!first) {
-            sc->zq = part[1];
-            sc->beta = sc->flexible ? (-sc->alpha * part[1]) / sc->rho : rho_new / sc->rho;
-        } else {
-            sc->beta = 0.0;
-        }
-        sc->rho = rho_new;
-        sc->start = 0;
-    }
+    block_partials<2>(part, red);
 }
 
 template <int T>
@@ -387,19 +391,7 @@ resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restric
             part[0] += e * e;
         }
     }
-    if (reduce_and_finish<1>(part, red) && threadIdx.x == 0) sc->tt = part[0];
-}
-
-// finish of r.z / z.q: beta and rho (start: beta = 0)
-__device__ __forceinline__ void finish_rz(PcgScalars *sc, double rz, double zq) {
-    if (!sc->start) {
-        sc->zq = zq;
-        sc->beta = sc->flexible ? (-sc->alpha * zq) / sc->rho : rz / sc->rho;
-    } else {
-        sc->beta = 0.0;
-    }
-    sc->rho = rz;
-    sc->start = 0;
+    block_partials<1>(part, red);
 }
 
 // level-0 post-smoothing z = x + d (b - A x) with r.z and z.q (r = b)
@@ -422,7 +414,7 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
         part[0] = bi * zi;
         part[1] = zi * q[i];
     }
-    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+    block_partials<2>(part, red);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -441,7 +433,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
         part[0] = bi * zi;
         part[1] = zi * q[i];
     }
-    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+    block_partials<2>(part, red);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -454,7 +446,7 @@ to_f64_rz_kernel(int32_t n, const float *__restrict__ z32, double *__restrict__ 
         part[0] += r[i] * zi;
         part[1] += zi * q[i];
     }
-    if (reduce_and_finish<2>(part, red) && threadIdx.x == 0) finish_rz(sc, part[0], part[1]);
+    block_partials<2>(part, red);
 }
 
 template <typename XT>
@@ -622,11 +614,14 @@ template <int T>
 static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     int blocks = reduce_blocks((int64_t)A.nrows * T, 1);
     { ap_kernel<T><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, p, q, sc, red); ::amg::count_launch(); }
+    launch_finish<1, kFinAp>(blocks, red, sc, s);
 }
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        { ap_sell_kernel<<<reduce_blocks(A.nrows, 1), kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        int blocks = reduce_blocks(A.nrows, 1);
+        { ap_sell_kernel<<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
     }
@@ -643,7 +638,9 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
                    double *x0, cudaStream_t s) {
-    { xr_update_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, p, q, x, r, sc, red, handle, use_handle ? 1 : 0, dinv0, x0); ::amg::count_launch(); }
+    int blocks = reduce_blocks(n, 1);
+    { xr_update_kernel<<<blocks, kThreads, 0, s>>>(n, p, q, x, r, sc, red, dinv0, x0); ::amg::count_launch(); }
+    launch_finish<1, kFinXr>(blocks, red, sc, s, handle, use_handle);
     AMG_CHECK_LAUNCH();
 }
 
@@ -655,6 +652,7 @@ bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, c
         int blocks = div_up(n, kThreads);
         if (blocks > kMaxReduceBlocks) return false;
         { post_rz_sell_kernel<<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+        launch_finish<2, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return true;
     }
@@ -669,13 +667,16 @@ bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, c
         case 16: { post_rz_csr_kernel<16><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
         default: { post_rz_csr_kernel<32><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
     }
+    launch_finish<2, kFinRz>((int)blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
     return true;
 }
 
 void to_f64_rz(int32_t n, const float *z32, double *z, const double *r, const double *q, PcgScalars *sc, Reduce red,
                cudaStream_t s) {
-    { to_f64_rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, z32, z, r, q, sc, red); ::amg::count_launch(); }
+    int blocks = reduce_blocks(n, 1);
+    { to_f64_rz_kernel<<<blocks, kThreads, 0, s>>>(n, z32, z, r, q, sc, red); ::amg::count_launch(); }
+    launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
 
@@ -695,7 +696,9 @@ void to_f32_scaled(int64_t n, const double *src, const float *d, float *dst, flo
 
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
             cudaStream_t s) {
-    { rz_kernel<<<reduce_blocks(n, 4), kThreads, 0, s>>>(n, r, z, q, sc, red); ::amg::count_launch(); }
+    int blocks = reduce_blocks(n, 1);
+    { rz_kernel<<<blocks, kThreads, 0, s>>>(n, r, z, q, sc, red); ::amg::count_launch(); }
+    launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
 
@@ -703,6 +706,7 @@ void true_residual(const CycMat<double> &A, const double *b, const double *x, do
                    Reduce red, cudaStream_t s) {
     int blocks = reduce_blocks((int64_t)A.nrows * 4, 1);
     { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
+    launch_finish<1, kFinTt>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
 

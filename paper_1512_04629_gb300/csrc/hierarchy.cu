@@ -105,6 +105,27 @@ void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &
 // ---------------------------------------------------------------------------
 // Algorithm 4 (Sparse Galerkin), Algorithm 3 / 3b per level
 // ---------------------------------------------------------------------------
+// Hybrid Galerkin (Algorithm 4, hybrid line): the minimal pattern of level l
+// comes from Phat^T Ahat_{l-1} P + P^T Ahat_{l-1} Phat with the *sparsified*
+// operator of level l-1, i.e. the C rows of Ahat_{l-1} P_{l-1} and their
+// transpose.  For l = 1, Ahat_0 = A_0 and the Sparse Galerkin flags apply.
+static const uint8_t *hybrid_pattern(Hierarchy &h, int l, cudaStream_t s) {
+    Level &F = *h.lev[l - 1];
+    Level &V = *h.lev[l];
+    if (!F.cpts.ptr) {  // assembled hierarchies carry C/F markers only
+        require(F.cf.ptr != nullptr, "hybrid sparsify needs the C/F markers of level l-1");
+        int64_t nc = F.P.ncols;
+        F.cmap.alloc(sizeof(int32_t) * (F.n() + 1));
+        F.cpts.alloc(sizeof(int32_t) * (nc + 1));
+        setup::coarse_map(F.cf.as<int8_t>(), F.n(), F.cmap.as<int32_t>(), F.cpts.as<int32_t>(), s);
+    }
+    DevCSR APh;
+    setup::spgemm(F.op(), F.P, APh, s);
+    V.inM_hybrid.alloc(V.A.nnz + kPad);
+    setup::minimal_pattern(V.A, APh, F.cpts.as<int32_t>(), V.inM_hybrid.as<uint8_t>(), s);
+    return V.inM_hybrid.as<uint8_t>();
+}
+
 void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
     Level &V = *h.lev[l];
     if (l == 0 || V.gamma == 0.0) {
@@ -113,9 +134,10 @@ void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
         AMG_CUDA(cudaMemsetAsync(V.keep.ptr, 1, V.A.nnz, s));
         return;
     }
+    const uint8_t *inM = V.inM.as<uint8_t>();
+    if (h.opt.method == AMG_METHOD_HYBRID && l >= 2) inM = hybrid_pattern(h, l, s);
     DevCSR H;
-    setup::sparsify(V.A, V.inM.as<uint8_t>(), V.tpos.as<int32_t>(), V.diagpos.as<int32_t>(), V.gamma,
-                    V.keep.as<uint8_t>(), H, s);
+    setup::sparsify(V.A, inM, V.tpos.as<int32_t>(), V.diagpos.as<int32_t>(), V.gamma, V.keep.as<uint8_t>(), H, s);
     V.H = std::move(H);
     V.h_alias = false;
 }

@@ -20,6 +20,7 @@ struct Level {
     DevBuf diagpos, tpos;  // int32 per row / per entry of A
     DevBuf strong;         // uint8 per entry of A (levels that were coarsened)
     DevBuf inM, keep;      // uint8 per entry of A
+    DevBuf inM_hybrid;     // Hybrid Galerkin: M from the sparsified operator of level l-1
     DevBuf cf;             // int8 per row (coarsened levels)
     DevBuf cmap, cpts;     // int32
     DevCSR P, R;           // interpolation and restriction (not on the coarsest level)

@@ -90,6 +90,31 @@ def test_sparsify_end_to_end_matches_oracle(amg, case, gamma):
         np.testing.assert_array_equal(h.export(l, "Ahat").val, h.export(l, "A").val)
 
 
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+@pytest.mark.parametrize("case", ["3d7_20", "fv7_15", "3d27_11"])
+def test_hybrid_end_to_end_matches_oracle(amg, case, gamma):
+    """Hybrid Galerkin: M from the sparsified level above; masks bit-exact,
+    also along an Algorithm 5 schedule."""
+    A = CASES[case]()
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, gamma], method=1)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, gamma], method=amg.METHOD_HYBRID)
+    for l in range(1, h.num_levels):
+        np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l), err_msg=f"keep_{l}")
+        _same_csr(h.export(l, "Ahat"), ref.matrix(l, "Ahat"), what=f"Ahat_{l}")
+    for _ in range(6):
+        c1 = h.reintroduce(1)
+        c2, _ = ref.reintroduce(1)
+        assert c1 == c2
+        for l in range(1, h.num_levels):
+            np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l))
+    if gamma <= 0.1:
+        b = gen.rhs_uniform(A.n, 1)
+        x, info = h.solve(b)
+        xr, ir = ref.pcg(b)
+        assert info.status == 0 and abs(info.iterations - ir.iterations) <= 1
+
+
 def test_per_level_on_oracle_matrices(amg):
     """Given the oracle's own A_l, the GPU's strength/PMIS/interpolation/RAP
     reproduce the oracle's level l (PMIS seeded with the level index)."""

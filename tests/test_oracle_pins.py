@@ -572,3 +572,59 @@ def test_adaptive_recovers_and_is_noop_for_galerkin():
     assert i4.status == 0 and i4.final_relres <= 1e-8
     assert i4.resets >= 1
     assert h4.gamma(1) < 1.0
+
+
+# ---------------------------------------------------------------------------
+# Hybrid Galerkin (Algorithm 4, hybrid line): M from the sparsified Ahat_{l-1}
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_hybrid_minimal_pattern_brute_force(gamma):
+    A = gen.poisson3d_7pt(9)
+    h = oracle.Hierarchy(A, max_size=20)
+    h.sparsify([0.0, gamma], method=1)
+    ref = oracle.Hierarchy(A, max_size=20)
+    for l in range(1, h.num_levels):
+        Ah_prev = h.matrix(l - 1, "Ahat")
+        P = h.matrix(l - 1, "P").todense()
+        cf = h.cf(l - 1)
+        Phat = np.zeros_like(P)
+        Phat[np.where(cf == 1)[0], np.arange(P.shape[1])] = 1.0
+        pa = pattern(Ah_prev).astype(int)
+        pp = pattern(h.matrix(l - 1, "P")).astype(int)
+        ph = (Phat > 0).astype(int)
+        M = ((ph.T @ pa @ pp) + (pp.T @ pa @ ph)) > 0
+        Ac = h.matrix(l, "A").to_scipy()
+        rows = np.repeat(np.arange(Ac.shape[0]), np.diff(Ac.indptr))
+        inM_h = M[rows, Ac.indices].astype(np.uint8)
+        # the kept pattern is what sparsify gives with that M (dense reference)
+        _, keep_ref = _dense_sparsify_reference(Ac, inM_h, gamma)
+        np.testing.assert_array_equal(h.keep(l), keep_ref.astype(np.uint8))
+        # Hybrid M is inside Sparse Galerkin's M (Ahat_{l-1} has fewer edges)
+        assert np.all(inM_h <= ref.inM(l))
+    # level 1 is identical for both methods (Ahat_0 = A_0)
+    hs = oracle.Hierarchy(A, max_size=20)
+    hs.sparsify([0.0, gamma], method=0)
+    np.testing.assert_array_equal(h.keep(1), hs.keep(1))
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_hybrid_keeps_theorem1_and_solves(gamma):
+    """Row sums and symmetry always; semi-definiteness where Theorem 1's
+    diagonal-dominance hypothesis holds (coarse Galerkin operators need not
+    be diagonally dominant, and aggressive Hybrid dropping can then make
+    Ahat_l indefinite)."""
+    A = gen.poisson3d_7pt(12)
+    h = oracle.Hierarchy(A, max_size=30)
+    h.sparsify([0.0, gamma], method=1)
+    for l in range(1, h.num_levels):
+        Hd = h.matrix(l, "Ahat").todense()
+        Ad = h.matrix(l, "A").todense()
+        scale = np.abs(Ad).max()
+        np.testing.assert_allclose(Hd.sum(axis=1), Ad.sum(axis=1), atol=1e-13 * scale)
+        np.testing.assert_allclose(Hd, Hd.T, atol=1e-14 * scale)
+        if np.all(2 * np.abs(np.diag(Ad)) >= np.abs(Ad).sum(axis=1) - 1e-12 * scale):
+            assert np.linalg.eigvalsh(Hd).min() > -1e-12 * scale
+    if gamma <= 0.1:
+        b = gen.rhs_uniform(A.n, 4)
+        x, info = h.pcg(b)
+        assert info.status == 0 and info.final_relres <= 1e-8
