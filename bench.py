@@ -207,6 +207,20 @@ KIND_NAMES = {0: "relax_pre_residual", 1: "restrict", 2: "prolong", 3: "relax_po
               5: "pcg_Ap_dot", 6: "pcg_vector"}
 
 
+def aggregate_replicas(elapsed_s: float, steps: int, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank did `steps`
+    solves; the job took the slowest rank's time (max over ranks)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        world = dist.get_world_size()
+        t = torch.tensor([elapsed_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_s = float(t.item())
+    return world * steps / elapsed_s, elapsed_s, world
+
+
 def collect_timing(h, nlev):
     rows = []
     for kind in range(7):

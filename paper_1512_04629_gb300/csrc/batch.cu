@@ -117,18 +117,16 @@ __global__ void coarse_kernel(int32_t n, int K, const double *__restrict__ inv, 
 }
 
 // ---------------------------------------------------------------------------
-// per-column deterministic reductions.  A thread's slot is its column; the
-// block sums slots in thread order, the last block sums block partials in
-// block order.
-// ---------------------------------------------------------------------------
+// per-column deterministic reductions.  A thread's slot is its column; each
+// block sums its slots in thread order and stores one partial per column; a
+// finisher kernel (one block per column) sums the partials in block order
+// and updates that column's scalars.  No atomics, no fences.
 template <int NV>
-__device__ bool col_reduce(double (&v)[NV], int K, int col, double *partials, unsigned *counter, double (&out)[NV]) {
+__device__ void col_partials(double (&v)[NV], int K, double *partials) {
     __shared__ double sh[NV][kThreads];
-    __shared__ bool last;
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
     __syncthreads();
-    // threads 0..K-1 sum the slots of their column (threads t with t % K == col)
     if (threadIdx.x < K) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
@@ -137,34 +135,60 @@ __device__ bool col_reduce(double (&v)[NV], int K, int col, double *partials, un
             partials[((size_t)k * kMaxCols + threadIdx.x) * kBatchReduceBlocks + blockIdx.x] = s;
         }
     }
-    (void)col;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned prev = atomicAdd(counter, 1u);
-        last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return false;
-    __threadfence();
-    if (threadIdx.x < K) {
+}
+
+enum ColFin { kColRz = 0, kColAp = 1, kColXr = 2, kColTt = 3 };
+
+template <int NV, int FIN>
+__global__ void __launch_bounds__(kThreads)
+col_finish_kernel(int nblocks, const double *partials, ColScalars sc, int flexible) {
+    const int c = blockIdx.x;
+    __shared__ double sh[NV][kThreads / 32];
+    double t[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double s = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b)
-                s += ((volatile double *)partials)[((size_t)k * kMaxCols + threadIdx.x) * kBatchReduceBlocks + b];
-            out[k] = s;
-        }
+    for (int k = 0; k < NV; ++k) {
+        t[k] = 0.0;
+        const double *p = partials + ((size_t)k * kMaxCols + c) * kBatchReduceBlocks;
+        for (int b = threadIdx.x; b < nblocks; b += kThreads) t[k] += p[b];
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = t[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[k][w] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *counter = 0u;
-    return true;
+    if (threadIdx.x != 0) return;
+    double out[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        out[k] = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) out[k] += sh[k][i];
+    }
+    if (FIN == kColRz) {
+        if (sc.active[c]) {
+            double rho_new = out[0];
+            if (sc.start[c]) sc.beta[c] = 0.0;
+            else sc.beta[c] = flexible ? (-sc.alpha[c] * out[NV - 1]) / sc.rho[c] : rho_new / sc.rho[c];
+            sc.zq[c] = out[NV - 1];
+            sc.rho[c] = rho_new;
+            sc.start[c] = 0;
+        }
+    } else if (FIN == kColAp) {
+        sc.pq[c] = out[0];
+        sc.alpha[c] = (sc.active[c] && out[0] > 0.0) ? sc.rho[c] / out[0] : 0.0;
+    } else if (FIN == kColXr) {
+        sc.rr[c] = out[0];
+    } else {
+        sc.tt[c] = out[0];
+    }
 }
 
 int grid_for(int64_t n, int K) {
     int64_t rows_per_block = kThreads / K;
     int64_t b = (n + rows_per_block - 1) / rows_per_block;
-    b = (b + 3) / 4;
+    b = (b + 3) / 4;  // about four rows per thread
     if (b < 1) b = 1;
     if (b > kBatchReduceBlocks) b = kBatchReduceBlocks;
     return (int)b;
@@ -173,7 +197,7 @@ int grid_for(int64_t n, int K) {
 // thread -> (row, column) with column = threadIdx % K (K divides 256)
 __global__ void __launch_bounds__(kThreads)
 rz_kernel(int32_t n, int K, const double *__restrict__ R, const double *__restrict__ Z, const double *__restrict__ Q,
-          ColScalars sc, int flexible, double *partials, unsigned *counter) {
+          double *partials) {
     int c = threadIdx.x % K;
     int rpb = kThreads / K;
     double v[2] = {0.0, 0.0};
@@ -182,18 +206,7 @@ rz_kernel(int32_t n, int K, const double *__restrict__ R, const double *__restri
         v[0] += R[i * K + c] * z;
         v[1] += z * Q[i * K + c];
     }
-    double out[2];
-    if (col_reduce<2>(v, K, c, partials, counter, out) && threadIdx.x < K) {
-        int cc = threadIdx.x;
-        if (sc.active[cc]) {
-            double rho_new = out[0];
-            if (sc.start[cc]) sc.beta[cc] = 0.0;
-            else sc.beta[cc] = flexible ? (-sc.alpha[cc] * out[1]) / sc.rho[cc] : rho_new / sc.rho[cc];
-            sc.zq[cc] = out[1];
-            sc.rho[cc] = rho_new;
-            sc.start[cc] = 0;
-        }
-    }
+    col_partials<2>(v, K, partials);
 }
 
 __global__ void p_update_kernel(int64_t total, int K, const double *__restrict__ Z, double *__restrict__ P, ColScalars sc) {
@@ -207,8 +220,8 @@ __global__ void p_update_kernel(int64_t total, int K, const double *__restrict__
 template <int G, int CPL, bool RESID>
 __global__ void __launch_bounds__(kThreads)
 ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
-          const double *__restrict__ Pin, const double *__restrict__ Bin, double *__restrict__ Qout, ColScalars sc,
-          double *partials, unsigned *counter) {
+          const double *__restrict__ Pin, const double *__restrict__ Bin, double *__restrict__ Qout,
+          double *partials) {
     constexpr int K = G * CPL;
     int t = threadIdx.x % G;
     double part[CPL];
@@ -250,9 +263,8 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
             }
         }
     }
-    // per-column reduction: slot of thread t, value u -> column t + u*G
+    // per-column partial: slot of thread t, value u -> column t + u*G
     __shared__ double sh[CPL][kThreads];
-    __shared__ bool last;
 #pragma unroll
     for (int u = 0; u < CPL; ++u) sh[u][threadIdx.x] = part[u];
     __syncthreads();
@@ -262,32 +274,11 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
         for (int r = tt; r < kThreads; r += G) s += sh[u][r];
         partials[(size_t)col * kBatchReduceBlocks + blockIdx.x] = s;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if (threadIdx.x < K) {
-        int col = threadIdx.x;
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)partials)[(size_t)col * kBatchReduceBlocks + b];
-        if (RESID) {
-            sc.tt[col] = s;
-        } else {
-            sc.pq[col] = s;
-            sc.alpha[col] = (sc.active[col] && s > 0.0) ? sc.rho[col] / s : 0.0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *counter = 0u;
 }
 
 __global__ void __launch_bounds__(kThreads)
 xr_kernel(int32_t n, int K, const double *__restrict__ P, const double *__restrict__ Q, double *__restrict__ X,
-          double *__restrict__ R, ColScalars sc, double *partials, unsigned *counter) {
+          double *__restrict__ R, ColScalars sc, double *partials) {
     int c = threadIdx.x % K;
     int rpb = kThreads / K;
     double alpha = sc.active[c] ? sc.alpha[c] : 0.0;
@@ -302,8 +293,7 @@ xr_kernel(int32_t n, int K, const double *__restrict__ P, const double *__restri
         }
         v[0] += r * r;
     }
-    double out[1];
-    if (col_reduce<1>(v, K, c, partials, counter, out) && threadIdx.x < K) sc.rr[threadIdx.x] = out[0];
+    col_partials<1>(v, K, partials);
 }
 
 __global__ void scatter_kernel(int32_t n, int K, int c, const double *v, double *M) {
@@ -364,7 +354,10 @@ void coarse_solve(int32_t n, int K, const double *inv, const XT *B, XT *X, cudaS
 
 void rz(int32_t n, int K, const double *R, const double *Z, const double *Q, ColScalars sc, int flexible,
         double *partials, unsigned *counter, cudaStream_t s) {
-    { rz_kernel<<<grid_for(n, K), kThreads, 0, s>>>(n, K, R, Z, Q, sc, flexible, partials, counter); ::amg::count_launch(); }
+    int blocks = grid_for(n, K);
+    { rz_kernel<<<blocks, kThreads, 0, s>>>(n, K, R, Z, Q, partials); ::amg::count_launch(); }
+    { col_finish_kernel<2, kColRz><<<K, kThreads, 0, s>>>(blocks, partials, sc, flexible); ::amg::count_launch(); }
+    (void)counter;
     AMG_CHECK_LAUNCH();
 }
 
@@ -383,13 +376,17 @@ static void launch_ap(const CycMat<double> &A, int K, const double *P, const dou
         int64_t b = ((n + rpb - 1) / rpb + 3) / 4;
         return (int)std::max<int64_t>(1, std::min<int64_t>(b, kBatchReduceBlocks));
     };
+    (void)counter;
+    int blocks = 0;
     switch (K) {
-        case 8: { ap_kernel<8, 1, RESID><<<grid(8), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, sc, partials, counter); ::amg::count_launch(); } break;
-        case 16: { ap_kernel<16, 1, RESID><<<grid(16), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, sc, partials, counter); ::amg::count_launch(); } break;
-        case 32: { ap_kernel<32, 1, RESID><<<grid(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, sc, partials, counter); ::amg::count_launch(); } break;
-        case 64: { ap_kernel<32, 2, RESID><<<grid(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, sc, partials, counter); ::amg::count_launch(); } break;
+        case 8: blocks = grid(8); { ap_kernel<8, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
+        case 16: blocks = grid(16); { ap_kernel<16, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
+        case 32: blocks = grid(32); { ap_kernel<32, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
+        case 64: blocks = grid(32); { ap_kernel<32, 2, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
         default: throw Error(AMG_ERR_INVALID, "batch width must be 8, 16, 32 or 64");
     }
+    if (RESID) { col_finish_kernel<1, kColTt><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
+    else { col_finish_kernel<1, kColAp><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -405,7 +402,10 @@ void residual(const CycMat<double> &A, int K, const double *B, const double *X, 
 
 void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, ColScalars sc,
                double *partials, unsigned *counter, cudaStream_t s) {
-    { xr_kernel<<<grid_for(n, K), kThreads, 0, s>>>(n, K, P, Q, X, R, sc, partials, counter); ::amg::count_launch(); }
+    int blocks = grid_for(n, K);
+    { xr_kernel<<<blocks, kThreads, 0, s>>>(n, K, P, Q, X, R, sc, partials); ::amg::count_launch(); }
+    { col_finish_kernel<1, kColXr><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
+    (void)counter;
     AMG_CHECK_LAUNCH();
 }
 

@@ -54,7 +54,7 @@ template <typename XT> void to_cycle(const double *src, XT *dst, int64_t n, cuda
 template <typename XT> void from_cycle(const XT *src, double *dst, int64_t n, cudaStream_t s);
 
 constexpr int kMaxCols = 64;
-constexpr int kBatchReduceBlocks = 256;
+constexpr int kBatchReduceBlocks = 8192;
 
 }  // namespace bat
 }  // namespace amg

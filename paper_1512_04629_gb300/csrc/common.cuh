@@ -46,6 +46,11 @@ void count_launch();
 inline void require(bool ok, const std::string &msg) {
     if (!ok) throw Error(AMG_ERR_INVALID, msg);
 }
+// literal messages bind here: nothing is constructed unless the check fails
+// (the host-side validation loops call this once per matrix entry)
+inline void require(bool ok, const char *msg) {
+    if (!ok) throw Error(AMG_ERR_INVALID, msg);
+}
 
 // ---------------------------------------------------------------------------
 // device buffers (RAII); every persistent allocation of the library goes
@@ -116,6 +121,7 @@ inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / 
 // exclusive scan of n int32 counts into out[0..n] (out[n] = total); returns total
 int64_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 
 template <typename T> T read_scalar(const T *dptr, cudaStream_t s) {
     T v;

@@ -207,15 +207,47 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Every block reduces its values (fixed tree) and thread 0 stores the block
-// partial; a one-block finisher kernel launched next sums the partials in
-// block order.  No atomics and no fences on the producers' critical path.
+// Block partials without a block-wide barrier at the end: each warp reduces
+// its values with shuffles and parks them in shared memory; the last warp of
+// the block to arrive (a shared arrival counter, zeroed when the kernel
+// starts) adds the warp values in warp order and stores the block partial.
+// Warps that finish early leave at once instead of waiting for the block's
+// slowest gathers.  A one-block finisher kernel launched next sums the block
+// partials in block order: no atomics on floating-point values, no fences on
+// the producers' critical path, a deterministic result.
+__device__ __forceinline__ unsigned *arrival_counter() {
+    __shared__ unsigned c;
+    return &c;
+}
+
+// every kernel that calls block_partials calls this first (all threads)
+__device__ __forceinline__ void block_partials_begin() {
+    if (threadIdx.x == 0) *arrival_counter() = 0u;
+    __syncthreads();
+}
+
 template <int NV>
 __device__ __forceinline__ void block_partials(double (&v)[NV], Reduce red) {
-    block_reduce<NV>(v);
-    if (threadIdx.x == 0) {
+    __shared__ double sh[NV][kThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double x[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) red.partials[k * kMaxReduceBlocks + blockIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) {
+        x[k] = v[k];
+        for (int o = 16; o > 0; o >>= 1) x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+    }
+    if (lane != 0) return;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][w] = x[k];
+    __threadfence_block();
+    const unsigned nw = blockDim.x >> 5;
+    if (atomicAdd(arrival_counter(), 1u) != nw - 1) return;
+    __threadfence_block();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double t = 0.0;
+        for (unsigned i = 0; i < nw; ++i) t += ((volatile double *)sh[k])[i];
+        red.partials[k * kMaxReduceBlocks + blockIdx.x] = t;
     }
 }
 
@@ -312,6 +344,7 @@ __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                const int32_t *__restrict__ sci, const double *__restrict__ sv, const double *__restrict__ p,
                double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     double part[1] = {0.0};
     for (int64_t pos = (int64_t)blockIdx.x * kThreads + threadIdx.x; pos < n; pos += (int64_t)gridDim.x * kThreads) {
         const int32_t i = perm ? __ldg(perm + pos) : (int32_t)pos;
@@ -327,6 +360,7 @@ template <int T>
 __global__ void __launch_bounds__(kThreads)
 ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
           const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
     for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T; g += stride) {
@@ -347,6 +381,7 @@ __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
                  double *__restrict__ r, const PcgScalars *sc, Reduce red, const double *__restrict__ dinv0,
                  double *__restrict__ x0) {
+    block_partials_begin();
     double alpha = sc->alpha;
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -362,6 +397,7 @@ xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restri
 __global__ void __launch_bounds__(kThreads)
 rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ q,
           PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     int first = sc->start;
     double part[2] = {0.0, 0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -377,6 +413,7 @@ __global__ void __launch_bounds__(kThreads)
 resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
              const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ t_out,
              PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
     for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T; g += stride) {
@@ -400,6 +437,7 @@ __global__ void __launch_bounds__(kThreads)
 post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                    double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t i = (int32_t)(g / T);
     int t = (int)(g % T);
@@ -422,6 +460,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
                     const int32_t *__restrict__ sw, const int32_t *__restrict__ sci, const double *__restrict__ sv,
                     const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                     double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     double part[2] = {0.0, 0.0};
     if (pos < n) {
@@ -439,6 +478,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
 __global__ void __launch_bounds__(kThreads)
 to_f64_rz_kernel(int32_t n, const float *__restrict__ z32, double *__restrict__ z, const double *__restrict__ r,
                  const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    block_partials_begin();
     double part[2] = {0.0, 0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         double zi = (double)z32[i];

@@ -206,7 +206,7 @@ template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
 }
 
 static void free_sell(Level &V) {
-    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release(); V.sperm.release();
+    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release(); V.sperm.release(); V.sv64.release();
     V.sell_entries = 0;
 }
 
@@ -370,6 +370,13 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
         if (V.variant != AMG_SPMV_SELL32) free_sell(V);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_store_locked(key, V.variant);
+    }
+    // FP32 cycles: the outer PCG multiplies by A_0 in FP64 -- give it the same
+    // SELL layout with FP64 values when level 0 relaxes through SELL
+    if (l == 0 && V.vbytes != 8 && V.variant == AMG_SPMV_SELL32 && V.sv.ptr) {
+        V.sv64.alloc(sizeof(double) * (V.sell_entries + kPad));
+        cyc::sell_fill<double>(M.nrows, M.rp(), M.ci(), M.v(), V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
+                               V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sci.as<int32_t>(), V.sv64.as<double>(), s);
     }
     if (l == h.nlev() - 1) {
         h.coarse_n = n;
@@ -679,7 +686,17 @@ CycMat<double> a0_mat(Hierarchy &h) {
         return m;
     }
     CycMat<double> m = make_mat<double>(V.A, V.A.v());
-    m.variant = heuristic_variant(V.A);
+    if (V.variant == AMG_SPMV_SELL32 && V.sv64.ptr) {
+        m.variant = AMG_SPMV_SELL32;
+        m.nslices = (V.A.nrows + 31) / 32;
+        m.soff = V.soff.as<int32_t>();
+        m.sw = V.sw.as<int32_t>();
+        m.sci = V.sci.as<int32_t>();
+        m.sv = V.sv64.as<double>();
+        m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
+    } else {
+        m.variant = V.variant == AMG_SPMV_SELL32 ? heuristic_variant(V.A) : V.variant;
+    }
     return m;
 }
 

@@ -36,6 +36,7 @@ struct Level {
     DevBuf dinv32;
     DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
     DevBuf sperm;              // SELL position -> row when rows are length-sorted
+    DevBuf sv64;               // level 0 in FP32 modes: FP64 values in the same SELL layout (outer PCG)
     int64_t sell_entries = 0;
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
     bool pr_tuned = false;  // transfer-operator variants chosen by timed trials

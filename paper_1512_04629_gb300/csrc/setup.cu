@@ -8,6 +8,7 @@
 // setup is deterministic and repeatable run to run.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "setup_ops.cuh"
@@ -326,10 +327,10 @@ __device__ __forceinline__ int32_t row_lookup(const RowTables &t, int32_t j) {
 }
 
 template <int NT>
-__device__ void row_numeric(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
-                            const double *av, const int32_t *brp, const int32_t *bci,
-                            const double *bv, RowTables &t, int32_t *counter,
-                            const int32_t *crp, int32_t *cci, double *cv, int64_t ub) {
+__device__ int32_t row_numeric(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
+                               const double *av, const int32_t *brp, const int32_t *bci,
+                               const double *bv, RowTables &t, int32_t *counter,
+                               const int64_t *obase, int32_t *cci, double *cv, int64_t ub) {
     int32_t u = row_insert<NT>(i, lane, arp, aci, brp, bci, t, counter, ub);
     // compact the distinct keys, pad to a power of two, bitonic sort
     if (lane == 0) *counter = 0;
@@ -357,7 +358,7 @@ __device__ void row_numeric(int32_t i, int32_t lane, const int32_t *arp, const i
     }
     // rank of each key, output columns, zero accumulators
     uint32_t mask = (uint32_t)t.hs - 1;
-    int32_t base = crp[i];
+    const int64_t base = obase[i];
     for (int32_t r = lane; r < u; r += NT) {
         int32_t j = t.list[r];
         uint32_t s = hash32(j) & mask;
@@ -380,6 +381,7 @@ __device__ void row_numeric(int32_t i, int32_t lane, const int32_t *arp, const i
     }
     for (int32_t r = lane; r < u; r += NT) cv[base + r] = t.acc[r];
     gsync<NT>();
+    return u;
 }
 
 __global__ void spgemm_ub_kernel(int32_t n, const int32_t *arp, const int32_t *aci,
@@ -445,7 +447,7 @@ template <int U, bool NUMERIC>
 __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
                             const double *__restrict__ av, const int32_t *__restrict__ brp,
                             const int32_t *__restrict__ bci, const double *__restrict__ bv, WarpTab<U> &t,
-                            int64_t ub, const int32_t *__restrict__ crp, int32_t *__restrict__ cci,
+                            int64_t ub, const int64_t *__restrict__ obase, int32_t *__restrict__ cci,
                             double *__restrict__ cv) {
     const int32_t hs = row_slots(ub, 2 * U);
     const uint32_t mask = (uint32_t)hs - 1;
@@ -528,7 +530,7 @@ __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp
             __syncwarp();
         }
     }
-    const int32_t cbase = crp[i];
+    const int64_t cbase = obase[i];
     for (int32_t r = lane; r < u; r += 32) {
         int32_t j = t.list[r];
         uint32_t sl = hash32(j) & mask;
@@ -592,14 +594,14 @@ template <int U, int WARPS, bool NUMERIC>
 __global__ void __launch_bounds__(WARPS * 32)
 spgemm_warp_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                    const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
-                   int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv, const int64_t *ub) {
+                   int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
     extern __shared__ __align__(16) unsigned char smem[];
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpTab<U> t(smem + (size_t)w * WarpTab<U>::kBytes);
     for (int32_t r = blockIdx.x * WARPS + w; r < nrows; r += gridDim.x * WARPS) {
         int32_t i = rows[r];
-        int32_t u = warp_row<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], crp, cci, cv);
-        if (!NUMERIC && lane == 0) cnt[i] = u;
+        int32_t u = warp_row<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], obase, cci, cv);
+        if (lane == 0) cnt[i] = u;
     }
 }
 
@@ -607,7 +609,7 @@ template <bool NUMERIC>
 __global__ void __launch_bounds__(kBlockThreads)
 spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                     const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
-                    int32_t *cnt, const int32_t *crp, int32_t *cci, double *cv, const int64_t *ub,
+                    int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub,
                     unsigned char *gscratch, int32_t ghs, int32_t gumax) {
     extern __shared__ __align__(16) unsigned char smem[];
     RowTables t;
@@ -629,8 +631,9 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
     for (int32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         int32_t i = rows[r];
         if (NUMERIC) {
-            row_numeric<kBlockThreads>(i, threadIdx.x, arp, aci, av, brp, bci, bv, t, &counter,
-                                       crp, cci, cv, ub[i]);
+            int32_t u = row_numeric<kBlockThreads>(i, threadIdx.x, arp, aci, av, brp, bci, bv, t, &counter,
+                                                   obase, cci, cv, ub[i]);
+            if (threadIdx.x == 0) cnt[i] = u;
         } else {
             int32_t u = row_insert<kBlockThreads>(i, threadIdx.x, arp, aci, brp, bci, t, &counter, ub[i]);
             if (threadIdx.x == 0) cnt[i] = u;
@@ -790,6 +793,20 @@ __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
     double s = 0.0;
     for (int32_t k = max(i, j); k < n; ++k) s += Linv[(size_t)k * n + i] * Linv[(size_t)k * n + j];
     inv[t] = s;
+}
+
+// copy each row's entries from its product-bound slot to the final CSR
+__global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int32_t *crp, const int32_t *tci,
+                                      const double *tv, int32_t *cci, double *cv) {
+    int32_t i = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int64_t src = obase[i];
+    int32_t dst = crp[i], len = crp[i + 1] - crp[i];
+    for (int32_t e = lane; e < len; e += 32) {
+        cci[dst + e] = tci[src + e];
+        cv[dst + e] = tv[src + e];
+    }
 }
 
 }  // namespace
@@ -985,61 +1002,85 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         gscr.alloc(per * gblocks, s);
     }
     const int64_t *ubp = ub.as<int64_t>();
-    auto launch = [&](bool numeric) {
+    // launch(numeric, obase, out_cols, out_vals): one pass over the bins
+    auto launch = [&](bool numeric, const int64_t *ob, int32_t *cc, double *cvv) {
         int32_t *cp = cnt.as<int32_t>();
-        int32_t *cc = numeric ? Cm.ci() : nullptr;
-        double *cvv = numeric ? Cm.v() : nullptr;
-        const int32_t *crp = numeric ? Cm.rp() : nullptr;
         if (nb[0] > 0) {
             int blocks = std::min(div_up(nb[0], kTinyWarps), 152 * 32);
             if (numeric)
                 { spgemm_warp_kernel<kTinyUmax, kTinyWarps, true><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
             else
                 { spgemm_warp_kernel<kTinyUmax, kTinyWarps, false><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[1] > 0) {
             int blocks = std::min(div_up(nb[1], kSmallWarps), 152 * 16);
             if (numeric)
                 { spgemm_warp_kernel<kSmallUmax, kSmallWarps, true><<<blocks, kSmallWarps * 32, small_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
             else
                 { spgemm_warp_kernel<kSmallUmax, kSmallWarps, false><<<blocks, kSmallWarps * 32, small_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, crp, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[2] > 0) {
             int blocks = std::min(nb[2], 152 * 4);
             if (numeric)
                 { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
+                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
+                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
         }
         if (nb[3] > 0) {
             if (numeric)
                 { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, Cm.rp(), Cm.ci(), Cm.v(),
+                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, nullptr, nullptr, nullptr,
+                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
         }
         AMG_CHECK_LAUNCH();
     };
-    launch(false);
-    int64_t nnz = exclusive_scan_i32(cnt.as<int32_t>(), Cm.rp(), n, s);
+    // one numeric pass into slots sized by each row's product bound, then a
+    // compaction -- unless the bound does not fit: then count first (symbolic)
+    TmpBuf obase(sizeof(int64_t) * (n + 1), s);
+    int64_t total_ub = exclusive_scan_i64(ub.as<int64_t>(), obase.as<int64_t>(), n, s);
+    size_t fr = 0, tot = 0;
+    AMG_CUDA(cudaMemGetInfo(&fr, &tot));
+    // AMG_SPGEMM_TWO_PASS=1 forces the counting path (it is otherwise taken
+    // only when the product bound would not fit in free memory)
+    const char *force = std::getenv("AMG_SPGEMM_TWO_PASS");
+    bool one_pass = (double)total_ub * 12.0 < 0.4 * (double)fr && !(force && force[0] == '1');
+    int64_t nnz;
+    if (one_pass) {
+        TmpBuf tci(sizeof(int32_t) * (total_ub + kPad), s), tv(sizeof(double) * (total_ub + kPad), s);
+        launch(true, obase.as<int64_t>(), tci.as<int32_t>(), tv.as<double>());
+        nnz = exclusive_scan_i32(cnt.as<int32_t>(), Cm.rp(), n, s);
+        require(nnz < ((int64_t)1 << 31), "spgemm: product has 2^31 or more entries");
+        Cm.nnz = nnz;
+        Cm.col.alloc(sizeof(int32_t) * (nnz + kPad));
+        Cm.val.alloc(sizeof(double) * (nnz + kPad));
+        AMG_CUDA(cudaMemsetAsync(Cm.col.ptr, 0, Cm.col.bytes, s));
+        AMG_CUDA(cudaMemsetAsync(Cm.val.ptr, 0, Cm.val.bytes, s));
+        { spgemm_compact_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(n, obase.as<int64_t>(), Cm.rp(), tci.as<int32_t>(), tv.as<double>(), Cm.ci(), Cm.v()); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+        return;  // the temporaries' stream-ordered frees follow the compaction
+    }
+    launch(false, nullptr, nullptr, nullptr);
+    nnz = exclusive_scan_i32(cnt.as<int32_t>(), Cm.rp(), n, s);
     require(nnz < ((int64_t)1 << 31), "spgemm: product has 2^31 or more entries");
     Cm.nnz = nnz;
     Cm.col.alloc(sizeof(int32_t) * (nnz + kPad));
     Cm.val.alloc(sizeof(double) * (nnz + kPad));
     AMG_CUDA(cudaMemsetAsync(Cm.col.ptr, 0, Cm.col.bytes, s));
     AMG_CUDA(cudaMemsetAsync(Cm.val.ptr, 0, Cm.val.bytes, s));
-    launch(true);
+    exclusive_scan_i64_from_i32(cnt.as<int32_t>(), obase.as<int64_t>(), n, s);
+    launch(true, obase.as<int64_t>(), Cm.ci(), Cm.v());
 }
 
 void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, uint8_t *inM,

@@ -190,5 +190,8 @@ int64_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStrea
 int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s) {
     return scan_impl<int64_t, int64_t>(in, out, n, s);
 }
+int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
+    return scan_impl<int32_t, int64_t>(in, out, n, s);
+}
 
 }  // namespace amg

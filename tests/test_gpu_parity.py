@@ -62,6 +62,18 @@ def test_setup_end_to_end_matches_oracle(amg, case):
         np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14)
 
 
+def test_setup_two_pass_spgemm_matches_oracle(amg, monkeypatch):
+    """The counting (two-pass) SpGEMM, used when product bounds do not fit in
+    memory, gives the same hierarchy."""
+    monkeypatch.setenv("AMG_SPGEMM_TWO_PASS", "1")
+    A = CASES["3d27_11"]()
+    ref = oracle.Hierarchy(A)
+    h = amg.Hierarchy.setup(A)
+    assert h.num_levels == ref.num_levels
+    for l in range(h.num_levels):
+        _same_csr(h.export(l, "A"), ref.matrix(l, "A"), what=f"A_{l}")
+
+
 @pytest.mark.parametrize("gamma", [0.01, 0.1, 1.0])
 @pytest.mark.parametrize("case", ["2d5_64", "3d7_20", "fv7_15"])
 def test_sparsify_end_to_end_matches_oracle(amg, case, gamma):
