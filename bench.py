@@ -205,6 +205,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 KIND_NAMES = {0: "relax_pre_residual", 1: "restrict", 2: "prolong", 3: "relax_post", 4: "coarse_solve",
               5: "pcg_Ap_dot", 6: "pcg_vector"}
+SETUP_KIND_NAMES = {8: "strength", 9: "cf_split", 10: "interpolation", 11: "galerkin_spgemm",
+                    12: "level_maps_minimal_pattern", 13: "sparsify", 14: "cycle_prep", 15: "coarse_cholesky"}
 
 
 def aggregate_replicas(elapsed_s: float, steps: int, dist=None, device=None):
@@ -229,6 +231,21 @@ def collect_timing(h, nlev):
             if n:
                 rows.append({"kind": KIND_NAMES[kind], "level": l, "launches": n, "ms": ms, "bytes": by})
     return rows
+
+
+def _median_phases(runs):
+    if not runs:
+        return None
+    return {k: round(statistics.median(r[k] for r in runs), 3) for k in runs[0]}
+
+
+def collect_setup_timing(h, nlev):
+    """Setup phase -> milliseconds summed over levels (event spans on the setup stream)."""
+    out = {}
+    for kind, name in SETUP_KIND_NAMES.items():
+        ms = sum(h.timing_get(kind, l)[1] for l in range(nlev))
+        out[name] = round(ms, 3)
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -415,11 +432,16 @@ def main():
     torch.cuda.synchronize()
 
     def step(timing=False):
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0 if args.eager else 1)
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0 if args.eager else 1,
+                                setup_timing=1 if timing else 0)
         if timing:
+            setup_phases.append(collect_setup_timing(h, h.num_levels))
+            h.timing_reset()
             h.timing_enable(True)
         x, info = h.solve(bd, xd, tol=args.tol)
         return h, info
+
+    setup_phases = []
 
     if args.ncu_solve:
         h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
@@ -582,7 +604,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
         "iterations": statistics.median(its), "levels": levels,
         "roofline": roofline, "vcycle_GBps": vcycle_bytes / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms else None,
-        "top_kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "clocks": clocks,
+        "top_kernels": kernels, "setup_phases_ms": _median_phases(setup_phases), "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "clocks": clocks,
         "gpu_launches": launches,
     }
     print(json.dumps(line))

@@ -88,6 +88,8 @@ typedef struct {
     int spmv_variant;    /* AMG_SPMV_AUTO (autotuned per level) or forced */
     int use_graph;       /* capture the PCG iteration in a CUDA graph, default 1 */
     int check_every;     /* PCG iterations between host stop tests, default 1 */
+    int setup_timing;    /* 1: time the setup phases with events (amg_timing_get
+                            kinds 8..15), default 0 */
 } amg_options;
 
 typedef struct {
@@ -209,7 +211,16 @@ amg_status amg_level_array(const amg_hierarchy *h, int level, int which, void *o
  * amg_timing_get returns, for kernel class `kind` (0 fused pre-smooth +
  * residual, 1 restrict, 2 prolong, 3 post-smooth, 4 coarse solve, 5 PCG
  * A p + dot, 6 PCG vector update) on `level`, the number of timed launches,
- * their total milliseconds and their algorithmic bytes. */
+ * their total milliseconds and their algorithmic bytes.  With
+ * amg_options.setup_timing, or while timing is enabled during amg_sparsify /
+ * amg_reintroduce, the setup phases are recorded too (bytes 0): 8 strength,
+ * 9 C/F splitting (PMIS and the coarse numbering), 10 interpolation P and
+ * R = P^T, 11 Galerkin products A P and R (A P), 12 level maps of the new
+ * level (diagonal and transpose positions) and its minimal pattern M,
+ * 13 sparsification (Algorithm 3 / 3b), 14 cycle preparation (ell1
+ * diagonal, precision copies, SELL layout, autotuning), 15 coarsest-level
+ * Cholesky inverse.  Kinds 8..12 are filed under the fine level l of the
+ * step that builds level l + 1. */
 amg_status amg_timing_enable(amg_hierarchy *h, int on);
 amg_status amg_timing_get(const amg_hierarchy *h, int kind, int level, int64_t *launches,
                           double *total_ms, double *bytes);

@@ -47,7 +47,8 @@ class Options(C.Structure):
                 ("seed", C.c_uint64), ("method", C.c_int), ("precision", C.c_int),
                 ("k_check", C.c_int), ("s_levels", C.c_int), ("gamma_min", C.c_double),
                 ("rho_max", C.c_double), ("level_offset", C.c_int), ("spmv_variant", C.c_int),
-                ("use_graph", C.c_int), ("check_every", C.c_int)]
+                ("use_graph", C.c_int), ("check_every", C.c_int),
+                ("setup_timing", C.c_int)]
 
 
 class SolveInfo(C.Structure):

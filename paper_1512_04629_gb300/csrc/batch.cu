@@ -185,12 +185,14 @@ col_finish_kernel(int nblocks, const double *partials, ColScalars sc, int flexib
     }
 }
 
+// at least four rows per thread and at most one resident wave of blocks
 int grid_for(int64_t n, int K) {
     int64_t rows_per_block = kThreads / K;
     int64_t b = (n + rows_per_block - 1) / rows_per_block;
-    b = (b + 3) / 4;  // about four rows per thread
+    b = (b + 3) / 4;
+    int64_t cap = std::min<int64_t>(kBatchReduceBlocks, ::amg::resident_blocks(kThreads));
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
-    if (b > kBatchReduceBlocks) b = kBatchReduceBlocks;
     return (int)b;
 }
 
@@ -374,7 +376,8 @@ static void launch_ap(const CycMat<double> &A, int K, const double *P, const dou
     auto grid = [&](int G) {
         int64_t rpb = kThreads / G;
         int64_t b = ((n + rpb - 1) / rpb + 3) / 4;
-        return (int)std::max<int64_t>(1, std::min<int64_t>(b, kBatchReduceBlocks));
+        int64_t cap = std::min<int64_t>(kBatchReduceBlocks, ::amg::resident_blocks(kThreads));
+        return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
     };
     (void)counter;
     int blocks = 0;

@@ -121,6 +121,10 @@ void finish_setup(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s
     prepare_cycle(h, s, all);
     ensure_workspace(h, s);
     AMG_CUDA(cudaStreamSynchronize(s));
+    if (h.opt.setup_timing) {  // setup phases were timed; the solve timing stays opt-in
+        timing_collect(h);
+        h.timing = false;
+    }
 }
 
 }  // namespace
@@ -162,6 +166,7 @@ amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_
         Hierarchy &h = H->h;
         h.opt = o;
         AMG_CUDA(cudaGetDevice(&h.device));
+        h.timing = o.setup_timing != 0;
         h.lev.push_back(std::make_unique<Level>());
         upload_csr(A, h.lev[0]->A, s);
         build_galerkin(h, h.lev[0]->A, s);

@@ -25,6 +25,9 @@ void set_last_error(const std::string &msg);
 
 // number of kernels the library has launched (diagnostic counter)
 void count_launch();
+// thread blocks of the given size that fit on the current device at once
+// (SM count x resident blocks per SM at full thread occupancy), cached
+int resident_blocks(int threads_per_block);
 
 #define AMG_CUDA(call)                                                                     \
     do {                                                                                   \

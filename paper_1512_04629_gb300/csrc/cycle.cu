@@ -321,10 +321,15 @@ void launch_finish(int nblocks, Reduce red, PcgScalars *sc, cudaStream_t s,
     { finish_kernel<NV, FIN><<<1, kFinThreads, 0, s>>>(nblocks, red, sc, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
 }
 
-int reduce_blocks(int64_t n, int per_thread = 1) {
-    int64_t b = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
-    if (b < 1) b = 1;
+// Grid of a reducing kernel: at most one resident wave, so every thread
+// loops over several rows and the shuffle tree of the block reduction (FP64
+// adds, the scarce pipe on this part) runs once per thread, not once per row.
+int reduce_blocks(int64_t threads_needed) {
+    int64_t b = (threads_needed + kThreads - 1) / kThreads;
+    int64_t cap = ::amg::resident_blocks(kThreads);
+    if (b > cap) b = cap;
     if (b > kMaxReduceBlocks) b = kMaxReduceBlocks;
+    if (b < 1) b = 1;
     return (int)b;
 }
 static_assert(kThreads == 256, "two-level reduction assumes groups of 256 blocks and 256 threads");
@@ -339,16 +344,21 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
     p[i] = z[i] + sc->beta * p[i];
 }
 
-// q = A p (SELL-32, one thread per row) and p . q
+// q = A p (SELL-32, one thread per row) and p . q; each warp walks slices
+// with a stride of the grid's warp count
 __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                const int32_t *__restrict__ sci, const double *__restrict__ sv, const double *__restrict__ p,
                double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
     double part[1] = {0.0};
-    for (int64_t pos = (int64_t)blockIdx.x * kThreads + threadIdx.x; pos < n; pos += (int64_t)gridDim.x * kThreads) {
-        const int32_t i = perm ? __ldg(perm + pos) : (int32_t)pos;
-        double s = sell_row_sum<double, double>((int32_t)pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
+    const int lane = threadIdx.x & 31;
+    const int32_t nsl = (n + 31) >> 5, nwarps = (int32_t)((gridDim.x * kThreads) >> 5);
+    for (int32_t sl = (int32_t)((blockIdx.x * kThreads + threadIdx.x) >> 5); sl < nsl; sl += nwarps) {
+        const int32_t pos = sl * 32 + lane;
+        if (pos >= n) continue;
+        const int32_t i = perm ? __ldg(perm + pos) : pos;
+        double s = sell_row_sum<double, double>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
         q[i] = s;
         part[0] += p[i] * s;
     }
@@ -438,19 +448,22 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                    double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
-    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t i = (int32_t)(g / T);
-    int t = (int)(g % T);
-    int32_t p0 = 0, p1 = 0;
-    if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-    double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
     double part[2] = {0.0, 0.0};
-    if (i < n && t == 0) {
-        double bi = b[i];
-        double zi = x[i] + dinv[i] * (bi - s);
-        z[i] = zi;
-        part[0] = bi * zi;
-        part[1] = zi * q[i];
+    const int64_t stride = (int64_t)gridDim.x * kThreads;
+    const int64_t gend = (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T;
+    for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < gend; g += stride) {
+        const int32_t i = (int32_t)(g / T);
+        const int t = (int)(g % T);
+        int32_t p0 = 0, p1 = 0;
+        if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        if (i < n && t == 0) {
+            double bi = b[i];
+            double zi = x[i] + dinv[i] * (bi - s);
+            z[i] = zi;
+            part[0] += bi * zi;
+            part[1] += zi * q[i];
+        }
     }
     block_partials<2>(part, red);
 }
@@ -461,16 +474,19 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
                     const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                     double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
-    int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     double part[2] = {0.0, 0.0};
-    if (pos < n) {
+    const int lane = threadIdx.x & 31;
+    const int32_t nsl = (n + 31) >> 5, nwarps = (int32_t)((gridDim.x * kThreads) >> 5);
+    for (int32_t sl = (int32_t)((blockIdx.x * kThreads + threadIdx.x) >> 5); sl < nsl; sl += nwarps) {
+        const int32_t pos = sl * 32 + lane;
+        if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
         double s = sell_row_sum<double, double>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
         double bi = b[i];
         double zi = x[i] + dinv[i] * (bi - s);
         z[i] = zi;
-        part[0] = bi * zi;
-        part[1] = zi * q[i];
+        part[0] += bi * zi;
+        part[1] += zi * q[i];
     }
     block_partials<2>(part, red);
 }
@@ -652,14 +668,14 @@ void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, c
 
 template <int T>
 static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
-    int blocks = reduce_blocks((int64_t)A.nrows * T, 1);
+    int blocks = reduce_blocks((int64_t)A.nrows * T);
     { ap_kernel<T><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, p, q, sc, red); ::amg::count_launch(); }
     launch_finish<1, kFinAp>(blocks, red, sc, s);
 }
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        int blocks = reduce_blocks(A.nrows, 1);
+        int blocks = reduce_blocks(A.nrows);
         { ap_sell_kernel<<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
@@ -678,7 +694,7 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
                    double *x0, cudaStream_t s) {
-    int blocks = reduce_blocks(n, 1);
+    int blocks = reduce_blocks(n);
     { xr_update_kernel<<<blocks, kThreads, 0, s>>>(n, p, q, x, r, sc, red, dinv0, x0); ::amg::count_launch(); }
     launch_finish<1, kFinXr>(blocks, red, sc, s, handle, use_handle);
     AMG_CHECK_LAUNCH();
@@ -689,32 +705,30 @@ bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, c
     int32_t n = A.nrows;
     if (n == 0) return false;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        int blocks = div_up(n, kThreads);
-        if (blocks > kMaxReduceBlocks) return false;
+        int blocks = reduce_blocks(n);
         { post_rz_sell_kernel<<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
         launch_finish<2, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return true;
     }
     int T = threads_per_row(A.variant);
-    int64_t blocks = ((int64_t)n * T + kThreads - 1) / kThreads;
-    if (blocks > kMaxReduceBlocks) return false;
+    int blocks = reduce_blocks((int64_t)n * T);
     switch (T) {
-        case 1: { post_rz_csr_kernel<1><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 2: { post_rz_csr_kernel<2><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 4: { post_rz_csr_kernel<4><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 8: { post_rz_csr_kernel<8><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 16: { post_rz_csr_kernel<16><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        default: { post_rz_csr_kernel<32><<<(int)blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 1: { post_rz_csr_kernel<1><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 2: { post_rz_csr_kernel<2><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 4: { post_rz_csr_kernel<4><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 8: { post_rz_csr_kernel<8><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 16: { post_rz_csr_kernel<16><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        default: { post_rz_csr_kernel<32><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
     }
-    launch_finish<2, kFinRz>((int)blocks, red, sc, s);
+    launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
     return true;
 }
 
 void to_f64_rz(int32_t n, const float *z32, double *z, const double *r, const double *q, PcgScalars *sc, Reduce red,
                cudaStream_t s) {
-    int blocks = reduce_blocks(n, 1);
+    int blocks = reduce_blocks(n);
     { to_f64_rz_kernel<<<blocks, kThreads, 0, s>>>(n, z32, z, r, q, sc, red); ::amg::count_launch(); }
     launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
@@ -736,7 +750,7 @@ void to_f32_scaled(int64_t n, const double *src, const float *d, float *dst, flo
 
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
             cudaStream_t s) {
-    int blocks = reduce_blocks(n, 1);
+    int blocks = reduce_blocks(n);
     { rz_kernel<<<blocks, kThreads, 0, s>>>(n, r, z, q, sc, red); ::amg::count_launch(); }
     launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
@@ -744,7 +758,7 @@ void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgSca
 
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s) {
-    int blocks = reduce_blocks((int64_t)A.nrows * 4, 1);
+    int blocks = reduce_blocks((int64_t)A.nrows * 4);
     { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
     launch_finish<1, kFinTt>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();

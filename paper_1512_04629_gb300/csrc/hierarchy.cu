@@ -31,6 +31,46 @@ Hierarchy::~Hierarchy() {
 // product, and the minimal-pattern flags of each coarse operator.
 // Stop: n_l <= max_size, max_levels reached, or |C| = 0 or |C| > 0.9 n_l.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// per-kernel timing with events on the launching stream
+// ---------------------------------------------------------------------------
+static cudaEvent_t get_event(Hierarchy &h) {
+    if (!h.event_pool.empty()) {
+        cudaEvent_t e = h.event_pool.back();
+        h.event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    AMG_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+template <class F> static void timed(Hierarchy &h, int kind, int level, double bytes, cudaStream_t s, F &&f) {
+    if (!h.timing) { f(); return; }
+    PendingEvent pe{kind, level, bytes, get_event(h), get_event(h)};
+    AMG_CUDA(cudaEventRecord(pe.a, s));
+    f();
+    AMG_CUDA(cudaEventRecord(pe.b, s));
+    h.pending.push_back(pe);
+}
+
+void timing_collect(Hierarchy &h) {
+    for (auto &pe : h.pending) {
+        AMG_CUDA(cudaEventSynchronize(pe.b));
+        float ms = 0.f;
+        AMG_CUDA(cudaEventElapsedTime(&ms, pe.a, pe.b));
+        if (pe.kind >= 0 && pe.kind < kTimingKinds && pe.level >= 0 && pe.level < kMaxLevels) {
+            Timing &t = h.timers[pe.kind][pe.level];
+            t.launches++;
+            t.ms += ms;
+            t.bytes += pe.bytes;
+        }
+        h.event_pool.push_back(pe.a);
+        h.event_pool.push_back(pe.b);
+    }
+    h.pending.clear();
+}
+
 static void init_level_maps(Level &V, cudaStream_t s) {
     V.diagpos.alloc(sizeof(int32_t) * (V.A.nrows + 1));
     V.tpos.alloc(sizeof(int32_t) * (V.A.nnz + 1));
@@ -44,14 +84,17 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
     const amg_options &o = h.opt;
     for (int l = 0;; ++l) {
         Level &V = *h.lev[l];
-        if (l == 0) init_level_maps(V, s);
+        if (l == 0) timed(h, 12, 0, 0.0, s, [&] { init_level_maps(V, s); });
         int32_t n = V.A.nrows;
         if (n <= o.max_size || l + 1 >= o.max_levels) break;
         V.strong.alloc(V.A.nnz + kPad);
         V.cf.alloc(n + kPad);
-        setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s);
-        int64_t nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed,
-                                 o.level_offset + l, V.cf.as<int8_t>(), s);
+        timed(h, 8, l, 0.0, s, [&] { setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s); });
+        int64_t nc = 0;
+        timed(h, 9, l, 0.0, s, [&] {
+            nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed, o.level_offset + l,
+                             V.cf.as<int8_t>(), s);
+        });
         if (nc == 0 || (double)nc > 0.9 * (double)n) {
             V.strong.release();
             V.cf.release();
@@ -59,17 +102,25 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
         }
         V.cmap.alloc(sizeof(int32_t) * (n + 1));
         V.cpts.alloc(sizeof(int32_t) * (nc + 1));
-        setup::coarse_map(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
-        setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
-                             (int32_t)nc, V.P, s);
-        setup::transpose(V.P, V.R, s);
+        timed(h, 9, l, 0.0, s, [&] {
+            setup::coarse_map(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
+        });
+        timed(h, 10, l, 0.0, s, [&] {
+            setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
+                                 (int32_t)nc, V.P, s);
+            setup::transpose(V.P, V.R, s);
+        });
         DevCSR AP;
-        setup::spgemm(V.A, V.P, AP, s);
         auto C = std::make_unique<Level>();
-        setup::spgemm(V.R, AP, C->A, s);
-        init_level_maps(*C, s);
-        C->inM.alloc(C->A.nnz + kPad);
-        setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+        timed(h, 11, l, 0.0, s, [&] {
+            setup::spgemm(V.A, V.P, AP, s);
+            setup::spgemm(V.R, AP, C->A, s);
+        });
+        timed(h, 12, l, 0.0, s, [&] {
+            init_level_maps(*C, s);
+            C->inM.alloc(C->A.nnz + kPad);
+            setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+        });
         h.lev.push_back(std::move(C));
     }
 }
@@ -147,7 +198,7 @@ void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s
         double g = 0.0;
         if (l > 0 && n_gamma > 0 && gamma) g = gamma[std::min(l, n_gamma - 1)];
         h.lev[l]->gamma = g;
-        resparsify_level(h, l, s);
+        timed(h, 13, l, 0.0, s, [&] { resparsify_level(h, l, s); });
     }
 }
 
@@ -164,7 +215,7 @@ int reintroduce(Hierarchy &h, int s_levels, cudaStream_t s) {
     for (int l = lstart; l < lstart + s_levels && l < L; ++l) {
         double g = h.lev[l]->gamma / 10.0;
         h.lev[l]->gamma = (g >= h.opt.gamma_min * (1.0 - 1e-12)) ? g : 0.0;
-        resparsify_level(h, l, s);
+        timed(h, 13, l, 0.0, s, [&] { resparsify_level(h, l, s); });
         changed.push_back(l);
     }
     prepare_cycle(h, s, changed);
@@ -378,11 +429,15 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
         cyc::sell_fill<double>(M.nrows, M.rp(), M.ci(), M.v(), V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
                                V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sci.as<int32_t>(), V.sv64.as<double>(), s);
     }
-    if (l == h.nlev() - 1) {
-        h.coarse_n = n;
-        h.coarse_inv.alloc(sizeof(double) * ((size_t)n * n + kPad));
-        setup::cholesky_inverse(M, h.coarse_inv.as<double>(), s);
-    }
+}
+
+static void prepare_coarse(Hierarchy &h, cudaStream_t s) {
+    Level &V = *h.lev[h.nlev() - 1];
+    const DevCSR &M = V.op();
+    int32_t n = V.n();
+    h.coarse_n = n;
+    h.coarse_inv.alloc(sizeof(double) * ((size_t)n * n + kPad));
+    setup::cholesky_inverse(M, h.coarse_inv.as<double>(), s);
 }
 
 // Transfer operators: time prolongation (x += P x_c) and restriction
@@ -440,12 +495,17 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
 }
 
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
-    for (int l : levels) prepare_level(h, l, s);
+    for (int l : levels) {
+        timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, s); });
+        if (l == h.nlev() - 1) timed(h, 15, l, 0.0, s, [&] { prepare_coarse(h, s); });
+    }
     if (h.opt.spmv_variant == AMG_SPMV_AUTO) {
         for (int l : levels) {
             if (l + 1 >= h.nlev() || h.lev[l]->pr_tuned) continue;
-            if (h.opt.precision == AMG_PREC_FP64) autotune_transfers<double>(h, l, s);
-            else autotune_transfers<float>(h, l, s);
+            timed(h, 14, l, 0.0, s, [&] {
+                if (h.opt.precision == AMG_PREC_FP64) autotune_transfers<double>(h, l, s);
+                else autotune_transfers<float>(h, l, s);
+            });
             h.lev[l]->pr_tuned = true;
         }
     }
@@ -496,46 +556,6 @@ double level_cycle_bytes(const Hierarchy &h, int l) {
     b += (l + 2 < h.nlev() ? bytes_restrict_x(V.R.nrows, n, V.R.nnz, xb, xb) : bytes_restrict(V.R.nrows, n, V.R.nnz, xb, xb)) +
          bytes_prolong(n, V.P.ncols, V.P.nnz, xb, xb);
     return b;
-}
-
-// ---------------------------------------------------------------------------
-// per-kernel timing with events on the launching stream
-// ---------------------------------------------------------------------------
-static cudaEvent_t get_event(Hierarchy &h) {
-    if (!h.event_pool.empty()) {
-        cudaEvent_t e = h.event_pool.back();
-        h.event_pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e;
-    AMG_CUDA(cudaEventCreate(&e));
-    return e;
-}
-
-template <class F> static void timed(Hierarchy &h, int kind, int level, double bytes, cudaStream_t s, F &&f) {
-    if (!h.timing) { f(); return; }
-    PendingEvent pe{kind, level, bytes, get_event(h), get_event(h)};
-    AMG_CUDA(cudaEventRecord(pe.a, s));
-    f();
-    AMG_CUDA(cudaEventRecord(pe.b, s));
-    h.pending.push_back(pe);
-}
-
-void timing_collect(Hierarchy &h) {
-    for (auto &pe : h.pending) {
-        AMG_CUDA(cudaEventSynchronize(pe.b));
-        float ms = 0.f;
-        AMG_CUDA(cudaEventElapsedTime(&ms, pe.a, pe.b));
-        if (pe.kind >= 0 && pe.kind < kTimingKinds && pe.level >= 0 && pe.level < kMaxLevels) {
-            Timing &t = h.timers[pe.kind][pe.level];
-            t.launches++;
-            t.ms += ms;
-            t.bytes += pe.bytes;
-        }
-        h.event_pool.push_back(pe.a);
-        h.event_pool.push_back(pe.b);
-    }
-    h.pending.clear();
 }
 
 // ---------------------------------------------------------------------------

@@ -53,7 +53,7 @@ struct Timing {
     double ms = 0.0;
     double bytes = 0.0;
 };
-constexpr int kTimingKinds = 8;
+constexpr int kTimingKinds = 16;
 constexpr int kMaxLevels = 64;
 
 struct PendingEvent {

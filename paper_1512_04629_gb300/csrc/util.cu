@@ -13,6 +13,19 @@ std::atomic<int64_t> g_launches{0};
 
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int resident_blocks(int threads_per_block) {
+    static std::atomic<int> sm_count[64];
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    int sms = dev < 64 ? sm_count[dev].load(std::memory_order_relaxed) : 0;
+    if (sms == 0) {
+        AMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (dev < 64) sm_count[dev].store(sms, std::memory_order_relaxed);
+    }
+    int per_sm = 2048 / threads_per_block;
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
 const char *last_error_cstr() { return g_last_error.c_str(); }
 
 void DevBuf::alloc(size_t b) {

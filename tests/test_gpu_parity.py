@@ -249,6 +249,30 @@ def test_timing_counters(amg):
     assert h.timing_get(amg.K_PRE, 0)[0] == 0
 
 
+def test_setup_phase_timing(amg):
+    """setup_timing records every setup phase and changes nothing in the result."""
+    A = gen.poisson3d_7pt(20)
+    h0 = amg.Hierarchy.setup(A, gamma=[0.0, 0.1])
+    h1 = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], setup_timing=1)
+    L = h1.num_levels
+    assert L == h0.num_levels and L >= 3
+    for kind in (8, 9, 10, 11, 12):
+        for l in range(L - 1):
+            n, ms, by = h1.timing_get(kind, l)
+            assert n >= 1 and ms > 0 and by == 0, (kind, l)
+    for l in range(1, L):
+        assert h1.timing_get(13, l)[0] == 1
+    for l in range(L):
+        assert h1.timing_get(14, l)[0] >= 1
+    assert h1.timing_get(15, L - 1)[0] == 1
+    for l in range(L):
+        for which in ("A", "Ahat"):
+            _same_csr(h1.export(l, which), h0.export(l, which), rtol=0.0, what=f"{which}_{l}")
+    # solve-phase timing stays off unless asked for
+    h1.solve(gen.rhs_uniform(A.n, 1))
+    assert h1.timing_get(amg.K_PRE, 0)[0] == 0
+
+
 def test_single_level_and_zero_rhs(amg):
     A = gen.poisson2d_5pt(9)
     h = amg.Hierarchy.setup(A, max_size=1000)
