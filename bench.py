@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=20.0)
     p.add_argument("--eager", action="store_true",
                    help="launch the PCG iterations one kernel at a time (no CUDA graph; for ncu launch lists)")
+    p.add_argument("--ncu-setup", action="store_true",
+                   help="profiling aid: one warm-up setup, then one setup between cudaProfilerStart/Stop")
     p.add_argument("--ncu-solve", action="store_true",
                    help="set up once, then run one solve between cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return p.parse_args()
@@ -442,6 +444,17 @@ def main():
         return h, info
 
     setup_phases = []
+
+    if args.ncu_setup:
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
+        del h
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"ncu_setup": True, "levels": h.num_levels}))
+        return
 
     if args.ncu_solve:
         h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)

@@ -125,6 +125,8 @@ inline int div_up(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / 
 int64_t exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// the same without reading back: out[n] and *total (device) are written on the stream
+void exclusive_scan_i64_async(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s);
 
 template <typename T> T read_scalar(const T *dptr, cudaStream_t s) {
     T v;

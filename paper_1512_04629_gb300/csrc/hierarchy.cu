@@ -74,8 +74,7 @@ void timing_collect(Hierarchy &h) {
 static void init_level_maps(Level &V, cudaStream_t s) {
     V.diagpos.alloc(sizeof(int32_t) * (V.A.nrows + 1));
     V.tpos.alloc(sizeof(int32_t) * (V.A.nnz + 1));
-    setup::validate(V.A, V.diagpos.as<int32_t>(), s);
-    setup::transpose_positions(V.A, V.tpos.as<int32_t>(), s);
+    setup::level_maps(V.A, V.diagpos.as<int32_t>(), V.tpos.as<int32_t>(), s);
     V.keep.alloc(V.A.nnz + kPad);
 }
 
@@ -89,21 +88,22 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
         if (n <= o.max_size || l + 1 >= o.max_levels) break;
         V.strong.alloc(V.A.nnz + kPad);
         V.cf.alloc(n + kPad);
+        V.cmap.alloc(sizeof(int32_t) * (n + 1));
         timed(h, 8, l, 0.0, s, [&] { setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s); });
         int64_t nc = 0;
         timed(h, 9, l, 0.0, s, [&] {
             nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed, o.level_offset + l,
-                             V.cf.as<int8_t>(), s);
+                             V.cf.as<int8_t>(), V.cmap.as<int32_t>(), s);
         });
         if (nc == 0 || (double)nc > 0.9 * (double)n) {
             V.strong.release();
             V.cf.release();
+            V.cmap.release();
             break;
         }
-        V.cmap.alloc(sizeof(int32_t) * (n + 1));
         V.cpts.alloc(sizeof(int32_t) * (nc + 1));
         timed(h, 9, l, 0.0, s, [&] {
-            setup::coarse_map(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
+            setup::coarse_points(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
         });
         timed(h, 10, l, 0.0, s, [&] {
             setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
@@ -138,6 +138,7 @@ void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &
             require(P[l].nrows == V->A.nrows && P[l].ncols == A[l + 1].nrows,
                     "assemble: P_l must be n_l x n_{l+1}");
             V->P = std::move(P[l]);
+            setup::validate_rect(V->P, "interpolation operator", s);
             setup::transpose(V->P, V->R, s);
             require((int64_t)cf[l].size() == V->A.nrows, "assemble: cf_l has the wrong length");
             V->cf.alloc(V->A.nrows + kPad);
@@ -168,7 +169,7 @@ static const uint8_t *hybrid_pattern(Hierarchy &h, int l, cudaStream_t s) {
         int64_t nc = F.P.ncols;
         F.cmap.alloc(sizeof(int32_t) * (F.n() + 1));
         F.cpts.alloc(sizeof(int32_t) * (nc + 1));
-        setup::coarse_map(F.cf.as<int8_t>(), F.n(), F.cmap.as<int32_t>(), F.cpts.as<int32_t>(), s);
+        setup::coarse_map(F.cf.as<int8_t>(), F.n(), F.cmap.as<int32_t>(), F.cpts.as<int32_t>(), nc, s);
     }
     DevCSR APh;
     setup::spgemm(F.op(), F.P, APh, s);

@@ -7,6 +7,7 @@
 // (one thread per row, or one ordered accumulator per output entry), so the
 // setup is deterministic and repeatable run to run.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdlib>
 
@@ -37,16 +38,27 @@ __device__ __forceinline__ bool contains(const int32_t *a, int32_t lo, int32_t h
 // ---------------------------------------------------------------------------
 // validation and structural maps
 // ---------------------------------------------------------------------------
-enum : int { kBadCol = 1, kUnsorted = 2, kNoDiag = 4, kBadDiag = 8, kNonFinite = 16, kAsym = 32 };
+enum : int { kBadCol = 1, kUnsorted = 2, kNoDiag = 4, kBadDiag = 8, kNonFinite = 16, kAsym = 32, kBadRowptr = 64 };
 
-__global__ void validate_kernel(int32_t n, int32_t ncols, const int32_t *rp, const int32_t *ci,
+// Every row range is checked against [0, nnz] before its entries are read,
+// so the kernel stays in bounds on any row-pointer array.
+__device__ __forceinline__ bool row_in_bounds(int32_t p0, int32_t p1, int64_t nnz) {
+    return p0 >= 0 && p0 <= p1 && (int64_t)p1 <= nnz;
+}
+
+__global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int32_t *rp, const int32_t *ci,
                                 const double *v, int32_t *diagpos, int *err) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int e = 0;
     int32_t dp = -1, prev = -1;
     int32_t p0 = rp[i], p1 = rp[i + 1];
-    if (p1 < p0) e |= kUnsorted;
+    if ((i == 0 && p0 != 0) || (i == n - 1 && (int64_t)p1 != nnz)) e |= kBadRowptr;
+    if (!row_in_bounds(p0, p1, nnz)) {
+        diagpos[i] = -1;
+        atomicOr(err, e | kBadRowptr);
+        return;
+    }
     for (int32_t p = p0; p < p1; ++p) {
         int32_t j = ci[p];
         if (j < 0 || j >= ncols) { e |= kBadCol; continue; }
@@ -61,13 +73,18 @@ __global__ void validate_kernel(int32_t n, int32_t ncols, const int32_t *rp, con
     if (e) atomicOr(err, e);
 }
 
-__global__ void tpos_kernel(int32_t n, const int32_t *rp, const int32_t *ci, int32_t *tpos,
+__global__ void tpos_kernel(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *tpos,
                             int *err) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const int32_t p0 = rp[i], p1 = rp[i + 1];
+    if (!row_in_bounds(p0, p1, nnz)) { atomicOr(err, (int)kBadRowptr); return; }
+    for (int32_t p = p0; p < p1; ++p) {
         int32_t j = ci[p];
-        int32_t q = lower_bound_i32(ci, rp[j], rp[j + 1], i);
+        if (j < 0 || j >= n) { tpos[p] = p; atomicOr(err, (int)kBadCol); continue; }  // reported, not followed
+        const int32_t q0 = rp[j], q1 = rp[j + 1];
+        if (!row_in_bounds(q0, q1, nnz)) { tpos[p] = p; atomicOr(err, (int)kBadRowptr); continue; }
+        int32_t q = lower_bound_i32(ci, q0, q1, i);
         if (q < rp[j + 1] && ci[q] == i) tpos[p] = q;
         else { tpos[p] = p; atomicOr(err, (int)kAsym); }
     }
@@ -123,9 +140,13 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
     if (threadIdx.x == 0 && add) atomicAdd(undecided, add);
 }
 
+// Rounds are launched in batches without reading back in between: every
+// round kernel first reads the undecided count the previous round left and
+// does nothing once it is zero.
 __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                    const int32_t *tpos, const uint8_t *strong, const double *w,
-                                   const int8_t *state, uint8_t *newc) {
+                                   const int8_t *state, uint8_t *newc, const int *prev) {
+    if (*prev == 0) return;
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint8_t win = 0;
@@ -143,13 +164,15 @@ __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *
     newc[i] = win;
 }
 
-__global__ void pmis_apply_c_kernel(int32_t n, const uint8_t *newc, int8_t *state) {
+__global__ void pmis_apply_c_kernel(int32_t n, const uint8_t *newc, int8_t *state, const int *prev) {
+    if (*prev == 0) return;
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && newc[i]) state[i] = kC;
 }
 
 __global__ void pmis_apply_f_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                    const uint8_t *strong, int8_t *state, int *undecided) {
+                                    const uint8_t *strong, int8_t *state, const int *prev, int *undecided) {
+    if (*prev == 0) return;
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int still = 0;
     if (i < n && state[i] == kU) {
@@ -397,74 +420,213 @@ __global__ void spgemm_ub_kernel(int32_t n, const int32_t *arp, const int32_t *a
 }
 
 constexpr int kBlockHS = 8192, kBlockUmax = 4096, kBlockThreads = 256;
-constexpr int kTinyUmax = 64, kTinyWarps = 8;     // bin 0: <= 64 products per row
-constexpr int kSmallUmax = 512, kSmallWarps = 4;  // bin 1: <= 512 products per row
+// Row bins by product bound: three register-sort widths (one row per 8, 16
+// or 32 lanes), two warp hash-accumulator sizes, a block table, a global table.
+constexpr int kNumBins = 7;
+constexpr int kSortW0 = 8, kSortW1 = 16, kSortW2 = 32;
+constexpr int kAccU0 = 128, kAccU1 = 512;
+constexpr int kAccWarps0 = 8, kAccWarps1 = 4;
+// bin of a row with product bound u (upper limits 8, 16, 32, 128, 512, 4096)
+__device__ __forceinline__ int bin_of(int64_t u) {
+    return (u > kSortW0) + (u > kSortW1) + (u > kSortW2) + (u > kAccU0) + (u > kAccU1) + (u > kBlockUmax);
+}
 
-__global__ void bin_rows_kernel(int32_t n, const int64_t *ub, int32_t *bins, int32_t *bin_count) {
-    __shared__ int32_t local[4], base[4];
-    if (threadIdx.x < 4) local[threadIdx.x] = 0;
+// Row counts of the SpGEMM bins, the largest product bound of the last bin
+// and the total product bound: read back together in one copy.
+struct SpgemmCounts {
+    int32_t nb[kNumBins];
+    int32_t pad;
+    unsigned long long max_ub_global;
+    int64_t total_ub;
+};
+
+__global__ void bin_rows_kernel(int32_t n, const int64_t *ub, int32_t *bins, SpgemmCounts *cnt) {
+    __shared__ int32_t local[kNumBins], base[kNumBins];
+    __shared__ unsigned long long lmax;
+    if (threadIdx.x < kNumBins) local[threadIdx.x] = 0;
+    if (threadIdx.x == 0) lmax = 0ull;
     __syncthreads();
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = -1;
     int32_t my = 0;
     if (i < n) {
         int64_t u = ub[i];
-        b = u <= kTinyUmax ? 0 : (u <= kSmallUmax ? 1 : (u <= kBlockUmax ? 2 : 3));
+        b = bin_of(u);
         my = atomicAdd(&local[b], 1);
+        if (b == kNumBins - 1) atomicMax(&lmax, (unsigned long long)u);
     }
     __syncthreads();
-    if (threadIdx.x < 4) base[threadIdx.x] = local[threadIdx.x] ? atomicAdd(&bin_count[threadIdx.x], local[threadIdx.x]) : 0;
+    if (threadIdx.x < kNumBins)
+        base[threadIdx.x] = local[threadIdx.x] ? atomicAdd(&cnt->nb[threadIdx.x], local[threadIdx.x]) : 0;
+    if (threadIdx.x == 0 && lmax) atomicMax(&cnt->max_ub_global, lmax);
     __syncthreads();
     if (b >= 0) bins[(int64_t)b * n + base[b] + my] = i;
 }
 
-// Per-warp shared layout for rows of at most U products: product values,
-// hash keys and ranks (2U slots), distinct columns, per-column counts /
-// cursors, product columns (later ranks), and the stable permutation.
-template <int U> struct WarpTab {
-    static constexpr size_t kBytes = (size_t)U * 8 + (size_t)4 * U * 4 + (size_t)(U + 4) * 4 + (size_t)U * 4 * 3;
-    double *pv;
-    int32_t *keys, *rank, *list, *cnt, *pj, *perm;
-    __device__ WarpTab(unsigned char *base) {
-        pv = reinterpret_cast<double *>(base);
-        keys = reinterpret_cast<int32_t *>(base + (size_t)U * 8);
-        rank = keys + 2 * U;
-        cnt = rank + 2 * U;
-        list = cnt + U + 4;
-        pj = list + U;
-        perm = pj + U;
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Rows with at most W products (W = 8, 16, 32): one row per group of W lanes.
+// Every lane holds one product (column j, value a_ik b_kj, index e in the
+// order of A's row and then B's row); a bitonic network across the group
+// sorts the keys (j, e), so equal columns become adjacent and keep product
+// order; the first lane of every run sums its run from 0.0 in that order --
+// the dense-accumulator order of the definition, so the result is exact to
+// the bit with it.
+// ---------------------------------------------------------------------------
+template <int W, bool NUMERIC>
+__global__ void __launch_bounds__(256)
+spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_t *__restrict__ arp,
+                   const int32_t *__restrict__ aci, const double *__restrict__ av, const int32_t *__restrict__ brp,
+                   const int32_t *__restrict__ bci, const double *__restrict__ bv, int32_t *__restrict__ cnt,
+                   const int64_t *__restrict__ obase, int32_t *__restrict__ cci, double *__restrict__ cv) {
+    constexpr int G = 32 / W;  // rows per warp
+    const int lane = threadIdx.x & 31, sl = lane % W, sub = lane / W;
+    const unsigned gmask = W == 32 ? kFull : (((1u << W) - 1u) << (sub * W));
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t rb = warp * G; rb < nrows; rb += nwarps * G) {
+        const int64_t r = rb + sub;
+        const bool live = r < nrows;
+        const int32_t i = live ? rows[r] : 0;
+        const int32_t p0 = live ? arp[i] : 0, nA = live ? arp[i + 1] - p0 : 0;
+        // expansion: lane sl owns product e = sl (there are at most W)
+        bool valid = false;
+        int32_t j = 0;
+        double val = 0.0;
+        int32_t done = 0;  // products of earlier chunks of A's row
+        for (int32_t c0 = 0; c0 < nA; c0 += W) {  // uniform within the group
+            const int32_t idx = c0 + sl;
+            int32_t b0 = 0, len = 0;
+            double a = 0.0;
+            if (idx < nA) {
+                const int32_t k = aci[p0 + idx];
+                if (NUMERIC) a = av[p0 + idx];
+                b0 = brp[k];
+                len = brp[k + 1] - b0;
+            }
+            int32_t incl = len;
+#pragma unroll
+            for (int o = 1; o < W; o <<= 1) {
+                int32_t y = __shfl_up_sync(gmask, incl, o, W);
+                if (sl >= o) incl += y;
+            }
+            const int32_t excl = incl - len;
+            const int32_t total = __shfl_sync(gmask, incl, W - 1, W);
+            // owner of product e = sl within this chunk: last lane with excl <= e - done
+            const int32_t e = sl - done;
+            int lo = 0;
+#pragma unroll
+            for (int st = W / 2; st > 0; st >>= 1) {
+                const int cand = lo + st;
+                const int32_t ex = __shfl_sync(gmask, excl, cand & (W - 1), W);
+                if (cand < W && ex <= e) lo = cand;
+            }
+            const int32_t kb0 = __shfl_sync(gmask, b0, lo, W);
+            const int32_t kex = __shfl_sync(gmask, excl, lo, W);
+            const double ka = __shfl_sync(gmask, a, lo, W);
+            if (e >= 0 && e < total) {
+                const int32_t q = kb0 + (e - kex);
+                j = bci[q];
+                if (NUMERIC) val = ka * bv[q];
+                valid = true;
+            }
+            done += total;
+        }
+        // bitonic sort of (j, e) across the group; empty lanes sort last
+        uint64_t key = valid ? (((uint64_t)(uint32_t)j << 8) | (uint64_t)sl) : ~0ull;
+#pragma unroll
+        for (int size = 2; size <= W; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                const uint64_t ok = __shfl_xor_sync(gmask, key, stride, W);
+                double ov = 0.0;
+                if (NUMERIC) ov = __shfl_xor_sync(gmask, val, stride, W);
+                const bool up = (sl & size) == 0;
+                const bool lower = (sl & stride) == 0;
+                const bool take = lower == up ? ok < key : ok > key;
+                if (take) {
+                    key = ok;
+                    if (NUMERIC) val = ov;
+                }
+            }
+        }
+        valid = key != ~0ull;
+        j = (int32_t)(key >> 8);
+        const int32_t jprev = __shfl_up_sync(gmask, j, 1, W);
+        const bool head = valid && (sl == 0 || jprev != j);
+        const unsigned hb = (__ballot_sync(gmask, head) & gmask) >> (sub * W);
+        const int32_t u = __popc(hb);
+        if (NUMERIC) {
+            // run sums in product order, from 0.0
+            double acc = 0.0 + val;
+            bool more = head;
+            for (int d = 1; d < W; ++d) {
+                if (!__any_sync(gmask, more)) break;
+                const double vd = __shfl_down_sync(gmask, val, d, W);
+                const uint64_t kd = __shfl_down_sync(gmask, key, d, W);
+                if (more) {
+                    if (sl + d < W && kd != ~0ull && (int32_t)(kd >> 8) == j) acc += vd;
+                    else more = false;
+                }
+            }
+            if (head) {
+                const int32_t pos = __popc(hb & ((1u << sl) - 1u));
+                const int64_t cb = obase[i];
+                cci[cb + pos] = j;
+                cv[cb + pos] = acc;
+            }
+        }
+        if (live && sl == 0) cnt[i] = u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rows with at most U products (U = 128, 512): one warp per row with a
+// shared hash table of the row's distinct columns and their accumulators.
+// Products are generated 32 at a time in product order; within such a round
+// the lanes that hold the same column (different k) are found with a match,
+// and the first of them adds the round's values to the accumulator one by
+// one in lane order -- so every accumulator receives its products in the
+// order of A's row, starting from 0.0, as the definition does.  The distinct
+// columns are then sorted and written with their sums.
+// ---------------------------------------------------------------------------
+template <int U> struct AccTab {
+    static constexpr int kSlots = 2 * U;
+    static constexpr size_t kBytes = (size_t)kSlots * 8 + (size_t)kSlots * 4 + (size_t)U * 4;
+    double *val;
+    int32_t *keys, *list;
+    __device__ AccTab(unsigned char *base) {
+        val = reinterpret_cast<double *>(base);
+        keys = reinterpret_cast<int32_t *>(base + (size_t)kSlots * 8);
+        list = keys + kSlots;
     }
 };
 
-constexpr unsigned kFull = 0xffffffffu;
-
-// One row of C = A B by one warp, all lanes working on the flattened product
-// space.  Symbolic: returns the number of distinct columns.  Numeric: writes
-// the sorted columns and, for every column, the sum of its products in the
-// order of A's row (a stable scatter keeps product order), i.e. exactly the
-// dense-accumulator order.
 template <int U, bool NUMERIC>
-__device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
-                            const double *__restrict__ av, const int32_t *__restrict__ brp,
-                            const int32_t *__restrict__ bci, const double *__restrict__ bv, WarpTab<U> &t,
-                            int64_t ub, const int64_t *__restrict__ obase, int32_t *__restrict__ cci,
-                            double *__restrict__ cv) {
-    const int32_t hs = row_slots(ub, 2 * U);
+__device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
+                                const double *__restrict__ av, const int32_t *__restrict__ brp,
+                                const int32_t *__restrict__ bci, const double *__restrict__ bv, AccTab<U> &t,
+                                int64_t ub, const int64_t *__restrict__ obase, int32_t *__restrict__ cci,
+                                double *__restrict__ cv) {
+    const int32_t hs = row_slots(ub, AccTab<U>::kSlots);
     const uint32_t mask = (uint32_t)hs - 1;
     for (int32_t s = lane; s < hs; s += 32) t.keys[s] = -1;
     __syncwarp();
     const int32_t p0 = arp[i], nA = arp[i + 1] - p0;
-    int32_t np = 0, uniq = 0;
+    int32_t uniq = 0;
     for (int32_t c0 = 0; c0 < nA; c0 += 32) {
-        int32_t idx = c0 + lane, b0 = 0, len = 0;
+        const int32_t idx = c0 + lane;
+        int32_t b0 = 0, len = 0;
         double a = 0.0;
         if (idx < nA) {
-            int32_t k = aci[p0 + idx];
+            const int32_t k = aci[p0 + idx];
             if (NUMERIC) a = av[p0 + idx];
             b0 = brp[k];
             len = brp[k + 1] - b0;
         }
         int32_t incl = len;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             int32_t y = __shfl_up_sync(kFull, incl, o);
             if (lane >= o) incl += y;
@@ -474,42 +636,66 @@ __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp
         for (int32_t eb = 0; eb < total; eb += 32) {
             const int32_t e = eb + lane;
             int lo = 0;
+#pragma unroll
             for (int st = 16; st > 0; st >>= 1) {
-                int cand = lo + st;
-                int32_t ex = __shfl_sync(kFull, excl, cand & 31);
+                const int cand = lo + st;
+                const int32_t ex = __shfl_sync(kFull, excl, cand & 31);
                 if (cand < 32 && ex <= e) lo = cand;
             }
             const int32_t kb0 = __shfl_sync(kFull, b0, lo);
             const int32_t kex = __shfl_sync(kFull, excl, lo);
             const double ka = __shfl_sync(kFull, a, lo);
-            if (e < total) {
+            const bool valid = e < total;
+            int32_t j = -1 - lane;  // distinct placeholder for empty lanes
+            double prod = 0.0;
+            if (valid) {
                 const int32_t q = kb0 + (e - kex);
-                const int32_t j = bci[q];
-                const int32_t E = np + e;
-                if (NUMERIC) {
-                    t.pj[E] = j;
-                    t.pv[E] = ka * bv[q];
-                }
+                j = bci[q];
+                if (NUMERIC) prod = ka * bv[q];
+            }
+            const unsigned peers = __match_any_sync(kFull, j);
+            const bool leader = valid && lane == __ffs(peers) - 1;
+            int32_t slot = 0;
+            bool fresh = false;
+            if (leader) {
                 uint32_t sl = hash32(j) & mask;
                 while (true) {
-                    int32_t old = atomicCAS(&t.keys[sl], -1, j);
-                    if (old == -1) { ++uniq; break; }
+                    const int32_t old = atomicCAS(&t.keys[sl], -1, j);
+                    if (old == -1) { fresh = true; break; }
                     if (old == j) break;
                     sl = (sl + 1) & mask;
                 }
+                slot = (int32_t)sl;
+                uniq += fresh;
             }
+            if (NUMERIC) {
+                double acc = 0.0;
+                if (leader && !fresh) acc = t.val[slot];
+                // the leader adds its peers' values in lane order (itself first)
+                unsigned rest = leader ? peers : 0u;
+                const int npeer = __reduce_max_sync(kFull, (unsigned)__popc(rest));
+                for (int q = 0; q < npeer; ++q) {
+                    const int src = rest ? __ffs(rest) - 1 : lane;
+                    const double v = __shfl_sync(kFull, prod, src);
+                    if (rest) {
+                        acc += v;
+                        rest &= rest - 1u;
+                    }
+                }
+                if (leader) t.val[slot] = acc;
+            }
+            __syncwarp();
         }
-        np += total;
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) uniq += __shfl_xor_sync(kFull, uniq, o);
-    __syncwarp();
     if (!NUMERIC) return uniq;
     const int32_t u = uniq;
-    // distinct columns -> list (ballot compaction), pad, bitonic sort
+    // distinct columns -> list (ballot compaction), pad to a power of two, bitonic sort
     int32_t base = 0;
     for (int32_t s0 = 0; s0 < hs; s0 += 32) {
-        int32_t key = s0 + lane < hs ? t.keys[s0 + lane] : -1;
-        unsigned m = __ballot_sync(kFull, key >= 0);
+        const int32_t key = s0 + lane < hs ? t.keys[s0 + lane] : -1;
+        const unsigned m = __ballot_sync(kFull, key >= 0);
         if (key >= 0) t.list[base + __popc(m & ((1u << lane) - 1u))] = key;
         base += __popc(m);
     }
@@ -520,10 +706,10 @@ __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp
     for (int32_t size = 2; size <= m2; size <<= 1) {
         for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
             for (int32_t r = lane; r < m2; r += 32) {
-                int32_t partner = r ^ stride;
+                const int32_t partner = r ^ stride;
                 if (partner > r) {
-                    bool up = (r & size) == 0;
-                    int32_t x = t.list[r], y = t.list[partner];
+                    const bool up = (r & size) == 0;
+                    const int32_t x = t.list[r], y = t.list[partner];
                     if ((x > y) == up) { t.list[r] = y; t.list[partner] = x; }
                 }
             }
@@ -532,59 +718,11 @@ __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp
     }
     const int64_t cbase = obase[i];
     for (int32_t r = lane; r < u; r += 32) {
-        int32_t j = t.list[r];
+        const int32_t j = t.list[r];
         uint32_t sl = hash32(j) & mask;
         while (t.keys[sl] != j) sl = (sl + 1) & mask;
-        t.rank[sl] = r;
-        t.cnt[r] = 0;
         cci[cbase + r] = j;
-    }
-    __syncwarp();
-    // products per column
-    for (int32_t e = lane; e < np; e += 32) {
-        int32_t j = t.pj[e];
-        uint32_t sl = hash32(j) & mask;
-        while (t.keys[sl] != j) sl = (sl + 1) & mask;
-        int32_t r = t.rank[sl];
-        t.pj[e] = r;
-        atomicAdd(&t.cnt[r], 1);
-    }
-    __syncwarp();
-    // counts -> start offsets
-    int32_t carry = 0;
-    for (int32_t r0 = 0; r0 < u; r0 += 32) {
-        int32_t r = r0 + lane;
-        int32_t c = r < u ? t.cnt[r] : 0;
-        int32_t incl = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (r < u) t.cnt[r] = carry + incl - c;
-        carry += __shfl_sync(kFull, incl, 31);
-    }
-    __syncwarp();
-    // stable scatter: product e goes to the next free slot of its column, in e order
-    for (int32_t eb = 0; eb < np; eb += 32) {
-        const int32_t e = eb + lane;
-        const bool valid = e < np;
-        const int32_t r = valid ? t.pj[e] : -1 - lane;
-        const unsigned peers = __match_any_sync(kFull, r);
-        const int32_t within = __popc(peers & ((1u << lane) - 1u));
-        const int32_t pos = valid ? t.cnt[r] + within : 0;
-        __syncwarp();
-        if (valid) {
-            t.perm[pos] = e;
-            if (lane == __ffs(peers) - 1) t.cnt[r] += __popc(peers);
-        }
-        __syncwarp();
-    }
-    // cnt[r] now holds the end of column r's segment (= start of r + 1)
-    for (int32_t r = lane; r < u; r += 32) {
-        int32_t s0 = r == 0 ? 0 : t.cnt[r - 1], s1 = t.cnt[r];
-        double acc = 0.0;
-        for (int32_t p = s0; p < s1; ++p) acc += t.pv[t.perm[p]];
-        cv[cbase + r] = acc;
+        cv[cbase + r] = t.val[sl];
     }
     __syncwarp();
     return u;
@@ -592,15 +730,15 @@ __device__ int32_t warp_row(int32_t i, int lane, const int32_t *__restrict__ arp
 
 template <int U, int WARPS, bool NUMERIC>
 __global__ void __launch_bounds__(WARPS * 32)
-spgemm_warp_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
-                   const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
-                   int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
+spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
+                  const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
+                  int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
     extern __shared__ __align__(16) unsigned char smem[];
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpTab<U> t(smem + (size_t)w * WarpTab<U>::kBytes);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    AccTab<U> t(smem + (size_t)w * AccTab<U>::kBytes);
     for (int32_t r = blockIdx.x * WARPS + w; r < nrows; r += gridDim.x * WARPS) {
-        int32_t i = rows[r];
-        int32_t u = warp_row<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], obase, cci, cv);
+        const int32_t i = rows[r];
+        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], obase, cci, cv);
         if (lane == 0) cnt[i] = u;
     }
 }
@@ -796,14 +934,17 @@ __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
 }
 
 // copy each row's entries from its product-bound slot to the final CSR
+// compaction of the product-bound slots: eight lanes per row
+constexpr int kCompactLanes = 8;
 __global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int32_t *crp, const int32_t *tci,
                                       const double *tv, int32_t *cci, double *cv) {
-    int32_t i = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    int lane = threadIdx.x & 31;
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t i = (int32_t)(g / kCompactLanes);
+    int lane = (int)(g % kCompactLanes);
     if (i >= n) return;
     int64_t src = obase[i];
     int32_t dst = crp[i], len = crp[i + 1] - crp[i];
-    for (int32_t e = lane; e < len; e += 32) {
+    for (int32_t e = lane; e < len; e += kCompactLanes) {
         cci[dst + e] = tci[src + e];
         cv[dst + e] = tv[src + e];
     }
@@ -814,12 +955,19 @@ __global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int
 // ===========================================================================
 // host entry points
 // ===========================================================================
-void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s) {
+// Validation and transpose positions in one pass over the stream with one
+// read-back.  The transpose-position kernel checks every column index itself
+// before following it, so it is safe on a matrix that fails validation.
+void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s) {
     TmpBuf err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
-    if (A.nrows > 0)
+    if (A.nrows > 0) {
         { validate_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(
-            A.nrows, A.ncols, A.rp(), A.ci(), A.v(), diagpos, err.as<int>()); ::amg::count_launch(); }
+            A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(), diagpos, err.as<int>()); ::amg::count_launch(); }
+        if (A.nrows == A.ncols)
+            { tpos_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(A.nrows, A.nnz, A.rp(), A.ci(), tpos,
+                                                                       err.as<int>()); ::amg::count_launch(); }
+    }
     AMG_CHECK_LAUNCH();
     int e = read_scalar(err.as<int>(), s);
     if (e) {
@@ -829,19 +977,50 @@ void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s) {
         if (e & kNoDiag) m += " missing diagonal;";
         if (e & kBadDiag) m += " non-positive diagonal;";
         if (e & kNonFinite) m += " non-finite value;";
+        if (e & kAsym) m += " sparsity pattern is not symmetric;";
+        if (e & kBadRowptr) m += " row pointers out of order or out of [0, nnz];";
         throw Error(AMG_ERR_INVALID, m);
     }
+    require(A.nrows == A.ncols, "invalid matrix: not square");
 }
 
-void transpose_positions(const DevCSR &A, int32_t *tpos, cudaStream_t s) {
+// rectangular operators given by the caller (interpolation): row pointers,
+// column range, strictly increasing columns, finite values
+__global__ void validate_rect_kernel(int32_t n, int32_t ncols, int64_t nnz, const int32_t *rp, const int32_t *ci,
+                                     const double *v, int *err) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int e = 0;
+    const int32_t p0 = rp[i], p1 = rp[i + 1];
+    if ((i == 0 && p0 != 0) || (i == n - 1 && (int64_t)p1 != nnz)) e |= kBadRowptr;
+    if (!row_in_bounds(p0, p1, nnz)) { atomicOr(err, e | kBadRowptr); return; }
+    int32_t prev = -1;
+    for (int32_t p = p0; p < p1; ++p) {
+        const int32_t j = ci[p];
+        if (j < 0 || j >= ncols) { e |= kBadCol; continue; }
+        if (j <= prev) e |= kUnsorted;
+        prev = j;
+        if (!isfinite(v[p])) e |= kNonFinite;
+    }
+    if (e) atomicOr(err, e);
+}
+
+void validate_rect(const DevCSR &M, const char *what, cudaStream_t s) {
     TmpBuf err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
-    if (A.nrows > 0)
-        { tpos_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(A.nrows, A.rp(), A.ci(), tpos,
-                                                                   err.as<int>()); ::amg::count_launch(); }
+    if (M.nrows > 0)
+        { validate_rect_kernel<<<div_up(M.nrows, kThreads), kThreads, 0, s>>>(
+            M.nrows, M.ncols, M.nnz, M.rp(), M.ci(), M.v(), err.as<int>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    if (read_scalar(err.as<int>(), s))
-        throw Error(AMG_ERR_INVALID, "invalid matrix: sparsity pattern is not symmetric");
+    int e = read_scalar(err.as<int>(), s);
+    if (e) {
+        std::string m = std::string("invalid ") + what + ":";
+        if (e & kBadCol) m += " column index out of range;";
+        if (e & kUnsorted) m += " columns not strictly increasing;";
+        if (e & kNonFinite) m += " non-finite value;";
+        if (e & kBadRowptr) m += " row pointers out of order or out of [0, nnz];";
+        throw Error(AMG_ERR_INVALID, m);
+    }
 }
 
 void strength(const DevCSR &A, double theta, uint8_t *strong, cudaStream_t s) {
@@ -852,45 +1031,66 @@ void strength(const DevCSR &A, double theta, uint8_t *strong, cudaStream_t s) {
 }
 
 int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64_t seed,
-             int32_t level, int8_t *cf, cudaStream_t s) {
+             int32_t level, int8_t *cf, int32_t *cmap, cudaStream_t s) {
     int32_t n = A.nrows;
-    if (n == 0) return 0;
-    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int), s);
-    int g = div_up(n, kThreads);
-    AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));
-    { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
-                                            cf, cnt.as<int>()); ::amg::count_launch(); }
-    AMG_CHECK_LAUNCH();
-    int undecided = read_scalar(cnt.as<int>(), s);
-    int rounds = 0;
-    while (undecided > 0) {
-        if (++rounds > 10000) throw Error(AMG_ERR_CUDA, "PMIS did not terminate");
-        { pmis_select_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), tpos, strong, w.as<double>(),
-                                                  cf, newc.as<uint8_t>()); ::amg::count_launch(); }
-        { pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf); ::amg::count_launch(); }
-        AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(int), s));
-        { pmis_apply_f_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, cnt.as<int>()); ::amg::count_launch(); }
-        AMG_CHECK_LAUNCH();
-        int next = read_scalar(cnt.as<int>(), s);
-        if (next >= undecided) throw Error(AMG_ERR_CUDA, "PMIS made no progress");
-        undecided = next;
+    if (n == 0) {
+        AMG_CUDA(cudaMemsetAsync(cmap, 0, sizeof(int32_t), s));
+        return 0;
     }
-    TmpBuf flag(sizeof(int32_t) * n, s), scan(sizeof(int32_t) * (n + 1), s);
+    constexpr int kBatch = 4, kMaxRounds = 10000;
+    // cnt[0]: undecided after the initial split; cnt[r]: after round r
+    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s);
+    int *dc = cnt.as<int>();
+    int g = div_up(n, kThreads);
+    AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
+    { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
+                                            cf, dc); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+    int done = 0;  // rounds launched
+    int last = -1; // undecided count before the current batch (-1: not read yet)
+    while (true) {
+        if (done + kBatch > kMaxRounds) throw Error(AMG_ERR_CUDA, "PMIS did not terminate");
+        for (int b = 0; b < kBatch; ++b) {
+            const int r = done + b + 1;
+            { pmis_select_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), tpos, strong, w.as<double>(),
+                                                      cf, newc.as<uint8_t>(), dc + r - 1); ::amg::count_launch(); }
+            { pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf, dc + r - 1); ::amg::count_launch(); }
+            { pmis_apply_f_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, dc + r - 1, dc + r); ::amg::count_launch(); }
+        }
+        AMG_CHECK_LAUNCH();
+        int hc[kBatch + 1];
+        AMG_CUDA(cudaMemcpyAsync(hc, dc + done, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (last >= 0 && hc[0] != last) throw Error(AMG_ERR_CUDA, "PMIS counters inconsistent");
+        // every round that started with undecided points must have decided some
+        for (int b = 0; b < kBatch; ++b)
+            if (hc[b] > 0 && hc[b + 1] >= hc[b]) throw Error(AMG_ERR_CUDA, "PMIS made no progress");
+        done += kBatch;
+        last = hc[kBatch];
+        if (hc[kBatch] == 0) break;
+    }
+    TmpBuf flag(sizeof(int32_t) * n, s);
     { is_c_kernel<<<g, kThreads, 0, s>>>(n, cf, flag.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    return exclusive_scan_i32(flag.as<int32_t>(), scan.as<int32_t>(), n, s);
+    return exclusive_scan_i32(flag.as<int32_t>(), cmap, n, s);
 }
 
-void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s) {
+void coarse_points(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s) {
+    if (n == 0) return;
+    { cmap_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, cf, cmap, cpts); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
+void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, int64_t nc, cudaStream_t s) {
     if (n == 0) return;
     TmpBuf flag(sizeof(int32_t) * n, s);
     int g = div_up(n, kThreads);
     { is_c_kernel<<<g, kThreads, 0, s>>>(n, cf, flag.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     // cmap has n+1 slots: exclusive scan of the C flags
-    exclusive_scan_i32(flag.as<int32_t>(), cmap, n, s);
-    { cmap_kernel<<<g, kThreads, 0, s>>>(n, cf, cmap, cpts); ::amg::count_launch(); }
-    AMG_CHECK_LAUNCH();
+    const int64_t c = exclusive_scan_i32(flag.as<int32_t>(), cmap, n, s);
+    if (c != nc) throw Error(AMG_ERR_INVALID, "C/F markers: the number of C points differs from the coarse size");
+    coarse_points(cf, n, cmap, cpts, s);
 }
 
 void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, const int32_t *cmap,
@@ -907,8 +1107,8 @@ void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, con
     P.nnz = nnz;
     P.col.alloc(sizeof(int32_t) * (nnz + kPad));
     P.val.alloc(sizeof(double) * (nnz + kPad));
-    AMG_CUDA(cudaMemsetAsync(P.col.ptr, 0, P.col.bytes, s));
-    AMG_CUDA(cudaMemsetAsync(P.val.ptr, 0, P.val.bytes, s));
+    AMG_CUDA(cudaMemsetAsync(P.ci() + nnz, 0, sizeof(int32_t) * kPad, s));  // the fill writes rows [0, nnz)
+    AMG_CUDA(cudaMemsetAsync(P.v() + nnz, 0, sizeof(double) * kPad, s));
     if (n > 0)
         { interp_fill_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), strong, cf, cmap, P.rp(),
                                                   P.ci(), P.v()); ::amg::count_launch(); }
@@ -928,8 +1128,8 @@ void transpose(const DevCSR &M, DevCSR &T, cudaStream_t s) {
     T.nnz = nnz;
     T.col.alloc(sizeof(int32_t) * (nnz + kPad));
     T.val.alloc(sizeof(double) * (nnz + kPad));
-    AMG_CUDA(cudaMemsetAsync(T.col.ptr, 0, T.col.bytes, s));
-    AMG_CUDA(cudaMemsetAsync(T.val.ptr, 0, T.val.bytes, s));
+    AMG_CUDA(cudaMemsetAsync(T.ci() + nnz, 0, sizeof(int32_t) * kPad, s));  // the fill writes [0, nnz)
+    AMG_CUDA(cudaMemsetAsync(T.v() + nnz, 0, sizeof(double) * kPad, s));
     AMG_CUDA(cudaMemcpyAsync(fill.ptr, T.rp(), sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToDevice, s));
     if (M.nrows > 0)
         { transpose_fill_kernel<<<div_up(M.nrows, kThreads), kThreads, 0, s>>>(
@@ -957,99 +1157,108 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         Cm.val.alloc(sizeof(double) * kPad);
         return;
     }
-    TmpBuf ub(sizeof(int64_t) * n, s), bins(sizeof(int32_t) * 4 * (size_t)n, s), bcount(sizeof(int32_t) * 4, s),
-        cnt(sizeof(int32_t) * (n + 1), s);
+    TmpBuf ub(sizeof(int64_t) * n, s), bins(sizeof(int32_t) * kNumBins * (size_t)n, s),
+        dcounts(sizeof(SpgemmCounts), s), cnt(sizeof(int32_t) * (n + 1), s), obase(sizeof(int64_t) * (n + 1), s);
     int g = div_up(n, kThreads);
+    SpgemmCounts *dc = dcounts.as<SpgemmCounts>();
     { spgemm_ub_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), B.rp(), ub.as<int64_t>()); ::amg::count_launch(); }
-    AMG_CUDA(cudaMemsetAsync(bcount.ptr, 0, bcount.bytes, s));
-    { bin_rows_kernel<<<g, kThreads, 0, s>>>(n, ub.as<int64_t>(), bins.as<int32_t>(), bcount.as<int32_t>()); ::amg::count_launch(); }
+    AMG_CUDA(cudaMemsetAsync(dcounts.ptr, 0, sizeof(SpgemmCounts), s));
+    { bin_rows_kernel<<<g, kThreads, 0, s>>>(n, ub.as<int64_t>(), bins.as<int32_t>(), dc); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    int32_t nb[4];
-    AMG_CUDA(cudaMemcpyAsync(nb, bcount.ptr, sizeof(nb), cudaMemcpyDeviceToHost, s));
-    // largest upper bound in the global-table bin
-    int64_t max_ub = 0;
-    if (true) {
-        std::vector<int64_t> h_ub(n);
-        AMG_CUDA(cudaMemcpyAsync(h_ub.data(), ub.ptr, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
-        AMG_CUDA(cudaStreamSynchronize(s));
-        for (int32_t i = 0; i < n; ++i) max_ub = std::max(max_ub, h_ub[i]);
-    }
-    const int32_t *rows0 = bins.as<int32_t>();
-    const int32_t *rows1 = rows0 + n;
-    const int32_t *rows2 = rows0 + 2 * (size_t)n;
-    const int32_t *rows3 = rows0 + 3 * (size_t)n;
-    size_t tiny_smem = (size_t)kTinyWarps * WarpTab<kTinyUmax>::kBytes;
-    size_t small_smem = (size_t)kSmallWarps * WarpTab<kSmallUmax>::kBytes;
-    size_t block_smem = (size_t)kBlockHS * 8 + (size_t)kBlockUmax * 12;
-    static bool attrs = false;
-    if (!attrs) {
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kTinyUmax, kTinyWarps, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiny_smem));
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kTinyUmax, kTinyWarps, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiny_smem));
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kSmallUmax, kSmallWarps, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
-        AMG_CUDA(cudaFuncSetAttribute(spgemm_warp_kernel<kSmallUmax, kSmallWarps, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)small_smem));
+    // product-bound offsets of the one-pass numeric kernel (total into the same record)
+    exclusive_scan_i64_async(ub.as<int64_t>(), obase.as<int64_t>(), n, &dc->total_ub, s);
+    SpgemmCounts hc;
+    AMG_CUDA(cudaMemcpyAsync(&hc, dc, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    const int32_t *nb = hc.nb;
+    const int64_t max_ub = (int64_t)hc.max_ub_global;
+    const int64_t total_ub = hc.total_ub;
+    auto rows_of = [&](int b) { return bins.as<int32_t>() + (size_t)b * n; };
+    constexpr size_t acc0_smem = (size_t)kAccWarps0 * AccTab<kAccU0>::kBytes;
+    constexpr size_t acc1_smem = (size_t)kAccWarps1 * AccTab<kAccU1>::kBytes;
+    constexpr size_t block_smem = (size_t)kBlockHS * 8 + (size_t)kBlockUmax * 12;
+    static std::atomic<bool> attrs[64];
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64 || !attrs[dev].load()) {
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU1, kAccWarps1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc1_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU1, kAccWarps1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc1_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
-        attrs = true;
+        if (dev < 64) attrs[dev].store(true);
     }
+    const int nres = ::amg::resident_blocks(256);  // blocks of 256 threads that fit at once
     int64_t gumax = next_pow2(std::max<int64_t>(max_ub, 1));
     int64_t ghs = 2 * gumax;
     int gblocks = 0;
     TmpBuf gscr;
-    if (nb[3] > 0) {
+    if (nb[kNumBins - 1] > 0) {
         size_t per = (size_t)ghs * 8 + (size_t)gumax * 12;
         int64_t cap = std::max<int64_t>(1, (int64_t)(((size_t)2 << 30) / per));  // <= 2 GiB scratch
-        gblocks = (int)std::min<int64_t>({(int64_t)nb[3], 304, cap});
+        gblocks = (int)std::min<int64_t>({(int64_t)nb[kNumBins - 1], 304, cap});
         gscr.alloc(per * gblocks, s);
     }
     const int64_t *ubp = ub.as<int64_t>();
     // launch(numeric, obase, out_cols, out_vals): one pass over the bins
     auto launch = [&](bool numeric, const int64_t *ob, int32_t *cc, double *cvv) {
         int32_t *cp = cnt.as<int32_t>();
-        if (nb[0] > 0) {
-            int blocks = std::min(div_up(nb[0], kTinyWarps), 152 * 32);
+        auto sort_bin = [&](auto kern_num, auto kern_sym, int b, int W) {
+            if (nb[b] == 0) return;
+            const int64_t warps = ((int64_t)nb[b] * W + 31) / 32;
+            const int blocks = (int)std::min<int64_t>((warps + 7) / 8, nres);
             if (numeric)
-                { spgemm_warp_kernel<kTinyUmax, kTinyWarps, true><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                { kern_num<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv); ::amg::count_launch(); }
             else
-                { spgemm_warp_kernel<kTinyUmax, kTinyWarps, false><<<blocks, kTinyWarps * 32, tiny_smem, s>>>(
-                    rows0, nb[0], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
-        }
-        if (nb[1] > 0) {
-            int blocks = std::min(div_up(nb[1], kSmallWarps), 152 * 16);
+                { kern_sym<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv); ::amg::count_launch(); }
+        };
+        sort_bin(spgemm_sort_kernel<kSortW0, true>, spgemm_sort_kernel<kSortW0, false>, 0, kSortW0);
+        sort_bin(spgemm_sort_kernel<kSortW1, true>, spgemm_sort_kernel<kSortW1, false>, 1, kSortW1);
+        sort_bin(spgemm_sort_kernel<kSortW2, true>, spgemm_sort_kernel<kSortW2, false>, 2, kSortW2);
+        if (nb[3] > 0) {
+            const int blocks = std::min(div_up(nb[3], kAccWarps0), 152 * 16);
             if (numeric)
-                { spgemm_warp_kernel<kSmallUmax, kSmallWarps, true><<<blocks, kSmallWarps * 32, small_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                { spgemm_acc_kernel<kAccU0, kAccWarps0, true><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
+                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
             else
-                { spgemm_warp_kernel<kSmallUmax, kSmallWarps, false><<<blocks, kSmallWarps * 32, small_smem, s>>>(
-                    rows1, nb[1], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                { spgemm_acc_kernel<kAccU0, kAccWarps0, false><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
+                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
-        if (nb[2] > 0) {
-            int blocks = std::min(nb[2], 152 * 4);
+        if (nb[4] > 0) {
+            const int blocks = std::min(div_up(nb[4], kAccWarps1), 152 * 16);
+            if (numeric)
+                { spgemm_acc_kernel<kAccU1, kAccWarps1, true><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
+                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+            else
+                { spgemm_acc_kernel<kAccU1, kAccWarps1, false><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
+                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+        }
+        if (nb[5] > 0) {
+            const int blocks = std::min(nb[5], 152 * 4);
             if (numeric)
                 { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows2, nb[2], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
         }
-        if (nb[3] > 0) {
+        if (nb[6] > 0) {
             if (numeric)
                 { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows3, nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
         }
         AMG_CHECK_LAUNCH();
     };
     // one numeric pass into slots sized by each row's product bound, then a
     // compaction -- unless the bound does not fit: then count first (symbolic)
-    TmpBuf obase(sizeof(int64_t) * (n + 1), s);
-    int64_t total_ub = exclusive_scan_i64(ub.as<int64_t>(), obase.as<int64_t>(), n, s);
     size_t fr = 0, tot = 0;
     AMG_CUDA(cudaMemGetInfo(&fr, &tot));
     // AMG_SPGEMM_TWO_PASS=1 forces the counting path (it is otherwise taken
@@ -1065,9 +1274,9 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         Cm.nnz = nnz;
         Cm.col.alloc(sizeof(int32_t) * (nnz + kPad));
         Cm.val.alloc(sizeof(double) * (nnz + kPad));
-        AMG_CUDA(cudaMemsetAsync(Cm.col.ptr, 0, Cm.col.bytes, s));
-        AMG_CUDA(cudaMemsetAsync(Cm.val.ptr, 0, Cm.val.bytes, s));
-        { spgemm_compact_kernel<<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(n, obase.as<int64_t>(), Cm.rp(), tci.as<int32_t>(), tv.as<double>(), Cm.ci(), Cm.v()); ::amg::count_launch(); }
+        AMG_CUDA(cudaMemsetAsync(Cm.ci() + nnz, 0, sizeof(int32_t) * kPad, s));
+        AMG_CUDA(cudaMemsetAsync(Cm.v() + nnz, 0, sizeof(double) * kPad, s));
+        { spgemm_compact_kernel<<<div_up((int64_t)n * kCompactLanes, 256), 256, 0, s>>>(n, obase.as<int64_t>(), Cm.rp(), tci.as<int32_t>(), tv.as<double>(), Cm.ci(), Cm.v()); ::amg::count_launch(); }
         AMG_CHECK_LAUNCH();
         return;  // the temporaries' stream-ordered frees follow the compaction
     }

@@ -5,19 +5,27 @@
 namespace amg {
 namespace setup {
 
-// Checks sortedness, column range, finite values, a stored positive diagonal;
-// writes the diagonal position of every row.  Throws AMG_ERR_INVALID.
-void validate(const DevCSR &A, int32_t *diagpos, cudaStream_t s);
-// Position of the mirrored entry (j,i) for every stored (i,j); throws
-// AMG_ERR_INVALID if the pattern is not symmetric.
-void transpose_positions(const DevCSR &A, int32_t *tpos, cudaStream_t s);
+// Checks squareness, sortedness, column range, finite values, a stored
+// positive diagonal and a symmetric pattern; writes the diagonal position of
+// every row and the position of the mirrored entry (j,i) of every stored
+// (i,j).  Throws AMG_ERR_INVALID naming every failed check.
+void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s);
+// Row pointers, column range, strictly increasing columns and finite values of
+// a rectangular operator; throws AMG_ERR_INVALID naming `what`.
+void validate_rect(const DevCSR &M, const char *what, cudaStream_t s);
 // Classical strength flags (one byte per stored entry).
 void strength(const DevCSR &A, double theta, uint8_t *strong, cudaStream_t s);
-// PMIS C/F splitting; cf[i] = 1 (C) / -1 (F); returns |C|.
+// PMIS C/F splitting; cf[i] = 1 (C) / -1 (F); cmap (n + 1 entries) receives
+// the exclusive scan of the C flags (the coarse number of every C point);
+// returns |C|.
 int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64_t seed,
-             int32_t level, int8_t *cf, cudaStream_t s);
-// Coarse numbering: cmap[i] for C points, cpts[c] = fine index of coarse point c.
-void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s);
+             int32_t level, int8_t *cf, int32_t *cmap, cudaStream_t s);
+// cpts[c] = fine index of coarse point c, from cf and the scanned cmap;
+// cmap[i] becomes -1 at F points.
+void coarse_points(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s);
+// Coarse numbering from cf alone: the scan into cmap, then coarse_points;
+// throws AMG_ERR_INVALID unless cf marks exactly nc C points (cpts holds nc).
+void coarse_map(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, int64_t nc, cudaStream_t s);
 // Direct interpolation P (n x nc).
 void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, const int32_t *cmap,
                    int32_t nc, DevCSR &P, cudaStream_t s);

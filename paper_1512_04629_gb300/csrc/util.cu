@@ -143,7 +143,8 @@ __global__ void tile_sum_kernel(const TI *in, int64_t n, int64_t *sums) {
     if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-__global__ void scan_sums_kernel(int64_t *sums, int64_t m, int64_t *total) {
+template <typename TO>
+__global__ void scan_sums_kernel(int64_t *sums, int64_t m, int64_t *total, TO *out_n) {
     int64_t carry = 0;
     for (int64_t b = 0; b < m; b += kScanThreads) {
         int64_t i = b + threadIdx.x;
@@ -153,7 +154,10 @@ __global__ void scan_sums_kernel(int64_t *sums, int64_t m, int64_t *total) {
         if (i < m) sums[i] = carry + ex;
         carry += tot;
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) {
+        *total = carry;
+        *out_n = (TO)carry;  // checked against the int32 range by the host reader
+    }
 }
 
 template <typename TI, typename TO>
@@ -175,24 +179,29 @@ __global__ void tile_scan_kernel(const TI *in, int64_t n, const int64_t *sums, T
     }
 }
 
+// all on the stream, nothing read back: out[0..n] and *total on the device
 template <typename TI, typename TO>
-int64_t scan_impl(const TI *in, TO *out, int64_t n, cudaStream_t s) {
+void scan_launch(const TI *in, TO *out, int64_t n, int64_t *total, cudaStream_t s) {
     int64_t tiles = (n + kTile - 1) / kTile;
-    TmpBuf sums(sizeof(int64_t) * (tiles + 1), s), total(sizeof(int64_t), s);
     if (n > 0) {
+        TmpBuf sums(sizeof(int64_t) * (tiles + 1), s);
         { tile_sum_kernel<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()); ::amg::count_launch(); }
-        { scan_sums_kernel<<<1, kScanThreads, 0, s>>>(sums.as<int64_t>(), tiles, total.as<int64_t>()); ::amg::count_launch(); }
+        { scan_sums_kernel<TO><<<1, kScanThreads, 0, s>>>(sums.as<int64_t>(), tiles, total, out + n); ::amg::count_launch(); }
         { tile_scan_kernel<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>(), out); ::amg::count_launch(); }
         AMG_CHECK_LAUNCH();
     } else {
-        AMG_CUDA(cudaMemsetAsync(total.ptr, 0, sizeof(int64_t), s));
+        AMG_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), s));
+        AMG_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), s));
     }
+}
+
+template <typename TI, typename TO>
+int64_t scan_impl(const TI *in, TO *out, int64_t n, cudaStream_t s) {
+    TmpBuf total(sizeof(int64_t), s);
+    scan_launch<TI, TO>(in, out, n, total.as<int64_t>(), s);
     int64_t t = read_scalar(total.as<int64_t>(), s);
     if (sizeof(TO) == 4 && t >= ((int64_t)1 << 31))
         throw Error(AMG_ERR_INVALID, "scan: total exceeds the int32 index range");
-    TO tt = (TO)t;
-    AMG_CUDA(cudaMemcpyAsync(out + n, &tt, sizeof(TO), cudaMemcpyHostToDevice, s));
-    AMG_CUDA(cudaStreamSynchronize(s));
     return t;
 }
 }  // namespace
@@ -205,6 +214,9 @@ int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStrea
 }
 int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s) {
     return scan_impl<int32_t, int64_t>(in, out, n, s);
+}
+void exclusive_scan_i64_async(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s) {
+    scan_launch<int64_t, int64_t>(in, out, n, total, s);
 }
 
 }  // namespace amg

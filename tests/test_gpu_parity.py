@@ -293,6 +293,59 @@ def test_tiny_matrix(amg):
     assert info.status == 0 and abs(x[0] - 1.5) < 1e-14
 
 
+def test_invalid_device_structures_rejected(amg):
+    """Row pointers and indices that would lead a kernel outside its arrays
+    are reported as AMG_ERR_INVALID by the kernels' own range checks."""
+    import copy
+
+    import torch
+
+    A = gen.poisson2d_5pt(12)
+    rp, ci, va = (torch.from_numpy(np.array(a)).cuda() for a in (A.rowptr, A.col, A.val))
+
+    def expect_invalid_dev(rp_, ci_, va_):
+        M = amg.amg.csr_struct(rp_, ci_, va_)
+        with pytest.raises(amg.AmgError) as e:
+            amg.Hierarchy.setup(M)
+        assert e.value.status == 1
+
+    bad_rp = rp.clone()
+    bad_rp[5] = bad_rp[7] + 3  # row 4 ends past row 5's end: pointers out of order
+    expect_invalid_dev(bad_rp, ci, va)
+    bad_rp = rp.clone()
+    bad_rp[3] = -4
+    expect_invalid_dev(bad_rp, ci, va)
+    bad_ci = ci.clone()
+    bad_ci[10] = A.n + 1000
+    expect_invalid_dev(rp, bad_ci, va)
+    bad_ci = ci.clone()
+    bad_ci[10] = -7
+    expect_invalid_dev(rp, bad_ci, va)
+    # still usable afterwards
+    h = amg.Hierarchy.setup(amg.amg.csr_struct(rp, ci, va))
+    assert h.solve(gen.rhs_uniform(A.n, 0))[1].status == 0
+
+    # caller-given interpolation with a column outside [0, n_{l+1})
+    ref = oracle.Hierarchy(gen.poisson3d_7pt(12))
+    L = ref.num_levels
+    As = [ref.matrix(l, "A") for l in range(L)]
+    Ps = [copy.deepcopy(ref.matrix(l, "P")) for l in range(L - 1)]
+    cfs = [ref.cf(l) for l in range(L - 1)]
+    inMs = [None] + [ref.inM(l) for l in range(1, L)]
+    Ps[0].col[3] = As[1].nrows + 5
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.assemble(As, Ps, cfs, inMs)
+    assert e.value.status == 1
+    # C/F markers whose C count differs from the coarse size (hybrid pattern path)
+    Ps = [ref.matrix(l, "P") for l in range(L - 1)]
+    cfs = [np.array(c, copy=True) for c in cfs]
+    assert L >= 3
+    cfs[1][np.flatnonzero(cfs[1] == -1)[0]] = 1  # the hybrid pattern of level 2 numbers level 1's C points
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.assemble(As, Ps, cfs, inMs, gamma=[0.0, 0.1], method=1)
+    assert e.value.status == 1
+
+
 def test_invalid_inputs_rejected(amg):
     import scipy.sparse as sp
 
