@@ -59,6 +59,12 @@ inline void require(bool ok, const char *msg) {
 // device buffers (RAII); every persistent allocation of the library goes
 // through DevBuf so amg_device_bytes can account for it.
 // ---------------------------------------------------------------------------
+// A device buffer owned by a hierarchy (or a server).  Memory comes from the
+// device's stream-ordered pool (kept warm: freed blocks stay in the pool for
+// the next setup instead of going back to the driver); the allocation is
+// complete when alloc() returns, so any stream may use it.  release() waits
+// for the whole device unless the owner has already done so and opened an
+// IdleRelease scope.
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
@@ -79,6 +85,16 @@ struct DevBuf {
     void alloc(size_t b);
     void release();
     template <typename T> T *as() const { return static_cast<T *>(ptr); }
+};
+
+// Bulk teardown: the owner synchronizes the device, then calls enter(); every
+// DevBuf released on this thread until the guard is destroyed goes back to
+// the pool without another device-wide wait.  Declare the guard as the
+// owner's first member so it outlives the members it covers.
+struct IdleRelease {
+    bool active = false;
+    void enter();
+    ~IdleRelease();
 };
 
 // A temporary device buffer with stream-ordered lifetime: allocated with

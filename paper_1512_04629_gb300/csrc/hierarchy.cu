@@ -18,6 +18,11 @@
 namespace amg {
 
 Hierarchy::~Hierarchy() {
+    // one wait for the device, then every buffer goes back to the pool
+    // (on another current device the buffers fall back to one wait each)
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur == device && cudaDeviceSynchronize() == cudaSuccess) idle_release.enter();
     if (g_update) cudaGraphExecDestroy(g_update);
     if (g_precond) cudaGraphExecDestroy(g_precond);
     if (graph_stream) cudaStreamDestroy(graph_stream);

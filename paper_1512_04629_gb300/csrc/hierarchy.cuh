@@ -87,6 +87,7 @@ struct BatchWS {
 };
 
 struct Hierarchy {
+    IdleRelease idle_release;  // first member: destroyed after every buffer below
     amg_options opt{};
     int device = 0;
     std::vector<std::unique_ptr<Level>> lev;

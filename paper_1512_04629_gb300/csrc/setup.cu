@@ -8,6 +8,7 @@
 // setup is deterministic and repeatable run to run.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <climits>
 #include <cstdlib>
 
@@ -39,6 +40,50 @@ __device__ __forceinline__ bool contains(const int32_t *a, int32_t lo, int32_t h
 // validation and structural maps
 // ---------------------------------------------------------------------------
 enum : int { kBadCol = 1, kUnsorted = 2, kNoDiag = 4, kBadDiag = 8, kNonFinite = 16, kAsym = 32, kBadRowptr = 64 };
+
+// FP64 instructions are the scarce pipe on this part (a few per SM and
+// clock), comparisons included; the tests below decide the same IEEE
+// comparisons of non-NaN doubles on the integer pipes, through an order key
+// of the bit pattern: key(x) < key(y) iff x < y, and key(+0) = key(-0).
+__device__ __forceinline__ int64_t f64_key(double x) {
+    const int64_t b = __double_as_longlong(x);
+    return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
+}
+// |x| as a key (the bit pattern without its sign)
+__device__ __forceinline__ int64_t f64_abs_key(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
+// Row kernels map a group of T lanes (T = 2..32, a power of two near the
+// mean row length) to each row; the lanes take the row's entries with stride
+// T, so the gathers of a row are in flight together instead of one after
+// another.  Group reductions below are exact (integer max / or / sum).
+template <int T> __device__ __forceinline__ bool group_any(bool x) {
+    const unsigned b = __ballot_sync(0xffffffffu, x);
+    if constexpr (T == 32) {
+        return b != 0u;
+    } else {
+        const int base = (threadIdx.x & 31) & ~(T - 1);
+        return ((b >> base) & ((1u << T) - 1u)) != 0u;
+    }
+}
+template <int T> __device__ __forceinline__ int64_t group_max_i64(int64_t x) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) x = max(x, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)x, o, T));
+    return x;
+}
+template <int T> __device__ __forceinline__ int32_t group_sum_i32(int32_t x) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, T);
+    return x;
+}
+// the double whose order key is k (inverse of f64_key, +0.0 for key 0)
+__device__ __forceinline__ double f64_from_key(int64_t k) {
+    return __longlong_as_double(k >= 0 ? k : ((-k) | (int64_t)0x8000000000000000ull));
+}
+
+// 0.0 + x without an FP64 add: x itself, except that -0.0 becomes +0.0
+__device__ __forceinline__ double f64_zero_plus(double x) {
+    const int64_t b = __double_as_longlong(x);
+    return __longlong_as_double(b == (int64_t)0x8000000000000000ull ? 0ll : b);
+}
 
 // Every row range is checked against [0, nnz] before its entries are read,
 // so the kernel stays in bounds on any row-pointer array.
@@ -73,19 +118,22 @@ __global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int
     if (e) atomicOr(err, e);
 }
 
+template <int T>
 __global__ void tpos_kernel(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *tpos,
                             int *err) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
     if (i >= n) return;
     const int32_t p0 = rp[i], p1 = rp[i + 1];
-    if (!row_in_bounds(p0, p1, nnz)) { atomicOr(err, (int)kBadRowptr); return; }
-    for (int32_t p = p0; p < p1; ++p) {
+    if (!row_in_bounds(p0, p1, nnz)) { if (t == 0) atomicOr(err, (int)kBadRowptr); return; }
+    for (int32_t p = p0 + t; p < p1; p += T) {
         int32_t j = ci[p];
         if (j < 0 || j >= n) { tpos[p] = p; atomicOr(err, (int)kBadCol); continue; }  // reported, not followed
         const int32_t q0 = rp[j], q1 = rp[j + 1];
         if (!row_in_bounds(q0, q1, nnz)) { tpos[p] = p; atomicOr(err, (int)kBadRowptr); continue; }
         int32_t q = lower_bound_i32(ci, q0, q1, i);
-        if (q < rp[j + 1] && ci[q] == i) tpos[p] = q;
+        if (q < q1 && ci[q] == i) tpos[p] = q;
         else { tpos[p] = p; atomicOr(err, (int)kAsym); }
     }
 }
@@ -93,21 +141,27 @@ __global__ void tpos_kernel(int32_t n, int64_t nnz, const int32_t *rp, const int
 // ---------------------------------------------------------------------------
 // strength: j in S_i iff j != i and -a_ij >= theta * max_{k != i}(-a_ik) > 0
 // ---------------------------------------------------------------------------
+template <int T>
 __global__ void strength_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
                                 double theta, uint8_t *strong) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int32_t p0 = rp[i], p1 = rp[i + 1];
-    double m = 0.0;
-    bool any = false;
-    for (int32_t p = p0; p < p1; ++p) {
-        if (ci[p] == i) continue;
-        double t = -v[p];
-        if (!any || t > m) { m = t; any = true; }
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reduction needs every lane
+    int32_t p0 = 0, p1 = 0;
+    if (live) { p0 = rp[i]; p1 = rp[i + 1]; }
+    constexpr int64_t kNone = INT64_MIN;  // below every key
+    int64_t mk = kNone;                   // max over j != i of -a_ij (as a key)
+    for (int32_t p = p0 + t; p < p1; p += T)
+        if (ci[p] != i) mk = max(mk, f64_key(-v[p]));
+    mk = group_max_i64<T>(mk);
+    if (!live || mk <= 0) {  // no off-diagonal, or max(-a_ij) <= 0: no strong entry
+        for (int32_t p = p0 + t; p < p1; p += T) strong[p] = 0;
+        return;
     }
-    double t = theta * m;
-    for (int32_t p = p0; p < p1; ++p)
-        strong[p] = (uint8_t)(any && m > 0.0 && ci[p] != i && -v[p] >= t);
+    const int64_t tk = f64_key(theta * f64_from_key(mk));
+    for (int32_t p = p0 + t; p < p1; p += T)
+        strong[p] = (uint8_t)(ci[p] != i && f64_key(-v[p]) >= tk);
 }
 
 // ---------------------------------------------------------------------------
@@ -143,25 +197,29 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
 // Rounds are launched in batches without reading back in between: every
 // round kernel first reads the undecided count the previous round left and
 // does nothing once it is zero.
+template <int T>
 __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                    const int32_t *tpos, const uint8_t *strong, const double *w,
                                    const int8_t *state, uint8_t *newc, const int *prev) {
-    if (*prev == 0) return;
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint8_t win = 0;
-    if (state[i] == kU) {
-        win = 1;
-        double wi = w[i];
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+    if (*prev == 0) return;  // the same for the whole grid
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool und = i < n && state[i] == kU;
+    bool lose = false;
+    if (und) {
+        // weights are >= 0: their bit patterns order like the values
+        const int64_t wi = __double_as_longlong(w[i]);
+        for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
             if (!(strong[p] || strong[tpos[p]])) continue;  // S_i u S^T_i
-            int32_t j = ci[p];
+            const int32_t j = ci[p];
             if (state[j] != kU) continue;
-            double wj = w[j];
-            if (wj > wi || (wj == wi && j > i)) { win = 0; break; }
+            const int64_t wj = __double_as_longlong(w[j]);
+            if (wj > wi || (wj == wi && j > i)) { lose = true; break; }
         }
     }
-    newc[i] = win;
+    lose = group_any<T>(lose);
+    if (i < n && t == 0) newc[i] = (uint8_t)(und && !lose);
 }
 
 __global__ void pmis_apply_c_kernel(int32_t n, const uint8_t *newc, int8_t *state, const int *prev) {
@@ -170,15 +228,21 @@ __global__ void pmis_apply_c_kernel(int32_t n, const uint8_t *newc, int8_t *stat
     if (i < n && newc[i]) state[i] = kC;
 }
 
+template <int T>
 __global__ void pmis_apply_f_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                     const uint8_t *strong, int8_t *state, const int *prev, int *undecided) {
-    if (*prev == 0) return;
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    int still = 0;
-    if (i < n && state[i] == kU) {
-        bool f = false;
-        for (int32_t p = rp[i]; p < rp[i + 1] && !f; ++p)
+    if (*prev == 0) return;  // the same for the whole grid
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool und = i < n && state[i] == kU;
+    bool f = false;
+    if (und)
+        for (int32_t p = rp[i] + t; p < rp[i + 1] && !f; p += T)
             if (strong[p] && state[ci[p]] == kC) f = true;
+    f = group_any<T>(f);
+    int still = 0;
+    if (und && t == 0) {
         if (f) state[i] = kF; else still = 1;
     }
     still = __syncthreads_count(still);
@@ -203,15 +267,19 @@ __global__ void cmap_kernel(int32_t n, const int8_t *cf, int32_t *cmap, int32_t 
 // ---------------------------------------------------------------------------
 // direct interpolation (count, then fill with the sums in column order)
 // ---------------------------------------------------------------------------
+template <int T>
 __global__ void interp_count_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                     const uint8_t *strong, const int8_t *cf, int32_t *cnt) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (cf[i] == kC) { cnt[i] = 1; return; }
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool fpt = i < n && cf[i] != kC;
     int32_t c = 0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
-        if (strong[p] && cf[ci[p]] == kC) ++c;
-    cnt[i] = c;
+    if (fpt)
+        for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T)
+            if (strong[p] && cf[ci[p]] == kC) ++c;
+    c = group_sum_i32<T>(c);
+    if (i < n && t == 0) cnt[i] = fpt ? c : 1;
 }
 
 __global__ void interp_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
@@ -228,23 +296,21 @@ __global__ void interp_fill_kernel(int32_t n, const int32_t *rp, const int32_t *
         int32_t j = ci[p];
         double a = v[p];
         if (j == i) { diag = a; continue; }
-        if (a < 0.0) sum_neg += a;
-        if (a > 0.0) sum_pos += a;
-        if (strong[p] && cf[j] == kC) {
-            if (a < 0.0) sum_neg_c += a;
-            if (a > 0.0) sum_pos_c += a;
-        }
+        const int64_t ak = f64_key(a);
+        const bool sc = strong[p] && cf[j] == kC;
+        if (ak < 0) { sum_neg += a; if (sc) sum_neg_c += a; }
+        if (ak > 0) { sum_pos += a; if (sc) sum_pos_c += a; }
     }
-    double alpha = (sum_neg_c != 0.0) ? sum_neg / sum_neg_c : 0.0;
+    double alpha = f64_key(sum_neg_c) != 0 ? sum_neg / sum_neg_c : 0.0;
     double beta = 0.0;
-    if (sum_pos_c != 0.0) beta = sum_pos / sum_pos_c;
+    if (f64_key(sum_pos_c) != 0) beta = sum_pos / sum_pos_c;
     else diag = diag + sum_pos;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
         if (j == i || !strong[p] || cf[j] != kC) continue;
         double a = v[p];
         pci[pos] = cmap[j];
-        pv[pos] = (a < 0.0) ? (-alpha * a) / diag : (-beta * a) / diag;
+        pv[pos] = f64_key(a) < 0 ? (-alpha * a) / diag : (-beta * a) / diag;
         ++pos;
     }
 }
@@ -559,7 +625,7 @@ spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_
         const int32_t u = __popc(hb);
         if (NUMERIC) {
             // run sums in product order, from 0.0
-            double acc = 0.0 + val;
+            double acc = f64_zero_plus(val);
             bool more = head;
             for (int d = 1; d < W; ++d) {
                 if (!__any_sync(gmask, more)) break;
@@ -669,16 +735,18 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
                 uniq += fresh;
             }
             if (NUMERIC) {
-                double acc = 0.0;
-                if (leader && !fresh) acc = t.val[slot];
-                // the leader adds its peers' values in lane order (itself first)
+                // the leader adds its peers' values in lane order (itself
+                // first); a fresh accumulator starts from 0.0
+                double acc = (leader && !fresh) ? t.val[slot] : 0.0;
+                bool first = leader && fresh;
                 unsigned rest = leader ? peers : 0u;
                 const int npeer = __reduce_max_sync(kFull, (unsigned)__popc(rest));
                 for (int q = 0; q < npeer; ++q) {
                     const int src = rest ? __ffs(rest) - 1 : lane;
                     const double v = __shfl_sync(kFull, prod, src);
                     if (rest) {
-                        acc += v;
+                        acc = first ? f64_zero_plus(v) : acc + v;
+                        first = false;
                         rest &= rest - 1u;
                     }
                 }
@@ -782,16 +850,19 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
 // ---------------------------------------------------------------------------
 // minimal pattern: (i,j) in M iff j in AP[cpts[i]] or i in AP[cpts[j]]
 // ---------------------------------------------------------------------------
+template <int T>
 __global__ void minimal_pattern_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                        const int32_t *aprp, const int32_t *apci,
                                        const int32_t *cpts, uint8_t *inM) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
     if (i >= n) return;
-    int32_t fi = cpts[i];
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        int32_t j = ci[p];
-        int32_t fj = cpts[j];
-        bool m = contains(apci, aprp[fi], aprp[fi + 1], j) || contains(apci, aprp[fj], aprp[fj + 1], i);
+    const int32_t fi = cpts[i];
+    for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
+        const int32_t j = ci[p];
+        const int32_t fj = cpts[j];
+        const bool m = contains(apci, aprp[fi], aprp[fi + 1], j) || contains(apci, aprp[fj], aprp[fj + 1], i);
         inM[p] = (uint8_t)m;
     }
 }
@@ -799,18 +870,26 @@ __global__ void minimal_pattern_kernel(int32_t n, const int32_t *rp, const int32
 // ---------------------------------------------------------------------------
 // sparsify (Algorithm 3 first loop + Algorithm 3b)
 // ---------------------------------------------------------------------------
+template <int T>
 __global__ void sparsify_flag_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                      const double *v, const uint8_t *inM, double gamma,
                                      double *rowmax, uint8_t *flag) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double m = 0.0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
-        if (ci[p] != i && fabs(v[p]) > m) m = fabs(v[p]);
-    rowmax[i] = m;
-    double t = gamma * m;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
-        flag[p] = (uint8_t)(ci[p] != i && (inM[p] || fabs(v[p]) >= t));
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reduction needs every lane
+    int32_t p0 = 0, p1 = 0;
+    if (live) { p0 = rp[i]; p1 = rp[i + 1]; }
+    int64_t mk = 0;  // key of max |a_ij| over j != i (0: +0.0)
+    for (int32_t p = p0 + t; p < p1; p += T)
+        if (ci[p] != i) mk = max(mk, f64_abs_key(v[p]));
+    mk = group_max_i64<T>(mk);
+    if (!live) return;
+    const double m = __longlong_as_double(mk);
+    if (t == 0) rowmax[i] = m;
+    const int64_t tk = f64_abs_key(gamma * m);  // gamma * m >= 0
+    for (int32_t p = p0 + t; p < p1; p += T)
+        flag[p] = (uint8_t)(ci[p] != i && (inM[p] || f64_abs_key(v[p]) >= tk));
 }
 
 __global__ void sparsify_sym_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
@@ -827,7 +906,7 @@ __global__ void sparsify_sym_kernel(int32_t n, const int32_t *rp, const int32_t 
         rs += v[p];
         ra += fabs(v[p]);
     }
-    guard[i] = (uint8_t)(!any_off && rowmax[i] > 0.0 && fabs(rs) <= 1e-12 * ra);
+    guard[i] = (uint8_t)(!any_off && f64_key(rowmax[i]) > 0 && f64_abs_key(rs) <= f64_key(1e-12 * ra));
 }
 
 __global__ void sparsify_guard_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
@@ -839,7 +918,8 @@ __global__ void sparsify_guard_kernel(int32_t n, const int32_t *rp, const int32_
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
         if (!keep[p] && j != i) {
-            if ((guard[i] && fabs(v[p]) == rowmax[i]) || (guard[j] && fabs(v[tpos[p]]) == rowmax[j]))
+            if ((guard[i] && f64_abs_key(v[p]) == f64_key(rowmax[i])) ||
+                (guard[j] && f64_abs_key(v[tpos[p]]) == f64_key(rowmax[j])))
                 keep[p] = 1;
         }
         c += keep[p];
@@ -952,6 +1032,24 @@ __global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int
 
 }  // namespace
 
+// lanes per row for the row kernels: the power of two (2..32) at or above
+// the mean row length
+static int row_lanes(const DevCSR &A) {
+    const double mean = A.nrows > 0 ? (double)A.nnz / (double)A.nrows : 0.0;
+    int T = 2;
+    while (T < 32 && (double)T < mean) T <<= 1;
+    return T;
+}
+template <class F> static void with_row_lanes(int T, F &&f) {
+    switch (T) {
+        case 2: f(std::integral_constant<int, 2>{}); break;
+        case 4: f(std::integral_constant<int, 4>{}); break;
+        case 8: f(std::integral_constant<int, 8>{}); break;
+        case 16: f(std::integral_constant<int, 16>{}); break;
+        default: f(std::integral_constant<int, 32>{}); break;
+    }
+}
+
 // ===========================================================================
 // host entry points
 // ===========================================================================
@@ -965,8 +1063,12 @@ void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s
         { validate_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(
             A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(), diagpos, err.as<int>()); ::amg::count_launch(); }
         if (A.nrows == A.ncols)
-            { tpos_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(A.nrows, A.nnz, A.rp(), A.ci(), tpos,
-                                                                       err.as<int>()); ::amg::count_launch(); }
+            with_row_lanes(row_lanes(A), [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                tpos_kernel<L><<<div_up((int64_t)A.nrows * L, kThreads), kThreads, 0, s>>>(
+                    A.nrows, A.nnz, A.rp(), A.ci(), tpos, err.as<int>());
+                ::amg::count_launch();
+            });
     }
     AMG_CHECK_LAUNCH();
     int e = read_scalar(err.as<int>(), s);
@@ -1025,8 +1127,12 @@ void validate_rect(const DevCSR &M, const char *what, cudaStream_t s) {
 
 void strength(const DevCSR &A, double theta, uint8_t *strong, cudaStream_t s) {
     if (A.nrows == 0) return;
-    { strength_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(A.nrows, A.rp(), A.ci(), A.v(),
-                                                                   theta, strong); ::amg::count_launch(); }
+    with_row_lanes(row_lanes(A), [&](auto tc) {
+        constexpr int L = decltype(tc)::value;
+        strength_kernel<L><<<div_up((int64_t)A.nrows * L, kThreads), kThreads, 0, s>>>(A.nrows, A.rp(), A.ci(),
+                                                                                   A.v(), theta, strong);
+        ::amg::count_launch();
+    });
     AMG_CHECK_LAUNCH();
 }
 
@@ -1042,6 +1148,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s);
     int *dc = cnt.as<int>();
     int g = div_up(n, kThreads);
+    const int T = row_lanes(A);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
                                             cf, dc); ::amg::count_launch(); }
@@ -1052,10 +1159,17 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         if (done + kBatch > kMaxRounds) throw Error(AMG_ERR_CUDA, "PMIS did not terminate");
         for (int b = 0; b < kBatch; ++b) {
             const int r = done + b + 1;
-            { pmis_select_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), tpos, strong, w.as<double>(),
-                                                      cf, newc.as<uint8_t>(), dc + r - 1); ::amg::count_launch(); }
-            { pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf, dc + r - 1); ::amg::count_launch(); }
-            { pmis_apply_f_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, dc + r - 1, dc + r); ::amg::count_launch(); }
+            with_row_lanes(T, [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                const int gl = div_up((int64_t)n * L, kThreads);
+                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), tpos, strong, w.as<double>(), cf,
+                                                              newc.as<uint8_t>(), dc + r - 1);
+                ::amg::count_launch();
+                pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf, dc + r - 1);
+                ::amg::count_launch();
+                pmis_apply_f_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, dc + r - 1, dc + r);
+                ::amg::count_launch();
+            });
         }
         AMG_CHECK_LAUNCH();
         int hc[kBatch + 1];
@@ -1099,7 +1213,13 @@ void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, con
     TmpBuf cnt(sizeof(int32_t) * (n + 1), s);
     P.rowptr.alloc(sizeof(int32_t) * (n + 1));
     int g = div_up(n, kThreads);
-    if (n > 0) { interp_count_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, cnt.as<int32_t>()); ::amg::count_launch(); }
+    if (n > 0)
+        with_row_lanes(row_lanes(A), [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            interp_count_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf,
+                                                                                       cnt.as<int32_t>());
+            ::amg::count_launch();
+        });
     AMG_CHECK_LAUNCH();
     int64_t nnz = exclusive_scan_i32(cnt.as<int32_t>(), P.rp(), n, s);
     P.nrows = n;
@@ -1295,8 +1415,12 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
 void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, uint8_t *inM,
                      cudaStream_t s) {
     if (Ac.nrows == 0) return;
-    { minimal_pattern_kernel<<<div_up(Ac.nrows, kThreads), kThreads, 0, s>>>(
-        Ac.nrows, Ac.rp(), Ac.ci(), AP.rp(), AP.ci(), cpts, inM); ::amg::count_launch(); }
+    with_row_lanes(row_lanes(Ac), [&](auto tc) {
+        constexpr int L = decltype(tc)::value;
+        minimal_pattern_kernel<L><<<div_up((int64_t)Ac.nrows * L, kThreads), kThreads, 0, s>>>(
+            Ac.nrows, Ac.rp(), Ac.ci(), AP.rp(), AP.ci(), cpts, inM);
+        ::amg::count_launch();
+    });
     AMG_CHECK_LAUNCH();
 }
 
@@ -1306,8 +1430,12 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
     TmpBuf rowmax(sizeof(double) * (n + 1), s), flag(A.nnz + 1, s), guard(n + 1, s), cnt(sizeof(int32_t) * (n + 1), s);
     int g = div_up(n, kThreads);
     if (n > 0) {
-        { sparsify_flag_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), inM, gamma,
-                                                    rowmax.as<double>(), flag.as<uint8_t>()); ::amg::count_launch(); }
+        with_row_lanes(row_lanes(A), [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            sparsify_flag_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+                n, A.rp(), A.ci(), A.v(), inM, gamma, rowmax.as<double>(), flag.as<uint8_t>());
+            ::amg::count_launch();
+        });
         { sparsify_sym_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, flag.as<uint8_t>(),
                                                    rowmax.as<double>(), keep, guard.as<uint8_t>()); ::amg::count_launch(); }
         { sparsify_guard_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, guard.as<uint8_t>(),

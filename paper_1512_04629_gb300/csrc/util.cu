@@ -1,5 +1,6 @@
 // util.cu -- device buffers, thread-local error text, exclusive scans.
 #include <atomic>
+#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -28,23 +29,57 @@ int resident_blocks(int threads_per_block) {
 }
 const char *last_error_cstr() { return g_last_error.c_str(); }
 
+namespace {
+thread_local int g_idle_depth = 0;
+
+// one non-blocking stream per device for pool allocations and bulk frees
+cudaStream_t pool_stream() {
+    static std::mutex mu;
+    static cudaStream_t streams[64] = {};
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64) throw Error(AMG_ERR_CUDA, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!streams[dev]) AMG_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    return streams[dev];
+}
+}  // namespace
+
+void IdleRelease::enter() {
+    if (!active) { ++g_idle_depth; active = true; }
+}
+IdleRelease::~IdleRelease() {
+    if (active) --g_idle_depth;
+}
+
+static void keep_pool_warm();
+
 void DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&ptr, b);
+    keep_pool_warm();
+    cudaStream_t ps = pool_stream();
+    cudaError_t e = cudaMallocAsync(&ptr, b, ps);
+    // the pool may order the allocation after frees still pending on other
+    // streams: wait for it, so the memory is usable from any stream at once
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
     if (e != cudaSuccess) {
         cudaGetLastError();
         ptr = nullptr;
         throw Error(e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA,
-                    std::string("cudaMalloc(") + std::to_string(b) + "): " + cudaGetErrorString(e));
+                    std::string("cudaMallocAsync(") + std::to_string(b) + "): " + cudaGetErrorString(e));
     }
     bytes = b;
     g_device_bytes += (int64_t)b;
 }
-
 void DevBuf::release() {
     if (ptr) {
-        cudaFree(ptr);
+        cudaStream_t ps = nullptr;
+        if (g_idle_depth > 0) {
+            try { ps = pool_stream(); } catch (...) { ps = nullptr; }
+        }
+        if (ps) cudaFreeAsync(ptr, ps);  // the owner synchronized the device
+        else cudaFree(ptr);              // waits for the device first
         g_device_bytes -= (int64_t)bytes;
     }
     ptr = nullptr;
