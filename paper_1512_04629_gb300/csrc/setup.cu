@@ -1032,12 +1032,12 @@ __global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int
 
 }  // namespace
 
-// lanes per row for the row kernels: the power of two (2..32) at or above
-// the mean row length
-static int row_lanes(const DevCSR &A) {
-    const double mean = A.nrows > 0 ? (double)A.nnz / (double)A.nrows : 0.0;
+// lanes per row for the row kernels: the power of two (2..cap) at or above
+// half the mean row length (about two entries per lane)
+static int row_lanes(const DevCSR &A, int cap = 32) {
+    const double half = A.nrows > 0 ? 0.5 * (double)A.nnz / (double)A.nrows : 0.0;
     int T = 2;
-    while (T < 32 && (double)T < mean) T <<= 1;
+    while (T < cap && (double)T < half) T <<= 1;
     return T;
 }
 template <class F> static void with_row_lanes(int T, F &&f) {
@@ -1148,7 +1148,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s);
     int *dc = cnt.as<int>();
     int g = div_up(n, kThreads);
-    const int T = row_lanes(A);
+    const int T = row_lanes(A, 8);  // later rounds find most rows decided: keep the grid small
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
                                             cf, dc); ::amg::count_launch(); }
