@@ -243,6 +243,26 @@ static int heuristic_variant(const DevCSR &M) {
 // SELL-32 copy of the relaxed operator.  If slices of consecutive rows would
 // pad the matrix by more than 3%, rows are sorted by length inside windows of
 // kSellSigma rows (SELL-C-sigma) and kernels write through the permutation.
+// SELL-32 layout of M with values vals (length-sorted rows when the plain
+// slicing would pad more than 3%)
+template <typename VT>
+static void build_sell_copy(const DevCSR &M, const VT *vals, SellCopy &S, cudaStream_t s) {
+    const int32_t nsl = (M.nrows + 31) / 32;
+    S.soff.alloc(sizeof(int32_t) * (nsl + 1));
+    S.sw.alloc(sizeof(int32_t) * (nsl + 1));
+    S.perm.release();
+    S.entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, S.soff.as<int32_t>(), S.sw.as<int32_t>(), s);
+    if ((double)S.entries > 1.03 * (double)M.nnz) {
+        S.perm.alloc(sizeof(int32_t) * (M.nrows + kPad));
+        S.entries = cyc::sell_layout(M.nrows, M.rp(), S.perm.as<int32_t>(), S.soff.as<int32_t>(),
+                                     S.sw.as<int32_t>(), s);
+    }
+    S.sci.alloc(sizeof(int32_t) * (S.entries + kPad));
+    S.sv.alloc(sizeof(VT) * (S.entries + kPad));
+    cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), vals, S.perm.ptr ? S.perm.as<int32_t>() : nullptr,
+                       S.soff.as<int32_t>(), S.sw.as<int32_t>(), S.sci.as<int32_t>(), S.sv.as<VT>(), s);
+}
+
 template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
     const DevCSR &M = V.op();
     int32_t nsl = (M.nrows + 31) / 32;
@@ -456,22 +476,30 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
     cudaEvent_t e0, e1;
     AMG_CUDA(cudaEventCreate(&e0));
     AMG_CUDA(cudaEventCreate(&e1));
-    auto tune = [&](const DevCSR &M, int kind, int &variant, auto run) {
+    auto tune = [&](const DevCSR &M, const XT *vals, SellCopy &S, int kind, int &variant, auto run) {
         TuneKey key{M.nrows, M.nnz, 100 * kind + vb};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             tune_cache_load_locked();
             auto it = g_tune_cache.find(key);
-            if (it != g_tune_cache.end()) { variant = it->second; return; }
+            if (it != g_tune_cache.end()) {
+                variant = it->second;
+                if (variant == AMG_SPMV_SELL32) build_sell_copy<XT>(M, vals, S, s);
+                return;
+            }
         }
+        build_sell_copy<XT>(M, vals, S, s);
         double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
         int V16 = 16 / vb;
         float best = 1e30f;
         int best_v = variant;
-        const int vars[] = {AMG_SPMV_CSR1, AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16};
+        const int vars[] = {AMG_SPMV_CSR1, AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16,
+                            AMG_SPMV_SELL32};
         for (int v : vars) {
             double cover = (double)cyc::threads_per_row(v) * V16;
-            if (v != AMG_SPMV_CSR1 && !(cover >= mean / 4.0 && cover <= std::max(4.0 * mean, (double)V16 * 2))) continue;
+            if (v != AMG_SPMV_CSR1 && v != AMG_SPMV_SELL32 &&
+                !(cover >= mean / 4.0 && cover <= std::max(4.0 * mean, (double)V16 * 2)))
+                continue;
             variant = v;
             run();
             float tmin = 1e30f;
@@ -487,12 +515,22 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
             if (tmin < best * 0.98f) { best = tmin; best_v = v; }
         }
         variant = best_v;
+        if (variant != AMG_SPMV_SELL32) S.release();
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_store_locked(key, best_v);
     };
     if (V.P.nnz >= 20000) {
-        tune(V.P, 1, V.variant_p, [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
-        tune(V.R, 2, V.variant_r, [&] {
+        const XT *pv, *rv;
+        if constexpr (sizeof(XT) == 8) {
+            pv = reinterpret_cast<const XT *>(V.P.v());
+            rv = reinterpret_cast<const XT *>(V.R.v());
+        } else {
+            pv = V.pv32.as<XT>();
+            rv = V.rv32.as<XT>();
+        }
+        tune(V.P, pv, V.psell, 1, V.variant_p,
+             [&] { cyc::spmv<XT, XT>(p_mat<XT>(V), C.xo.as<XT>(), V.x.as<XT>(), true, s); });
+        tune(V.R, rv, V.rsell, 2, V.variant_r, [&] {
             cyc::spmv_scaled<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), dinv_of<XT>(C), C.b.as<XT>(), C.x.as<XT>(), s);
         });
     }

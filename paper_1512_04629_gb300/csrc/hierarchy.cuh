@@ -12,6 +12,17 @@
 
 namespace amg {
 
+// SELL-32 copy of a CSR operator (slices of 32 rows stored column-major;
+// rows length-sorted within windows when that cuts the padding).
+struct SellCopy {
+    DevBuf soff, sw, sci, sv, perm;
+    int64_t entries = 0;
+    void release() {
+        soff.release(); sw.release(); sci.release(); sv.release(); perm.release();
+        entries = 0;
+    }
+};
+
 // One level l of the hierarchy.  A is the retained Galerkin operator
 // (Algorithm 4 keeps it so Algorithm 5 can reintroduce entries); H is the
 // relaxed operator Ahat_l (an alias of A where nothing is dropped).
@@ -38,6 +49,7 @@ struct Level {
     DevBuf sperm;              // SELL position -> row when rows are length-sorted
     DevBuf sv64;               // level 0 in FP32 modes: FP64 values in the same SELL layout (outer PCG)
     int64_t sell_entries = 0;
+    SellCopy psell, rsell;     // SELL copies of P and R (cycle precision) when they win the trial
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
     bool pr_tuned = false;  // transfer-operator variants chosen by timed trials
 
@@ -155,11 +167,22 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
     return m;
 }
 
+template <typename VT> inline void attach_sell(CycMat<VT> &m, const SellCopy &S) {
+    if (!S.sv.ptr) return;
+    m.nslices = (m.nrows + 31) / 32;
+    m.soff = S.soff.as<int32_t>();
+    m.sw = S.sw.as<int32_t>();
+    m.sci = S.sci.as<int32_t>();
+    m.sv = S.sv.as<VT>();
+    m.perm = S.perm.ptr ? S.perm.as<int32_t>() : nullptr;
+}
+
 template <typename XT> inline CycMat<XT> p_mat(const Level &V) {
     const XT *vals;
     if constexpr (sizeof(XT) == 8) vals = reinterpret_cast<const XT *>(V.P.v());
     else vals = V.pv32.as<XT>();
     CycMat<XT> m = make_mat<XT>(V.P, vals);
+    attach_sell<XT>(m, V.psell);
     m.variant = V.variant_p;
     return m;
 }
@@ -169,6 +192,7 @@ template <typename XT> inline CycMat<XT> r_mat(const Level &V) {
     if constexpr (sizeof(XT) == 8) vals = reinterpret_cast<const XT *>(V.R.v());
     else vals = V.rv32.as<XT>();
     CycMat<XT> m = make_mat<XT>(V.R, vals);
+    attach_sell<XT>(m, V.rsell);
     m.variant = V.variant_r;
     return m;
 }

@@ -91,30 +91,41 @@ __device__ __forceinline__ bool row_in_bounds(int32_t p0, int32_t p1, int64_t nn
     return p0 >= 0 && p0 <= p1 && (int64_t)p1 <= nnz;
 }
 
+template <int T>
 __global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int32_t *rp, const int32_t *ci,
                                 const double *v, int32_t *diagpos, int *err) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reductions need every lane
     int e = 0;
-    int32_t dp = -1, prev = -1;
-    int32_t p0 = rp[i], p1 = rp[i + 1];
-    if ((i == 0 && p0 != 0) || (i == n - 1 && (int64_t)p1 != nnz)) e |= kBadRowptr;
-    if (!row_in_bounds(p0, p1, nnz)) {
+    int32_t p0 = 0, p1 = 0;
+    bool inb = false;
+    if (live) {
+        p0 = rp[i];
+        p1 = rp[i + 1];
+        if ((i == 0 && p0 != 0) || (i == n - 1 && (int64_t)p1 != nnz)) e |= kBadRowptr;
+        inb = row_in_bounds(p0, p1, nnz);
+        if (!inb) e |= kBadRowptr;
+    }
+    int32_t dp = -1;
+    if (inb) {
+        for (int32_t p = p0 + t; p < p1; p += T) {
+            const int32_t j = ci[p];
+            if (j < 0 || j >= ncols) { e |= kBadCol; continue; }
+            if (p > p0 && ci[p - 1] >= j) e |= kUnsorted;  // strictly increasing columns
+            if (!isfinite(v[p])) e |= kNonFinite;
+            if (j == i) dp = p;
+        }
+    }
+    dp = (int32_t)group_max_i64<T>((int64_t)dp);  // the diagonal position, if stored (one lane holds it)
+    if (live && t == 0 && inb) {
+        if (dp < 0) e |= kNoDiag;
+        else if (!(f64_key(v[dp]) > 0)) e |= kBadDiag;
+        diagpos[i] = dp;
+    } else if (live && t == 0) {
         diagpos[i] = -1;
-        atomicOr(err, e | kBadRowptr);
-        return;
     }
-    for (int32_t p = p0; p < p1; ++p) {
-        int32_t j = ci[p];
-        if (j < 0 || j >= ncols) { e |= kBadCol; continue; }
-        if (j <= prev) e |= kUnsorted;
-        prev = j;
-        if (!isfinite(v[p])) e |= kNonFinite;
-        if (j == i) dp = p;
-    }
-    if (dp < 0) e |= kNoDiag;
-    else if (!(v[dp] > 0.0)) e |= kBadDiag;
-    diagpos[i] = dp;
     if (e) atomicOr(err, e);
 }
 
@@ -282,14 +293,20 @@ __global__ void interp_count_kernel(int32_t n, const int32_t *rp, const int32_t 
     if (i < n && t == 0) cnt[i] = fpt ? c : 1;
 }
 
-__global__ void interp_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
+// Direct interpolation in two passes.  The row pass forms the row sums in
+// column order and the two ratios (alpha, beta) and the lumped diagonal,
+// and lays out P's pattern with a_ij in place of the weight; the entry pass
+// turns every a_ij into (-alpha a_ij) / d or (-beta a_ij) / d, one entry per
+// thread -- the divisions are the FP64-heavy part, and there every lane of a
+// warp holds a live entry.
+__global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                    const double *v, const uint8_t *strong, const int8_t *cf,
                                    const int32_t *cmap, const int32_t *prp, int32_t *pci,
-                                   double *pv) {
+                                   double *pv, int32_t *prow, double *coef) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int32_t pos = prp[i];
-    if (cf[i] == kC) { pci[pos] = cmap[i]; pv[pos] = 1.0; return; }
+    if (cf[i] == kC) { pci[pos] = cmap[i]; pv[pos] = 1.0; prow[pos] = -1; return; }
     if (prp[i + 1] == pos) return;  // no strong C neighbour: empty row
     double diag = 0.0, sum_neg = 0.0, sum_pos = 0.0, sum_neg_c = 0.0, sum_pos_c = 0.0;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
@@ -305,14 +322,27 @@ __global__ void interp_fill_kernel(int32_t n, const int32_t *rp, const int32_t *
     double beta = 0.0;
     if (f64_key(sum_pos_c) != 0) beta = sum_pos / sum_pos_c;
     else diag = diag + sum_pos;
+    coef[3 * (int64_t)i] = alpha;
+    coef[3 * (int64_t)i + 1] = beta;
+    coef[3 * (int64_t)i + 2] = diag;
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
         if (j == i || !strong[p] || cf[j] != kC) continue;
-        double a = v[p];
         pci[pos] = cmap[j];
-        pv[pos] = f64_key(a) < 0 ? (-alpha * a) / diag : (-beta * a) / diag;
+        pv[pos] = v[p];
+        prow[pos] = i;
         ++pos;
     }
+}
+
+__global__ void interp_weights_kernel(int64_t nnz, const int32_t *prow, const double *coef, double *pv) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    const int32_t i = prow[e];
+    if (i < 0) return;  // C row: weight 1
+    const double a = pv[e];
+    const double c = coef[3 * (int64_t)i + (f64_key(a) < 0 ? 0 : 1)];
+    pv[e] = (-c * a) / coef[3 * (int64_t)i + 2];
 }
 
 // ---------------------------------------------------------------------------
@@ -334,16 +364,59 @@ __global__ void transpose_fill_kernel(int32_t n, const int32_t *rp, const int32_
     }
 }
 
+// Sorts every row of the transpose by column, in place.  A group of W lanes
+// holds a row of up to 4W entries in registers; each entry's rank is the
+// number of smaller columns in the row (columns are distinct), found by
+// broadcasting the row's entries one by one; entries are written back to
+// their ranks.  Longer rows are sorted by one lane (insertion sort).
+template <int W>
 __global__ void sort_rows_kernel(int32_t n, const int32_t *rp, int32_t *ci, double *v) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    for (int32_t p = rp[i] + 1; p < rp[i + 1]; ++p) {
-        int32_t c = ci[p];
-        double x = v[p];
-        int32_t q = p - 1;
-        while (q >= rp[i] && ci[q] > c) { ci[q + 1] = ci[q]; v[q + 1] = v[q]; --q; }
-        ci[q + 1] = c;
-        v[q + 1] = x;
+    constexpr int E = 4;
+    const int sl = threadIdx.x & (W - 1);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / W);
+    const bool live = i < n;
+    int32_t p0 = 0, len = 0;
+    if (live) { p0 = rp[i]; len = rp[i + 1] - p0; }
+    const bool small = len <= E * W;
+    int32_t key[E];
+    double val[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int32_t e = r * W + sl;
+        key[r] = INT_MAX;
+        val[r] = 0.0;
+        if (small && e < len) { key[r] = ci[p0 + e]; val[r] = v[p0 + e]; }
+    }
+    const int32_t m = small ? len : 0;
+    const int32_t mmax = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)m);
+    int32_t rank[E] = {};
+    for (int32_t src = 0; src < mmax; ++src) {  // every entry of the row is broadcast once
+        const int rsrc = src / W;
+        int32_t kv = key[0];
+#pragma unroll
+        for (int r = 1; r < E; ++r)
+            if (rsrc == r) kv = key[r];
+        const int32_t other = __shfl_sync(0xffffffffu, kv, src & (W - 1), W);
+        if (src < m) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) rank[r] += other < key[r];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int32_t e = r * W + sl;
+        if (small && e < len) { ci[p0 + rank[r]] = key[r]; v[p0 + rank[r]] = val[r]; }
+    }
+    if (!small && live && sl == 0) {
+        for (int32_t p = p0 + 1; p < p0 + len; ++p) {
+            int32_t c = ci[p];
+            double x = v[p];
+            int32_t q = p - 1;
+            while (q >= p0 && ci[q] > c) { ci[q + 1] = ci[q]; v[q + 1] = v[q]; --q; }
+            ci[q + 1] = c;
+            v[q + 1] = x;
+        }
     }
 }
 
@@ -892,39 +965,61 @@ __global__ void sparsify_flag_kernel(int32_t n, const int32_t *rp, const int32_t
         flag[p] = (uint8_t)(ci[p] != i && (inM[p] || f64_abs_key(v[p]) >= tk));
 }
 
+template <int T>
 __global__ void sparsify_sym_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                     const double *v, const int32_t *tpos, const uint8_t *flag,
                                     const double *rowmax, uint8_t *keep, uint8_t *guard) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reduction needs every lane
+    int32_t p0 = 0, p1 = 0;
+    if (live) { p0 = rp[i]; p1 = rp[i + 1]; }
     bool any_off = false;
-    double rs = 0.0, ra = 0.0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        bool k = ci[p] == i || flag[p] || flag[tpos[p]];
+    for (int32_t p = p0 + t; p < p1; p += T) {
+        const bool k = ci[p] == i || flag[p] || flag[tpos[p]];
         keep[p] = (uint8_t)k;
         if (k && ci[p] != i) any_off = true;
-        rs += v[p];
-        ra += fabs(v[p]);
     }
-    guard[i] = (uint8_t)(!any_off && f64_key(rowmax[i]) > 0 && f64_abs_key(rs) <= f64_key(1e-12 * ra));
+    any_off = group_any<T>(any_off);
+    if (!live || t != 0) return;
+    // Algorithm 3b guard, for rows left with no off-diagonal entry: the row
+    // sums (in column order) are only needed there
+    bool gd = false;
+    if (!any_off && f64_key(rowmax[i]) > 0) {
+        double rs = 0.0, ra = 0.0;
+        for (int32_t p = p0; p < p1; ++p) {
+            rs += v[p];
+            ra += fabs(v[p]);
+        }
+        gd = f64_abs_key(rs) <= f64_key(1e-12 * ra);
+    }
+    guard[i] = (uint8_t)gd;
 }
 
+template <int T>
 __global__ void sparsify_guard_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                       const double *v, const int32_t *tpos, const uint8_t *guard,
                                       const double *rowmax, uint8_t *keep, int32_t *cnt) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reduction needs every lane
+    int32_t p0 = 0, p1 = 0;
+    if (live) { p0 = rp[i]; p1 = rp[i + 1]; }
+    const bool gi = live && guard[i];
     int32_t c = 0;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        int32_t j = ci[p];
+    for (int32_t p = p0 + t; p < p1; p += T) {
+        const int32_t j = ci[p];
         if (!keep[p] && j != i) {
-            if ((guard[i] && f64_abs_key(v[p]) == f64_key(rowmax[i])) ||
+            if ((gi && f64_abs_key(v[p]) == f64_key(rowmax[i])) ||
                 (guard[j] && f64_abs_key(v[tpos[p]]) == f64_key(rowmax[j])))
                 keep[p] = 1;
         }
         c += keep[p];
     }
-    cnt[i] = c;
+    c = group_sum_i32<T>(c);
+    if (live && t == 0) cnt[i] = c;
 }
 
 __global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
@@ -1060,8 +1155,12 @@ void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s
     TmpBuf err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
     if (A.nrows > 0) {
-        { validate_kernel<<<div_up(A.nrows, kThreads), kThreads, 0, s>>>(
-            A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(), diagpos, err.as<int>()); ::amg::count_launch(); }
+        with_row_lanes(row_lanes(A), [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            validate_kernel<L><<<div_up((int64_t)A.nrows * L, kThreads), kThreads, 0, s>>>(
+                A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(), diagpos, err.as<int>());
+            ::amg::count_launch();
+        });
         if (A.nrows == A.ncols)
             with_row_lanes(row_lanes(A), [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
@@ -1229,9 +1328,14 @@ void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, con
     P.val.alloc(sizeof(double) * (nnz + kPad));
     AMG_CUDA(cudaMemsetAsync(P.ci() + nnz, 0, sizeof(int32_t) * kPad, s));  // the fill writes rows [0, nnz)
     AMG_CUDA(cudaMemsetAsync(P.v() + nnz, 0, sizeof(double) * kPad, s));
-    if (n > 0)
-        { interp_fill_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), strong, cf, cmap, P.rp(),
-                                                  P.ci(), P.v()); ::amg::count_launch(); }
+    if (n > 0) {
+        TmpBuf prow(sizeof(int32_t) * (nnz + 1), s), coef(sizeof(double) * 3 * (size_t)n, s);
+        { interp_rows_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), strong, cf, cmap, P.rp(), P.ci(),
+                                                  P.v(), prow.as<int32_t>(), coef.as<double>()); ::amg::count_launch(); }
+        if (nnz > 0)
+            { interp_weights_kernel<<<div_up(nnz, kThreads), kThreads, 0, s>>>(nnz, prow.as<int32_t>(),
+                                                                             coef.as<double>(), P.v()); ::amg::count_launch(); }
+    }
     AMG_CHECK_LAUNCH();
 }
 
@@ -1254,7 +1358,16 @@ void transpose(const DevCSR &M, DevCSR &T, cudaStream_t s) {
     if (M.nrows > 0)
         { transpose_fill_kernel<<<div_up(M.nrows, kThreads), kThreads, 0, s>>>(
             M.nrows, M.rp(), M.ci(), M.v(), fill.as<int32_t>(), T.ci(), T.v()); ::amg::count_launch(); }
-    if (m > 0) { sort_rows_kernel<<<div_up(m, kThreads), kThreads, 0, s>>>(m, T.rp(), T.ci(), T.v()); ::amg::count_launch(); }
+    if (m > 0) {
+        const double mean = (double)nnz / (double)m;
+        int W = 2;
+        while (W < 32 && (double)W < mean) W <<= 1;
+        with_row_lanes(W, [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            sort_rows_kernel<L><<<div_up((int64_t)m * L, kThreads), kThreads, 0, s>>>(m, T.rp(), T.ci(), T.v());
+            ::amg::count_launch();
+        });
+    }
     AMG_CHECK_LAUNCH();
 }
 
@@ -1436,10 +1549,16 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
                 n, A.rp(), A.ci(), A.v(), inM, gamma, rowmax.as<double>(), flag.as<uint8_t>());
             ::amg::count_launch();
         });
-        { sparsify_sym_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, flag.as<uint8_t>(),
-                                                   rowmax.as<double>(), keep, guard.as<uint8_t>()); ::amg::count_launch(); }
-        { sparsify_guard_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, guard.as<uint8_t>(),
-                                                     rowmax.as<double>(), keep, cnt.as<int32_t>()); ::amg::count_launch(); }
+        with_row_lanes(row_lanes(A), [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            const int gl = div_up((int64_t)n * L, kThreads);
+            sparsify_sym_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, flag.as<uint8_t>(),
+                                                           rowmax.as<double>(), keep, guard.as<uint8_t>());
+            ::amg::count_launch();
+            sparsify_guard_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, guard.as<uint8_t>(),
+                                                             rowmax.as<double>(), keep, cnt.as<int32_t>());
+            ::amg::count_launch();
+        });
         AMG_CHECK_LAUNCH();
     }
     H.rowptr.alloc(sizeof(int32_t) * (n + 1));
@@ -1449,8 +1568,8 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
     H.nnz = nnz;
     H.col.alloc(sizeof(int32_t) * (nnz + kPad));
     H.val.alloc(sizeof(double) * (nnz + kPad));
-    AMG_CUDA(cudaMemsetAsync(H.col.ptr, 0, H.col.bytes, s));
-    AMG_CUDA(cudaMemsetAsync(H.val.ptr, 0, H.val.bytes, s));
+    AMG_CUDA(cudaMemsetAsync(H.ci() + nnz, 0, sizeof(int32_t) * kPad, s));  // the compaction writes [0, nnz)
+    AMG_CUDA(cudaMemsetAsync(H.v() + nnz, 0, sizeof(double) * kPad, s));
     if (n > 0) {
         { sparsify_compact_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(),
                                                        H.ci(), H.v()); ::amg::count_launch(); }
