@@ -746,7 +746,6 @@ static int hybrid_pattern(orc_hier *h, int32_t l, uint8_t *inM) {
 /* (Re)build Ahat_l from the retained A_l at the level's gamma; method 1
  * (Hybrid) takes M from the current Ahat_{l-1}. */
 static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method);
-static int resparsify_level(orc_hier *h, int32_t l) { return resparsify_level_m(h, l, 0); }
 
 static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method) {
     orc_level *L = &h->lev[l];
@@ -1019,11 +1018,17 @@ int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int3
                 status = -cnt;
                 break;
             }
-            if (cnt == 0 && breakdown) break;
+            /* a restart, or a final breakdown, goes back to the checkpoint
+               whenever the residual did not decrease -- a non-finite residual
+               included (!(rend <= rstart) holds for NaN) */
+            if (cnt == 0 && breakdown) {
+                if (!(rend <= rstart)) memcpy(x, xs, sizeof(double) * (size_t)n);
+                break;
+            }
             if (cnt > 0) {
                 info->resets++;
                 breakdown = 0;
-                if (rend > rstart) {
+                if (!(rend <= rstart)) {
                     memcpy(x, xs, sizeof(double) * (size_t)n);
                     rend = rstart;
                 }

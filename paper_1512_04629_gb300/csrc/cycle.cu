@@ -392,12 +392,16 @@ xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restri
                  double *__restrict__ r, const PcgScalars *sc, Reduce red, const double *__restrict__ dinv0,
                  double *__restrict__ x0) {
     block_partials_begin();
-    double alpha = sc->alpha;
+    const double alpha = sc->alpha;
+    const bool step = alpha != 0.0;  // 0: breakdown -- x and r stay as they are
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        x[i] += alpha * p[i];
-        double ri = r[i] - alpha * q[i];
-        r[i] = ri;
+        double ri = r[i];
+        if (step) {
+            x[i] += alpha * p[i];
+            ri -= alpha * q[i];
+            r[i] = ri;
+        }
         if (x0) x0[i] = ri * dinv0[i];  // the next cycle's level-0 pre-smooth from zero
         part[0] += ri * ri;
     }

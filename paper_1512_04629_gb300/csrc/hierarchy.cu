@@ -958,11 +958,17 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
             double factor = run.steps > 0 ? std::pow(rend / rstart, 1.0 / run.steps) : 1.0;
             if (factor > h.opt.rho_max || breakdown) {
                 int cnt = reintroduce(h, sl, s);
-                if (cnt == 0 && breakdown) break;
+                // back to the checkpoint whenever the residual did not
+                // decrease (a non-finite residual included)
+                const bool back = !(rend <= rstart);
+                if (cnt == 0 && breakdown) {
+                    if (back) AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    break;
+                }
                 if (cnt > 0) {
                     info->resets++;
                     breakdown = false;
-                    if (rend > rstart) {
+                    if (back) {
                         AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
                         rend = rstart;
                     }

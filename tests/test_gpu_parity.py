@@ -218,6 +218,23 @@ def test_adaptive_matches_oracle(amg, use_graph):
         assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
 
 
+def test_adaptive_large_converges(amg):
+    """Algorithm 5 on the 128^3 benchmark problem from gamma = 1: every check
+    that reintroduces entries lowers one level's tolerance, the solve
+    converges and the iterate stays finite (a breakdown leaves x untouched
+    and a restart falls back to the checkpoint)."""
+    A = gen.poisson3d_7pt(128)
+    b = gen.rhs_uniform(A.n, 1)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0])
+    x, info = h.solve(b, tol=1e-8, adaptive=True)
+    assert np.isfinite(x).all()
+    assert info.status == 0 and info.final_relres <= 1e-8, info.as_dict()
+    gam = [h.level_stats(l)["gamma"] for l in range(h.num_levels)]
+    # each reset moved one level one step down the schedule 1 -> 0.1 -> 0.01 -> 0
+    steps = sum({1.0: 0, 0.1: 1, 0.01: 2, 0.0: 3}[round(g, 12)] for g in gam[1:])
+    assert steps == info.resets
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_mixed_precision_reaches_fp64_tolerance(amg, prec):
     A = gen.poisson3d_27pt(14)
