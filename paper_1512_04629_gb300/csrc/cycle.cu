@@ -614,11 +614,14 @@ __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     int32_t off = soff[s] + lane, w = sw[s];
     int32_t i = pos < n ? (perm ? perm[pos] : pos) : -1;
     int32_t p0 = i >= 0 ? rp[i] : 0, len = i >= 0 ? rp[i + 1] - p0 : 0;
-    int32_t self = i >= 0 ? i : 0;
+    // padding: value 0 at a column the row itself holds (its last one), or
+    // column 0 for an empty row -- always inside x, also for rectangular
+    // operators (P is n x n_c)
+    const int32_t pad_col = len > 0 ? ci[p0 + len - 1] : 0;
     for (int32_t k = 0; k < w; ++k) {
         int32_t p = off + k * 32;
         if (k < len) { sci[p] = ci[p0 + k]; sv[p] = v[p0 + k]; }
-        else { sci[p] = self; sv[p] = VT(0); }
+        else { sci[p] = pad_col; sv[p] = VT(0); }
     }
 }
 
