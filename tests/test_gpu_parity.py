@@ -218,6 +218,27 @@ def test_adaptive_matches_oracle(amg, use_graph):
         assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
 
 
+def test_reintroduce_equals_fresh_setup(amg):
+    """Reintroducing entries level by level leaves the hierarchy a fresh setup
+    with the resulting tolerances would build: the same operators and, to the
+    bit, the same PCG iterate -- with the CUDA graph and without it."""
+    A = gen.poisson3d_7pt(64)
+    b = gen.rhs_uniform(A.n, 3)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0])
+    for _ in range(5):
+        assert h.reintroduce(1) == 1
+        gam = [h.level_stats(l)["gamma"] for l in range(h.num_levels)]
+        x1, i1 = h.solve(b, tol=1e-8)
+        assert i1.status == 0
+        for use_graph in (1, 0):
+            hf = amg.Hierarchy.setup(A, gamma=[0.0] + gam[1:], use_graph=use_graph)
+            for l in range(h.num_levels):
+                _same_csr(h.export(l, "Ahat"), hf.export(l, "Ahat"), rtol=0.0, what=f"Ahat_{l}")
+            x2, i2 = hf.solve(b, tol=1e-8)
+            assert i2.iterations == i1.iterations
+            np.testing.assert_array_equal(x1, x2)
+
+
 def test_adaptive_large_converges(amg):
     """Algorithm 5 on the 128^3 benchmark problem from gamma = 1: every check
     that reintroduces entries lowers one level's tolerance, the solve
