@@ -131,6 +131,28 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+# FP64 pipe of a GB300: one FP64 warp instruction per 16 clocks per SM, i.e. 2 FMA per clock per SM
+# (measured 2.00 with a DFMA throughput probe); peak = 2 x 152 SMs x the sampled SM clock.
+FP64_FMA_PER_CLK_SM = 2.0
+GB300_SMS = 152
+
+
+def fp64_ops_per_launch(kind, level, n, nnz, precision):
+    """FP64 lane operations (FMA / add / mul, one each) of one launch of a solve-phase kernel class,
+    counted from the arithmetic each kernel performs per stored entry and per row."""
+    if precision != "fp64" and kind not in ("pcg_Ap_dot", "pcg_vector"):
+        return None
+    if kind == "relax_pre_residual":
+        return nnz + n                      # s = A x; r = b - s
+    if kind == "relax_post":
+        return nnz + (4 if level == 0 else 2) * n   # x + d (b - s); level 0 adds r.z and z.q
+    if kind == "pcg_Ap_dot":
+        return nnz + n                      # q = A p; p.q
+    if kind == "pcg_vector":
+        return 4 * n                        # x += a p; r -= a q; x0 = d r; r.r
+    return None
+
+
 def ncu_traffic():
     """Per-launch DRAM bytes of kernels captured with ncu (profiles/)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
@@ -540,8 +562,24 @@ def main():
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": per_launch_bytes, "avg_launch_ms": avg_ms,
                 "launches": dom["launches"]}
+    # the second ceiling of these kernels: the FP64 pipe (GB300 has 2 FP64 FMA per clock per SM)
+    lv = levels[dom_key[1]]
+    ops = fp64_ops_per_launch(dom_key[0], dom_key[1], lv["n"], lv["nnz_operator"] if dom_key[1] > 0 else lv["nnz_galerkin"],
+                              "fp64")
+    if ops is not None:
+        clk = (clocks or {}).get("sm_mhz") or 2070.0
+        fpeak = FP64_FMA_PER_CLK_SM * GB300_SMS * clk * 1e6 / 1e12
+        fach = ops / (avg_ms * 1e-3) / 1e12
+        roofline["fp64"] = {"ops_per_launch": ops, "achieved": fach, "peak": fpeak, "unit": "Tops/s",
+                            "frac": fach / fpeak,
+                            "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x sampled SM clock"}
     vcycle_ms = sum(v["ms"] for k, v in timings.items() if k[0] not in ("pcg_Ap_dot", "pcg_vector"))
     vcycle_bytes = sum(v["bytes"] for k, v in timings.items() if k[0] not in ("pcg_Ap_dot", "pcg_vector"))
+    per_level_ms = {}
+    for (kind, lv), v in timings.items():
+        per_level_ms[lv] = per_level_ms.get(lv, 0.0) + v["ms"]
+    steps_timed = max(1, min(args.steps, 5))
+    per_level_ms = {f"L{lv}": round(ms / steps_timed, 3) for lv, ms in sorted(per_level_ms.items())}
     kernels = sorted(({"kernel": f"{k[0]} L{k[1]}", "launches": v["launches"], "ms": round(v["ms"], 4),
                        "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 else None}
                       for k, v in timings.items()), key=lambda r: -r["ms"])[:12]
@@ -617,7 +655,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
         "iterations": statistics.median(its), "levels": levels,
         "roofline": roofline, "vcycle_GBps": vcycle_bytes / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms else None,
-        "top_kernels": kernels, "setup_phases_ms": _median_phases(setup_phases), "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "clocks": clocks,
+        "top_kernels": kernels, "solve_ms_per_level": per_level_ms, "setup_phases_ms": _median_phases(setup_phases), "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "clocks": clocks,
         "gpu_launches": launches,
     }
     print(json.dumps(line))

@@ -189,12 +189,16 @@ enum : int8_t { kU = 0, kC = 1, kF = -1 };
 
 __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tpos,
                                  const uint8_t *strong, uint64_t seed, int32_t level, double *w,
-                                 int8_t *state, int *undecided) {
+                                 int8_t *state, int *undecided, uint8_t *sym) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     int add = 0;
     if (i < n) {
         int32_t cnt = 0;  // |S^T_i|: rows j whose strong set holds i
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) cnt += strong[tpos[p]];
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+            const uint8_t st = strong[tpos[p]];
+            cnt += st;
+            sym[p] = (uint8_t)(st | strong[p]);  // j in S_i u S^T_i, read by every round
+        }
         uint64_t key = seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)i;
         double u = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
         w[i] = (double)cnt + u;
@@ -210,7 +214,7 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
 // does nothing once it is zero.
 template <int T>
 __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                   const int32_t *tpos, const uint8_t *strong, const double *w,
+                                   const uint8_t *sym, const double *w,
                                    const int8_t *state, uint8_t *newc, const int *prev) {
     if (*prev == 0) return;  // the same for the whole grid
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -222,7 +226,7 @@ __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *
         // weights are >= 0: their bit patterns order like the values
         const int64_t wi = __double_as_longlong(w[i]);
         for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
-            if (!(strong[p] || strong[tpos[p]])) continue;  // S_i u S^T_i
+            if (!sym[p]) continue;  // S_i u S^T_i
             const int32_t j = ci[p];
             if (state[j] != kU) continue;
             const int64_t wj = __double_as_longlong(w[j]);
@@ -753,6 +757,10 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
     for (int32_t s = lane; s < hs; s += 32) t.keys[s] = -1;
     __syncwarp();
     const int32_t p0 = arp[i], nA = arp[i + 1] - p0;
+    // Long rows of B (12 or more products per entry of A's row on average):
+    // one round per k, the lanes covering B_k -- columns within a round are
+    // distinct, so no matching is needed and rounds follow k's order.
+    const bool per_k = ub >= 12 * (int64_t)nA;
     int32_t uniq = 0;
     for (int32_t c0 = 0; c0 < nA; c0 += 32) {
         const int32_t idx = c0 + lane;
@@ -763,6 +771,34 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
             if (NUMERIC) a = av[p0 + idx];
             b0 = brp[k];
             len = brp[k + 1] - b0;
+        }
+        if (per_k) {
+            const int kend = min(32, nA - c0);
+            for (int kk = 0; kk < kend; ++kk) {
+                const int32_t kb0 = __shfl_sync(kFull, b0, kk), klen = __shfl_sync(kFull, len, kk);
+                const double ka = __shfl_sync(kFull, a, kk);
+                for (int32_t e0 = 0; e0 < klen; e0 += 32) {
+                    const int32_t e = e0 + lane;
+                    if (e < klen) {
+                        const int32_t j = bci[kb0 + e];
+                        uint32_t sl = hash32(j) & mask;
+                        bool fresh = false;
+                        while (true) {
+                            const int32_t old = atomicCAS(&t.keys[sl], -1, j);
+                            if (old == -1) { fresh = true; break; }
+                            if (old == j) break;
+                            sl = (sl + 1) & mask;
+                        }
+                        uniq += fresh;
+                        if (NUMERIC) {
+                            const double prod = ka * bv[kb0 + e];
+                            t.val[sl] = fresh ? f64_zero_plus(prod) : t.val[sl] + prod;
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            continue;
         }
         int32_t incl = len;
 #pragma unroll
@@ -1244,13 +1280,13 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     }
     constexpr int kBatch = 4, kMaxRounds = 10000;
     // cnt[0]: undecided after the initial split; cnt[r]: after round r
-    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s);
+    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s), sym(A.nnz + 1, s);
     int *dc = cnt.as<int>();
     int g = div_up(n, kThreads);
     const int T = row_lanes(A, 8);  // later rounds find most rows decided: keep the grid small
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
-                                            cf, dc); ::amg::count_launch(); }
+                                            cf, dc, sym.as<uint8_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     int done = 0;  // rounds launched
     int last = -1; // undecided count before the current batch (-1: not read yet)
@@ -1261,8 +1297,8 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
             with_row_lanes(T, [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
                 const int gl = div_up((int64_t)n * L, kThreads);
-                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), tpos, strong, w.as<double>(), cf,
-                                                              newc.as<uint8_t>(), dc + r - 1);
+                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(),
+                                                              cf, newc.as<uint8_t>(), dc + r - 1);
                 ::amg::count_launch();
                 pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf, dc + r - 1);
                 ::amg::count_launch();
