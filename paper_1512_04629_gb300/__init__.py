@@ -7,5 +7,5 @@ from .amg import (  # noqa: F401
     AmgError, Hierarchy, Matrix, Server, SolveInfo, default_options, device_bytes, kernel_launches, lib,
     METHOD_SPARSE, METHOD_HYBRID, PREC_FP64, PREC_FP32, PREC_FP32_BF16,
     SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_NAMES,
-    K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC, K_TAIL,
+    K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC,
 )
