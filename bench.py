@@ -228,7 +228,7 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 KIND_NAMES = {0: "relax_pre_residual", 1: "restrict", 2: "prolong", 3: "relax_post", 4: "coarse_solve",
-              5: "pcg_Ap_dot", 6: "pcg_vector", 7: "coarse_tail"}
+              5: "pcg_Ap_dot", 6: "pcg_vector"}
 SETUP_KIND_NAMES = {8: "strength", 9: "cf_split", 10: "interpolation", 11: "galerkin_spgemm",
                     12: "level_maps_minimal_pattern", 13: "sparsify", 14: "cycle_prep", 15: "coarse_cholesky"}
 
@@ -249,7 +249,7 @@ def aggregate_replicas(elapsed_s: float, steps: int, dist=None, device=None):
 
 def collect_timing(h, nlev):
     rows = []
-    for kind in range(8):
+    for kind in range(7):
         for l in range(nlev):
             n, ms, by = h.timing_get(kind, l)
             if n:

@@ -210,9 +210,8 @@ amg_status amg_level_array(const amg_hierarchy *h, int level, int which, void *o
 /* Per-kernel timing with CUDA events on the solve stream (off by default).
  * amg_timing_get returns, for kernel class `kind` (0 fused pre-smooth +
  * residual, 1 restrict, 2 prolong, 3 post-smooth, 4 coarse solve, 5 PCG
- * A p + dot, 6 PCG vector update, 7 the fused coarse end of the cycle -- all
- * levels from `level` down in one launch) on `level`, the number of timed
- * launches, their total milliseconds and their algorithmic bytes.  With
+ * A p + dot, 6 PCG vector update) on `level`, the number of timed launches,
+ * their total milliseconds and their algorithmic bytes.  With
  * amg_options.setup_timing, or while timing is enabled during amg_sparsify /
  * amg_reintroduce, the setup phases are recorded too (bytes 0): 8 strength,
  * 9 C/F splitting (PMIS and the coarse numbering), 10 interpolation P and

@@ -23,7 +23,7 @@ PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_CSR1 = -1, 1, 2, 3, 4, 5, 6, 7
 SPMV_NAMES = {1: "csr2", 2: "csr4", 3: "csr8", 4: "csr16", 5: "csr32", 6: "sell32", 7: "csr1"}
 # kernel classes of amg_timing_get
-K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC, K_TAIL = range(8)
+K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC = range(7)
 
 
 class AmgError(RuntimeError):

@@ -33,7 +33,7 @@ struct PcgScalars {
     int its;         // CG steps taken
     int max_its;     // the graph loop stops at this count
     int breakdown;   // p.Ap <= 0 or r.z <= 0 was met
-    int tail_err;    // a grid-barrier wait of the fused coarse end ran out
+    int pad;
 };
 
 // Deterministic reduction workspace: per-block partials + arrival counter.

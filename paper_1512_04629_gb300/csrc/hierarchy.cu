@@ -538,71 +538,6 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
     cudaEventDestroy(e1);
 }
 
-// ---------------------------------------------------------------------------
-// coarse end of the cycle in one cooperative launch (tail.cu)
-// ---------------------------------------------------------------------------
-constexpr int32_t kTailRows = 32768;  // levels at or below this size join the fused coarse end
-
-template <typename VT, typename XT> static void fill_tail(Hierarchy &h, cudaStream_t s) {
-    const int L = h.nlev(), nl = L - h.tail_from;
-    std::vector<TailLevel<VT, XT>> d(nl);
-    for (int k = 0; k < nl; ++k) {
-        Level &V = *h.lev[h.tail_from + k];
-        CycMat<VT> a = op_mat<VT>(V);
-        TailLevel<VT, XT> &t = d[k];
-        t = TailLevel<VT, XT>{};
-        t.n = V.n();
-        t.rp = a.rp; t.ci = a.ci; t.v = a.v;
-        if (k + 1 < nl) {
-            CycMat<XT> p = p_mat<XT>(V), r = r_mat<XT>(V);
-            t.prp = p.rp; t.pci = p.ci; t.pv = p.v;
-            t.rrp = r.rp; t.rci = r.ci; t.rv = r.v;
-        }
-        t.dinv = dinv_of<XT>(V);
-        t.b = V.b.as<XT>(); t.x = V.x.as<XT>(); t.r = V.r.as<XT>(); t.xo = V.xo.as<XT>();
-    }
-    h.tail_desc.alloc(sizeof(TailLevel<VT, XT>) * nl);
-    AMG_CUDA(cudaMemcpyAsync(h.tail_desc.ptr, d.data(), sizeof(TailLevel<VT, XT>) * nl, cudaMemcpyHostToDevice, s));
-    AMG_CUDA(cudaStreamSynchronize(s));  // d is a host temporary
-    h.tail_grid = cyc::tail_grid<VT, XT>();
-}
-
-static void build_tail(Hierarchy &h, cudaStream_t s) {
-    h.tail_from = -1;
-    const int L = h.nlev();
-    const char *off = std::getenv("AMG_NO_TAIL");
-    if (L < 3 || (off && off[0] == '1')) return;
-    int from = L - 1;
-    while (from > 1 && h.lev[from - 1]->n() <= kTailRows) --from;
-    // one value type on every fused level (BF16 mode keeps level 1 in FP32)
-    while (from < L - 1 && h.lev[from]->vbytes != h.lev[L - 1]->vbytes) ++from;
-    if (L - from < 2) return;  // the coarsest level alone: nothing to fuse
-    h.tail_from = from;
-    if (!h.tail_state.ptr) {
-        h.tail_state.alloc(64);
-        AMG_CUDA(cudaMemsetAsync(h.tail_state.ptr, 0, 64, s));
-    }
-    const int vb = h.lev[L - 1]->vbytes;
-    if (h.opt.precision == AMG_PREC_FP64) fill_tail<double, double>(h, s);
-    else if (vb == 4) fill_tail<float, float>(h, s);
-    else fill_tail<__nv_bfloat16, float>(h, s);
-}
-
-template <typename XT> static void run_tail(Hierarchy &h, cudaStream_t s) {
-    const int L = h.nlev(), nl = L - h.tail_from;
-    TailSync sync{h.tail_state.as<unsigned>(), h.tail_state.as<unsigned>() + 1, &h.dscal()->tail_err};
-    if constexpr (sizeof(XT) == 8) {
-        cyc::tail_cycle<double, double>(h.tail_desc.as<TailLevel<double, double>>(), nl, h.coarse_inv.as<double>(),
-                                        h.coarse_n, sync, h.tail_grid, s);
-    } else if (h.lev[L - 1]->vbytes == 4) {
-        cyc::tail_cycle<float, float>(h.tail_desc.as<TailLevel<float, float>>(), nl, h.coarse_inv.as<double>(),
-                                      h.coarse_n, sync, h.tail_grid, s);
-    } else {
-        cyc::tail_cycle<__nv_bfloat16, float>(h.tail_desc.as<TailLevel<__nv_bfloat16, float>>(), nl,
-                                              h.coarse_inv.as<double>(), h.coarse_n, sync, h.tail_grid, s);
-    }
-}
-
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
     for (int l : levels) {
         timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, s); });
@@ -618,7 +553,6 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
             h.lev[l]->pr_tuned = true;
         }
     }
-    build_tail(h, s);
     h.graph_dirty = true;
     h.version++;
     AMG_CUDA(cudaStreamSynchronize(s));
@@ -729,9 +663,7 @@ static bool vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s, cons
               [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), b0, z0, s); });
         return false;
     }
-    // levels from Lt on run as one fused launch (the coarse end)
-    const int Lt = h.tail_from >= 1 ? h.tail_from : L - 1;
-    for (int l = 0; l < Lt; ++l) {
+    for (int l = 0; l + 1 < L; ++l) {
         Level &V = *h.lev[l];
         const XT *b = l == 0 ? b0 : V.b.as<XT>();
         relax_pre<XT>(h, l, b, s, l > 0 || ctl.x0_ready);
@@ -745,16 +677,10 @@ static bool vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s, cons
                   [&] { cyc::spmv<XT, XT>(r_mat<XT>(V), V.r.as<XT>(), C.b.as<XT>(), false, s); });
         }
     }
-    if (Lt < L - 1) {
-        double tb = (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb;
-        for (int l = Lt; l + 1 < L; ++l) tb += level_cycle_bytes(h, l);
-        timed(h, 7, Lt, tb, s, [&] { run_tail<XT>(h, s); });
-    } else {
-        Level &Cl = *h.lev[L - 1];
-        timed(h, 4, L - 1, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,
-              [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), Cl.b.as<XT>(), Cl.xo.as<XT>(), s); });
-    }
-    for (int l = Lt - 1; l >= 0; --l) {
+    Level &Cl = *h.lev[L - 1];
+    timed(h, 4, L - 1, (double)h.coarse_n * h.coarse_n * 8 + 2.0 * h.coarse_n * xb, s,
+          [&] { cyc::coarse_solve<XT>(h.coarse_n, h.coarse_inv.as<double>(), Cl.b.as<XT>(), Cl.xo.as<XT>(), s); });
+    for (int l = L - 2; l >= 0; --l) {
         Level &V = *h.lev[l];
         Level &C = *h.lev[l + 1];
         timed(h, 2, l, bytes_prolong(V.n(), V.P.ncols, V.P.nnz, xb, xb), s,
@@ -975,7 +901,6 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
             }
         }
         const PcgScalars &sc = *h.h_scal;
-        if (sc.tail_err) tail_failed(h, s);
         run.steps += sc.its;
         if (sc.breakdown || !std::isfinite(sc.rr)) { run.breakdown = true; return; }
         run.rnorm = std::sqrt(sc.rr);
@@ -989,26 +914,6 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
     }
 }
 }  // namespace
-
-// the fused coarse end reports a grid-barrier wait that ran out through the
-// PCG scalars; the cycle's result is then invalid
-void check_tail(Hierarchy &h, cudaStream_t s) {
-    int e = 0;
-    if (h.tail_from >= 1) {
-        AMG_CUDA(cudaMemcpyAsync(&e, &h.dscal()->tail_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    }
-    AMG_CUDA(cudaStreamSynchronize(s));
-    if (e) tail_failed(h, s);
-}
-
-// after a timed-out barrier: clear the flag and the arrival count (blocks may
-// have left mid-barrier) so the next launch starts clean, then report
-void tail_failed(Hierarchy &h, cudaStream_t s) {
-    if (h.tail_state.ptr) cudaMemsetAsync(h.tail_state.ptr, 0, h.tail_state.bytes, s);
-    if (h.scal.ptr) cudaMemsetAsync(&h.dscal()->tail_err, 0, sizeof(int), s);
-    cudaStreamSynchronize(s);
-    throw Error(AMG_ERR_CUDA, "coarse-level cycle kernel: a grid barrier wait timed out");
-}
 
 amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int max_it, bool adaptive,
                  cudaStream_t s, amg_solve_info *info) {

@@ -9,7 +9,6 @@
 #include "batch_ops.cuh"
 #include "common.cuh"
 #include "cycle_ops.cuh"
-#include "tail_ops.cuh"
 
 namespace amg {
 
@@ -102,11 +101,6 @@ struct BatchWS {
 struct Hierarchy {
     IdleRelease idle_release;  // first member: destroyed after every buffer below
     amg_options opt{};
-    // coarse end of the cycle in one cooperative launch: levels tail_from ..
-    // nlev-1 (tail_from < 1: off); descriptor array and barrier state
-    int tail_from = -1;
-    int tail_grid = 0;
-    DevBuf tail_desc, tail_state;
     int device = 0;
     std::vector<std::unique_ptr<Level>> lev;
     DevBuf coarse_inv;  // FP64 dense inverse of the coarsest relaxed operator
@@ -230,8 +224,6 @@ bool vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s, const 
 amg_status solve(Hierarchy &h, const double *b_dev, double *x_dev, double tol, int max_it, bool adaptive,
                  cudaStream_t s, amg_solve_info *info);
 void timing_collect(Hierarchy &h);
-void check_tail(Hierarchy &h, cudaStream_t s);
-[[noreturn]] void tail_failed(Hierarchy &h, cudaStream_t s);
 
 // multi-right-hand-side solves (batch_driver.cu)
 BatchWS &batch_workspace(Hierarchy &h, int K, cudaStream_t s);

@@ -218,34 +218,6 @@ def test_adaptive_matches_oracle(amg, use_graph):
         assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
 
 
-def test_fused_coarse_end_matches_per_level_kernels(amg, monkeypatch):
-    """The single-launch coarse end computes the same V-cycle as the
-    per-level kernels (only the summation order inside a row differs)."""
-    A = gen.poisson3d_7pt(48)
-    b = gen.rhs_uniform(A.n, 4)
-    for prec in (0, 1, 2):
-        monkeypatch.delenv("AMG_NO_TAIL", raising=False)
-        h1 = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=prec)
-        monkeypatch.setenv("AMG_NO_TAIL", "1")
-        h2 = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=prec)
-        monkeypatch.delenv("AMG_NO_TAIL")
-        assert h1.num_levels >= 4
-        x1, i1 = h1.solve(b, tol=1e-8)
-        x2, i2 = h2.solve(b, tol=1e-8)
-        assert i1.status == 0 and i2.status == 0
-        assert abs(i1.iterations - i2.iterations) <= 1
-        tol = 1e-9 if prec == 0 else 1e-6
-        assert np.linalg.norm(x1 - x2) <= tol * np.linalg.norm(x2)
-        # the preconditioner itself, applied once
-        import torch
-        r = torch.from_numpy(gen.rhs_uniform(A.n, 5)).cuda()
-        z1, z2 = torch.empty_like(r), torch.empty_like(r)
-        h1.precond_apply(r, z1)
-        h2.precond_apply(r, z2)
-        rel = (torch.linalg.norm(z1 - z2) / torch.linalg.norm(z2)).item()
-        assert rel <= (1e-12 if prec == 0 else 1e-5), (prec, rel)
-
-
 def test_reintroduce_equals_fresh_setup(amg):
     """Reintroducing entries level by level leaves the hierarchy a fresh setup
     with the resulting tolerances would build: the same operators and, to the
@@ -305,20 +277,10 @@ def test_timing_counters(amg):
     h.timing_enable(True)
     x, info = h.solve(gen.rhs_uniform(A.n, 1))
     assert info.status == 0
-    # the coarse end of the cycle (if fused) is one launch timed at its first level
-    tails = [l for l in range(h.num_levels) if h.timing_get(amg.K_TAIL, l)[0] > 0]
-    assert len(tails) <= 1
-    first_fused = tails[0] if tails else h.num_levels - 1
-    if tails:
-        n, ms, by = h.timing_get(amg.K_TAIL, first_fused)
-        assert n == info.iterations and ms > 0 and by > 0
     for kind in (amg.K_PRE, amg.K_POST, amg.K_RESTRICT, amg.K_PROLONG):
         for l in range(h.num_levels - 1):
             n, ms, by = h.timing_get(kind, l)
-            if l < first_fused:
-                assert n == info.iterations and ms > 0 and by > 0
-            else:
-                assert n == 0
+            assert n == info.iterations and ms > 0 and by > 0
     n, ms, by = h.timing_get(amg.K_AP, 0)
     assert n == info.iterations
     h.timing_reset()
