@@ -759,8 +759,11 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
     const int32_t p0 = arp[i], nA = arp[i + 1] - p0;
     // Long rows of B (12 or more products per entry of A's row on average):
     // one round per k, the lanes covering B_k -- columns within a round are
-    // distinct, so no matching is needed and rounds follow k's order.
-    const bool per_k = ub >= 12 * (int64_t)nA;
+    // distinct, so no matching is needed and rounds follow k's order.  Only
+    // for the smaller table: with the large one a warp's shared memory limits
+    // residency to a quarter, and the extra rounds' latency then dominates
+    // (measured slower).
+    const bool per_k = U <= 128 && ub >= 12 * (int64_t)nA;
     int32_t uniq = 0;
     for (int32_t c0 = 0; c0 < nA; c0 += 32) {
         const int32_t idx = c0 + lane;
