@@ -7,10 +7,6 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
-#include <thread>
-#include <exception>
-#include <deque>
-#include <condition_variable>
 #include <map>
 #include <mutex>
 
@@ -44,7 +40,6 @@ Hierarchy::~Hierarchy() {
 // per-kernel timing with events on the launching stream
 // ---------------------------------------------------------------------------
 static cudaEvent_t get_event(Hierarchy &h) {
-    std::lock_guard<std::mutex> lk(h.timing_mu);
     if (!h.event_pool.empty()) {
         cudaEvent_t e = h.event_pool.back();
         h.event_pool.pop_back();
@@ -61,7 +56,6 @@ template <class F> static void timed(Hierarchy &h, int kind, int level, double b
     AMG_CUDA(cudaEventRecord(pe.a, s));
     f();
     AMG_CUDA(cudaEventRecord(pe.b, s));
-    std::lock_guard<std::mutex> lk(h.timing_mu);
     h.pending.push_back(pe);
 }
 
@@ -89,51 +83,51 @@ static void init_level_maps(Level &V, cudaStream_t s) {
     V.keep.alloc(V.A.nnz + kPad);
 }
 
-// One coarsening step from level l (whose operator, maps and M are in
-// place): strength, C/F splitting, interpolation, Galerkin product, and the
-// new level's maps and M.  Returns false when level l is the coarsest.
-static bool coarsen_step(Hierarchy &h, int l, cudaStream_t s) {
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
+    (void)A0in;
     const amg_options &o = h.opt;
-    Level &V = *h.lev[l];
-    int32_t n = V.A.nrows;
-    if (n <= o.max_size || l + 1 >= o.max_levels) return false;
-    V.strong.alloc(V.A.nnz + kPad);
-    V.cf.alloc(n + kPad);
-    V.cmap.alloc(sizeof(int32_t) * (n + 1));
-    timed(h, 8, l, 0.0, s, [&] { setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s); });
-    int64_t nc = 0;
-    timed(h, 9, l, 0.0, s, [&] {
-        nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed, o.level_offset + l,
-                         V.cf.as<int8_t>(), V.cmap.as<int32_t>(), s);
-    });
-    if (nc == 0 || (double)nc > 0.9 * (double)n) {
-        V.strong.release();
-        V.cf.release();
-        V.cmap.release();
-        return false;
+    for (int l = 0;; ++l) {
+        Level &V = *h.lev[l];
+        if (l == 0) timed(h, 12, 0, 0.0, s, [&] { init_level_maps(V, s); });
+        int32_t n = V.A.nrows;
+        if (n <= o.max_size || l + 1 >= o.max_levels) break;
+        V.strong.alloc(V.A.nnz + kPad);
+        V.cf.alloc(n + kPad);
+        V.cmap.alloc(sizeof(int32_t) * (n + 1));
+        timed(h, 8, l, 0.0, s, [&] { setup::strength(V.A, o.theta, V.strong.as<uint8_t>(), s); });
+        int64_t nc = 0;
+        timed(h, 9, l, 0.0, s, [&] {
+            nc = setup::pmis(V.A, V.strong.as<uint8_t>(), V.tpos.as<int32_t>(), o.seed, o.level_offset + l,
+                             V.cf.as<int8_t>(), V.cmap.as<int32_t>(), s);
+        });
+        if (nc == 0 || (double)nc > 0.9 * (double)n) {
+            V.strong.release();
+            V.cf.release();
+            V.cmap.release();
+            break;
+        }
+        V.cpts.alloc(sizeof(int32_t) * (nc + 1));
+        timed(h, 9, l, 0.0, s, [&] {
+            setup::coarse_points(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
+        });
+        timed(h, 10, l, 0.0, s, [&] {
+            setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
+                                 (int32_t)nc, V.P, s);
+            setup::transpose(V.P, V.R, s);
+        });
+        DevCSR AP;
+        auto C = std::make_unique<Level>();
+        timed(h, 11, l, 0.0, s, [&] {
+            setup::spgemm(V.A, V.P, AP, s);
+            setup::spgemm(V.R, AP, C->A, s);
+        });
+        timed(h, 12, l, 0.0, s, [&] {
+            init_level_maps(*C, s);
+            C->inM.alloc(C->A.nnz + kPad);
+            setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+        });
+        h.lev.push_back(std::move(C));
     }
-    V.cpts.alloc(sizeof(int32_t) * (nc + 1));
-    timed(h, 9, l, 0.0, s, [&] {
-        setup::coarse_points(V.cf.as<int8_t>(), n, V.cmap.as<int32_t>(), V.cpts.as<int32_t>(), s);
-    });
-    timed(h, 10, l, 0.0, s, [&] {
-        setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
-                             (int32_t)nc, V.P, s);
-        setup::transpose(V.P, V.R, s);
-    });
-    DevCSR AP;
-    auto C = std::make_unique<Level>();
-    timed(h, 11, l, 0.0, s, [&] {
-        setup::spgemm(V.A, V.P, AP, s);
-        setup::spgemm(V.R, AP, C->A, s);
-    });
-    timed(h, 12, l, 0.0, s, [&] {
-        init_level_maps(*C, s);
-        C->inM.alloc(C->A.nnz + kPad);
-        setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
-    });
-    h.lev.push_back(std::move(C));
-    return true;
 }
 
 // Levels given by the caller (amg_hierarchy_assemble / load).
@@ -383,7 +377,7 @@ template <typename T> static void alloc_zero(DevBuf &b, int64_t n, cudaStream_t 
     AMG_CUDA(cudaMemsetAsync(b.ptr, 0, b.bytes, s));
 }
 
-static void prepare_level(Hierarchy &h, int l, bool has_p, cudaStream_t s) {
+static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     Level &V = *h.lev[l];
     const DevCSR &M = V.op();
     int32_t n = V.n();
@@ -396,6 +390,7 @@ static void prepare_level(Hierarchy &h, int l, bool has_p, cudaStream_t s) {
     V.hv16.release();
     V.dinv32.release();
     free_sell(V);
+    bool has_p = l + 1 < h.nlev();
     if (prec == AMG_PREC_FP64) {
         alloc_zero<double>(V.b, n, s); alloc_zero<double>(V.x, n, s);
         alloc_zero<double>(V.r, n, s); alloc_zero<double>(V.xo, n, s);
@@ -545,7 +540,7 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
 
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
     for (int l : levels) {
-        timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, l + 1 < h.nlev(), s); });
+        timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, s); });
         if (l == h.nlev() - 1) timed(h, 15, l, 0.0, s, [&] { prepare_coarse(h, s); });
     }
     if (h.opt.spmv_variant == AMG_SPMV_AUTO) {
@@ -561,110 +556,6 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
     h.graph_dirty = true;
     h.version++;
     AMG_CUDA(cudaStreamSynchronize(s));
-}
-
-// ---------------------------------------------------------------------------
-// Setup with the per-level finishing work -- sparsification (Algorithms 3 /
-// 3b at the level's gamma), cycle preparation, transfer trials -- on a second
-// host thread and stream, overlapped with the coarsening of the next levels.
-// Each thread blocks only on its own stream's read-backs, so the GPU keeps
-// work from one while the host waits on the other.  Level l is handed over
-// once its coarsening step is done (an event orders the streams); the worker
-// takes levels in order (Hybrid Galerkin reads the level above's sparsified
-// operator).  The level vector's capacity is reserved up front so its element
-// storage never moves while the worker indexes it.
-// ---------------------------------------------------------------------------
-void setup_pipelined(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s) {
-    h.lev.reserve(kMaxLevels + 1);
-    cudaStream_t s2 = nullptr;
-    AMG_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
-    struct Item {
-        int l;
-        bool coarsest;
-        cudaEvent_t ready;
-    };
-    std::mutex mu;
-    std::condition_variable cv;
-    std::deque<Item> q;
-    bool closed = false;
-    std::exception_ptr werr;
-    auto gamma_of = [&](int l) {
-        return (l > 0 && n_gamma > 0 && gamma) ? gamma[std::min(l, n_gamma - 1)] : 0.0;
-    };
-    std::thread worker([&] {
-        try {
-            AMG_CUDA(cudaSetDevice(h.device));
-            while (true) {
-                Item it;
-                {
-                    std::unique_lock<std::mutex> lk(mu);
-                    cv.wait(lk, [&] { return !q.empty() || closed; });
-                    if (q.empty()) break;
-                    it = q.front();
-                    q.pop_front();
-                }
-                AMG_CUDA(cudaStreamWaitEvent(s2, it.ready, 0));
-                cudaEventDestroy(it.ready);
-                const int l = it.l;
-                h.lev[l]->gamma = gamma_of(l);
-                timed(h, 13, l, 0.0, s2, [&] { resparsify_level(h, l, s2); });
-                timed(h, 14, l, 0.0, s2, [&] { prepare_level(h, l, !it.coarsest, s2); });
-                if (it.coarsest) timed(h, 15, l, 0.0, s2, [&] { prepare_coarse(h, s2); });
-                if (l >= 1 && h.opt.spmv_variant == AMG_SPMV_AUTO && !h.lev[l - 1]->pr_tuned) {
-                    timed(h, 14, l - 1, 0.0, s2, [&] {
-                        if (h.opt.precision == AMG_PREC_FP64) autotune_transfers<double>(h, l - 1, s2);
-                        else autotune_transfers<float>(h, l - 1, s2);
-                    });
-                    h.lev[l - 1]->pr_tuned = true;
-                }
-            }
-        } catch (...) {
-            werr = std::current_exception();
-            // drain what is still queued so no event leaks
-            std::lock_guard<std::mutex> lk(mu);
-            for (auto &it : q) cudaEventDestroy(it.ready);
-            q.clear();
-        }
-    });
-    auto hand_over = [&](int l, bool coarsest) {
-        cudaEvent_t e;
-        AMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        AMG_CUDA(cudaEventRecord(e, s));
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            if (werr) {  // the worker stopped: do not queue more
-                cudaEventDestroy(e);
-                return;
-            }
-            q.push_back(Item{l, coarsest, e});
-        }
-        cv.notify_one();
-    };
-    std::exception_ptr merr;
-    try {
-        timed(h, 12, 0, 0.0, s, [&] { init_level_maps(*h.lev[0], s); });
-        int l = 0;
-        while (coarsen_step(h, l, s)) {
-            hand_over(l, false);
-            ++l;
-        }
-        hand_over(l, true);
-    } catch (...) {
-        merr = std::current_exception();
-    }
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        closed = true;
-    }
-    cv.notify_one();
-    worker.join();
-    const cudaError_t se = cudaStreamSynchronize(s2);
-    cudaStreamDestroy(s2);
-    if (merr) std::rethrow_exception(merr);
-    if (werr) std::rethrow_exception(werr);
-    AMG_CUDA(se);
-    h.graph_dirty = true;
-    h.version++;
 }
 
 void ensure_workspace(Hierarchy &h, cudaStream_t s) {

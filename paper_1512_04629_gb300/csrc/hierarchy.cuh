@@ -2,7 +2,6 @@
 #pragma once
 
 #include <memory>
-#include <mutex>
 #include <vector>
 
 #include <map>
@@ -119,7 +118,6 @@ struct Hierarchy {
     bool timing = false;
     Timing timers[kTimingKinds][kMaxLevels];
     std::vector<PendingEvent> pending;
-    std::mutex timing_mu;  // the setup's worker thread records events too
     std::vector<cudaEvent_t> event_pool;
 
     // CUDA graphs of the PCG iteration halves (captured per stream)
@@ -205,9 +203,7 @@ template <typename XT> inline const XT *dinv_of(const Level &V) {
 }
 
 // drivers (hierarchy.cu)
-// coarsening on s, per-level sparsify / cycle preparation on a worker thread
-// and stream, overlapped; leaves the hierarchy ready except the workspace
-void setup_pipelined(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s);
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s);
 void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &P,
                      const std::vector<std::vector<int8_t>> &cf,
                      const std::vector<std::vector<uint8_t>> &inM, cudaStream_t s);
