@@ -260,15 +260,23 @@ def collect_timing(h, nlev):
 def _median_phases(runs):
     if not runs:
         return None
-    return {k: round(statistics.median(r[k] for r in runs), 3) for k in runs[0]}
+    out = {}
+    for k in runs[0]:
+        if k.endswith("_by_level"):
+            out[k] = [round(statistics.median(r[k][i] for r in runs), 3) for i in range(len(runs[0][k]))]
+        else:
+            out[k] = round(statistics.median(r[k] for r in runs), 3)
+    return out
 
 
 def collect_setup_timing(h, nlev):
-    """Setup phase -> milliseconds summed over levels (event spans on the setup stream)."""
+    """Setup phase -> milliseconds summed over levels (event spans on the setup stream),
+    plus the same per level under "<phase>_by_level"."""
     out = {}
     for kind, name in SETUP_KIND_NAMES.items():
-        ms = sum(h.timing_get(kind, l)[1] for l in range(nlev))
-        out[name] = round(ms, 3)
+        per = [h.timing_get(kind, l)[1] for l in range(nlev)]
+        out[name] = round(sum(per), 3)
+        out[name + "_by_level"] = [round(x, 3) for x in per]
     return out
 
 
