@@ -187,11 +187,23 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t key) {
 
 enum : int8_t { kU = 0, kC = 1, kF = -1 };
 
+// Appends row i to a list when `keep` holds, with one atomic per warp; the
+// list's order varies from run to run, its contents do not.
+__device__ __forceinline__ void warp_append(bool keep, int32_t i, int32_t *list, int *count) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+    if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+}
+
 __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tpos,
                                  const uint8_t *strong, uint64_t seed, int32_t level, double *w,
-                                 int8_t *state, int *undecided, uint8_t *sym) {
+                                 int8_t *state, int *undecided, uint8_t *sym, int32_t *list) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    int add = 0;
+    bool und = false;
     if (i < n) {
         int32_t cnt = 0;  // |S^T_i|: rows j whose strong set holds i
         for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
@@ -203,26 +215,28 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
         double u = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
         w[i] = (double)cnt + u;
         state[i] = cnt == 0 ? kF : kU;
-        add = cnt != 0;
+        und = cnt != 0;
     }
-    add = __syncthreads_count(add);
-    if (threadIdx.x == 0 && add) atomicAdd(undecided, add);
+    warp_append(und, i, list, undecided);
 }
 
-// Rounds are launched in batches without reading back in between: every
-// round kernel first reads the undecided count the previous round left and
+// Every round works on the list of rows still undecided when it starts (the
+// previous round's output, with its length on the device).  Rounds are
+// launched in batches without reading back in between, each grid sized for
+// the batch's first list; a kernel reads the list's actual length first and
 // does nothing once it is zero.
 template <int T>
-__global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                   const uint8_t *sym, const double *w,
-                                   const int8_t *state, uint8_t *newc, const int *prev) {
-    if (*prev == 0) return;  // the same for the whole grid
+__global__ void pmis_select_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
+                                   const uint8_t *sym, const double *w, const int8_t *state, uint8_t *newc) {
+    const int m = *len;  // the same for the whole grid
+    if (m == 0) return;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t i = (int32_t)(g / T);
+    const int64_t k = g / T;
     const int t = (int)(g % T);
-    const bool und = i < n && state[i] == kU;
+    const bool live = k < m;  // no early exit: the group reduction needs every lane
+    const int32_t i = live ? list[k] : 0;
     bool lose = false;
-    if (und) {
+    if (live) {
         // weights are >= 0: their bit patterns order like the values
         const int64_t wi = __double_as_longlong(w[i]);
         for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
@@ -234,34 +248,35 @@ __global__ void pmis_select_kernel(int32_t n, const int32_t *rp, const int32_t *
         }
     }
     lose = group_any<T>(lose);
-    if (i < n && t == 0) newc[i] = (uint8_t)(und && !lose);
+    if (live && t == 0) newc[i] = (uint8_t)!lose;
 }
 
-__global__ void pmis_apply_c_kernel(int32_t n, const uint8_t *newc, int8_t *state, const int *prev) {
-    if (*prev == 0) return;
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && newc[i]) state[i] = kC;
+__global__ void pmis_apply_c_kernel(const int32_t *list, const int *len, const uint8_t *newc, int8_t *state) {
+    const int m = *len;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int32_t i = list[k];
+    if (newc[i]) state[i] = kC;
 }
 
 template <int T>
-__global__ void pmis_apply_f_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                    const uint8_t *strong, int8_t *state, const int *prev, int *undecided) {
-    if (*prev == 0) return;  // the same for the whole grid
+__global__ void pmis_apply_f_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
+                                    const uint8_t *strong, int8_t *state, int32_t *next, int *next_len) {
+    const int m = *len;  // the same for the whole grid
+    if (m == 0) return;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t i = (int32_t)(g / T);
+    const int64_t k = g / T;
     const int t = (int)(g % T);
-    const bool und = i < n && state[i] == kU;
+    const bool live = k < m;
+    const int32_t i = live ? list[k] : 0;
+    const bool und = live && state[i] == kU;
     bool f = false;
     if (und)
         for (int32_t p = rp[i] + t; p < rp[i + 1] && !f; p += T)
             if (strong[p] && state[ci[p]] == kC) f = true;
     f = group_any<T>(f);
-    int still = 0;
-    if (und && t == 0) {
-        if (f) state[i] = kF; else still = 1;
-    }
-    still = __syncthreads_count(still);
-    if (threadIdx.x == 0 && still) atomicAdd(undecided, still);
+    if (und && t == 0 && f) state[i] = kF;
+    warp_append(und && t == 0 && !f, i, next, next_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -1282,30 +1297,39 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         return 0;
     }
     constexpr int kBatch = 4, kMaxRounds = 10000;
-    // cnt[0]: undecided after the initial split; cnt[r]: after round r
-    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s), sym(A.nnz + 1, s);
+    // cnt[0]: undecided after the initial split; cnt[r]: after round r; the
+    // undecided rows alternate between two lists
+    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s), sym(A.nnz + 1, s),
+        lists(sizeof(int32_t) * 2 * (size_t)n, s);
     int *dc = cnt.as<int>();
+    int32_t *list[2] = {lists.as<int32_t>(), lists.as<int32_t>() + n};
     int g = div_up(n, kThreads);
-    const int T = row_lanes(A, 8);  // later rounds find most rows decided: keep the grid small
+    const int T = row_lanes(A, 8);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
-                                            cf, dc, sym.as<uint8_t>()); ::amg::count_launch(); }
+                                            cf, dc, sym.as<uint8_t>(), list[0]); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    int done = 0;  // rounds launched
-    int last = -1; // undecided count before the current batch (-1: not read yet)
+    int done = 0;   // rounds launched
+    int last = n;   // bound on the list length at the start of the batch
+    bool first = true;
     while (true) {
         if (done + kBatch > kMaxRounds) throw Error(AMG_ERR_CUDA, "PMIS did not terminate");
+        const int64_t bound = std::max(last, 1);
         for (int b = 0; b < kBatch; ++b) {
             const int r = done + b + 1;
+            const int32_t *cur = list[(r - 1) & 1];
+            int32_t *nxt = list[r & 1];
             with_row_lanes(T, [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
-                const int gl = div_up((int64_t)n * L, kThreads);
-                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(),
-                                                              cf, newc.as<uint8_t>(), dc + r - 1);
+                const int gl = div_up(bound * L, kThreads);
+                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), sym.as<uint8_t>(),
+                                                              w.as<double>(), cf, newc.as<uint8_t>());
                 ::amg::count_launch();
-                pmis_apply_c_kernel<<<g, kThreads, 0, s>>>(n, newc.as<uint8_t>(), cf, dc + r - 1);
+                pmis_apply_c_kernel<<<div_up(bound, kThreads), kThreads, 0, s>>>(cur, dc + r - 1,
+                                                                               newc.as<uint8_t>(), cf);
                 ::amg::count_launch();
-                pmis_apply_f_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), strong, cf, dc + r - 1, dc + r);
+                pmis_apply_f_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), strong, cf, nxt,
+                                                               dc + r);
                 ::amg::count_launch();
             });
         }
@@ -1313,10 +1337,11 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         int hc[kBatch + 1];
         AMG_CUDA(cudaMemcpyAsync(hc, dc + done, sizeof(hc), cudaMemcpyDeviceToHost, s));
         AMG_CUDA(cudaStreamSynchronize(s));
-        if (last >= 0 && hc[0] != last) throw Error(AMG_ERR_CUDA, "PMIS counters inconsistent");
+        if (!first && hc[0] != last) throw Error(AMG_ERR_CUDA, "PMIS counters inconsistent");
         // every round that started with undecided points must have decided some
         for (int b = 0; b < kBatch; ++b)
             if (hc[b] > 0 && hc[b + 1] >= hc[b]) throw Error(AMG_ERR_CUDA, "PMIS made no progress");
+        first = false;
         done += kBatch;
         last = hc[kBatch];
         if (hc[kBatch] == 0) break;
