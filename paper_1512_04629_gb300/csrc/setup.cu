@@ -1153,6 +1153,52 @@ __global__ void tri_inverse_kernel(int32_t n, const double *L, double *Linv) {
 }
 
 // inv = Linv^T Linv
+// Small coarsest levels (n <= kSmemCoarse): Cholesky factor and its inverse
+// in shared memory by one block -- the global-memory kernels above walk long
+// chains of dependent loads, which dominates at these sizes.  Same
+// right-looking factorization (same operation order) as cholesky_kernel;
+// column c of L^{-1} by forward substitution, one thread per column.
+constexpr int kSmemCoarse = 112;  // 2 n^2 doubles = 196 KB of shared memory
+
+__global__ void __launch_bounds__(1024)
+coarse_factor_smem_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double *linv_out,
+                          int *err) {
+    extern __shared__ __align__(16) double sm[];
+    double *a = sm, *li = sm + (size_t)n * n;
+    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = 0.0;
+    __syncthreads();
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x)
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) a[i * n + ci[p]] = v[p];
+    __shared__ double piv;
+    for (int32_t j = 0; j < n; ++j) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double d = a[j * n + j];
+            if (!(d > 0.0)) { *err = 1; d = 1.0; }
+            piv = sqrt(d);
+            a[j * n + j] = piv;
+        }
+        __syncthreads();
+        for (int32_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) a[i * n + j] /= piv;
+        __syncthreads();
+        const int32_t m = n - j - 1;
+        for (int32_t t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int32_t r = j + 1 + t / m, c = j + 1 + t % m;
+            if (c <= r) a[r * n + c] -= a[r * n + j] * a[c * n + j];
+        }
+    }
+    __syncthreads();
+    for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+        for (int32_t i = 0; i < n; ++i) {
+            double s2 = (i == c) ? 1.0 : 0.0;
+            for (int32_t k = c; k < i; ++k) s2 -= a[i * n + k] * li[k * n + c];
+            li[i * n + c] = (i < c) ? 0.0 : s2 / a[i * n + i];
+        }
+    }
+    __syncthreads();
+    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) linv_out[t] = li[t];
+}
+
 __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n * n) return;
@@ -1557,7 +1603,8 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     // one numeric pass into slots sized by each row's product bound, then a
     // compaction -- unless the bound does not fit: then count first (symbolic)
     size_t fr = 0, tot = 0;
-    AMG_CUDA(cudaMemGetInfo(&fr, &tot));
+    if ((double)total_ub * 12.0 > (double)((size_t)1 << 30)) AMG_CUDA(cudaMemGetInfo(&fr, &tot));  // only when it may matter
+    else fr = (size_t)1 << 40;
     // AMG_SPGEMM_TWO_PASS=1 forces the counting path (it is otherwise taken
     // only when the product bound would not fit in free memory)
     const char *force = std::getenv("AMG_SPGEMM_TWO_PASS");
@@ -1666,11 +1713,19 @@ void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
     require(n <= 8192, "coarsest level too large for the dense direct solve (n > 8192)");
-    TmpBuf a(sizeof(double) * (size_t)n * n, s), linv(sizeof(double) * (size_t)n * n, s), err(sizeof(int), s);
+    TmpBuf linv(sizeof(double) * (size_t)n * n, s), err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
-    { densify_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), a.as<double>()); ::amg::count_launch(); }
-    { cholesky_kernel<<<1, 1024, 0, s>>>(n, a.as<double>(), err.as<int>()); ::amg::count_launch(); }
-    { tri_inverse_kernel<<<div_up(n, 128), 128, 0, s>>>(n, a.as<double>(), linv.as<double>()); ::amg::count_launch(); }
+    if (n <= kSmemCoarse) {
+        const size_t smem = 2 * sizeof(double) * (size_t)n * n;
+        AMG_CUDA(cudaFuncSetAttribute(coarse_factor_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(2 * sizeof(double) * kSmemCoarse * kSmemCoarse)));
+        { coarse_factor_smem_kernel<<<1, 1024, smem, s>>>(n, A.rp(), A.ci(), A.v(), linv.as<double>(), err.as<int>()); ::amg::count_launch(); }
+    } else {
+        TmpBuf a(sizeof(double) * (size_t)n * n, s);
+        { densify_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), a.as<double>()); ::amg::count_launch(); }
+        { cholesky_kernel<<<1, 1024, 0, s>>>(n, a.as<double>(), err.as<int>()); ::amg::count_launch(); }
+        { tri_inverse_kernel<<<div_up(n, 128), 128, 0, s>>>(n, a.as<double>(), linv.as<double>()); ::amg::count_launch(); }
+    }
     { gram_kernel<<<div_up((int64_t)n * n, kThreads), kThreads, 0, s>>>(n, linv.as<double>(), inv); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     if (read_scalar(err.as<int>(), s))
