@@ -633,7 +633,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // the bit with it.
 // ---------------------------------------------------------------------------
 template <int W, bool NUMERIC>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 8)  // 32 registers: a full SM of warps to hide the load chains
 spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_t *__restrict__ arp,
                    const int32_t *__restrict__ aci, const double *__restrict__ av, const int32_t *__restrict__ brp,
                    const int32_t *__restrict__ bci, const double *__restrict__ bv, int32_t *__restrict__ cnt,
@@ -924,7 +924,7 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
 }
 
 template <int U, int WARPS, bool NUMERIC>
-__global__ void __launch_bounds__(WARPS * 32)
+__global__ void __launch_bounds__(WARPS * 32, U <= 128 ? 8 : 1)  // the small table allows a full SM of warps
 spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                   const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
                   int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
