@@ -83,17 +83,30 @@ __device__ __forceinline__ XT csr_row_sum(int32_t p0, int32_t p1, int t, const i
     return acc;
 }
 
+// SELL column indices: int32 columns, or int16 offsets from the row (when
+// every |column - row| of the operator fits; 2 bytes less per stored entry)
+struct SellIdx {
+    const int32_t *col;
+    const int16_t *delta;
+};
+template <bool D16>
+__device__ __forceinline__ int32_t sell_col(const SellIdx &ix, int32_t p, int32_t row) {
+    if constexpr (D16) return row + (int32_t)__ldg(ix.delta + p);
+    else return __ldg(ix.col + p);
+}
+
 // sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32)
-template <typename VT, typename XT, class G>
-__device__ __forceinline__ XT sell_row_sum(int32_t pos, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
-                                           const int32_t *__restrict__ sci, const VT *__restrict__ sv, G gather) {
+template <typename VT, typename XT, bool D16, class G>
+__device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32_t *__restrict__ soff,
+                                           const int32_t *__restrict__ sw, const SellIdx &ix,
+                                           const VT *__restrict__ sv, G gather) {
     int32_t s = pos >> 5, lane = pos & 31;
     int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
     XT acc = XT(0);
 #pragma unroll 4
     for (int32_t k = 0; k < w; ++k) {
         int32_t p = off + k * 32;
-        acc += cvt<VT, XT>(__ldg(sv + p)) * gather(__ldg(sci + p));
+        acc += cvt<VT, XT>(__ldg(sv + p)) * gather(sell_col<D16>(ix, p, row));
     }
     return acc;
 }
@@ -132,17 +145,17 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
     }
 }
 
-template <typename VT, typename XT, int OP>
+template <typename VT, typename XT, int OP, bool D16>
 __global__ void __launch_bounds__(kThreads)
 sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
-               const int32_t *__restrict__ sci, const VT *__restrict__ sv, const XT *__restrict__ b,
+               SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
                const XT *__restrict__ dinv, const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
     const int32_t i = perm ? __ldg(perm + pos) : pos;
     XT s;
-    if (OP == kPre) s = sell_row_sum<VT, XT>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -166,7 +179,11 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
     int32_t n = A.nrows;
     if (n == 0) return;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        { sell_op_kernel<VT, XT, OP><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        const SellIdx ix{A.sci, A.sd};
+        if (A.sd)
+            { sell_op_kernel<VT, XT, OP, true><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        else
+            { sell_op_kernel<VT, XT, OP, false><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
     } else {
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);
@@ -346,9 +363,10 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
 
 // q = A p (SELL-32, one thread per row) and p . q; each warp walks slices
 // with a stride of the grid's warp count
+template <bool D16>
 __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
-               const int32_t *__restrict__ sci, const double *__restrict__ sv, const double *__restrict__ p,
+               SellIdx ix, const double *__restrict__ sv, const double *__restrict__ p,
                double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
     double part[1] = {0.0};
@@ -358,7 +376,7 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         const int32_t pos = sl * 32 + lane;
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
-        double s = sell_row_sum<double, double>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(p + j); });
+        double s = sell_row_sum<double, double, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
         q[i] = s;
         part[0] += p[i] * s;
     }
@@ -472,9 +490,10 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
     block_partials<2>(part, red);
 }
 
+template <bool D16>
 __global__ void __launch_bounds__(kThreads)
 post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
-                    const int32_t *__restrict__ sw, const int32_t *__restrict__ sci, const double *__restrict__ sv,
+                    const int32_t *__restrict__ sw, SellIdx ix, const double *__restrict__ sv,
                     const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                     double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
@@ -485,7 +504,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
         const int32_t pos = sl * 32 + lane;
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
-        double s = sell_row_sum<double, double>(pos, soff, sw, sci, sv, [&](int32_t j) { return __ldg(x + j); });
+        double s = sell_row_sum<double, double, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
         double bi = b[i];
         double zi = x[i] + dinv[i] * (bi - s);
         z[i] = zi;
@@ -606,7 +625,7 @@ __global__ void slice_size_kernel(int32_t nsl, const int32_t *sw, int32_t *sz) {
 
 template <typename VT>
 __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
-                                 const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv) {
+                                 const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, int16_t *sd) {
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     int32_t nsl = (n + 31) / 32;
     if (pos >= nsl * 32) return;
@@ -616,13 +635,25 @@ __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     int32_t p0 = i >= 0 ? rp[i] : 0, len = i >= 0 ? rp[i + 1] - p0 : 0;
     // padding: value 0 at a column the row itself holds (its last one), or
     // column 0 for an empty row -- always inside x, also for rectangular
-    // operators (P is n x n_c)
-    const int32_t pad_col = len > 0 ? ci[p0 + len - 1] : 0;
+    // operators (P is n x n_c); with int16 offsets an empty row pads with
+    // its own index (offset 0; those operators are square)
+    const int32_t pad_col = len > 0 ? ci[p0 + len - 1] : (sd ? (i >= 0 ? i : 0) : 0);
     for (int32_t k = 0; k < w; ++k) {
         int32_t p = off + k * 32;
-        if (k < len) { sci[p] = ci[p0 + k]; sv[p] = v[p0 + k]; }
-        else { sci[p] = pad_col; sv[p] = VT(0); }
+        const int32_t c = k < len ? ci[p0 + k] : pad_col;
+        if (sd) sd[p] = (int16_t)(i >= 0 ? c - i : 0);
+        else sci[p] = c;
+        sv[p] = k < len ? v[p0 + k] : VT(0);
     }
+}
+
+__global__ void max_col_offset_kernel(int32_t n, const int32_t *rp, const int32_t *ci, int *out) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int m = 0;
+    if (i < n)
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) m = max(m, abs(ci[p] - i));
+    m = __reduce_max_sync(0xffffffffu, (unsigned)m);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 }  // namespace
@@ -683,12 +714,17 @@ static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgSc
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         int blocks = reduce_blocks(A.nrows);
-        { ap_sell_kernel<<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, A.sci, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        const SellIdx ix{A.sci, A.sd};
+        if (A.sd)
+            { ap_sell_kernel<true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        else
+            { ap_sell_kernel<false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
     }
     switch (threads_per_row(A.variant == AMG_SPMV_SELL32 ? AMG_SPMV_CSR4 : A.variant)) {
+        case 1: launch_ap<1>(A, p, q, sc, red, s); break;
         case 2: launch_ap<2>(A, p, q, sc, red, s); break;
         case 4: launch_ap<4>(A, p, q, sc, red, s); break;
         case 8: launch_ap<8>(A, p, q, sc, red, s); break;
@@ -713,7 +749,11 @@ bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, c
     if (n == 0) return false;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         int blocks = reduce_blocks(n);
-        { post_rz_sell_kernel<<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, A.sci, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+        const SellIdx ix{A.sci, A.sd};
+        if (A.sd)
+            { post_rz_sell_kernel<true><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+        else
+            { post_rz_sell_kernel<false><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
         launch_finish<2, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return true;
@@ -798,11 +838,20 @@ int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, 
 
 template <typename VT>
 void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm, const int32_t *soff,
-               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s) {
+               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd) {
     int32_t nsl = (n + 31) / 32;
     if (nsl == 0) return;
-    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, perm, soff, sw, sci, sv); ::amg::count_launch(); }
+    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, perm, soff, sw, sci, sv, sd); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
+}
+
+int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s) {
+    if (n == 0) return 0;
+    TmpBuf out(sizeof(int), s);
+    AMG_CUDA(cudaMemsetAsync(out.ptr, 0, sizeof(int), s));
+    { max_col_offset_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, rp, ci, out.as<int>()); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+    return read_scalar(out.as<int>(), s);
 }
 
 // explicit instantiations
@@ -823,12 +872,12 @@ template void convert_values<__nv_bfloat16>(const double *, __nv_bfloat16 *, int
 template void convert_vec_from_f64<float>(const double *, float *, int64_t, cudaStream_t);
 template void convert_vec_to_f64<float>(const float *, double *, int64_t, cudaStream_t);
 template void sell_fill<double>(int32_t, const int32_t *, const int32_t *, const double *, const int32_t *,
-                                const int32_t *, const int32_t *, int32_t *, double *, cudaStream_t);
+                                const int32_t *, const int32_t *, int32_t *, double *, cudaStream_t, int16_t *);
 template void sell_fill<float>(int32_t, const int32_t *, const int32_t *, const float *, const int32_t *,
-                               const int32_t *, const int32_t *, int32_t *, float *, cudaStream_t);
+                               const int32_t *, const int32_t *, int32_t *, float *, cudaStream_t, int16_t *);
 template void sell_fill<__nv_bfloat16>(int32_t, const int32_t *, const int32_t *, const __nv_bfloat16 *,
                                        const int32_t *, const int32_t *, const int32_t *, int32_t *, __nv_bfloat16 *,
-                                       cudaStream_t);
+                                       cudaStream_t, int16_t *);
 
 }  // namespace cyc
 }  // namespace amg

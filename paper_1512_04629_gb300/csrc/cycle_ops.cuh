@@ -14,6 +14,7 @@ template <typename VT> struct CycMat {
     const VT *v = nullptr;
     int32_t nslices = 0;
     const int32_t *soff = nullptr, *sw = nullptr, *sci = nullptr;
+    const int16_t *sd = nullptr;    // SELL column as int16 offset from the row (replaces sci when set)
     const int32_t *perm = nullptr;  // SELL position -> row (null: identity)
     const VT *sv = nullptr;
     int variant = AMG_SPMV_CSR4;
@@ -103,7 +104,9 @@ constexpr int kSellSigma = 1024;
 int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s);
 template <typename VT>
 void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
-               const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s);
+               const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd = nullptr);
+// max over stored entries of |column - row| (square operators), for the int16 SELL offsets
+int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s);
 
 }  // namespace cyc
 }  // namespace amg

@@ -275,15 +275,22 @@ template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
         V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), V.sperm.as<int32_t>(), V.soff.as<int32_t>(),
                                           V.sw.as<int32_t>(), s);
     }
-    V.sci.alloc(sizeof(int32_t) * (V.sell_entries + kPad));
+    // columns as int16 offsets from the row when every one fits (2 bytes less per entry)
+    V.sci.release();
+    V.sd.release();
+    const bool d16 = M.nrows == M.ncols && cyc::max_col_offset(M.nrows, M.rp(), M.ci(), s) <= 32767;
+    if (d16) V.sd.alloc(sizeof(int16_t) * (V.sell_entries + kPad));
+    else V.sci.alloc(sizeof(int32_t) * (V.sell_entries + kPad));
     V.sv.alloc(sizeof(VT) * (V.sell_entries + kPad));
     CycMat<VT> m = op_mat<VT>(V);
     cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), m.v, V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
-                       V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sci.as<int32_t>(), V.sv.as<VT>(), s);
+                       V.soff.as<int32_t>(), V.sw.as<int32_t>(), d16 ? nullptr : V.sci.as<int32_t>(),
+                       V.sv.as<VT>(), s, d16 ? V.sd.as<int16_t>() : nullptr);
 }
 
 static void free_sell(Level &V) {
-    V.soff.release(); V.sw.release(); V.sci.release(); V.sv.release(); V.sperm.release(); V.sv64.release();
+    V.soff.release(); V.sw.release(); V.sci.release(); V.sd.release(); V.sv.release(); V.sperm.release();
+    V.sv64.release();
     V.sell_entries = 0;
 }
 
@@ -451,9 +458,12 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     // FP32 cycles: the outer PCG multiplies by A_0 in FP64 -- give it the same
     // SELL layout with FP64 values when level 0 relaxes through SELL
     if (l == 0 && V.vbytes != 8 && V.variant == AMG_SPMV_SELL32 && V.sv.ptr) {
+        // the index array is the one already filled (same layout); only the values are written again
         V.sv64.alloc(sizeof(double) * (V.sell_entries + kPad));
+        TmpBuf junk_idx(V.sd.ptr ? sizeof(int16_t) * (V.sell_entries + kPad) : sizeof(int32_t) * (V.sell_entries + kPad), s);
         cyc::sell_fill<double>(M.nrows, M.rp(), M.ci(), M.v(), V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
-                               V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sci.as<int32_t>(), V.sv64.as<double>(), s);
+                               V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sd.ptr ? nullptr : junk_idx.as<int32_t>(),
+                               V.sv64.as<double>(), s, V.sd.ptr ? junk_idx.as<int16_t>() : nullptr);
     }
 }
 
@@ -755,7 +765,8 @@ CycMat<double> a0_mat(Hierarchy &h) {
         m.nslices = (V.A.nrows + 31) / 32;
         m.soff = V.soff.as<int32_t>();
         m.sw = V.sw.as<int32_t>();
-        m.sci = V.sci.as<int32_t>();
+        m.sci = V.sci.ptr ? V.sci.as<int32_t>() : nullptr;
+        m.sd = V.sd.ptr ? V.sd.as<int16_t>() : nullptr;
         m.sv = V.sv64.as<double>();
         m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
     } else {

@@ -46,6 +46,7 @@ struct Level {
     DevBuf pv32, rv32;     // FP32 values of P and R
     DevBuf dinv32;
     DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
+    DevBuf sd;                 // its columns as int16 offsets from the row (instead of sci) when they fit
     DevBuf sperm;              // SELL position -> row when rows are length-sorted
     DevBuf sv64;               // level 0 in FP32 modes: FP64 values in the same SELL layout (outer PCG)
     int64_t sell_entries = 0;
@@ -159,7 +160,8 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
         m.nslices = (M.nrows + 31) / 32;
         m.soff = V.soff.as<int32_t>();
         m.sw = V.sw.as<int32_t>();
-        m.sci = V.sci.as<int32_t>();
+        m.sci = V.sci.ptr ? V.sci.as<int32_t>() : nullptr;
+        m.sd = V.sd.ptr ? V.sd.as<int16_t>() : nullptr;
         m.sv = V.sv.as<VT>();
         m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
     }

@@ -218,6 +218,30 @@ def test_adaptive_matches_oracle(amg, use_graph):
         assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
 
 
+@pytest.mark.parametrize("permute", [False, True])
+def test_sell_matches_sequential_csr(amg, permute):
+    """SELL-32 (int16 column offsets, or int32 columns when a random symmetric
+    permutation puts offsets beyond 32767) sums each row in the same order as
+    the one-lane CSR kernel; only the dot products' grids differ, so the two
+    PCG iterates agree to rounding."""
+    import scipy.sparse as sp
+
+    A = gen.poisson2d_5pt(200).to_scipy()
+    if permute:
+        perm = np.random.default_rng(7).permutation(A.shape[0])
+        A = A[perm][:, perm].tocsr()
+        A.sort_indices()
+    b = gen.rhs_uniform(A.shape[0], 2)
+    xs = []
+    for variant in (amg.SPMV_SELL32, 7):
+        h = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], spmv_variant=variant)
+        x, info = h.solve(b, tol=1e-8)
+        assert info.status == 0
+        xs.append((x, info.iterations))
+    assert abs(xs[0][1] - xs[1][1]) <= 1
+    assert np.linalg.norm(xs[0][0] - xs[1][0]) <= 1e-9 * np.linalg.norm(xs[1][0])
+
+
 def test_reintroduce_equals_fresh_setup(amg):
     """Reintroducing entries level by level leaves the hierarchy a fresh setup
     with the resulting tolerances would build: the same operators and, to the
