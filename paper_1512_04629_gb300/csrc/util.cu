@@ -215,9 +215,37 @@ __global__ void tile_scan_kernel(const TI *in, int64_t n, const int64_t *sums, T
 }
 
 // all on the stream, nothing read back: out[0..n] and *total on the device
+// Short arrays: the whole scan in one block (one launch instead of three);
+// each thread scans a contiguous chunk, the block scans the chunk sums.
+constexpr int64_t kOneBlockScan = 16 * 1024;
+
+template <typename TI, typename TO>
+__global__ void one_block_scan_kernel(const TI *in, int64_t n, TO *out, int64_t *total) {
+    const int64_t chunk = (n + kScanThreads - 1) / kScanThreads;
+    const int64_t b0 = (int64_t)threadIdx.x * chunk, b1 = b0 + chunk < n ? b0 + chunk : n;
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += (int64_t)in[i];
+    int64_t tot;
+    int64_t ex = block_exclusive_scan<int64_t>(s, &tot);
+    for (int64_t i = b0; i < b1; ++i) {
+        const int64_t v = (int64_t)in[i];
+        out[i] = (TO)ex;
+        ex += v;
+    }
+    if (threadIdx.x == 0) {
+        *total = tot;
+        out[n] = (TO)tot;  // checked against the int32 range by the host reader
+    }
+}
+
 template <typename TI, typename TO>
 void scan_launch(const TI *in, TO *out, int64_t n, int64_t *total, cudaStream_t s) {
     int64_t tiles = (n + kTile - 1) / kTile;
+    if (n > 0 && n <= kOneBlockScan) {
+        { one_block_scan_kernel<TI, TO><<<1, kScanThreads, 0, s>>>(in, n, out, total); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     if (n > 0) {
         TmpBuf sums(sizeof(int64_t) * (tiles + 1), s);
         { tile_sum_kernel<TI><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums.as<int64_t>()); ::amg::count_launch(); }
