@@ -162,6 +162,7 @@ amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_
         check_csr_header(A, true);
         check_gammas(gamma, n_gamma);
         cudaStream_t s = as_stream(stream);
+        AllocOn alloc_scope(s);
         auto H = std::make_unique<amg_hierarchy>();
         Hierarchy &h = H->h;
         h.opt = o;
@@ -189,6 +190,7 @@ amg_status amg_hierarchy_assemble(int levels, const amg_csr *A, const amg_csr *P
         check_options(o);
         check_gammas(gamma, n_gamma);
         cudaStream_t s = as_stream(stream);
+        AllocOn alloc_scope(s);
         std::vector<DevCSR> dA(levels), dP(levels > 1 ? levels - 1 : 0);
         std::vector<std::vector<int8_t>> hcf(levels);
         std::vector<std::vector<uint8_t>> hinM(levels);
@@ -223,6 +225,7 @@ amg_status amg_sparsify(amg_hierarchy *H, const double *gamma, int n_gamma) {
         check_gammas(gamma, n_gamma);
         Hierarchy &h = H->h;
         cudaStream_t s = nullptr;
+        AllocOn alloc_scope(s);
         apply_gammas(h, gamma, n_gamma, s);
         std::vector<int> all;
         for (int l = 0; l < h.nlev(); ++l) all.push_back(l);
@@ -235,6 +238,7 @@ amg_status amg_reintroduce(amg_hierarchy *H, int s_levels, int *changed) {
     return guarded([&] {
         require(H != nullptr, "hierarchy is NULL");
         require(s_levels >= 1, "s_levels must be >= 1");
+        AllocOn alloc_scope(nullptr);
         int c = reintroduce(H->h, s_levels, nullptr);
         if (changed) *changed = c;
         return AMG_OK;
@@ -253,6 +257,7 @@ amg_status amg_solve(amg_hierarchy *H, const double *b, double *x, double tol, i
         require(max_it >= 1, "max_it must be >= 1");
         Hierarchy &h = H->h;
         cudaStream_t s = as_stream(stream);
+        AllocOn alloc_scope(s);
         ensure_workspace(h, s);
         int64_t n = h.lev[0]->n();
         const double *bd = b;
@@ -290,6 +295,7 @@ amg_status amg_solve_batch(amg_hierarchy *H, int k, const double *B, double *X, 
         } else {
             for (int64_t i = 0; i < n * k; ++i) require(std::isfinite(B[i]), "B has a non-finite value");
         }
+        AllocOn alloc_scope(as_stream(stream));
         amg_status st = solve_batch(h, k, B, X, on_device != 0, tol, max_it, as_stream(stream), info_k);
         double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         for (int c = 0; c < k; ++c) info_k[c].solve_ms = ms;
@@ -303,6 +309,7 @@ amg_status amg_precond_apply(amg_hierarchy *H, const double *r, double *z, void 
         require(is_device_ptr(r) && is_device_ptr(z), "r and z must be device memory");
         Hierarchy &h = H->h;
         cudaStream_t s = as_stream(stream);
+        AllocOn alloc_scope(s);
         ensure_workspace(h, s);
         vcycle_f64(h, r, z, s);
         timing_collect(h);

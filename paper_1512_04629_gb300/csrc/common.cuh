@@ -97,6 +97,17 @@ struct IdleRelease {
     ~IdleRelease();
 };
 
+// While an entry point runs on stream s, buffers it allocates are ordered on
+// s (no wait for the allocation); whoever later uses them on another stream
+// does so after the entry point has synchronized s.  Without a scope,
+// allocation waits for the pool's own stream.
+struct AllocOn {
+    cudaStream_t prev;
+    bool prev_scoped;
+    explicit AllocOn(cudaStream_t s);
+    ~AllocOn();
+};
+
 // A temporary device buffer with stream-ordered lifetime: allocated with
 // cudaMallocAsync and returned with cudaFreeAsync on the stream that uses it,
 // so freeing never waits for the device (the pool keeps the memory).

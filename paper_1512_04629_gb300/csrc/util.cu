@@ -31,6 +31,8 @@ const char *last_error_cstr() { return g_last_error.c_str(); }
 
 namespace {
 thread_local int g_idle_depth = 0;
+thread_local cudaStream_t g_alloc_stream = nullptr;
+thread_local bool g_alloc_scoped = false;
 
 // one non-blocking stream per device for pool allocations and bulk frees
 cudaStream_t pool_stream() {
@@ -45,6 +47,15 @@ cudaStream_t pool_stream() {
 }
 }  // namespace
 
+AllocOn::AllocOn(cudaStream_t s) : prev(g_alloc_stream), prev_scoped(g_alloc_scoped) {
+    g_alloc_stream = s;
+    g_alloc_scoped = true;
+}
+AllocOn::~AllocOn() {
+    g_alloc_stream = prev;
+    g_alloc_scoped = prev_scoped;
+}
+
 void IdleRelease::enter() {
     if (!active) { ++g_idle_depth; active = true; }
 }
@@ -58,11 +69,17 @@ void DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 16;
     keep_pool_warm();
-    cudaStream_t ps = pool_stream();
-    cudaError_t e = cudaMallocAsync(&ptr, b, ps);
-    // the pool may order the allocation after frees still pending on other
-    // streams: wait for it, so the memory is usable from any stream at once
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    cudaError_t e;
+    if (g_alloc_scoped) {
+        // ordered on the entry point's stream: usable by the work that follows there
+        e = cudaMallocAsync(&ptr, b, g_alloc_stream);
+    } else {
+        cudaStream_t ps = pool_stream();
+        e = cudaMallocAsync(&ptr, b, ps);
+        // the pool may order the allocation after frees still pending on other
+        // streams: wait for it, so the memory is usable from any stream at once
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         ptr = nullptr;
