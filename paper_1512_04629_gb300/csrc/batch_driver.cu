@@ -226,6 +226,7 @@ amg_status solve_batch(Hierarchy &h, int k, const double *B, double *X, bool on_
     std::vector<int> its(K, 0), reps(K, 0), status(K, AMG_NOT_CONVERGED);
     for (int c = 0; c < K; ++c) {
         bnorm[c] = std::sqrt(w.h_tt()[c]);
+        if (c < k && !std::isfinite(bnorm[c])) throw Error(AMG_ERR_INVALID, "B has a non-finite value");
         rnorm[c] = bnorm[c];
         bool live = c < k && bnorm[c] > 0.0;
         w.h_active()[c] = live ? 1 : 0;

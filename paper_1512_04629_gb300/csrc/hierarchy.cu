@@ -937,6 +937,7 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
     write_scalars(h, s);
     AMG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     double bnorm = true_resnorm(h, b, x, s);
+    if (!std::isfinite(bnorm)) throw Error(AMG_ERR_INVALID, "b has a non-finite value");
     amg_status st = AMG_OK;
     if (bnorm == 0.0) {
         info->status = AMG_OK;

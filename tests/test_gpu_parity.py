@@ -438,4 +438,21 @@ def test_invalid_inputs_rejected(amg):
     unsorted.data[r0] = unsorted.data[r0][::-1].copy()
     expect_invalid(unsorted)
     expect_invalid(good, gamma=[0.5, 0.1])  # gamma_0 must be 0
+    # non-finite right-hand sides, host and device, single and batched
+    import torch
+
+    h = amg.Hierarchy.setup(good)
+    bad_b = np.ones(good.shape[0])
+    bad_b[5] = np.inf
+    for rhs in (bad_b, torch.from_numpy(bad_b).cuda()):
+        with pytest.raises(amg.AmgError) as e:
+            h.solve(rhs)
+        assert e.value.status == 1
+    B = np.ones((good.shape[0], 3))
+    B[7, 1] = np.nan
+    with pytest.raises(amg.AmgError) as e:
+        h.solve_batch(B)
+    assert e.value.status == 1
+    x, info = h.solve(np.ones(good.shape[0]))  # still usable
+    assert info.status == 0
     expect_invalid(sp.csr_matrix(np.ones((2, 3))))
