@@ -62,6 +62,42 @@ def test_setup_end_to_end_matches_oracle(amg, case):
         np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14)
 
 
+def test_full_size_bench_workload_matches_oracle(amg):
+    """The bench workload at its full size (3D 7-point 128^3, Sparse Galerkin
+    gamma = 0.1, FP64, the same entry points and launch configuration the
+    bench times): every level of the GPU hierarchy -- strength, C/F split, P,
+    R, Galerkin A_l, M, kept entries, sparsified operators, l1 diagonals -- is
+    identical to the oracle's, and the PCG solve matches it (iterations within
+    one, solution within the stopping tolerance)."""
+    import torch
+
+    A = gen.poisson3d_7pt(128)
+    b = gen.rhs_uniform(A.n, 1)
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, 0.1])
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+    h = amg.Hierarchy.setup(amg.amg.csr_struct(rp, ci, va), gamma=[0.0, 0.1])
+    assert h.num_levels == ref.num_levels == 7
+    for l in range(h.num_levels):
+        _same_csr(h.export(l, "A"), ref.matrix(l, "A"), rtol=0.0, what=f"A_{l}")
+        _same_csr(h.export(l, "Ahat"), ref.matrix(l, "Ahat"), rtol=0.0, what=f"Ahat_{l}")
+        if l + 1 < h.num_levels:
+            np.testing.assert_array_equal(h.level_array(l, "strong"), ref.strong(l), err_msg=f"S_{l}")
+            np.testing.assert_array_equal(h.level_array(l, "cf"), ref.cf(l), err_msg=f"cf_{l}")
+            _same_csr(h.export(l, "P"), ref.matrix(l, "P"), rtol=0.0, what=f"P_{l}")
+        if l > 0:
+            np.testing.assert_array_equal(h.level_array(l, "inM"), ref.inM(l), err_msg=f"inM_{l}")
+            np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l), err_msg=f"keep_{l}")
+        np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14, err_msg=f"l1_{l}")
+    bd = torch.from_numpy(b).cuda()
+    x, info = h.solve(bd, tol=1e-8)
+    xr, ir = ref.pcg(b, tol=1e-8)
+    assert info.status == 0 and info.final_relres <= 1e-8
+    assert abs(info.iterations - ir.iterations) <= 1
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
+
+
 def test_setup_two_pass_spgemm_matches_oracle(amg, monkeypatch):
     """The counting (two-pass) SpGEMM, used when product bounds do not fit in
     memory, gives the same hierarchy."""
