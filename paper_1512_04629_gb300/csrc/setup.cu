@@ -49,6 +49,10 @@ __device__ __forceinline__ int64_t f64_key(double x) {
     const int64_t b = __double_as_longlong(x);
     return b >= 0 ? b : -(b & 0x7fffffffffffffffll);
 }
+// key(-x), the sign flipped on the integer pipes
+__device__ __forceinline__ int64_t f64_key_neg(double x) {
+    return f64_key(__longlong_as_double(__double_as_longlong(x) ^ (int64_t)0x8000000000000000ull));
+}
 // |x| as a key (the bit pattern without its sign)
 __device__ __forceinline__ int64_t f64_abs_key(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
 // Row kernels map a group of T lanes (T = 2..32, a power of two near the
@@ -164,7 +168,7 @@ __global__ void strength_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
     constexpr int64_t kNone = INT64_MIN;  // below every key
     int64_t mk = kNone;                   // max over j != i of -a_ij (as a key)
     for (int32_t p = p0 + t; p < p1; p += T)
-        if (ci[p] != i) mk = max(mk, f64_key(-v[p]));
+        if (ci[p] != i) mk = max(mk, f64_key_neg(v[p]));
     mk = group_max_i64<T>(mk);
     if (!live || mk <= 0) {  // no off-diagonal, or max(-a_ij) <= 0: no strong entry
         for (int32_t p = p0 + t; p < p1; p += T) strong[p] = 0;
@@ -172,7 +176,7 @@ __global__ void strength_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
     }
     const int64_t tk = f64_key(theta * f64_from_key(mk));
     for (int32_t p = p0 + t; p < p1; p += T)
-        strong[p] = (uint8_t)(ci[p] != i && f64_key(-v[p]) >= tk);
+        strong[p] = (uint8_t)(ci[p] != i && f64_key_neg(v[p]) >= tk);
 }
 
 // ---------------------------------------------------------------------------
@@ -328,6 +332,7 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
     if (cf[i] == kC) { pci[pos] = cmap[i]; pv[pos] = 1.0; prow[pos] = -1; return; }
     if (prp[i + 1] == pos) return;  // no strong C neighbour: empty row
     double diag = 0.0, sum_neg = 0.0, sum_pos = 0.0, sum_neg_c = 0.0, sum_pos_c = 0.0;
+#pragma unroll 4
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
         double a = v[p];
@@ -1083,6 +1088,7 @@ __global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int3
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double d = v[diagpos[i]];
+#pragma unroll 8
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
         if (!keep[p]) d += v[p];
     int32_t pos = hrp[i];
@@ -1187,12 +1193,21 @@ coarse_factor_smem_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const
             if (c <= r) a[r * n + c] -= a[r * n + j] * a[c * n + j];
         }
     }
+    // L^{-1} right-looking: start from the identity; at step i, row i of the
+    // result is final once divided by L_ii, and every later row r subtracts
+    // L_ri times it.  Entry (r, c) thus sees the terms L_rk X_kc in increasing
+    // k, then its division -- the forward substitution's order, with every
+    // thread busy at each step instead of one thread per column.
     __syncthreads();
-    for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
-        for (int32_t i = 0; i < n; ++i) {
-            double s2 = (i == c) ? 1.0 : 0.0;
-            for (int32_t k = c; k < i; ++k) s2 -= a[i * n + k] * li[k * n + c];
-            li[i * n + c] = (i < c) ? 0.0 : s2 / a[i * n + i];
+    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) li[t] = (t / n == t % n) ? 1.0 : 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        __syncthreads();
+        for (int32_t c = threadIdx.x; c <= i; c += blockDim.x) li[i * n + c] /= a[i * n + i];
+        __syncthreads();
+        const int32_t rows = n - i - 1, cols = i + 1;
+        for (int32_t t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+            const int32_t r = i + 1 + t / cols, c = t % cols;
+            li[r * n + c] -= a[r * n + i] * li[i * n + c];
         }
     }
     __syncthreads();
