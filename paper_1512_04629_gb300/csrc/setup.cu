@@ -203,18 +203,25 @@ __device__ __forceinline__ void warp_append(bool keep, int32_t i, int32_t *list,
     if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = i;
 }
 
+template <int T>
 __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tpos,
                                  const uint8_t *strong, uint64_t seed, int32_t level, double *w,
                                  int8_t *state, int *undecided, uint8_t *sym, int32_t *list) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool und = false;
-    if (i < n) {
-        int32_t cnt = 0;  // |S^T_i|: rows j whose strong set holds i
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: the group reduction and the append need every lane
+    int32_t cnt = 0;  // |S^T_i|: rows j whose strong set holds i
+    if (live) {
+        for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
             const uint8_t st = strong[tpos[p]];
             cnt += st;
             sym[p] = (uint8_t)(st | strong[p]);  // j in S_i u S^T_i, read by every round
         }
+    }
+    cnt = group_sum_i32<T>(cnt);
+    bool und = false;
+    if (live && t == 0) {
         uint64_t key = seed ^ ((uint64_t)(uint32_t)level << 40) ^ (uint64_t)i;
         double u = (double)(splitmix64(key) >> 11) * (1.0 / 9007199254740992.0);
         w[i] = (double)cnt + u;
@@ -648,11 +655,19 @@ spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_
     const unsigned gmask = W == 32 ? kFull : (((1u << W) - 1u) << (sub * W));
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t rb = warp * G; rb < nrows; rb += nwarps * G) {
+    // the next iteration's row and its A-row bounds are loaded one iteration
+    // ahead, so two of the four dependent loads per row overlap with work
+    const int64_t step = nwarps * G;
+    int64_t rb = warp * G;
+    int32_t i_nx = rb + sub < nrows ? rows[rb + sub] : 0;
+    int32_t p0_nx = rb + sub < nrows ? arp[i_nx] : 0, p1_nx = rb + sub < nrows ? arp[i_nx + 1] : 0;
+    for (; rb < nrows; rb += step) {
         const int64_t r = rb + sub;
         const bool live = r < nrows;
-        const int32_t i = live ? rows[r] : 0;
-        const int32_t p0 = live ? arp[i] : 0, nA = live ? arp[i + 1] - p0 : 0;
+        const int32_t i = i_nx;
+        const int32_t p0 = p0_nx, nA = p1_nx - p0_nx;
+        const int64_t rn = rb + step + sub;
+        i_nx = rn < nrows ? rows[rn] : 0;
         // expansion: lane sl owns product e = sl (there are at most W)
         bool valid = false;
         int32_t j = 0;
@@ -696,6 +711,8 @@ spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_
             }
             done += total;
         }
+        p0_nx = rn < nrows ? arp[i_nx] : 0;
+        p1_nx = rn < nrows ? arp[i_nx + 1] : 0;
         // bitonic sort of (j, e) across the group; empty lanes sort last
         uint64_t key = valid ? (((uint64_t)(uint32_t)j << 8) | (uint64_t)sl) : ~0ull;
 #pragma unroll
@@ -936,9 +953,18 @@ spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const 
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     AccTab<U> t(smem + (size_t)w * AccTab<U>::kBytes);
-    for (int32_t r = blockIdx.x * WARPS + w; r < nrows; r += gridDim.x * WARPS) {
-        const int32_t i = rows[r];
-        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ub[i], obase, cci, cv);
+    const int32_t step = gridDim.x * WARPS;
+    int32_t r = blockIdx.x * WARPS + w;
+    int32_t i_nx = r < nrows ? rows[r] : 0;  // loaded one row ahead
+    int64_t ub_nx = r < nrows ? ub[i_nx] : 0;
+    for (; r < nrows; r += step) {
+        const int32_t i = i_nx;
+        const int64_t ubi = ub_nx;
+        if (r + step < nrows) {
+            i_nx = rows[r + step];
+            ub_nx = ub[i_nx];
+        }
+        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ubi, obase, cci, cv);
         if (lane == 0) cnt[i] = u;
     }
 }
@@ -1367,8 +1393,12 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     int g = div_up(n, kThreads);
     const int T = row_lanes(A, 8);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
-    { pmis_init_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), tpos, strong, seed, level, w.as<double>(),
-                                            cf, dc, sym.as<uint8_t>(), list[0]); ::amg::count_launch(); }
+    with_row_lanes(T, [&](auto tc) {
+        constexpr int L = decltype(tc)::value;
+        pmis_init_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+            n, A.rp(), tpos, strong, seed, level, w.as<double>(), cf, dc, sym.as<uint8_t>(), list[0]);
+        ::amg::count_launch();
+    });
     AMG_CHECK_LAUNCH();
     int done = 0;   // rounds launched
     int last = n;   // bound on the list length at the start of the batch
