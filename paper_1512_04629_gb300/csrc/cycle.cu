@@ -103,27 +103,10 @@ __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32
     int32_t s = pos >> 5, lane = pos & 31;
     int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
     XT acc = XT(0);
-    // chunks of 8 entries: every value and column of the chunk is requested,
-    // then every gather, then the products are added in entry order -- two
-    // dependent round trips per chunk instead of two per entry group of 4
-    for (int32_t k0 = 0; k0 < w; k0 += 8) {
-        VT vv[8];
-        int32_t jj[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int32_t p = off + (k0 + u) * 32;
-            if (k0 + u < w) {
-                vv[u] = __ldg(sv + p);
-                jj[u] = sell_col<D16>(ix, p, row);
-            }
-        }
-        XT xx[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (k0 + u < w) xx[u] = gather(jj[u]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (k0 + u < w) acc += cvt<VT, XT>(vv[u]) * xx[u];
+#pragma unroll 4
+    for (int32_t k = 0; k < w; ++k) {
+        int32_t p = off + k * 32;
+        acc += cvt<VT, XT>(__ldg(sv + p)) * gather(sell_col<D16>(ix, p, row));
     }
     return acc;
 }
