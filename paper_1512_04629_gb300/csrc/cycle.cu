@@ -174,62 +174,11 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     }
 }
 
-// Length-sorted SELL (rows permuted inside windows of kSellSigma): one block
-// of kSellSigma threads per window.  The row sums go to shared memory under
-// their row's place in the window, and the epilogue then walks the window's
-// rows in order, so b, x, d and the outputs are read and written coalesced
-// instead of at permuted addresses (8-byte scattered stores cost a 32-byte
-// sector each).
-template <typename VT, typename XT, int OP, bool D16>
-__global__ void __launch_bounds__(kSellSigma, 2)
-sell_op_window_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
-                      const int32_t *__restrict__ sw, SellIdx ix, const VT *__restrict__ sv,
-                      const XT *__restrict__ b, const XT *__restrict__ dinv, const XT *__restrict__ x,
-                      XT *__restrict__ o1, XT *__restrict__ o2) {
-    __shared__ XT res[kSellSigma];
-    const int32_t base = blockIdx.x * kSellSigma;
-    const int32_t pos = base + threadIdx.x;
-    if (pos < n) {
-        const int32_t i = __ldg(perm + pos);  // inside [base, base + kSellSigma)
-        XT s;
-        if (OP == kPre) s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-        else s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
-        res[i - base] = s;
-    }
-    __syncthreads();
-    const int32_t i = base + threadIdx.x;
-    if (i >= n) return;
-    const XT s = res[threadIdx.x];
-    if (OP == kPre) {
-        XT bi = b[i];
-        o1[i] = bi * dinv[i];
-        o2[i] = bi - s;
-    } else if (OP == kPost) {
-        o1[i] = x[i] + dinv[i] * (b[i] - s);
-    } else if (OP == kSpmv) {
-        o1[i] = s;
-    } else if (OP == kSpmvScale) {
-        o1[i] = s;
-        o2[i] = s * dinv[i];
-    } else if (OP == kResX) {
-        o2[i] = b[i] - s;
-    } else {
-        o1[i] += s;
-    }
-}
-
 template <typename VT, typename XT, int OP>
 void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, XT *o1, XT *o2, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
-    if (A.variant == AMG_SPMV_SELL32 && A.sv && A.perm) {
-        const SellIdx ix{A.sci, A.sd};
-        const int grid = div_up(n, kSellSigma);
-        if (A.sd)
-            { sell_op_window_kernel<VT, XT, OP, true><<<grid, kSellSigma, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-        else
-            { sell_op_window_kernel<VT, XT, OP, false><<<grid, kSellSigma, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-    } else if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         const SellIdx ix{A.sci, A.sd};
         if (A.sd)
             { sell_op_kernel<VT, XT, OP, true><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
