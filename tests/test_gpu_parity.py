@@ -389,6 +389,16 @@ def test_tiny_matrix(amg):
     h = amg.Hierarchy.setup(A)
     x, info = h.solve(np.array([3.0]))
     assert info.status == 0 and abs(x[0] - 1.5) < 1e-14
+    # 2 x 2 SPD with both couplings: one level (below max_size), direct solve
+    A2 = sp.csr_matrix(np.array([[4.0, -1.0], [-1.0, 3.0]]))
+    h2 = amg.Hierarchy.setup(A2)
+    x2, info2 = h2.solve(np.array([1.0, 2.0]))
+    np.testing.assert_allclose(x2, np.linalg.solve(A2.toarray(), [1.0, 2.0]), rtol=1e-13)
+    # an empty matrix is rejected, not set up
+    E = amg.amg.csr_struct(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.setup(E)
+    assert e.value.status == 1
 
 
 def test_invalid_device_structures_rejected(amg):
