@@ -69,9 +69,13 @@ def _load():
         lib.orc_minimal_pattern.argtypes = [P(_CSR), P(_CSR), vp, vp]
         lib.orc_sparsify_diag.argtypes = [P(_CSR), vp, C.c_double, vp]
         lib.orc_sparsify_diag.restype = P(_CSR)
+        lib.orc_sparsify_full.argtypes = [P(_CSR), vp, C.c_double, C.c_double, vp]
+        lib.orc_sparsify_full.restype = P(_CSR)
         lib.orc_l1_diag.argtypes = [P(_CSR), vp]
         lib.orc_cholesky.argtypes = [C.c_int32, vp]
         lib.orc_chol_solve.argtypes = [C.c_int32, vp, vp, vp]
+        lib.orc_lu.argtypes = [C.c_int32, vp, vp]
+        lib.orc_lu_solve.argtypes = [C.c_int32, vp, vp, vp, vp]
         lib.orc_spmv.argtypes = [P(_CSR), vp, vp]
         lib.orc_uniform_weight.argtypes = [C.c_uint64, C.c_int32, C.c_int64]
         lib.orc_uniform_weight.restype = C.c_double
@@ -82,6 +86,13 @@ def _load():
         lib.orc_sparsify.argtypes = [vp, vp, C.c_int32]
         lib.orc_reintroduce.argtypes = [vp, C.c_int32, C.c_double, vp]
         lib.orc_sparsify_method.argtypes = [vp, vp, C.c_int32, C.c_int32]
+        lib.orc_sparsify_opts.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32]
+        lib.orc_gmres.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32, P(_Info)]
+        lib.orc_gmres_plain.argtypes = [P(_CSR), vp, vp, C.c_double, C.c_int32, C.c_int32,
+                                        P(_Info)]
+        lib.orc_adaptive_gmres.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
+                                           C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                           P(_Info)]
         lib.orc_vcycle.argtypes = [vp, vp, vp]
         lib.orc_pcg.argtypes = [vp, vp, vp, C.c_double, C.c_int32, P(_Info)]
         lib.orc_adaptive_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
@@ -222,6 +233,15 @@ def sparsify_diag(Ac, inM, gamma: float):
     return H, keep
 
 
+def sparsify_full(Ac, inM, gamma: float, theta: float = 0.25):
+    """Algorithm 3 with full lumping to strong neighbours; returns (Ahat, keep)."""
+    ca = to_c(Ac)
+    inM = np.ascontiguousarray(inM, dtype=np.uint8)
+    keep = np.zeros(ca.nnz, dtype=np.uint8)
+    H = _from_c(_load().orc_sparsify_full(C.byref(ca), _ptr(inM), gamma, theta, _ptr(keep)), True)
+    return H, keep
+
+
 def l1_diag(A) -> np.ndarray:
     c = to_c(A)
     d = np.zeros(c.nrows, dtype=np.float64)
@@ -251,6 +271,35 @@ def chol_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
     x = np.zeros_like(b)
     _load().orc_chol_solve(L.shape[0], _ptr(L), _ptr(b), _ptr(x))
     return x
+
+
+def lu(a: np.ndarray):
+    """Dense LU with partial pivoting; returns (LU in place, pivot rows)."""
+    a = np.array(a, dtype=np.float64, order="C", copy=True)
+    piv = np.zeros(a.shape[0], dtype=np.int32)
+    st = _load().orc_lu(a.shape[0], _ptr(a), _ptr(piv))
+    if st:
+        raise np.linalg.LinAlgError("singular")
+    return a, piv
+
+
+def lu_solve(LU: np.ndarray, piv: np.ndarray, b: np.ndarray) -> np.ndarray:
+    LU = np.ascontiguousarray(LU, dtype=np.float64)
+    piv = np.ascontiguousarray(piv, dtype=np.int32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    _load().orc_lu_solve(LU.shape[0], _ptr(LU), _ptr(piv), _ptr(b), _ptr(x))
+    return x
+
+
+def gmres_plain(A, b, tol: float = 1e-8, max_it: int = 500, restart: int = 30):
+    """Unpreconditioned restarted GMRES from x0 = 0 (the oracle's GMRES core)."""
+    c = to_c(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    info = _Info()
+    _load().orc_gmres_plain(C.byref(c), _ptr(b), _ptr(x), tol, max_it, restart, C.byref(info))
+    return x, _info(info)
 
 
 def gamma_schedule(gamma, s: int, gamma_min: float = 0.01):
@@ -333,10 +382,11 @@ class Hierarchy:
     def gamma(self, level) -> float:
         return self._lib.orc_level_gamma(self._h, level)
 
-    def sparsify(self, gamma, method: int = 0):
-        """method 0: Sparse Galerkin; 1: Hybrid Galerkin."""
+    def sparsify(self, gamma, method: int = 0, lump: int = 0):
+        """method 0: Sparse Galerkin; 1: Hybrid Galerkin.  lump 0: diagonal
+        lumping (Algorithm 3b); 1: full lumping to strong neighbours (Algorithm 3)."""
         g = np.ascontiguousarray(gamma, dtype=np.float64)
-        st = self._lib.orc_sparsify_method(self._h, _ptr(g), len(g), method)
+        st = self._lib.orc_sparsify_opts(self._h, _ptr(g), len(g), method, lump)
         if st:
             raise RuntimeError(f"orc_sparsify status {st}")
 
@@ -367,6 +417,22 @@ class Hierarchy:
         info = _Info()
         self._lib.orc_adaptive_solve(self._h, _ptr(b), _ptr(x), tol, max_it, k, s, gamma_min,
                                      rho_max, C.byref(info))
+        return x, _info(info)
+
+    def gmres(self, b, tol: float = 1e-8, max_it: int = 500, restart: int = 30):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        info = _Info()
+        self._lib.orc_gmres(self._h, _ptr(b), _ptr(x), tol, max_it, restart, C.byref(info))
+        return x, _info(info)
+
+    def adaptive_gmres(self, b, tol: float = 1e-8, max_it: int = 500, restart: int = 30,
+                       k: int = 3, s: int = 1, gamma_min: float = 0.01, rho_max: float = 0.5):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros_like(b)
+        info = _Info()
+        self._lib.orc_adaptive_gmres(self._h, _ptr(b), _ptr(x), tol, max_it, restart, k, s,
+                                     gamma_min, rho_max, C.byref(info))
         return x, _info(info)
 
     def level_sizes(self):

@@ -519,6 +519,117 @@ orc_csr *orc_sparsify_diag(const orc_csr *Ac, const uint8_t *inM, double gamma, 
     return H;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Algorithm 3 with its own second loop (full lumping to strong neighbours, */
+/* the non-Galerkin sparsify of Falgout and Schroder).  The first loop and  */
+/* N are those of orc_sparsify_diag (the diagonal always kept, no ismax     */
+/* guard: Algorithm 3 has none).  Readings:                                 */
+/*  - S is the classical strength matrix of Ac itself (the indices j, k of  */
+/*    W are coarse points), with the rule of orc_strength and the setup's   */
+/*    theta; S_{j,k} = (Ac)_{j,k} on strong entries, 0 elsewhere;           */
+/*  - the loop over "omega" runs over W (the set just built);               */
+/*  - "(Ahat_c)_{i,j} = (A_c)_{i,j}" for (i,j) in N is the starting value   */
+/*    of Ahat_c, not an assignment that could overwrite lumped values       */
+/*    added earlier in the loop: Ahat_c starts as Ac restricted to N and    */
+/*    every update below accumulates on it;                                 */
+/*  - a dropped entry whose W is empty (or whose strong weights sum to 0)   */
+/*    has no neighbour to take it: it is lumped to the diagonal of its row, */
+/*    as in Algorithm 3b, so row sums stay exact;                           */
+/*  - dropped entries are processed in CSR order (row by row, increasing    */
+/*    column), each k of W in increasing column order, and the three        */
+/*    updates of one k in the order written: (i,k), (k,i), (k,k).           */
+/* Each update is symmetric and leaves every row sum unchanged, so Ahat_c   */
+/* is symmetric with the row sums of Ac -- but it can lose definiteness.    */
+/* ------------------------------------------------------------------------ */
+orc_csr *orc_sparsify_full(const orc_csr *Ac, const uint8_t *inM, double gamma, double theta,
+                           uint8_t *keep) {
+    int32_t n = Ac->nrows;
+    int32_t nnz = Ac->nnz;
+    uint8_t *flag = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    uint8_t *S = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    double *val = (double *)malloc(sizeof(double) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!flag || !S || !val) {
+        free(flag); free(S); free(val);
+        return NULL;
+    }
+    /* first loop: entries passing the drop test or in M */
+    for (int32_t i = 0; i < n; ++i) {
+        double m = 0.0;
+        for (int32_t p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p)
+            if (Ac->col[p] != i && fabs(Ac->val[p]) > m) m = fabs(Ac->val[p]);
+        double t = gamma * m;
+        for (int32_t p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p)
+            flag[p] = (uint8_t)(Ac->col[p] != i && (inM[p] || fabs(Ac->val[p]) >= t));
+    }
+    /* N: flagged entries, their mirrors and the diagonal */
+    for (int32_t p = 0; p < nnz; ++p) keep[p] = 0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p) {
+            int32_t j = Ac->col[p];
+            if (j == i) {
+                keep[p] = 1;
+            } else if (flag[p]) {
+                keep[p] = 1;
+                int32_t q = find_entry(Ac, j, i);
+                if (q >= 0) keep[q] = 1;
+            }
+        }
+    orc_strength(Ac, theta, S);
+    /* Ahat_c starts as Ac on N */
+    for (int32_t p = 0; p < nnz; ++p) val[p] = keep[p] ? Ac->val[p] : 0.0;
+    /* second loop: lump every dropped entry to the strong neighbours of j */
+    /* that row i keeps                                                     */
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p) {
+            if (keep[p]) continue;
+            int32_t j = Ac->col[p];
+            double a = Ac->val[p];
+            /* sum over W of |S_{j,m}| */
+            double denom = 0.0;
+            for (int32_t q = Ac->rowptr[j]; q < Ac->rowptr[j + 1]; ++q) {
+                if (!S[q]) continue;
+                int32_t pik = find_entry(Ac, i, Ac->col[q]);
+                if (pik >= 0 && keep[pik]) denom += fabs(Ac->val[q]);
+            }
+            if (!(denom > 0.0)) {
+                int32_t pii = find_entry(Ac, i, i);
+                if (pii >= 0) val[pii] += a;
+                continue;
+            }
+            for (int32_t q = Ac->rowptr[j]; q < Ac->rowptr[j + 1]; ++q) {
+                if (!S[q]) continue;
+                int32_t k = Ac->col[q];
+                int32_t pik = find_entry(Ac, i, k);
+                if (pik < 0 || !keep[pik]) continue;
+                double alpha = fabs(Ac->val[q]) / denom;
+                double t = alpha * a;
+                val[pik] += t;
+                int32_t pki = find_entry(Ac, k, i);
+                if (pki >= 0) val[pki] += t;
+                int32_t pkk = find_entry(Ac, k, k);
+                if (pkk >= 0) val[pkk] -= t;
+            }
+        }
+    int64_t knnz = 0;
+    for (int32_t p = 0; p < nnz; ++p) knnz += keep[p];
+    orc_csr *H = csr_alloc(n, Ac->ncols, knnz);
+    if (H) {
+        int32_t pos = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            H->rowptr[i] = pos;
+            for (int32_t p = Ac->rowptr[i]; p < Ac->rowptr[i + 1]; ++p) {
+                if (!keep[p]) continue;
+                H->col[pos] = Ac->col[p];
+                H->val[pos] = val[p];
+                pos++;
+            }
+        }
+        H->rowptr[n] = pos;
+    }
+    free(flag); free(S); free(val);
+    return H;
+}
+
 /* ell1 diagonal d_i = sum_j |a_ij| of the relaxed operator (reading: the    */
 /* paper's "relax" is e.g. Jacobi; ell1-Jacobi without damping is used).    */
 void orc_l1_diag(const orc_csr *A, double *d) {
@@ -558,6 +669,50 @@ void orc_chol_solve(int32_t n, const double *L, const double *b, double *x) {
         double s = x[i];
         for (int32_t k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * x[k];
         x[i] = s / L[(size_t)i * n + i];
+    }
+}
+
+/* Dense LU with partial pivoting, P A = L U in place (row-major; unit L    */
+/* below the diagonal).  piv[j] is the row swapped with row j at step j (the */
+/* first row of largest |a_ij|, i >= j).  ORC_BREAKDOWN if a pivot is 0.    */
+int orc_lu(int32_t n, double *a, int32_t *piv) {
+    for (int32_t j = 0; j < n; ++j) {
+        int32_t r = j;
+        for (int32_t i = j + 1; i < n; ++i)
+            if (fabs(a[(size_t)i * n + j]) > fabs(a[(size_t)r * n + j])) r = i;
+        piv[j] = r;
+        if (!(a[(size_t)r * n + j] != 0.0)) return ORC_BREAKDOWN;
+        if (r != j)
+            for (int32_t c = 0; c < n; ++c) {
+                double t = a[(size_t)j * n + c];
+                a[(size_t)j * n + c] = a[(size_t)r * n + c];
+                a[(size_t)r * n + c] = t;
+            }
+        for (int32_t i = j + 1; i < n; ++i) {
+            double l = a[(size_t)i * n + j] / a[(size_t)j * n + j];
+            a[(size_t)i * n + j] = l;
+            for (int32_t c = j + 1; c < n; ++c) a[(size_t)i * n + c] -= l * a[(size_t)j * n + c];
+        }
+    }
+    return ORC_OK;
+}
+
+void orc_lu_solve(int32_t n, const double *LU, const int32_t *piv, const double *b, double *x) {
+    for (int32_t i = 0; i < n; ++i) x[i] = b[i];
+    for (int32_t j = 0; j < n; ++j) {
+        double t = x[j];
+        x[j] = x[piv[j]];
+        x[piv[j]] = t;
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int32_t k = 0; k < i; ++k) s -= LU[(size_t)i * n + k] * x[k];
+        x[i] = s;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int32_t k = i + 1; k < n; ++k) s -= LU[(size_t)i * n + k] * x[k];
+        x[i] = s / LU[(size_t)i * n + i];
     }
 }
 
@@ -608,8 +763,11 @@ typedef struct {
 struct orc_hier {
     int32_t nlev;
     int32_t method; /* 0 Sparse Galerkin, 1 Hybrid Galerkin (set by orc_sparsify_method) */
+    int32_t lump;   /* 0 diagonal lumping (Algorithm 3b), 1 full lumping (Algorithm 3) */
+    double theta;   /* strength threshold of the setup (full lumping's S) */
     orc_level lev[64];
-    double *chol; /* dense Cholesky factor of Ahat of the coarsest level */
+    double *chol;   /* dense factor of Ahat of the coarsest level: Cholesky, or LU */
+    int32_t *piv;   /* row permutation of the LU factor (NULL: Cholesky) */
 };
 
 static void level_free(orc_level *L) {
@@ -627,6 +785,7 @@ void orc_free(orc_hier *h) {
     if (!h) return;
     for (int32_t l = 0; l < h->nlev; ++l) level_free(&h->lev[l]);
     free(h->chol);
+    free(h->piv);
     free(h);
 }
 
@@ -643,16 +802,32 @@ static int level_workspace(orc_level *L) {
     return ORC_OK;
 }
 
+/* Coarsest-level direct solve of Algorithm 2 (the paper does not name the  */
+/* factorization).  Reading: Cholesky; when the coarsest relaxed operator is */
+/* not positive definite (full lumping can make it indefinite) an LU        */
+/* factorization with partial pivoting takes its place.                     */
+static void densify_coarsest(const orc_level *L, double *a) {
+    int32_t n = L->A->nrows;
+    for (size_t t = 0; t < (size_t)n * (size_t)n; ++t) a[t] = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t p = L->Ahat->rowptr[i]; p < L->Ahat->rowptr[i + 1]; ++p)
+            a[(size_t)i * n + L->Ahat->col[p]] = L->Ahat->val[p];
+}
+
 static int factor_coarsest(orc_hier *h) {
     orc_level *L = &h->lev[h->nlev - 1];
     int32_t n = L->A->nrows;
     free(h->chol);
+    free(h->piv);
+    h->piv = NULL;
     h->chol = (double *)calloc((size_t)n * (size_t)n + 1, sizeof(double));
     if (!h->chol) return ORC_OOM;
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t p = L->Ahat->rowptr[i]; p < L->Ahat->rowptr[i + 1]; ++p)
-            h->chol[(size_t)i * n + L->Ahat->col[p]] = L->Ahat->val[p];
-    return orc_cholesky(n, h->chol);
+    densify_coarsest(L, h->chol);
+    if (orc_cholesky(n, h->chol) == ORC_OK) return ORC_OK;
+    h->piv = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    if (!h->piv) return ORC_OOM;
+    densify_coarsest(L, h->chol);
+    return orc_lu(n, h->chol, h->piv);
 }
 
 /* Algorithm 1 with sparsify off (the Galerkin hierarchy of Algorithm 4's   */
@@ -673,6 +848,7 @@ orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t m
     }
     h->lev[0].A = csr_copy(A0);
     h->nlev = 1;
+    h->theta = theta;
     if (!h->lev[0].A) goto oom;
     for (int32_t l = 0; l + 1 < max_levels; ++l) {
         orc_level *L = &h->lev[l];
@@ -766,7 +942,8 @@ static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method) {
             }
             inM = hyb;
         }
-        orc_csr *H = orc_sparsify_diag(L->A, inM, L->gamma, L->keep);
+        orc_csr *H = h->lump ? orc_sparsify_full(L->A, inM, L->gamma, h->theta, L->keep)
+                             : orc_sparsify_diag(L->A, inM, L->gamma, L->keep);
         free(hyb);
         if (!H) return ORC_OOM;
         L->Ahat = H;
@@ -781,10 +958,18 @@ static int resparsify_level_m(orc_hier *h, int32_t l, int32_t method) {
 /* loop writes Ahat_l; Ahat_0 = A_0).  gamma[l] applies to level l, levels  */
 /* past ngamma - 1 use gamma[ngamma - 1]; gamma[0] must be 0.               */
 int orc_sparsify_method(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method) {
-    if (ngamma < 1 || gamma[0] != 0.0 || method < 0 || method > 1) return ORC_INVALID;
+    return orc_sparsify_opts(h, gamma, ngamma, method, 0);
+}
+
+/* lump 0: the loop of Algorithm 3b (diagonal lumping); 1: Algorithm 3's own */
+/* loop (full lumping to strong neighbours). */
+int orc_sparsify_opts(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method, int32_t lump) {
+    if (ngamma < 1 || gamma[0] != 0.0 || method < 0 || method > 1 || lump < 0 || lump > 1)
+        return ORC_INVALID;
     for (int32_t l = 0; l < ngamma; ++l)
         if (!(gamma[l] >= 0.0) || !isfinite(gamma[l])) return ORC_INVALID;
     h->method = method;
+    h->lump = lump;
     for (int32_t l = 1; l < h->nlev; ++l) {  /* in order: Hybrid reads Ahat_{l-1} */
         h->lev[l].gamma = gamma[l < ngamma ? l : ngamma - 1];
         int st = resparsify_level_m(h, l, method);
@@ -831,7 +1016,8 @@ int orc_vcycle(orc_hier *h, const double *b, double *x) {
         orc_spmv(V->R, V->r, h->lev[l + 1].b);                          /* restrict */
     }
     orc_level *Cl = &h->lev[L - 1];
-    orc_chol_solve(Cl->A->nrows, h->chol, Cl->b, Cl->x);                /* coarse solve */
+    if (h->piv) orc_lu_solve(Cl->A->nrows, h->chol, h->piv, Cl->b, Cl->x);  /* coarse solve */
+    else orc_chol_solve(Cl->A->nrows, h->chol, Cl->b, Cl->x);
     for (int32_t l = L - 2; l >= 0; --l) {
         orc_level *V = &h->lev[l];
         int32_t n = V->A->nrows;
@@ -1045,6 +1231,266 @@ int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int3
     info->status = status;
     free(xs); free(work);
     pcg_free(&st);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restarted GMRES, right-preconditioned in the flexible form (FGMRES,      */
+/* Saad 1993): z_j = M v_j is kept and x = x0 + Z y.  The paper solves with */
+/* GMRES where full lumping (Algorithm 3) can cost positive definiteness.   */
+/* Readings: x0 = 0; Arnoldi by modified Gram-Schmidt; Givens rotations     */
+/* reduce the Hessenberg matrix column by column, so |g_{j+1}| is the       */
+/* residual norm of the j-step iterate; a run stops when that estimate      */
+/* reaches tol ||b|| and the true residual b - A_0 x confirms it (else the  */
+/* cycle restarts from x, a residual replacement), restarts after `restart` */
+/* steps, and ends at max_it steps.  M is one V-cycle, or the identity in   */
+/* the unpreconditioned variant.  The state is resumable: Algorithm 5 reads */
+/* the iterate between checks without ending the cycle.                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    const orc_csr *A;
+    orc_hier *h;        /* preconditioner: V-cycle of h, or NULL = identity */
+    int32_t n, m, j;    /* size, restart length, steps in the current cycle */
+    double *V, *Z;      /* (m + 1) x n and m x n, row j = vector j */
+    double *H;          /* (m + 1) x m, H[i * m + c] */
+    double *cs, *sn, *g, *y, *x0, *w;
+} gm_state;
+
+typedef struct {
+    int32_t steps, converged, breakdown, replacements;
+    double rnorm; /* residual estimate (or true residual at convergence) */
+} gm_run;
+
+static void gm_free(gm_state *s) {
+    free(s->V); free(s->Z); free(s->H); free(s->cs); free(s->sn); free(s->g); free(s->y);
+    free(s->x0); free(s->w);
+    memset(s, 0, sizeof(*s));
+}
+
+static int gm_alloc(gm_state *s, const orc_csr *A, orc_hier *h, int32_t m) {
+    memset(s, 0, sizeof(*s));
+    s->A = A;
+    s->h = h;
+    s->n = A->nrows;
+    s->m = m;
+    size_t n = (size_t)(s->n > 0 ? s->n : 1);
+    s->V = (double *)calloc(n * (size_t)(m + 1), sizeof(double));
+    s->Z = (double *)calloc(n * (size_t)m, sizeof(double));
+    s->H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+    s->cs = (double *)calloc((size_t)m, sizeof(double));
+    s->sn = (double *)calloc((size_t)m, sizeof(double));
+    s->g = (double *)calloc((size_t)m + 1, sizeof(double));
+    s->y = (double *)calloc((size_t)m, sizeof(double));
+    s->x0 = (double *)calloc(n, sizeof(double));
+    s->w = (double *)calloc(n, sizeof(double));
+    if (!s->V || !s->Z || !s->H || !s->cs || !s->sn || !s->g || !s->y || !s->x0 || !s->w) {
+        gm_free(s);
+        return ORC_OOM;
+    }
+    return ORC_OK;
+}
+
+/* new cycle from x: v_0 = r / ||r||, g = ||r|| e_1; returns ||r|| */
+static double gm_start(gm_state *s, const double *b, const double *x) {
+    int32_t n = s->n;
+    orc_spmv(s->A, x, s->w);
+    for (int32_t i = 0; i < n; ++i) s->w[i] = b[i] - s->w[i];
+    double beta = norm2(n, s->w);
+    for (int32_t i = 0; i < n; ++i) s->V[i] = (beta > 0.0) ? s->w[i] / beta : 0.0;
+    memcpy(s->x0, x, sizeof(double) * (size_t)n);
+    for (int32_t i = 0; i <= s->m; ++i) s->g[i] = 0.0;
+    s->g[0] = beta;
+    s->j = 0;
+    return beta;
+}
+
+/* x = x0 + Z y with R y = g over the cycle's first j steps (back substitution) */
+static void gm_form_x(gm_state *s, double *x) {
+    int32_t n = s->n, m = s->m, j = s->j;
+    for (int32_t i = j - 1; i >= 0; --i) {
+        double t = s->g[i];
+        for (int32_t c = i + 1; c < j; ++c) t -= s->H[(size_t)i * m + c] * s->y[c];
+        s->y[i] = t / s->H[(size_t)i * m + i];
+    }
+    for (int32_t e = 0; e < n; ++e) {
+        double t = s->x0[e];
+        for (int32_t i = 0; i < j; ++i) t += s->y[i] * s->Z[(size_t)i * n + e];
+        x[e] = t;
+    }
+}
+
+static void gm_iterate(gm_state *s, const double *b, double *x, double bnorm, double tol, int32_t max_steps,
+                       gm_run *run) {
+    int32_t n = s->n, m = s->m;
+    memset(run, 0, sizeof(*run));
+    run->rnorm = fabs(s->g[s->j]);
+    if (run->rnorm <= tol * bnorm) {
+        run->converged = 1;
+        return;
+    }
+    while (run->steps < max_steps) {
+        if (s->j == m) {                        /* restart */
+            gm_form_x(s, x);
+            gm_start(s, b, x);
+        }
+        int32_t j = s->j;
+        double *vj = s->V + (size_t)j * n, *zj = s->Z + (size_t)j * n, *w = s->w;
+        if (s->h) orc_vcycle(s->h, vj, zj);
+        else memcpy(zj, vj, sizeof(double) * (size_t)n);
+        orc_spmv(s->A, zj, w);
+        run->steps++;
+        for (int32_t i = 0; i <= j; ++i) {      /* modified Gram-Schmidt */
+            const double *vi = s->V + (size_t)i * n;
+            double hij = dot(n, w, vi);
+            s->H[(size_t)i * m + j] = hij;
+            for (int32_t e = 0; e < n; ++e) w[e] -= hij * vi[e];
+        }
+        double hn = norm2(n, w);
+        if (!isfinite(hn)) {                    /* the step is lost: keep the iterate of j steps */
+            run->breakdown = 1;
+            gm_form_x(s, x);
+            return;
+        }
+        s->H[(size_t)(j + 1) * m + j] = hn;
+        double *vn = s->V + (size_t)(j + 1) * n;
+        for (int32_t e = 0; e < n; ++e) vn[e] = (hn > 0.0) ? w[e] / hn : 0.0;
+        for (int32_t i = 0; i < j; ++i) {       /* earlier rotations on column j */
+            double a = s->H[(size_t)i * m + j], c = s->H[(size_t)(i + 1) * m + j];
+            s->H[(size_t)i * m + j] = s->cs[i] * a + s->sn[i] * c;
+            s->H[(size_t)(i + 1) * m + j] = -s->sn[i] * a + s->cs[i] * c;
+        }
+        double a = s->H[(size_t)j * m + j], c = hn;
+        double r = sqrt(a * a + c * c);
+        s->cs[j] = (r > 0.0) ? a / r : 1.0;
+        s->sn[j] = (r > 0.0) ? c / r : 0.0;
+        s->H[(size_t)j * m + j] = r;
+        s->H[(size_t)(j + 1) * m + j] = 0.0;
+        s->g[j + 1] = -s->sn[j] * s->g[j];
+        s->g[j] = s->cs[j] * s->g[j];
+        s->j = j + 1;
+        run->rnorm = fabs(s->g[j + 1]);
+        if (!(r > 0.0)) {                       /* singular Hessenberg column */
+            run->breakdown = 1;
+            s->j = j;
+            gm_form_x(s, x);
+            return;
+        }
+        if (run->rnorm <= tol * bnorm || hn == 0.0) {
+            gm_form_x(s, x);
+            double tn = gm_start(s, b, x);
+            run->rnorm = tn;
+            if (tn <= tol * bnorm) {
+                run->converged = 1;
+                return;
+            }
+            run->replacements++;
+        }
+    }
+    gm_form_x(s, x);
+}
+
+static int gmres_solve(const orc_csr *A, orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                       int32_t restart, orc_info *info) {
+    int32_t n = A->nrows;
+    memset(info, 0, sizeof(*info));
+    if (restart < 1 || max_it < 0) return ORC_INVALID;
+    for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+    double bnorm = norm2(n, b);
+    if (bnorm == 0.0) return ORC_OK;
+    gm_state s;
+    if (gm_alloc(&s, A, h, restart) != ORC_OK) return ORC_OOM;
+    double r0 = gm_start(&s, b, x);
+    gm_run run;
+    gm_iterate(&s, b, x, bnorm, tol, max_it, &run);
+    orc_spmv(A, x, s.w);
+    double t = 0.0;
+    for (int32_t i = 0; i < n; ++i) t += (b[i] - s.w[i]) * (b[i] - s.w[i]);
+    info->iterations = run.steps;
+    info->replacements = run.replacements;
+    info->final_relres = sqrt(t) / bnorm;
+    info->conv_factor = run.steps > 0 ? pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
+    info->status = run.converged ? ORC_OK : (run.breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
+    gm_free(&s);
+    return info->status;
+}
+
+int orc_gmres(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
+              orc_info *info) {
+    return gmres_solve(h->lev[0].A, h, b, x, tol, max_it, restart, info);
+}
+
+int orc_gmres_plain(const orc_csr *A, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
+                    orc_info *info) {
+    return gmres_solve(A, NULL, b, x, tol, max_it, restart, info);
+}
+
+/* Algorithm 5 around GMRES: as orc_adaptive_solve, every k steps the       */
+/* iterate is formed (the cycle goes on) and its true residual checked; a  */
+/* reintroduction ends the cycle and GMRES restarts with the new M.         */
+int orc_adaptive_gmres(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
+                       int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info) {
+    int32_t n = h->lev[0].A->nrows;
+    memset(info, 0, sizeof(*info));
+    if (k < 1 || s < 1 || restart < 1) return ORC_INVALID;
+    for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
+    double bnorm = norm2(n, b);
+    if (bnorm == 0.0) return ORC_OK;
+    double *xs = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *work = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    gm_state st;
+    if (!xs || !work || gm_alloc(&st, h->lev[0].A, h, restart) != ORC_OK) {
+        free(xs); free(work);
+        return ORC_OOM;
+    }
+    gm_start(&st, b, x);
+    double rstart = bnorm, rend = bnorm;
+    int32_t total = 0;
+    int converged = 0, breakdown = 0, status = ORC_OK;
+    int32_t changed[64];
+    while (total < max_it) {
+        memcpy(xs, x, sizeof(double) * (size_t)n);
+        gm_run run;
+        int32_t steps = (max_it - total < k) ? max_it - total : k;
+        gm_iterate(&st, b, x, bnorm, tol, steps, &run);
+        total += run.steps;
+        info->replacements += run.replacements;
+        rend = true_resnorm(h, b, x, work);
+        if (run.converged || rend <= tol * bnorm) {
+            converged = 1;
+            break;
+        }
+        breakdown = run.breakdown;
+        double factor = (run.steps > 0) ? pow(rend / rstart, 1.0 / run.steps) : 1.0;
+        if (factor > rho_max || breakdown) {
+            int cnt = orc_reintroduce(h, s, gamma_min, changed);
+            if (cnt < 0) {
+                status = -cnt;
+                break;
+            }
+            if (cnt == 0 && breakdown) {
+                if (!(rend <= rstart)) memcpy(x, xs, sizeof(double) * (size_t)n);
+                break;
+            }
+            if (cnt > 0) {
+                info->resets++;
+                breakdown = 0;
+                if (!(rend <= rstart)) {
+                    memcpy(x, xs, sizeof(double) * (size_t)n);
+                    rend = rstart;
+                }
+                gm_start(&st, b, x);
+            }
+        }
+        rstart = rend;
+    }
+    info->iterations = total;
+    info->final_relres = true_resnorm(h, b, x, work) / bnorm;
+    info->conv_factor = total > 0 ? pow(info->final_relres, 1.0 / total) : 0.0;
+    if (status == ORC_OK)
+        status = converged ? ORC_OK : (breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
+    info->status = status;
+    free(xs); free(work);
+    gm_free(&st);
     return status;
 }
 

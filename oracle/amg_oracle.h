@@ -60,9 +60,13 @@ orc_csr *orc_transpose(const orc_csr *M);
 orc_csr *orc_spgemm(const orc_csr *A, const orc_csr *B);
 int orc_minimal_pattern(const orc_csr *Ac, const orc_csr *AP, const int8_t *cf, uint8_t *inM);
 orc_csr *orc_sparsify_diag(const orc_csr *Ac, const uint8_t *inM, double gamma, uint8_t *keep);
+orc_csr *orc_sparsify_full(const orc_csr *Ac, const uint8_t *inM, double gamma, double theta,
+                           uint8_t *keep);
 void orc_l1_diag(const orc_csr *A, double *d);
 int orc_cholesky(int32_t n, double *a);
 void orc_chol_solve(int32_t n, const double *L, const double *b, double *x);
+int orc_lu(int32_t n, double *a, int32_t *piv);
+void orc_lu_solve(int32_t n, const double *LU, const int32_t *piv, const double *b, double *x);
 void orc_spmv(const orc_csr *A, const double *x, double *y);
 double orc_uniform_weight(uint64_t seed, int32_t level, int64_t i);
 int orc_gamma_schedule(double *gamma, int32_t nlev, int32_t s, double gamma_min, int32_t *changed);
@@ -74,10 +78,21 @@ int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma);
 /* method 0: Sparse Galerkin (M from the Galerkin A_{l-1}); 1: Hybrid Galerkin
  * (M from the sparsified Ahat_{l-1}, levels processed in order). */
 int orc_sparsify_method(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method);
+/* the same with lump 0: diagonal lumping (Algorithm 3b), 1: full lumping to
+ * strong neighbours (Algorithm 3's own loop) */
+int orc_sparsify_opts(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method, int32_t lump);
 int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed);
 int orc_vcycle(orc_hier *h, const double *b, double *x);
 int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info);
 int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                       int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info);
+/* restarted right-preconditioned (flexible) GMRES with M = one V-cycle, the
+ * same unpreconditioned on a plain CSR matrix, and Algorithm 5 around it */
+int orc_gmres(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
+              orc_info *info);
+int orc_gmres_plain(const orc_csr *A, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
+                    orc_info *info);
+int orc_adaptive_gmres(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t restart,
                        int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info);
 void orc_free(orc_hier *h);
 void orc_csr_free(orc_csr *m);

@@ -628,3 +628,269 @@ def test_hybrid_keeps_theorem1_and_solves(gamma):
         b = gen.rhs_uniform(A.n, 4)
         x, info = h.pcg(b)
         assert info.status == 0 and info.final_relres <= 1e-8
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 3's own loop: full lumping to strong neighbours
+# ---------------------------------------------------------------------------
+def test_full_lumping_hand_example():
+    """Worked by hand (gamma = 0.5, theta = 0.25, M empty).
+
+    Row maxima 2, 2, 1, 2: only a_03 = a_30 = -0.5 fail the drop test, so N is
+    every other entry plus the diagonal.  Strength rows (theta 0.25): row 0 ->
+    {1, 3}, row 3 -> {0, 1, 2}.
+    Drop (0,3): W = {k : S_3k != 0, (0,k) in N} = {0, 1}, weights |a_30| = 0.5
+    and |a_31| = 2 -> alpha = 0.2, 0.8; t = -0.1, -0.4.  k = 0 adds t twice to
+    a_00 and subtracts it once (net -0.1); k = 1 adds -0.4 to a_01 and a_10
+    and +0.4 to a_11.
+    Drop (3,0): W = {k : S_0k != 0, (3,k) in N} = {1, 3}, weights 2 and 0.5
+    -> t = -0.4 (k = 1: a_31, a_13 -= 0.4, a_11 += 0.4) and t = -0.1 (k = 3:
+    net -0.1 on a_33).
+    """
+    A = np.array([[4.0, -2.0, 0.0, -0.5],
+                  [-2.0, 6.0, -1.0, -2.0],
+                  [0.0, -1.0, 3.0, -1.0],
+                  [-0.5, -2.0, -1.0, 4.0]])
+    want = np.array([[3.9, -2.4, 0.0, 0.0],
+                     [-2.4, 6.8, -1.0, -2.4],
+                     [0.0, -1.0, 3.0, -1.0],
+                     [0.0, -2.4, -1.0, 3.9]])
+    Ac = csr_from_dense(A)
+    H, keep = oracle.sparsify_full(Ac, np.zeros(Ac.nnz, np.uint8), 0.5, 0.25)
+    np.testing.assert_allclose(H.todense(), want, rtol=0, atol=1e-15)
+    assert H.nnz == Ac.nnz - 2 and keep.sum() == Ac.nnz - 2
+
+
+def test_full_lumping_empty_w_goes_to_diagonal():
+    """Worked by hand: a_02 = a_20 = -0.1 are dropped (gamma 0.5); row 2's only
+    strong neighbour is 3, which row 0 does not hold, and row 0's only strong
+    neighbour is 1, which row 2 does not hold, so both W are empty and each
+    value goes to its own row's diagonal (4 -> 3.9)."""
+    A = np.array([[4.0, -3.0, -0.1, 0.0],
+                  [-3.0, 5.0, 0.0, 0.0],
+                  [-0.1, 0.0, 4.0, -3.0],
+                  [0.0, 0.0, -3.0, 5.0]])
+    want = np.array([[3.9, -3.0, 0.0, 0.0],
+                     [-3.0, 5.0, 0.0, 0.0],
+                     [0.0, 0.0, 3.9, -3.0],
+                     [0.0, 0.0, -3.0, 5.0]])
+    Ac = csr_from_dense(A)
+    H, _ = oracle.sparsify_full(Ac, np.zeros(Ac.nnz, np.uint8), 0.5, 0.25)
+    np.testing.assert_allclose(H.todense(), want, rtol=0, atol=1e-15)
+
+
+def _dense_full_lumping(Ac, inM, gamma, theta):
+    """Brute force on a dense copy: Ahat = A on N, then for each dropped
+    (i, j) in row-major order the rank-3 symmetric update
+    t (e_i e_k^T + e_k e_i^T - e_k e_k^T) for every k in W, t = alpha a_ij."""
+    D = Ac.toarray()
+    n = D.shape[0]
+    rows = np.repeat(np.arange(n), np.diff(Ac.indptr))
+    stored = np.zeros_like(D, dtype=bool)
+    stored[rows, Ac.indices] = True
+    _, keep = _dense_sparsify_reference(Ac, inM, gamma)
+    N = np.zeros_like(stored)
+    N[rows, Ac.indices] = keep
+    # classical strength on negative couplings (an independent dense form)
+    off = stored & ~np.eye(n, dtype=bool)
+    neg = np.where(off, -D, -np.inf)
+    m = neg.max(axis=1)
+    S = off & (m[:, None] > 0) & (-D >= theta * m[:, None])
+    H = np.where(N, D, 0.0)
+    for i in range(n):
+        for j in range(n):
+            if not stored[i, j] or N[i, j]:
+                continue
+            a = D[i, j]
+            W = [k for k in range(n) if S[j, k] and N[i, k]]
+            den = sum(abs(D[j, k]) for k in W)
+            if not den > 0:
+                H[i, i] += a
+                continue
+            for k in W:
+                t = abs(D[j, k]) / den * a
+                U = np.zeros((n, n))
+                U[i, k] += t
+                U[k, i] += t
+                U[k, k] -= t
+                H += U
+    return H, N[rows, Ac.indices]
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.1, 0.5, 1.0])
+def test_full_lumping_against_dense(gamma):
+    h = _level_pair(gen.poisson3d_7pt(8))
+    for l in range(1, h.num_levels):
+        Ac = h.matrix(l, "A").to_scipy()
+        H, keep = oracle.sparsify_full(Ac, h.inM(l), gamma, 0.25)
+        Href, keep_ref = _dense_full_lumping(Ac, h.inM(l), gamma, 0.25)
+        np.testing.assert_array_equal(keep, keep_ref.astype(np.uint8))
+        scale = np.abs(Href).max()
+        np.testing.assert_allclose(H.todense(), Href, rtol=0, atol=1e-13 * scale)
+        if gamma == 0.0:
+            np.testing.assert_array_equal(H.todense(), Ac.toarray())
+
+
+@pytest.mark.parametrize("gamma", [0.1, 1.0])
+def test_full_lumping_symmetry_rowsums_and_pattern(gamma):
+    """Each update is symmetric with zero row sums: Ahat stays symmetric with
+    the row sums of A_c; it keeps exactly N (no guard); off-diagonal values
+    change where diagonal lumping would leave them."""
+    h = _level_pair(gen.poisson3d_7pt(10), max_levels=5)
+    changed_offdiag = False
+    for l in range(1, h.num_levels):
+        Ac = h.matrix(l, "A").to_scipy()
+        Hf, kf = oracle.sparsify_full(Ac, h.inM(l), gamma, 0.25)
+        Hd, kd = oracle.sparsify_diag(Ac, h.inM(l), gamma)
+        np.testing.assert_array_equal(kf, kd)
+        F, Ad = Hf.todense(), Ac.toarray()
+        scale = np.abs(Ad).max()
+        np.testing.assert_allclose(F, F.T, rtol=0, atol=1e-14 * scale)
+        np.testing.assert_allclose(F.sum(axis=1), Ad.sum(axis=1), rtol=0, atol=1e-13 * scale)
+        G = Hd.todense()
+        offd = ~np.eye(F.shape[0], dtype=bool)
+        changed_offdiag |= bool(np.any(np.abs(F - G)[offd] > 1e-12 * scale))
+    assert changed_offdiag
+
+
+def test_full_lumping_hierarchy_and_reintroduction():
+    """Through the hierarchy (Sparse and Hybrid): reintroduction down to gamma
+    = 0 restores the Galerkin operators exactly."""
+    A = gen.poisson3d_7pt(10)
+    for method in (0, 1):
+        h = oracle.Hierarchy(A, max_size=20)
+        L = h.num_levels
+        h.sparsify([0.0] + [1.0] * (L - 1), method=method, lump=1)
+        for l in range(1, L):
+            Ac = h.matrix(l, "A").to_scipy()
+            if method == 0:
+                Hf, _ = oracle.sparsify_full(Ac, h.inM(l), 1.0, 0.25)
+                np.testing.assert_array_equal(h.matrix(l, "Ahat").val, Hf.val)
+        for _ in range(10 * L):
+            cnt, _ = h.reintroduce(s=1)
+            if cnt == 0:
+                break
+        for l in range(L):
+            np.testing.assert_array_equal(h.matrix(l, "Ahat").val, h.matrix(l, "A").val)
+
+
+# ---------------------------------------------------------------------------
+# LU with partial pivoting (coarsest-level fallback) and GMRES
+# ---------------------------------------------------------------------------
+def test_lu_matches_library():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((9, 9))
+    LU, piv = oracle.lu(A)
+    lu_ref, piv_ref = sla.lu_factor(A)
+    np.testing.assert_array_equal(piv, piv_ref)
+    np.testing.assert_allclose(LU, lu_ref, rtol=1e-12, atol=1e-13)
+    b = rng.standard_normal(9)
+    np.testing.assert_allclose(oracle.lu_solve(LU, piv, b), sla.solve(A, b), rtol=1e-11)
+
+
+def test_indefinite_coarsest_uses_lu():
+    """A one-level hierarchy of a symmetric indefinite matrix: Cholesky fails,
+    the pivoted LU solves it exactly."""
+    rng = np.random.default_rng(6)
+    Q, _ = np.linalg.qr(rng.standard_normal((8, 8)))
+    A = Q @ np.diag([3.0, 2.0, 1.5, 1.0, -0.5, 2.5, -1.0, 4.0]) @ Q.T
+    A = 0.5 * (A + A.T)
+    h = oracle.Hierarchy(csr_from_dense(A), max_size=100)
+    assert h.num_levels == 1
+    b = rng.standard_normal(8)
+    np.testing.assert_allclose(h.vcycle(b), sla.solve(A, b), rtol=1e-11, atol=1e-12)
+
+
+def _krylov_minimiser(Aop, r0, k):
+    """argmin over u in K_k(Aop, r0) of ||r0 - Aop u|| (orthonormal basis by QR)."""
+    K = np.empty((r0.size, k))
+    v = r0.copy()
+    for c in range(k):
+        K[:, c] = v
+        v = Aop @ v
+    Q, _ = np.linalg.qr(K)
+    y, *_ = np.linalg.lstsq(Aop @ Q, r0, rcond=None)
+    return Q @ y
+
+
+def _nonsym(n, seed):
+    rng = np.random.default_rng(seed)
+    return np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_gmres_iterate_is_krylov_minimiser(k):
+    A = _nonsym(12, 1)
+    b = np.random.default_rng(2).standard_normal(12)
+    x, info = oracle.gmres_plain(csr_from_dense(A), b, tol=0.0, max_it=k, restart=30)
+    assert info.iterations == k
+    np.testing.assert_allclose(x, _krylov_minimiser(A, b, k), rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_restart_is_two_minimisations():
+    A = _nonsym(12, 3)
+    b = np.random.default_rng(4).standard_normal(12)
+    x, _ = oracle.gmres_plain(csr_from_dense(A), b, tol=0.0, max_it=5, restart=3)
+    x3 = _krylov_minimiser(A, b, 3)
+    x5 = x3 + _krylov_minimiser(A, b - A @ x3, 2)
+    np.testing.assert_allclose(x, x5, rtol=1e-10, atol=1e-12)
+
+
+def test_gmres_exact_within_n_steps():
+    A = _nonsym(10, 7)
+    b = np.random.default_rng(8).standard_normal(10)
+    x, info = oracle.gmres_plain(csr_from_dense(A), b, tol=1e-12, max_it=50, restart=10)
+    assert info.status == 0 and info.iterations <= 10
+    np.testing.assert_allclose(x, sla.solve(A, b), rtol=1e-10)
+
+
+def test_gmres_preconditioned_minimiser():
+    """Right preconditioning: x_k = M u_k, u_k minimising ||b - A M u|| over
+    K_k(A M, b), with M the (linear) V-cycle assembled column by column."""
+    A = gen.poisson2d_5pt(9)
+    h = oracle.Hierarchy(A, max_size=20)
+    assert h.num_levels >= 2
+    h.sparsify([0.0, 0.5])
+    n = A.n
+    Ad = A.to_scipy().toarray()
+    M = np.column_stack([h.vcycle(e) for e in np.eye(n)])
+    b = gen.rhs_uniform(n, 9)
+    for k in (1, 2, 4):
+        x, _ = h.gmres(b, tol=0.0, max_it=k, restart=30)
+        u = _krylov_minimiser(Ad @ M, b, k)
+        np.testing.assert_allclose(x, M @ u, rtol=1e-9, atol=1e-11)
+
+
+def test_gmres_single_level_converges_in_one_step():
+    A = gen.poisson2d_5pt(8)
+    h = oracle.Hierarchy(A, max_size=1000)
+    b = gen.rhs_uniform(A.n, 0)
+    x, info = h.gmres(b)
+    assert info.iterations == 1 and info.status == 0
+    np.testing.assert_allclose(x, sla.solve(A.to_scipy().toarray(), b), rtol=1e-11)
+
+
+def test_gmres_solves_full_lumping_hierarchy():
+    A = gen.poisson3d_7pt(16)
+    b = gen.rhs_uniform(A.n, 1)
+    h = oracle.Hierarchy(A)
+    xg, ig = h.gmres(b, tol=1e-8)
+    assert ig.status == 0 and ig.final_relres <= 1e-8
+    xp, ip = h.pcg(b, tol=1e-8)
+    S = A.to_scipy().tocsc()
+    xs = spla.spsolve(S, b)
+    assert np.linalg.norm(xg - xs) <= 1e-5 * np.linalg.norm(xs)
+    h.sparsify([0.0, 0.1, 1.0], lump=1)
+    x, info = h.gmres(b, tol=1e-8)
+    assert info.status == 0 and info.final_relres <= 1e-8
+    h2 = oracle.Hierarchy(A)
+    h2.sparsify([0.0, 1.0], lump=1)
+    x2, i2 = h2.adaptive_gmres(b, tol=1e-8, rho_max=0.2)
+    assert i2.status == 0 and i2.final_relres <= 1e-8
+
+
+def test_gmres_zero_rhs():
+    A = gen.poisson2d_5pt(8)
+    h = oracle.Hierarchy(A)
+    x, info = h.gmres(np.zeros(A.n))
+    assert info.iterations == 0 and not x.any()
