@@ -65,6 +65,16 @@ typedef struct {
 } amg_csr;
 
 enum { AMG_METHOD_SPARSE = 0, AMG_METHOD_HYBRID = 1 };
+/* How sparsify treats a dropped entry: AMG_LUMP_DIAG adds it to the diagonal
+ * of its row (Algorithm 3b; keeps an SPD diagonally dominant operator SPD,
+ * Theorem 1); AMG_LUMP_STRONG spreads it symmetrically over the strong
+ * neighbours that the row keeps (Algorithm 3's own loop: symmetry and row
+ * sums are kept, definiteness is not -- solve with GMRES). */
+enum { AMG_LUMP_DIAG = 0, AMG_LUMP_STRONG = 1 };
+/* Outer Krylov method of amg_solve: preconditioned CG, or restarted GMRES
+ * right-preconditioned by the V-cycle (the paper's solver where full lumping
+ * can cost positive definiteness, Section 5). */
+enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
 enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_FP32_BF16 = 2 };
 /* SpMV kernel variants: CSR with T threads per row, or SELL-32 slices. */
 enum {
@@ -90,6 +100,9 @@ typedef struct {
     int check_every;     /* PCG iterations between host stop tests, default 1 */
     int setup_timing;    /* 1: time the setup phases with events (amg_timing_get
                             kinds 8..15), default 0 */
+    int lump;            /* AMG_LUMP_DIAG (default) or AMG_LUMP_STRONG */
+    int krylov;          /* AMG_KRYLOV_CG (default) or AMG_KRYLOV_GMRES */
+    int restart;         /* GMRES restart length m (Krylov vectors kept), default 30 */
 } amg_options;
 
 typedef struct {

@@ -5,7 +5,8 @@ include/amg.h; this package is its ctypes binding and build script.
 """
 from .amg import (  # noqa: F401
     AmgError, Hierarchy, Matrix, Server, SolveInfo, default_options, device_bytes, kernel_launches, lib,
-    METHOD_SPARSE, METHOD_HYBRID, PREC_FP64, PREC_FP32, PREC_FP32_BF16,
+    METHOD_SPARSE, METHOD_HYBRID, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,
+    PREC_FP64, PREC_FP32, PREC_FP32_BF16,
     SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_NAMES,
     K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC,
 )

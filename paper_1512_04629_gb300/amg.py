@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libamg.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, BREAKDOWN, TIMEOUT, REJECTED = range(9)
 METHOD_SPARSE, METHOD_HYBRID = 0, 1
+LUMP_DIAG, LUMP_STRONG = 0, 1
+KRYLOV_CG, KRYLOV_GMRES = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_CSR1 = -1, 1, 2, 3, 4, 5, 6, 7
 SPMV_NAMES = {1: "csr2", 2: "csr4", 3: "csr8", 4: "csr16", 5: "csr32", 6: "sell32", 7: "csr1"}
@@ -48,7 +50,8 @@ class Options(C.Structure):
                 ("k_check", C.c_int), ("s_levels", C.c_int), ("gamma_min", C.c_double),
                 ("rho_max", C.c_double), ("level_offset", C.c_int), ("spmv_variant", C.c_int),
                 ("use_graph", C.c_int), ("check_every", C.c_int),
-                ("setup_timing", C.c_int)]
+                ("setup_timing", C.c_int), ("lump", C.c_int), ("krylov", C.c_int),
+                ("restart", C.c_int)]
 
 
 class SolveInfo(C.Structure):

@@ -100,6 +100,9 @@ void check_options(const amg_options &o) {
     require(o.spmv_variant == AMG_SPMV_AUTO || (o.spmv_variant >= AMG_SPMV_CSR2 && o.spmv_variant <= AMG_SPMV_CSR1),
             "unknown spmv_variant");
     require(o.check_every >= 1, "check_every must be >= 1");
+    require(o.lump == AMG_LUMP_DIAG || o.lump == AMG_LUMP_STRONG, "unknown lump");
+    require(o.krylov == AMG_KRYLOV_CG || o.krylov == AMG_KRYLOV_GMRES, "unknown krylov");
+    require(o.restart >= 1 && o.restart <= 512, "restart must be in [1, 512]");
 }
 
 void check_gammas(const double *g, int n) {
@@ -145,6 +148,9 @@ void amg_options_default(amg_options *o) {
     o->spmv_variant = AMG_SPMV_AUTO;
     o->use_graph = 1;
     o->check_every = 1;
+    o->lump = AMG_LUMP_DIAG;
+    o->krylov = AMG_KRYLOV_CG;
+    o->restart = 30;
 }
 
 amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_gamma, const amg_options *opt,

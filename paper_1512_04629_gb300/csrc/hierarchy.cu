@@ -29,6 +29,8 @@ Hierarchy::~Hierarchy() {
     for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : event_pool) cudaEventDestroy(e);
     if (h_scal) cudaFreeHost(h_scal);
+    if (g_gmres) cudaGraphExecDestroy(g_gmres);
+    if (h_gsc) cudaFreeHost(h_gsc);
 }
 
 // ---------------------------------------------------------------------------
@@ -194,7 +196,13 @@ void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
     const uint8_t *inM = V.inM.as<uint8_t>();
     if (h.opt.method == AMG_METHOD_HYBRID && l >= 2) inM = hybrid_pattern(h, l, s);
     DevCSR H;
-    setup::sparsify(V.A, inM, V.tpos.as<int32_t>(), V.diagpos.as<int32_t>(), V.gamma, V.keep.as<uint8_t>(), H, s);
+    TmpBuf S;
+    if (h.opt.lump == AMG_LUMP_STRONG) {  // Algorithm 3's S: strength of A_l itself
+        S.alloc(V.A.nnz + kPad, s);
+        setup::strength(V.A, h.opt.theta, S.as<uint8_t>(), s);
+    }
+    setup::sparsify(V.A, inM, V.tpos.as<int32_t>(), V.diagpos.as<int32_t>(), V.gamma, V.keep.as<uint8_t>(), H, s,
+                    S.as<uint8_t>());
     V.H = std::move(H);
     V.h_alias = false;
 }
@@ -924,6 +932,240 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
         run.replacements++;
     }
 }
+// ---------------------------------------------------------------------------
+// Restarted flexible GMRES (FGMRES(m)) with the V-cycle as right
+// preconditioner, FP64 recurrences.  Each Arnoldi step is the fixed sequence
+// [z = M v_j, store z_j, w = A_0 z, two classical Gram-Schmidt passes,
+// Givens rotation, v_{j+1} = w / h_{j+1,j}]; with graphs on, a cycle runs as
+// one WHILE-node graph launch whose condition the rotation kernel sets.  The
+// host forms x = x0 + Z y at the end of a cycle (or of an Algorithm 5
+// window), confirms convergence with the true residual and restarts.
+// ---------------------------------------------------------------------------
+struct GmRun {
+    int steps = 0, replacements = 0;
+    bool converged = false, breakdown = false;
+    double rnorm = 0.0;
+};
+
+GmresArrays gm_arrays(Hierarchy &h) { return gmres_arrays(h.garr.as<double>(), h.gm_m); }
+GmresScalars *gm_dsc(Hierarchy &h) { return h.gsc.as<GmresScalars>(); }
+
+void gm_read(Hierarchy &h, cudaStream_t s) {
+    AMG_CUDA(cudaMemcpyAsync(h.h_gsc, gm_dsc(h), sizeof(GmresScalars), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+void gm_write(Hierarchy &h, cudaStream_t s) {
+    AMG_CUDA(cudaMemcpyAsync(gm_dsc(h), h.h_gsc, sizeof(GmresScalars), cudaMemcpyHostToDevice, s));
+}
+
+void gm_workspace(Hierarchy &h, cudaStream_t s) {
+    const int m = h.opt.restart;
+    const int64_t n = h.lev[0]->n();
+    if (h.gm_m == m && h.gm_n == n) return;
+    h.gV.alloc(sizeof(double) * ((size_t)(m + 1) * n + kPad));
+    h.gZ.alloc(sizeof(double) * ((size_t)m * n + kPad));
+    h.gx0.alloc(sizeof(double) * (n + kPad));
+    h.garr.alloc(sizeof(double) * gmres_array_doubles(m));
+    h.gsc.alloc(sizeof(GmresScalars));
+    AMG_CUDA(cudaMemsetAsync(h.garr.ptr, 0, h.garr.bytes, s));
+    AMG_CUDA(cudaMemsetAsync(h.gsc.ptr, 0, sizeof(GmresScalars), s));
+    if (!h.h_gsc) AMG_CUDA(cudaMallocHost(&h.h_gsc, sizeof(GmresScalars)));
+    std::memset(h.h_gsc, 0, sizeof(GmresScalars));
+    h.gm_m = m;
+    h.gm_n = n;
+    h.g_gmres_version = -1;
+}
+
+void gm_step(Hierarchy &h, cudaStream_t s, cudaGraphConditionalHandle handle, bool use_handle) {
+    const int64_t n = h.lev[0]->n();
+    const int m = h.gm_m;
+    GmresArrays ar = gm_arrays(h);
+    GmresScalars *sc = gm_dsc(h);
+    double *V = h.gV.as<double>(), *Z = h.gZ.as<double>(), *w = h.pq.as<double>();
+    vcycle_f64(h, h.pr.as<double>(), h.pz.as<double>(), s);
+    timed(h, 6, 0, 16.0 * n, s, [&] { gm::store_z(n, h.pz.as<double>(), Z, sc, s); });
+    CycMat<double> A0 = a0_mat(h);
+    const double ap_bytes = (double)A0.nnz * 12 + 4.0 * (n + 1) + 16.0 * n;
+    timed(h, 5, 0, ap_bytes, s, [&] { cyc::spmv<double, double>(A0, h.pz.as<double>(), w, false, s); });
+    timed(h, 6, 0, 0.0, s, [&] {
+        gm::mdot(n, m, V, w, sc, ar, false, s);
+        gm::mupdate(n, m, V, w, sc, ar, false, handle, false, s);
+        gm::mdot(n, m, V, w, sc, ar, true, s);
+        gm::mupdate(n, m, V, w, sc, ar, true, handle, use_handle, s);
+        gm::normalize(n, w, V, h.pr.as<double>(), sc, s);
+    });
+}
+
+void gm_ensure_graph(Hierarchy &h) {
+    if (h.g_gmres && h.g_gmres_version == h.version) return;
+    if (h.g_gmres) cudaGraphExecDestroy(h.g_gmres);
+    h.g_gmres = nullptr;
+    if (!h.graph_stream) AMG_CUDA(cudaStreamCreateWithFlags(&h.graph_stream, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    AMG_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle handle;
+    AMG_CUDA(cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        AMG_CUDA(e);
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    AMG_CUDA(cudaStreamBeginCaptureToGraph(h.graph_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    bool was = h.timing;
+    h.timing = false;
+    try {
+        gm_step(h, h.graph_stream, handle, true);
+    } catch (...) {
+        cudaGraph_t junk;
+        cudaStreamEndCapture(h.graph_stream, &junk);
+        h.timing = was;
+        cudaGraphDestroy(g);
+        throw;
+    }
+    h.timing = was;
+    cudaGraph_t captured;
+    AMG_CUDA(cudaStreamEndCapture(h.graph_stream, &captured));
+    e = cudaGraphInstantiate(&h.g_gmres, g, 0);
+    cudaGraphDestroy(g);
+    AMG_CUDA(e);
+    h.g_gmres_version = h.version;
+}
+
+// new cycle from the internal x (h.px): r = b - A x, v_0 = r / ||r||,
+// g = ||r|| e_1, x0 = x; returns ||r||
+double gm_start(Hierarchy &h, const double *b, double thresh, cudaStream_t s) {
+    const int64_t n = h.lev[0]->n();
+    double rn = true_resnorm(h, b, h.px.as<double>(), s);
+    AMG_CUDA(cudaMemcpyAsync(h.gx0.ptr, h.px.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GmresScalars &c = *h.h_gsc;
+    c.m = h.gm_m;
+    c.thresh = thresh;
+    c.tt = rn * rn;
+    gm_write(h, s);
+    gm::start(n, h.pt.as<double>(), h.gV.as<double>(), h.pr.as<double>(), gm_dsc(h), gm_arrays(h), s);
+    gm_read(h, s);
+    return rn;
+}
+
+void gm_form_x(Hierarchy &h, cudaStream_t s) {
+    const int64_t n = h.lev[0]->n();
+    timed(h, 6, 0, 0.0, s, [&] {
+        gm::form_x(n, h.gm_m, h.gZ.as<double>(), h.gx0.as<double>(), h.px.as<double>(), gm_dsc(h), gm_arrays(h), s);
+    });
+}
+
+// Up to max_steps Arnoldi steps from the current cycle; x (h.px) holds the
+// iterate on return, the cycle itself goes on unless it converged, broke
+// down or was restarted.
+void gm_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int max_steps, cudaStream_t s,
+                GmRun &run) {
+    run = GmRun();
+    const double thresh = tol * bnorm;
+    GmresScalars &c = *h.h_gsc;
+    run.rnorm = c.est;
+    if (c.est <= thresh) { run.converged = true; return; }
+    const bool graph = h.opt.use_graph && !h.timing;
+    if (graph) gm_ensure_graph(h);
+    while (run.steps < max_steps) {
+        if (c.j == h.gm_m) {  // restart
+            gm_form_x(h, s);
+            gm_start(h, b, thresh, s);
+        }
+        const int before = c.its;
+        c.max_its = c.its + (max_steps - run.steps);
+        gm_write(h, s);
+        if (graph) {
+            AMG_CUDA(cudaGraphLaunch(h.g_gmres, s));
+            gm_read(h, s);
+        } else {
+            while (true) {
+                gm_step(h, s, cudaGraphConditionalHandle{}, false);
+                gm_read(h, s);
+                if (!(c.est > c.thresh && c.hn > 0.0 && c.j < c.m && c.its < c.max_its && !c.breakdown)) break;
+            }
+        }
+        run.steps += c.its - before;
+        if (c.breakdown) {
+            gm_form_x(h, s);
+            run.breakdown = true;
+            return;
+        }
+        run.rnorm = c.est;
+        if (c.est <= thresh || c.happy) {
+            gm_form_x(h, s);
+            const double tn = gm_start(h, b, thresh, s);
+            run.rnorm = tn;
+            if (tn <= thresh) { run.converged = true; return; }
+            run.replacements++;
+        }
+    }
+    gm_form_x(h, s);
+}
+
+amg_status solve_gmres(Hierarchy &h, const double *b, double bnorm, double tol, int max_it, bool adaptive,
+                       cudaStream_t s, amg_solve_info *info) {
+    gm_workspace(h, s);
+    const int64_t n = h.lev[0]->n();
+    double *x = h.px.as<double>();
+    const double thresh = tol * bnorm;
+    h.h_gsc->its = 0;
+    if (!adaptive) {
+        const double r0 = gm_start(h, b, thresh, s);
+        GmRun run;
+        gm_iterate(h, b, bnorm, tol, max_it, s, run);
+        info->iterations = run.steps;
+        info->replacements = run.replacements;
+        info->conv_factor = run.steps > 0 ? std::pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
+        return run.converged ? AMG_OK : (run.breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+    }
+    // Algorithm 5 around GMRES: every k steps the iterate is formed (the
+    // cycle goes on) and checked; a reintroduction restarts GMRES with the
+    // new preconditioner
+    const int k = std::max(1, h.opt.k_check), sl = std::max(1, h.opt.s_levels);
+    TmpBuf xs(sizeof(double) * (n + kPad), s);
+    double rstart = bnorm;
+    gm_start(h, b, thresh, s);
+    int total = 0;
+    bool converged = false, breakdown = false;
+    while (total < max_it) {
+        AMG_CUDA(cudaMemcpyAsync(xs.ptr, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        GmRun run;
+        gm_iterate(h, b, bnorm, tol, std::min(k, max_it - total), s, run);
+        total += run.steps;
+        info->replacements += run.replacements;
+        double rend = true_resnorm(h, b, x, s);
+        if (run.converged || rend <= thresh) { converged = true; break; }
+        breakdown = run.breakdown;
+        const double factor = run.steps > 0 ? std::pow(rend / rstart, 1.0 / run.steps) : 1.0;
+        if (factor > h.opt.rho_max || breakdown) {
+            const int cnt = reintroduce(h, sl, s);
+            const bool back = !(rend <= rstart);
+            if (cnt == 0 && breakdown) {
+                if (back) AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                break;
+            }
+            if (cnt > 0) {
+                info->resets++;
+                breakdown = false;
+                if (back) {
+                    AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    rend = rstart;
+                }
+                gm_start(h, b, thresh, s);
+            }
+        }
+        rstart = rend;
+    }
+    info->iterations = total;
+    return converged ? AMG_OK : (breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+}
 }  // namespace
 
 amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int max_it, bool adaptive,
@@ -941,6 +1183,8 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
     amg_status st = AMG_OK;
     if (bnorm == 0.0) {
         info->status = AMG_OK;
+    } else if (h.opt.krylov == AMG_KRYLOV_GMRES) {
+        st = solve_gmres(h, b, bnorm, tol, max_it, adaptive, s, info);
     } else if (!adaptive) {
         double r0 = pcg_start(h, b, x, s);
         Run run;

@@ -9,6 +9,7 @@
 #include "batch_ops.cuh"
 #include "common.cuh"
 #include "cycle_ops.cuh"
+#include "gmres_ops.cuh"
 
 namespace amg {
 
@@ -128,6 +129,16 @@ struct Hierarchy {
     int version = 0;  // bumped whenever the cycle's buffers or operators change
 
     std::map<int, std::unique_ptr<BatchWS>> batch;
+
+    // GMRES workspace (the first GMRES solve allocates it): basis V
+    // ((m + 1) x n), preconditioned vectors Z (m x n), the cycle's starting
+    // x, the Hessenberg arrays and the device scalars
+    DevBuf gV, gZ, gx0, garr, gsc;
+    int gm_m = 0;
+    int64_t gm_n = -1;
+    GmresScalars *h_gsc = nullptr;  // pinned
+    cudaGraphExec_t g_gmres = nullptr;  // one captured Arnoldi step in a WHILE loop
+    int g_gmres_version = -1;
 
     ~Hierarchy();
     int nlev() const { return (int)lev.size(); }

@@ -1126,6 +1126,157 @@ __global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int3
     }
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 3's own loop: full lumping to strong neighbours.  Every dropped
+// entry (i,j) becomes a list of "lump edges" (k, t): for each k in
+// W = {k : S_jk != 0, (i,k) kept}, t = (|a_jk| / sum_W |a_jm|) a_ij, or one
+// fallback edge (~i, a_ij) when W is empty (the value goes to a_ii).  The
+// edges of row i are stored in entry order, each entry's in increasing k --
+// the order in which the sequential loop applies the updates.  A kept entry
+// then gathers the updates that reach it in that same order, so the result
+// does not depend on thread scheduling (no atomics):
+//   (r,c), r != c: t of row r's edges with k = c (update (i,k)) and of row
+//     c's edges with k = r (update (k,i)), the lower row's first;
+//   (r,r): over the kept columns i of row r in increasing order -- row r's
+//     own edges with k = r add t, add t, subtract t (updates (i,k), (k,i),
+//     (k,k) with k = i) and its fallback edges add the value; another row
+//     i's edges with k = r subtract t (update (k,k)).
+// The kept pattern is symmetric (N is), which is what lets row r find every
+// row i that can reach it among its own kept columns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t find_col(const int32_t *ci, int32_t lo, int32_t hi, int32_t c) {
+    const int32_t p = lower_bound_i32(ci, lo, hi, c);
+    return (p < hi && ci[p] == c) ? p : -1;
+}
+
+// per dropped entry: |W| (edges; 1 for the fallback) and sum_W |a_jm| in
+// increasing m
+template <int T>
+__global__ void lump_count_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                                  const uint8_t *keep, const uint8_t *S, double *den, int32_t *ecnt) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    if (i >= n) return;
+    const int32_t p0 = rp[i], p1 = rp[i + 1];
+    for (int32_t p = p0 + t; p < p1; p += T) {
+        if (keep[p]) {
+            ecnt[p] = 0;
+            continue;
+        }
+        const int32_t j = ci[p];
+        double d = 0.0;
+        int32_t w = 0;
+        for (int32_t q = rp[j]; q < rp[j + 1]; ++q) {
+            if (!S[q]) continue;
+            const int32_t pk = find_col(ci, p0, p1, ci[q]);
+            if (pk >= 0 && keep[pk]) {
+                d += fabs(v[q]);
+                ++w;
+            }
+        }
+        den[p] = d;
+        ecnt[p] = (d > 0.0) ? w : 1;
+    }
+}
+
+template <int T>
+__global__ void lump_emit_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                                 const uint8_t *keep, const uint8_t *S, const double *den, const int64_t *eoff,
+                                 int32_t *ek, double *et) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    if (i >= n) return;
+    const int32_t p0 = rp[i], p1 = rp[i + 1];
+    for (int32_t p = p0 + t; p < p1; p += T) {
+        if (keep[p]) continue;
+        int64_t e = eoff[p];
+        const double a = v[p], d = den[p];
+        if (!(d > 0.0)) {
+            ek[e] = ~i;
+            et[e] = a;
+            continue;
+        }
+        const int32_t j = ci[p];
+        for (int32_t q = rp[j]; q < rp[j + 1]; ++q) {
+            if (!S[q]) continue;
+            const int32_t k = ci[q];
+            const int32_t pk = find_col(ci, p0, p1, k);
+            if (pk >= 0 && keep[pk]) {
+                ek[e] = k;
+                et[e] = (fabs(v[q]) / d) * a;
+                ++e;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double lump_add_row(double x, int64_t e0, int64_t e1, const int32_t *ek,
+                                               const double *et, int32_t k) {
+    for (int64_t e = e0; e < e1; ++e)
+        if (ek[e] == k) x += et[e];
+    return x;
+}
+
+template <int T>
+__global__ void lump_gather_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                                   const uint8_t *keep, const int64_t *eoff, const int32_t *ek,
+                                   const double *et, double *hval) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t r = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    if (r >= n) return;
+    const int32_t p0 = rp[r], p1 = rp[r + 1];
+    for (int32_t p = p0 + t; p < p1; p += T) {
+        if (!keep[p]) continue;
+        const int32_t c = ci[p];
+        double x = v[p];
+        if (c != r) {
+            const int32_t lo = min(r, c), hi = max(r, c);
+            x = lump_add_row(x, eoff[rp[lo]], eoff[rp[lo + 1]], ek, et, lo == r ? c : r);
+            x = lump_add_row(x, eoff[rp[hi]], eoff[rp[hi + 1]], ek, et, hi == r ? c : r);
+        } else {
+            for (int32_t q = p0; q < p1; ++q) {
+                if (!keep[q]) continue;
+                const int32_t i = ci[q];
+                const int64_t e1 = eoff[rp[i + 1]];
+                if (i == r) {
+                    for (int64_t e = eoff[rp[i]]; e < e1; ++e) {
+                        const int32_t k = ek[e];
+                        if (k == r) {
+                            const double tt = et[e];
+                            x += tt;
+                            x += tt;
+                            x -= tt;
+                        } else if (k == ~r) {
+                            x += et[e];
+                        }
+                    }
+                } else {
+                    for (int64_t e = eoff[rp[i]]; e < e1; ++e)
+                        if (ek[e] == r) x -= et[e];
+                }
+            }
+        }
+        hval[p] = x;
+    }
+}
+
+// compaction of the kept entries with their gathered values
+__global__ void compact_values_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const uint8_t *keep,
+                                      const double *hval, const int32_t *hrp, int32_t *hci, double *hv) {
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t pos = hrp[i];
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
+        if (!keep[p]) continue;
+        hci[pos] = ci[p];
+        hv[pos] = hval[p];
+        ++pos;
+    }
+}
+
 __global__ void fill_u8_kernel(int64_t n, uint8_t *a, uint8_t val) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < n) a[p] = val;
@@ -1247,6 +1398,67 @@ __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
     double s = 0.0;
     for (int32_t k = max(i, j); k < n; ++k) s += Linv[(size_t)k * n + i] * Linv[(size_t)k * n + j];
     inv[t] = s;
+}
+
+// Gauss-Jordan inverse with partial pivoting (one block): the coarsest-level
+// direct solve when the relaxed operator is not positive definite (full
+// lumping can make it indefinite).  Pivot: the first row of largest |a_ik|,
+// i >= k.  err = 1 if a pivot is 0 (singular operator).
+__global__ void __launch_bounds__(1024)
+gauss_jordan_kernel(int32_t n, double *a, double *inv, double *fac, int *err) {
+    __shared__ double wv[32];
+    __shared__ int wi[32];
+    __shared__ int piv;
+    __shared__ double pv;
+    for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) inv[t] = (t / n == t % n) ? 1.0 : 0.0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int32_t k = 0; k < n; ++k) {
+        __syncthreads();
+        double bv = -1.0;
+        int bi = n;
+        for (int32_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+            const double x = fabs(a[(size_t)i * n + k]);
+            if (x > bv) { bv = x; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0) { wv[w] = bv; wi[w] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = -1.0;
+            int bix = n;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q)
+                if (wv[q] > b || (wv[q] == b && wi[q] < bix)) { b = wv[q]; bix = wi[q]; }
+            piv = bix < n ? bix : k;
+            pv = a[(size_t)piv * n + k];
+            if (!(fabs(pv) > 0.0)) *err = 1;
+        }
+        __syncthreads();
+        if (!(fabs(pv) > 0.0)) return;  // uniform: every thread reads the same pivot
+        const int32_t r = piv;
+        if (r != k)
+            for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+                double t = a[(size_t)k * n + c]; a[(size_t)k * n + c] = a[(size_t)r * n + c]; a[(size_t)r * n + c] = t;
+                t = inv[(size_t)k * n + c]; inv[(size_t)k * n + c] = inv[(size_t)r * n + c]; inv[(size_t)r * n + c] = t;
+            }
+        __syncthreads();
+        for (int32_t c = threadIdx.x; c < n; c += blockDim.x) {
+            a[(size_t)k * n + c] /= pv;
+            inv[(size_t)k * n + c] /= pv;
+        }
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) fac[i] = (i == k) ? 0.0 : a[(size_t)i * n + k];
+        __syncthreads();
+        for (int64_t t = threadIdx.x; t < (int64_t)n * n; t += blockDim.x) {
+            const int32_t i = (int32_t)(t / n), c = (int32_t)(t % n);
+            const double f = fac[i];
+            if (f == 0.0) continue;
+            if (c >= k) a[t] -= f * a[(size_t)k * n + c];
+            inv[t] -= f * inv[(size_t)k * n + c];
+        }
+    }
 }
 
 // copy each row's entries from its product-bound slot to the final CSR
@@ -1694,10 +1906,12 @@ void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, ui
 }
 
 int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const int32_t *diagpos,
-                 double gamma, uint8_t *keep, DevCSR &H, cudaStream_t s) {
+                 double gamma, uint8_t *keep, DevCSR &H, cudaStream_t s, const uint8_t *S) {
     int32_t n = A.nrows;
+    const bool full = S != nullptr;
     TmpBuf rowmax(sizeof(double) * (n + 1), s), flag(A.nnz + 1, s), guard(n + 1, s), cnt(sizeof(int32_t) * (n + 1), s);
     int g = div_up(n, kThreads);
+    TmpBuf hval;
     if (n > 0) {
         with_row_lanes(row_lanes(A), [&](auto tc) {
             constexpr int L = decltype(tc)::value;
@@ -1711,11 +1925,40 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
             sparsify_sym_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, flag.as<uint8_t>(),
                                                            rowmax.as<double>(), keep, guard.as<uint8_t>());
             ::amg::count_launch();
+            // Algorithm 3 has no ismax guard: with every guard clear the
+            // guard kernel only counts the kept entries of each row
+            if (full) AMG_CUDA(cudaMemsetAsync(guard.ptr, 0, n, s));
             sparsify_guard_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), tpos, guard.as<uint8_t>(),
                                                              rowmax.as<double>(), keep, cnt.as<int32_t>());
             ::amg::count_launch();
         });
         AMG_CHECK_LAUNCH();
+        if (full) {
+            TmpBuf den(sizeof(double) * (A.nnz + 1), s), ecnt(sizeof(int32_t) * (A.nnz + 1), s),
+                eoff(sizeof(int64_t) * (A.nnz + 1), s);
+            const int lanes = row_lanes(A);
+            with_row_lanes(lanes, [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                lump_count_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+                    n, A.rp(), A.ci(), A.v(), keep, S, den.as<double>(), ecnt.as<int32_t>());
+                ::amg::count_launch();
+            });
+            AMG_CHECK_LAUNCH();
+            const int64_t E = exclusive_scan_i64_from_i32(ecnt.as<int32_t>(), eoff.as<int64_t>(), A.nnz, s);
+            TmpBuf ek(sizeof(int32_t) * (E + 1), s), et(sizeof(double) * (E + 1), s);
+            hval.alloc(sizeof(double) * (A.nnz + 1), s);
+            with_row_lanes(lanes, [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                const int gl = div_up((int64_t)n * L, kThreads);
+                lump_emit_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), keep, S, den.as<double>(),
+                                                            eoff.as<int64_t>(), ek.as<int32_t>(), et.as<double>());
+                ::amg::count_launch();
+                lump_gather_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), keep, eoff.as<int64_t>(),
+                                                              ek.as<int32_t>(), et.as<double>(), hval.as<double>());
+                ::amg::count_launch();
+            });
+            AMG_CHECK_LAUNCH();
+        }
     }
     H.rowptr.alloc(sizeof(int32_t) * (n + 1));
     int64_t nnz = exclusive_scan_i32(cnt.as<int32_t>(), H.rp(), n, s);
@@ -1727,8 +1970,14 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
     AMG_CUDA(cudaMemsetAsync(H.ci() + nnz, 0, sizeof(int32_t) * kPad, s));  // the compaction writes [0, nnz)
     AMG_CUDA(cudaMemsetAsync(H.v() + nnz, 0, sizeof(double) * kPad, s));
     if (n > 0) {
-        { sparsify_compact_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(),
-                                                       H.ci(), H.v()); ::amg::count_launch(); }
+        if (full) {
+            compact_values_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), keep, hval.as<double>(), H.rp(), H.ci(),
+                                                        H.v());
+        } else {
+            sparsify_compact_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(), H.ci(),
+                                                           H.v());
+        }
+        ::amg::count_launch();
         AMG_CHECK_LAUNCH();
     }
     return nnz;
@@ -1773,8 +2022,15 @@ void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s) {
     }
     { gram_kernel<<<div_up((int64_t)n * n, kThreads), kThreads, 0, s>>>(n, linv.as<double>(), inv); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
+    if (!read_scalar(err.as<int>(), s)) return;
+    // not positive definite: Gauss-Jordan with partial pivoting instead
+    TmpBuf a(sizeof(double) * (size_t)n * n, s), fac(sizeof(double) * (size_t)n, s);
+    AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
+    { densify_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), a.as<double>()); ::amg::count_launch(); }
+    { gauss_jordan_kernel<<<1, 1024, 0, s>>>(n, a.as<double>(), inv, fac.as<double>(), err.as<int>()); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
     if (read_scalar(err.as<int>(), s))
-        throw Error(AMG_BREAKDOWN, "coarsest operator is not positive definite (Cholesky pivot <= 0)");
+        throw Error(AMG_BREAKDOWN, "coarsest operator is singular (zero pivot in Gauss-Jordan elimination)");
 }
 
 }  // namespace setup

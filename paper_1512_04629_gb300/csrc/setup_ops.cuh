@@ -38,15 +38,19 @@ void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, ui
                      cudaStream_t s);
 // Hybrid variant: pattern of Phat^T Ahat P (+ transpose) with Ahat the
 // sparsified fine operator.  Recomputes AP from Ahat.
-// Sparsify with diagonal lumping; fills keep[] and Ahat; returns nnz(Ahat).
+// Sparsify (Algorithm 3's drop test and symmetric N); fills keep[] and Ahat;
+// returns nnz(Ahat).  S == nullptr: diagonal lumping (Algorithm 3b, with its
+// ismax guard); otherwise full lumping to the strong neighbours given by the
+// strength flags S of A (Algorithm 3's own loop).
 int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const int32_t *diagpos,
-                 double gamma, uint8_t *keep, DevCSR &Ahat, cudaStream_t s);
+                 double gamma, uint8_t *keep, DevCSR &Ahat, cudaStream_t s, const uint8_t *S = nullptr);
 // Copy of A (Ahat = A when gamma = 0) with keep[] = 1.
 void copy_all(const DevCSR &A, uint8_t *keep, DevCSR &Ahat, cudaStream_t s);
 // ell1 diagonal d_i = sum_j |a_ij| and its inverse.
 void l1_diag(const DevCSR &A, double *d, double *dinv, cudaStream_t s);
-// Dense inverse of the SPD coarsest operator through its Cholesky factor.
-// Throws AMG_BREAKDOWN if a pivot is not positive.
+// Dense inverse of the coarsest operator through its Cholesky factor; when a
+// Cholesky pivot is not positive, by Gauss-Jordan elimination with partial
+// pivoting.  Throws AMG_BREAKDOWN if the operator is singular.
 void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s);
 
 }  // namespace setup
