@@ -12,9 +12,10 @@ Conventions (all generators):
   eliminated, no ``h^2`` scaling, lexicographic order with x fastest;
 * CSR with ``int32`` row pointers and column indices, ``float64`` values,
   columns strictly increasing in every row, the diagonal always stored;
-* the matrix is symmetric (structurally and numerically) and an M-matrix
-  (positive diagonal, non-positive off-diagonals, weakly diagonally dominant,
-  strictly dominant on boundary rows).
+* the matrix is symmetric (structurally and numerically) with a positive
+  diagonal; every generator but the rotated anisotropic one also gives an
+  M-matrix (non-positive off-diagonals, weakly diagonally dominant, strictly
+  dominant on boundary rows).
 
 Random numbers come from one counter-based generator, SplitMix64
 (G. Steele, D. Lea, C. Flood, "Fast splittable pseudorandom number
@@ -217,6 +218,62 @@ def fv7_lognormal(N: int, seed: int = 3, sigma: float = 2.0) -> CSR:
     return _assemble(n, cols, vals, f"fv7_lognormal_{N}_s{seed}")
 
 
+def q1_element_stiffness(K: np.ndarray) -> np.ndarray:
+    """4 x 4 bilinear (Q1) element matrix int grad(phi_a)^T K grad(phi_b) on
+    a square element (independent of its size in 2D).  Local nodes
+    0 (0,0), 1 (1,0), 2 (0,1), 3 (1,1); 2 x 2 Gauss quadrature, exact here
+    (each integrand is at most quadratic in each coordinate)."""
+    g = np.array([0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)])
+    Ke = np.zeros((4, 4))
+    for x in g:
+        for y in g:
+            grads = np.array([[-(1 - y), -(1 - x)], [1 - y, -x], [-y, 1 - x], [y, x]])
+            Ke += 0.25 * grads @ K @ grads.T
+    return Ke
+
+
+def rotated_aniso_q1(N: int, theta: float = np.pi / 8, eps: float = 1e-3) -> CSR:
+    """2D rotated anisotropic diffusion -div(K grad u) = f, K = Q^T D Q with
+    Q = [[cos t, sin t], [-sin t, cos t]], D = diag(1, eps) (paper Section 5),
+    Q1 elements on a uniform square mesh of (N + 1)^2 elements, homogeneous
+    Dirichlet boundary: the N x N interior nodes, a 9-point stencil (no h
+    scaling: the 2D Q1 stiffness does not depend on h).  Off-diagonals of
+    either sign: not an M-matrix."""
+    c, s = np.cos(theta), np.sin(theta)
+    Q = np.array([[c, s], [-s, c]])
+    K = Q.T @ np.diag([1.0, eps]) @ Q
+    Ke = q1_element_stiffness(K)
+    local = {(0, 0): 0, (1, 0): 1, (0, 1): 2, (1, 1): 3}
+    st = {}
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            v = 0.0
+            for ey in (0, 1):          # the four elements around the node
+                for ex in (0, 1):
+                    cpos = (1 - ex, 1 - ey)
+                    npos = (cpos[0] + dx, cpos[1] + dy)
+                    if npos in local:
+                        v += Ke[local[cpos], local[npos]]
+            st[(dy, dx)] = v
+    n = N * N
+    i = np.arange(n, dtype=np.int64)
+    x = i % N
+    y = i // N
+    pts = [(dy, dx) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if st[(dy, dx)] != 0.0]
+    cols = np.empty((n, len(pts)), dtype=np.int64)
+    vals = np.empty((n, len(pts)), dtype=np.float64)
+    for k, (dy, dx) in enumerate(pts):
+        ok = np.ones(n, dtype=bool)
+        for d, cc in ((dx, x), (dy, y)):
+            if d < 0:
+                ok &= cc > 0
+            elif d > 0:
+                ok &= cc < N - 1
+        cols[:, k] = np.where(ok, i + dy * N + dx, -1)
+        vals[:, k] = st[(dy, dx)]
+    return _assemble(n, cols, vals, f"rotated_aniso_q1_{N}")
+
+
 def generate(kind: str, N: int, seed: int = 3) -> CSR:
     """Dispatch by stencil name."""
     if kind == "2d5":
@@ -229,4 +286,6 @@ def generate(kind: str, N: int, seed: int = 3) -> CSR:
         return q1_laplace3d(N)
     if kind == "fv7":
         return fv7_lognormal(N, seed)
+    if kind == "aniso":
+        return rotated_aniso_q1(N)
     raise ValueError(f"unknown stencil {kind!r}")

@@ -46,10 +46,17 @@ def parse():
     p.add_argument("--no-arms", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    p.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "lump", "aniso"],
                    help="c2 (default, the bench line): 3D 7-pt 128^3; c3: 27-pt 192^3 precision arms; "
-                        "c4: lognormal FV 160^3 batched k in {1,8,32,64}; c5: serving stream")
+                        "c4: lognormal FV 160^3 batched k in {1,8,32,64}; c5: serving stream; "
+                        "lump: 3D 7-pt 128^3, diagonal vs full lumping, CG vs GMRES; "
+                        "aniso: rotated anisotropic Q1 2D 2048^2 (theta pi/8, eps 1e-3), GMRES arms")
     p.add_argument("--serve-seconds", type=float, default=20.0)
+    p.add_argument("--lump", default="diag", choices=["diag", "strong"],
+                   help="sparsify: diagonal lumping (Algorithm 3b, default) or full lumping to strong neighbours "
+                        "(Algorithm 3)")
+    p.add_argument("--krylov", default="cg", choices=["cg", "gmres"],
+                   help="outer solver: PCG (default) or restarted GMRES(30)")
     p.add_argument("--eager", action="store_true",
                    help="launch the PCG iterations one kernel at a time (no CUDA graph; for ncu launch lists)")
     p.add_argument("--ncu-setup", action="store_true",
@@ -61,10 +68,14 @@ def parse():
 
 def workload_config(args):
     n = args.grid ** 3
+    lump = "full lumping to strong neighbours (Algorithm 3)" if args.lump == "strong" else \
+        "diagonal lumping (Algorithm 3b)"
+    solver = "GMRES(30)" if args.krylov == "gmres" else "PCG"
     return {
         "workload": f"3D 7-point Poisson {args.grid}^3 (n={n}), Sparse Galerkin gamma={args.gamma} on levels>=1, "
-                    f"PCG + V(1,1) l1-Jacobi to {args.tol:g}, FP64; step = GPU setup + sparsify + solve",
+                    f"{lump}, {solver} + V(1,1) l1-Jacobi to {args.tol:g}, FP64; step = GPU setup + sparsify + solve",
         "grid": args.grid, "n": n, "gamma": args.gamma, "tol": args.tol, "precision": "fp64",
+        "lump": args.lump, "krylov": args.krylov,
         "theta": 0.25, "coarsening": "PMIS", "interpolation": "direct",
         "l2_policy": "inputs larger than L2 (A = 175 MB FP64 CSR at 128^3)",
         "parallelism": "replicas",
@@ -169,13 +180,13 @@ def ncu_traffic():
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
-def oracle_step(A, b, gamma, tol):
+def oracle_step(A, b, gamma, tol, lump="diag", krylov="cg"):
     import oracle
 
     t0 = time.perf_counter()
     h = oracle.Hierarchy(A)
-    h.sparsify([0.0, gamma])
-    x, info = h.pcg(b, tol=tol)
+    h.sparsify([0.0, gamma], lump=1 if lump == "strong" else 0)
+    x, info = h.gmres(b, tol=tol) if krylov == "gmres" else h.pcg(b, tol=tol)
     dt = time.perf_counter() - t0
     assert info.status == 0, info
     return dt, info
@@ -194,7 +205,7 @@ def run_reference(args):
     budget = 200.0 / max(1, args.steps + args.warmup)  # seconds per step
     # one untimed full-size step sizes the sample: full size if it fits the
     # per-step budget, else the largest sub-grid that does (value scaled by n)
-    t_full, _ = oracle_step(A, b, args.gamma, args.tol)
+    t_full, _ = oracle_step(A, b, args.gamma, args.tol, args.lump, args.krylov)
     N, As, bs, scale = args.grid, A, b, 1.0
     if t_full > budget:
         N = max(16, int(args.grid * (budget / t_full) ** (1.0 / 3.0)))
@@ -202,11 +213,11 @@ def run_reference(args):
         bs = gen.rhs_uniform(As.n, 1)
         scale = As.n / A.n
     for _ in range(max(0, args.warmup - (1 if scale == 1.0 else 0))):
-        oracle_step(As, bs, args.gamma, args.tol)
+        oracle_step(As, bs, args.gamma, args.tol, args.lump, args.krylov)
     times = []
     its = None
     for _ in range(args.steps):
-        dt, info = oracle_step(As, bs, args.gamma, args.tol)
+        dt, info = oracle_step(As, bs, args.gamma, args.tol, args.lump, args.krylov)
         times.append(dt)
         its = info.iterations
     total = sum(times)
@@ -228,7 +239,7 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 KIND_NAMES = {0: "relax_pre_residual", 1: "restrict", 2: "prolong", 3: "relax_post", 4: "coarse_solve",
-              5: "pcg_Ap_dot", 6: "pcg_vector"}
+              5: "pcg_Ap_dot", 6: "pcg_vector"}  # under GMRES: 5 = A z, 6 = orthogonalisation and updates
 SETUP_KIND_NAMES = {8: "strength", 9: "cf_split", 10: "interpolation", 11: "galerkin_spgemm",
                     12: "level_maps_minimal_pattern", 13: "sparsify", 14: "cycle_prep", 15: "coarse_cholesky"}
 
@@ -416,6 +427,77 @@ def run_c5(args):
                       "max_ms": float(lat.max()), "iterations_median": float(np.median(its))}))
 
 
+def _lumping_arms(args, A, arms, workload):
+    """One line of arms: setup (median of 3, events), the sparsify phase
+    (setup_timing), solve (median of 3), iterations and operator sizes."""
+    import torch
+
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    b = gen.rhs_uniform(A.n, 1)
+    rp, ci, va = (torch.from_numpy(a).cuda() for a in (A.rowptr, A.col, A.val))
+    A_dev = amg.amg.csr_struct(rp, ci, va)
+    bd = torch.from_numpy(b).cuda()
+    out = {}
+    for name, opts in arms:
+        hs = []  # every timed hierarchy is kept until the timing ends (no teardown inside it)
+        ms_setup, _ = _events_ms(lambda: hs.append(amg.Hierarchy.setup(A_dev, **opts)))
+        del hs
+        ht = amg.Hierarchy.setup(A_dev, setup_timing=1, **opts)
+        phases = collect_setup_timing(ht, ht.num_levels)
+        del ht
+        h = amg.Hierarchy.setup(A_dev, **opts)
+        xd = torch.zeros_like(bd)
+        ms_solve, (x, info) = _events_ms(lambda: h.solve(bd, xd, tol=args.tol, max_it=1000))
+        nnz = [h.level_stats(l)["nnz_operator"] for l in range(h.num_levels)]
+        gal = [h.level_stats(l)["nnz_galerkin"] for l in range(h.num_levels)]
+        out[name] = {"setup_ms": round(ms_setup, 3), "sparsify_ms": phases.get("sparsify"),
+                     "solve_ms": round(ms_solve, 3), "iterations": info.iterations, "status": info.status,
+                     "final_relres": info.final_relres,
+                     "ms_per_iteration": round(ms_solve / max(info.iterations, 1), 4),
+                     "conv_factor": round(info.conv_factor, 4),
+                     "operator_complexity": round(sum(nnz) / nnz[0], 4),
+                     "galerkin_complexity": round(sum(gal) / gal[0], 4), "nnz_per_level": nnz}
+        del h
+    print(json.dumps({"workload": workload, "unit": "ms", "tol": args.tol, "arms": out}))
+
+
+def run_lump(args):
+    """3D 7-point 128^3: Algorithm 3b (diagonal) vs Algorithm 3 (full lumping to
+    strong neighbours), each under PCG and GMRES(30), gamma 0.1 and 1.0 on
+    every coarse level."""
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    A = gen.poisson3d_7pt(args.grid)
+    arms = [("galerkin_cg", {})]
+    for g in (0.1, 1.0):
+        for lump, ln in ((amg.LUMP_DIAG, "diag"), (amg.LUMP_STRONG, "full")):
+            for kr, kn in ((amg.KRYLOV_CG, "cg"), (amg.KRYLOV_GMRES, "gmres")):
+                arms.append((f"{ln}_{kn}_gamma{g}", {"gamma": [0.0, g], "lump": lump, "krylov": kr}))
+    _lumping_arms(args, A, arms, f"lump: 3D 7-point {args.grid}^3 (n={A.n}), Sparse Galerkin")
+
+
+def run_aniso(args):
+    """Rotated anisotropic diffusion (Q1, theta = pi/8, eps = 1e-3) on a 2D
+    grid: Galerkin, Sparse and Hybrid Galerkin with diagonal and full
+    lumping, all under GMRES(30)."""
+    import amg_inputs as gen
+    import paper_1512_04629_gb300 as amg
+
+    N = 2048 if args.grid == 128 else args.grid
+    A = gen.rotated_aniso_q1(N)
+    G = amg.KRYLOV_GMRES
+    arms = [("galerkin", {"krylov": G})]
+    for sched, sn in (([0.0, 0.1, 1.0], "0.1-1"), ([0.0, 1.0], "1")):
+        for method, mn in ((amg.METHOD_SPARSE, "sparse"), (amg.METHOD_HYBRID, "hybrid")):
+            for lump, ln in ((amg.LUMP_DIAG, "diag"), (amg.LUMP_STRONG, "full")):
+                arms.append((f"{mn}_{ln}_gamma{sn}", {"gamma": sched, "method": method, "lump": lump,
+                                                       "krylov": G}))
+    _lumping_arms(args, A, arms, f"aniso: rotated anisotropic Q1 {N}^2 (n={A.n}, theta pi/8, eps 1e-3), GMRES(30)")
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -428,7 +510,7 @@ def main():
 
         build.build()
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        {"c3": run_c3, "c4": run_c4, "c5": run_c5}[args.workload](args)
+        {"c3": run_c3, "c4": run_c4, "c5": run_c5, "lump": run_lump, "aniso": run_aniso}[args.workload](args)
         return
     import numpy as np
     import torch
@@ -461,10 +543,12 @@ def main():
     xd = torch.zeros_like(bd)
     A_dev = amg.amg.csr_struct(rp, ci, va)
     gamma = [0.0, args.gamma]
+    hopts = {"lump": amg.LUMP_STRONG if args.lump == "strong" else amg.LUMP_DIAG,
+             "krylov": amg.KRYLOV_GMRES if args.krylov == "gmres" else amg.KRYLOV_CG}
     torch.cuda.synchronize()
 
     def step(timing=False):
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0 if args.eager else 1,
+        h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0 if args.eager else 1,
                                 setup_timing=1 if timing else 0)
         if timing:
             setup_phases.append(collect_setup_timing(h, h.num_levels))
@@ -476,18 +560,18 @@ def main():
     setup_phases = []
 
     if args.ncu_setup:
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
+        h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0)
         del h
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
+        h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
         print(json.dumps({"ncu_setup": True, "levels": h.num_levels}))
         return
 
     if args.ncu_solve:
-        h = amg.Hierarchy.setup(A_dev, gamma=gamma, use_graph=0)
+        h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0)
         h.solve(bd, xd, tol=args.tol)
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
@@ -601,13 +685,13 @@ def main():
         bh = hp[3].numpy()
         xn = xh.numpy()
         ke = max(1, min(args.steps, 5))
-        h = amg.Hierarchy.setup(A_host, gamma=gamma)
+        h = amg.Hierarchy.setup(A_host, **hopts, gamma=gamma)
         h.solve(bh, xn, tol=args.tol)
         del h
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            h = amg.Hierarchy.setup(A_host, gamma=gamma)
+            h = amg.Hierarchy.setup(A_host, **hopts, gamma=gamma)
             _, info = h.solve(bh, xn, tol=args.tol)
             assert info.status == 0
             del h
@@ -653,7 +737,7 @@ def main():
 
     cpu = None
     if not args.no_cpu:
-        dt, info = oracle_step(A, b, args.gamma, args.tol)
+        dt, info = oracle_step(A, b, args.gamma, args.tol, args.lump, args.krylov)
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one full step ({args.grid}^3 setup + sparsify + PCG, {info.iterations} its) on one host core"}
 

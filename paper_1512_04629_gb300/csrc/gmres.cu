@@ -1,10 +1,14 @@
 // gmres.cu -- kernels of the restarted flexible GMRES outer solver.
 //
 // One Arnoldi step of FGMRES(m) (Saad 1993) with the V-cycle as right
-// preconditioner: z_j = M v_j, w = A_0 z_j, two passes of classical
-// Gram-Schmidt (h = V^T w, w -= V h, twice: every pass is one streaming read
-// of the basis instead of j + 1 dependent reductions), h_{j+1,j} = ||w||,
-// the Givens rotations of the Hessenberg column, v_{j+1} = w / h_{j+1,j}.
+// preconditioner: z_j = M v_j, w = A_0 z_j, classical Gram-Schmidt
+// (h = V^T w, w -= V h: each pass is one streaming read of the basis instead
+// of j + 1 dependent reductions) with a second pass only when the first
+// removed more than half of ||w||^2 (Daniel, Gragg, Kaufman, Stewart 1976:
+// "twice is enough"), h_{j+1,j} = ||w||, the Givens rotations of the
+// Hessenberg column, v_{j+1} = w / h_{j+1,j}.  On this part the FP64 FMAs
+// of the passes cost as much as their HBM traffic, so the skipped pass
+// halves the orthogonalisation.
 // The basis size j is a device scalar, so the step is one fixed launch
 // sequence and a restart cycle runs as one CUDA-graph WHILE loop.  Every
 // reduction is deterministic: per-block partials in a fixed layout, summed
@@ -31,7 +35,7 @@ namespace gm {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kGroup = 4;       // basis vectors per block row of the dot kernel
+constexpr int kGroup = 8;       // basis vectors per block row of the dot kernel
 constexpr int kMaxCoef = 513;   // restart length <= 512
 
 template <int NV>
@@ -55,45 +59,81 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
-// partial dot products of w with basis vectors 4 y .. 4 y + 3 (y = blockIdx.y)
+// partial dot products of w with basis vectors 8 y .. 8 y + 7 (y = blockIdx.y):
+// eight independent loads per element keep enough requests in flight;
+// WW: the y = 0 blocks also sum w . w into part row m + 1
+template <bool WW>
 __global__ void __launch_bounds__(kThreads)
-mdot_kernel(int64_t n, const double *__restrict__ V, const double *__restrict__ w, const GmresScalars *sc,
+mdot_kernel(int64_t n, int m, const double *__restrict__ V, const double *__restrict__ w, const GmresScalars *sc,
             double *part) {
+    if (!WW && !sc->reorth) return;  // second pass skipped (uniform)
     const int j = sc->j;
     const int i0 = blockIdx.y * kGroup;
     if (i0 > j) return;  // uniform over the block
     const int nv = min(kGroup, j + 1 - i0);
-    double acc[kGroup] = {0.0, 0.0, 0.0, 0.0};
+    double acc[kGroup + 1];
+#pragma unroll
+    for (int q = 0; q <= kGroup; ++q) acc[q] = 0.0;
+    const bool ww = WW && blockIdx.y == 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
         const double we = w[e];
 #pragma unroll
         for (int q = 0; q < kGroup; ++q)
             if (q < nv) acc[q] += V[(size_t)(i0 + q) * n + e] * we;
+        if (ww) acc[kGroup] += we * we;
     }
-    block_sum<kGroup>(acc);
-    if (threadIdx.x == 0)
+    block_sum<kGroup + 1>(acc);
+    if (threadIdx.x == 0) {
         for (int q = 0; q < nv; ++q) part[(size_t)(i0 + q) * kGmresMaxBlocks + blockIdx.x] = acc[q];
+        if (ww) part[(size_t)(m + 1) * kGmresMaxBlocks + blockIdx.x] = acc[kGroup];
+    }
 }
 
-// out[i] = sum over blocks of part row i, i = 0..j: one warp per vector
-__global__ void mdot_finish_kernel(int nblocks, const GmresScalars *sc, const double *part, double *out) {
+// out[i] = sum over blocks of part row i, i = 0..j (and, WW, sc->ww from
+// row m + 1): one warp per vector
+template <bool WW>
+__global__ void mdot_finish_kernel(int nblocks, int m, GmresScalars *sc, const double *part, double *out) {
+    if (!WW && !sc->reorth) return;
     const int j = sc->j;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = wid; i <= j; i += nw) {
+    const int rows = WW ? j + 2 : j + 1;
+    for (int q = wid; q < rows; q += nw) {
+        const int i = q <= j ? q : m + 1;
         double t = 0.0;
         for (int b = lane; b < nblocks; b += 32) t += part[(size_t)i * kGmresMaxBlocks + b];
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) out[i] = t;
+        if (lane == 0) {
+            if (q <= j) out[i] = t;
+            else sc->ww = t;
+        }
+    }
+}
+
+// second pass or not: ||w'||^2 from the first update's partials
+__global__ void decide_kernel(int nblocks, GmresScalars *sc, GmresArrays ar) {
+    const int lane = threadIdx.x;
+    double t = 0.0;
+    for (int b = lane; b < nblocks; b += 32) t += ar.part[b];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    const bool again = !(t >= 0.5 * sc->ww);  // also on a non-finite norm
+    const int j = sc->j;
+    if (!again)
+        for (int i = lane; i <= j; i += 32) ar.hc2[i] = 0.0;
+    if (lane == 0) {
+        sc->wn2 = t;
+        sc->reorth = again ? 1 : 0;
     }
 }
 
 // out = base + sign * sum_{i < cnt} coef[i] V_i, cnt = j + 1 (update) or j
-// (forming x); NORM: ||out||^2 block partials into part row 0
-template <bool NORM>
+// (forming x); NORM: ||out||^2 block partials into part row 0; IFREORTH:
+// only when the second pass runs
+template <bool NORM, bool IFREORTH>
 __global__ void __launch_bounds__(kThreads)
 combo_kernel(int64_t n, const double *base, double *out, const double *__restrict__ V, const double *coef,
              const GmresScalars *sc, int cnt_plus, double sign, double *part) {
+    if (IFREORTH && !sc->reorth) return;
     __shared__ double c[kMaxCoef];
     const int cnt = sc->j + cnt_plus;
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) c[i] = sign * coef[i];
@@ -117,8 +157,12 @@ __global__ void step_finish_kernel(int nblocks, GmresScalars *sc, GmresArrays ar
                                    cudaGraphConditionalHandle handle, int use_handle) {
     const int lane = threadIdx.x;
     double t = 0.0;
-    for (int b = lane; b < nblocks; b += 32) t += ar.part[b];
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (sc->reorth) {
+        for (int b = lane; b < nblocks; b += 32) t += ar.part[b];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    } else {
+        t = sc->wn2;
+    }
     if (lane != 0) return;
     const int j = sc->j, m = sc->m;
     const double hn = sqrt(t);
@@ -232,8 +276,13 @@ void mdot(int64_t n, int m, const double *V, const double *w, GmresScalars *sc, 
           cudaStream_t s) {
     const int bx = dot_blocks(n);
     const dim3 grid(bx, (m + 1 + kGroup - 1) / kGroup);
-    { mdot_kernel<<<grid, kThreads, 0, s>>>(n, V, w, sc, ar.part); ::amg::count_launch(); }
-    { mdot_finish_kernel<<<1, 1024, 0, s>>>(bx, sc, ar.part, second ? ar.hc2 : ar.hc); ::amg::count_launch(); }
+    if (second) {
+        { mdot_kernel<false><<<grid, kThreads, 0, s>>>(n, m, V, w, sc, ar.part); ::amg::count_launch(); }
+        { mdot_finish_kernel<false><<<1, 1024, 0, s>>>(bx, m, sc, ar.part, ar.hc2); ::amg::count_launch(); }
+    } else {
+        { mdot_kernel<true><<<grid, kThreads, 0, s>>>(n, m, V, w, sc, ar.part); ::amg::count_launch(); }
+        { mdot_finish_kernel<true><<<1, 1024, 0, s>>>(bx, m, sc, ar.part, ar.hc); ::amg::count_launch(); }
+    }
     AMG_CHECK_LAUNCH();
 }
 
@@ -242,10 +291,11 @@ void mupdate(int64_t n, int m, const double *V, double *w, GmresScalars *sc, Gmr
     (void)m;
     const int bx = dot_blocks(n);
     if (second) {
-        { combo_kernel<true><<<bx, kThreads, 0, s>>>(n, w, w, V, ar.hc2, sc, 1, -1.0, ar.part); ::amg::count_launch(); }
+        { combo_kernel<true, true><<<bx, kThreads, 0, s>>>(n, w, w, V, ar.hc2, sc, 1, -1.0, ar.part); ::amg::count_launch(); }
         { step_finish_kernel<<<1, 32, 0, s>>>(bx, sc, ar, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
     } else {
-        { combo_kernel<false><<<bx, kThreads, 0, s>>>(n, w, w, V, ar.hc, sc, 1, -1.0, ar.part); ::amg::count_launch(); }
+        { combo_kernel<true, false><<<bx, kThreads, 0, s>>>(n, w, w, V, ar.hc, sc, 1, -1.0, ar.part); ::amg::count_launch(); }
+        { decide_kernel<<<1, 32, 0, s>>>(bx, sc, ar); ::amg::count_launch(); }
     }
     AMG_CHECK_LAUNCH();
 }
@@ -269,7 +319,7 @@ void form_x(int64_t n, int m, const double *Z, const double *x0, double *x, Gmre
             cudaStream_t s) {
     (void)m;
     { solve_y_kernel<<<1, 1, 0, s>>>(sc, ar); ::amg::count_launch(); }
-    { combo_kernel<false><<<dot_blocks(n), kThreads, 0, s>>>(n, x0, x, Z, ar.y, sc, 0, 1.0, ar.part); ::amg::count_launch(); }
+    { combo_kernel<false, false><<<dot_blocks(n), kThreads, 0, s>>>(n, x0, x, Z, ar.y, sc, 0, 1.0, ar.part); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 

@@ -1130,23 +1130,38 @@ __global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int3
 // Algorithm 3's own loop: full lumping to strong neighbours.  Every dropped
 // entry (i,j) becomes a list of "lump edges" (k, t): for each k in
 // W = {k : S_jk != 0, (i,k) kept}, t = (|a_jk| / sum_W |a_jm|) a_ij, or one
-// fallback edge (~i, a_ij) when W is empty (the value goes to a_ii).  The
-// edges of row i are stored in entry order, each entry's in increasing k --
-// the order in which the sequential loop applies the updates.  A kept entry
-// then gathers the updates that reach it in that same order, so the result
-// does not depend on thread scheduling (no atomics):
-//   (r,c), r != c: t of row r's edges with k = c (update (i,k)) and of row
-//     c's edges with k = r (update (k,i)), the lower row's first;
-//   (r,r): over the kept columns i of row r in increasing order -- row r's
-//     own edges with k = r add t, add t, subtract t (updates (i,k), (k,i),
-//     (k,k) with k = i) and its fallback edges add the value; another row
-//     i's edges with k = r subtract t (update (k,k)).
-// The kept pattern is symmetric (N is), which is what lets row r find every
-// row i that can reach it among its own kept columns.
+// fallback edge (~i, a_ij) when W is empty (the value goes to a_ii).  Edges
+// are numbered in entry order, each entry's in increasing k -- the order in
+// which the sequential loop applies the updates.  Each edge's first update
+// lands on the kept position (i,k) (the fallback's on (i,i)); the edges are
+// grouped by that position (a counting sort, then each small group ordered
+// by edge number), and a kept entry gathers in the loop's order, without
+// atomics on values:
+//   (r,c), r != c: the group of (r,c) (updates (i,k) from row r) and the
+//     group of the mirror (c,r) (updates (k,i) from row c), the lower row's
+//     first;
+//   (r,r): over the kept columns i of row r in increasing order -- for i = r
+//     the group of (r,r): a fallback adds its value, an edge with k = r adds
+//     t, adds t, subtracts t (updates (i,k), (k,i), (k,k)); for i != r the
+//     group of the mirror (i,r), whose edges have k = r: subtract t (update
+//     (k,k)).
+// The kept pattern is symmetric (N is), so the mirror position of every kept
+// entry exists and row r finds every row that can reach (r,r) among its own
+// kept columns.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int32_t find_col(const int32_t *ci, int32_t lo, int32_t hi, int32_t c) {
-    const int32_t p = lower_bound_i32(ci, lo, hi, c);
-    return (p < hi && ci[p] == c) ? p : -1;
+// W in increasing k: row j's strong entries merged with row i's sorted
+// columns; f(q, pk) for q = position of (j,k), pk = position of (i,k)
+template <class F>
+__device__ __forceinline__ void walk_w(const int32_t *ci, const uint8_t *keep, const uint8_t *S, int32_t pi0,
+                                       int32_t pi1, int32_t pj0, int32_t pj1, F &&f) {
+    int32_t a = pi0;
+    for (int32_t q = pj0; q < pj1; ++q) {
+        if (!S[q]) continue;
+        const int32_t k = ci[q];
+        while (a < pi1 && ci[a] < k) ++a;
+        if (a == pi1) return;
+        if (ci[a] == k && keep[a]) f(q, a);
+    }
 }
 
 // per dropped entry: |W| (edges; 1 for the fallback) and sum_W |a_jm| in
@@ -1167,23 +1182,21 @@ __global__ void lump_count_kernel(int32_t n, const int32_t *rp, const int32_t *c
         const int32_t j = ci[p];
         double d = 0.0;
         int32_t w = 0;
-        for (int32_t q = rp[j]; q < rp[j + 1]; ++q) {
-            if (!S[q]) continue;
-            const int32_t pk = find_col(ci, p0, p1, ci[q]);
-            if (pk >= 0 && keep[pk]) {
-                d += fabs(v[q]);
-                ++w;
-            }
-        }
+        walk_w(ci, keep, S, p0, p1, rp[j], rp[j + 1], [&](int32_t q, int32_t) {
+            d += fabs(v[q]);
+            ++w;
+        });
         den[p] = d;
         ecnt[p] = (d > 0.0) ? w : 1;
     }
 }
 
+// the edges: ek = k (or ~i for the fallback), et = t, etg = the position of
+// the first update's target
 template <int T>
 __global__ void lump_emit_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
-                                 const uint8_t *keep, const uint8_t *S, const double *den, const int64_t *eoff,
-                                 int32_t *ek, double *et) {
+                                 const uint8_t *keep, const uint8_t *S, const int32_t *diagpos, const double *den,
+                                 const int64_t *eoff, int32_t *ek, double *et, int32_t *etg) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(g / T);
     const int t = (int)(g % T);
@@ -1196,33 +1209,53 @@ __global__ void lump_emit_kernel(int32_t n, const int32_t *rp, const int32_t *ci
         if (!(d > 0.0)) {
             ek[e] = ~i;
             et[e] = a;
+            etg[e] = diagpos[i];
             continue;
         }
         const int32_t j = ci[p];
-        for (int32_t q = rp[j]; q < rp[j + 1]; ++q) {
-            if (!S[q]) continue;
-            const int32_t k = ci[q];
-            const int32_t pk = find_col(ci, p0, p1, k);
-            if (pk >= 0 && keep[pk]) {
-                ek[e] = k;
-                et[e] = (fabs(v[q]) / d) * a;
-                ++e;
-            }
-        }
+        walk_w(ci, keep, S, p0, p1, rp[j], rp[j + 1], [&](int32_t q, int32_t pk) {
+            ek[e] = ci[q];
+            et[e] = (fabs(v[q]) / d) * a;
+            etg[e] = pk;
+            ++e;
+        });
     }
 }
 
-__device__ __forceinline__ double lump_add_row(double x, int64_t e0, int64_t e1, const int32_t *ek,
-                                               const double *et, int32_t k) {
-    for (int64_t e = e0; e < e1; ++e)
-        if (ek[e] == k) x += et[e];
-    return x;
+__global__ void lump_hist_kernel(int64_t E, const int32_t *etg, int32_t *tcnt) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E) atomicAdd(&tcnt[etg[e]], 1);
+}
+
+// unordered placement into the groups (the next kernel orders each group)
+__global__ void lump_place_kernel(int64_t E, const int32_t *etg, const int64_t *toff, int32_t *tfill,
+                                  int32_t *tlist) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int32_t q = etg[e];
+    tlist[toff[q] + atomicAdd(&tfill[q], 1)] = (int32_t)e;
+}
+
+// each group in increasing edge number (insertion sort: groups hold a few edges)
+__global__ void lump_group_sort_kernel(int64_t nnz, const int64_t *toff, int32_t *tlist) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nnz) return;
+    const int64_t a = toff[q], b = toff[q + 1];
+    for (int64_t s = a + 1; s < b; ++s) {
+        const int32_t x = tlist[s];
+        int64_t u = s - 1;
+        while (u >= a && tlist[u] > x) {
+            tlist[u + 1] = tlist[u];
+            --u;
+        }
+        tlist[u + 1] = x;
+    }
 }
 
 template <int T>
 __global__ void lump_gather_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
-                                   const uint8_t *keep, const int64_t *eoff, const int32_t *ek,
-                                   const double *et, double *hval) {
+                                   const uint8_t *keep, const int32_t *tpos, const int64_t *toff,
+                                   const int32_t *tlist, const int32_t *ek, const double *et, double *hval) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t r = (int32_t)(g / T);
     const int t = (int)(g % T);
@@ -1233,29 +1266,27 @@ __global__ void lump_gather_kernel(int32_t n, const int32_t *rp, const int32_t *
         const int32_t c = ci[p];
         double x = v[p];
         if (c != r) {
-            const int32_t lo = min(r, c), hi = max(r, c);
-            x = lump_add_row(x, eoff[rp[lo]], eoff[rp[lo + 1]], ek, et, lo == r ? c : r);
-            x = lump_add_row(x, eoff[rp[hi]], eoff[rp[hi + 1]], ek, et, hi == r ? c : r);
+            const int32_t first = r < c ? p : tpos[p], second = r < c ? tpos[p] : p;
+            for (int64_t s = toff[first]; s < toff[first + 1]; ++s) x += et[tlist[s]];
+            for (int64_t s = toff[second]; s < toff[second + 1]; ++s) x += et[tlist[s]];
         } else {
             for (int32_t q = p0; q < p1; ++q) {
                 if (!keep[q]) continue;
-                const int32_t i = ci[q];
-                const int64_t e1 = eoff[rp[i + 1]];
-                if (i == r) {
-                    for (int64_t e = eoff[rp[i]]; e < e1; ++e) {
-                        const int32_t k = ek[e];
-                        if (k == r) {
-                            const double tt = et[e];
+                if (ci[q] == r) {
+                    for (int64_t s = toff[q]; s < toff[q + 1]; ++s) {
+                        const int32_t e = tlist[s];
+                        const double tt = et[e];
+                        if (ek[e] < 0) {
+                            x += tt;
+                        } else {
                             x += tt;
                             x += tt;
                             x -= tt;
-                        } else if (k == ~r) {
-                            x += et[e];
                         }
                     }
                 } else {
-                    for (int64_t e = eoff[rp[i]]; e < e1; ++e)
-                        if (ek[e] == r) x -= et[e];
+                    const int32_t m = tpos[q];
+                    for (int64_t s = toff[m]; s < toff[m + 1]; ++s) x -= et[tlist[s]];
                 }
             }
         }
@@ -1945,16 +1976,38 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
             });
             AMG_CHECK_LAUNCH();
             const int64_t E = exclusive_scan_i64_from_i32(ecnt.as<int32_t>(), eoff.as<int64_t>(), A.nnz, s);
-            TmpBuf ek(sizeof(int32_t) * (E + 1), s), et(sizeof(double) * (E + 1), s);
+            require(E < ((int64_t)1 << 31), "full lumping: 2^31 or more lump edges");
+            TmpBuf ek(sizeof(int32_t) * (E + 1), s), et(sizeof(double) * (E + 1), s), etg(sizeof(int32_t) * (E + 1), s),
+                tlist(sizeof(int32_t) * (E + 1), s), tcnt(sizeof(int32_t) * (A.nnz + 1), s),
+                toff(sizeof(int64_t) * (A.nnz + 1), s);
             hval.alloc(sizeof(double) * (A.nnz + 1), s);
             with_row_lanes(lanes, [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
-                const int gl = div_up((int64_t)n * L, kThreads);
-                lump_emit_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), keep, S, den.as<double>(),
-                                                            eoff.as<int64_t>(), ek.as<int32_t>(), et.as<double>());
+                lump_emit_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+                    n, A.rp(), A.ci(), A.v(), keep, S, diagpos, den.as<double>(), eoff.as<int64_t>(),
+                    ek.as<int32_t>(), et.as<double>(), etg.as<int32_t>());
                 ::amg::count_launch();
-                lump_gather_kernel<L><<<gl, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), keep, eoff.as<int64_t>(),
-                                                              ek.as<int32_t>(), et.as<double>(), hval.as<double>());
+            });
+            AMG_CUDA(cudaMemsetAsync(tcnt.ptr, 0, sizeof(int32_t) * A.nnz, s));
+            if (E > 0) {
+                lump_hist_kernel<<<div_up(E, kThreads), kThreads, 0, s>>>(E, etg.as<int32_t>(), tcnt.as<int32_t>());
+                ::amg::count_launch();
+            }
+            exclusive_scan_i64_from_i32(tcnt.as<int32_t>(), toff.as<int64_t>(), A.nnz, s);
+            AMG_CUDA(cudaMemsetAsync(tcnt.ptr, 0, sizeof(int32_t) * A.nnz, s));
+            if (E > 0) {
+                lump_place_kernel<<<div_up(E, kThreads), kThreads, 0, s>>>(E, etg.as<int32_t>(), toff.as<int64_t>(),
+                                                                          tcnt.as<int32_t>(), tlist.as<int32_t>());
+                ::amg::count_launch();
+                lump_group_sort_kernel<<<div_up(A.nnz, kThreads), kThreads, 0, s>>>(A.nnz, toff.as<int64_t>(),
+                                                                                   tlist.as<int32_t>());
+                ::amg::count_launch();
+            }
+            with_row_lanes(lanes, [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                lump_gather_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+                    n, A.rp(), A.ci(), A.v(), keep, tpos, toff.as<int64_t>(), tlist.as<int32_t>(), ek.as<int32_t>(),
+                    et.as<double>(), hval.as<double>());
                 ::amg::count_launch();
             });
             AMG_CHECK_LAUNCH();

@@ -894,3 +894,33 @@ def test_gmres_zero_rhs():
     h = oracle.Hierarchy(A)
     x, info = h.gmres(np.zeros(A.n))
     assert info.iterations == 0 and not x.any()
+
+
+# ---------------------------------------------------------------------------
+# rotated anisotropic Q1 generator (the paper's second test problem)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("theta,eps", [(np.pi / 8, 1e-3), (0.0, 0.01), (np.pi / 3, 0.2), (0.7, 1.0)])
+def test_rotated_aniso_q1_consistency(theta, eps):
+    """Q1 on a uniform grid reproduces -div(K grad u) exactly at interior
+    nodes for polynomials of degree <= 2 (grid units): the stencil sums to 0,
+    annihilates x and y, and maps x^2, y^2, xy to -2 K11, -2 K22, -2 K12."""
+    N = 9
+    A = gen.rotated_aniso_q1(N, theta=theta, eps=eps).to_scipy().toarray()
+    c, s = np.cos(theta), np.sin(theta)
+    K11, K22, K12 = c * c + eps * s * s, s * s + eps * c * c, c * s * (1 - eps)
+    yy, xx = np.divmod(np.arange(N * N), N)
+    row = 4 * N + 4  # centre node: all 9 neighbours interior
+    for u, want in ((np.ones(N * N), 0.0), (xx * 1.0, 0.0), (yy * 1.0, 0.0),
+                    (xx ** 2.0, -2 * K11), (yy ** 2.0, -2 * K22), (xx * yy * 1.0, -2 * K12)):
+        assert A[row] @ u == pytest.approx(want, abs=1e-12)
+    np.testing.assert_allclose(A, A.T, atol=1e-15)
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_rotated_aniso_q1_isotropic_is_q1_laplacian():
+    """eps = 1: K = I for every rotation; the textbook Q1 stencil 8/3, -1/3."""
+    A = gen.rotated_aniso_q1(5, theta=0.3, eps=1.0).to_scipy().toarray()
+    st = A[12].reshape(5, 5)[1:4, 1:4]
+    want = np.full((3, 3), -1.0 / 3.0)
+    want[1, 1] = 8.0 / 3.0
+    np.testing.assert_allclose(st, want, atol=1e-15)
