@@ -59,8 +59,54 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     }
 }
 
+// Block sums of NV values through shared memory: each of NV x 8 threads adds
+// 32 values in a fixed order, then NV threads add the 8 results.  A shuffle
+// tree costs five warp-wide FP64 adds per value and warp, and on this part
+// each occupies the FP64 pipe for 16 clocks: with a few elements per thread
+// those trees took more FP64 issue than the dot products themselves; this
+// takes about a quarter of it.  Result in v[] of thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum_smem(double (&v)[NV]) {
+    constexpr int kPadRow = kThreads + 4;
+    __shared__ double sh[NV][kPadRow];
+    __shared__ double sh2[NV][8];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NV * 8; t += blockDim.x) {
+        const int k = t >> 3, s = t & 7;
+        double x = 0.0;
+        for (int u = 0; u < kThreads / 8; ++u) x += sh[k][u * 8 + s];
+        sh2[k][s] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = 0.0;
+            for (int s = 0; s < 8; ++s) x += sh2[k][s];
+            v[k] = x;
+        }
+    }
+}
+
+// partial dot products of w with NV basis vectors from i0, and w . w (WW)
+template <int NV, bool WW>
+__device__ __forceinline__ void mdot_loop(int64_t n, const double *__restrict__ V, const double *__restrict__ w,
+                                          int i0, double (&acc)[kGroup + 1]) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+        const double we = w[e];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += V[(size_t)(i0 + q) * n + e] * we;
+        if (WW) acc[kGroup] += we * we;
+    }
+}
+
 // partial dot products of w with basis vectors 8 y .. 8 y + 7 (y = blockIdx.y):
-// eight independent loads per element keep enough requests in flight;
+// eight independent loads per element keep enough requests in flight, and a
+// loop specialised on the block's vector count issues no predicated-off FP64
+// FMAs (they would still occupy the FP64 pipe);
 // WW: the y = 0 blocks also sum w . w into part row m + 1
 template <bool WW>
 __global__ void __launch_bounds__(kThreads)
@@ -75,15 +121,17 @@ mdot_kernel(int64_t n, int m, const double *__restrict__ V, const double *__rest
 #pragma unroll
     for (int q = 0; q <= kGroup; ++q) acc[q] = 0.0;
     const bool ww = WW && blockIdx.y == 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-        const double we = w[e];
-#pragma unroll
-        for (int q = 0; q < kGroup; ++q)
-            if (q < nv) acc[q] += V[(size_t)(i0 + q) * n + e] * we;
-        if (ww) acc[kGroup] += we * we;
+    switch (nv) {
+        case 1: ww ? mdot_loop<1, true>(n, V, w, i0, acc) : mdot_loop<1, false>(n, V, w, i0, acc); break;
+        case 2: ww ? mdot_loop<2, true>(n, V, w, i0, acc) : mdot_loop<2, false>(n, V, w, i0, acc); break;
+        case 3: ww ? mdot_loop<3, true>(n, V, w, i0, acc) : mdot_loop<3, false>(n, V, w, i0, acc); break;
+        case 4: ww ? mdot_loop<4, true>(n, V, w, i0, acc) : mdot_loop<4, false>(n, V, w, i0, acc); break;
+        case 5: ww ? mdot_loop<5, true>(n, V, w, i0, acc) : mdot_loop<5, false>(n, V, w, i0, acc); break;
+        case 6: ww ? mdot_loop<6, true>(n, V, w, i0, acc) : mdot_loop<6, false>(n, V, w, i0, acc); break;
+        case 7: ww ? mdot_loop<7, true>(n, V, w, i0, acc) : mdot_loop<7, false>(n, V, w, i0, acc); break;
+        default: ww ? mdot_loop<8, true>(n, V, w, i0, acc) : mdot_loop<8, false>(n, V, w, i0, acc); break;
     }
-    block_sum<kGroup + 1>(acc);
+    block_sum_smem<kGroup + 1>(acc);
     if (threadIdx.x == 0) {
         for (int q = 0; q < nv; ++q) part[(size_t)(i0 + q) * kGmresMaxBlocks + blockIdx.x] = acc[q];
         if (ww) part[(size_t)(m + 1) * kGmresMaxBlocks + blockIdx.x] = acc[kGroup];
@@ -272,9 +320,18 @@ int dot_blocks(int64_t n) {
     return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
+namespace {
+// the dot kernel's block columns: at least 8 elements per thread, so the
+// per-block sums stay small next to the streaming FMAs
+int mdot_blocks(int64_t n) {
+    int64_t b = (n + kThreads * 8 - 1) / (kThreads * 8);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, dot_blocks(n)));
+}
+}  // namespace
+
 void mdot(int64_t n, int m, const double *V, const double *w, GmresScalars *sc, GmresArrays ar, bool second,
           cudaStream_t s) {
-    const int bx = dot_blocks(n);
+    const int bx = mdot_blocks(n);
     const dim3 grid(bx, (m + 1 + kGroup - 1) / kGroup);
     if (second) {
         { mdot_kernel<false><<<grid, kThreads, 0, s>>>(n, m, V, w, sc, ar.part); ::amg::count_launch(); }
