@@ -83,6 +83,9 @@ def _load():
         lib.orc_setup.argtypes = [P(_CSR), C.c_double, C.c_int32, C.c_int32, C.c_uint64,
                                   P(C.c_int32)]
         lib.orc_setup.restype = vp
+        lib.orc_setup_nongalerkin.argtypes = [P(_CSR), C.c_double, C.c_int32, C.c_int32, C.c_uint64,
+                                              vp, C.c_int32, C.c_int32, P(C.c_int32)]
+        lib.orc_setup_nongalerkin.restype = vp
         lib.orc_sparsify.argtypes = [vp, vp, C.c_int32]
         lib.orc_reintroduce.argtypes = [vp, C.c_int32, C.c_double, vp]
         lib.orc_sparsify_method.argtypes = [vp, vp, C.c_int32, C.c_int32]
@@ -332,12 +335,19 @@ class Hierarchy:
     """Oracle AMG hierarchy (Algorithm 1 Galerkin setup + Algorithm 4 sparsify)."""
 
     def __init__(self, A, theta: float = 0.25, max_size: int = 100, max_levels: int = 25,
-                 seed: int = 0):
+                 seed: int = 0, nongalerkin=None, lump: int = 0):
+        """nongalerkin: per-level drop tolerances for Algorithm 1's in-loop
+        (non-Galerkin) sparsify; None builds the Galerkin hierarchy."""
         lib = _load()
         self._lib = lib
         c = to_c(A)
         st = C.c_int32(0)
-        self._h = lib.orc_setup(C.byref(c), theta, max_size, max_levels, seed, C.byref(st))
+        if nongalerkin is None:
+            self._h = lib.orc_setup(C.byref(c), theta, max_size, max_levels, seed, C.byref(st))
+        else:
+            g = np.ascontiguousarray(nongalerkin, dtype=np.float64)
+            self._h = lib.orc_setup_nongalerkin(C.byref(c), theta, max_size, max_levels, seed, _ptr(g),
+                                                len(g), lump, C.byref(st))
         if not self._h:
             raise RuntimeError(f"orc_setup failed with status {st.value}")
         self.n = c.nrows

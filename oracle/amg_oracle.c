@@ -762,7 +762,7 @@ typedef struct {
 
 struct orc_hier {
     int32_t nlev;
-    int32_t method; /* 0 Sparse Galerkin, 1 Hybrid Galerkin (set by orc_sparsify_method) */
+    int32_t method; /* 0 Sparse Galerkin, 1 Hybrid Galerkin (set by orc_sparsify_method), 2 non-Galerkin */
     int32_t lump;   /* 0 diagonal lumping (Algorithm 3b), 1 full lumping (Algorithm 3) */
     double theta;   /* strength threshold of the setup (full lumping's S) */
     orc_level lev[64];
@@ -834,8 +834,44 @@ static int factor_coarsest(orc_hier *h) {
 /* first line).  Stop rule (the paper leaves max_size unvalued): stop when  */
 /* n_l <= max_size, at max_levels levels, or when the coarse grid would be  */
 /* empty or larger than 0.9 n_l; the last level is the coarsest.            */
+static orc_hier *setup_core(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
+                            uint64_t seed, const double *gamma, int32_t ngamma, int32_t lump,
+                            int32_t *status);
+
 orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
                     uint64_t seed, int32_t *status) {
+    return setup_core(A0, theta, max_size, max_levels, seed, NULL, 0, 0, status);
+}
+
+/* Algorithm 1 with its optional non-Galerkin step (Section 2.1, the       */
+/* method of Falgout and Schroder the paper compares against): each coarse */
+/* operator is sparsified as soon as the Galerkin product forms it, and    */
+/* the sparsified operator replaces it -- strength, C/F splitting,         */
+/* interpolation and the next Galerkin product all use it.  Readings: the  */
+/* call's garbled tolerance index is the per-level convention of           */
+/* Algorithm 4 (gamma[l] thins the operator of level l, levels past        */
+/* ngamma - 1 use the last value, gamma[0] = 0); M is formed from the      */
+/* current (already sparsified) A_l; S of full lumping is the strength of  */
+/* the coarse operator being thinned.  No Galerkin operator is retained,   */
+/* so Algorithm 5 does not apply (orc_sparsify / orc_reintroduce refuse).  */
+orc_hier *orc_setup_nongalerkin(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
+                                uint64_t seed, const double *gamma, int32_t ngamma, int32_t lump,
+                                int32_t *status) {
+    if (ngamma < 1 || gamma[0] != 0.0 || lump < 0 || lump > 1) {
+        *status = ORC_INVALID;
+        return NULL;
+    }
+    for (int32_t l = 0; l < ngamma; ++l)
+        if (!(gamma[l] >= 0.0) || !isfinite(gamma[l])) {
+            *status = ORC_INVALID;
+            return NULL;
+        }
+    return setup_core(A0, theta, max_size, max_levels, seed, gamma, ngamma, lump, status);
+}
+
+static orc_hier *setup_core(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
+                            uint64_t seed, const double *gamma, int32_t ngamma, int32_t lump,
+                            int32_t *status) {
     *status = ORC_OK;
     if (max_levels < 1 || max_levels > 64) {
         *status = ORC_INVALID;
@@ -879,11 +915,31 @@ orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t m
         if (!Lc->inM) goto oom;
         if (orc_minimal_pattern(Lc->A, L->AP, L->cf, Lc->inM) != ORC_OK) goto oom;
         h->nlev = l + 2;
+        if (gamma) {  /* non-Galerkin: the thinned operator replaces A_{l+1} */
+            double g = gamma[(l + 1) < ngamma ? (l + 1) : ngamma - 1];
+            Lc->gamma = g;
+            if (g > 0.0) {
+                uint8_t *keep = (uint8_t *)malloc((size_t)(Lc->A->nnz > 0 ? Lc->A->nnz : 1));
+                if (!keep) goto oom;
+                orc_csr *H = lump ? orc_sparsify_full(Lc->A, Lc->inM, g, theta, keep)
+                                  : orc_sparsify_diag(Lc->A, Lc->inM, g, keep);
+                free(keep);
+                if (!H) goto oom;
+                orc_csr_free(Lc->A);
+                Lc->A = H;
+                free(Lc->inM);   /* M belonged to the Galerkin pattern */
+                Lc->inM = NULL;
+            }
+        }
+    }
+    if (gamma) {
+        h->method = 2;
+        h->lump = lump;
     }
     for (int32_t l = 0; l < h->nlev; ++l) {
         orc_level *L = &h->lev[l];
         L->Ahat = L->A;
-        L->gamma = 0.0;
+        if (!gamma) L->gamma = 0.0;
         if (level_workspace(L) != ORC_OK) goto oom;
         orc_l1_diag(L->Ahat, L->d);
     }
@@ -964,7 +1020,7 @@ int orc_sparsify_method(orc_hier *h, const double *gamma, int32_t ngamma, int32_
 /* lump 0: the loop of Algorithm 3b (diagonal lumping); 1: Algorithm 3's own */
 /* loop (full lumping to strong neighbours). */
 int orc_sparsify_opts(orc_hier *h, const double *gamma, int32_t ngamma, int32_t method, int32_t lump) {
-    if (ngamma < 1 || gamma[0] != 0.0 || method < 0 || method > 1 || lump < 0 || lump > 1)
+    if (ngamma < 1 || gamma[0] != 0.0 || method < 0 || method > 1 || lump < 0 || lump > 1 || h->method == 2)
         return ORC_INVALID;
     for (int32_t l = 0; l < ngamma; ++l)
         if (!(gamma[l] >= 0.0) || !isfinite(gamma[l])) return ORC_INVALID;
@@ -987,6 +1043,7 @@ int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma) {
 /* Algorithm 5 re-sparsifies only the levels whose gamma changed; with the
  * Hybrid method their M comes from the current Ahat_{l-1}. */
 int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed) {
+    if (h->method == 2) return -ORC_INVALID;  /* non-Galerkin: nothing retained to reintroduce */
     double g[64];
     for (int32_t l = 0; l < h->nlev; ++l) g[l] = h->lev[l].gamma;
     int cnt = orc_gamma_schedule(g, h->nlev, s, gamma_min, changed);

@@ -9,9 +9,11 @@
  * "Reducing Parallel Communication in Algebraic Multigrid through
  * Sparsification" (arXiv:1512.04629):
  *   Algorithm 1 (amg_setup), Algorithm 2 (amg_solve, the V-cycle),
- *   Algorithm 3 (sparsify: minimal pattern M, drop test, symmetric N) with the
- *   diagonal-lumping loop of Algorithm 3b, Algorithm 4 (Sparse Galerkin),
- *   Algorithm 5 (adaptive_solve) and PCG (Section 5.5 / Section 6).
+ *   Algorithm 3 (sparsify: minimal pattern M, drop test, symmetric N) with its
+ *   own loop (full lumping to strong neighbours) and the diagonal-lumping loop
+ *   of Algorithm 3b, Algorithm 4 (Sparse and Hybrid Galerkin), Algorithm 1's
+ *   non-Galerkin option, Algorithm 5 (adaptive_solve), PCG (Section 5.5 /
+ *   Section 6) and restarted GMRES (Section 5.3).
  * Where the paper leaves a choice open (strength formula, PMIS details, direct
  * interpolation, stop rule, ell1-Jacobi, the garbled lines of Algorithms 4 and
  * 5) the reading taken is stated at the function that implements it.
@@ -74,6 +76,13 @@ int orc_gamma_schedule(double *gamma, int32_t nlev, int32_t s, double gamma_min,
 /* ---- hierarchy (Algorithms 1, 2, 4, 5) ---- */
 orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
                     uint64_t seed, int32_t *status);
+/* Algorithm 1 with the non-Galerkin sparsify inside the loop (the paper's
+ * comparator): gamma[l] thins the operator of level l as soon as it is formed
+ * (gamma[0] = 0); lump as orc_sparsify_opts.  Nothing Galerkin is retained:
+ * orc_sparsify* and orc_reintroduce refuse such a hierarchy. */
+orc_hier *orc_setup_nongalerkin(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
+                                uint64_t seed, const double *gamma, int32_t ngamma, int32_t lump,
+                                int32_t *status);
 int orc_sparsify(orc_hier *h, const double *gamma, int32_t ngamma);
 /* method 0: Sparse Galerkin (M from the Galerkin A_{l-1}); 1: Hybrid Galerkin
  * (M from the sparsified Ahat_{l-1}, levels processed in order). */

@@ -924,3 +924,79 @@ def test_rotated_aniso_q1_isotropic_is_q1_laplacian():
     want = np.full((3, 3), -1.0 / 3.0)
     want[1, 1] = 8.0 / 3.0
     np.testing.assert_allclose(st, want, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# non-Galerkin (Algorithm 1 with the in-loop sparsify)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lump", [0, 1])
+def test_nongalerkin_levels_built_from_sparsified_operators(lump):
+    """Level by level, from the oracle's own building blocks (each pinned
+    above): strength, PMIS and interpolation of the *sparsified* A_l, the
+    Galerkin product, M from A_l, then the dense sparsify reference."""
+    A = gen.poisson3d_7pt(10)
+    g = [0.0, 0.5, 1.0]
+    h = oracle.Hierarchy(A, max_size=20, nongalerkin=g, lump=lump)
+    assert h.num_levels >= 3
+    Al = A.to_scipy()
+    for l in range(h.num_levels - 1):
+        np.testing.assert_array_equal(h.matrix(l, "A").todense(), Al.toarray())
+        S = oracle.strength(Al)
+        cf = oracle.pmis(Al, S, seed=0, level=l)
+        np.testing.assert_array_equal(h.cf(l), cf)
+        Pm = oracle.direct_interp(Al, S, cf)
+        P = Pm.todense()
+        Ac = csr_from_dense(P.T @ Al.toarray() @ P)
+        Gal = h.matrix(l + 1, "A")
+        # M of the coarse operator from the current A_l (dense brute force
+        # over the stored patterns: edges are structural)
+        pa = pattern(Al).astype(int)
+        pp = pattern(Pm).astype(int)
+        ph = np.zeros_like(pp)
+        ph[np.where(cf == 1)[0], np.arange(P.shape[1])] = 1
+        Mset = ((ph.T @ pa @ pp) + (pp.T @ pa @ ph)) > 0
+        AP = oracle.spgemm(Al, Pm)
+        Ac_or = oracle.spgemm(oracle.transpose(Pm), AP).to_scipy()
+        rows = np.repeat(np.arange(Ac_or.shape[0]), np.diff(Ac_or.indptr))
+        inM = Mset[rows, Ac_or.indices].astype(np.uint8)
+        gam = g[min(l + 1, len(g) - 1)]
+        if lump:
+            Href, _ = _dense_full_lumping(Ac_or, inM, gam, 0.25)
+        else:
+            Href, _ = _dense_sparsify_reference(Ac_or, inM, gam)
+        scale = np.abs(Href).max()
+        np.testing.assert_allclose(Gal.todense(), Href, rtol=0, atol=1e-12 * scale)
+        assert Gal.nnz < Ac.nnz  # thinned, so not the Galerkin product any more
+        Al = Gal.to_scipy()
+
+
+def test_nongalerkin_gamma_zero_is_galerkin_and_refuses_alg5():
+    A = gen.poisson3d_7pt(12)
+    h0 = oracle.Hierarchy(A, max_size=20)
+    h1 = oracle.Hierarchy(A, max_size=20, nongalerkin=[0.0])
+    assert h0.num_levels == h1.num_levels
+    for l in range(h0.num_levels):
+        np.testing.assert_array_equal(h0.matrix(l, "A").val, h1.matrix(l, "A").val)
+    h2 = oracle.Hierarchy(A, max_size=20, nongalerkin=[0.0, 1.0])
+    with pytest.raises(RuntimeError):
+        h2.sparsify([0.0, 0.1])
+    with pytest.raises(RuntimeError):
+        h2.reintroduce(1)
+
+
+def test_nongalerkin_full_lumping_rescues_aggressive_dropping():
+    """The paper's motivating example (Section 2.1, Figures 1-2): gamma = 1
+    from the first coarse level on removes essential entries.  With diagonal
+    lumping PCG breaks down here; Algorithm 3's lumping to strong neighbours
+    keeps every operator's row sums and symmetry and converges."""
+    A = gen.poisson3d_7pt(16)
+    b = gen.rhs_uniform(A.n, 1)
+    hd = oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=0)
+    _, idg = hd.pcg(b)
+    hf = oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=1)
+    _, ifl = hf.pcg(b)
+    assert ifl.status == 0 and ifl.final_relres <= 1e-8
+    assert idg.status != 0 or idg.iterations > 3 * ifl.iterations
+    for l in range(1, hf.num_levels):
+        H = hf.matrix(l, "A").todense()
+        np.testing.assert_allclose(H, H.T, atol=1e-13 * np.abs(H).max())
