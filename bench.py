@@ -50,7 +50,8 @@ def parse():
                    help="c2 (default, the bench line): 3D 7-pt 128^3; c3: 27-pt 192^3 precision arms; "
                         "c4: lognormal FV 160^3 batched k in {1,8,32,64}; c5: serving stream; "
                         "lump: 3D 7-pt 128^3, diagonal vs full lumping, CG vs GMRES; "
-                        "aniso: rotated anisotropic Q1 2D 2048^2 (theta pi/8, eps 1e-3), GMRES arms")
+                        "aniso: rotated anisotropic Q1 2D 2048^2 (theta pi/8, eps 1e-3), GMRES arms "
+                        "(Galerkin, Sparse, Hybrid, non-Galerkin)")
     p.add_argument("--serve-seconds", type=float, default=20.0)
     p.add_argument("--lump", default="diag", choices=["diag", "strong"],
                    help="sparsify: diagonal lumping (Algorithm 3b, default) or full lumping to strong neighbours "
@@ -442,7 +443,11 @@ def _lumping_arms(args, A, arms, workload):
     out = {}
     for name, opts in arms:
         hs = []  # every timed hierarchy is kept until the timing ends (no teardown inside it)
-        ms_setup, _ = _events_ms(lambda: hs.append(amg.Hierarchy.setup(A_dev, **opts)))
+        try:
+            ms_setup, _ = _events_ms(lambda: hs.append(amg.Hierarchy.setup(A_dev, **opts)))
+        except amg.AmgError as e:  # e.g. a non-Galerkin operator losing its positive diagonal
+            out[name] = {"setup_status": e.status, "setup_error": str(e)}
+            continue
         del hs
         ht = amg.Hierarchy.setup(A_dev, setup_timing=1, **opts)
         phases = collect_setup_timing(ht, ht.num_levels)
@@ -476,12 +481,18 @@ def run_lump(args):
         for lump, ln in ((amg.LUMP_DIAG, "diag"), (amg.LUMP_STRONG, "full")):
             for kr, kn in ((amg.KRYLOV_CG, "cg"), (amg.KRYLOV_GMRES, "gmres")):
                 arms.append((f"{ln}_{kn}_gamma{g}", {"gamma": [0.0, g], "lump": lump, "krylov": kr}))
+    # the paper's comparator: non-Galerkin (thinned inside the setup loop), GMRES
+    for sched, sn in (([0.0, 0.1], "0.1"), ([0.0, 0.0, 1.0], "0-1"), ([0.0, 1.0], "1.0")):
+        for lump, ln in ((amg.LUMP_DIAG, "diag"), (amg.LUMP_STRONG, "full")):
+            arms.append((f"nongalerkin_{ln}_gmres_gamma{sn}", {"gamma": sched, "lump": lump,
+                                                              "method": amg.METHOD_NONGALERKIN,
+                                                              "krylov": amg.KRYLOV_GMRES}))
     _lumping_arms(args, A, arms, f"lump: 3D 7-point {args.grid}^3 (n={A.n}), Sparse Galerkin")
 
 
 def run_aniso(args):
     """Rotated anisotropic diffusion (Q1, theta = pi/8, eps = 1e-3) on a 2D
-    grid: Galerkin, Sparse and Hybrid Galerkin with diagonal and full
+    grid: Galerkin, Sparse, Hybrid and non-Galerkin with diagonal and full
     lumping, all under GMRES(30)."""
     import amg_inputs as gen
     import paper_1512_04629_gb300 as amg
@@ -491,7 +502,8 @@ def run_aniso(args):
     G = amg.KRYLOV_GMRES
     arms = [("galerkin", {"krylov": G})]
     for sched, sn in (([0.0, 0.1, 1.0], "0.1-1"), ([0.0, 1.0], "1")):
-        for method, mn in ((amg.METHOD_SPARSE, "sparse"), (amg.METHOD_HYBRID, "hybrid")):
+        for method, mn in ((amg.METHOD_SPARSE, "sparse"), (amg.METHOD_HYBRID, "hybrid"),
+                           (amg.METHOD_NONGALERKIN, "nongalerkin")):
             for lump, ln in ((amg.LUMP_DIAG, "diag"), (amg.LUMP_STRONG, "full")):
                 arms.append((f"{mn}_{ln}_gamma{sn}", {"gamma": sched, "method": method, "lump": lump,
                                                        "krylov": G}))

@@ -64,7 +64,16 @@ typedef struct {
     int64_t ncols;         /* 0 means ncols = n */
 } amg_csr;
 
-enum { AMG_METHOD_SPARSE = 0, AMG_METHOD_HYBRID = 1 };
+/* AMG_METHOD_SPARSE / AMG_METHOD_HYBRID: Algorithm 4 on a retained Galerkin
+ * hierarchy (minimal pattern M from the Galerkin, resp. the sparsified, level
+ * above).  AMG_METHOD_NONGALERKIN: Algorithm 1's optional step, the paper's
+ * comparator -- each coarse operator is thinned as soon as the Galerkin
+ * product forms it and replaces it for the rest of the setup; nothing
+ * Galerkin is retained, so amg_sparsify, amg_reintroduce, adaptive solves,
+ * amg_hierarchy_save and amg_hierarchy_assemble reject such a hierarchy /
+ * method (AMG_ERR_INVALID), and amg_level_stats reports the thinned operator
+ * as nnz_galerkin. */
+enum { AMG_METHOD_SPARSE = 0, AMG_METHOD_HYBRID = 1, AMG_METHOD_NONGALERKIN = 2 };
 /* How sparsify treats a dropped entry: AMG_LUMP_DIAG adds it to the diagonal
  * of its row (Algorithm 3b; keeps an SPD diagonally dominant operator SPD,
  * Theorem 1); AMG_LUMP_STRONG spreads it symmetrically over the strong
@@ -88,7 +97,7 @@ typedef struct {
     int max_size;        /* stop coarsening at n <= max_size, default 100 */
     int max_levels;      /* default 25 */
     uint64_t seed;       /* PMIS random weights, default 0 */
-    int method;          /* AMG_METHOD_SPARSE (default) or AMG_METHOD_HYBRID */
+    int method;          /* AMG_METHOD_SPARSE (default), _HYBRID or _NONGALERKIN */
     int precision;       /* AMG_PREC_*: storage/arithmetic of the V-cycle */
     int k_check;         /* Algorithm 5: PCG steps between checks, default 3 */
     int s_levels;        /* Algorithm 5: levels updated per step, default 1 */

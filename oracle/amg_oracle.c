@@ -854,6 +854,9 @@ orc_hier *orc_setup(const orc_csr *A0, double theta, int32_t max_size, int32_t m
 /* current (already sparsified) A_l; S of full lumping is the strength of  */
 /* the coarse operator being thinned.  No Galerkin operator is retained,   */
 /* so Algorithm 5 does not apply (orc_sparsify / orc_reintroduce refuse).  */
+/* A thinned operator with a non-positive diagonal entry ends the setup    */
+/* with ORC_BREAKDOWN (lumping can push a diagonal to or below zero when   */
+/* the coarse operator is not diagonally dominant).                        */
 orc_hier *orc_setup_nongalerkin(const orc_csr *A0, double theta, int32_t max_size, int32_t max_levels,
                                 uint64_t seed, const double *gamma, int32_t ngamma, int32_t lump,
                                 int32_t *status) {
@@ -929,6 +932,16 @@ static orc_hier *setup_core(const orc_csr *A0, double theta, int32_t max_size, i
                 Lc->A = H;
                 free(Lc->inM);   /* M belonged to the Galerkin pattern */
                 Lc->inM = NULL;
+                /* a thinned operator whose diagonal is no longer positive   */
+                /* cannot be coarsened or relaxed: the setup breaks down      */
+                for (int32_t i = 0; i < H->nrows; ++i) {
+                    int32_t pd = find_entry(H, i, i);
+                    if (pd < 0 || !(H->val[pd] > 0.0)) {
+                        *status = ORC_BREAKDOWN;
+                        orc_free(h);
+                        return NULL;
+                    }
+                }
             }
         }
     }

@@ -4,8 +4,9 @@ The computation lives in libamg.so (CUDA, sm_103a) behind the C ABI of
 include/amg.h; this package is its ctypes binding and build script.
 """
 from .amg import (  # noqa: F401
+    OK, ERR_INVALID, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, BREAKDOWN, TIMEOUT, REJECTED,
     AmgError, Hierarchy, Matrix, Server, SolveInfo, default_options, device_bytes, kernel_launches, lib,
-    METHOD_SPARSE, METHOD_HYBRID, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,
+    METHOD_SPARSE, METHOD_HYBRID, METHOD_NONGALERKIN, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,
     PREC_FP64, PREC_FP32, PREC_FP32_BF16,
     SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_NAMES,
     K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC,

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libamg.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, BREAKDOWN, TIMEOUT, REJECTED = range(9)
-METHOD_SPARSE, METHOD_HYBRID = 0, 1
+METHOD_SPARSE, METHOD_HYBRID, METHOD_NONGALERKIN = 0, 1, 2
 LUMP_DIAG, LUMP_STRONG = 0, 1
 KRYLOV_CG, KRYLOV_GMRES = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2

@@ -93,7 +93,8 @@ void check_options(const amg_options &o) {
     require(std::isfinite(o.theta) && o.theta >= 0.0 && o.theta <= 1.0, "theta must be in [0, 1]");
     require(o.max_size >= 1, "max_size must be >= 1");
     require(o.max_levels >= 1 && o.max_levels <= kMaxLevels, "max_levels must be in [1, 64]");
-    require(o.method == AMG_METHOD_SPARSE || o.method == AMG_METHOD_HYBRID, "unknown method");
+    require(o.method == AMG_METHOD_SPARSE || o.method == AMG_METHOD_HYBRID || o.method == AMG_METHOD_NONGALERKIN,
+            "unknown method");
     require(o.precision >= AMG_PREC_FP64 && o.precision <= AMG_PREC_FP32_BF16, "unknown precision");
     require(o.k_check >= 1 && o.s_levels >= 1, "k_check and s_levels must be >= 1");
     require(o.gamma_min >= 0.0 && std::isfinite(o.rho_max), "bad gamma_min / rho_max");
@@ -173,7 +174,7 @@ amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_
         h.timing = o.setup_timing != 0;
         h.lev.push_back(std::make_unique<Level>());
         upload_csr(A, h.lev[0]->A, s);
-        build_galerkin(h, h.lev[0]->A, s);
+        build_galerkin(h, h.lev[0]->A, s, gamma, n_gamma);
         finish_setup(h, gamma, n_gamma, s);
         *out = H.release();
         return AMG_OK;
@@ -191,6 +192,8 @@ amg_status amg_hierarchy_assemble(int levels, const amg_csr *A, const amg_csr *P
         amg_options o;
         if (opt) o = *opt; else amg_options_default(&o);
         check_options(o);
+        require(o.method != AMG_METHOD_NONGALERKIN,
+                "non-Galerkin coarse operators are formed during the setup; assemble takes Galerkin levels");
         check_gammas(gamma, n_gamma);
         cudaStream_t s = as_stream(stream);
         AllocOn alloc_scope(s);
@@ -227,6 +230,7 @@ amg_status amg_sparsify(amg_hierarchy *H, const double *gamma, int n_gamma) {
         require(H != nullptr, "hierarchy is NULL");
         check_gammas(gamma, n_gamma);
         Hierarchy &h = H->h;
+        require(h.opt.method != AMG_METHOD_NONGALERKIN, "a non-Galerkin hierarchy retains no Galerkin operator");
         cudaStream_t s = nullptr;
         AllocOn alloc_scope(s);
         apply_gammas(h, gamma, n_gamma, s);
@@ -241,6 +245,7 @@ amg_status amg_reintroduce(amg_hierarchy *H, int s_levels, int *changed) {
     return guarded([&] {
         require(H != nullptr, "hierarchy is NULL");
         require(s_levels >= 1, "s_levels must be >= 1");
+        require(H->h.opt.method != AMG_METHOD_NONGALERKIN, "a non-Galerkin hierarchy retains no Galerkin operator");
         AllocOn alloc_scope(nullptr);
         int c = reintroduce(H->h, s_levels, nullptr);
         if (changed) *changed = c;
@@ -259,6 +264,8 @@ amg_status amg_solve(amg_hierarchy *H, const double *b, double *x, double tol, i
         require(std::isfinite(tol) && tol > 0.0, "tol must be > 0");
         require(max_it >= 1, "max_it must be >= 1");
         Hierarchy &h = H->h;
+        require(!adaptive || h.opt.method != AMG_METHOD_NONGALERKIN,
+                "adaptive solves reintroduce from retained Galerkin operators; a non-Galerkin hierarchy has none");
         cudaStream_t s = as_stream(stream);
         AllocOn alloc_scope(s);
         ensure_workspace(h, s);
@@ -432,6 +439,8 @@ amg_status amg_hierarchy_save(const amg_hierarchy *H, const char *path) {
     return guarded([&] {
         require(H != nullptr && path != nullptr, "NULL argument");
         const Hierarchy &h = H->h;
+        require(h.opt.method != AMG_METHOD_NONGALERKIN,
+                "a non-Galerkin hierarchy retains no Galerkin operator to save (rebuild it from A_0)");
         std::ofstream f(path, std::ios::binary);
         require((bool)f, std::string("cannot open ") + path);
         auto put = [&](const void *p, size_t n) { f.write(reinterpret_cast<const char *>(p), (std::streamsize)n); };

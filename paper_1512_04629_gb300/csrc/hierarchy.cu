@@ -85,9 +85,35 @@ static void init_level_maps(Level &V, cudaStream_t s) {
     V.keep.alloc(V.A.nnz + kPad);
 }
 
-void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
+// Non-Galerkin step of Algorithm 1: the coarse operator just formed is
+// thinned and replaces the Galerkin product (its maps are rebuilt, M and the
+// Galerkin values are dropped).
+static void nongalerkin_thin(Hierarchy &h, Level &C, double g, cudaStream_t s) {
+    C.gamma = g;
+    if (g == 0.0) return;
+    TmpBuf S;
+    if (h.opt.lump == AMG_LUMP_STRONG) {
+        S.alloc(C.A.nnz + kPad, s);
+        setup::strength(C.A, h.opt.theta, S.as<uint8_t>(), s);
+    }
+    DevCSR H;
+    setup::sparsify(C.A, C.inM.as<uint8_t>(), C.tpos.as<int32_t>(), C.diagpos.as<int32_t>(), g,
+                    C.keep.as<uint8_t>(), H, s, S.as<uint8_t>());
+    C.A = std::move(H);
+    C.inM.release();
+    try {
+        init_level_maps(C, s);  // validates the thinned operator (diagonal positive)
+    } catch (const Error &e) {
+        if (e.status != AMG_ERR_INVALID) throw;
+        throw Error(AMG_BREAKDOWN, "non-Galerkin: a thinned coarse operator has a non-positive diagonal entry "
+                                   "(lower gamma on that level, or use full lumping)");
+    }
+}
+
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const double *gamma, int n_gamma) {
     (void)A0in;
     const amg_options &o = h.opt;
+    const bool nongal = o.method == AMG_METHOD_NONGALERKIN;
     for (int l = 0;; ++l) {
         Level &V = *h.lev[l];
         if (l == 0) timed(h, 12, 0, 0.0, s, [&] { init_level_maps(V, s); });
@@ -128,6 +154,10 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s) {
             C->inM.alloc(C->A.nnz + kPad);
             setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
         });
+        if (nongal) {
+            const double g = (n_gamma > 0 && gamma) ? gamma[std::min(l + 1, n_gamma - 1)] : 0.0;
+            timed(h, 13, l + 1, 0.0, s, [&] { nongalerkin_thin(h, *C, g, s); });
+        }
         h.lev.push_back(std::move(C));
     }
 }
@@ -208,6 +238,15 @@ void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
 }
 
 void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s) {
+    if (h.opt.method == AMG_METHOD_NONGALERKIN) {  // thinned during the setup: every level is final
+        for (int l = 0; l < h.nlev(); ++l) {
+            Level &V = *h.lev[l];
+            V.H = DevCSR();
+            V.h_alias = true;
+            AMG_CUDA(cudaMemsetAsync(V.keep.ptr, 1, V.A.nnz, s));
+        }
+        return;
+    }
     for (int l = 0; l < h.nlev(); ++l) {
         double g = 0.0;
         if (l > 0 && n_gamma > 0 && gamma) g = gamma[std::min(l, n_gamma - 1)];

@@ -216,7 +216,10 @@ template <typename XT> inline const XT *dinv_of(const Level &V) {
 }
 
 // drivers (hierarchy.cu)
-void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s);
+// Algorithm 1; with method AMG_METHOD_NONGALERKIN each new coarse operator is
+// thinned (gamma convention of amg_setup) before it is coarsened further.
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const double *gamma = nullptr,
+                    int n_gamma = 0);
 void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &P,
                      const std::vector<std::vector<int8_t>> &cf,
                      const std::vector<std::vector<uint8_t>> &inM, cudaStream_t s);

@@ -222,3 +222,59 @@ def test_full_size_full_lumping_levels_match_oracle(amg):
     for l in range(1, h.num_levels):
         np.testing.assert_array_equal(h.level_array(l, "keep"), ref.keep(l))
         np.testing.assert_array_equal(h.export(l, "Ahat").val, ref.matrix(l, "Ahat").val)
+
+
+# ---------------------------------------------------------------------------
+# non-Galerkin (Algorithm 1 with the in-loop sparsify)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("lump", [0, 1])
+@pytest.mark.parametrize("case,gamma", [("3d7_20", [0.0, 0.5, 1.0]), ("fv7_15", [0.0, 0.1]),
+                                        ("3d27_11", [0.0, 0.0, 1.0]), ("2d5_64", [0.0, 1.0])])
+def test_nongalerkin_matches_oracle(amg, case, gamma, lump):
+    """Every level -- operators, C/F splits, P -- bit-identical: the thinned
+    operator feeds the next level's strength, PMIS, interpolation and RAP."""
+    A = CASES[case]()
+    ref = oracle.Hierarchy(A, nongalerkin=gamma, lump=lump)
+    h = amg.Hierarchy.setup(A, gamma=gamma, method=amg.METHOD_NONGALERKIN, lump=lump)
+    assert h.num_levels == ref.num_levels
+    for l in range(h.num_levels):
+        _same_csr(h.export(l, "A"), ref.matrix(l, "A"), what=f"A_{l}")
+        np.testing.assert_array_equal(h.export(l, "A").val, ref.matrix(l, "A").val)
+        _same_csr(h.export(l, "Ahat"), ref.matrix(l, "A"), what=f"Ahat_{l}")
+        if l + 1 < h.num_levels:
+            np.testing.assert_array_equal(h.level_array(l, "cf"), ref.cf(l), err_msg=f"cf_{l}")
+            _same_csr(h.export(l, "P"), ref.matrix(l, "P"), what=f"P_{l}")
+        np.testing.assert_allclose(h.level_array(l, "l1"), ref.l1(l), rtol=1e-14)
+    b = gen.rhs_uniform(A.n, 1)
+    xr, ir = ref.gmres(b, tol=1e-8)
+    h2 = amg.Hierarchy.setup(A, gamma=gamma, method=amg.METHOD_NONGALERKIN, lump=lump, krylov=amg.KRYLOV_GMRES)
+    x, info = h2.solve(b, tol=1e-8)
+    assert ir.status == 0 and info.status == 0 and info.final_relres <= 1e-8
+    assert abs(info.iterations - ir.iterations) <= 1, (info.iterations, ir.iterations)
+
+
+def test_nongalerkin_breakdown_matches_oracle(amg):
+    """12^3 Poisson, gamma 1 from level 1, diagonal lumping: level 2's thinned
+    operator has a negative diagonal entry; both sides stop the setup with a
+    breakdown.  Full lumping of the same case sets up and solves."""
+    A = gen.poisson3d_7pt(12)
+    with pytest.raises(RuntimeError, match="status 6"):
+        oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=0)
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.setup(A, gamma=[0.0, 1.0], method=amg.METHOD_NONGALERKIN)
+    assert e.value.status == amg.BREAKDOWN
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 1.0], method=amg.METHOD_NONGALERKIN, lump=amg.LUMP_STRONG,
+                            krylov=amg.KRYLOV_GMRES)
+    _, info = h.solve(gen.rhs_uniform(A.n, 0))
+    assert info.status == 0
+
+
+def test_nongalerkin_refuses_retained_operator_calls(amg, tmp_path):
+    A = gen.poisson3d_7pt(12)
+    h = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], method=amg.METHOD_NONGALERKIN)
+    for call in (lambda: h.sparsify([0.0, 0.1]), lambda: h.reintroduce(1),
+                 lambda: h.solve(gen.rhs_uniform(A.n, 0), adaptive=True),
+                 lambda: h.save(str(tmp_path / "h.bin"))):
+        with pytest.raises(amg.AmgError) as e:
+            call()
+        assert e.value.status == 1

@@ -977,26 +977,48 @@ def test_nongalerkin_gamma_zero_is_galerkin_and_refuses_alg5():
     assert h0.num_levels == h1.num_levels
     for l in range(h0.num_levels):
         np.testing.assert_array_equal(h0.matrix(l, "A").val, h1.matrix(l, "A").val)
-    h2 = oracle.Hierarchy(A, max_size=20, nongalerkin=[0.0, 1.0])
+    h2 = oracle.Hierarchy(A, max_size=20, nongalerkin=[0.0, 1.0], lump=1)
     with pytest.raises(RuntimeError):
         h2.sparsify([0.0, 0.1])
     with pytest.raises(RuntimeError):
         h2.reintroduce(1)
 
 
+def test_nongalerkin_negative_diagonal_is_a_breakdown():
+    """12^3 Poisson, gamma 1 from level 1 with diagonal lumping: rebuilding
+    level 2 from the pinned building blocks (strength, PMIS with level index
+    1, direct interpolation, Galerkin product, M, dense-pinned 3b sparsify)
+    on the thinned level 1 gives a non-positive diagonal entry, and the
+    non-Galerkin setup reports that as a breakdown."""
+    A = gen.poisson3d_7pt(12)
+    with pytest.raises(RuntimeError, match="status 6"):
+        oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=0)
+    h1 = oracle.Hierarchy(A, max_levels=2, nongalerkin=[0.0, 1.0], lump=0)
+    A1 = h1.matrix(1, "A")
+    assert (A1.to_scipy().diagonal() > 0).all()
+    S = oracle.strength(A1)
+    cf = oracle.pmis(A1, S, seed=0, level=1)
+    P = oracle.direct_interp(A1, S, cf)
+    AP = oracle.spgemm(A1, P)
+    Ac = oracle.spgemm(oracle.transpose(P), AP)
+    inM = oracle.minimal_pattern(Ac, AP, cf)
+    H, _ = oracle.sparsify_diag(Ac, inM, 1.0)
+    assert H.to_scipy().diagonal().min() <= 0.0
+
+
 def test_nongalerkin_full_lumping_rescues_aggressive_dropping():
     """The paper's motivating example (Section 2.1, Figures 1-2): gamma = 1
     from the first coarse level on removes essential entries.  With diagonal
-    lumping PCG breaks down here; Algorithm 3's lumping to strong neighbours
-    keeps every operator's row sums and symmetry and converges."""
+    lumping the non-Galerkin setup breaks down here (a thinned diagonal
+    crosses zero); Algorithm 3's lumping to strong neighbours keeps every
+    operator's row sums and symmetry and converges."""
     A = gen.poisson3d_7pt(16)
     b = gen.rhs_uniform(A.n, 1)
-    hd = oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=0)
-    _, idg = hd.pcg(b)
+    with pytest.raises(RuntimeError, match="status 6"):  # a thinned diagonal crosses zero
+        oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=0)
     hf = oracle.Hierarchy(A, nongalerkin=[0.0, 1.0], lump=1)
     _, ifl = hf.pcg(b)
     assert ifl.status == 0 and ifl.final_relres <= 1e-8
-    assert idg.status != 0 or idg.iterations > 3 * ifl.iterations
     for l in range(1, hf.num_levels):
         H = hf.matrix(l, "A").todense()
         np.testing.assert_allclose(H, H.T, atol=1e-13 * np.abs(H).max())
