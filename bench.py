@@ -157,7 +157,7 @@ def fp64_ops_per_launch(kind, level, n, nnz, precision):
     if kind == "relax_pre_residual":
         return nnz + n                      # s = A x; r = b - s
     if kind == "relax_post":
-        return nnz + (4 if level == 0 else 2) * n   # x + d (b - s); level 0 adds r.z and z.q
+        return nnz + (3 if level == 0 else 2) * n   # x + d (b - s); level 0 adds r.z (plain CG: no z.q)
     if kind == "pcg_Ap_dot":
         return nnz + n                      # q = A p; p.q
     if kind == "pcg_vector":

@@ -463,14 +463,18 @@ resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restric
     block_partials<1>(part, red);
 }
 
-// level-0 post-smoothing z = x + d (b - A x) with r.z and z.q (r = b)
-template <int T>
+// level-0 post-smoothing z = x + d (b - A x) with r.z (r = b) and, for
+// flexible CG only (ZQ), z.q -- plain CG's beta needs no z.q, so the FP64
+// cycle reads no q and issues one FMA less per row
+template <int T, bool ZQ>
 __global__ void __launch_bounds__(kThreads)
 post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                    double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
-    double part[2] = {0.0, 0.0};
+    double part[ZQ ? 2 : 1];
+#pragma unroll
+    for (int k = 0; k < (ZQ ? 2 : 1); ++k) part[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * kThreads;
     const int64_t gend = (int64_t)((n + (kThreads / T) - 1) / (kThreads / T)) * (kThreads / T) * T;
     for (int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x; g < gend; g += stride) {
@@ -484,20 +488,22 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
             double zi = x[i] + dinv[i] * (bi - s);
             z[i] = zi;
             part[0] += bi * zi;
-            part[1] += zi * q[i];
+            if (ZQ) part[ZQ ? 1 : 0] += zi * q[i];
         }
     }
-    block_partials<2>(part, red);
+    block_partials<ZQ ? 2 : 1>(part, red);
 }
 
-template <bool D16>
+template <bool D16, bool ZQ>
 __global__ void __launch_bounds__(kThreads)
 post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
                     const int32_t *__restrict__ sw, SellIdx ix, const double *__restrict__ sv,
                     const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                     double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
-    double part[2] = {0.0, 0.0};
+    double part[ZQ ? 2 : 1];
+#pragma unroll
+    for (int k = 0; k < (ZQ ? 2 : 1); ++k) part[k] = 0.0;
     const int lane = threadIdx.x & 31;
     const int32_t nsl = (n + 31) >> 5, nwarps = (int32_t)((gridDim.x * kThreads) >> 5);
     for (int32_t sl = (int32_t)((blockIdx.x * kThreads + threadIdx.x) >> 5); sl < nsl; sl += nwarps) {
@@ -509,9 +515,9 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
         double zi = x[i] + dinv[i] * (bi - s);
         z[i] = zi;
         part[0] += bi * zi;
-        part[1] += zi * q[i];
+        if (ZQ) part[ZQ ? 1 : 0] += zi * q[i];
     }
-    block_partials<2>(part, red);
+    block_partials<ZQ ? 2 : 1>(part, red);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -743,33 +749,41 @@ void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, doubl
     AMG_CHECK_LAUNCH();
 }
 
-bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, const double *dinv, double *z,
-                    const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
-    int32_t n = A.nrows;
-    if (n == 0) return false;
+template <bool ZQ>
+static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, const double *b, const double *dinv,
+                                  double *z, const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    const int32_t n = A.nrows;
+    constexpr int NV = ZQ ? 2 : 1;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         int blocks = reduce_blocks(n);
         const SellIdx ix{A.sci, A.sd};
         if (A.sd)
-            { post_rz_sell_kernel<true><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+            { post_rz_sell_kernel<true, ZQ><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
         else
-            { post_rz_sell_kernel<false><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
-        launch_finish<2, kFinRz>(blocks, red, sc, s);
+            { post_rz_sell_kernel<false, ZQ><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+        launch_finish<NV, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
-        return true;
+        return;
     }
     int T = threads_per_row(A.variant);
     int blocks = reduce_blocks((int64_t)n * T);
     switch (T) {
-        case 1: { post_rz_csr_kernel<1><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 2: { post_rz_csr_kernel<2><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 4: { post_rz_csr_kernel<4><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 8: { post_rz_csr_kernel<8><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 16: { post_rz_csr_kernel<16><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        default: { post_rz_csr_kernel<32><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 1: { post_rz_csr_kernel<1, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 2: { post_rz_csr_kernel<2, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 4: { post_rz_csr_kernel<4, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 8: { post_rz_csr_kernel<8, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 16: { post_rz_csr_kernel<16, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        default: { post_rz_csr_kernel<32, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
     }
-    launch_finish<2, kFinRz>(blocks, red, sc, s);
+    launch_finish<NV, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
+}
+
+bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, const double *dinv, double *z,
+                    const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    if (A.nrows == 0) return false;
+    if (q) post_smooth_rz_launch<true>(A, x, b, dinv, z, q, sc, red, s);
+    else post_smooth_rz_launch<false>(A, x, b, dinv, z, q, sc, red, s);
     return true;
 }
 

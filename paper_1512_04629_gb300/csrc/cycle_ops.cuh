@@ -75,9 +75,9 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
                    double *x0, cudaStream_t s);
-// level-0 post-smoothing that also forms rho = r.z and z.q (and beta): z is
-// the output, r = b the cycle input.  Returns false (nothing launched) when
-// the grid would exceed the reduction capacity.
+// level-0 post-smoothing that also forms rho = r.z and, when q is given
+// (flexible CG), z.q, and beta: z is the output, r = b the cycle input.
+// Returns false (nothing launched) for an empty level.
 bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, const double *dinv, double *z,
                     const double *q, PcgScalars *sc, Reduce red, cudaStream_t s);
 // z = (double) z32 and rho = r.z, z.q (FP32 cycles)

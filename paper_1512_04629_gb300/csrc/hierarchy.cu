@@ -745,8 +745,10 @@ static bool vcycle_impl(Hierarchy &h, const XT *b0, XT *z0, cudaStream_t s, cons
         const XT *b = l == 0 ? b0 : V.b.as<XT>();
         if constexpr (sizeof(XT) == 8) {
             if (l == 0 && ctl.fuse_rz && V.vbytes == 8) {
-                timed(h, 3, 0, bytes_post(V.n(), V.op().nnz, V.vbytes, xb) + 8.0 * V.n(), s, [&] {
-                    fused = cyc::post_smooth_rz(op_mat<double>(V), V.x.as<double>(), b, dinv_of<double>(V), z0, ctl.q,
+                // z.q only for flexible CG (plain CG's beta is r.z / rho)
+                const double *q = h.opt.precision != AMG_PREC_FP64 ? ctl.q : nullptr;
+                timed(h, 3, 0, bytes_post(V.n(), V.op().nnz, V.vbytes, xb) + (q ? 8.0 * V.n() : 0.0), s, [&] {
+                    fused = cyc::post_smooth_rz(op_mat<double>(V), V.x.as<double>(), b, dinv_of<double>(V), z0, q,
                                                 h.dscal(), h.reduce(), s);
                 });
                 if (fused) continue;
