@@ -95,13 +95,47 @@ __device__ __forceinline__ int32_t sell_col(const SellIdx &ix, int32_t p, int32_
     else return __ldg(ix.col + p);
 }
 
-// sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32)
-template <typename VT, typename XT, bool D16, class G>
+// a slice of width W (W <= 4): every value and column load first, then every
+// gather, then the products in k order -- short rows (interpolation P,
+// coarse operators) otherwise pay a load -> gather round trip per entry
+template <int W, typename VT, typename XT, bool D16, class G>
+__device__ __forceinline__ XT sell_short_sum(int32_t off, int32_t row, const SellIdx &ix,
+                                             const VT *__restrict__ sv, G gather) {
+    VT v[W];
+    int32_t c[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        v[k] = __ldg(sv + off + k * 32);
+        c[k] = sell_col<D16>(ix, off + k * 32, row);
+    }
+    XT g[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) g[k] = gather(c[k]);
+    XT acc = XT(0);
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc += cvt<VT, XT>(v[k]) * g[k];
+    return acc;
+}
+
+// sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32),
+// entries in k order whatever the path; SHORT: slices of width <= 4 take the
+// load-everything-first path (the transfer operators P and R, whose rows are
+// short; the relaxation kernels measured slower with it)
+template <typename VT, typename XT, bool D16, bool SHORT = false, class G>
 __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32_t *__restrict__ soff,
                                            const int32_t *__restrict__ sw, const SellIdx &ix,
                                            const VT *__restrict__ sv, G gather) {
     int32_t s = pos >> 5, lane = pos & 31;
     int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
+    if constexpr (SHORT) {
+        switch (w) {  // uniform over the warp (one slice)
+            case 1: return sell_short_sum<1, VT, XT, D16>(off, row, ix, sv, gather);
+            case 2: return sell_short_sum<2, VT, XT, D16>(off, row, ix, sv, gather);
+            case 3: return sell_short_sum<3, VT, XT, D16>(off, row, ix, sv, gather);
+            case 4: return sell_short_sum<4, VT, XT, D16>(off, row, ix, sv, gather);
+            default: break;
+        }
+    }
     XT acc = XT(0);
 #pragma unroll 4
     for (int32_t k = 0; k < w; ++k) {
@@ -153,9 +187,15 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
     const int32_t i = perm ? __ldg(perm + pos) : pos;
+    // transfers (P, R: short rows, latency-bound): the row's own operand is
+    // loaded before the row sum so its latency overlaps the gathers
+    constexpr bool kTransfer = OP == kSpmvAdd || OP == kSpmvScale;
+    XT own = XT(0);
+    if (OP == kSpmvAdd) own = o1[i];
+    if (OP == kSpmvScale) own = dinv[i];
     XT s;
     if (OP == kPre) s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
+    else s = sell_row_sum<VT, XT, D16, kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -166,11 +206,11 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         o1[i] = s;
     } else if (OP == kSpmvScale) {
         o1[i] = s;
-        o2[i] = s * dinv[i];
+        o2[i] = s * own;
     } else if (OP == kResX) {
         o2[i] = b[i] - s;
     } else {
-        o1[i] += s;
+        o1[i] = own + s;
     }
 }
 
