@@ -95,7 +95,7 @@ __device__ __forceinline__ int32_t sell_col(const SellIdx &ix, int32_t p, int32_
     else return __ldg(ix.col + p);
 }
 
-// a slice of width W (W <= 4): every value and column load first, then every
+// a slice of width W (W <= 8): every value and column load first, then every
 // gather, then the products in k order -- short rows (interpolation P,
 // coarse operators) otherwise pay a load -> gather round trip per entry
 template <int W, typename VT, typename XT, bool D16, class G>
@@ -118,7 +118,7 @@ __device__ __forceinline__ XT sell_short_sum(int32_t off, int32_t row, const Sel
 }
 
 // sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32),
-// entries in k order whatever the path; SHORT: slices of width <= 4 take the
+// entries in k order whatever the path; SHORT: slices of width <= 8 take the
 // load-everything-first path (the transfer operators P and R, whose rows are
 // short; the relaxation kernels measured slower with it)
 template <typename VT, typename XT, bool D16, bool SHORT = false, class G>
@@ -133,6 +133,10 @@ __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32
             case 2: return sell_short_sum<2, VT, XT, D16>(off, row, ix, sv, gather);
             case 3: return sell_short_sum<3, VT, XT, D16>(off, row, ix, sv, gather);
             case 4: return sell_short_sum<4, VT, XT, D16>(off, row, ix, sv, gather);
+            case 5: return sell_short_sum<5, VT, XT, D16>(off, row, ix, sv, gather);
+            case 6: return sell_short_sum<6, VT, XT, D16>(off, row, ix, sv, gather);
+            case 7: return sell_short_sum<7, VT, XT, D16>(off, row, ix, sv, gather);
+            case 8: return sell_short_sum<8, VT, XT, D16>(off, row, ix, sv, gather);
             default: break;
         }
     }
