@@ -95,6 +95,8 @@ __device__ __forceinline__ int32_t sell_col(const SellIdx &ix, int32_t p, int32_
     else return __ldg(ix.col + p);
 }
 
+constexpr int kShortMax = 8;  // widest slice of the load-first path
+
 // a slice of width W (W <= 8): every value and column load first, then every
 // gather, then the products in k order -- short rows (interpolation P,
 // coarse operators) otherwise pay a load -> gather round trip per entry
@@ -183,7 +185,7 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
     }
 }
 
-template <typename VT, typename XT, int OP, bool D16>
+template <typename VT, typename XT, int OP, bool D16, bool SHORT>
 __global__ void __launch_bounds__(kThreads)
 sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
@@ -198,8 +200,8 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     if (OP == kSpmvAdd) own = o1[i];
     if (OP == kSpmvScale) own = dinv[i];
     XT s;
-    if (OP == kPre) s = sell_row_sum<VT, XT, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT, D16, kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) s = sell_row_sum<VT, XT, D16, SHORT || kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT, D16, SHORT || kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -224,10 +226,18 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
     if (n == 0) return;
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         const SellIdx ix{A.sci, A.sd};
-        if (A.sd)
-            { sell_op_kernel<VT, XT, OP, true><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        // the load-first path for operators whose rows all fit it (measured:
+        // faster at level 0, slower on the longer, irregular coarse rows)
+        const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
+        const int g = div_up(n, kThreads);
+        if (A.sd && sh)
+            { sell_op_kernel<VT, XT, OP, true, true><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        else if (A.sd)
+            { sell_op_kernel<VT, XT, OP, true, false><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        else if (sh)
+            { sell_op_kernel<VT, XT, OP, false, true><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
         else
-            { sell_op_kernel<VT, XT, OP, false><<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            { sell_op_kernel<VT, XT, OP, false, false><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
     } else {
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);
@@ -407,7 +417,7 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
 
 // q = A p (SELL-32, one thread per row) and p . q; each warp walks slices
 // with a stride of the grid's warp count
-template <bool D16>
+template <bool D16, bool SHORT>
 __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                SellIdx ix, const double *__restrict__ sv, const double *__restrict__ p,
@@ -420,7 +430,7 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         const int32_t pos = sl * 32 + lane;
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
-        double s = sell_row_sum<double, double, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
+        double s = sell_row_sum<double, double, D16, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
         q[i] = s;
         part[0] += p[i] * s;
     }
@@ -697,13 +707,18 @@ __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     }
 }
 
+// out[0] = max |column - row|, out[1] = max stored entries of a row
 __global__ void max_col_offset_kernel(int32_t n, const int32_t *rp, const int32_t *ci, int *out) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    int m = 0;
-    if (i < n)
+    int m = 0, len = 0;
+    if (i < n) {
         for (int32_t p = rp[i]; p < rp[i + 1]; ++p) m = max(m, abs(ci[p] - i));
+        len = rp[i + 1] - rp[i];
+    }
     m = __reduce_max_sync(0xffffffffu, (unsigned)m);
+    len = __reduce_max_sync(0xffffffffu, (unsigned)len);
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+    if ((threadIdx.x & 31) == 0 && len) atomicMax(out + 1, len);
 }
 
 }  // namespace
@@ -765,10 +780,15 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
         int blocks = reduce_blocks(A.nrows);
         const SellIdx ix{A.sci, A.sd};
-        if (A.sd)
-            { ap_sell_kernel<true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
+        if (A.sd && sh)
+            { ap_sell_kernel<true, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        else if (A.sd)
+            { ap_sell_kernel<true, false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        else if (sh)
+            { ap_sell_kernel<false, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
         else
-            { ap_sell_kernel<false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+            { ap_sell_kernel<false, false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -903,13 +923,18 @@ void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, con
     AMG_CHECK_LAUNCH();
 }
 
-int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s) {
+int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s, int32_t *max_row) {
+    if (max_row) *max_row = 0;
     if (n == 0) return 0;
-    TmpBuf out(sizeof(int), s);
-    AMG_CUDA(cudaMemsetAsync(out.ptr, 0, sizeof(int), s));
+    TmpBuf out(sizeof(int) * 2, s);
+    AMG_CUDA(cudaMemsetAsync(out.ptr, 0, sizeof(int) * 2, s));
     { max_col_offset_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, rp, ci, out.as<int>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    return read_scalar(out.as<int>(), s);
+    int h[2];
+    AMG_CUDA(cudaMemcpyAsync(h, out.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (max_row) *max_row = h[1];
+    return h[0];
 }
 
 // explicit instantiations

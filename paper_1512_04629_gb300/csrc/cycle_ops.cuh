@@ -17,6 +17,7 @@ template <typename VT> struct CycMat {
     const int16_t *sd = nullptr;    // SELL column as int16 offset from the row (replaces sci when set)
     const int32_t *perm = nullptr;  // SELL position -> row (null: identity)
     const VT *sv = nullptr;
+    int32_t max_row = 0;  // most stored entries of a row (0: not known)
     int variant = AMG_SPMV_CSR4;
 };
 
@@ -105,8 +106,9 @@ int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, 
 template <typename VT>
 void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
                const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd = nullptr);
-// max over stored entries of |column - row| (square operators), for the int16 SELL offsets
-int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s);
+// max over stored entries of |column - row| (square operators), for the int16 SELL offsets;
+// *max_row (if given) receives the longest row
+int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s, int32_t *max_row = nullptr);
 
 }  // namespace cyc
 }  // namespace amg

@@ -325,7 +325,8 @@ template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
     // columns as int16 offsets from the row when every one fits (2 bytes less per entry)
     V.sci.release();
     V.sd.release();
-    const bool d16 = M.nrows == M.ncols && cyc::max_col_offset(M.nrows, M.rp(), M.ci(), s) <= 32767;
+    V.max_row = 0;
+    const bool d16 = M.nrows == M.ncols && cyc::max_col_offset(M.nrows, M.rp(), M.ci(), s, &V.max_row) <= 32767;
     if (d16) V.sd.alloc(sizeof(int16_t) * (V.sell_entries + kPad));
     else V.sci.alloc(sizeof(int32_t) * (V.sell_entries + kPad));
     V.sv.alloc(sizeof(VT) * (V.sell_entries + kPad));
@@ -818,6 +819,7 @@ CycMat<double> a0_mat(Hierarchy &h) {
         m.sd = V.sd.ptr ? V.sd.as<int16_t>() : nullptr;
         m.sv = V.sv64.as<double>();
         m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
+        m.max_row = V.max_row;
     } else {
         m.variant = V.variant == AMG_SPMV_SELL32 ? heuristic_variant(V.A) : V.variant;
     }

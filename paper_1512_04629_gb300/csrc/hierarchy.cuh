@@ -51,6 +51,7 @@ struct Level {
     DevBuf sperm;              // SELL position -> row when rows are length-sorted
     DevBuf sv64;               // level 0 in FP32 modes: FP64 values in the same SELL layout (outer PCG)
     int64_t sell_entries = 0;
+    int32_t max_row = 0;       // longest row of the relaxed operator (kernel choice)
     SellCopy psell, rsell;     // SELL copies of P and R (cycle precision) when they win the trial
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
     bool pr_tuned = false;  // transfer-operator variants chosen by timed trials
@@ -176,6 +177,7 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
         m.sv = V.sv.as<VT>();
         m.perm = V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr;
     }
+    m.max_row = V.max_row;
     m.variant = V.variant;
     return m;
 }
