@@ -154,6 +154,8 @@ int64_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStrea
 int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // the same without reading back: out[n] and *total (device) are written on the stream
 void exclusive_scan_i64_async(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s);
+// int32 scan whose total the caller already knows (no read-back)
+void exclusive_scan_i32_known(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 
 template <typename T> T read_scalar(const T *dptr, cudaStream_t s) {
     T v;

@@ -78,10 +78,10 @@ void timing_collect(Hierarchy &h) {
     h.pending.clear();
 }
 
-static void init_level_maps(Level &V, cudaStream_t s) {
+static void init_level_maps(Level &V, cudaStream_t s, bool check = true) {
     V.diagpos.alloc(sizeof(int32_t) * (V.A.nrows + 1));
     V.tpos.alloc(sizeof(int32_t) * (V.A.nnz + 1));
-    setup::level_maps(V.A, V.diagpos.as<int32_t>(), V.tpos.as<int32_t>(), s);
+    setup::level_maps(V.A, V.diagpos.as<int32_t>(), V.tpos.as<int32_t>(), s, check);
     V.keep.alloc(V.A.nnz + kPad);
 }
 
@@ -150,7 +150,7 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
             setup::spgemm(V.R, AP, C->A, s);
         });
         timed(h, 12, l, 0.0, s, [&] {
-            init_level_maps(*C, s);
+            init_level_maps(*C, s, false);  // R (A P) of a checked A_l
             C->inM.alloc(C->A.nnz + kPad);
             setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
         });

@@ -8,8 +8,10 @@ namespace setup {
 // Checks squareness, sortedness, column range, finite values, a stored
 // positive diagonal and a symmetric pattern; writes the diagonal position of
 // every row and the position of the mirrored entry (j,i) of every stored
-// (i,j).  Throws AMG_ERR_INVALID naming every failed check.
-void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s);
+// (i,j).  Throws AMG_ERR_INVALID naming every failed check.  check = false
+// skips the read-back of the checks (a Galerkin product this library formed:
+// sorted rows and a symmetric pattern by construction).
+void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s, bool check = true);
 // Row pointers, column range, strictly increasing columns and finite values of
 // a rectangular operator; throws AMG_ERR_INVALID naming `what`.
 void validate_rect(const DevCSR &M, const char *what, cudaStream_t s);

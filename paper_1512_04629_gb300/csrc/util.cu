@@ -298,5 +298,9 @@ int64_t exclusive_scan_i64_from_i32(const int32_t *in, int64_t *out, int64_t n, 
 void exclusive_scan_i64_async(const int64_t *in, int64_t *out, int64_t n, int64_t *total, cudaStream_t s) {
     scan_launch<int64_t, int64_t>(in, out, n, total, s);
 }
+void exclusive_scan_i32_known(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s) {
+    TmpBuf total(sizeof(int64_t), s);
+    scan_launch<int32_t, int32_t>(in, out, n, total.as<int64_t>(), s);
+}
 
 }  // namespace amg
