@@ -63,3 +63,33 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(amg, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="missing"):
         amg.lib()
+
+
+def header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/amg.h, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", text, flags=re.S)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        parts = [p.strip() for p in decl.split(",") if p.strip()]
+        for p in parts:  # "int32_t nrows" / "ncols" / "const int32_t *rowptr"
+            fields.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", p)[-1])
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("amg_options", "Options"), ("amg_solve_info", "SolveInfo"),
+                                          ("amg_level_info", "LevelInfo")])
+def test_binding_structs_mirror_header(cname, pyname):
+    from paper_1512_04629_gb300 import amg
+
+    assert [f for f, _ in getattr(amg, pyname)._fields_] == header_struct_fields(cname)
+
+
+def test_option_defaults_without_gpu(libpath):
+    from paper_1512_04629_gb300 import amg
+
+    o = amg.default_options()
+    assert (o.theta, o.max_size, o.max_levels, o.method, o.precision) == (0.25, 100, 25, amg.METHOD_SPARSE, 0)
+    assert (o.lump, o.krylov, o.restart) == (amg.LUMP_DIAG, amg.KRYLOV_CG, 30)
+    assert (o.k_check, o.s_levels, o.gamma_min, o.rho_max) == (3, 1, 0.01, 0.5)
