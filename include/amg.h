@@ -82,7 +82,9 @@ enum { AMG_METHOD_SPARSE = 0, AMG_METHOD_HYBRID = 1, AMG_METHOD_NONGALERKIN = 2 
 enum { AMG_LUMP_DIAG = 0, AMG_LUMP_STRONG = 1 };
 /* Outer Krylov method of amg_solve: preconditioned CG, or restarted GMRES
  * right-preconditioned by the V-cycle (the paper's solver where full lumping
- * can cost positive definiteness, Section 5). */
+ * can cost positive definiteness, Section 5).  amg_solve_batch and the server
+ * run per-column CG whatever this says; a column that meets an indefinite
+ * preconditioner ends with AMG_BREAKDOWN in its own info. */
 enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
 enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_FP32_BF16 = 2 };
 /* SpMV kernel variants: CSR with T threads per row, or SELL-32 slices. */
@@ -198,7 +200,8 @@ amg_status amg_solve(amg_hierarchy *h, const double *b, double *x, double tol, i
  * amg_solve_batch -- k independent solves sharing one hierarchy; B and X are
  * row-major n x k (column j = right-hand side j), host or device per
  * on_device.  The V-cycle runs as a multi-right-hand-side SpMM; each column
- * keeps its own CG scalars and stops on its own.  info_k has k entries.
+ * keeps its own CG scalars and stops on its own (always CG: amg_options.krylov
+ * applies to amg_solve only).  info_k has k entries.
  */
 amg_status amg_solve_batch(amg_hierarchy *h, int k, const double *B, double *X, double tol,
                            int max_it, int on_device, void *stream, amg_solve_info *info_k);
