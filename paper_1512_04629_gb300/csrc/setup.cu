@@ -783,6 +783,67 @@ template <int U> struct AccTab {
     }
 };
 
+// Bitonic sort of 32 R keys held in registers (position p = lane + 32 r),
+// ascending: partners in other lanes by shuffles, partners in the same lane
+// (strides >= 32) by register swaps -- no shared memory, no warp barriers.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_sort(int32_t (&k)[R], int lane) {
+    constexpr int N = 32 * R;
+#pragma unroll
+    for (int size = 2; size <= N; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int rs = stride >> 5;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int pr = r ^ rs;
+                    if (pr > r) {
+                        const bool asc = ((lane + 32 * r) & size) == 0;
+                        const int32_t a = k[r], b = k[pr];
+                        const bool sw = (a > b) == asc;
+                        k[r] = sw ? b : a;
+                        k[pr] = sw ? a : b;
+                    }
+                }
+            } else {
+                const bool lower = (lane & stride) == 0;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const bool asc = ((lane + 32 * r) & size) == 0;
+                    const int32_t y = __shfl_xor_sync(kFull, k[r], stride);
+                    k[r] = (lower == asc) ? min(k[r], y) : max(k[r], y);
+                }
+            }
+        }
+    }
+}
+
+// the row's u <= 32 R distinct columns (t.list[0 .. u)) sorted in registers,
+// then written with their accumulated values
+template <int R, int U>
+__device__ __forceinline__ void warp_emit_sorted(AccTab<U> &t, int32_t u, uint32_t mask, int lane, int64_t cbase,
+                                                 int32_t *__restrict__ cci, double *__restrict__ cv) {
+    int32_t k[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int p = lane + 32 * r;
+        k[r] = p < u ? t.list[p] : INT_MAX;
+    }
+    warp_bitonic_sort<R>(k, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int p = lane + 32 * r;
+        if (p < u) {
+            const int32_t j = k[r];
+            uint32_t sl = hash32(j) & mask;
+            while (t.keys[sl] != j) sl = (sl + 1) & mask;
+            cci[cbase + p] = j;
+            cv[cbase + p] = t.val[sl];
+        }
+    }
+}
+
 template <int U, bool NUMERIC>
 __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
                                 const double *__restrict__ av, const int32_t *__restrict__ brp,
@@ -916,6 +977,13 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
         if (key >= 0) t.list[base + __popc(m & ((1u << lane) - 1u))] = key;
         base += __popc(m);
     }
+    __syncwarp();
+    const int64_t cbase = obase[i];
+    // up to 128 distinct columns: sorted in registers (the shared-memory
+    // network below was most of this kernel's instructions)
+    if (u <= 32) { warp_emit_sorted<1, U>(t, u, mask, lane, cbase, cci, cv); __syncwarp(); return u; }
+    if (u <= 64) { warp_emit_sorted<2, U>(t, u, mask, lane, cbase, cci, cv); __syncwarp(); return u; }
+    if (u <= 128) { warp_emit_sorted<4, U>(t, u, mask, lane, cbase, cci, cv); __syncwarp(); return u; }
     int32_t m2 = 1;
     while (m2 < u) m2 <<= 1;
     for (int32_t r = u + lane; r < m2; r += 32) t.list[r] = INT_MAX;
@@ -933,7 +1001,6 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
             __syncwarp();
         }
     }
-    const int64_t cbase = obase[i];
     for (int32_t r = lane; r < u; r += 32) {
         const int32_t j = t.list[r];
         uint32_t sl = hash32(j) & mask;
