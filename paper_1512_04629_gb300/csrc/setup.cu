@@ -483,6 +483,23 @@ __device__ __forceinline__ int32_t row_slots(int64_t ub, int32_t cap) {
     return h;
 }
 
+template <int R>
+__device__ __forceinline__ void warp_bitonic_sort(int32_t (&k)[R], int lane);
+
+// t.list[0 .. u) (u <= 32 R) sorted in place by the first warp of the block
+template <int R, int NT>
+__device__ __forceinline__ void block_list_sort_warp(int32_t *list, int32_t u, int32_t lane) {
+    if (lane < 32) {
+        int32_t k[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) k[r] = lane + 32 * r < u ? list[lane + 32 * r] : INT_MAX;
+        warp_bitonic_sort<R>(k, lane);
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (lane + 32 * r < u) list[lane + 32 * r] = k[r];
+    }
+}
+
 // Inserts every product column of row i; returns the number of distinct columns.
 template <int NT>
 __device__ int32_t row_insert(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
@@ -534,19 +551,27 @@ __device__ int32_t row_numeric(int32_t i, int32_t lane, const int32_t *arp, cons
     }
     int32_t m = 1;
     while (m < u) m <<= 1;
-    for (int32_t r = u + lane; r < m; r += NT) t.list[r] = INT_MAX;
-    gsync<NT>();
-    for (int32_t size = 2; size <= m; size <<= 1) {
-        for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int32_t r = lane; r < m; r += NT) {
-                int32_t partner = r ^ stride;
-                if (partner > r) {
-                    bool up = (r & size) == 0;
-                    int32_t a = t.list[r], b = t.list[partner];
-                    if ((a > b) == up) { t.list[r] = b; t.list[partner] = a; }
+    if (m <= 128) {  // one warp sorts in registers: two barriers instead of one per pass
+        gsync<NT>();
+        if (m <= 32) block_list_sort_warp<1, NT>(t.list, u, lane);
+        else if (m <= 64) block_list_sort_warp<2, NT>(t.list, u, lane);
+        else block_list_sort_warp<4, NT>(t.list, u, lane);
+        gsync<NT>();
+    } else {
+        for (int32_t r = u + lane; r < m; r += NT) t.list[r] = INT_MAX;
+        gsync<NT>();
+        for (int32_t size = 2; size <= m; size <<= 1) {
+            for (int32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int32_t r = lane; r < m; r += NT) {
+                    int32_t partner = r ^ stride;
+                    if (partner > r) {
+                        bool up = (r & size) == 0;
+                        int32_t a = t.list[r], b = t.list[partner];
+                        if ((a > b) == up) { t.list[r] = b; t.list[partner] = a; }
+                    }
                 }
+                gsync<NT>();
             }
-            gsync<NT>();
         }
     }
     // rank of each key, output columns, zero accumulators
