@@ -339,6 +339,8 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
     if (cf[i] == kC) { pci[pos] = cmap[i]; pv[pos] = 1.0; prow[pos] = -1; return; }
     if (prp[i + 1] == pos) return;  // no strong C neighbour: empty row
     double diag = 0.0, sum_neg = 0.0, sum_pos = 0.0, sum_neg_c = 0.0, sum_pos_c = 0.0;
+    // one pass: the row sums in column order, and P's pattern with a_ij in
+    // place of the weight (the weights need the finished sums)
 #pragma unroll 4
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
@@ -348,6 +350,12 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
         const bool sc = strong[p] && cf[j] == kC;
         if (ak < 0) { sum_neg += a; if (sc) sum_neg_c += a; }
         if (ak > 0) { sum_pos += a; if (sc) sum_pos_c += a; }
+        if (sc) {
+            pci[pos] = cmap[j];
+            pv[pos] = a;
+            prow[pos] = i;
+            ++pos;
+        }
     }
     double alpha = f64_key(sum_neg_c) != 0 ? sum_neg / sum_neg_c : 0.0;
     double beta = 0.0;
@@ -356,14 +364,6 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
     coef[3 * (int64_t)i] = alpha;
     coef[3 * (int64_t)i + 1] = beta;
     coef[3 * (int64_t)i + 2] = diag;
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        int32_t j = ci[p];
-        if (j == i || !strong[p] || cf[j] != kC) continue;
-        pci[pos] = cmap[j];
-        pv[pos] = v[p];
-        prow[pos] = i;
-        ++pos;
-    }
 }
 
 __global__ void interp_weights_kernel(int64_t nnz, const int32_t *prow, const double *coef, double *pv) {
@@ -1205,17 +1205,25 @@ __global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int3
                                         double *hv) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // one pass in column order: the lumped diagonal starts from a_ii (read
+    // first, from its known position) and takes the dropped entries in
+    // order; kept entries are written as met, the diagonal's value last
     double d = v[diagpos[i]];
-#pragma unroll 8
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
-        if (!keep[p]) d += v[p];
-    int32_t pos = hrp[i];
+    int32_t pos = hrp[i], dpos = -1;
+#pragma unroll 4
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        if (!keep[p]) continue;
-        hci[pos] = ci[p];
-        hv[pos] = (ci[p] == i) ? d : v[p];
+        const double a = v[p];
+        if (!keep[p]) {
+            d += a;
+            continue;
+        }
+        const int32_t j = ci[p];
+        hci[pos] = j;
+        hv[pos] = a;
+        if (j == i) dpos = pos;
         ++pos;
     }
+    if (dpos >= 0) hv[dpos] = d;
 }
 
 // ---------------------------------------------------------------------------
