@@ -383,7 +383,16 @@ def run_c4(args):
 
 
 def run_c5(args):
-    """Serving: 8 resident hierarchies, Poisson arrivals at 200/s, continuous batching."""
+    """Serving: 8 resident hierarchies, Poisson arrivals at 200/s, continuous batching.
+
+    The right-hand sides are generated before the clock starts (a pool of
+    seeded vectors per hierarchy, used in turn), and a waiter thread retires
+    tickets while requests keep arriving, so the client does not limit the
+    offered rate; the line reports the rate it achieved and its worst lag
+    behind the arrival schedule."""
+    import queue
+    import threading
+
     import numpy as np
 
     import amg_inputs as gen
@@ -396,6 +405,9 @@ def run_c5(args):
         A = gen.generate(kind, N)
         hs.append(amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=1))
         ns.append(A.n)
+    pool_per_h = 4
+    pool = [[gen.rhs_uniform(ns[hid], 10_000 + pool_per_h * hid + k) for k in range(pool_per_h)]
+            for hid in range(len(hs))]
     srv = amg.Server(max_batch=32)
     ids = [srv.register(h) for h in hs]
     rng = np.random.default_rng(5)
@@ -403,27 +415,43 @@ def run_c5(args):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * T * 1.5)))
     arrivals = arrivals[arrivals < T]
     picks = rng.integers(0, len(hs), size=len(arrivals))
-    tickets = []
+
+    pending: queue.Queue = queue.Queue()
+    results = []
+
+    def waiter():
+        while True:
+            item = pending.get()
+            if item is None:
+                return
+            t, hid = item
+            st, _, info = srv.wait(t, ids[hid], timeout_ms=600000)
+            results.append((st, info))
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    lag = 0.0
     t0 = time.perf_counter()
     for r, (ta, hid) in enumerate(zip(arrivals, picks)):
-        b = gen.rhs_uniform(ns[hid], 10_000 + r)
         now = time.perf_counter() - t0
         if ta > now:
             time.sleep(ta - now)
-        tickets.append((srv.submit(ids[hid], b), hid))
-    lat, its, bad = [], [], 0
-    for t, hid in tickets:
-        st, x, info = srv.wait(t, ids[hid], timeout_ms=600000)
-        if st != 0 or info.final_relres > args.tol:
-            bad += 1
-        lat.append(info.solve_ms)
-        its.append(info.iterations)
+        else:
+            lag = max(lag, now - ta)
+        pending.put((srv.submit(ids[hid], pool[hid][r % pool_per_h]), hid))
+    t_sub = time.perf_counter() - t0
+    pending.put(None)
+    th.join()
     wall = time.perf_counter() - t0
     srv.close()
-    lat = np.array(lat)
+    bad = sum(1 for st, info in results if st != 0 or info.final_relres > args.tol)
+    lat = np.array([info.solve_ms for _, info in results])
+    its = [info.iterations for _, info in results]
     print(json.dumps({"workload": "c5: serving 8 hierarchies (2D 256^2..2048^2, 3D 32^3..128^3, gamma 0.1, FP32 cycle), "
                                   f"Poisson arrivals {rate:g}/s for {T:g} s, max_batch 32",
-                      "requests": len(tickets), "failed": bad, "solves_per_s": len(tickets) / wall,
+                      "requests": len(results), "failed": bad, "solves_per_s": len(results) / wall,
+                      "offered_per_s": len(results) / T, "submitted_per_s": len(results) / t_sub,
+                      "client_max_lag_ms": 1e3 * lag,
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "max_ms": float(lat.max()), "iterations_median": float(np.median(its))}))
 

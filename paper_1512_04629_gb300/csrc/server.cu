@@ -1,14 +1,17 @@
 // server.cu -- continuous-batching solve server (amg_server_*).
 //
 // One worker thread owns the device work.  Each registered hierarchy has a
-// K-column batch (K = batch width >= max_batch) on its own stream.  Between
-// two iterations the worker admits queued requests into free columns (the
-// batch workspace is allocated on first use, within the memory budget, and
-// released when the hierarchy goes idle), launches one PCG iteration on every
-// hierarchy with work -- so different hierarchies' batches overlap on the
-// device -- then polls the streams' completion events with a time limit and
-// retires converged columns.  A column's arithmetic does not depend on the
-// other columns, so a request's result is the same alone and in any mix.
+// K-column batch (K = batch width >= max_batch) on its own stream and moves
+// through its own cycle -- admit queued requests into free columns, one PCG
+// iteration, and when some column's recurrence residual reached its
+// tolerance (or its iteration budget) the true-residual check -- driven by
+// polling its stream's completion event.  Hierarchies do not wait for one
+// another: a small hierarchy runs many iterations while a large one runs one,
+// and while the worker admits or retires requests of one hierarchy the
+// others keep the device busy.  The batch workspace is allocated on first
+// use, within the memory budget, and released when the hierarchy goes idle.
+// A column's arithmetic does not depend on the other columns, so a request's
+// result is the same alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -47,7 +50,11 @@ struct Slot {
     Request *req = nullptr;
     int its = 0, reps = 0;
     double rnorm = 0.0;
+    bool out_of_budget = false;  // retire as not converged after the residual check
 };
+
+// where a hierarchy is in its cycle
+enum Phase { kIdle = 0, kIter = 1, kResid = 2 };
 
 struct HState {
     Hierarchy *h = nullptr;
@@ -60,7 +67,8 @@ struct HState {
     std::deque<Request *> queue;
     DevBuf dstage;          // n doubles: admission / retirement staging
     double *hstage = nullptr;  // pinned n doubles
-    bool launched = false;
+    Phase phase = kIdle;
+    Clock::time_point launched_at;
 };
 
 constexpr double kWaitLimitSeconds = 120.0;
@@ -94,18 +102,6 @@ int64_t batch_bytes(const Hierarchy &h, int K) {
     return cyc + pcg + (1 << 20);
 }
 
-// polls the stream's completion event; false on time-out
-bool wait_event(cudaEvent_t ev, double limit_s) {
-    auto t0 = Clock::now();
-    while (true) {
-        cudaError_t e = cudaEventQuery(ev);
-        if (e == cudaSuccess) return true;
-        if (e != cudaErrorNotReady) throw Error(AMG_ERR_CUDA, std::string("stream failed: ") + cudaGetErrorString(e));
-        if (std::chrono::duration<double>(Clock::now() - t0).count() > limit_s) return false;
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-    }
-}
-
 void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
     Slot &sl = H.slots[c];
     Request *r = sl.req;
@@ -114,8 +110,9 @@ void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
     bat::gather_column(H.n, w.K, c, w.X.as<double>(), H.dstage.as<double>(), H.stream);
     AMG_CUDA(cudaMemcpyAsync(H.hstage, H.dstage.ptr, sizeof(double) * H.n, cudaMemcpyDeviceToHost, H.stream));
     AMG_CUDA(cudaStreamSynchronize(H.stream));
+    std::vector<double> x(H.hstage, H.hstage + H.n);  // outside the lock: clients keep submitting and waiting
     std::lock_guard<std::mutex> lk(S->mu);
-    r->x.assign(H.hstage, H.hstage + H.n);
+    r->x = std::move(x);
     r->status = status;
     r->info.iterations = sl.its;
     r->info.replacements = sl.reps;
@@ -217,89 +214,147 @@ void fail_all(amg_server *S, const std::string &msg) {
     S->cv_done.notify_all();
 }
 
+bool has_live(const HState &H) {
+    for (auto &sl : H.slots)
+        if (sl.req) return true;
+    return false;
+}
+
+// admit, then one iteration if any column is live (else idle)
+void start_iteration(amg_server *S, HState &H) {
+    admit(S, H);
+    if (!H.ws || !has_live(H)) {
+        H.phase = kIdle;
+        release_if_idle(S, H);
+        return;
+    }
+    batch_iteration(*H.h, *H.ws, H.stream);
+    AMG_CUDA(cudaEventRecord(H.done_ev, H.stream));
+    H.phase = kIter;
+    H.launched_at = Clock::now();
+}
+
+// an iteration finished: retire broken-down columns, flag candidates and
+// columns out of budget for the true-residual check, or go on
+void after_iteration(amg_server *S, HState &H) {
+    BatchWS &w = *H.ws;
+    bool check = false, changed = false;
+    for (int c = 0; c < S->K; ++c) {
+        Slot &sl = H.slots[c];
+        if (!sl.req || !w.h_active()[c]) continue;
+        sl.its++;
+        const double pq = w.h_pq()[c], rho = w.h_rho()[c], rr = w.h_rr()[c];
+        w.h_mask()[c] = 0;
+        if (!(pq > 0.0) || !(rho > 0.0) || !std::isfinite(rr)) {
+            finish_request(S, H, c, AMG_BREAKDOWN, rr);
+            changed = true;
+            continue;
+        }
+        sl.rnorm = std::sqrt(rr);
+        if (sl.rnorm <= sl.req->tol * sl.req->bnorm) {
+            w.h_mask()[c] = 1;
+            check = true;
+        } else if (sl.its >= S->opt.max_it) {
+            sl.out_of_budget = true;
+            check = true;
+        }
+    }
+    if (changed) {
+        for (int c = 0; c < S->K; ++c) w.h_start()[c] = 0;
+        batch_push_flags(w, H.stream);
+    }
+    if (check) {
+        batch_true_residual(*H.h, w, H.stream);
+        AMG_CUDA(cudaEventRecord(H.done_ev, H.stream));
+        H.phase = kResid;
+        H.launched_at = Clock::now();
+        return;
+    }
+    start_iteration(S, H);
+}
+
+// the true residuals are in: retire converged and out-of-budget columns,
+// replace the residual of the others, then go on
+void after_residual(amg_server *S, HState &H) {
+    BatchWS &w = *H.ws;
+    bool replace = false, changed = false;
+    for (int c = 0; c < S->K; ++c) {
+        Slot &sl = H.slots[c];
+        if (!sl.req) continue;
+        const double tt = w.h_tt()[c];
+        if (w.h_mask()[c]) {
+            const double tn = std::sqrt(tt);
+            sl.rnorm = tn;
+            if (tn <= sl.req->tol * sl.req->bnorm) {
+                w.h_mask()[c] = 0;
+                finish_request(S, H, c, AMG_OK, tt);
+                changed = true;
+                continue;
+            }
+            sl.reps++;
+            replace = true;
+        }
+        if (sl.req && sl.out_of_budget) {
+            w.h_mask()[c] = 0;
+            finish_request(S, H, c, AMG_NOT_CONVERGED, tt);
+            changed = true;
+        }
+    }
+    if (replace) {
+        AMG_CUDA(cudaMemcpyAsync(w.mask.ptr, w.h_mask(), sizeof(int) * w.K, cudaMemcpyHostToDevice, H.stream));
+        bat::copy_masked_columns(H.n, w.K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), H.stream);
+    }
+    for (int c = 0; c < S->K; ++c) w.h_mask()[c] = 0;
+    if (changed) {
+        for (int c = 0; c < S->K; ++c) w.h_start()[c] = 0;
+        batch_push_flags(w, H.stream);
+    }
+    start_iteration(S, H);
+}
+
 void worker_loop(amg_server *S) {
     cudaSetDevice(S->device);
     try {
         while (true) {
+            bool queued;
             {
                 std::unique_lock<std::mutex> lk(S->mu);
-                bool busy = S->queued > 0;
-                for (auto &H : S->hs)
-                    for (auto &sl : H->slots) busy |= sl.req != nullptr;
+                queued = S->queued > 0;
+                bool busy = queued;
+                for (auto &H : S->hs) busy |= H->phase != kIdle || has_live(*H);
                 if (S->stop && !busy) break;
                 if (!busy) {
                     S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
                     continue;
                 }
             }
-            for (auto &H : S->hs) admit(S, *H);
-            // one iteration on every hierarchy with live columns, all launched before any wait
-            for (auto &H : S->hs) {
-                H->launched = false;
-                if (!H->ws) continue;
-                bool live = false;
-                for (auto &sl : H->slots) live |= sl.req != nullptr;
-                if (!live) continue;
-                batch_iteration(*H->h, *H->ws, H->stream);
-                AMG_CUDA(cudaEventRecord(H->done_ev, H->stream));
-                H->launched = true;
+            bool progressed = false;
+            for (auto &Hp : S->hs) {
+                HState &H = *Hp;
+                if (H.phase == kIdle) {
+                    bool waiting;
+                    {
+                        std::lock_guard<std::mutex> lk(S->mu);
+                        waiting = !H.queue.empty();
+                    }
+                    if (waiting || has_live(H)) {
+                        start_iteration(S, H);
+                        progressed |= H.phase != kIdle;
+                    }
+                    continue;
+                }
+                const cudaError_t e = cudaEventQuery(H.done_ev);
+                if (e == cudaErrorNotReady) {
+                    if (std::chrono::duration<double>(Clock::now() - H.launched_at).count() > kWaitLimitSeconds)
+                        throw Error(AMG_TIMEOUT, "batch iteration timed out");
+                    continue;
+                }
+                if (e != cudaSuccess) throw Error(AMG_ERR_CUDA, std::string("stream failed: ") + cudaGetErrorString(e));
+                progressed = true;
+                if (H.phase == kIter) after_iteration(S, H);
+                else after_residual(S, H);
             }
-            for (auto &H : S->hs) {
-                if (!H->launched) continue;
-                if (!wait_event(H->done_ev, kWaitLimitSeconds)) throw Error(AMG_TIMEOUT, "batch iteration timed out");
-                BatchWS &w = *H->ws;
-                bool candidate = false, changed = false;
-                for (int c = 0; c < S->K; ++c) {
-                    Slot &sl = H->slots[c];
-                    if (!sl.req || !w.h_active()[c]) continue;
-                    sl.its++;
-                    double pq = w.h_pq()[c], rho = w.h_rho()[c], rr = w.h_rr()[c];
-                    w.h_mask()[c] = 0;
-                    if (!(pq > 0.0) || !(rho > 0.0) || !std::isfinite(rr)) {
-                        finish_request(S, *H, c, AMG_BREAKDOWN, rr);
-                        changed = true;
-                        continue;
-                    }
-                    sl.rnorm = std::sqrt(rr);
-                    if (sl.rnorm <= sl.req->tol * sl.req->bnorm) { w.h_mask()[c] = 1; candidate = true; }
-                    else if (sl.its >= S->opt.max_it) {
-                        batch_true_residual(*H->h, w, H->stream);
-                        AMG_CUDA(cudaStreamSynchronize(H->stream));
-                        finish_request(S, *H, c, AMG_NOT_CONVERGED, w.h_tt()[c]);
-                        changed = true;
-                    }
-                }
-                if (candidate) {
-                    batch_true_residual(*H->h, w, H->stream);
-                    AMG_CUDA(cudaEventRecord(H->done_ev, H->stream));
-                    if (!wait_event(H->done_ev, kWaitLimitSeconds)) throw Error(AMG_TIMEOUT, "residual check timed out");
-                    bool replace = false;
-                    for (int c = 0; c < S->K; ++c) {
-                        Slot &sl = H->slots[c];
-                        if (!sl.req || !w.h_mask()[c]) continue;
-                        double tn = std::sqrt(w.h_tt()[c]);
-                        sl.rnorm = tn;
-                        if (tn <= sl.req->tol * sl.req->bnorm) {
-                            w.h_mask()[c] = 0;
-                            finish_request(S, *H, c, AMG_OK, w.h_tt()[c]);
-                            changed = true;
-                        } else {
-                            sl.reps++;
-                            replace = true;
-                        }
-                    }
-                    if (replace) {
-                        AMG_CUDA(cudaMemcpyAsync(w.mask.ptr, w.h_mask(), sizeof(int) * w.K, cudaMemcpyHostToDevice, H->stream));
-                        bat::copy_masked_columns(H->n, w.K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), H->stream);
-                    }
-                    for (int c = 0; c < S->K; ++c) w.h_mask()[c] = 0;
-                }
-                if (changed) {
-                    for (int c = 0; c < S->K; ++c) w.h_start()[c] = 0;
-                    batch_push_flags(w, H->stream);
-                }
-                release_if_idle(S, *H);
-            }
+            if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
     } catch (const std::exception &e) {
         fail_all(S, e.what());
