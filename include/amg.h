@@ -295,23 +295,41 @@ int64_t amg_device_bytes(const amg_hierarchy *h);
  * next iteration boundary when a column slot and device memory are free
  * (continuous batching).  Each column's CG scalars are its own, so a result
  * does not depend on what else is in the batch.
+ *
+ * Each registered hierarchy runs on its own stream, and submit/wait copy on
+ * one more.  CUDA maps streams onto CUDA_DEVICE_MAX_CONNECTIONS hardware
+ * queues (8 unless set), and streams sharing a queue wait on one another: a
+ * caller serving more than a handful of hierarchies should set it (up to 32)
+ * before the process creates its CUDA context.  The Python package sets 32
+ * on import unless the variable is already set.
  */
 typedef struct {
     int max_batch;          /* column slots per hierarchy, default 32 */
-    int64_t hbm_budget;     /* bytes the server may allocate for batches; 0 = free HBM */
+    int64_t hbm_budget;     /* bytes the server may allocate for batch workspaces;
+                               0 = 70% of the HBM free at create */
     int max_queue;          /* pending requests before submits are rejected, default 4096 */
     int max_it;             /* per request, default 500 */
+    int64_t stage_budget;   /* bytes of device memory, on top of hbm_budget, for requests
+                               held on the device: right-hand sides from submit to
+                               admission, results from retirement to wait.  0 (default)
+                               = a quarter of the workspace budget; -1 = none.  A request
+                               that finds no room is staged through host memory by the
+                               worker thread instead (same result, slower). */
 } amg_server_opts;
 
 void amg_server_opts_default(amg_server_opts *o);
 amg_status amg_server_create(const amg_server_opts *o, amg_server **out);
 /* The hierarchy stays owned by the caller and must outlive the server. */
 amg_status amg_server_register(amg_server *s, amg_hierarchy *h, int *hid);
-/* b: host n-vector, copied at submit.  Returns a ticket. */
+/* b: host n-vector, copied at submit (uploaded to the device when the
+ * staging budget has room; b is free for reuse when the call returns).
+ * Returns a ticket. */
 amg_status amg_server_submit(amg_server *s, int hid, const double *b, double tol,
                              uint64_t *ticket);
-/* Waits up to timeout_ms for the ticket; x: host n-vector.  AMG_TIMEOUT if
- * not finished in time (the request stays queued and can be waited again). */
+/* Waits up to timeout_ms for the ticket; x: host n-vector, written on the
+ * calling thread (the download of a device-staged result runs here, not on
+ * the worker).  AMG_TIMEOUT if not finished in time (the request stays
+ * queued and can be waited again). */
 amg_status amg_server_wait(amg_server *s, uint64_t ticket, double *x, int timeout_ms,
                            amg_solve_info *info);
 /* Stops the worker after the running batches finish; frees the server. */

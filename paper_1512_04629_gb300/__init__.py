@@ -3,7 +3,17 @@
 The computation lives in libamg.so (CUDA, sm_103a) behind the C ABI of
 include/amg.h; this package is its ctypes binding and build script.
 """
-from .amg import (  # noqa: F401
+import os as _os
+
+# The server runs each registered hierarchy on its own stream.  CUDA spreads
+# streams over CUDA_DEVICE_MAX_CONNECTIONS hardware queues (8 by default), and
+# streams that share a queue wait on one another; 32 queues keep the
+# hierarchies and the server's copies apart.  Read when the process creates
+# its CUDA context, so it takes effect only if that happens after this import;
+# a value the user set is kept.
+_os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+from .amg import (  # noqa: F401,E402
     OK, ERR_INVALID, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, BREAKDOWN, TIMEOUT, REJECTED,
     AmgError, Hierarchy, Matrix, Server, SolveInfo, default_options, device_bytes, kernel_launches, lib,
     METHOD_SPARSE, METHOD_HYBRID, METHOD_NONGALERKIN, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,

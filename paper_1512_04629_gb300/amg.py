@@ -74,7 +74,7 @@ class LevelInfo(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("hbm_budget", C.c_int64), ("max_queue", C.c_int),
-                ("max_it", C.c_int)]
+                ("max_it", C.c_int), ("stage_budget", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -410,11 +410,13 @@ def kernel_launches() -> int:
 class Server:
     """Continuous-batching solve server (amg_server_*)."""
 
-    def __init__(self, max_batch: int = 32, hbm_budget: int = 0, max_queue: int = 4096, max_it: int = 500):
+    def __init__(self, max_batch: int = 32, hbm_budget: int = 0, max_queue: int = 4096, max_it: int = 500,
+                 stage_budget: int = 0):
         L = lib()
         o = ServerOpts()
         L.amg_server_opts_default(C.byref(o))
         o.max_batch, o.hbm_budget, o.max_queue, o.max_it = max_batch, hbm_budget, max_queue, max_it
+        o.stage_budget = stage_budget
         out = C.c_void_p()
         _check(L.amg_server_create(C.byref(o), C.byref(out)), "amg_server_create")
         self._s = out

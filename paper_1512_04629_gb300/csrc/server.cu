@@ -12,7 +12,16 @@
 // use, within the memory budget, and released when the hierarchy goes idle.
 // A column's arithmetic does not depend on the other columns, so a request's
 // result is the same alone and in any mix.
+//
+// Host copies stay off the worker: submit uploads the right-hand side into a
+// device buffer of the request (from a staging pool with its own budget) and
+// wait downloads the result from another, so admitting a request is a
+// device-side scatter and retiring one a device-side gather, both queued on
+// the hierarchy's stream without a host wait.  When the staging budget is
+// used up (or set to none), a request goes through the worker's pinned host
+// buffer instead, as a synchronous copy.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -37,7 +46,12 @@ namespace {
 struct Request {
     uint64_t ticket = 0;
     int hid = 0;
-    std::vector<double> b, x;
+    int32_t n = 0;
+    std::vector<double> b, x;  // host copies: host staging, or the zero solution
+    double *d_b = nullptr;     // the right-hand side staged on the device at submit
+    double *d_x = nullptr;     // the result staged on the device at retirement
+    int64_t staged = 0;        // staging bytes the request holds
+    cudaEvent_t ev = nullptr;  // upload at submit, then the result's gather
     double tol = 1e-8;
     double bnorm = 0.0;
     amg_solve_info info{};
@@ -89,9 +103,66 @@ struct amg_server {
     int64_t budget = 0, in_use = 0;
     int device = 0;
     std::string fatal;
+    // device staging of requests (submit uploads, wait downloads)
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t io = nullptr;
+    int64_t stage_cap = 0;
+    std::atomic<int64_t> staged{0};
 };
 
 namespace {
+
+// the calling thread works on the server's device for the guard's lifetime
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+        if (old != dev) AMG_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+    }
+};
+
+// Stream-ordered allocation of `bytes` from the staging pool, within the
+// staging budget; nullptr when the budget or the pool has no room (the
+// request then goes through host staging).
+double *stage_alloc(amg_server *S, int64_t bytes, cudaStream_t s) {
+    if (!S->pool) return nullptr;
+    int64_t cur = S->staged.load();
+    do {
+        if (cur + bytes > S->stage_cap) return nullptr;
+    } while (!S->staged.compare_exchange_weak(cur, cur + bytes));
+    void *p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, (size_t)bytes, S->pool, s) != cudaSuccess) {
+        (void)cudaGetLastError();  // an allocation failure is not sticky
+        S->staged -= bytes;
+        return nullptr;
+    }
+    return static_cast<double *>(p);
+}
+
+// free a staged buffer of the request, stream-ordered on `s`
+void stage_free(amg_server *S, Request *r, double *&p, cudaStream_t s) {
+    if (!p) return;
+    const int64_t bytes = (int64_t)sizeof(double) * r->n;
+    AMG_CUDA(cudaFreeAsync(p, s));
+    p = nullptr;
+    r->staged -= bytes;
+    S->staged -= bytes;
+}
+
+// the device resources of a request that leaves the server (no throw)
+void drop_request(amg_server *S, Request *r) {
+    for (double **p : {&r->d_b, &r->d_x})
+        if (*p) cudaFreeAsync(*p, S->io);
+    r->d_b = r->d_x = nullptr;
+    S->staged -= r->staged;
+    r->staged = 0;
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->ev = nullptr;
+}
 
 int64_t batch_bytes(const Hierarchy &h, int K) {
     int64_t xb = h.opt.precision == AMG_PREC_FP64 ? 8 : 4;
@@ -106,13 +177,27 @@ void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
     Slot &sl = H.slots[c];
     Request *r = sl.req;
     BatchWS &w = *H.ws;
-    // X column -> host
-    bat::gather_column(H.n, w.K, c, w.X.as<double>(), H.dstage.as<double>(), H.stream);
-    AMG_CUDA(cudaMemcpyAsync(H.hstage, H.dstage.ptr, sizeof(double) * H.n, cudaMemcpyDeviceToHost, H.stream));
-    AMG_CUDA(cudaStreamSynchronize(H.stream));
-    std::vector<double> x(H.hstage, H.hstage + H.n);  // outside the lock: clients keep submitting and waiting
+    const int64_t bytes = (int64_t)sizeof(double) * H.n;
+    // X column -> a device buffer of the request, which wait copies to the
+    // caller; the column slot can take a new request right behind the gather
+    double *dx = stage_alloc(S, bytes, H.stream);
+    std::vector<double> x;
+    if (dx) {
+        bat::gather_column(H.n, w.K, c, w.X.as<double>(), dx, H.stream);
+        AMG_CUDA(cudaEventRecord(r->ev, H.stream));
+    } else {  // host staging
+        bat::gather_column(H.n, w.K, c, w.X.as<double>(), H.dstage.as<double>(), H.stream);
+        AMG_CUDA(cudaMemcpyAsync(H.hstage, H.dstage.ptr, bytes, cudaMemcpyDeviceToHost, H.stream));
+        AMG_CUDA(cudaStreamSynchronize(H.stream));
+        x.assign(H.hstage, H.hstage + H.n);  // outside the lock: clients keep submitting and waiting
+    }
     std::lock_guard<std::mutex> lk(S->mu);
-    r->x = std::move(x);
+    if (dx) {
+        r->d_x = dx;
+        r->staged += bytes;
+    } else {
+        r->x = std::move(x);
+    }
     r->status = status;
     r->info.iterations = sl.its;
     r->info.replacements = sl.reps;
@@ -165,14 +250,23 @@ bool admit(amg_server *S, HState &H) {
     for (auto &a : adm) {
         int c = a.first;
         Request *r = a.second;
-        std::memcpy(H.hstage, r->b.data(), sizeof(double) * H.n);
-        AMG_CUDA(cudaMemcpyAsync(H.dstage.ptr, H.hstage, sizeof(double) * H.n, cudaMemcpyHostToDevice, H.stream));
-        bat::scatter_column(H.n, w.K, c, H.dstage.as<double>(), w.B.as<double>(), H.stream);
-        bat::scatter_column(H.n, w.K, c, H.dstage.as<double>(), w.R.as<double>(), H.stream);
+        const double *src = r->d_b;
+        if (!src) {  // host staging
+            std::memcpy(H.hstage, r->b.data(), sizeof(double) * H.n);
+            AMG_CUDA(cudaMemcpyAsync(H.dstage.ptr, H.hstage, sizeof(double) * H.n, cudaMemcpyHostToDevice, H.stream));
+            src = H.dstage.as<double>();
+        }
+        bat::scatter_column(H.n, w.K, c, src, w.B.as<double>(), H.stream);
+        bat::scatter_column(H.n, w.K, c, src, w.R.as<double>(), H.stream);
         bat::zero_column(H.n, w.K, c, w.X.as<double>(), H.stream);
         bat::zero_column(H.n, w.K, c, w.P.as<double>(), H.stream);
         bat::zero_column(H.n, w.K, c, w.Q.as<double>(), H.stream);
-        AMG_CUDA(cudaStreamSynchronize(H.stream));  // staging buffers are reused
+        if (r->d_b) {
+            stage_free(S, r, r->d_b, H.stream);  // after the scatters, in stream order
+        } else {
+            AMG_CUDA(cudaStreamSynchronize(H.stream));  // the host staging buffers are reused
+            std::vector<double>().swap(r->b);
+        }
         H.slots[c].req = r;
         H.slots[c].its = H.slots[c].reps = 0;
         H.slots[c].rnorm = r->bnorm;
@@ -371,6 +465,7 @@ void amg_server_opts_default(amg_server_opts *o) {
     o->hbm_budget = 0;
     o->max_queue = 4096;
     o->max_it = 500;
+    o->stage_budget = 0;
 }
 
 amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
@@ -388,12 +483,27 @@ amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
         S->opt = opt;
         S->K = bat::batch_width(opt.max_batch);
         AMG_CUDA(cudaGetDevice(&S->device));
+        if (opt.stage_budget < -1) {
+            set_last_error("stage_budget must be >= -1");
+            return AMG_ERR_INVALID;
+        }
         if (opt.hbm_budget > 0) {
             S->budget = opt.hbm_budget;
         } else {
             size_t fr = 0, tot = 0;
             AMG_CUDA(cudaMemGetInfo(&fr, &tot));
-            S->budget = (int64_t)(fr * 0.9);
+            S->budget = (int64_t)(fr * 0.7);  // with the default staging quarter on top: 7/8 of free HBM
+        }
+        S->stage_cap = opt.stage_budget > 0 ? opt.stage_budget : opt.stage_budget == 0 ? S->budget / 4 : 0;
+        AMG_CUDA(cudaStreamCreateWithFlags(&S->io, cudaStreamNonBlocking));
+        if (S->stage_cap > 0) {
+            cudaMemPoolProps pp{};
+            pp.allocType = cudaMemAllocationTypePinned;
+            pp.location.type = cudaMemLocationTypeDevice;
+            pp.location.id = S->device;
+            AMG_CUDA(cudaMemPoolCreate(&S->pool, &pp));
+            uint64_t keep = (uint64_t)S->stage_cap;  // freed blocks stay with the pool up to the budget
+            AMG_CUDA(cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep));
         }
         S->worker = std::thread(worker_loop, S.get());
         *out = S.release();
@@ -444,9 +554,9 @@ amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol
         if (hid < 0 || hid >= (int)S->hs.size()) { set_last_error("unknown hierarchy id"); return AMG_ERR_INVALID; }
         if (!S->fatal.empty()) { set_last_error("server failed: " + S->fatal); return AMG_ERR_CUDA; }
         if (S->queued >= S->opt.max_queue) { set_last_error("queue full"); return AMG_REJECTED; }
+        r->n = S->hs[hid]->n;
     }
-    int32_t n = S->hs[hid]->n;
-    r->b.assign(b, b + n);
+    const int32_t n = r->n;
     double s2 = 0.0;
     for (int32_t i = 0; i < n; ++i) {
         if (!std::isfinite(b[i])) { set_last_error("b has a non-finite value"); return AMG_ERR_INVALID; }
@@ -455,39 +565,81 @@ amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol
     r->bnorm = std::sqrt(s2);
     r->tol = tol;
     r->hid = hid;
+    if (r->bnorm == 0.0) {  // x = 0 solves it
+        r->x.assign(n, 0.0);
+        r->done = true;
+        r->status = AMG_OK;
+    } else {
+        try {
+            DeviceGuard dg(S->device);
+            AMG_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+            const int64_t bytes = (int64_t)sizeof(double) * n;
+            r->d_b = stage_alloc(S, bytes, S->io);
+            if (r->d_b) {
+                r->staged = bytes;
+                AMG_CUDA(cudaMemcpyAsync(r->d_b, b, bytes, cudaMemcpyHostToDevice, S->io));
+                AMG_CUDA(cudaEventRecord(r->ev, S->io));
+                AMG_CUDA(cudaEventSynchronize(r->ev));  // b is the caller's again once submit returns
+            } else {
+                r->b.assign(b, b + n);
+            }
+        } catch (const Error &e) {
+            drop_request(S, r.get());
+            set_last_error(e.what());
+            return e.status;
+        }
+    }
     r->submitted = Clock::now();
     std::lock_guard<std::mutex> lk(S->mu);
     r->ticket = S->next_ticket++;
     *ticket = r->ticket;
     Request *rp = r.get();
-    if (r->bnorm == 0.0) {  // x = 0 solves it
-        r->x.assign(n, 0.0);
-        r->done = true;
-        r->status = AMG_OK;
-        S->reqs[rp->ticket] = std::move(r);
-        return AMG_OK;
-    }
+    const bool done = r->done;
     S->reqs[rp->ticket] = std::move(r);
-    S->hs[hid]->queue.push_back(rp);
-    S->queued++;
-    S->cv_work.notify_all();
+    if (!done) {
+        S->hs[hid]->queue.push_back(rp);
+        S->queued++;
+        S->cv_work.notify_all();
+    }
     return AMG_OK;
 }
 
 amg_status amg_server_wait(amg_server *S, uint64_t ticket, double *x, int timeout_ms, amg_solve_info *info) {
     set_last_error("");
     if (!S || !x) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
-    std::unique_lock<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(ticket);
-    if (it == S->reqs.end()) { set_last_error("unknown ticket"); return AMG_ERR_INVALID; }
-    Request *r = it->second.get();
-    bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] { return r->done; });
-    if (!ok) { set_last_error("request not finished within the time limit"); return AMG_TIMEOUT; }
-    std::memcpy(x, r->x.data(), sizeof(double) * r->x.size());
-    if (info) *info = r->info;
+    std::unique_ptr<Request> r;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) { set_last_error("unknown ticket"); return AMG_ERR_INVALID; }
+        Request *rp = it->second.get();
+        bool ok = S->cv_done.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] { return rp->done; });
+        if (!ok) { set_last_error("request not finished within the time limit"); return AMG_TIMEOUT; }
+        r = std::move(it->second);
+        S->reqs.erase(it);
+        if (r->status == AMG_ERR_CUDA) set_last_error("server failed: " + S->fatal);
+    }
     amg_status st = (amg_status)r->status;
-    if (st == AMG_ERR_CUDA) set_last_error("server failed: " + S->fatal);
-    S->reqs.erase(it);
+    try {  // the copy to the caller runs outside the lock
+        DeviceGuard dg(S->device);
+        if (st != AMG_ERR_CUDA) {
+            if (r->d_x) {
+                AMG_CUDA(cudaStreamWaitEvent(S->io, r->ev, 0));
+                AMG_CUDA(cudaMemcpyAsync(x, r->d_x, sizeof(double) * r->n, cudaMemcpyDeviceToHost, S->io));
+                stage_free(S, r.get(), r->d_x, S->io);
+                AMG_CUDA(cudaEventRecord(r->ev, S->io));
+                AMG_CUDA(cudaEventSynchronize(r->ev));
+            } else {
+                std::memcpy(x, r->x.data(), sizeof(double) * r->x.size());
+            }
+        }
+        drop_request(S, r.get());
+    } catch (const Error &e) {
+        drop_request(S, r.get());
+        set_last_error(e.what());
+        return e.status;
+    }
+    if (info) *info = r->info;
     return st;
 }
 
@@ -499,12 +651,21 @@ void amg_server_destroy(amg_server *S) {
         S->cv_work.notify_all();
     }
     if (S->worker.joinable()) S->worker.join();
+    for (auto &H : S->hs)
+        if (H->stream) cudaStreamSynchronize(H->stream);  // gathers into results not yet waited for
+    for (auto &kv : S->reqs) drop_request(S, kv.second.get());  // requests never waited for
+    S->reqs.clear();
     for (auto &H : S->hs) {
         if (H->ws) H->h->batch.erase(S->K);
         if (H->stream) cudaStreamDestroy(H->stream);
         if (H->done_ev) cudaEventDestroy(H->done_ev);
         if (H->hstage) cudaFreeHost(H->hstage);
     }
+    if (S->io) {
+        cudaStreamSynchronize(S->io);
+        cudaStreamDestroy(S->io);
+    }
+    if (S->pool) cudaMemPoolDestroy(S->pool);
     delete S;
 }
 

@@ -79,7 +79,7 @@ def header_struct_fields(name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("amg_options", "Options"), ("amg_solve_info", "SolveInfo"),
-                                          ("amg_level_info", "LevelInfo")])
+                                          ("amg_level_info", "LevelInfo"), ("amg_server_opts", "ServerOpts")])
 def test_binding_structs_mirror_header(cname, pyname):
     from paper_1512_04629_gb300 import amg
 
@@ -93,3 +93,6 @@ def test_option_defaults_without_gpu(libpath):
     assert (o.theta, o.max_size, o.max_levels, o.method, o.precision) == (0.25, 100, 25, amg.METHOD_SPARSE, 0)
     assert (o.lump, o.krylov, o.restart) == (amg.LUMP_DIAG, amg.KRYLOV_CG, 30)
     assert (o.k_check, o.s_levels, o.gamma_min, o.rho_max) == (3, 1, 0.01, 0.5)
+    so = amg.ServerOpts()
+    amg.lib().amg_server_opts_default(ctypes.byref(so))
+    assert (so.max_batch, so.hbm_budget, so.max_queue, so.max_it, so.stage_budget) == (32, 0, 4096, 500, 0)

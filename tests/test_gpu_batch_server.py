@@ -162,3 +162,56 @@ def test_server_rejects_and_times_out(amg):
     with pytest.raises(amg.AmgError):
         srv.submit(57, gen.rhs_uniform(A.n, 1))
     srv.close()
+
+
+def _serve(amg, hs, reqs, **opts):
+    """Submit every (hierarchy index, b) of `reqs`, then wait them in order."""
+    srv = amg.Server(max_batch=8, **opts)
+    ids = [srv.register(h) for h in hs]
+    ts = [srv.submit(ids[i], b) for i, b in reqs]
+    out = [srv.wait(t, ids[i]) for t, (i, _) in zip(ts, reqs)]
+    srv.close()
+    return out
+
+
+@pytest.mark.parametrize("stage", ["tight", "none"])
+def test_server_staging_paths_agree(amg, stage):
+    """Requests staged on the device (submit uploads, wait downloads) and
+    through the worker's host buffer give the same bits; a staging budget
+    that holds only a few vectors mixes the two paths."""
+    A1, h1 = _hier(amg, "2d5", 40)
+    A2, h2 = _hier(amg, "3d7", 14)
+    reqs = [(r % 2, gen.rhs_uniform((A1 if r % 2 == 0 else A2).n, 500 + r)) for r in range(24)]
+    ref = _serve(amg, [h1, h2], reqs)
+    budget = 3 * 8 * max(A1.n, A2.n) if stage == "tight" else -1
+    got = _serve(amg, [h1, h2], reqs, stage_budget=budget)
+    for (st0, x0, i0), (st1, x1, i1), (i, b) in zip(ref, got, reqs):
+        assert st0 == 0 and st1 == 0
+        np.testing.assert_array_equal(x1, x0)
+        assert i1.iterations == i0.iterations and i1.final_relres == i0.final_relres
+        A = A1 if i == 0 else A2
+        assert np.linalg.norm(b - A.to_scipy() @ x1) <= 1e-8 * np.linalg.norm(b) * (1 + 1e-6)
+
+
+def test_server_submit_copies_b_and_close_frees_unwaited(amg):
+    A, h = _hier(amg, "2d5", 40)
+    srv = amg.Server(max_batch=8)
+    hid = srv.register(h)
+    b = gen.rhs_uniform(A.n, 7)
+    keep = b.copy()
+    t = srv.submit(hid, b)
+    b[:] = np.nan  # the caller's buffer is free once submit returns
+    st, x, info = srv.wait(t, hid)
+    assert st == 0
+    assert np.linalg.norm(keep - A.to_scipy() @ x) <= 1e-8 * np.linalg.norm(keep) * (1 + 1e-6)
+    for r in range(12):  # results never waited for are freed by close
+        srv.submit(hid, gen.rhs_uniform(A.n, 60 + r))
+    srv.close()
+    srv2 = amg.Server(max_batch=8, stage_budget=1 << 20)
+    hid2 = srv2.register(h)
+    st, x2, _ = srv2.wait(srv2.submit(hid2, keep), hid2)
+    assert st == 0
+    np.testing.assert_array_equal(x2, x)
+    srv2.close()
+    with pytest.raises(amg.AmgError):
+        amg.Server(stage_budget=-2)
