@@ -59,6 +59,8 @@ def parse():
                         "aniso: rotated anisotropic Q1 2D 2048^2 (theta pi/8, eps 1e-3), GMRES arms "
                         "(Galerkin, Sparse, Hybrid, non-Galerkin)")
     p.add_argument("--serve-seconds", type=float, default=20.0)
+    p.add_argument("--batch-k", type=int, nargs="*", default=None,
+                   help="lognormal-batched: the widths to run (default 1 8 32 64)")
     p.add_argument("--lump", default="diag", choices=["diag", "strong"],
                    help="sparsify: diagonal lumping (Algorithm 3b, default) or full lumping to strong neighbours "
                         "(Algorithm 3)")
@@ -371,7 +373,7 @@ def run_lognormal_batched(args):
     out["fp64_single"] = {"solve_ms": ms64, "solves_per_s": 1e3 / ms64, "iterations": i64.iterations}
     del h64
     h = amg.Hierarchy.setup(A_dev, gamma=[0.0, 0.1], precision=1)
-    for k in (1, 8, 32, 64):
+    for k in args.batch_k or (1, 8, 32, 64):
         B = torch.from_numpy(np.stack([gen.rhs_uniform(A.n, c) for c in range(k)], axis=1)).cuda().contiguous()
         if k == 1:
             bb = B[:, 0].contiguous()

@@ -1,10 +1,13 @@
 // batch.cu -- multi-right-hand-side (SpMM) V-cycle kernels and batched PCG.
 //
-// SpMM layout: a group of G lanes owns a row; the lanes load G consecutive
-// (column index, value) pairs of the row with one coalesced access, then
-// broadcast them with shuffles; lane t applies each entry to its CPL columns
-// t, t+G, ... of the K-wide row block.  The matrix is read once per block of
-// K right-hand sides instead of K times.
+// SpMM layout: the K right-hand sides of a row are contiguous (row-major
+// n x K).  A group of G = K / W lanes owns a row, and lane t owns the W
+// consecutive columns W t .. W t + W - 1, moved as one 16-byte vector (W = 4
+// floats or 2 doubles).  Every lane of the group reads the row's (column,
+// value) pairs itself -- the same address across the group, served as one
+// broadcast -- and keeps the vector loads of kAhead entries in flight before
+// it uses them; each column still sums its entries in row order.  The matrix
+// is read once per block of K right-hand sides instead of K times.
 #include <cuda_bf16.h>
 
 #include "batch_ops.cuh"
@@ -19,75 +22,126 @@ constexpr int kThreads = 256;
 
 template <typename VT, typename XT> __device__ __forceinline__ XT cvt(VT v) { return (XT)v; }
 
-// lanes of this thread's G-lane group (groups never straddle a warp); the
-// groups of one warp own different rows and run different trip counts, so
-// their shuffles name only their own lanes
-template <int G> __device__ __forceinline__ unsigned group_mask() {
-    if constexpr (G == 32) {
-        return 0xffffffffu;
-    } else {
-        unsigned lane = threadIdx.x & 31u;
-        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
-    }
-}
 template <> __device__ __forceinline__ float cvt<__nv_bfloat16, float>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 enum Op { kPre = 0, kPost = 1, kSpmv = 2, kSpmvAdd = 3 };
 
-template <typename VT, typename XT, int G, int CPL, int OP>
+constexpr int kAhead = 4;  // entries whose vector loads are in flight together
+
+// 16-byte vectors of a row block (the block's base is 16-byte aligned: K is a
+// multiple of 8 and every n x K buffer starts on an allocation boundary)
+__device__ __forceinline__ void vload(const float *p, float (&x)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+}
+__device__ __forceinline__ void vload(const double *p, double (&x)[2]) {
+    const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+    x[0] = q.x; x[1] = q.y;
+}
+// for a buffer the same kernel writes (its own row only)
+__device__ __forceinline__ void vload_rw(const float *p, float (&x)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+}
+__device__ __forceinline__ void vload_rw(const double *p, double (&x)[2]) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    x[0] = q.x; x[1] = q.y;
+}
+__device__ __forceinline__ void vstore(float *p, const float (&x)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void vstore(double *p, const double (&x)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+}
+
+// acc[w] += sum over the row's entries, in entry order, of a_ij * src_j[c0 + w]
+// (times dinv_j when SCALE: the pre-smoothing's x_j = dinv_j b_j)
+template <typename VT, typename XT, int K, bool SCALE>
+__device__ __forceinline__ void row_block_sum(int32_t p0, int32_t p1, const int32_t *__restrict__ ci,
+                                              const VT *__restrict__ v, const XT *__restrict__ src,
+                                              const XT *__restrict__ dinv, int c0, XT (&acc)[16 / sizeof(XT)]) {
+    constexpr int W = 16 / sizeof(XT);
+    int32_t e = p0;
+    for (; e + kAhead <= p1; e += kAhead) {
+        int32_t j[kAhead];
+        XT a[kAhead], d[kAhead], x[kAhead][W];
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) {
+            j[q] = __ldg(ci + e + q);
+            a[q] = cvt<VT, XT>(__ldg(v + e + q));
+        }
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) {
+            vload(src + (int64_t)j[q] * K + c0, x[q]);
+            if (SCALE) d[q] = __ldg(dinv + j[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kAhead; ++q) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (SCALE) acc[w] += a[q] * (x[q][w] * d[q]);
+                else acc[w] += a[q] * x[q][w];
+            }
+        }
+    }
+    for (; e < p1; ++e) {
+        const int32_t j = __ldg(ci + e);
+        const XT a = cvt<VT, XT>(__ldg(v + e));
+        XT x[W];
+        vload(src + (int64_t)j * K + c0, x);
+        if (SCALE) {
+            const XT d = __ldg(dinv + j);
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc[w] += a * (x[w] * d);
+        } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) acc[w] += a * x[w];
+        }
+    }
+}
+
+template <typename VT, typename XT, int K, int OP>
 __global__ void __launch_bounds__(kThreads)
 spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const VT *__restrict__ v,
             const XT *__restrict__ B, const XT *__restrict__ dinv, const XT *__restrict__ X,
             XT *__restrict__ O1, XT *__restrict__ O2) {
-    constexpr int K = G * CPL;
-    int64_t g = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / G;
-    int t = threadIdx.x % G;
-    int32_t i = (int32_t)g;
-    int32_t p0 = 0, p1 = 0;
-    if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-    XT acc[CPL];
-#pragma unroll
-    for (int u = 0; u < CPL; ++u) acc[u] = XT(0);
-    const unsigned gm = group_mask<G>();
-    for (int32_t e0 = p0; e0 < p1; e0 += G) {
-        int32_t my_j = 0;
-        XT my_a = XT(0);
-        if (e0 + t < p1) { my_j = __ldg(ci + e0 + t); my_a = cvt<VT, XT>(__ldg(v + e0 + t)); }
-        int cnt = min(G, p1 - e0);
-        for (int e = 0; e < cnt; ++e) {
-            int32_t j = __shfl_sync(gm, my_j, e, G);
-            XT a = __shfl_sync(gm, my_a, e, G);
-            const XT *src = (OP == kPre ? B : X) + (int64_t)j * K + t;
-            if (OP == kPre) {
-                XT dj = __ldg(dinv + j);
-#pragma unroll
-                for (int u = 0; u < CPL; ++u) acc[u] += a * (__ldg(src + u * G) * dj);
-            } else {
-#pragma unroll
-                for (int u = 0; u < CPL; ++u) acc[u] += a * __ldg(src + u * G);
-            }
-        }
-    }
+    constexpr int W = 16 / sizeof(XT), G = K / W;
+    const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    const int32_t i = (int32_t)(g / G);
     if (i >= n) return;
-    int64_t base = (int64_t)i * K + t;
+    const int c0 = (int)(g % G) * W;
+    XT acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = XT(0);
+    row_block_sum<VT, XT, K, OP == kPre>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, OP == kPre ? B : X, dinv, c0, acc);
+    const int64_t base = (int64_t)i * K + c0;
+    XT o[W];
     if (OP == kPre) {
-        XT di = dinv[i];
+        const XT di = dinv[i];
+        XT bi[W], r[W];
+        vload(B + base, bi);
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) {
-            XT bi = B[base + u * G];
-            O1[base + u * G] = bi * di;
-            O2[base + u * G] = bi - acc[u];
+        for (int w = 0; w < W; ++w) {
+            o[w] = bi[w] * di;
+            r[w] = bi[w] - acc[w];
         }
+        vstore(O1 + base, o);
+        vstore(O2 + base, r);
     } else if (OP == kPost) {
-        XT di = dinv[i];
+        const XT di = dinv[i];
+        XT xi[W], bi[W];
+        vload(X + base, xi);
+        vload(B + base, bi);
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) O1[base + u * G] = X[base + u * G] + di * (B[base + u * G] - acc[u]);
+        for (int w = 0; w < W; ++w) o[w] = xi[w] + di * (bi[w] - acc[w]);
+        vstore(O1 + base, o);
     } else if (OP == kSpmv) {
-#pragma unroll
-        for (int u = 0; u < CPL; ++u) O1[base + u * G] = acc[u];
+        vstore(O1 + base, acc);
     } else {
+        vload_rw(O1 + base, o);
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) O1[base + u * G] += acc[u];
+        for (int w = 0; w < W; ++w) o[w] += acc[w];
+        vstore(O1 + base, o);
     }
 }
 
@@ -95,12 +149,13 @@ template <typename VT, typename XT, int OP>
 void dispatch(const CycMat<VT> &A, int K, const XT *B, const XT *dinv, const XT *X, XT *O1, XT *O2, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
-    auto blocks = [&](int G) { return div_up((int64_t)n * G, kThreads); };
+    constexpr int W = 16 / sizeof(XT);
+    auto blocks = [&](int k) { return div_up((int64_t)n * (k / W), kThreads); };
     switch (K) {
-        case 8: { spmm_kernel<VT, XT, 8, 1, OP><<<blocks(8), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 16: { spmm_kernel<VT, XT, 16, 1, OP><<<blocks(16), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 32: { spmm_kernel<VT, XT, 32, 1, OP><<<blocks(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 64: { spmm_kernel<VT, XT, 32, 2, OP><<<blocks(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 8: { spmm_kernel<VT, XT, 8, OP><<<blocks(8), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 16: { spmm_kernel<VT, XT, 16, OP><<<blocks(16), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 32: { spmm_kernel<VT, XT, 32, OP><<<blocks(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 64: { spmm_kernel<VT, XT, 64, OP><<<blocks(64), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
         default: throw Error(AMG_ERR_INVALID, "batch width must be 8, 16, 32 or 64");
     }
     AMG_CHECK_LAUNCH();
@@ -219,62 +274,48 @@ __global__ void p_update_kernel(int64_t total, int K, const double *__restrict__
     P[e] = Z[e] + sc.beta[c] * P[e];
 }
 
-template <int G, int CPL, bool RESID>
+// Q = A P (or T = B - A X when RESID) on the FP64 n x K blocks, with the
+// per-column partials of p . Ap (or ||t||^2); the row-block mapping of
+// spmm_kernel with W = 2, rows taken grid-stride
+template <int K, bool RESID>
 __global__ void __launch_bounds__(kThreads)
 ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
           const double *__restrict__ Pin, const double *__restrict__ Bin, double *__restrict__ Qout,
           double *partials) {
-    constexpr int K = G * CPL;
-    int t = threadIdx.x % G;
-    double part[CPL];
+    constexpr int W = 2, G = K / W, RPB = kThreads / G;
+    const int t = threadIdx.x % G, c0 = t * W;
+    double part[W] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * RPB + threadIdx.x / G; i < n; i += (int64_t)gridDim.x * RPB) {
+        double acc[W] = {0.0, 0.0};
+        row_block_sum<double, double, K, false>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, Pin, nullptr, c0, acc);
+        const int64_t base = i * K + c0;
+        if (RESID) {
+            double b[W], r[W];
+            vload(Bin + base, b);
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) part[u] = 0.0;
-    int rpb = kThreads / G;
-    for (int64_t i = (int64_t)blockIdx.x * rpb + threadIdx.x / G; i < ((n + rpb - 1) / rpb) * (int64_t)rpb;
-         i += (int64_t)gridDim.x * rpb) {
-        int32_t p0 = 0, p1 = 0;
-        if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-        double acc[CPL];
-#pragma unroll
-        for (int u = 0; u < CPL; ++u) acc[u] = 0.0;
-        const unsigned gm = group_mask<G>();
-        for (int32_t e0 = p0; e0 < p1; e0 += G) {
-            int32_t my_j = 0;
-            double my_a = 0.0;
-            if (e0 + t < p1) { my_j = __ldg(ci + e0 + t); my_a = __ldg(v + e0 + t); }
-            int cnt = min(G, p1 - e0);
-            for (int e = 0; e < cnt; ++e) {
-                int32_t j = __shfl_sync(gm, my_j, e, G);
-                double a = __shfl_sync(gm, my_a, e, G);
-#pragma unroll
-                for (int u = 0; u < CPL; ++u) acc[u] += a * __ldg(Pin + (int64_t)j * K + t + u * G);
+            for (int w = 0; w < W; ++w) {
+                r[w] = b[w] - acc[w];
+                part[w] += r[w] * r[w];
             }
-        }
-        if (i < n) {
+            vstore(Qout + base, r);
+        } else {
+            double p[W];
+            vload(Pin + base, p);
+            vstore(Qout + base, acc);
 #pragma unroll
-            for (int u = 0; u < CPL; ++u) {
-                int64_t e = i * K + t + u * G;
-                if (RESID) {
-                    double r = Bin[e] - acc[u];
-                    Qout[e] = r;
-                    part[u] += r * r;
-                } else {
-                    Qout[e] = acc[u];
-                    part[u] += Pin[e] * acc[u];
-                }
-            }
+            for (int w = 0; w < W; ++w) part[w] += p[w] * acc[w];
         }
     }
-    // per-column partial: slot of thread t, value u -> column t + u*G
-    __shared__ double sh[CPL][kThreads];
+    // per-column partial: column W t + w sums slot w of the threads with lane t, in thread order
+    __shared__ double sh[W][kThreads];
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) sh[u][threadIdx.x] = part[u];
+    for (int w = 0; w < W; ++w) sh[w][threadIdx.x] = part[w];
     __syncthreads();
     if (threadIdx.x < K) {
-        int col = threadIdx.x, u = col / G, tt = col % G;
-        double s = 0.0;
-        for (int r = tt; r < kThreads; r += G) s += sh[u][r];
-        partials[(size_t)col * kBatchReduceBlocks + blockIdx.x] = s;
+        const int col = threadIdx.x, tt = col / W, w = col % W;
+        double sum = 0.0;
+        for (int r = tt; r < kThreads; r += G) sum += sh[w][r];
+        partials[(size_t)col * kBatchReduceBlocks + blockIdx.x] = sum;
     }
 }
 
@@ -369,28 +410,42 @@ void p_update(int32_t n, int K, const double *Z, double *P, ColScalars sc, cudaS
     AMG_CHECK_LAUNCH();
 }
 
-template <bool RESID>
-static void launch_ap(const CycMat<double> &A, int K, const double *P, const double *B, double *Q, ColScalars sc,
-                      double *partials, unsigned *counter, cudaStream_t s) {
-    int32_t n = A.nrows;
-    auto grid = [&](int G) {
-        int64_t rpb = kThreads / G;
-        int64_t b = ((n + rpb - 1) / rpb + 3) / 4;
-        int64_t cap = std::min<int64_t>(kBatchReduceBlocks, ::amg::resident_blocks(kThreads));
-        return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
-    };
-    (void)counter;
-    int blocks = 0;
-    switch (K) {
-        case 8: blocks = grid(8); { ap_kernel<8, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
-        case 16: blocks = grid(16); { ap_kernel<16, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
-        case 32: blocks = grid(32); { ap_kernel<32, 1, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
-        case 64: blocks = grid(32); { ap_kernel<32, 2, RESID><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); } break;
-        default: throw Error(AMG_ERR_INVALID, "batch width must be 8, 16, 32 or 64");
+// one resident wave of ap_kernel blocks (at least four rows per thread group)
+template <int K, bool RESID>
+static int ap_grid(int32_t n) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ap_kernel<K, RESID>, kThreads, 0));
+        per_sm = std::max(b, 1);
     }
+    const int64_t rpb = kThreads / (K / 2);
+    const int64_t want = ((n + rpb - 1) / rpb + 3) / 4;
+    const int64_t cap = std::min<int64_t>(kBatchReduceBlocks, (int64_t)per_sm * ::amg::resident_blocks(2048));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+}
+
+template <int K, bool RESID>
+static void launch_ap_k(const CycMat<double> &A, const double *P, const double *B, double *Q, ColScalars sc,
+                        double *partials, cudaStream_t s) {
+    const int blocks = ap_grid<K, RESID>(A.nrows);
+    { ap_kernel<K, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, P, B, Q, partials); ::amg::count_launch(); }
     if (RESID) { col_finish_kernel<1, kColTt><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
     else { col_finish_kernel<1, kColAp><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
+}
+
+template <bool RESID>
+static void launch_ap(const CycMat<double> &A, int K, const double *P, const double *B, double *Q, ColScalars sc,
+                      double *partials, unsigned *counter, cudaStream_t s) {
+    (void)counter;
+    switch (K) {
+        case 8: launch_ap_k<8, RESID>(A, P, B, Q, sc, partials, s); break;
+        case 16: launch_ap_k<16, RESID>(A, P, B, Q, sc, partials, s); break;
+        case 32: launch_ap_k<32, RESID>(A, P, B, Q, sc, partials, s); break;
+        case 64: launch_ap_k<64, RESID>(A, P, B, Q, sc, partials, s); break;
+        default: throw Error(AMG_ERR_INVALID, "batch width must be 8, 16, 32 or 64");
+    }
 }
 
 void ap(const CycMat<double> &A, int K, const double *P, double *Q, ColScalars sc, double *partials,
