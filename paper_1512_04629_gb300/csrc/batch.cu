@@ -53,12 +53,21 @@ __device__ __forceinline__ void vstore(float *p, const float (&x)[4]) {
 __device__ __forceinline__ void vstore(double *p, const double (&x)[2]) {
     *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
 }
+// the FP32 cycle's finest post-smoothing writes the FP64 correction itself
+// (4 floats widened exactly into 32 bytes of doubles) instead of a separate
+// conversion pass.  Its input stays the FP32 copy of the residual: a gather
+// that rounded FP64 neighbours on load would convert every value once per
+// row that uses it, on GB300's narrow FP64 pipe.
+__device__ __forceinline__ void vstore(double *p, const float (&x)[4]) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2((double)x[0], (double)x[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2((double)x[2], (double)x[3]);
+}
 
 // acc[w] += sum over the row's entries, in entry order, of a_ij * src_j[c0 + w]
 // (times dinv_j when SCALE: the pre-smoothing's x_j = dinv_j b_j)
-template <typename VT, typename XT, int K, bool SCALE>
+template <typename VT, typename XT, typename ST, int K, bool SCALE>
 __device__ __forceinline__ void row_block_sum(int32_t p0, int32_t p1, const int32_t *__restrict__ ci,
-                                              const VT *__restrict__ v, const XT *__restrict__ src,
+                                              const VT *__restrict__ v, const ST *__restrict__ src,
                                               const XT *__restrict__ dinv, int c0, XT (&acc)[16 / sizeof(XT)]) {
     constexpr int W = 16 / sizeof(XT);
     int32_t e = p0;
@@ -100,11 +109,13 @@ __device__ __forceinline__ void row_block_sum(int32_t p0, int32_t p1, const int3
     }
 }
 
-template <typename VT, typename XT, int K, int OP>
+// BT: type of B (the right-hand side); OT: type of O1 for the
+// post-smoothing (double on the FP32 cycle's level 0, else XT)
+template <typename VT, typename XT, typename BT, typename OT, int K, int OP>
 __global__ void __launch_bounds__(kThreads)
 spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const VT *__restrict__ v,
-            const XT *__restrict__ B, const XT *__restrict__ dinv, const XT *__restrict__ X,
-            XT *__restrict__ O1, XT *__restrict__ O2) {
+            const BT *__restrict__ B, const XT *__restrict__ dinv, const XT *__restrict__ X,
+            OT *__restrict__ O1, XT *__restrict__ O2) {
     constexpr int W = 16 / sizeof(XT), G = K / W;
     const int64_t g = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     const int32_t i = (int32_t)(g / G);
@@ -113,10 +124,11 @@ spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     XT acc[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) acc[w] = XT(0);
-    row_block_sum<VT, XT, K, OP == kPre>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, OP == kPre ? B : X, dinv, c0, acc);
+    if constexpr (OP == kPre) row_block_sum<VT, XT, BT, K, true>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, B, dinv, c0, acc);
+    else row_block_sum<VT, XT, XT, K, false>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, X, dinv, c0, acc);
     const int64_t base = (int64_t)i * K + c0;
     XT o[W];
-    if (OP == kPre) {
+    if constexpr (OP == kPre) {
         const XT di = dinv[i];
         XT bi[W], r[W];
         vload(B + base, bi);
@@ -127,7 +139,7 @@ spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
         }
         vstore(O1 + base, o);
         vstore(O2 + base, r);
-    } else if (OP == kPost) {
+    } else if constexpr (OP == kPost) {
         const XT di = dinv[i];
         XT xi[W], bi[W];
         vload(X + base, xi);
@@ -135,7 +147,7 @@ spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
 #pragma unroll
         for (int w = 0; w < W; ++w) o[w] = xi[w] + di * (bi[w] - acc[w]);
         vstore(O1 + base, o);
-    } else if (OP == kSpmv) {
+    } else if constexpr (OP == kSpmv) {
         vstore(O1 + base, acc);
     } else {
         vload_rw(O1 + base, o);
@@ -145,17 +157,17 @@ spmm_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict
     }
 }
 
-template <typename VT, typename XT, int OP>
-void dispatch(const CycMat<VT> &A, int K, const XT *B, const XT *dinv, const XT *X, XT *O1, XT *O2, cudaStream_t s) {
+template <typename VT, typename XT, int OP, typename BT = XT, typename OT = XT>
+void dispatch(const CycMat<VT> &A, int K, const BT *B, const XT *dinv, const XT *X, OT *O1, XT *O2, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
     constexpr int W = 16 / sizeof(XT);
     auto blocks = [&](int k) { return div_up((int64_t)n * (k / W), kThreads); };
     switch (K) {
-        case 8: { spmm_kernel<VT, XT, 8, OP><<<blocks(8), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 16: { spmm_kernel<VT, XT, 16, OP><<<blocks(16), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 32: { spmm_kernel<VT, XT, 32, OP><<<blocks(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
-        case 64: { spmm_kernel<VT, XT, 64, OP><<<blocks(64), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 8: { spmm_kernel<VT, XT, BT, OT, 8, OP><<<blocks(8), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 16: { spmm_kernel<VT, XT, BT, OT, 16, OP><<<blocks(16), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 32: { spmm_kernel<VT, XT, BT, OT, 32, OP><<<blocks(32), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
+        case 64: { spmm_kernel<VT, XT, BT, OT, 64, OP><<<blocks(64), kThreads, 0, s>>>(n, A.rp, A.ci, A.v, B, dinv, X, O1, O2); ::amg::count_launch(); } break;
         default: throw Error(AMG_ERR_INVALID, "batch width must be 8, 16, 32 or 64");
     }
     AMG_CHECK_LAUNCH();
@@ -287,7 +299,7 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
     double part[W] = {0.0, 0.0};
     for (int64_t i = (int64_t)blockIdx.x * RPB + threadIdx.x / G; i < n; i += (int64_t)gridDim.x * RPB) {
         double acc[W] = {0.0, 0.0};
-        row_block_sum<double, double, K, false>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, Pin, nullptr, c0, acc);
+        row_block_sum<double, double, double, K, false>(__ldg(rp + i), __ldg(rp + i + 1), ci, v, Pin, nullptr, c0, acc);
         const int64_t base = i * K + c0;
         if (RESID) {
             double b[W], r[W];
@@ -377,16 +389,16 @@ int batch_width(int k) {
 
 template <typename VT, typename XT>
 void pre_smooth_residual(const CycMat<VT> &A, int K, const XT *B, const XT *dinv, XT *X, XT *R, cudaStream_t s) {
-    dispatch<VT, XT, kPre>(A, K, B, dinv, nullptr, X, R, s);
+    dispatch<VT, XT, kPre, XT, XT>(A, K, B, dinv, nullptr, X, R, s);
 }
-template <typename VT, typename XT>
-void post_smooth(const CycMat<VT> &A, int K, const XT *X, const XT *B, const XT *dinv, XT *XO, cudaStream_t s) {
-    dispatch<VT, XT, kPost>(A, K, B, dinv, X, XO, nullptr, s);
+template <typename VT, typename XT, typename OT>
+void post_smooth(const CycMat<VT> &A, int K, const XT *X, const XT *B, const XT *dinv, OT *XO, cudaStream_t s) {
+    dispatch<VT, XT, kPost, XT, OT>(A, K, B, dinv, X, XO, nullptr, s);
 }
 template <typename VT, typename XT>
 void spmm(const CycMat<VT> &A, int K, const XT *X, XT *Y, bool accumulate, cudaStream_t s) {
-    if (accumulate) dispatch<VT, XT, kSpmvAdd>(A, K, nullptr, nullptr, X, Y, nullptr, s);
-    else dispatch<VT, XT, kSpmv>(A, K, nullptr, nullptr, X, Y, nullptr, s);
+    if (accumulate) dispatch<VT, XT, kSpmvAdd, XT, XT>(A, K, nullptr, nullptr, X, Y, nullptr, s);
+    else dispatch<VT, XT, kSpmv, XT, XT>(A, K, nullptr, nullptr, X, Y, nullptr, s);
 }
 template <typename XT>
 void coarse_solve(int32_t n, int K, const double *inv, const XT *B, XT *X, cudaStream_t s) {
@@ -494,14 +506,25 @@ template <typename XT> void from_cycle(const XT *src, double *dst, int64_t n, cu
     AMG_CHECK_LAUNCH();
 }
 
-#define AMG_BINST(VT, XT)                                                                                       \
-    template void pre_smooth_residual<VT, XT>(const CycMat<VT> &, int, const XT *, const XT *, XT *, XT *, cudaStream_t); \
-    template void post_smooth<VT, XT>(const CycMat<VT> &, int, const XT *, const XT *, const XT *, XT *, cudaStream_t); \
-    template void spmm<VT, XT>(const CycMat<VT> &, int, const XT *, XT *, bool, cudaStream_t);
-AMG_BINST(double, double)
-AMG_BINST(float, float)
-AMG_BINST(__nv_bfloat16, float)
-#undef AMG_BINST
+#define AMG_PINST(VT, XT) \
+    template void pre_smooth_residual<VT, XT>(const CycMat<VT> &, int, const XT *, const XT *, XT *, XT *, cudaStream_t);
+AMG_PINST(double, double)
+AMG_PINST(float, float)
+AMG_PINST(__nv_bfloat16, float)
+#undef AMG_PINST
+#define AMG_QINST(VT, XT, OT) \
+    template void post_smooth<VT, XT, OT>(const CycMat<VT> &, int, const XT *, const XT *, const XT *, OT *, cudaStream_t);
+AMG_QINST(double, double, double)
+AMG_QINST(float, float, float)
+AMG_QINST(__nv_bfloat16, float, float)
+AMG_QINST(float, float, double)
+AMG_QINST(__nv_bfloat16, float, double)
+#undef AMG_QINST
+#define AMG_SINST(VT, XT) template void spmm<VT, XT>(const CycMat<VT> &, int, const XT *, XT *, bool, cudaStream_t);
+AMG_SINST(double, double)
+AMG_SINST(float, float)
+AMG_SINST(__nv_bfloat16, float)
+#undef AMG_SINST
 template void coarse_solve<double>(int32_t, int, const double *, const double *, double *, cudaStream_t);
 template void coarse_solve<float>(int32_t, int, const double *, const float *, float *, cudaStream_t);
 template void to_cycle<float>(const double *, float *, int64_t, cudaStream_t);

@@ -44,7 +44,7 @@ BatchWS &batch_workspace(Hierarchy &h, int K, cudaStream_t s) {
     if (h.opt.precision != AMG_PREC_FP64) {
         size_t fb = sizeof(float) * ((size_t)h.lev[0]->n() * K + kPad);
         w->R32.alloc(fb);
-        w->Z32.alloc(fb);
+        if (L == 1) w->Z32.alloc(fb);  // deeper cycles write Z themselves
     }
     w->sc_buf.alloc(sizeof(double) * 7 * K + sizeof(int) * 3 * K);
     AMG_CUDA(cudaMemsetAsync(w->sc_buf.ptr, 0, w->sc_buf.bytes, s));
@@ -69,25 +69,37 @@ void batch_push_flags(BatchWS &w, cudaStream_t s) {
     AMG_CUDA(cudaMemcpyAsync(w.sc.active, w.h_i, sizeof(int) * 2 * w.K, cudaMemcpyHostToDevice, s));
 }
 
+// level l's smoothers; the finest post-smoothing writes Z0 of type OT0
+// (double on the FP32 cycle: no separate conversion pass back)
 template <typename XT>
-static void batch_vcycle_impl(Hierarchy &h, BatchWS &w, const XT *B0, XT *Z0, cudaStream_t s) {
-    int L = h.nlev(), K = w.K;
-    if (L == 1) {
-        bat::coarse_solve<XT>(h.coarse_n, K, h.coarse_inv.as<double>(), B0, Z0, s);
-        return;
+static void pre_level(Level &V, int K, const XT *b, XT *x, XT *r, cudaStream_t s) {
+    if constexpr (sizeof(XT) == 8) {
+        bat::pre_smooth_residual<double, double>(op_mat<double>(V), K, b, dinv_of<XT>(V), x, r, s);
+    } else if (V.vbytes == 2) {
+        bat::pre_smooth_residual<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), K, b, dinv_of<XT>(V), x, r, s);
+    } else {
+        bat::pre_smooth_residual<float, float>(op_mat<float>(V), K, b, dinv_of<XT>(V), x, r, s);
     }
+}
+template <typename XT, typename OT>
+static void post_level(Level &V, int K, const XT *x, const XT *b, OT *out, cudaStream_t s) {
+    if constexpr (sizeof(XT) == 8) {
+        bat::post_smooth<double, double, OT>(op_mat<double>(V), K, x, b, dinv_of<XT>(V), out, s);
+    } else if (V.vbytes == 2) {
+        bat::post_smooth<__nv_bfloat16, float, OT>(op_mat<__nv_bfloat16>(V), K, x, b, dinv_of<XT>(V), out, s);
+    } else {
+        bat::post_smooth<float, float, OT>(op_mat<float>(V), K, x, b, dinv_of<XT>(V), out, s);
+    }
+}
+
+// Z0 = M B0 over the hierarchy's levels (at least two)
+template <typename XT, typename OT0>
+static void batch_vcycle_impl(Hierarchy &h, BatchWS &w, const XT *B0, OT0 *Z0, cudaStream_t s) {
+    int L = h.nlev(), K = w.K;
     for (int l = 0; l + 1 < L; ++l) {
         Level &V = *h.lev[l];
-        const XT *b = l == 0 ? B0 : w.b[l].as<XT>();
         XT *x = w.x[l].as<XT>(), *r = w.r[l].as<XT>();
-        if constexpr (sizeof(XT) == 8) {
-            bat::pre_smooth_residual<double, double>(op_mat<double>(V), K, b, dinv_of<XT>(V), x, r, s);
-        } else {
-            if (V.vbytes == 2)
-                bat::pre_smooth_residual<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), K, b, dinv_of<XT>(V), x, r, s);
-            else
-                bat::pre_smooth_residual<float, float>(op_mat<float>(V), K, b, dinv_of<XT>(V), x, r, s);
-        }
+        pre_level<XT>(V, K, l == 0 ? B0 : w.b[l].as<XT>(), x, r, s);
         bat::spmm<XT, XT>(r_mat<XT>(V), K, r, w.b[l + 1].as<XT>(), false, s);
     }
     bat::coarse_solve<XT>(h.coarse_n, K, h.coarse_inv.as<double>(), w.b[L - 1].as<XT>(), w.xo[L - 1].as<XT>(), s);
@@ -95,28 +107,28 @@ static void batch_vcycle_impl(Hierarchy &h, BatchWS &w, const XT *B0, XT *Z0, cu
         Level &V = *h.lev[l];
         XT *x = w.x[l].as<XT>();
         bat::spmm<XT, XT>(p_mat<XT>(V), K, w.xo[l + 1].as<XT>(), x, true, s);
-        const XT *b = l == 0 ? B0 : w.b[l].as<XT>();
-        XT *out = l == 0 ? Z0 : w.xo[l].as<XT>();
-        if constexpr (sizeof(XT) == 8) {
-            bat::post_smooth<double, double>(op_mat<double>(V), K, x, b, dinv_of<XT>(V), out, s);
-        } else {
-            if (V.vbytes == 2)
-                bat::post_smooth<__nv_bfloat16, float>(op_mat<__nv_bfloat16>(V), K, x, b, dinv_of<XT>(V), out, s);
-            else
-                bat::post_smooth<float, float>(op_mat<float>(V), K, x, b, dinv_of<XT>(V), out, s);
-        }
+        if (l == 0) post_level<XT, OT0>(V, K, x, B0, Z0, s);
+        else post_level<XT, XT>(V, K, x, w.b[l].as<XT>(), w.xo[l].as<XT>(), s);
     }
 }
 
 // Z = M R for all K columns
 void batch_vcycle(Hierarchy &h, BatchWS &w, cudaStream_t s) {
     int64_t nk = (int64_t)h.lev[0]->n() * w.K;
-    if (h.opt.precision == AMG_PREC_FP64) {
-        batch_vcycle_impl<double>(h, w, w.R.as<double>(), w.Z.as<double>(), s);
-    } else {
-        bat::to_cycle<float>(w.R.as<double>(), w.R32.as<float>(), nk, s);
-        batch_vcycle_impl<float>(h, w, w.R32.as<float>(), w.Z32.as<float>(), s);
+    const bool fp64 = h.opt.precision == AMG_PREC_FP64;
+    if (fp64) {
+        if (h.nlev() == 1)
+            bat::coarse_solve<double>(h.coarse_n, w.K, h.coarse_inv.as<double>(), w.R.as<double>(), w.Z.as<double>(), s);
+        else
+            batch_vcycle_impl<double, double>(h, w, w.R.as<double>(), w.Z.as<double>(), s);
+        return;
+    }
+    bat::to_cycle<float>(w.R.as<double>(), w.R32.as<float>(), nk, s);
+    if (h.nlev() == 1) {  // the coarse solve alone, in FP32 vectors
+        bat::coarse_solve<float>(h.coarse_n, w.K, h.coarse_inv.as<double>(), w.R32.as<float>(), w.Z32.as<float>(), s);
         bat::from_cycle<float>(w.Z32.as<float>(), w.Z.as<double>(), nk, s);
+    } else {
+        batch_vcycle_impl<float, double>(h, w, w.R32.as<float>(), w.Z.as<double>(), s);
     }
 }
 

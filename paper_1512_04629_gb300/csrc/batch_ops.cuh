@@ -18,8 +18,10 @@ int batch_width(int k);
 
 template <typename VT, typename XT>
 void pre_smooth_residual(const CycMat<VT> &A, int K, const XT *B, const XT *dinv, XT *X, XT *R, cudaStream_t s);
-template <typename VT, typename XT>
-void post_smooth(const CycMat<VT> &A, int K, const XT *X, const XT *B, const XT *dinv, XT *XO, cudaStream_t s);
+// OT: type of the output -- XT, or double for the FP32 cycle's finest level,
+// which writes the FP64 correction Z directly
+template <typename VT, typename XT, typename OT = XT>
+void post_smooth(const CycMat<VT> &A, int K, const XT *X, const XT *B, const XT *dinv, OT *XO, cudaStream_t s);
 template <typename VT, typename XT>
 void spmm(const CycMat<VT> &A, int K, const XT *X, XT *Y, bool accumulate, cudaStream_t s);
 template <typename XT>

@@ -169,7 +169,7 @@ int64_t batch_bytes(const Hierarchy &h, int K) {
     int64_t cyc = 0;
     for (int l = 0; l < h.nlev(); ++l) cyc += 4 * xb * (int64_t)h.lev[l]->n() * K;
     int64_t n0 = h.lev[0]->n();
-    int64_t pcg = 7 * 8 * n0 * K + (xb == 4 ? 2 * 4 * n0 * K : 0);
+    int64_t pcg = 7 * 8 * n0 * K + (xb == 4 ? (h.nlev() == 1 ? 2 : 1) * 4 * n0 * K : 0);
     return cyc + pcg + (1 << 20);
 }
 
