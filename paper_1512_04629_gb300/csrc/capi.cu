@@ -82,9 +82,8 @@ void upload_csr(const amg_csr *A, DevCSR &M, cudaStream_t s) {
     }
     if (A->on_device) {
         int32_t ends[2];
-        AMG_CUDA(cudaMemcpyAsync(&ends[0], M.rp(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA(cudaMemcpyAsync(&ends[1], M.rp() + A->n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA(cudaStreamSynchronize(s));
+        read_back(&ends[0], M.rp(), sizeof(int32_t), s);
+        read_back(&ends[1], M.rp() + A->n, sizeof(int32_t), s);
         require(ends[0] == 0 && ends[1] == A->nnz, "rowptr[0] must be 0 and rowptr[n] = nnz");
     }
 }

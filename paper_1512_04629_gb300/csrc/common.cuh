@@ -157,10 +157,17 @@ void exclusive_scan_i64_async(const int64_t *in, int64_t *out, int64_t n, int64_
 // int32 scan whose total the caller already knows (no read-back)
 void exclusive_scan_i32_known(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
 
+// Copies `bytes` (at most kReadBackMax) of device memory to dst once the
+// stream's work before it has finished.  A one-block kernel writes them into
+// mapped pinned host memory of the calling thread and the stream is
+// synchronised: on this part that round trip costs what the synchronisation
+// alone costs, where a copy into pageable (pinned) memory added 5 (3) us.
+constexpr size_t kReadBackMax = 256;
+void read_back(void *dst, const void *dsrc, size_t bytes, cudaStream_t s);
+
 template <typename T> T read_scalar(const T *dptr, cudaStream_t s) {
     T v;
-    AMG_CUDA(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, s));
-    AMG_CUDA(cudaStreamSynchronize(s));
+    read_back(&v, dptr, sizeof(T), s);
     return v;
 }
 

@@ -931,8 +931,7 @@ int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStre
     { max_col_offset_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, rp, ci, out.as<int>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     int h[2];
-    AMG_CUDA(cudaMemcpyAsync(h, out.ptr, sizeof(h), cudaMemcpyDeviceToHost, s));
-    AMG_CUDA(cudaStreamSynchronize(s));
+    read_back(h, out.ptr, sizeof(h), s);
     if (max_row) *max_row = h[1];
     return h[0];
 }

@@ -1770,8 +1770,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         }
         AMG_CHECK_LAUNCH();
         int hc[kBatch + 1];
-        AMG_CUDA(cudaMemcpyAsync(hc, dc + done, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA(cudaStreamSynchronize(s));
+        read_back(hc, dc + done, sizeof(hc), s);
         if (!first && hc[0] != last) throw Error(AMG_ERR_CUDA, "PMIS counters inconsistent");
         // every round that started with undecided points must have decided some
         for (int b = 0; b < kBatch; ++b)
@@ -1901,8 +1900,8 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     // product-bound offsets of the one-pass numeric kernel (total into the same record)
     exclusive_scan_i64_async(ub.as<int64_t>(), obase.as<int64_t>(), n, &dc->total_ub, s);
     SpgemmCounts hc;
-    AMG_CUDA(cudaMemcpyAsync(&hc, dc, sizeof(hc), cudaMemcpyDeviceToHost, s));
-    AMG_CUDA(cudaStreamSynchronize(s));
+    static_assert(sizeof(SpgemmCounts) <= kReadBackMax, "SpgemmCounts read back in one piece");
+    read_back(&hc, dc, sizeof(hc), s);
     const int32_t *nb = hc.nb;
     const int64_t max_ub = (int64_t)hc.max_ub_global;
     const int64_t total_ub = hc.total_ub;

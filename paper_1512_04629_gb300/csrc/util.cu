@@ -1,4 +1,5 @@
 // util.cu -- device buffers, thread-local error text, exclusive scans.
+#include <cstring>
 #include <atomic>
 #include <mutex>
 #include <string>
@@ -28,6 +29,38 @@ int resident_blocks(int threads_per_block) {
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 const char *last_error_cstr() { return g_last_error.c_str(); }
+
+namespace {
+__global__ void read_back_kernel(const unsigned char *__restrict__ src, unsigned char *__restrict__ dst, int bytes) {
+    for (int i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = src[i];
+}
+// one mapped pinned buffer per thread and device, kept for the thread's life
+struct MappedBuf {
+    unsigned char *host = nullptr, *dev = nullptr;
+};
+constexpr int kMaxDevices = 64;
+thread_local MappedBuf g_mapped[kMaxDevices];
+}  // namespace
+
+void read_back(void *dst, const void *dsrc, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    if (bytes > kReadBackMax) throw Error(AMG_ERR_INVALID, "read_back: more than kReadBackMax bytes");
+    int dev = 0;
+    AMG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) throw Error(AMG_ERR_INVALID, "read_back: device index out of range");
+    MappedBuf &m = g_mapped[dev];
+    if (!m.host) {
+        void *h = nullptr, *d = nullptr;
+        AMG_CUDA(cudaHostAlloc(&h, kReadBackMax, cudaHostAllocMapped));
+        AMG_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+        m.host = static_cast<unsigned char *>(h);
+        m.dev = static_cast<unsigned char *>(d);
+    }
+    { read_back_kernel<<<1, 32, 0, s>>>(static_cast<const unsigned char *>(dsrc), m.dev, (int)bytes); count_launch(); }
+    AMG_CHECK_LAUNCH();
+    AMG_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(dst, m.host, bytes);
+}
 
 namespace {
 thread_local int g_idle_depth = 0;
