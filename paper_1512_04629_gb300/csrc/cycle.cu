@@ -416,11 +416,12 @@ __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double 
 }
 
 // q = A p (SELL-32, one thread per row) and p . q; each warp walks slices
-// with a stride of the grid's warp count
-template <bool D16, bool SHORT>
+// with a stride of the grid's warp count.  RESID: q = b - A p and q . q (the
+// true residual of p = x)
+template <bool D16, bool SHORT, bool RESID>
 __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
-               SellIdx ix, const double *__restrict__ sv, const double *__restrict__ p,
+               SellIdx ix, const double *__restrict__ sv, const double *__restrict__ p, const double *__restrict__ b,
                double *__restrict__ q, PcgScalars *sc, Reduce red) {
     block_partials_begin();
     double part[1] = {0.0};
@@ -431,8 +432,14 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
         double s = sell_row_sum<double, double, D16, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
-        q[i] = s;
-        part[0] += p[i] * s;
+        if (RESID) {
+            const double e = b[i] - s;
+            q[i] = e;
+            part[0] += e * e;
+        } else {
+            q[i] = s;
+            part[0] += p[i] * s;
+        }
     }
     block_partials<1>(part, red);
 }
@@ -776,19 +783,27 @@ static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgSc
     launch_finish<1, kFinAp>(blocks, red, sc, s);
 }
 
+// the SELL forms of A p and of the true residual; returns the block count
+template <bool RESID>
+static int launch_ap_sell(const CycMat<double> &A, const double *p, const double *b, double *q, PcgScalars *sc,
+                          Reduce red, cudaStream_t s) {
+    const int blocks = reduce_blocks(A.nrows);
+    const SellIdx ix{A.sci, A.sd};
+    const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
+    if (A.sd && sh)
+        { ap_sell_kernel<true, true, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+    else if (A.sd)
+        { ap_sell_kernel<true, false, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+    else if (sh)
+        { ap_sell_kernel<false, true, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+    else
+        { ap_sell_kernel<false, false, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+    return blocks;
+}
+
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     if (A.variant == AMG_SPMV_SELL32 && A.sv) {
-        int blocks = reduce_blocks(A.nrows);
-        const SellIdx ix{A.sci, A.sd};
-        const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
-        if (A.sd && sh)
-            { ap_sell_kernel<true, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
-        else if (A.sd)
-            { ap_sell_kernel<true, false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
-        else if (sh)
-            { ap_sell_kernel<false, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
-        else
-            { ap_sell_kernel<false, false><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, q, sc, red); ::amg::count_launch(); }
+        const int blocks = launch_ap_sell<false>(A, p, nullptr, q, sc, red, s);
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -883,6 +898,12 @@ void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgSca
 
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s) {
+    if (A.variant == AMG_SPMV_SELL32 && A.sv) {  // the operator's tuned SELL copy, as A p uses
+        const int blocks = launch_ap_sell<true>(A, x, b, t, sc, red, s);
+        launch_finish<1, kFinTt>(blocks, red, sc, s);
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     int blocks = reduce_blocks((int64_t)A.nrows * 4);
     { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
     launch_finish<1, kFinTt>(blocks, red, sc, s);
