@@ -475,18 +475,16 @@ amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
         *out = nullptr;
         amg_server_opts opt;
         if (o) opt = *o; else amg_server_opts_default(&opt);
-        if (opt.max_batch < 1 || opt.max_batch > 64 || opt.max_queue < 1 || opt.max_it < 1 || opt.hbm_budget < 0) {
-            set_last_error("server options out of range (max_batch 1..64, max_queue >= 1, max_it >= 1)");
+        if (opt.max_batch < 1 || opt.max_batch > 64 || opt.max_queue < 1 || opt.max_it < 1 || opt.hbm_budget < 0 ||
+            opt.stage_budget < -1) {
+            set_last_error("server options out of range (max_batch 1..64, max_queue >= 1, max_it >= 1, "
+                           "hbm_budget >= 0, stage_budget >= -1)");
             return AMG_ERR_INVALID;
         }
         auto S = std::make_unique<amg_server>();
         S->opt = opt;
         S->K = bat::batch_width(opt.max_batch);
         AMG_CUDA(cudaGetDevice(&S->device));
-        if (opt.stage_budget < -1) {
-            set_last_error("stage_budget must be >= -1");
-            return AMG_ERR_INVALID;
-        }
         if (opt.hbm_budget > 0) {
             S->budget = opt.hbm_budget;
         } else {
