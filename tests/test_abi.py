@@ -111,3 +111,37 @@ def test_server_options_rejected_before_any_cuda_call(libpath, field, value):
     assert L.amg_server_create(ctypes.byref(o), ctypes.byref(out)) == amg.ERR_INVALID
     assert not out.value
     assert b"out of range" in L.amg_last_error()
+
+
+@pytest.mark.parametrize("theta,kw,gamma,msg", [
+    (1.5, {}, None, "theta"), (float("nan"), {}, None, "theta"),
+    (0.25, dict(max_size=0), None, "max_size"), (0.25, dict(max_levels=0), None, "max_levels"),
+    (0.25, dict(max_levels=65), None, "max_levels"), (0.25, dict(method=9), None, "method"),
+    (0.25, dict(precision=7), None, "precision"), (0.25, dict(k_check=0), None, "k_check"),
+    (0.25, dict(check_every=0), None, "check_every"), (0.25, dict(lump=4), None, "lump"),
+    (0.25, dict(krylov=3), None, "krylov"), (0.25, dict(restart=0), None, "restart"),
+    (0.25, dict(restart=513), None, "restart"),
+    (0.25, {}, [0.5, 0.1], "level 0 is never sparsified"), (0.25, {}, [0.0, float("nan")], "finite"),
+    (0.25, {}, [0.0, -0.1], ">= 0"),
+])
+def test_setup_rejects_bad_arguments_before_any_cuda_call(libpath, theta, kw, gamma, msg):
+    import amg_inputs as gen
+    from paper_1512_04629_gb300 import amg
+
+    A = gen.poisson2d_5pt(6)
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.setup(A, theta=theta, gamma=gamma, **kw)
+    assert e.value.status == amg.ERR_INVALID
+    assert msg in str(e.value)
+
+
+def test_setup_rejects_a_non_square_matrix(libpath):
+    import numpy as np
+
+    from paper_1512_04629_gb300 import amg
+
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    A = amg.csr_struct(rp, np.array([0, 2], dtype=np.int32), np.array([1.0, 1.0]), ncols=3)
+    with pytest.raises(amg.AmgError) as e:
+        amg.Hierarchy.setup(A)
+    assert e.value.status == amg.ERR_INVALID and "square" in str(e.value)
