@@ -408,11 +408,10 @@ void coarse_solve(int32_t n, int K, const double *inv, const XT *B, XT *X, cudaS
 }
 
 void rz(int32_t n, int K, const double *R, const double *Z, const double *Q, ColScalars sc, int flexible,
-        double *partials, unsigned *counter, cudaStream_t s) {
+        double *partials, cudaStream_t s) {
     int blocks = grid_for(n, K);
     { rz_kernel<<<blocks, kThreads, 0, s>>>(n, K, R, Z, Q, partials); ::amg::count_launch(); }
     { col_finish_kernel<2, kColRz><<<K, kThreads, 0, s>>>(blocks, partials, sc, flexible); ::amg::count_launch(); }
-    (void)counter;
     AMG_CHECK_LAUNCH();
 }
 
@@ -449,8 +448,7 @@ static void launch_ap_k(const CycMat<double> &A, const double *P, const double *
 
 template <bool RESID>
 static void launch_ap(const CycMat<double> &A, int K, const double *P, const double *B, double *Q, ColScalars sc,
-                      double *partials, unsigned *counter, cudaStream_t s) {
-    (void)counter;
+                      double *partials, cudaStream_t s) {
     switch (K) {
         case 8: launch_ap_k<8, RESID>(A, P, B, Q, sc, partials, s); break;
         case 16: launch_ap_k<16, RESID>(A, P, B, Q, sc, partials, s); break;
@@ -461,21 +459,20 @@ static void launch_ap(const CycMat<double> &A, int K, const double *P, const dou
 }
 
 void ap(const CycMat<double> &A, int K, const double *P, double *Q, ColScalars sc, double *partials,
-        unsigned *counter, cudaStream_t s) {
-    launch_ap<false>(A, K, P, nullptr, Q, sc, partials, counter, s);
+        cudaStream_t s) {
+    launch_ap<false>(A, K, P, nullptr, Q, sc, partials, s);
 }
 
 void residual(const CycMat<double> &A, int K, const double *B, const double *X, double *T, ColScalars sc,
-              double *partials, unsigned *counter, cudaStream_t s) {
-    launch_ap<true>(A, K, X, B, T, sc, partials, counter, s);
+              double *partials, cudaStream_t s) {
+    launch_ap<true>(A, K, X, B, T, sc, partials, s);
 }
 
 void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, ColScalars sc,
-               double *partials, unsigned *counter, cudaStream_t s) {
+               double *partials, cudaStream_t s) {
     int blocks = grid_for(n, K);
     { xr_kernel<<<blocks, kThreads, 0, s>>>(n, K, P, Q, X, R, sc, partials); ::amg::count_launch(); }
     { col_finish_kernel<1, kColXr><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
-    (void)counter;
     AMG_CHECK_LAUNCH();
 }
 

@@ -53,8 +53,6 @@ BatchWS &batch_workspace(Hierarchy &h, int K, cudaStream_t s) {
     w->sc = bat::ColScalars{d, d + K, d + 2 * K, d + 3 * K, d + 4 * K, d + 5 * K, d + 6 * K, iv, iv + K};
     w->mask.alloc(sizeof(int) * K);
     w->partials.alloc(sizeof(double) * 3 * bat::kMaxCols * bat::kBatchReduceBlocks);
-    w->counter.alloc(sizeof(unsigned) * 4);
-    AMG_CUDA(cudaMemsetAsync(w->counter.ptr, 0, w->counter.bytes, s));
     AMG_CUDA(cudaMallocHost(&w->h_d, sizeof(double) * 7 * K));
     AMG_CUDA(cudaMallocHost(&w->h_i, sizeof(int) * 3 * K));
     std::memset(w->h_d, 0, sizeof(double) * 7 * K);
@@ -145,12 +143,11 @@ static void batch_iteration_body(Hierarchy &h, BatchWS &w, cudaStream_t s) {
     int K = w.K;
     int flexible = h.opt.precision != AMG_PREC_FP64;
     batch_vcycle(h, w, s);
-    bat::rz(n, K, w.R.as<double>(), w.Z.as<double>(), w.Q.as<double>(), w.sc, flexible, w.partials.as<double>(),
-            w.counter.as<unsigned>(), s);
+    bat::rz(n, K, w.R.as<double>(), w.Z.as<double>(), w.Q.as<double>(), w.sc, flexible, w.partials.as<double>(), s);
     bat::p_update(n, K, w.Z.as<double>(), w.P.as<double>(), w.sc, s);
-    bat::ap(a0(h), K, w.P.as<double>(), w.Q.as<double>(), w.sc, w.partials.as<double>(), w.counter.as<unsigned>(), s);
+    bat::ap(a0(h), K, w.P.as<double>(), w.Q.as<double>(), w.sc, w.partials.as<double>(), s);
     bat::xr_update(n, K, w.P.as<double>(), w.Q.as<double>(), w.X.as<double>(), w.R.as<double>(), w.sc,
-                   w.partials.as<double>(), w.counter.as<unsigned>(), s);
+                   w.partials.as<double>(), s);
     AMG_CUDA(cudaMemcpyAsync(w.h_d, w.sc_buf.ptr, sizeof(double) * 6 * K, cudaMemcpyDeviceToHost, s));
 }
 
@@ -188,8 +185,7 @@ void batch_iteration(Hierarchy &h, BatchWS &w, cudaStream_t s) {
 
 // T = B - A X and tt per column
 void batch_true_residual(Hierarchy &h, BatchWS &w, cudaStream_t s) {
-    bat::residual(a0(h), w.K, w.B.as<double>(), w.X.as<double>(), w.T.as<double>(), w.sc, w.partials.as<double>(),
-                  w.counter.as<unsigned>(), s);
+    bat::residual(a0(h), w.K, w.B.as<double>(), w.X.as<double>(), w.T.as<double>(), w.sc, w.partials.as<double>(), s);
     AMG_CUDA(cudaMemcpyAsync(w.h_tt(), w.sc.tt, sizeof(double) * w.K, cudaMemcpyDeviceToHost, s));
 }
 

@@ -36,15 +36,15 @@ struct ColScalars {
 
 // Z = M R done by the caller; then:
 void rz(int32_t n, int K, const double *R, const double *Z, const double *Q, ColScalars sc, int flexible,
-        double *partials, unsigned *counter, cudaStream_t s);
+        double *partials, cudaStream_t s);
 void p_update(int32_t n, int K, const double *Z, double *P, ColScalars sc, cudaStream_t s);
 void ap(const CycMat<double> &A, int K, const double *P, double *Q, ColScalars sc, double *partials,
-        unsigned *counter, cudaStream_t s);
+        cudaStream_t s);
 void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, ColScalars sc,
-               double *partials, unsigned *counter, cudaStream_t s);
+               double *partials, cudaStream_t s);
 // T = B - A X, tt[c] = ||T_c||^2
 void residual(const CycMat<double> &A, int K, const double *B, const double *X, double *T, ColScalars sc,
-              double *partials, unsigned *counter, cudaStream_t s);
+              double *partials, cudaStream_t s);
 // column c of an n x K block <- / -> a contiguous n-vector
 void scatter_column(int32_t n, int K, int c, const double *v, double *M, cudaStream_t s);
 void gather_column(int32_t n, int K, int c, const double *M, double *v, cudaStream_t s);

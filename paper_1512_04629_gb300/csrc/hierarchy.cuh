@@ -85,7 +85,7 @@ struct BatchWS {
     std::vector<DevBuf> b, x, r, xo;
     DevBuf B, X, R, Z, P, Q, T;
     DevBuf R32, Z32;
-    DevBuf sc_buf, partials, counter, mask;
+    DevBuf sc_buf, partials, mask;
     bat::ColScalars sc{};
     double *h_d = nullptr;  // pinned: rho, pq, alpha, beta, rr, zq, tt (K each)
     int *h_i = nullptr;     // pinned: active, start, mask (K each)
