@@ -333,7 +333,7 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
 
 __global__ void __launch_bounds__(kThreads)
 xr_kernel(int32_t n, int K, const double *__restrict__ P, const double *__restrict__ Q, double *__restrict__ X,
-          double *__restrict__ R, ColScalars sc, double *partials) {
+          double *__restrict__ R, float *__restrict__ R32, ColScalars sc, double *partials) {
     int c = threadIdx.x % K;
     int rpb = kThreads / K;
     double alpha = sc.active[c] ? sc.alpha[c] : 0.0;
@@ -346,14 +346,17 @@ xr_kernel(int32_t n, int K, const double *__restrict__ P, const double *__restri
             r -= alpha * Q[e];
             R[e] = r;
         }
+        if (R32) R32[e] = (float)r;  // the next FP32 cycle's input, every column
         v[0] += r * r;
     }
     col_partials<1>(v, K, partials);
 }
 
-__global__ void scatter_kernel(int32_t n, int K, int c, const double *v, double *M) {
+__global__ void scatter_kernel(int32_t n, int K, int c, const double *v, double *M, float *M32) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) M[i * K + c] = v[i];
+    if (i >= n) return;
+    M[i * K + c] = v[i];
+    if (M32) M32[i * K + c] = (float)v[i];
 }
 __global__ void gather_kernel(int32_t n, int K, int c, const double *M, double *v) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -363,9 +366,11 @@ __global__ void zero_col_kernel(int32_t n, int K, int c, double *M) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) M[i * K + c] = 0.0;
 }
-__global__ void copy_masked_kernel(int64_t total, int K, const double *T, double *R, const int *mask) {
+__global__ void copy_masked_kernel(int64_t total, int K, const double *T, double *R, float *R32, const int *mask) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < total && mask[e % K]) R[e] = T[e];
+    if (e >= total || !mask[e % K]) return;
+    R[e] = T[e];
+    if (R32) R32[e] = (float)T[e];
 }
 
 template <typename XT> __global__ void to_cycle_kernel(const double *src, XT *dst, int64_t n) {
@@ -468,16 +473,16 @@ void residual(const CycMat<double> &A, int K, const double *B, const double *X, 
     launch_ap<true>(A, K, X, B, T, sc, partials, s);
 }
 
-void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, ColScalars sc,
+void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, float *R32, ColScalars sc,
                double *partials, cudaStream_t s) {
     int blocks = grid_for(n, K);
-    { xr_kernel<<<blocks, kThreads, 0, s>>>(n, K, P, Q, X, R, sc, partials); ::amg::count_launch(); }
+    { xr_kernel<<<blocks, kThreads, 0, s>>>(n, K, P, Q, X, R, R32, sc, partials); ::amg::count_launch(); }
     { col_finish_kernel<1, kColXr><<<K, kThreads, 0, s>>>(blocks, partials, sc, 0); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
-void scatter_column(int32_t n, int K, int c, const double *v, double *M, cudaStream_t s) {
-    { scatter_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, K, c, v, M); ::amg::count_launch(); }
+void scatter_column(int32_t n, int K, int c, const double *v, double *M, cudaStream_t s, float *M32) {
+    { scatter_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, K, c, v, M, M32); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 void gather_column(int32_t n, int K, int c, const double *M, double *v, cudaStream_t s) {
@@ -488,9 +493,9 @@ void zero_column(int32_t n, int K, int c, double *M, cudaStream_t s) {
     { zero_col_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, K, c, M); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
-void copy_masked_columns(int32_t n, int K, const double *T, double *R, const int *mask, cudaStream_t s) {
+void copy_masked_columns(int32_t n, int K, const double *T, double *R, const int *mask, cudaStream_t s, float *R32) {
     int64_t total = (int64_t)n * K;
-    { copy_masked_kernel<<<div_up(total, kThreads), kThreads, 0, s>>>(total, K, T, R, mask); ::amg::count_launch(); }
+    { copy_masked_kernel<<<div_up(total, kThreads), kThreads, 0, s>>>(total, K, T, R, R32, mask); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 

@@ -44,6 +44,7 @@ BatchWS &batch_workspace(Hierarchy &h, int K, cudaStream_t s) {
     if (h.opt.precision != AMG_PREC_FP64) {
         size_t fb = sizeof(float) * ((size_t)h.lev[0]->n() * K + kPad);
         w->R32.alloc(fb);
+        AMG_CUDA(cudaMemsetAsync(w->R32.ptr, 0, fb, s));  // kept equal to (float) R by every writer of R
         if (L == 1) w->Z32.alloc(fb);  // deeper cycles write Z themselves
     }
     w->sc_buf.alloc(sizeof(double) * 7 * K + sizeof(int) * 3 * K);
@@ -121,7 +122,8 @@ void batch_vcycle(Hierarchy &h, BatchWS &w, cudaStream_t s) {
             batch_vcycle_impl<double, double>(h, w, w.R.as<double>(), w.Z.as<double>(), s);
         return;
     }
-    bat::to_cycle<float>(w.R.as<double>(), w.R32.as<float>(), nk, s);
+    // R32 = (float) R already: written with R by the x, r update, admission
+    // and residual replacement
     if (h.nlev() == 1) {  // the coarse solve alone, in FP32 vectors
         bat::coarse_solve<float>(h.coarse_n, w.K, h.coarse_inv.as<double>(), w.R32.as<float>(), w.Z32.as<float>(), s);
         bat::from_cycle<float>(w.Z32.as<float>(), w.Z.as<double>(), nk, s);
@@ -146,7 +148,7 @@ static void batch_iteration_body(Hierarchy &h, BatchWS &w, cudaStream_t s) {
     bat::rz(n, K, w.R.as<double>(), w.Z.as<double>(), w.Q.as<double>(), w.sc, flexible, w.partials.as<double>(), s);
     bat::p_update(n, K, w.Z.as<double>(), w.P.as<double>(), w.sc, s);
     bat::ap(a0(h), K, w.P.as<double>(), w.Q.as<double>(), w.sc, w.partials.as<double>(), s);
-    bat::xr_update(n, K, w.P.as<double>(), w.Q.as<double>(), w.X.as<double>(), w.R.as<double>(), w.sc,
+    bat::xr_update(n, K, w.P.as<double>(), w.Q.as<double>(), w.X.as<double>(), w.R.as<double>(), w.R32.as<float>(), w.sc,
                    w.partials.as<double>(), s);
     AMG_CUDA(cudaMemcpyAsync(w.h_d, w.sc_buf.ptr, sizeof(double) * 6 * K, cudaMemcpyDeviceToHost, s));
 }
@@ -227,6 +229,7 @@ amg_status solve_batch(Hierarchy &h, int k, const double *B, double *X, bool on_
     AMG_CUDA(cudaMemsetAsync(w.P.ptr, 0, nb, s));
     AMG_CUDA(cudaMemsetAsync(w.Q.ptr, 0, nb, s));
     AMG_CUDA(cudaMemcpyAsync(w.R.ptr, w.B.ptr, nb, cudaMemcpyDeviceToDevice, s));
+    if (w.R32.ptr) bat::to_cycle<float>(w.R.as<double>(), w.R32.as<float>(), (int64_t)n * K, s);
     // ||b_c|| through the true residual at X = 0
     batch_true_residual(h, w, s);
     AMG_CUDA(cudaStreamSynchronize(s));
@@ -282,7 +285,8 @@ amg_status solve_batch(Hierarchy &h, int k, const double *B, double *X, bool on_
             }
             if (replace) {
                 AMG_CUDA(cudaMemcpyAsync(w.mask.ptr, w.h_mask(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
-                bat::copy_masked_columns(n, K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), s);
+                bat::copy_masked_columns(n, K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), s,
+                                         w.R32.as<float>());
             }
             for (int c = 0; c < K; ++c) w.h_mask()[c] = 0;
         }

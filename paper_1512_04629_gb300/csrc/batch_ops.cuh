@@ -40,17 +40,21 @@ void rz(int32_t n, int K, const double *R, const double *Z, const double *Q, Col
 void p_update(int32_t n, int K, const double *Z, double *P, ColScalars sc, cudaStream_t s);
 void ap(const CycMat<double> &A, int K, const double *P, double *Q, ColScalars sc, double *partials,
         cudaStream_t s);
-void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, ColScalars sc,
+// R32 (FP32 cycles; else nullptr): also written with every column's new
+// residual, which the next V-cycle reads -- no separate conversion pass
+void xr_update(int32_t n, int K, const double *P, const double *Q, double *X, double *R, float *R32, ColScalars sc,
                double *partials, cudaStream_t s);
 // T = B - A X, tt[c] = ||T_c||^2
 void residual(const CycMat<double> &A, int K, const double *B, const double *X, double *T, ColScalars sc,
               double *partials, cudaStream_t s);
 // column c of an n x K block <- / -> a contiguous n-vector
-void scatter_column(int32_t n, int K, int c, const double *v, double *M, cudaStream_t s);
+// (M32: when given, column c of the FP32 copy of M too)
+void scatter_column(int32_t n, int K, int c, const double *v, double *M, cudaStream_t s, float *M32 = nullptr);
 void gather_column(int32_t n, int K, int c, const double *M, double *v, cudaStream_t s);
 void zero_column(int32_t n, int K, int c, double *M, cudaStream_t s);
 // R = T for the columns flagged in mask (residual replacement)
-void copy_masked_columns(int32_t n, int K, const double *T, double *R, const int *mask, cudaStream_t s);
+void copy_masked_columns(int32_t n, int K, const double *T, double *R, const int *mask, cudaStream_t s,
+                         float *R32 = nullptr);
 
 template <typename XT> void to_cycle(const double *src, XT *dst, int64_t n, cudaStream_t s);
 template <typename XT> void from_cycle(const XT *src, double *dst, int64_t n, cudaStream_t s);

@@ -257,7 +257,7 @@ bool admit(amg_server *S, HState &H) {
             src = H.dstage.as<double>();
         }
         bat::scatter_column(H.n, w.K, c, src, w.B.as<double>(), H.stream);
-        bat::scatter_column(H.n, w.K, c, src, w.R.as<double>(), H.stream);
+        bat::scatter_column(H.n, w.K, c, src, w.R.as<double>(), H.stream, w.R32.as<float>());
         bat::zero_column(H.n, w.K, c, w.X.as<double>(), H.stream);
         bat::zero_column(H.n, w.K, c, w.P.as<double>(), H.stream);
         bat::zero_column(H.n, w.K, c, w.Q.as<double>(), H.stream);
@@ -396,7 +396,8 @@ void after_residual(amg_server *S, HState &H) {
     }
     if (replace) {
         AMG_CUDA(cudaMemcpyAsync(w.mask.ptr, w.h_mask(), sizeof(int) * w.K, cudaMemcpyHostToDevice, H.stream));
-        bat::copy_masked_columns(H.n, w.K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), H.stream);
+        bat::copy_masked_columns(H.n, w.K, w.T.as<double>(), w.R.as<double>(), w.mask.as<int>(), H.stream,
+                                 w.R32.as<float>());
     }
     for (int c = 0; c < S->K; ++c) w.h_mask()[c] = 0;
     if (changed) {
