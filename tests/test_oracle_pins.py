@@ -1022,3 +1022,41 @@ def test_nongalerkin_full_lumping_rescues_aggressive_dropping():
     for l in range(1, hf.num_levels):
         H = hf.matrix(l, "A").todense()
         np.testing.assert_allclose(H, H.T, atol=1e-13 * np.abs(H).max())
+
+
+# ---------------------------------------------------------------------------
+# l1 smoother diagonal d_i = sum_j |a_ij| (the relaxation weight of the
+# l1-Jacobi smoother on every level)
+# ---------------------------------------------------------------------------
+def test_l1_diag_closed_form_on_2d_poisson():
+    N = 7
+    d = oracle.l1_diag(gen.poisson2d_5pt(N)).reshape(N, N)
+    # 4 on the diagonal plus one per neighbour inside the grid (Dirichlet boundary)
+    expect = np.full((N, N), 8.0)
+    expect[0, :] -= 1
+    expect[-1, :] -= 1
+    expect[:, 0] -= 1
+    expect[:, -1] -= 1
+    assert np.array_equal(d, expect)
+    assert d[0, 0] == 6.0 and d[0, 3] == 7.0 and d[3, 3] == 8.0
+
+
+def test_l1_diag_of_zero_row_sum_m_matrix_is_twice_the_diagonal():
+    # graph Laplacian of a path with weights: every row sums to zero, off-diagonals negative
+    w = np.array([1.5, 0.25, 2.0, 3.0])
+    n = len(w) + 1
+    L = np.zeros((n, n))
+    for k, wk in enumerate(w):
+        L[k, k] += wk
+        L[k + 1, k + 1] += wk
+        L[k, k + 1] -= wk
+        L[k + 1, k] -= wk
+    A = sp.csr_matrix(L)
+    d = oracle.l1_diag(A)
+    assert np.array_equal(d, 2.0 * np.diag(L))
+
+
+def test_l1_diag_counts_positive_couplings_by_absolute_value():
+    # row 0: 5 -2 +3  -> 10;  row 1: -2 4 0 -> 6;  row 2: +3 0 9 -> 12
+    A = sp.csr_matrix(np.array([[5.0, -2.0, 3.0], [-2.0, 4.0, 0.0], [3.0, 0.0, 9.0]]))
+    assert np.array_equal(oracle.l1_diag(A), [10.0, 6.0, 12.0])
