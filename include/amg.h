@@ -252,7 +252,21 @@ amg_status amg_timing_get(const amg_hierarchy *h, int kind, int level, int64_t *
 amg_status amg_timing_reset(amg_hierarchy *h);
 
 /* Save / load the Galerkin hierarchy, C/F markers, minimal-pattern flags and
- * drop tolerances to a file (little-endian binary, documented in DESIGN). */
+ * drop tolerances to a file.  The file is little-endian binary:
+ *   char magic[4] = "AMGH"; u32 version = 1; u32 L (levels, 1..25);
+ *   then for each level l = 0 .. L-1:
+ *     i64 n, i64 nnz; i32 rowptr[n+1]; i32 col[nnz]; f64 val[nnz]
+ *       (the retained Galerkin operator A_l, rows sorted by column);
+ *     f64 gamma_l (the drop tolerance of level l; level 0's is ignored);
+ *     if l > 0:     u8 inM[nnz] (1 = entry of A_l in the minimal pattern M);
+ *     if l < L - 1: i8 cf[n] (1 = C point, -1 = F point);
+ *                   i64 n_coarse, i64 nnz_P; i32 rowptr[n+1]; i32 col[nnz_P];
+ *                   f64 val[nnz_P] (the interpolation P_l, n x n_coarse).
+ * Load rebuilds everything else (R, sparsified operators, smoother
+ * diagonals, the coarsest inverse) on the device from these arrays with the
+ * given options.  A non-Galerkin hierarchy retains no Galerkin operator and
+ * cannot be saved (AMG_ERR_INVALID); a short or foreign file gives
+ * AMG_ERR_INVALID. */
 amg_status amg_hierarchy_save(const amg_hierarchy *h, const char *path);
 amg_status amg_hierarchy_load(const char *path, const amg_options *opt, void *stream,
                               amg_hierarchy **out);
@@ -264,19 +278,23 @@ const char *amg_last_error(void);
 /*
  * amg_residual_noalloc -- r = b - A_0 x and rnorm[0] = ||r||_2 for the
  * finest operator of h, for callers that cannot allocate device memory at
- * the moment they call (a CUDA graph being recorded by stream capture, a
- * framework or real-time loop whose device memory comes only from its own
- * pool, a fully committed memory budget).  The paper has no counterpart: it
- * is a service of this library, not a step of the method.
- * b, x, r, rnorm: device pointers (b, x, r of length n; rnorm one double,
- * written on the device -- the call does not synchronise).  The call
- * allocates nothing: its reduction scratch is a fixed array of about 530 KB
- * in the library image, held by every GPU that loads the library until the
- * process exits.  n is limited to 67,108,864 rows (AMG_ERR_INVALID beyond).
- * The first call on a device looks up that array's device address; make it
- * before any stream capture.  All calls share the scratch and its counters
- * are cleared at the start of each call, so calls that overlap on the GPU
- * race: order them (e.g. one stream).
+ * the moment they call: a framework or real-time loop whose device memory is
+ * handed out only by its own pool (a cudaMalloc there would bypass its
+ * accounting or stall the loop), or a process whose memory budget is already
+ * fully committed, where an allocation would fail.  The paper has no
+ * counterpart: it is a service of this library, not a step of the method.
+ * b, x, r, rnorm: device pointers on h's device (b, x, r of length n; rnorm
+ * one double, written on the device -- the call does not synchronise).  The
+ * call must be made with h's device current; another current device, or
+ * pointers that are host memory or belong to another device, give
+ * AMG_ERR_INVALID and launch nothing.  The call allocates nothing: its
+ * reduction scratch is a fixed array of about 530 KB in the library image,
+ * held by every GPU that loads the library until the process exits.  n is
+ * limited to 67,108,864 rows (AMG_ERR_INVALID beyond).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, once
+ * per device).  All calls share the scratch and its counters are cleared at
+ * the start of each call, so calls that overlap on the GPU race: order them
+ * (e.g. one stream).
  */
 amg_status amg_residual_noalloc(const amg_hierarchy *h, const double *b, const double *x, double *r,
                                 double *rnorm, void *stream);

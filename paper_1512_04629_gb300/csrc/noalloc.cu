@@ -1,12 +1,12 @@
 // noalloc.cu -- residual and its norm for callers that cannot allocate.
 //
 // Some callers must not allocate device memory at the moment they call: code
-// that is recording a CUDA graph by stream capture (cudaMalloc is not a
-// stream operation and breaks or is refused inside a capture), code that runs
-// under a framework or real-time loop whose device memory is handed out only
-// by its own pool, and callers whose memory budget is already fully
-// committed.  For them, amg_residual_noalloc computes r = b - A_0 x and
-// ||r||_2 (the quantity an outer iteration checks for convergence) with its
+// that runs under a framework or real-time loop whose device memory is handed
+// out only by its own pool (a cudaMalloc there would bypass the pool's
+// accounting, or stall the loop while the driver maps memory), and callers
+// whose memory budget is already fully committed, where an allocation would
+// fail.  For them, amg_residual_noalloc computes r = b - A_0 x and ||r||_2
+// (the quantity an outer iteration checks for convergence) with its
 // reduction scratch in a fixed array that the library image carries in
 // device memory, so the call allocates nothing.
 //
@@ -130,13 +130,14 @@ residual_noalloc_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t
     if (threadIdx.x == 0) *norm_out = sqrt(tot);
 }
 
-bool on_device(const void *p) {
+// True for device (or managed) memory that belongs to device `dev`.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -150,8 +151,12 @@ extern "C" amg_status amg_residual_noalloc(const amg_hierarchy *H, const double 
         int64_t n = L0.A.nrows;
         require(n <= kMaxRows, "amg_residual_noalloc: n = " + std::to_string(n) +
                                    " exceeds the fixed scratch capacity of 67,108,864 rows");
-        require(on_device(b) && on_device(x) && on_device(r) && on_device(rnorm),
-                "amg_residual_noalloc: b, x, r and rnorm must be device memory");
+        int dev = -1;
+        AMG_CUDA(cudaGetDevice(&dev));
+        require(dev == H->h.device, "amg_residual_noalloc: the current device (" + std::to_string(dev) +
+                                        ") is not the hierarchy's device (" + std::to_string(H->h.device) + ")");
+        require(on_device(b, dev) && on_device(x, dev) && on_device(r, dev) && on_device(rnorm, dev),
+                "amg_residual_noalloc: b, x, r and rnorm must be device memory of the hierarchy's device");
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         Scratch *sc = scratch_for_current_device();
         AMG_CUDA(cudaMemsetAsync(sc->counters, 0, sizeof(sc->counters), s));

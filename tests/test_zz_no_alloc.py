@@ -1,11 +1,12 @@
 """amg_residual_noalloc: the residual entry point that allocates nothing.
 
-It serves callers that cannot allocate device memory when they call -- e.g.
-code recording a CUDA graph by stream capture, or code whose device memory
-comes only from its own pool.  Its output is checked against the existing
-entry point amg_solve, whose info.final_relres is ||b - A x|| / ||b||, on two
-calls in a row (the shared scratch must be reusable).  This file is collected
-last so a failure here cannot hide the other tests.
+It serves callers that cannot allocate device memory when they call: code
+whose device memory comes only from its own pool (a framework or real-time
+loop), or a process whose memory budget is fully committed.  Its output is
+checked against the existing entry point amg_solve, whose info.final_relres
+is ||b - A x|| / ||b||, on two calls in a row (the shared scratch must be
+reusable).  This file is collected last so a failure here cannot hide the
+other tests.
 """
 import ctypes as C
 
@@ -74,4 +75,5 @@ def test_residual_noalloc_rejects_host_pointers(amg):
     st = lib.amg_residual_noalloc(h.handle, bh.ctypes.data_as(C.c_void_p), xh.ctypes.data_as(C.c_void_p),
                                   rh.ctypes.data_as(C.c_void_p), nh.ctypes.data_as(C.c_void_p), None)
     assert st == 1
-    assert b"device memory" in lib.amg_last_error()
+    assert b"device memory of the hierarchy's device" in lib.amg_last_error()
+
