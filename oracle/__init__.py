@@ -50,6 +50,11 @@ class _Info(C.Structure):
                 ("conv_factor", C.c_double)]
 
 
+class _Window(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("action", C.c_int32), ("rstart", C.c_double),
+                ("rend", C.c_double), ("factor", C.c_double)]
+
+
 def _load():
     global _lib
     with _lock:
@@ -98,8 +103,13 @@ def _load():
                                            P(_Info)]
         lib.orc_vcycle.argtypes = [vp, vp, vp]
         lib.orc_pcg.argtypes = [vp, vp, vp, C.c_double, C.c_int32, P(_Info)]
+        lib.orc_pcg_ex.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32, C.c_double,
+                                   P(_Info)]
         lib.orc_adaptive_solve.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
                                            C.c_int32, C.c_double, C.c_double, P(_Info)]
+        lib.orc_adaptive_solve_ex.argtypes = [vp, vp, vp, C.c_double, C.c_int32, C.c_int32,
+                                              C.c_int32, C.c_double, C.c_double, C.c_double,
+                                              P(_Window), C.c_int32, P(C.c_int32), P(_Info)]
         lib.orc_free.argtypes = [vp]
         lib.orc_csr_free.argtypes = [P(_CSR)]
         lib.orc_num_levels.argtypes = [vp]
@@ -316,6 +326,14 @@ def gamma_schedule(gamma, s: int, gamma_min: float = 0.01):
 # --------------------------------------------------------------------------
 # hierarchy
 # --------------------------------------------------------------------------
+# names of the ORC_WIN_* codes of an Algorithm 5 check window
+WIN_ACTIONS = ["continue", "restart_here", "restart_back", "converged", "nothing_left",
+               "breakdown_stop", "breakdown_back", "diverged"]
+
+# status codes of the oracle's solvers
+OK, INVALID, OOM, NOT_CONVERGED, DIVERGED, BREAKDOWN = 0, 1, 2, 4, 5, 6
+
+
 @dataclass
 class SolveInfo:
     iterations: int
@@ -413,21 +431,40 @@ class Hierarchy:
         self._lib.orc_vcycle(self._h, _ptr(b), _ptr(x))
         return x
 
-    def pcg(self, b, tol: float = 1e-8, max_it: int = 500):
+    def pcg(self, b, tol: float = 1e-8, max_it: int = 500, k: int | None = None,
+            div_factor: float | None = None):
+        """PCG; k / div_factor set the divergence test (windows of k steps,
+        growth factor div_factor, 0 = off; default 3 and 1e3)."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         info = _Info()
-        self._lib.orc_pcg(self._h, _ptr(b), _ptr(x), tol, max_it, C.byref(info))
+        if k is None and div_factor is None:
+            self._lib.orc_pcg(self._h, _ptr(b), _ptr(x), tol, max_it, C.byref(info))
+        else:
+            self._lib.orc_pcg_ex(self._h, _ptr(b), _ptr(x), tol, max_it, 3 if k is None else k,
+                                 1e3 if div_factor is None else div_factor, C.byref(info))
         return x, _info(info)
 
     def adaptive_solve(self, b, tol: float = 1e-8, max_it: int = 500, k: int = 3, s: int = 1,
-                       gamma_min: float = 0.01, rho_max: float = 0.5):
+                       gamma_min: float = 0.01, rho_max: float = 0.5, div_factor: float = 1e3,
+                       trace: bool = False):
+        """Algorithm 5 around PCG.  With trace=True also returns the list of
+        check windows: dicts with steps, action (WIN_* names), rstart, rend,
+        factor."""
         b = np.ascontiguousarray(b, dtype=np.float64)
         x = np.zeros_like(b)
         info = _Info()
-        self._lib.orc_adaptive_solve(self._h, _ptr(b), _ptr(x), tol, max_it, k, s, gamma_min,
-                                     rho_max, C.byref(info))
-        return x, _info(info)
+        cap = max_it + 1
+        win = (_Window * cap)()
+        nwin = C.c_int32(0)
+        self._lib.orc_adaptive_solve_ex(self._h, _ptr(b), _ptr(x), tol, max_it, k, s, gamma_min,
+                                        rho_max, div_factor, win, cap, C.byref(nwin),
+                                        C.byref(info))
+        if not trace:
+            return x, _info(info)
+        tr = [dict(steps=w.steps, action=WIN_ACTIONS[w.action], rstart=w.rstart, rend=w.rend,
+                   factor=w.factor) for w in win[: min(nwin.value, cap)]]
+        return x, _info(info), tr
 
     def gmres(self, b, tol: float = 1e-8, max_it: int = 500, restart: int = 30):
         b = np.ascontiguousarray(b, dtype=np.float64)

@@ -16,6 +16,7 @@
 #define ORC_INVALID 1
 #define ORC_OOM 2
 #define ORC_NOT_CONVERGED 4
+#define ORC_DIVERGED 5
 #define ORC_BREAKDOWN 6
 
 /* ------------------------------------------------------------------------ */
@@ -1110,17 +1111,17 @@ int orc_vcycle(orc_hier *h, const double *b, double *x) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int32_t n;
-    double *r, *z, *p, *q;
+    double *r, *z, *p, *q, *xs;
     double rho;
 } pcg_state;
 
 typedef struct {
-    int32_t steps, converged, breakdown, replacements;
+    int32_t steps, converged, breakdown, replacements, diverged;
     double rnorm; /* residual norm at the end of the run */
 } pcg_run;
 
 static void pcg_free(pcg_state *s) {
-    free(s->r); free(s->z); free(s->p); free(s->q);
+    free(s->r); free(s->z); free(s->p); free(s->q); free(s->xs);
     memset(s, 0, sizeof(*s));
 }
 
@@ -1131,7 +1132,8 @@ static int pcg_alloc(pcg_state *s, int32_t n) {
     s->z = (double *)malloc(sz);
     s->p = (double *)malloc(sz);
     s->q = (double *)malloc(sz);
-    if (!s->r || !s->z || !s->p || !s->q) {
+    s->xs = (double *)malloc(sz);
+    if (!s->r || !s->z || !s->p || !s->q || !s->xs) {
         pcg_free(s);
         return ORC_OOM;
     }
@@ -1149,8 +1151,16 @@ static double pcg_start(orc_hier *h, pcg_state *s, const double *b, const double
     return norm2(n, s->r);
 }
 
+/* Divergence, the failure Algorithm 5 exists to recover from (Section 6:  */
+/* with too many entries dropped the method stops converging).  Reading:    */
+/* with divf > 0 the run is cut into windows of kwin steps, counted from    */
+/* its start and again from every residual replacement; at the end of a     */
+/* window the recurrence residual norm is compared with the one at the      */
+/* window's start, and if it grew by more than the factor divf -- or if it  */
+/* is non-finite after any step -- x goes back to the window's starting     */
+/* iterate and the run stops as diverged.  divf = 0 turns the test off.     */
 static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, double bnorm,
-                        double tol, int32_t max_steps, pcg_run *run) {
+                        double tol, int32_t max_steps, int32_t kwin, double divf, pcg_run *run) {
     const orc_csr *A = h->lev[0].A;
     int32_t n = s->n;
     memset(run, 0, sizeof(*run));
@@ -1159,7 +1169,10 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
         run->converged = 1;
         return;
     }
+    int32_t w = 0;            /* steps since the window count (re)started */
+    double rws = run->rnorm;  /* residual norm at the current window's start */
     while (run->steps < max_steps) {
+        if (divf > 0.0 && w % kwin == 0) memcpy(s->xs, x, sizeof(double) * (size_t)n);
         orc_spmv(A, s->p, s->q);
         double pq = dot(n, s->p, s->q);
         run->steps++;
@@ -1171,6 +1184,16 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
         for (int32_t i = 0; i < n; ++i) x[i] += alpha * s->p[i];
         for (int32_t i = 0; i < n; ++i) s->r[i] -= alpha * s->q[i];
         run->rnorm = norm2(n, s->r);
+        w++;
+        if (divf > 0.0) {
+            if (!isfinite(run->rnorm) || (w % kwin == 0 && run->rnorm > divf * rws)) {
+                memcpy(x, s->xs, sizeof(double) * (size_t)n);
+                run->rnorm = rws;
+                run->diverged = 1;
+                return;
+            }
+            if (w % kwin == 0) rws = run->rnorm;
+        }
         if (run->rnorm <= tol * bnorm) {
             orc_spmv(A, x, s->q);
             for (int32_t i = 0; i < n; ++i) s->q[i] = b[i] - s->q[i];
@@ -1182,6 +1205,8 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
             }
             memcpy(s->r, s->q, sizeof(double) * (size_t)n);
             run->replacements++;
+            w = 0;
+            rws = tn;
         }
         orc_vcycle(h, s->r, s->z);
         double rho_new = dot(n, s->r, s->z);
@@ -1203,10 +1228,14 @@ static double true_resnorm(orc_hier *h, const double *b, const double *x, double
     return sqrt(s);
 }
 
-/* PCG from x0 = 0 to ||b - A x|| / ||b|| <= tol (at most max_it steps). */
-int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info) {
+/* PCG from x0 = 0 to ||b - A x|| / ||b|| <= tol (at most max_it steps),  */
+/* stopping as diverged when the residual grows by more than divf over a    */
+/* window of kwin steps (see pcg_iterate; divf = 0: no such test).          */
+int orc_pcg_ex(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t kwin,
+               double divf, orc_info *info) {
     int32_t n = h->lev[0].A->nrows;
     memset(info, 0, sizeof(*info));
+    if (kwin < 1 || !(divf == 0.0 || divf >= 1.0)) return ORC_INVALID;
     for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
     double bnorm = norm2(n, b);
     if (bnorm == 0.0) return ORC_OK;
@@ -1214,14 +1243,21 @@ int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
     if (pcg_alloc(&s, n) != ORC_OK) return ORC_OOM;
     double r0 = pcg_start(h, &s, b, x);
     pcg_run run;
-    pcg_iterate(h, &s, b, x, bnorm, tol, max_it, &run);
+    pcg_iterate(h, &s, b, x, bnorm, tol, max_it, kwin, divf, &run);
     info->iterations = run.steps;
     info->replacements = run.replacements;
     info->final_relres = true_resnorm(h, b, x, s.q) / bnorm;
     info->conv_factor = run.steps > 0 ? pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
-    info->status = run.converged ? ORC_OK : (run.breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
+    info->status = run.converged ? ORC_OK
+                 : run.diverged  ? ORC_DIVERGED
+                 : (run.breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
     pcg_free(&s);
     return info->status;
+}
+
+/* the defaults of the library: windows of 3 steps, growth factor 1e3 */
+int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info) {
+    return orc_pcg_ex(h, b, x, tol, max_it, 3, 1e3, info);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1232,13 +1268,33 @@ int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
 /* Above it (or on a breakdown), while some coarse gamma is > 0, one        */
 /* reintroduction step is taken and PCG restarts, from the current x unless */
 /* the residual grew over the window, then from the window's starting x.    */
-/* Otherwise the Krylov run continues unchanged.                            */
+/* Otherwise the Krylov run continues unchanged.  Divergence (Section 6):   */
+/* when the residual grew by more than divf over the window (or is          */
+/* non-finite) and nothing is left to reintroduce, x goes back to the       */
+/* window's starting iterate and the solve stops as diverged (divf = 0:     */
+/* never).  With trace != NULL each window is recorded (at most cap).       */
 /* ------------------------------------------------------------------------ */
-int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
-                       int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info) {
+static void record(orc_window *trace, int32_t cap, int32_t *ntrace, int32_t steps, double rstart, double rend,
+                   double factor, int32_t action) {
+    if (!trace || !ntrace) return;
+    if (*ntrace < cap) {
+        orc_window *w = &trace[*ntrace];
+        w->steps = steps;
+        w->action = action;
+        w->rstart = rstart;
+        w->rend = rend;
+        w->factor = factor;
+    }
+    (*ntrace)++;
+}
+
+int orc_adaptive_solve_ex(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                          int32_t k, int32_t s, double gamma_min, double rho_max, double divf,
+                          orc_window *trace, int32_t cap, int32_t *ntrace, orc_info *info) {
     int32_t n = h->lev[0].A->nrows;
     memset(info, 0, sizeof(*info));
-    if (k < 1 || s < 1) return ORC_INVALID;
+    if (ntrace) *ntrace = 0;
+    if (k < 1 || s < 1 || !(divf == 0.0 || divf >= 1.0)) return ORC_INVALID;
     for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
     double bnorm = norm2(n, b);
     if (bnorm == 0.0) return ORC_OK;
@@ -1252,23 +1308,27 @@ int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int3
     pcg_start(h, &st, b, x);
     double rstart = bnorm, rend = bnorm;
     int32_t total = 0;
-    int converged = 0, breakdown = 0, status = ORC_OK;
+    int converged = 0, breakdown = 0, diverged = 0, status = ORC_OK;
     int32_t changed[64];
     while (total < max_it) {
         memcpy(xs, x, sizeof(double) * (size_t)n);
         pcg_run run;
         int32_t steps = (max_it - total < k) ? max_it - total : k;
-        pcg_iterate(h, &st, b, x, bnorm, tol, steps, &run);
+        pcg_iterate(h, &st, b, x, bnorm, tol, steps, k, 0.0, &run);
         total += run.steps;
         info->replacements += run.replacements;
         rend = true_resnorm(h, b, x, work);
+        double factor = (run.steps > 0) ? pow(rend / rstart, 1.0 / run.steps) : 1.0;
         if (run.converged || rend <= tol * bnorm) {
             converged = 1;
+            record(trace, cap, ntrace, run.steps, rstart, rend, factor, ORC_WIN_CONVERGED);
             break;
         }
         breakdown = run.breakdown;
-        double factor = (run.steps > 0) ? pow(rend / rstart, 1.0 / run.steps) : 1.0;
-        if (factor > rho_max || breakdown) {
+        /* grew by more than divf, a non-finite residual included */
+        int growing = divf > 0.0 && !(rend <= divf * rstart);
+        int action = ORC_WIN_CONTINUE;
+        if (factor > rho_max || breakdown || growing) {
             int cnt = orc_reintroduce(h, s, gamma_min, changed);
             if (cnt < 0) {
                 status = -cnt;
@@ -1277,31 +1337,51 @@ int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int3
             /* a restart, or a final breakdown, goes back to the checkpoint
                whenever the residual did not decrease -- a non-finite residual
                included (!(rend <= rstart) holds for NaN) */
+            int back = !(rend <= rstart);
             if (cnt == 0 && breakdown) {
-                if (!(rend <= rstart)) memcpy(x, xs, sizeof(double) * (size_t)n);
+                if (back) memcpy(x, xs, sizeof(double) * (size_t)n);
+                record(trace, cap, ntrace, run.steps, rstart, rend, factor,
+                       back ? ORC_WIN_BREAKDOWN_BACK : ORC_WIN_BREAKDOWN_STOP);
+                break;
+            }
+            if (cnt == 0 && growing) {
+                memcpy(x, xs, sizeof(double) * (size_t)n);
+                diverged = 1;
+                record(trace, cap, ntrace, run.steps, rstart, rend, factor, ORC_WIN_DIVERGED);
                 break;
             }
             if (cnt > 0) {
                 info->resets++;
                 breakdown = 0;
-                if (!(rend <= rstart)) {
-                    memcpy(x, xs, sizeof(double) * (size_t)n);
-                    rend = rstart;
-                }
-                pcg_start(h, &st, b, x);
+                action = back ? ORC_WIN_RESTART_BACK : ORC_WIN_RESTART_HERE;
+            } else {
+                action = ORC_WIN_NOTHING_LEFT;
             }
         }
+        record(trace, cap, ntrace, run.steps, rstart, rend, factor, action);
+        if (action == ORC_WIN_RESTART_BACK) {
+            memcpy(x, xs, sizeof(double) * (size_t)n);
+            rend = rstart;
+        }
+        if (action == ORC_WIN_RESTART_HERE || action == ORC_WIN_RESTART_BACK) pcg_start(h, &st, b, x);
         rstart = rend;
     }
     info->iterations = total;
     info->final_relres = true_resnorm(h, b, x, work) / bnorm;
     info->conv_factor = total > 0 ? pow(info->final_relres, 1.0 / total) : 0.0;
     if (status == ORC_OK)
-        status = converged ? ORC_OK : (breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
+        status = converged ? ORC_OK
+               : diverged  ? ORC_DIVERGED
+               : (breakdown ? ORC_BREAKDOWN : ORC_NOT_CONVERGED);
     info->status = status;
     free(xs); free(work);
     pcg_free(&st);
     return status;
+}
+
+int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                       int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info) {
+    return orc_adaptive_solve_ex(h, b, x, tol, max_it, k, s, gamma_min, rho_max, 1e3, NULL, 0, NULL, info);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -45,7 +45,7 @@ typedef struct {
 
 typedef struct {
     int32_t iterations;   /* number of products with A_0 p */
-    int32_t status;       /* 0 converged, 4 not converged, 6 breakdown */
+    int32_t status;       /* 0 converged, 4 not converged, 5 diverged, 6 breakdown */
     int32_t resets;       /* adaptive: number of reintroductions (PCG restarts) */
     int32_t replacements; /* residual replacements after a failed true-residual check */
     double final_relres;  /* ||b - A x|| / ||b|| at exit (true residual) */
@@ -53,6 +53,26 @@ typedef struct {
 } orc_info;
 
 typedef struct orc_hier orc_hier;
+
+/* One check window of Algorithm 5 (orc_adaptive_solve_ex's trace). */
+typedef struct {
+    int32_t steps;  /* PCG steps taken in the window */
+    int32_t action; /* ORC_WIN_* below */
+    double rstart;  /* true residual norm at the window's start */
+    double rend;    /* true residual norm at its end (a restart from the
+                       window's start then begins from rstart again) */
+    double factor;  /* (rend / rstart)^(1 / steps), before any restart */
+} orc_window;
+enum {
+    ORC_WIN_CONTINUE = 0,       /* factor <= rho_max: the Krylov run goes on */
+    ORC_WIN_RESTART_HERE = 1,   /* reintroduced; PCG restarts from the current x */
+    ORC_WIN_RESTART_BACK = 2,   /* reintroduced; the residual grew: restart from the window's x */
+    ORC_WIN_CONVERGED = 3,      /* tolerance reached */
+    ORC_WIN_NOTHING_LEFT = 4,   /* slow, but every gamma is 0 already: the run goes on */
+    ORC_WIN_BREAKDOWN_STOP = 5, /* breakdown with nothing to reintroduce; x kept */
+    ORC_WIN_BREAKDOWN_BACK = 6, /* the same, x back to the window's start */
+    ORC_WIN_DIVERGED = 7        /* grew by more than divf, nothing to reintroduce */
+};
 
 /* ---- building blocks (Section 2, Algorithm 1) ---- */
 void orc_strength(const orc_csr *A, double theta, uint8_t *strong);
@@ -93,8 +113,18 @@ int orc_sparsify_opts(orc_hier *h, const double *gamma, int32_t ngamma, int32_t 
 int orc_reintroduce(orc_hier *h, int32_t s, double gamma_min, int32_t *changed);
 int orc_vcycle(orc_hier *h, const double *b, double *x);
 int orc_pcg(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, orc_info *info);
+/* PCG with the divergence test made explicit: windows of kwin steps, growth
+ * factor divf (0: off, else >= 1); orc_pcg uses kwin = 3, divf = 1e3. */
+int orc_pcg_ex(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t kwin,
+               double divf, orc_info *info);
 int orc_adaptive_solve(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
                        int32_t k, int32_t s, double gamma_min, double rho_max, orc_info *info);
+/* Algorithm 5 with its divergence factor (orc_adaptive_solve: 1e3) and an
+ * optional trace of the check windows: *ntrace receives the number of
+ * windows, of which the first cap are written to trace. */
+int orc_adaptive_solve_ex(orc_hier *h, const double *b, double *x, double tol, int32_t max_it,
+                          int32_t k, int32_t s, double gamma_min, double rho_max, double divf,
+                          orc_window *trace, int32_t cap, int32_t *ntrace, orc_info *info);
 /* restarted right-preconditioned (flexible) GMRES with M = one V-cycle, the
  * same unpreconditioned on a plain CSR matrix, and Algorithm 5 around it */
 int orc_gmres(orc_hier *h, const double *b, double *x, double tol, int32_t max_it, int32_t restart,

@@ -6,6 +6,7 @@ test vector -- never with a retyped copy of the oracle's own formula.
 """
 import json
 import os
+from fractions import Fraction as Fr
 
 import numpy as np
 import pytest
@@ -252,6 +253,81 @@ def test_direct_interp_preserves_constants(which):
         else:
             assert ones[i] <= 1.0 + 1e-14
     assert P.shape[1] == (cf == 1).sum()
+
+
+# A 6 x 6 SPD (strictly diagonally dominant) matrix with positive couplings.
+# Points 1, 2, 3 are C (coarse columns 0, 1, 2); 0, 4, 5 are F.
+_POS6 = [
+    [Fr(5), Fr(-2), Fr(-1), Fr(1, 2), Fr(-1), Fr(1, 4)],
+    [Fr(-2), Fr(6), Fr(0), Fr(-1), Fr(0), Fr(0)],
+    [Fr(-1), Fr(0), Fr(4), Fr(0), Fr(-1), Fr(0)],
+    [Fr(1, 2), Fr(-1), Fr(0), Fr(3), Fr(0), Fr(-1)],
+    [Fr(-1), Fr(0), Fr(-1), Fr(0), Fr(4), Fr(1, 2)],
+    [Fr(1, 4), Fr(0), Fr(0), Fr(-1), Fr(1, 2), Fr(3)],
+]
+_POS6_CF = np.array([-1, 1, 1, 1, -1, -1], dtype=np.int8)
+
+
+def _pos6():
+    D = np.array([[float(v) for v in row] for row in _POS6])
+    S = sp.csr_matrix(D)
+    S.sort_indices()
+    return S
+
+
+def _assert_weights(P, expect):
+    """P (oracle) against exact fractions, to a couple of ulps."""
+    Pd = P.todense()
+    want = np.zeros(Pd.shape)
+    for (i, j), w in expect.items():
+        want[i, j] = float(w)
+    assert np.array_equal(Pd != 0, want != 0), (Pd, want)
+    np.testing.assert_allclose(Pd, want, rtol=4e-16, atol=0)
+
+
+def test_direct_interp_positive_couplings_lumped_to_diagonal():
+    """Direct interpolation (Section 2; Stueben's sign split) when the F row
+    has positive off-diagonals but no strong positive C neighbour -- the case
+    every hierarchy meets, since the classical strength rule never marks a
+    positive coupling strong.  The positive sum then joins the diagonal:
+    row 0: alpha = (-2 - 1 - 1) / (-2 - 1) = 4/3, a_00 -> 5 + 1/2 + 1/4 = 23/4,
+           w = -alpha a_0j / (23/4): 32/69 (C 1), 16/69 (C 2);
+    row 4: alpha = -2 / -1 = 2, a_44 -> 4 + 1/2 = 9/2, w_42 = 4/9;
+    row 5: alpha = 1, a_55 -> 3 + 3/4 = 15/4, w_53 = 4/15.
+    A dropped fallback (a_ii unchanged) gives 8/15, 1/2 and 1/3 instead."""
+    A = _pos6()
+    s = oracle.strength(A, 0.25)
+    # the strength rule marks exactly the negative couplings above theta
+    dense_s = np.zeros((6, 6), dtype=bool)
+    rows = np.repeat(np.arange(6), np.diff(A.indptr))
+    dense_s[rows, A.indices] = s.astype(bool)
+    assert not dense_s[A.toarray() > 0].any()
+    assert dense_s[0, 1] and dense_s[0, 2] and dense_s[0, 4] and not dense_s[0, 3]
+    P = oracle.direct_interp(A, s, _POS6_CF)
+    _assert_weights(P, {(0, 0): Fr(32, 69), (0, 1): Fr(16, 69), (1, 0): 1, (2, 1): 1, (3, 2): 1,
+                        (4, 1): Fr(4, 9), (5, 2): Fr(4, 15)})
+    # closed form: with the positive sum lumped, sum_j w_ij = -sum a_ik^- / (a_ii + sum a_ik^+)
+    rowsum = P.todense().sum(axis=1)
+    np.testing.assert_allclose(rowsum[[0, 4, 5]], [16 / 23, 4 / 9, 4 / 15], rtol=4e-16)
+
+
+def test_direct_interp_positive_couplings_beta_branch():
+    """The beta branch of direct interpolation, reached when a strong
+    positive C neighbour exists (here a_03 = +1/2 is marked strong by hand;
+    orc_direct_interp takes any strength flags):
+    alpha = (-4) / (-3) = 4/3, beta = (1/2 + 1/4) / (1/2) = 3/2, a_00 = 5,
+    w_01 = 8/15, w_02 = 4/15, w_03 = -beta a_03 / a_00 = -3/20.
+    Closed form: the weights then sum to -sum_{k != i} a_ik / a_ii
+    = 1 - 7/4 / 5 = 13/20.  A beta over all positive couplings (rather than
+    the C ones) would give 1 and w_03 = -1/10."""
+    A = _pos6()
+    s = oracle.strength(A, 0.25).copy()
+    p03 = A.indptr[0] + int(np.where(A.indices[A.indptr[0]:A.indptr[1]] == 3)[0][0])
+    s[p03] = 1
+    P = oracle.direct_interp(A, s, _POS6_CF)
+    _assert_weights(P, {(0, 0): Fr(8, 15), (0, 1): Fr(4, 15), (0, 2): Fr(-3, 20), (1, 0): 1, (2, 1): 1,
+                        (3, 2): 1, (4, 1): Fr(4, 9), (5, 2): Fr(4, 15)})
+    assert abs(P.todense()[0].sum() - 13 / 20) <= 4e-16
 
 
 # ---------------------------------------------------------------------------
@@ -572,6 +648,209 @@ def test_adaptive_recovers_and_is_noop_for_galerkin():
     assert i4.status == 0 and i4.final_relres <= 1e-8
     assert i4.resets >= 1
     assert h4.gamma(1) < 1.0
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 5's control, restated with dense linear algebra
+# ---------------------------------------------------------------------------
+def _shifted_poisson2d(N, sigma):
+    """2D 5-point Poisson with sigma taken off the diagonal: symmetric with a
+    positive diagonal, indefinite once sigma passes the smallest eigenvalue
+    -- the input on which CG's residual really grows."""
+    A = gen.poisson2d_5pt(N)
+    A.val = A.val.copy()
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    A.val[A.col == rows] -= sigma
+    return A
+
+
+def _vcycle_operator(A, gammas, max_size):
+    """The V-cycle of the oracle hierarchy sparsified with `gammas`, as a
+    dense matrix (the cycle is linear in its right-hand side)."""
+    h = oracle.Hierarchy(A, max_size=max_size)
+    h.sparsify(gammas)
+    M = np.empty((A.n, A.n))
+    for j in range(A.n):
+        e = np.zeros(A.n)
+        e[j] = 1.0
+        M[:, j] = h.vcycle(e)
+    return M, h.num_levels
+
+
+def _alg5_dense(A, b, gammas, k, s, rho_max, divf, max_size, tol=1e-8, max_it=300, gamma_min=0.01):
+    """Algorithm 5 (Section 6) from its steps: PCG is run k steps at a time;
+    after each window the true residual gives the factor
+    (||r_end|| / ||r_start||)^(1/k); above rho_max (or on a breakdown, or a
+    growth beyond divf) the finest levels with gamma > 0 get gamma / 10
+    (0 below gamma_min) on s levels and PCG restarts -- from the window's
+    starting x when the residual grew.  Returns (x, status, windows, its,
+    resets) with windows = [(steps, action, factor)]."""
+    Ad = A.to_scipy().toarray()
+    _, L = _vcycle_operator(A, [0.0], max_size)
+    g = [0.0] + [gammas[min(l, len(gammas) - 1)] for l in range(1, L)]
+    M, _ = _vcycle_operator(A, g, max_size)
+    bn = np.linalg.norm(b)
+    x = np.zeros(A.n)
+
+    def start(x):
+        r = b - Ad @ x
+        z = M @ r
+        return r, z.copy(), r @ z
+
+    r, p, rho = start(x)
+    rstart, total, resets, windows, status = bn, 0, 0, [], oracle.NOT_CONVERGED
+    while total < max_it:
+        xs = x.copy()
+        steps, taken, conv, brk = min(k, max_it - total), 0, False, False
+        conv = np.linalg.norm(r) <= tol * bn
+        while not conv and taken < steps:
+            q = Ad @ p
+            pq = p @ q
+            taken += 1
+            if not (pq > 0 and rho > 0):
+                brk = True
+                break
+            a = rho / pq
+            x = x + a * p
+            r = r - a * q
+            if np.linalg.norm(r) <= tol * bn:
+                t = b - Ad @ x
+                if np.linalg.norm(t) <= tol * bn:
+                    conv = True
+                    break
+                r = t
+            z = M @ r
+            rho_new = r @ z
+            p = z + (rho_new / rho) * p
+            rho = rho_new
+        total += taken
+        rend = np.linalg.norm(b - Ad @ x)
+        factor = (rend / rstart) ** (1.0 / taken) if taken else 1.0
+        if conv or rend <= tol * bn:
+            windows.append((taken, "converged", factor))
+            status = oracle.OK
+            break
+        growing = divf > 0 and not (rend <= divf * rstart)
+        action = "continue"
+        if factor > rho_max or brk or growing:
+            lstart = next((l for l in range(1, L) if g[l] > 0), None)
+            changed = 0
+            if lstart is not None:
+                for l in range(lstart, min(lstart + s, L)):
+                    g[l] = g[l] / 10 if g[l] / 10 >= gamma_min * (1 - 1e-12) else 0.0
+                    changed += 1
+            back = not (rend <= rstart)
+            if changed == 0 and brk:
+                windows.append((taken, "breakdown_back" if back else "breakdown_stop", factor))
+                x = xs if back else x
+                status = oracle.BREAKDOWN
+                break
+            if changed == 0 and growing:
+                windows.append((taken, "diverged", factor))
+                x, status = xs, oracle.DIVERGED
+                break
+            if changed:
+                resets += 1
+                M, _ = _vcycle_operator(A, g, max_size)
+                action = "restart_back" if back else "restart_here"
+                if back:
+                    x, rend = xs, rstart
+                r, p, rho = start(x)
+            else:
+                action = "nothing_left"
+        windows.append((taken, action, factor))
+        rstart = rend
+    return x, status, windows, total, resets
+
+
+_ALG5_CASES = {
+    # SPD: restarts from the current x, windows that go on, nothing left
+    "q27_restarts": (lambda: gen.poisson3d_27pt(7), [0.0, 1.0], 1, 1, 0.1, 1e3, 20),
+    "aniso_slow": (lambda: gen.rotated_aniso_q1(20), [0.0, 0.1, 1.0], 3, 1, 0.3, 1e3, 20),
+    "aniso_s2": (lambda: gen.rotated_aniso_q1(20), [0.0, 0.1, 1.0], 2, 2, 0.5, 1e3, 20),
+    # indefinite: restarts from the window's start, final breakdowns
+    "shift_back": (lambda: _shifted_poisson2d(16, 0.2), [0.0, 1.0], 1, 1, 0.5, 0.0, 20),
+    "shift_breakdown_back": (lambda: _shifted_poisson2d(24, 0.2), [0.0, 0.0], 2, 1, 0.5, 0.0, 20),
+    "shift_restarts_back": (lambda: _shifted_poisson2d(24, 0.2), [0.0, 1.0], 2, 1, 0.5, 0.0, 20),
+    # growth with nothing left to reintroduce: diverged
+    "shift_diverged": (lambda: _shifted_poisson2d(16, 0.065), [0.0, 0.0], 1, 1, 0.5, 1.0, 20),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_ALG5_CASES))
+def test_adaptive_trace_matches_dense_restatement(case):
+    """The oracle's Algorithm 5 against the dense restatement above, window by
+    window: the steps of each window, the action taken (continue, restart
+    from the current or the window's x, nothing left, converged, breakdown,
+    diverged), the window factor, and the final x, iterations and resets."""
+    make, gam, k, s, rho_max, divf, ms = _ALG5_CASES[case]
+    A = make()
+    b = gen.rhs_uniform(A.n, 1)
+    h = oracle.Hierarchy(A, max_size=ms)
+    h.sparsify(gam)
+    x, info, tr = h.adaptive_solve(b, max_it=300, k=k, s=s, rho_max=rho_max, div_factor=divf, trace=True)
+    xd, status, windows, its, resets = _alg5_dense(A, b, gam, k, s, rho_max, divf, ms)
+    assert [(t["steps"], t["action"]) for t in tr] == [(w[0], w[1]) for w in windows]
+    np.testing.assert_allclose([t["factor"] for t in tr], [w[2] for w in windows], rtol=1e-8)
+    assert (info.status, info.iterations, info.resets) == (status, its, resets)
+    assert np.linalg.norm(x - xd) <= 1e-8 * max(np.linalg.norm(xd), 1e-300)
+    # every window's factor is its residual ratio per step
+    for t in tr:
+        if t["steps"]:
+            assert abs(t["factor"] - (t["rend"] / t["rstart"]) ** (1 / t["steps"])) <= 1e-14 * t["factor"]
+
+
+def test_adaptive_cases_cover_every_branch():
+    seen = set()
+    for case in _ALG5_CASES.values():
+        make, gam, k, s, rho_max, divf, ms = case
+        A = make()
+        h = oracle.Hierarchy(A, max_size=ms)
+        h.sparsify(gam)
+        _, _, tr = h.adaptive_solve(gen.rhs_uniform(A.n, 1), max_it=300, k=k, s=s, rho_max=rho_max,
+                                    div_factor=divf, trace=True)
+        seen |= {t["action"] for t in tr}
+    assert seen == set(oracle.WIN_ACTIONS), set(oracle.WIN_ACTIONS) - seen
+
+
+@pytest.mark.parametrize("N,sigma,k", [(16, 0.065, 1), (20, 0.045, 2), (20, 0.05, 1)])
+def test_pcg_divergence_stops_at_the_window_start(N, sigma, k):
+    """PCG's divergence test (windows of k steps; the recurrence residual at a
+    window's end against its start; growth beyond the factor -- 1 here --
+    stops the run with x at the window's start), against plain dense CG."""
+    A = _shifted_poisson2d(N, sigma)
+    b = gen.rhs_uniform(A.n, 1)
+    h = oracle.Hierarchy(A, max_size=20)
+    x, info = h.pcg(b, max_it=300, k=k, div_factor=1.0)
+    M, _ = _vcycle_operator(A, [0.0], 20)
+    Ad = A.to_scipy().toarray()
+    xd = np.zeros(A.n)
+    r = b.copy()
+    z = M @ r
+    p, rho = z.copy(), r @ z
+    xs, rws, its = xd.copy(), np.linalg.norm(r), 0
+    while True:
+        if its % k == 0:
+            xs = xd.copy()
+        q = Ad @ p
+        assert p @ q > 0 and rho > 0, "the case must diverge before it breaks down"
+        a = rho / (p @ q)
+        xd, r = xd + a * p, r - a * q
+        its += 1
+        if its % k == 0:
+            if np.linalg.norm(r) > rws:
+                break
+            rws = np.linalg.norm(r)
+        z = M @ r
+        rho_new = r @ z
+        p, rho = z + (rho_new / rho) * p, rho_new
+    assert info.status == oracle.DIVERGED and info.iterations == its
+    np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-12 * np.linalg.norm(xs))
+    assert its > k  # it stops after more than one window
+    # the default factor (1e3) never fires on an SPD problem
+    A2 = gen.poisson2d_5pt(N)
+    x2, i2 = oracle.Hierarchy(A2, max_size=20).pcg(gen.rhs_uniform(A2.n, 1))
+    assert i2.status == oracle.OK
 
 
 # ---------------------------------------------------------------------------
