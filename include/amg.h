@@ -46,7 +46,8 @@ typedef enum {
     AMG_ERR_OOM = 2,       /* device or host allocation failed */
     AMG_ERR_CUDA = 3,      /* a CUDA call failed; see amg_last_error() */
     AMG_NOT_CONVERGED = 4, /* max_it reached; x and info are still filled */
-    AMG_DIVERGED = 5,      /* residual grew by 1e3 over a check window */
+    AMG_DIVERGED = 5,      /* residual grew by more than div_factor (1e3) over a
+                              check window; x is the window's starting iterate */
     AMG_BREAKDOWN = 6,     /* CG lost positive definiteness (rho or p.Ap <= 0) */
     AMG_TIMEOUT = 7,       /* a wait ran past its time limit */
     AMG_REJECTED = 8       /* admission refused (server: memory budget / queue) */
@@ -108,12 +109,16 @@ typedef struct {
     int level_offset;    /* PMIS level index of the first level, default 0 */
     int spmv_variant;    /* AMG_SPMV_AUTO (autotuned per level) or forced */
     int use_graph;       /* capture the PCG iteration in a CUDA graph, default 1 */
-    int check_every;     /* PCG iterations between host stop tests, default 1 */
+    int check_every;     /* reserved, must be >= 1 (default 1): the recurrence
+                            stop test runs on the device after every step */
     int setup_timing;    /* 1: time the setup phases with events (amg_timing_get
                             kinds 8..15), default 0 */
     int lump;            /* AMG_LUMP_DIAG (default) or AMG_LUMP_STRONG */
     int krylov;          /* AMG_KRYLOV_CG (default) or AMG_KRYLOV_GMRES */
     int restart;         /* GMRES restart length m (Krylov vectors kept), default 30 */
+    double div_factor;   /* AMG_DIVERGED when the residual grows by more than this
+                            factor over a check window of k_check CG steps,
+                            default 1e3; 0 turns the test off, else >= 1 */
 } amg_options;
 
 typedef struct {
@@ -192,6 +197,16 @@ amg_status amg_reintroduce(amg_hierarchy *h, int s_levels, int *levels_changed);
  * rho_max from the options given at setup).  b and x are n-vectors, both host
  * or both device: on_device says which.  In the FP32 precision modes the
  * outer loop is flexible CG.  Returns the solve status (also in info->status).
+ * Divergence (Section 6: with too many entries dropped the method stops
+ * converging): a plain CG solve is cut into windows of k_check steps (counted
+ * again after each true-residual replacement); when the recurrence residual
+ * at a window's end exceeds div_factor times the one at its start, or is not
+ * finite, the solve stops with AMG_DIVERGED and x is the iterate at the
+ * window's start.  An adaptive solve applies the same factor to the true
+ * residual of its Algorithm 5 windows, and first tries to recover by
+ * reintroduction; it returns AMG_DIVERGED (x at the window's start) only
+ * when every gamma is already 0.  GMRES minimises the residual, so it never
+ * reports AMG_DIVERGED; neither do batched or served solves.
  */
 amg_status amg_solve(amg_hierarchy *h, const double *b, double *x, double tol, int max_it,
                      int adaptive, int on_device, void *stream, amg_solve_info *info);

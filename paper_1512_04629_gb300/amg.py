@@ -51,7 +51,7 @@ class Options(C.Structure):
                 ("rho_max", C.c_double), ("level_offset", C.c_int), ("spmv_variant", C.c_int),
                 ("use_graph", C.c_int), ("check_every", C.c_int),
                 ("setup_timing", C.c_int), ("lump", C.c_int), ("krylov", C.c_int),
-                ("restart", C.c_int)]
+                ("restart", C.c_int), ("div_factor", C.c_double)]
 
 
 class SolveInfo(C.Structure):

@@ -103,6 +103,8 @@ void check_options(const amg_options &o) {
     require(o.lump == AMG_LUMP_DIAG || o.lump == AMG_LUMP_STRONG, "unknown lump");
     require(o.krylov == AMG_KRYLOV_CG || o.krylov == AMG_KRYLOV_GMRES, "unknown krylov");
     require(o.restart >= 1 && o.restart <= 512, "restart must be in [1, 512]");
+    require(o.div_factor == 0.0 || (std::isfinite(o.div_factor) && o.div_factor >= 1.0),
+            "div_factor must be 0 (off) or a finite value >= 1");
 }
 
 void check_gammas(const double *g, int n) {
@@ -151,6 +153,7 @@ void amg_options_default(amg_options *o) {
     o->lump = AMG_LUMP_DIAG;
     o->krylov = AMG_KRYLOV_CG;
     o->restart = 30;
+    o->div_factor = 1e3;
 }
 
 amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_gamma, const amg_options *opt,

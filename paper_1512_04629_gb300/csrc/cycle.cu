@@ -375,8 +375,15 @@ finish_kernel(int nblocks, Reduce red, PcgScalars *sc, cudaGraphConditionalHandl
         sc->rr = t[0];
         int its = sc->its + 1;
         sc->its = its;
+        if (sc->divf > 0.0 && !sc->breakdown) {
+            // the window test, in the oracle's form: norms, not squares
+            const double rn = sqrt(t[0]);
+            const bool end = its % sc->kwin == 0;
+            if (!isfinite(rn) || (end && rn > sc->divf * sc->rn_ws)) sc->diverged = 1;
+            else if (end) sc->rn_ws = rn;
+        }
         if (use_handle) {
-            bool go = t[0] > sc->thresh2 && its < sc->max_its && !sc->breakdown && isfinite(t[0]);
+            bool go = t[0] > sc->thresh2 && its < sc->max_its && !sc->breakdown && !sc->diverged && isfinite(t[0]);
             cudaGraphSetConditional(handle, go ? 1u : 0u);
         }
     } else if (FIN == kFinRz) {
@@ -469,13 +476,16 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
 __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
                  double *__restrict__ r, const PcgScalars *sc, Reduce red, const double *__restrict__ dinv0,
-                 double *__restrict__ x0) {
+                 double *__restrict__ x0, double *__restrict__ xs) {
     block_partials_begin();
     const double alpha = sc->alpha;
     const bool step = alpha != 0.0;  // 0: breakdown -- x and r stay as they are
+    // this step starts a divergence-test window: keep x as it was
+    const bool ckpt = xs != nullptr && sc->divf > 0.0 && sc->its % sc->kwin == 0;
     double part[1] = {0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         double ri = r[i];
+        if (ckpt) xs[i] = x[i];
         if (step) {
             x[i] += alpha * p[i];
             ri -= alpha * q[i];
@@ -821,9 +831,9 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
 
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
-                   double *x0, cudaStream_t s) {
+                   double *x0, double *xs, cudaStream_t s) {
     int blocks = reduce_blocks(n);
-    { xr_update_kernel<<<blocks, kThreads, 0, s>>>(n, p, q, x, r, sc, red, dinv0, x0); ::amg::count_launch(); }
+    { xr_update_kernel<<<blocks, kThreads, 0, s>>>(n, p, q, x, r, sc, red, dinv0, x0, xs); ::amg::count_launch(); }
     launch_finish<1, kFinXr>(blocks, red, sc, s, handle, use_handle);
     AMG_CHECK_LAUNCH();
 }

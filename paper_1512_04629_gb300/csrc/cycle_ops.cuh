@@ -35,6 +35,13 @@ struct PcgScalars {
     int its;         // CG steps taken
     int max_its;     // the graph loop stops at this count
     int breakdown;   // p.Ap <= 0 or r.z <= 0 was met
+    int diverged;    // the residual grew by more than divf over a window
+    // divergence test (off when divf == 0): windows of kwin steps counted
+    // by `its`; at a window's end sqrt(rr) is compared with rn_ws, the norm
+    // at its start, and x at the window's start is kept in the checkpoint
+    double divf;
+    double rn_ws;
+    int kwin;
     int pad;
 };
 
@@ -72,10 +79,12 @@ void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t
 void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, cudaStream_t s);
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s);
 // x += alpha p, r -= alpha q, rr, its += 1; with a graph handle, the WHILE
-// condition is set to continue while rr > thresh2, its < max_its, no breakdown
+// condition is set to continue while rr > thresh2, its < max_its, no
+// breakdown and no divergence.  With the divergence test on (sc->divf > 0),
+// a step that starts a window first copies x to xs.
 void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, double *r, PcgScalars *sc,
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
-                   double *x0, cudaStream_t s);
+                   double *x0, double *xs, cudaStream_t s);
 // level-0 post-smoothing that also forms rho = r.z and, when q is given
 // (flexible CG), z.q, and beta: z is the output, r = b the cycle input.
 // Returns false (nothing launched) for an empty level.

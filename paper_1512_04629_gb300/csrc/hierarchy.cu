@@ -622,7 +622,7 @@ void ensure_workspace(Hierarchy &h, cudaStream_t s) {
     alloc_zero<double>(h.pb, n, s); alloc_zero<double>(h.px, n, s);
     alloc_zero<double>(h.pr, n, s); alloc_zero<double>(h.pz, n, s);
     alloc_zero<double>(h.pp, n, s); alloc_zero<double>(h.pq, n, s);
-    alloc_zero<double>(h.pt, n, s);
+    alloc_zero<double>(h.pt, n, s); alloc_zero<double>(h.pxs, n, s);
     if (h.opt.precision != AMG_PREC_FP64) {
         alloc_zero<float>(h.r32, n, s);
         alloc_zero<float>(h.z32, n, s);
@@ -796,7 +796,7 @@ bool vcycle_f64(Hierarchy &h, const double *r, double *z, cudaStream_t s, const 
 namespace {
 struct Run {
     int steps = 0, replacements = 0;
-    bool converged = false, breakdown = false;
+    bool converged = false, breakdown = false, diverged = false;
     double rnorm = 0.0;
 };
 
@@ -885,7 +885,7 @@ void pcg_body(Hierarchy &h, cudaStream_t s, cudaGraphConditionalHandle handle, b
     timed(h, 6, 0, fp64 ? 64.0 * n : 48.0 * n, s, [&] {
         cyc::pcg_xr_update(n, h.pp.as<double>(), h.pq.as<double>(), h.px.as<double>(), h.pr.as<double>(), h.dscal(),
                            h.reduce(), handle, use_handle, fp64 ? V0.dinv.as<double>() : nullptr,
-                           fp64 ? V0.x.as<double>() : nullptr, s);
+                           fp64 ? V0.x.as<double>() : nullptr, h.pxs.as<double>(), s);
     });
 }
 
@@ -937,8 +937,13 @@ void ensure_graph(Hierarchy &h) {
 
 // Runs up to max_steps CG steps (stopping at the recurrence test, then
 // confirming with the true residual; a failed confirmation replaces r).
+// divf > 0 adds the divergence test (Section 6: with too many entries
+// dropped the method stops converging): windows of k_check steps, counted
+// from the run's start and from every replacement; a window whose recurrence
+// residual grew by more than divf, or a non-finite residual, stops the run
+// with x back at the window's start.
 void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int max_steps, double rnorm_now,
-                 cudaStream_t s, Run &run) {
+                 double divf, cudaStream_t s, Run &run) {
     run = Run();
     run.rnorm = rnorm_now;
     if (rnorm_now <= tol * bnorm) { run.converged = true; return; }
@@ -946,10 +951,15 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
     if (graph) ensure_graph(h);
     double thresh2 = (tol * bnorm) * (tol * bnorm);
     int32_t n = h.lev[0]->n();
+    double rn_ws = rnorm_now;
     while (run.steps < max_steps) {
         h.h_scal->its = 0;
         h.h_scal->max_its = max_steps - run.steps;
         h.h_scal->thresh2 = thresh2;
+        h.h_scal->divf = divf;
+        h.h_scal->kwin = std::max(1, h.opt.k_check);
+        h.h_scal->rn_ws = rn_ws;
+        h.h_scal->diverged = 0;
         write_scalars(h, s);
         if (graph) {
             AMG_CUDA(cudaGraphLaunch(h.g_update, s));
@@ -959,11 +969,18 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
                 pcg_body(h, s, cudaGraphConditionalHandle{}, false);
                 read_scalars(h, s);
                 const PcgScalars &c = *h.h_scal;
-                if (!(c.rr > c.thresh2 && c.its < c.max_its && !c.breakdown && std::isfinite(c.rr))) break;
+                if (!(c.rr > c.thresh2 && c.its < c.max_its && !c.breakdown && !c.diverged && std::isfinite(c.rr)))
+                    break;
             }
         }
         const PcgScalars &sc = *h.h_scal;
         run.steps += sc.its;
+        if (sc.diverged) {
+            AMG_CUDA(cudaMemcpyAsync(h.px.ptr, h.pxs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            run.rnorm = sc.rn_ws;
+            run.diverged = true;
+            return;
+        }
         if (sc.breakdown || !std::isfinite(sc.rr)) { run.breakdown = true; return; }
         run.rnorm = std::sqrt(sc.rr);
         if (sc.rr > thresh2) return;  // step budget used up
@@ -973,6 +990,7 @@ void pcg_iterate(Hierarchy &h, const double *b, double bnorm, double tol, int ma
         AMG_CUDA(cudaMemcpyAsync(h.pr.ptr, h.pt.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         refresh_x0(h, s);
         run.replacements++;
+        rn_ws = tn;  // the window count restarts with the replaced residual
     }
 }
 // ---------------------------------------------------------------------------
@@ -1231,11 +1249,13 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
     } else if (!adaptive) {
         double r0 = pcg_start(h, b, x, s);
         Run run;
-        pcg_iterate(h, b, bnorm, tol, max_it, r0, s, run);
+        pcg_iterate(h, b, bnorm, tol, max_it, r0, h.opt.div_factor, s, run);
         info->iterations = run.steps;
         info->replacements = run.replacements;
         info->conv_factor = run.steps > 0 ? std::pow(run.rnorm / r0, 1.0 / run.steps) : 0.0;
-        st = run.converged ? AMG_OK : (run.breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+        st = run.converged ? AMG_OK
+           : run.diverged  ? AMG_DIVERGED
+           : (run.breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
     } else {
         // Algorithm 5: check every k steps; reintroduce on slow convergence
         int k = std::max(1, h.opt.k_check), sl = std::max(1, h.opt.s_levels);
@@ -1243,11 +1263,12 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
         double rstart = bnorm;
         double rnow = pcg_start(h, b, x, s);
         int total = 0;
-        bool converged = false, breakdown = false;
+        bool converged = false, breakdown = false, diverged = false;
+        const double divf = h.opt.div_factor;
         while (total < max_it) {
             AMG_CUDA(cudaMemcpyAsync(xs.ptr, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             Run run;
-            pcg_iterate(h, b, bnorm, tol, std::min(k, max_it - total), rnow, s, run);
+            pcg_iterate(h, b, bnorm, tol, std::min(k, max_it - total), rnow, 0.0, s, run);
             total += run.steps;
             info->replacements += run.replacements;
             double rend = true_resnorm(h, b, x, s);
@@ -1255,13 +1276,20 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
             breakdown = run.breakdown;
             rnow = run.rnorm;
             double factor = run.steps > 0 ? std::pow(rend / rstart, 1.0 / run.steps) : 1.0;
-            if (factor > h.opt.rho_max || breakdown) {
+            // grew by more than divf over the window (a non-finite residual included)
+            const bool growing = divf > 0.0 && !(rend <= divf * rstart);
+            if (factor > h.opt.rho_max || breakdown || growing) {
                 int cnt = reintroduce(h, sl, s);
                 // back to the checkpoint whenever the residual did not
                 // decrease (a non-finite residual included)
                 const bool back = !(rend <= rstart);
                 if (cnt == 0 && breakdown) {
                     if (back) AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    break;
+                }
+                if (cnt == 0 && growing) {  // diverged, nothing left to reintroduce
+                    AMG_CUDA(cudaMemcpyAsync(x, xs.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+                    diverged = true;
                     break;
                 }
                 if (cnt > 0) {
@@ -1277,7 +1305,7 @@ amg_status solve(Hierarchy &h, const double *b, double *x_out, double tol, int m
             rstart = rend;
         }
         info->iterations = total;
-        st = converged ? AMG_OK : (breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
+        st = converged ? AMG_OK : diverged ? AMG_DIVERGED : (breakdown ? AMG_BREAKDOWN : AMG_NOT_CONVERGED);
     }
     if (bnorm > 0.0) {
         double fin = true_resnorm(h, b, x, s);

@@ -111,6 +111,7 @@ struct Hierarchy {
 
     // FP64 PCG workspace
     DevBuf pb, px, pr, pz, pp, pq, pt;
+    DevBuf pxs;  // x at the start of the current divergence-test window
     DevBuf scal;          // PcgScalars
     DevBuf partials, counter;
     PcgScalars *h_scal = nullptr;  // pinned

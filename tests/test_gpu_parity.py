@@ -254,6 +254,69 @@ def test_adaptive_matches_oracle(amg, use_graph):
         assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
 
 
+def _shifted_poisson2d(N, sigma):
+    """2D 5-point Poisson minus sigma on the diagonal: symmetric, positive
+    diagonal, indefinite past the smallest eigenvalue (CG's residual grows)."""
+    A = gen.poisson2d_5pt(N)
+    A.val = A.val.copy()
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    A.val[A.col == rows] -= sigma
+    return A
+
+
+@pytest.mark.parametrize("N,sigma,k", [(16, 0.065, 1), (20, 0.045, 2), (20, 0.05, 1)])
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_divergence_matches_oracle(amg, N, sigma, k, use_graph):
+    """The divergence stop (a window whose residual grew by more than
+    div_factor; forced here with div_factor = 1 on indefinite inputs): the
+    same status and step count as the oracle, x at the window's start."""
+    A = _shifted_poisson2d(N, sigma)
+    b = gen.rhs_uniform(A.n, 1)
+    ref = oracle.Hierarchy(A, max_size=20)
+    xr, ir = ref.pcg(b, max_it=300, k=k, div_factor=1.0)
+    assert ir.status == oracle.DIVERGED
+    h = amg.Hierarchy.setup(A, max_size=20, k_check=k, div_factor=1.0, use_graph=use_graph)
+    x, info = h.solve(b, tol=1e-8, max_it=300)
+    assert info.status == amg.DIVERGED
+    assert info.iterations == ir.iterations
+    assert np.linalg.norm(x - xr) <= 1e-10 * np.linalg.norm(xr)
+    # the default factor (1e3) lets the same solve run on (to convergence or a breakdown)
+    h2 = amg.Hierarchy.setup(A, max_size=20, k_check=k, use_graph=use_graph)
+    _, i2 = h2.solve(b, tol=1e-8, max_it=300)
+    _, i2r = ref.pcg(b, max_it=300, k=k)
+    assert i2.status == i2r.status != amg.DIVERGED
+
+
+_ALG5_GPU = {
+    # (matrix, gammas, k, s, rho_max, div_factor): indefinite inputs that reach
+    # restarts from the window's start, breakdowns and divergence
+    "shift_back": (lambda: _shifted_poisson2d(16, 0.2), [0.0, 1.0], 1, 1, 0.5, 0.0),
+    "shift_breakdown_back": (lambda: _shifted_poisson2d(24, 0.2), [0.0, 0.0], 2, 1, 0.5, 0.0),
+    "shift_restarts_back": (lambda: _shifted_poisson2d(24, 0.2), [0.0, 1.0], 2, 1, 0.5, 0.0),
+    "shift_diverged": (lambda: _shifted_poisson2d(16, 0.065), [0.0, 0.0], 1, 1, 0.5, 1.0),
+    "aniso_s2": (lambda: gen.rotated_aniso_q1(20), [0.0, 0.1, 1.0], 2, 2, 0.5, 1e3),
+}
+
+
+@pytest.mark.parametrize("case", sorted(_ALG5_GPU))
+def test_adaptive_branches_match_oracle(amg, case):
+    """Algorithm 5 on the GPU takes the oracle's branch at every window:
+    same status, steps, resets and final x (restarts from the window's start,
+    final breakdowns and divergence included)."""
+    make, gam, k, s, rho_max, divf = _ALG5_GPU[case]
+    A = make()
+    b = gen.rhs_uniform(A.n, 1)
+    ref = oracle.Hierarchy(A, max_size=20)
+    ref.sparsify(gam)
+    xr, ir, tr = ref.adaptive_solve(b, max_it=300, k=k, s=s, rho_max=rho_max, div_factor=divf, trace=True)
+    h = amg.Hierarchy.setup(A, gamma=gam, max_size=20, k_check=k, s_levels=s, rho_max=rho_max, div_factor=divf)
+    x, info = h.solve(b, tol=1e-8, max_it=300, adaptive=True)
+    assert (info.status, info.iterations, info.resets) == (ir.status, ir.iterations, ir.resets), tr
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+    for l in range(h.num_levels):
+        assert h.level_stats(l)["gamma"] == pytest.approx(ref.gamma(l), rel=1e-12)
+
+
 @pytest.mark.parametrize("permute", [False, True])
 def test_sell_matches_sequential_csr(amg, permute):
     """SELL-32 (int16 column offsets, or int32 columns when a random symmetric
