@@ -20,22 +20,29 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amg_oracle.c")
 _HDR = os.path.join(_HERE, "amg_oracle.h")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
-OK, INVALID, OOM, NOT_CONVERGED, BREAKDOWN = 0, 1, 2, 4, 6
+
+def _compile(path: str, extra) -> None:
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
+           "-shared", "-Wall", "-Wno-unknown-pragmas", *extra, "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, path)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, -O2 -ffp-contract=off)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2 -ffp-contract=off): the
+    sequential parity build, or with omp=True the all-core timing build of
+    the same source (-fopenmp: the solve phase's row loops run in parallel)."""
+    path = _OMP_PATH if omp else _LIB_PATH
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < newest:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC",
-               "-shared", "-Wall", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    if force or not os.path.exists(path) or os.path.getmtime(path) < newest:
+        _compile(path, ["-fopenmp"] if omp else [])
+    return path
 
 
 class _CSR(C.Structure):
@@ -55,12 +62,12 @@ class _Window(C.Structure):
                 ("rend", C.c_double), ("factor", C.c_double)]
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build())
+        if (_lib_omp if omp else _lib) is not None:
+            return _lib_omp if omp else _lib
+        lib = C.CDLL(build(omp=omp))
         P = C.POINTER
         vp = C.c_void_p
         lib.orc_strength.argtypes = [P(_CSR), C.c_double, vp]
@@ -119,7 +126,10 @@ def _load():
         lib.orc_level_array.restype = vp
         lib.orc_level_gamma.argtypes = [vp, C.c_int32]
         lib.orc_level_gamma.restype = C.c_double
-        _lib = lib
+        if omp:
+            _lib_omp = lib
+        else:
+            _lib = lib
         return lib
 
 
@@ -353,10 +363,13 @@ class Hierarchy:
     """Oracle AMG hierarchy (Algorithm 1 Galerkin setup + Algorithm 4 sparsify)."""
 
     def __init__(self, A, theta: float = 0.25, max_size: int = 100, max_levels: int = 25,
-                 seed: int = 0, nongalerkin=None, lump: int = 0):
+                 seed: int = 0, nongalerkin=None, lump: int = 0, omp: bool = False):
         """nongalerkin: per-level drop tolerances for Algorithm 1's in-loop
-        (non-Galerkin) sparsify; None builds the Galerkin hierarchy."""
-        lib = _load()
+        (non-Galerkin) sparsify; None builds the Galerkin hierarchy.  omp:
+        use the all-core timing build (the solve phase's row loops on every
+        host thread; results differ from the sequential build only by the
+        summation order of dot products)."""
+        lib = _load(omp)
         self._lib = lib
         c = to_c(A)
         st = C.c_int32(0)

@@ -62,8 +62,18 @@ static int cmp_i32(const void *a, const void *b) {
     return (x > y) - (x < y);
 }
 
+/* The all-core timing build (compiled with -fopenmp) splits the row loops
+ * of the solve phase -- SpMV, vector updates, dot products -- over the host's
+ * threads; the setup stays sequential.  Without -fopenmp these pragmas are
+ * ignored and every loop runs in order: that build is the parity reference.
+ * Only the dot products' summation order differs between the two. */
+#define ORC_PRAGMA(x) _Pragma(#x)
+#define ORC_PAR_FOR(n) ORC_PRAGMA(omp parallel for schedule(static) if ((n) > 16384))
+#define ORC_PAR_SUM(n, v) ORC_PRAGMA(omp parallel for schedule(static) reduction(+ : v) if ((n) > 16384))
+
 static double dot(int32_t n, const double *a, const double *b) {
     double s = 0.0;
+    ORC_PAR_SUM(n, s)
     for (int32_t i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
 }
@@ -72,6 +82,7 @@ static double norm2(int32_t n, const double *a) { return sqrt(dot(n, a, a)); }
 
 /* y = A x, each row summed in column order. */
 void orc_spmv(const orc_csr *A, const double *x, double *y) {
+    ORC_PAR_FOR(A->nrows)
     for (int32_t i = 0; i < A->nrows; ++i) {
         double s = 0.0;
         for (int32_t p = A->rowptr[i]; p < A->rowptr[i + 1]; ++p) s += A->val[p] * x[A->col[p]];
@@ -1081,8 +1092,10 @@ int orc_vcycle(orc_hier *h, const double *b, double *x) {
     for (int32_t l = 0; l + 1 < L; ++l) {
         orc_level *V = &h->lev[l];
         int32_t n = V->A->nrows;
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) V->x[i] = V->b[i] / V->d[i];   /* pre-smooth */
         orc_spmv(V->Ahat, V->x, V->r);
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) V->r[i] = V->b[i] - V->r[i];    /* residual */
         orc_spmv(V->R, V->r, h->lev[l + 1].b);                          /* restrict */
     }
@@ -1093,8 +1106,10 @@ int orc_vcycle(orc_hier *h, const double *b, double *x) {
         orc_level *V = &h->lev[l];
         int32_t n = V->A->nrows;
         orc_spmv(V->P, h->lev[l + 1].x, V->r);
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) V->x[i] += V->r[i];             /* interpolate, correct */
         orc_spmv(V->Ahat, V->x, V->r);
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) V->r[i] = V->x[i] + (V->b[i] - V->r[i]) / V->d[i];
         memcpy(V->x, V->r, sizeof(double) * (size_t)n);                  /* post-smooth */
     }
@@ -1144,6 +1159,7 @@ static int pcg_alloc(pcg_state *s, int32_t n) {
 static double pcg_start(orc_hier *h, pcg_state *s, const double *b, const double *x) {
     int32_t n = s->n;
     orc_spmv(h->lev[0].A, x, s->q);
+    ORC_PAR_FOR(n)
     for (int32_t i = 0; i < n; ++i) s->r[i] = b[i] - s->q[i];
     orc_vcycle(h, s->r, s->z);
     memcpy(s->p, s->z, sizeof(double) * (size_t)n);
@@ -1181,7 +1197,9 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
             return;
         }
         double alpha = s->rho / pq;
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) x[i] += alpha * s->p[i];
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) s->r[i] -= alpha * s->q[i];
         run->rnorm = norm2(n, s->r);
         w++;
@@ -1196,6 +1214,7 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
         }
         if (run->rnorm <= tol * bnorm) {
             orc_spmv(A, x, s->q);
+            ORC_PAR_FOR(n)
             for (int32_t i = 0; i < n; ++i) s->q[i] = b[i] - s->q[i];
             double tn = norm2(n, s->q);
             run->rnorm = tn;
@@ -1212,6 +1231,7 @@ static void pcg_iterate(orc_hier *h, pcg_state *s, const double *b, double *x, d
         double rho_new = dot(n, s->r, s->z);
         double beta = rho_new / s->rho;
         s->rho = rho_new;
+        ORC_PAR_FOR(n)
         for (int32_t i = 0; i < n; ++i) s->p[i] = s->z[i] + beta * s->p[i];
     }
 }
@@ -1221,6 +1241,7 @@ static double true_resnorm(orc_hier *h, const double *b, const double *x, double
     int32_t n = A->nrows;
     orc_spmv(A, x, work);
     double s = 0.0;
+    ORC_PAR_SUM(n, s)
     for (int32_t i = 0; i < n; ++i) {
         double e = b[i] - work[i];
         s += e * e;

@@ -1339,3 +1339,21 @@ def test_l1_diag_counts_positive_couplings_by_absolute_value():
     # row 0: 5 -2 +3  -> 10;  row 1: -2 4 0 -> 6;  row 2: +3 0 9 -> 12
     A = sp.csr_matrix(np.array([[5.0, -2.0, 3.0], [-2.0, 4.0, 0.0], [3.0, 0.0, 9.0]]))
     assert np.array_equal(oracle.l1_diag(A), [10.0, 6.0, 12.0])
+
+
+def test_openmp_timing_build_matches_sequential_oracle():
+    """The all-core timing build of the oracle (the same source with the
+    solve phase's row loops split over threads) solves like the sequential
+    parity build: same iterations, x within 1e-12 (only dot products sum in
+    another order).  Sized above the loops' threading threshold."""
+    A = gen.poisson3d_7pt(40)
+    b = gen.rhs_uniform(A.n, 1)
+    out = []
+    for omp in (False, True):
+        h = oracle.Hierarchy(A, omp=omp)
+        h.sparsify([0.0, 0.1])
+        out.append(h.pcg(b) + (h.level_sizes(),))
+    (x0, i0, s0), (x1, i1, s1) = out
+    assert s0 == s1 and i0.status == i1.status == 0
+    assert abs(i0.iterations - i1.iterations) <= 1
+    assert np.linalg.norm(x1 - x0) <= 1e-12 * np.linalg.norm(x0)
