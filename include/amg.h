@@ -318,6 +318,14 @@ amg_status amg_residual_noalloc(const amg_hierarchy *h, const double *b, const d
  * far (a diagnostic counter, e.g. to count the launches of one solve). */
 int64_t amg_kernel_launches(void);
 
+/* Host-side fault injection for tests of the out-of-memory paths: the device
+ * allocation that comes `after` allocations from now (0: the next one) fails
+ * as if the device had no memory left -- the entry point that made it returns
+ * AMG_ERR_OOM and releases what it had allocated, and the library stays
+ * usable.  One failure per arming; after < 0 disarms.  No GPU fault is
+ * involved: the allocation is refused on the host before CUDA is asked. */
+void amg_debug_fail_allocation(int64_t after);
+
 /* Device memory the library currently holds for hierarchies (bytes). */
 int64_t amg_device_bytes(const amg_hierarchy *h);
 
@@ -348,6 +356,16 @@ typedef struct {
                                = a quarter of the workspace budget; -1 = none.  A request
                                that finds no room is staged through host memory by the
                                worker thread instead (same result, slower). */
+    int64_t wait_limit_ms;  /* longest the worker waits for one piece of device work (a
+                               batch iteration, a residual check, a host staging copy),
+                               default 120000; must be >= 1.  Every such wait is a poll
+                               of an event.  When one runs out, the worker stops: every
+                               request not yet finished ends with AMG_TIMEOUT (wait
+                               returns it and the ticket is consumed), and later
+                               submits return AMG_TIMEOUT.  The copies of b in submit
+                               and of x in wait always run to completion before those
+                               calls return (the device reads or writes the caller's
+                               memory). */
 } amg_server_opts;
 
 void amg_server_opts_default(amg_server_opts *o);

@@ -74,7 +74,7 @@ class LevelInfo(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("hbm_budget", C.c_int64), ("max_queue", C.c_int),
-                ("max_it", C.c_int), ("stage_budget", C.c_int64)]
+                ("max_it", C.c_int), ("stage_budget", C.c_int64), ("wait_limit_ms", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -107,6 +107,7 @@ SIGNATURES = {
     "amg_last_error": (C.c_char_p, []),
     "amg_device_bytes": (_i64, [_vp]),
     "amg_kernel_launches": (_i64, []),
+    "amg_debug_fail_allocation": (None, [_i64]),
     "amg_residual_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "amg_server_opts_default": (None, [C.POINTER(ServerOpts)]),
     "amg_server_create": (_i, [C.POINTER(ServerOpts), C.POINTER(_vp)]),
@@ -404,6 +405,12 @@ def kernel_launches() -> int:
     return lib().amg_kernel_launches()
 
 
+def debug_fail_allocation(after: int) -> None:
+    """Host-side fault injection: the device allocation `after` allocations
+    from now fails as out of memory (-1 disarms)."""
+    lib().amg_debug_fail_allocation(after)
+
+
 # ---------------------------------------------------------------------------
 # server
 # ---------------------------------------------------------------------------
@@ -411,12 +418,14 @@ class Server:
     """Continuous-batching solve server (amg_server_*)."""
 
     def __init__(self, max_batch: int = 32, hbm_budget: int = 0, max_queue: int = 4096, max_it: int = 500,
-                 stage_budget: int = 0):
+                 stage_budget: int = 0, wait_limit_ms: int | None = None):
         L = lib()
         o = ServerOpts()
         L.amg_server_opts_default(C.byref(o))
         o.max_batch, o.hbm_budget, o.max_queue, o.max_it = max_batch, hbm_budget, max_queue, max_it
         o.stage_budget = stage_budget
+        if wait_limit_ms is not None:
+            o.wait_limit_ms = wait_limit_ms
         out = C.c_void_p()
         _check(L.amg_server_create(C.byref(o), C.byref(out)), "amg_server_create")
         self._s = out

@@ -567,6 +567,8 @@ const char *amg_last_error(void) { return amg::last_error_cstr(); }
 
 int64_t amg_kernel_launches(void) { return amg::g_launches.load(); }
 
+void amg_debug_fail_allocation(int64_t after) { amg::arm_allocation_failure(after); }
+
 int64_t amg_device_bytes(const amg_hierarchy *H) {
     (void)H;
     return amg::g_device_bytes.load();

@@ -25,6 +25,11 @@ void set_last_error(const std::string &msg);
 
 // number of kernels the library has launched (diagnostic counter)
 void count_launch();
+// host-side fault injection: the allocation `after` device allocations from
+// now fails as out of memory (-1: off); injected_allocation_failure() is
+// asked by every device allocation and answers true for the one that fails
+void arm_allocation_failure(int64_t after);
+bool injected_allocation_failure();
 // thread blocks of the given size that fit on the current device at once
 // (SM count x resident blocks per SM at full thread occupancy), cached
 int resident_blocks(int threads_per_block);

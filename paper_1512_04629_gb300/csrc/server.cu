@@ -20,6 +20,13 @@
 // the hierarchy's stream without a host wait.  When the staging budget is
 // used up (or set to none), a request goes through the worker's pinned host
 // buffer instead, as a synchronous copy.
+//
+// Every wait of the worker for device work -- an iteration, a residual
+// check, a host staging copy -- polls an event with the limit
+// opt.wait_limit_ms.  When one runs out the worker stops and every request
+// not yet finished ends with AMG_TIMEOUT.  The copies between the caller's
+// memory and the device in submit and wait run to completion before those
+// calls return: the caller may free that memory afterwards.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -57,6 +64,7 @@ struct Request {
     amg_solve_info info{};
     int status = AMG_NOT_CONVERGED;
     bool done = false;
+    bool has_result = false;   // x (host or d_x) holds the solution
     Clock::time_point submitted;
 };
 
@@ -81,11 +89,10 @@ struct HState {
     std::deque<Request *> queue;
     DevBuf dstage;          // n doubles: admission / retirement staging
     double *hstage = nullptr;  // pinned n doubles
+    cudaEvent_t copy_ev = nullptr;  // host staging copies
     Phase phase = kIdle;
     Clock::time_point launched_at;
 };
-
-constexpr double kWaitLimitSeconds = 120.0;
 
 }  // namespace
 
@@ -103,6 +110,7 @@ struct amg_server {
     int64_t budget = 0, in_use = 0;
     int device = 0;
     std::string fatal;
+    int fatal_status = AMG_ERR_CUDA;
     // device staging of requests (submit uploads, wait downloads)
     cudaMemPool_t pool = nullptr;
     cudaStream_t io = nullptr;
@@ -125,11 +133,31 @@ struct DeviceGuard {
     }
 };
 
+// Waits for `ev` by polling it, at most opt.wait_limit_ms (AMG_TIMEOUT).
+void poll_event(const amg_server *S, cudaEvent_t ev, const char *what) {
+    const auto t0 = Clock::now();
+    while (true) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return;
+        if (e != cudaErrorNotReady) throw Error(AMG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        if (std::chrono::duration<double, std::milli>(Clock::now() - t0).count() > (double)S->opt.wait_limit_ms)
+            throw Error(AMG_TIMEOUT, std::string(what) + " ran past the server's wait limit");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+}
+
+// Waits, bounded, for the work queued on `s` so far (host staging copies).
+void poll_stream(const amg_server *S, cudaStream_t s, cudaEvent_t ev, const char *what) {
+    AMG_CUDA(cudaEventRecord(ev, s));
+    poll_event(S, ev, what);
+}
+
 // Stream-ordered allocation of `bytes` from the staging pool, within the
 // staging budget; nullptr when the budget or the pool has no room (the
 // request then goes through host staging).
 double *stage_alloc(amg_server *S, int64_t bytes, cudaStream_t s) {
     if (!S->pool) return nullptr;
+    if (injected_allocation_failure()) return nullptr;  // as a full pool
     int64_t cur = S->staged.load();
     do {
         if (cur + bytes > S->stage_cap) return nullptr;
@@ -188,7 +216,7 @@ void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
     } else {  // host staging
         bat::gather_column(H.n, w.K, c, w.X.as<double>(), H.dstage.as<double>(), H.stream);
         AMG_CUDA(cudaMemcpyAsync(H.hstage, H.dstage.ptr, bytes, cudaMemcpyDeviceToHost, H.stream));
-        AMG_CUDA(cudaStreamSynchronize(H.stream));
+        poll_stream(S, H.stream, H.copy_ev, "result download (host staging)");
         x.assign(H.hstage, H.hstage + H.n);  // outside the lock: clients keep submitting and waiting
     }
     std::lock_guard<std::mutex> lk(S->mu);
@@ -199,6 +227,7 @@ void finish_request(amg_server *S, HState &H, int c, int status, double tt) {
         r->x = std::move(x);
     }
     r->status = status;
+    r->has_result = true;
     r->info.iterations = sl.its;
     r->info.replacements = sl.reps;
     r->info.status = status;
@@ -264,7 +293,7 @@ bool admit(amg_server *S, HState &H) {
         if (r->d_b) {
             stage_free(S, r, r->d_b, H.stream);  // after the scatters, in stream order
         } else {
-            AMG_CUDA(cudaStreamSynchronize(H.stream));  // the host staging buffers are reused
+            poll_stream(S, H.stream, H.copy_ev, "right-hand side upload (host staging)");  // the buffers are reused
             std::vector<double>().swap(r->b);
         }
         H.slots[c].req = r;
@@ -289,15 +318,17 @@ void release_if_idle(amg_server *S, HState &H) {
     H.ws_bytes = 0;
 }
 
-void fail_all(amg_server *S, const std::string &msg) {
+// the worker stops: every request not yet finished ends with `status`
+void fail_all(amg_server *S, const std::string &msg, int status) {
     std::lock_guard<std::mutex> lk(S->mu);
     S->fatal = msg;
+    S->fatal_status = status;
     for (auto &kv : S->reqs) {
         Request *r = kv.second.get();
         if (!r->done) {
             r->done = true;
-            r->status = AMG_ERR_CUDA;
-            r->info.status = AMG_ERR_CUDA;
+            r->status = status;
+            r->info.status = status;
         }
     }
     for (auto &H : S->hs) {
@@ -440,8 +471,10 @@ void worker_loop(amg_server *S) {
                 }
                 const cudaError_t e = cudaEventQuery(H.done_ev);
                 if (e == cudaErrorNotReady) {
-                    if (std::chrono::duration<double>(Clock::now() - H.launched_at).count() > kWaitLimitSeconds)
-                        throw Error(AMG_TIMEOUT, "batch iteration timed out");
+                    if (std::chrono::duration<double, std::milli>(Clock::now() - H.launched_at).count() >
+                        (double)S->opt.wait_limit_ms)
+                        throw Error(AMG_TIMEOUT, H.phase == kIter ? "a batch iteration ran past the wait limit"
+                                                                  : "a residual check ran past the wait limit");
                     continue;
                 }
                 if (e != cudaSuccess) throw Error(AMG_ERR_CUDA, std::string("stream failed: ") + cudaGetErrorString(e));
@@ -451,8 +484,10 @@ void worker_loop(amg_server *S) {
             }
             if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
+    } catch (const Error &e) {
+        fail_all(S, e.what(), e.status == AMG_TIMEOUT ? AMG_TIMEOUT : AMG_ERR_CUDA);
     } catch (const std::exception &e) {
-        fail_all(S, e.what());
+        fail_all(S, e.what(), AMG_ERR_CUDA);
     }
 }
 
@@ -467,6 +502,7 @@ void amg_server_opts_default(amg_server_opts *o) {
     o->max_queue = 4096;
     o->max_it = 500;
     o->stage_budget = 0;
+    o->wait_limit_ms = 120000;
 }
 
 amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
@@ -477,9 +513,9 @@ amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
         amg_server_opts opt;
         if (o) opt = *o; else amg_server_opts_default(&opt);
         if (opt.max_batch < 1 || opt.max_batch > 64 || opt.max_queue < 1 || opt.max_it < 1 || opt.hbm_budget < 0 ||
-            opt.stage_budget < -1) {
+            opt.stage_budget < -1 || opt.wait_limit_ms < 1) {
             set_last_error("server options out of range (max_batch 1..64, max_queue >= 1, max_it >= 1, "
-                           "hbm_budget >= 0, stage_budget >= -1)");
+                           "hbm_budget >= 0, stage_budget >= -1, wait_limit_ms >= 1)");
             return AMG_ERR_INVALID;
         }
         auto S = std::make_unique<amg_server>();
@@ -516,28 +552,43 @@ amg_status amg_server_create(const amg_server_opts *o, amg_server **out) {
     }
 }
 
+// the CUDA objects of a hierarchy state that never joined the server
+void drop_hstate(HState &H) {
+    if (H.stream) cudaStreamSynchronize(H.stream);
+    if (H.stream) cudaStreamDestroy(H.stream);
+    if (H.done_ev) cudaEventDestroy(H.done_ev);
+    if (H.copy_ev) cudaEventDestroy(H.copy_ev);
+    if (H.hstage) cudaFreeHost(H.hstage);
+    H.stream = nullptr;
+    H.done_ev = H.copy_ev = nullptr;
+    H.hstage = nullptr;
+}
+
 amg_status amg_server_register(amg_server *S, amg_hierarchy *h, int *hid) {
+    set_last_error("");
+    if (!S || !h || !hid) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
+    auto H = std::make_unique<HState>();
     try {
-        set_last_error("");
-        if (!S || !h || !hid) { set_last_error("NULL argument"); return AMG_ERR_INVALID; }
-        auto H = std::make_unique<HState>();
         H->h = &h->h;
         H->n = h->h.lev[0]->n();
         H->slots.resize(S->K);
         AMG_CUDA(cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking));
         AMG_CUDA(cudaEventCreateWithFlags(&H->done_ev, cudaEventDisableTiming));
+        AMG_CUDA(cudaEventCreateWithFlags(&H->copy_ev, cudaEventDisableTiming));
         H->dstage.alloc(sizeof(double) * (H->n + kPad));
         AMG_CUDA(cudaMallocHost(&H->hstage, sizeof(double) * (H->n + kPad)));
         ensure_workspace(h->h, H->stream);
-        AMG_CUDA(cudaStreamSynchronize(H->stream));
+        poll_stream(S, H->stream, H->copy_ev, "hierarchy workspace preparation");
         std::lock_guard<std::mutex> lk(S->mu);
         *hid = (int)S->hs.size();
         S->hs.push_back(std::move(H));
         return AMG_OK;
     } catch (const Error &e) {
+        drop_hstate(*H);
         set_last_error(e.what());
         return e.status;
     } catch (const std::exception &e) {
+        drop_hstate(*H);
         set_last_error(e.what());
         return AMG_ERR_CUDA;
     }
@@ -551,7 +602,7 @@ amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (hid < 0 || hid >= (int)S->hs.size()) { set_last_error("unknown hierarchy id"); return AMG_ERR_INVALID; }
-        if (!S->fatal.empty()) { set_last_error("server failed: " + S->fatal); return AMG_ERR_CUDA; }
+        if (!S->fatal.empty()) { set_last_error("server stopped: " + S->fatal); return (amg_status)S->fatal_status; }
         if (S->queued >= S->opt.max_queue) { set_last_error("queue full"); return AMG_REJECTED; }
         r->n = S->hs[hid]->n;
     }
@@ -567,6 +618,7 @@ amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol
     if (r->bnorm == 0.0) {  // x = 0 solves it
         r->x.assign(n, 0.0);
         r->done = true;
+        r->has_result = true;
         r->status = AMG_OK;
     } else {
         try {
@@ -578,7 +630,9 @@ amg_status amg_server_submit(amg_server *S, int hid, const double *b, double tol
                 r->staged = bytes;
                 AMG_CUDA(cudaMemcpyAsync(r->d_b, b, bytes, cudaMemcpyHostToDevice, S->io));
                 AMG_CUDA(cudaEventRecord(r->ev, S->io));
-                AMG_CUDA(cudaEventSynchronize(r->ev));  // b is the caller's again once submit returns
+                // runs to completion, unbounded: the device reads the caller's b, which
+                // is the caller's again once submit returns
+                AMG_CUDA(cudaEventSynchronize(r->ev));
             } else {
                 r->b.assign(b, b + n);
             }
@@ -616,18 +670,18 @@ amg_status amg_server_wait(amg_server *S, uint64_t ticket, double *x, int timeou
         if (!ok) { set_last_error("request not finished within the time limit"); return AMG_TIMEOUT; }
         r = std::move(it->second);
         S->reqs.erase(it);
-        if (r->status == AMG_ERR_CUDA) set_last_error("server failed: " + S->fatal);
+        if (!r->has_result) set_last_error("server stopped: " + S->fatal);
     }
     amg_status st = (amg_status)r->status;
     try {  // the copy to the caller runs outside the lock
         DeviceGuard dg(S->device);
-        if (st != AMG_ERR_CUDA) {
+        if (r->has_result) {
             if (r->d_x) {
                 AMG_CUDA(cudaStreamWaitEvent(S->io, r->ev, 0));
                 AMG_CUDA(cudaMemcpyAsync(x, r->d_x, sizeof(double) * r->n, cudaMemcpyDeviceToHost, S->io));
                 stage_free(S, r.get(), r->d_x, S->io);
                 AMG_CUDA(cudaEventRecord(r->ev, S->io));
-                AMG_CUDA(cudaEventSynchronize(r->ev));
+                AMG_CUDA(cudaEventSynchronize(r->ev));  // unbounded: the device writes the caller's x
             } else {
                 std::memcpy(x, r->x.data(), sizeof(double) * r->x.size());
             }
@@ -658,6 +712,7 @@ void amg_server_destroy(amg_server *S) {
         if (H->ws) H->h->batch.erase(S->K);
         if (H->stream) cudaStreamDestroy(H->stream);
         if (H->done_ev) cudaEventDestroy(H->done_ev);
+        if (H->copy_ev) cudaEventDestroy(H->copy_ev);
         if (H->hstage) cudaFreeHost(H->hstage);
     }
     if (S->io) {

@@ -16,6 +16,18 @@ std::atomic<int64_t> g_launches{0};
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Host-side fault injection (amg_debug_fail_allocation): while the count is
+// >= 0, every device allocation decrements it, and the one that finds it at
+// 0 fails as out of memory (which disarms it).  No CUDA call is involved.
+static std::atomic<int64_t> g_fail_after{-1};
+void arm_allocation_failure(int64_t after) { g_fail_after.store(after < 0 ? -1 : after); }
+bool injected_allocation_failure() {
+    int64_t v = g_fail_after.load();
+    while (v >= 0)
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    return false;
+}
+
 int resident_blocks(int threads_per_block) {
     static std::atomic<int> sm_count[64];
     int dev = 0;
@@ -101,6 +113,8 @@ static void keep_pool_warm();
 void DevBuf::alloc(size_t b) {
     release();
     if (b == 0) b = 16;
+    if (injected_allocation_failure())
+        throw Error(AMG_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed (injected)");
     keep_pool_warm();
     cudaError_t e;
     if (g_alloc_scoped) {
@@ -156,6 +170,8 @@ void TmpBuf::alloc(size_t b, cudaStream_t s) {
     release();
     keep_pool_warm();
     if (b == 0) b = 16;
+    if (injected_allocation_failure())
+        throw Error(AMG_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed (injected)");
     cudaError_t e = cudaMallocAsync(&ptr, b, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -97,10 +97,11 @@ def test_option_defaults_without_gpu(libpath):
     so = amg.ServerOpts()
     amg.lib().amg_server_opts_default(ctypes.byref(so))
     assert (so.max_batch, so.hbm_budget, so.max_queue, so.max_it, so.stage_budget) == (32, 0, 4096, 500, 0)
+    assert so.wait_limit_ms == 120000
 
 
 @pytest.mark.parametrize("field,value", [("max_batch", 0), ("max_batch", 65), ("max_queue", 0), ("max_it", 0),
-                                         ("hbm_budget", -1), ("stage_budget", -2)])
+                                         ("hbm_budget", -1), ("stage_budget", -2), ("wait_limit_ms", 0)])
 def test_server_options_rejected_before_any_cuda_call(libpath, field, value):
     from paper_1512_04629_gb300 import amg
 
