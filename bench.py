@@ -858,7 +858,10 @@ def main():
     for l in range(last_h.num_levels):
         st = last_h.level_stats(l)
         levels.append({"n": st["n"], "nnz_galerkin": st["nnz_galerkin"], "nnz_operator": st["nnz_operator"],
-                       "spmv": amg.SPMV_NAMES.get(st["spmv_variant"], "?"), "bytes_per_cycle": st["bytes_per_cycle"]})
+                       "spmv": amg.SPMV_NAMES.get(st["spmv_variant"], "?"),
+                       "spmv_P": amg.SPMV_NAMES.get(st["spmv_variant_p"], "-"),
+                       "spmv_R": amg.SPMV_NAMES.get(st["spmv_variant_r"], "-"),
+                       "bytes_per_cycle": st["bytes_per_cycle"]})
 
     # roofline of the dominant solve-phase kernel
     peak, peak_kind = measured_peak()

@@ -88,11 +88,13 @@ enum { AMG_LUMP_DIAG = 0, AMG_LUMP_STRONG = 1 };
  * preconditioner ends with AMG_BREAKDOWN in its own info. */
 enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
 enum { AMG_PREC_FP64 = 0, AMG_PREC_FP32 = 1, AMG_PREC_FP32_BF16 = 2 };
-/* SpMV kernel variants: CSR with T threads per row, or SELL-32 slices. */
+/* SpMV kernel variants: CSR with T threads per row, or SELL-C slices (C rows
+ * per slice, column-major inside it, read by one warp with 32 / C lanes per
+ * row: SELL32 one lane per row, SELL16 two, SELL8 four). */
 enum {
     AMG_SPMV_AUTO = -1,
     AMG_SPMV_CSR2 = 1, AMG_SPMV_CSR4 = 2, AMG_SPMV_CSR8 = 3, AMG_SPMV_CSR16 = 4,
-    AMG_SPMV_CSR32 = 5, AMG_SPMV_SELL32 = 6, AMG_SPMV_CSR1 = 7
+    AMG_SPMV_CSR32 = 5, AMG_SPMV_SELL32 = 6, AMG_SPMV_CSR1 = 7, AMG_SPMV_SELL16 = 8, AMG_SPMV_SELL8 = 9
 };
 
 typedef struct {
@@ -119,6 +121,9 @@ typedef struct {
     double div_factor;   /* AMG_DIVERGED when the residual grows by more than this
                             factor over a check window of k_check CG steps,
                             default 1e3; 0 turns the test off, else >= 1 */
+    int transfer_variant; /* AMG_SPMV_AUTO (default: P and R timed per level
+                            when spmv_variant is AUTO, else the mean-row
+                            heuristic) or an AMG_SPMV_* forced for P and R */
 } amg_options;
 
 typedef struct {
@@ -141,6 +146,8 @@ typedef struct {
     int spmv_variant;       /* AMG_SPMV_* used by the level's relaxation */
     int value_bytes;        /* bytes per stored value in the cycle (8, 4, 2) */
     double bytes_per_cycle; /* algorithmic HBM bytes of the level per V(1,1) cycle */
+    int spmv_variant_p;     /* AMG_SPMV_* of the interpolation x += P x_c (0 on the coarsest) */
+    int spmv_variant_r;     /* AMG_SPMV_* of the restriction b_c = R r (0 on the coarsest) */
 } amg_level_info;
 
 typedef struct amg_hierarchy amg_hierarchy;

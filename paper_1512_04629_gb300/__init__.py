@@ -19,6 +19,7 @@ from .amg import (  # noqa: F401,E402
     debug_fail_allocation,
     METHOD_SPARSE, METHOD_HYBRID, METHOD_NONGALERKIN, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,
     PREC_FP64, PREC_FP32, PREC_FP32_BF16,
-    SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_NAMES,
+    SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_SELL16, SPMV_SELL8,
+    SPMV_CSR1, SPMV_NAMES,
     K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC,
 )

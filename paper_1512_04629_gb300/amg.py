@@ -23,7 +23,9 @@ LUMP_DIAG, LUMP_STRONG = 0, 1
 KRYLOV_CG, KRYLOV_GMRES = 0, 1
 PREC_FP64, PREC_FP32, PREC_FP32_BF16 = 0, 1, 2
 SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_CSR1 = -1, 1, 2, 3, 4, 5, 6, 7
-SPMV_NAMES = {1: "csr2", 2: "csr4", 3: "csr8", 4: "csr16", 5: "csr32", 6: "sell32", 7: "csr1"}
+SPMV_SELL16, SPMV_SELL8 = 8, 9
+SPMV_NAMES = {1: "csr2", 2: "csr4", 3: "csr8", 4: "csr16", 5: "csr32", 6: "sell32", 7: "csr1", 8: "sell16",
+              9: "sell8"}
 # kernel classes of amg_timing_get
 K_PRE, K_RESTRICT, K_PROLONG, K_POST, K_COARSE, K_AP, K_VEC = range(7)
 
@@ -51,7 +53,7 @@ class Options(C.Structure):
                 ("rho_max", C.c_double), ("level_offset", C.c_int), ("spmv_variant", C.c_int),
                 ("use_graph", C.c_int), ("check_every", C.c_int),
                 ("setup_timing", C.c_int), ("lump", C.c_int), ("krylov", C.c_int),
-                ("restart", C.c_int), ("div_factor", C.c_double)]
+                ("restart", C.c_int), ("div_factor", C.c_double), ("transfer_variant", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -66,7 +68,8 @@ class SolveInfo(C.Structure):
 class LevelInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_galerkin", C.c_int64), ("nnz_operator", C.c_int64),
                 ("nnz_p", C.c_int64), ("n_coarse", C.c_int64), ("gamma", C.c_double),
-                ("spmv_variant", C.c_int), ("value_bytes", C.c_int), ("bytes_per_cycle", C.c_double)]
+                ("spmv_variant", C.c_int), ("value_bytes", C.c_int), ("bytes_per_cycle", C.c_double),
+                ("spmv_variant_p", C.c_int), ("spmv_variant_r", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

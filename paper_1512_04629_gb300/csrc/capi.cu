@@ -97,7 +97,7 @@ void check_options(const amg_options &o) {
     require(o.precision >= AMG_PREC_FP64 && o.precision <= AMG_PREC_FP32_BF16, "unknown precision");
     require(o.k_check >= 1 && o.s_levels >= 1, "k_check and s_levels must be >= 1");
     require(o.gamma_min >= 0.0 && std::isfinite(o.rho_max), "bad gamma_min / rho_max");
-    require(o.spmv_variant == AMG_SPMV_AUTO || (o.spmv_variant >= AMG_SPMV_CSR2 && o.spmv_variant <= AMG_SPMV_CSR1),
+    require(o.spmv_variant == AMG_SPMV_AUTO || (o.spmv_variant >= AMG_SPMV_CSR2 && o.spmv_variant <= AMG_SPMV_SELL8),
             "unknown spmv_variant");
     require(o.check_every >= 1, "check_every must be >= 1");
     require(o.lump == AMG_LUMP_DIAG || o.lump == AMG_LUMP_STRONG, "unknown lump");
@@ -105,6 +105,9 @@ void check_options(const amg_options &o) {
     require(o.restart >= 1 && o.restart <= 512, "restart must be in [1, 512]");
     require(o.div_factor == 0.0 || (std::isfinite(o.div_factor) && o.div_factor >= 1.0),
             "div_factor must be 0 (off) or a finite value >= 1");
+    require(o.transfer_variant == AMG_SPMV_AUTO ||
+                (o.transfer_variant >= AMG_SPMV_CSR2 && o.transfer_variant <= AMG_SPMV_SELL8),
+            "unknown transfer_variant");
 }
 
 void check_gammas(const double *g, int n) {
@@ -154,6 +157,7 @@ void amg_options_default(amg_options *o) {
     o->krylov = AMG_KRYLOV_CG;
     o->restart = 30;
     o->div_factor = 1e3;
+    o->transfer_variant = AMG_SPMV_AUTO;
 }
 
 amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_gamma, const amg_options *opt,
@@ -345,6 +349,8 @@ amg_status amg_level_stats(const amg_hierarchy *H, int level, amg_level_info *ou
         out->spmv_variant = V.variant;
         out->value_bytes = V.vbytes;
         out->bytes_per_cycle = level_cycle_bytes(h, level);
+        out->spmv_variant_p = level + 1 < h.nlev() ? V.variant_p : 0;
+        out->spmv_variant_r = level + 1 < h.nlev() ? V.variant_r : 0;
         return AMG_OK;
     });
 }

@@ -6,8 +6,11 @@
 //    16-byte vectors of values and column indices (2 FP64 / 4 FP32 / 8 BF16
 //    entries) read through the non-coherent path, masks the entries outside
 //    its row, gathers x, and the group reduces with xor shuffles;
-//  * SELL-32: one thread per row, 32-row slices stored column-major so each
-//    warp load is one contiguous 128/256-byte segment.
+//  * SELL-C (C = 32, 16, 8): C-row slices stored column-major, read by one
+//    warp with T = 32 / C lanes per row -- lane l takes row l % C and every
+//    T-th entry from l / C -- so each warp load is one contiguous
+//    128/256-byte segment whatever C; a shorter C splits long rows over more
+//    lanes (shorter dependent chains per thread) and pads less.
 // Reductions for PCG are deterministic: fixed grid, per-block partials, and
 // the last block to arrive sums them in block order.
 #include <cuda_bf16.h>
@@ -220,11 +223,99 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     }
 }
 
+// SELL-C with C < 32: one warp per slice of C rows, T = 32 / C lanes per
+// row.  Lane l holds row l % C and the entries k = l / C, l / C + T, ... (the
+// slice width is a multiple of T); its part of the row is loaded U entries
+// at a time -- all values and columns, then all gathers, then the products
+// -- and the T parts are added by xor shuffles.  The row's sum therefore
+// runs in another order than a sequential one (not bit-equal to CSR).
+template <typename VT, typename XT, int OP, bool D16, int C>
+__global__ void __launch_bounds__(kThreads)
+sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
+                     const int32_t *__restrict__ sw, SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
+                     const XT *__restrict__ dinv, const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
+    constexpr int T = 32 / C, U = 4;
+    const int32_t slice = (int32_t)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31, r = lane % C, t = lane / C;
+    if (slice * C >= n) return;  // whole warp: slices are warp-uniform
+    const int32_t pos = slice * C + r;
+    const bool valid = pos < n;
+    const int32_t i = valid ? (perm ? __ldg(perm + pos) : pos) : 0;
+    const int32_t off = __ldg(soff + slice) + lane, w = __ldg(sw + slice);
+    auto gather = [&](int32_t j) {
+        if (OP == kPre) return __ldg(b + j) * __ldg(dinv + j);
+        return __ldg(x + j);
+    };
+    XT acc = XT(0);
+    if (valid) {
+        const int32_t nk = w / T;  // entries of this lane
+        int32_t k = 0;
+        for (; k + U <= nk; k += U) {
+            VT v[U];
+            int32_t c[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int32_t p = off + (k + u) * 32;
+                v[u] = __ldg(sv + p);
+                c[u] = sell_col<D16>(ix, p, i);
+            }
+            XT g[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) g[u] = gather(c[u]);
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc += cvt<VT, XT>(v[u]) * g[u];
+        }
+        for (; k < nk; ++k) {
+            const int32_t p = off + k * 32;
+            acc += cvt<VT, XT>(__ldg(sv + p)) * gather(sell_col<D16>(ix, p, i));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= C; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (!valid || t != 0) return;
+    const XT sum = acc;
+    if (OP == kPre) {
+        XT bi = b[i];
+        o1[i] = bi * dinv[i];
+        o2[i] = bi - sum;
+    } else if (OP == kPost) {
+        o1[i] = x[i] + dinv[i] * (b[i] - sum);
+    } else if (OP == kSpmv) {
+        o1[i] = sum;
+    } else if (OP == kSpmvScale) {
+        o1[i] = sum;
+        o2[i] = sum * dinv[i];
+    } else if (OP == kResX) {
+        o2[i] = b[i] - sum;
+    } else {
+        o1[i] += sum;
+    }
+}
+
+template <typename VT, typename XT, int OP, int C>
+void launch_sell_lanes(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, XT *o1, XT *o2,
+                       cudaStream_t s) {
+    const int32_t n = A.nrows;
+    const SellIdx ix{A.sci, A.sd};
+    const int64_t warps = div_up((int64_t)n, (int64_t)C);
+    const int g = (int)div_up(warps * 32, (int64_t)kThreads);
+    if (A.sd)
+        { sell_lanes_op_kernel<VT, XT, OP, true, C><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    else
+        { sell_lanes_op_kernel<VT, XT, OP, false, C><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+}
+
 template <typename VT, typename XT, int OP>
 void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, XT *o1, XT *o2, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
-    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+    if ((A.variant == AMG_SPMV_SELL16 || A.variant == AMG_SPMV_SELL8) && A.sv && A.sell_c == sell_height(A.variant)) {
+        if (A.sell_c == 16) launch_sell_lanes<VT, XT, OP, 16>(A, b, dinv, x, o1, o2, s);
+        else launch_sell_lanes<VT, XT, OP, 8>(A, b, dinv, x, o1, o2, s);
+        AMG_CHECK_LAUNCH();
+        return;
+    }
+    if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {
         const SellIdx ix{A.sci, A.sd};
         // the load-first path for operators whose rows all fit it (measured:
         // faster at level 0, slower on the longer, irregular coarse rows)
@@ -683,30 +774,33 @@ __global__ void __launch_bounds__(512) sell_sort_kernel(int32_t n, const int32_t
     }
 }
 
-__global__ void slice_width_kernel(int32_t n, const int32_t *rp, const int32_t *perm, int32_t *sw) {
+// width of each slice of C rows: its longest row, rounded up to a multiple
+// of the 32 / C lanes that share a row
+__global__ void slice_width_kernel(int32_t n, const int32_t *rp, const int32_t *perm, int32_t *sw, int C) {
     int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t nsl = (n + 31) / 32;
+    int32_t nsl = (n + C - 1) / C;
     if (s >= nsl) return;
     int32_t w = 0;
-    for (int32_t pos = s * 32; pos < min(n, s * 32 + 32); ++pos) {
+    for (int32_t pos = s * C; pos < min(n, s * C + C); ++pos) {
         int32_t i = perm ? perm[pos] : pos;
         w = max(w, rp[i + 1] - rp[i]);
     }
-    sw[s] = w;
+    const int32_t T = 32 / C;
+    sw[s] = (w + T - 1) / T * T;
 }
 
-__global__ void slice_size_kernel(int32_t nsl, const int32_t *sw, int32_t *sz) {
+__global__ void slice_size_kernel(int32_t nsl, const int32_t *sw, int32_t *sz, int C) {
     int32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < nsl) sz[s] = sw[s] * 32;
+    if (s < nsl) sz[s] = sw[s] * C;
 }
 
 template <typename VT>
 __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
-                                 const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, int16_t *sd) {
+                                 const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, int16_t *sd, int C) {
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t nsl = (n + 31) / 32;
-    if (pos >= nsl * 32) return;
-    int32_t s = pos >> 5, lane = pos & 31;
+    int32_t nsl = (n + C - 1) / C;
+    if (pos >= nsl * C) return;
+    int32_t s = pos / C, lane = pos % C;
     int32_t off = soff[s] + lane, w = sw[s];
     int32_t i = pos < n ? (perm ? perm[pos] : pos) : -1;
     int32_t p0 = i >= 0 ? rp[i] : 0, len = i >= 0 ? rp[i + 1] - p0 : 0;
@@ -716,7 +810,7 @@ __global__ void sell_fill_kernel(int32_t n, const int32_t *rp, const int32_t *ci
     // its own index (offset 0; those operators are square)
     const int32_t pad_col = len > 0 ? ci[p0 + len - 1] : (sd ? (i >= 0 ? i : 0) : 0);
     for (int32_t k = 0; k < w; ++k) {
-        int32_t p = off + k * 32;
+        int32_t p = off + k * C;
         const int32_t c = k < len ? ci[p0 + k] : pad_col;
         if (sd) sd[p] = (int16_t)(i >= 0 ? c - i : 0);
         else sci[p] = c;
@@ -812,7 +906,7 @@ static int launch_ap_sell(const CycMat<double> &A, const double *p, const double
 }
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
-    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+    if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {
         const int blocks = launch_ap_sell<false>(A, p, nullptr, q, sc, red, s);
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
@@ -843,7 +937,7 @@ static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, cons
                                   double *z, const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     const int32_t n = A.nrows;
     constexpr int NV = ZQ ? 2 : 1;
-    if (A.variant == AMG_SPMV_SELL32 && A.sv) {
+    if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {
         int blocks = reduce_blocks(n);
         const SellIdx ix{A.sci, A.sd};
         if (A.sd)
@@ -908,7 +1002,7 @@ void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgSca
 
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s) {
-    if (A.variant == AMG_SPMV_SELL32 && A.sv) {  // the operator's tuned SELL copy, as A p uses
+    if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {  // the operator's tuned SELL copy, as A p uses
         const int blocks = launch_ap_sell<true>(A, x, b, t, sc, red, s);
         launch_finish<1, kFinTt>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
@@ -934,23 +1028,24 @@ template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64
     AMG_CHECK_LAUNCH();
 }
 
-int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s) {
-    int32_t nsl = (n + 31) / 32;
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s, int C) {
+    if (C != 32 && C != 16 && C != 8) throw Error(AMG_ERR_INVALID, "SELL slice height must be 32, 16 or 8");
+    int32_t nsl = (n + C - 1) / C;
     if (nsl == 0) return 0;
     TmpBuf sz(sizeof(int32_t) * (nsl + 1), s);
     if (perm) { sell_sort_kernel<<<div_up(n, kSellSigma), 512, 0, s>>>(n, rp, perm); ::amg::count_launch(); }
-    { slice_width_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(n, rp, perm, sw); ::amg::count_launch(); }
-    { slice_size_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(nsl, sw, sz.as<int32_t>()); ::amg::count_launch(); }
+    { slice_width_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(n, rp, perm, sw, C); ::amg::count_launch(); }
+    { slice_size_kernel<<<div_up(nsl, kThreads), kThreads, 0, s>>>(nsl, sw, sz.as<int32_t>(), C); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     return exclusive_scan_i32(sz.as<int32_t>(), soff, nsl, s);
 }
 
 template <typename VT>
 void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm, const int32_t *soff,
-               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd) {
-    int32_t nsl = (n + 31) / 32;
+               const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd, int C) {
+    int32_t nsl = (n + C - 1) / C;
     if (nsl == 0) return;
-    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * 32, kThreads), kThreads, 0, s>>>(n, rp, ci, v, perm, soff, sw, sci, sv, sd); ::amg::count_launch(); }
+    { sell_fill_kernel<VT><<<div_up((int64_t)nsl * C, kThreads), kThreads, 0, s>>>(n, rp, ci, v, perm, soff, sw, sci, sv, sd, C); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -985,12 +1080,12 @@ template void convert_values<__nv_bfloat16>(const double *, __nv_bfloat16 *, int
 template void convert_vec_from_f64<float>(const double *, float *, int64_t, cudaStream_t);
 template void convert_vec_to_f64<float>(const float *, double *, int64_t, cudaStream_t);
 template void sell_fill<double>(int32_t, const int32_t *, const int32_t *, const double *, const int32_t *,
-                                const int32_t *, const int32_t *, int32_t *, double *, cudaStream_t, int16_t *);
+                                const int32_t *, const int32_t *, int32_t *, double *, cudaStream_t, int16_t *, int);
 template void sell_fill<float>(int32_t, const int32_t *, const int32_t *, const float *, const int32_t *,
-                               const int32_t *, const int32_t *, int32_t *, float *, cudaStream_t, int16_t *);
+                               const int32_t *, const int32_t *, int32_t *, float *, cudaStream_t, int16_t *, int);
 template void sell_fill<__nv_bfloat16>(int32_t, const int32_t *, const int32_t *, const __nv_bfloat16 *,
                                        const int32_t *, const int32_t *, const int32_t *, int32_t *, __nv_bfloat16 *,
-                                       cudaStream_t, int16_t *);
+                                       cudaStream_t, int16_t *, int);
 
 }  // namespace cyc
 }  // namespace amg

@@ -5,8 +5,14 @@
 
 namespace amg {
 
+// SELL slice height of an SpMV variant (32, 16, 8), 0 for the CSR variants.
+// A slice of C rows is read by one warp with 32 / C lanes per row.
+inline int sell_height(int variant) {
+    return variant == AMG_SPMV_SELL32 ? 32 : variant == AMG_SPMV_SELL16 ? 16 : variant == AMG_SPMV_SELL8 ? 8 : 0;
+}
+
 // A matrix as the cycle kernels read it: CSR in value type VT, plus an
-// optional SELL-32 copy (slices of 32 rows, column-major inside a slice).
+// optional SELL-C copy (slices of C rows, column-major inside a slice).
 template <typename VT> struct CycMat {
     int32_t nrows = 0, ncols = 0;
     int64_t nnz = 0;
@@ -19,6 +25,7 @@ template <typename VT> struct CycMat {
     const VT *sv = nullptr;
     int32_t max_row = 0;  // most stored entries of a row (0: not known)
     int variant = AMG_SPMV_CSR4;
+    int sell_c = 32;      // slice height of the SELL copy
 };
 
 // Device-side scalars of one PCG run.
@@ -107,14 +114,18 @@ void true_residual(const CycMat<double> &A, const double *b, const double *x, do
 template <typename VT> void convert_values(const double *src, VT *dst, int64_t n, cudaStream_t s);
 template <typename XT> void convert_vec_from_f64(const double *src, XT *dst, int64_t n, cudaStream_t s);
 template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64_t n, cudaStream_t s);
-// SELL-32 layout: slice widths and offsets, optionally over rows sorted by
-// length (descending) inside windows of kSellSigma rows (perm: position ->
-// row); returns the padded entry count
+// SELL-C layout (C = 32, 16 or 8 rows per slice): slice widths (a multiple
+// of 32 / C, the lanes that share a row) and offsets, optionally over rows
+// sorted by length (descending) inside windows of kSellSigma rows (perm:
+// position -> row); returns the padded entry count.  sw and soff hold
+// ceil(n / C) + 1 entries.
 constexpr int kSellSigma = 1024;
-int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s);
+int64_t sell_layout(int32_t n, const int32_t *rp, int32_t *perm, int32_t *soff, int32_t *sw, cudaStream_t s,
+                    int C = 32);
 template <typename VT>
 void sell_fill(int32_t n, const int32_t *rp, const int32_t *ci, const VT *v, const int32_t *perm,
-               const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd = nullptr);
+               const int32_t *soff, const int32_t *sw, int32_t *sci, VT *sv, cudaStream_t s, int16_t *sd = nullptr,
+               int C = 32);
 // max over stored entries of |column - row| (square operators), for the int16 SELL offsets;
 // *max_row (if given) receives the longest row
 int32_t max_col_offset(int32_t n, const int32_t *rp, const int32_t *ci, cudaStream_t s, int32_t *max_row = nullptr);

@@ -287,40 +287,42 @@ static int heuristic_variant(const DevCSR &M) {
     return AMG_SPMV_CSR32;
 }
 
-// SELL-32 copy of the relaxed operator.  If slices of consecutive rows would
-// pad the matrix by more than 3%, rows are sorted by length inside windows of
-// kSellSigma rows (SELL-C-sigma) and kernels write through the permutation.
-// SELL-32 layout of M with values vals (length-sorted rows when the plain
-// slicing would pad more than 3%)
+// SELL-C copy (C = 32, 16 or 8 rows per slice) of M with values vals.  If
+// slices of consecutive rows would pad the matrix by more than 3%, rows are
+// sorted by length inside windows of kSellSigma rows (SELL-C-sigma) and
+// kernels write through the permutation.
 template <typename VT>
-static void build_sell_copy(const DevCSR &M, const VT *vals, SellCopy &S, cudaStream_t s) {
-    const int32_t nsl = (M.nrows + 31) / 32;
+static void build_sell_copy(const DevCSR &M, const VT *vals, SellCopy &S, cudaStream_t s, int C = 32) {
+    const int32_t nsl = (M.nrows + C - 1) / C;
+    S.c = C;
     S.soff.alloc(sizeof(int32_t) * (nsl + 1));
     S.sw.alloc(sizeof(int32_t) * (nsl + 1));
     S.perm.release();
-    S.entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, S.soff.as<int32_t>(), S.sw.as<int32_t>(), s);
+    S.entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, S.soff.as<int32_t>(), S.sw.as<int32_t>(), s, C);
     if ((double)S.entries > 1.03 * (double)M.nnz) {
         S.perm.alloc(sizeof(int32_t) * (M.nrows + kPad));
         S.entries = cyc::sell_layout(M.nrows, M.rp(), S.perm.as<int32_t>(), S.soff.as<int32_t>(),
-                                     S.sw.as<int32_t>(), s);
+                                     S.sw.as<int32_t>(), s, C);
     }
     S.sci.alloc(sizeof(int32_t) * (S.entries + kPad));
     S.sv.alloc(sizeof(VT) * (S.entries + kPad));
     cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), vals, S.perm.ptr ? S.perm.as<int32_t>() : nullptr,
-                       S.soff.as<int32_t>(), S.sw.as<int32_t>(), S.sci.as<int32_t>(), S.sv.as<VT>(), s);
+                       S.soff.as<int32_t>(), S.sw.as<int32_t>(), S.sci.as<int32_t>(), S.sv.as<VT>(), s, nullptr, C);
 }
 
-template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
+// SELL-C copy of the relaxed operator of V (C = 32, 16 or 8)
+template <typename VT> static void build_sell(Level &V, cudaStream_t s, int C = 32) {
     const DevCSR &M = V.op();
-    int32_t nsl = (M.nrows + 31) / 32;
+    int32_t nsl = (M.nrows + C - 1) / C;
+    V.sell_c = C;
     V.soff.alloc(sizeof(int32_t) * (nsl + 1));
     V.sw.alloc(sizeof(int32_t) * (nsl + 1));
     V.sperm.release();
-    V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, V.soff.as<int32_t>(), V.sw.as<int32_t>(), s);
+    V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), nullptr, V.soff.as<int32_t>(), V.sw.as<int32_t>(), s, C);
     if ((double)V.sell_entries > 1.03 * (double)M.nnz) {
         V.sperm.alloc(sizeof(int32_t) * (M.nrows + kPad));
         V.sell_entries = cyc::sell_layout(M.nrows, M.rp(), V.sperm.as<int32_t>(), V.soff.as<int32_t>(),
-                                          V.sw.as<int32_t>(), s);
+                                          V.sw.as<int32_t>(), s, C);
     }
     // columns as int16 offsets from the row when every one fits (2 bytes less per entry)
     V.sci.release();
@@ -333,8 +335,9 @@ template <typename VT> static void build_sell(Level &V, cudaStream_t s) {
     CycMat<VT> m = op_mat<VT>(V);
     cyc::sell_fill<VT>(M.nrows, M.rp(), M.ci(), m.v, V.sperm.ptr ? V.sperm.as<int32_t>() : nullptr,
                        V.soff.as<int32_t>(), V.sw.as<int32_t>(), d16 ? nullptr : V.sci.as<int32_t>(),
-                       V.sv.as<VT>(), s, d16 ? V.sd.as<int16_t>() : nullptr);
+                       V.sv.as<VT>(), s, d16 ? V.sd.as<int16_t>() : nullptr, C);
 }
+
 
 static void free_sell(Level &V) {
     V.soff.release(); V.sw.release(); V.sci.release(); V.sd.release(); V.sv.release(); V.sperm.release();
@@ -383,7 +386,10 @@ static void tune_cache_store_locked(const TuneKey &k, int variant) {
     }
 }
 
-static std::vector<int> tune_candidates(const DevCSR &M, int vbytes) {
+// fine: level 0, whose SELL copy also serves the outer PCG's fused SELL-32
+// kernels, keeps one lane per row; the coarse levels' longer rows may split
+// over 2 or 4 lanes (SELL-16, SELL-8)
+static std::vector<int> tune_candidates(const DevCSR &M, int vbytes, bool fine) {
     double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
     int V = 16 / vbytes;  // entries per 16-byte load
     std::vector<int> c;
@@ -394,11 +400,30 @@ static std::vector<int> tune_candidates(const DevCSR &M, int vbytes) {
     }
     if (c.empty()) c.push_back(AMG_SPMV_CSR4);
     c.push_back(AMG_SPMV_SELL32);
+    if (!fine && mean >= 4.0) c.push_back(AMG_SPMV_SELL16);
+    if (!fine && mean >= 8.0) c.push_back(AMG_SPMV_SELL8);
     return c;
 }
 
-template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Level &V, cudaStream_t s) {
-    const std::vector<int> cands = tune_candidates(V.op(), V.vbytes);
+// Evicts the L2 cache before a timed trial: in the V-cycle a level's
+// operator is re-read after the finer levels' traffic has passed through L2,
+// so a trial on an L2-resident operator would favour the wrong variant.
+struct L2Flush {
+    TmpBuf buf;
+    void run(cudaStream_t s) {
+        if (!buf.ptr) {
+            int dev = 0, l2 = 0;
+            AMG_CUDA(cudaGetDevice(&dev));
+            AMG_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+            buf.alloc((size_t)std::max(l2, 1 << 20) * 3 / 2, s);
+        }
+        AMG_CUDA(cudaMemsetAsync(buf.ptr, 0, buf.bytes, s));
+    }
+};
+
+template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Level &V, cudaStream_t s, bool fine) {
+    const std::vector<int> cands = tune_candidates(V.op(), V.vbytes, fine);
+    L2Flush flush;
     cudaEvent_t e0, e1;
     AMG_CUDA(cudaEventCreate(&e0));
     AMG_CUDA(cudaEventCreate(&e1));
@@ -407,10 +432,13 @@ template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Lev
     const XT *dinv = sizeof(XT) == 8 ? reinterpret_cast<const XT *>(V.dinv.ptr) : V.dinv32.as<XT>();
     for (int c : cands) {
         V.variant = c;
+        const int C = sell_height(c);
+        if (C && V.sell_c != C) build_sell<VT>(V, s, C);
         CycMat<VT> m = op_mat<VT>(V);
         cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);  // warm-up
         float tmin = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
+            flush.run(s);
             AMG_CUDA(cudaEventRecord(e0, s));
             cyc::post_smooth<VT, XT>(m, V.x.as<XT>(), V.b.as<XT>(), dinv, V.xo.as<XT>(), s);
             AMG_CUDA(cudaEventRecord(e1, s));
@@ -422,6 +450,8 @@ template <typename VT, typename XT> static void autotune_level(Hierarchy &h, Lev
         if (tmin < best * 0.98f) { best = tmin; best_v = c; }
     }
     V.variant = best_v;
+    const int C = sell_height(best_v);
+    if (C && V.sell_c != C) build_sell<VT>(V, s, C);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     (void)h;
@@ -490,16 +520,17 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
             tune = false;
         }
     }
-    if (tune || V.variant == AMG_SPMV_SELL32) {
-        if (V.vbytes == 8) build_sell<double>(V, s);
-        else if (V.vbytes == 4) build_sell<float>(V, s);
-        else build_sell<__nv_bfloat16>(V, s);
+    if (tune || sell_height(V.variant)) {
+        const int C = tune ? 32 : sell_height(V.variant);
+        if (V.vbytes == 8) build_sell<double>(V, s, C);
+        else if (V.vbytes == 4) build_sell<float>(V, s, C);
+        else build_sell<__nv_bfloat16>(V, s, C);
     }
     if (tune) {
-        if (V.vbytes == 8) autotune_level<double, double>(h, V, s);
-        else if (V.vbytes == 4) autotune_level<float, float>(h, V, s);
-        else autotune_level<__nv_bfloat16, float>(h, V, s);
-        if (V.variant != AMG_SPMV_SELL32) free_sell(V);
+        if (V.vbytes == 8) autotune_level<double, double>(h, V, s, l == 0);
+        else if (V.vbytes == 4) autotune_level<float, float>(h, V, s, l == 0);
+        else autotune_level<__nv_bfloat16, float>(h, V, s, l == 0);
+        if (!sell_height(V.variant)) free_sell(V);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_store_locked(key, V.variant);
     }
@@ -531,6 +562,7 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
     Level &V = *h.lev[l];
     Level &C = *h.lev[l + 1];
     int vb = sizeof(XT);
+    L2Flush flush;
     cudaEvent_t e0, e1;
     AMG_CUDA(cudaEventCreate(&e0));
     AMG_CUDA(cudaEventCreate(&e1));
@@ -542,26 +574,30 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
             auto it = g_tune_cache.find(key);
             if (it != g_tune_cache.end()) {
                 variant = it->second;
-                if (variant == AMG_SPMV_SELL32) build_sell_copy<XT>(M, vals, S, s);
+                if (sell_height(variant)) build_sell_copy<XT>(M, vals, S, s, sell_height(variant));
                 return;
             }
         }
-        build_sell_copy<XT>(M, vals, S, s);
+        S.release();  // a copy of an earlier operator must not stand in for this one
         double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
         int V16 = 16 / vb;
         float best = 1e30f;
         int best_v = variant;
         const int vars[] = {AMG_SPMV_CSR1, AMG_SPMV_CSR2, AMG_SPMV_CSR4, AMG_SPMV_CSR8, AMG_SPMV_CSR16,
-                            AMG_SPMV_SELL32};
+                            AMG_SPMV_SELL32, AMG_SPMV_SELL16, AMG_SPMV_SELL8};
         for (int v : vars) {
+            const int C = sell_height(v);
             double cover = (double)cyc::threads_per_row(v) * V16;
-            if (v != AMG_SPMV_CSR1 && v != AMG_SPMV_SELL32 &&
+            if (!C && v != AMG_SPMV_CSR1 &&
                 !(cover >= mean / 4.0 && cover <= std::max(4.0 * mean, (double)V16 * 2)))
                 continue;
+            if ((C == 16 && mean < 4.0) || (C == 8 && mean < 8.0)) continue;
+            if (C && (!S.sv.ptr || S.c != C)) build_sell_copy<XT>(M, vals, S, s, C);
             variant = v;
             run();
             float tmin = 1e30f;
             for (int rep = 0; rep < 2; ++rep) {
+                flush.run(s);
                 AMG_CUDA(cudaEventRecord(e0, s));
                 run();
                 AMG_CUDA(cudaEventRecord(e1, s));
@@ -573,7 +609,9 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
             if (tmin < best * 0.98f) { best = tmin; best_v = v; }
         }
         variant = best_v;
-        if (variant != AMG_SPMV_SELL32) S.release();
+        const int C = sell_height(variant);
+        if (!C) S.release();
+        else if (S.c != C) build_sell_copy<XT>(M, vals, S, s, C);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_cache_store_locked(key, best_v);
     };
@@ -601,7 +639,22 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
         timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, s); });
         if (l == h.nlev() - 1) timed(h, 15, l, 0.0, s, [&] { prepare_coarse(h, s); });
     }
-    if (h.opt.spmv_variant == AMG_SPMV_AUTO) {
+    if (h.opt.transfer_variant != AMG_SPMV_AUTO) {  // forced for P and R
+        const int tv = h.opt.transfer_variant, C = sell_height(tv);
+        for (int l : levels) {
+            if (l + 1 >= h.nlev() || h.lev[l]->pr_tuned) continue;
+            Level &V = *h.lev[l];
+            V.variant_p = V.variant_r = tv;
+            if (C && h.opt.precision == AMG_PREC_FP64) {
+                build_sell_copy<double>(V.P, V.P.v(), V.psell, s, C);
+                build_sell_copy<double>(V.R, V.R.v(), V.rsell, s, C);
+            } else if (C) {
+                build_sell_copy<float>(V.P, V.pv32.as<float>(), V.psell, s, C);
+                build_sell_copy<float>(V.R, V.rv32.as<float>(), V.rsell, s, C);
+            }
+            V.pr_tuned = true;
+        }
+    } else if (h.opt.spmv_variant == AMG_SPMV_AUTO) {
         for (int l : levels) {
             if (l + 1 >= h.nlev() || h.lev[l]->pr_tuned) continue;
             timed(h, 14, l, 0.0, s, [&] {

@@ -18,6 +18,7 @@ namespace amg {
 struct SellCopy {
     DevBuf soff, sw, sci, sv, perm;
     int64_t entries = 0;
+    int c = 32;  // slice height
     void release() {
         soff.release(); sw.release(); sci.release(); sv.release(); perm.release();
         entries = 0;
@@ -46,11 +47,12 @@ struct Level {
     DevBuf hv32, hv16;     // FP32 / BF16 values of the relaxed operator
     DevBuf pv32, rv32;     // FP32 values of P and R
     DevBuf dinv32;
-    DevBuf soff, sw, sci, sv;  // SELL-32 copy of the relaxed operator
+    DevBuf soff, sw, sci, sv;  // SELL-C copy of the relaxed operator (C = sell_c)
     DevBuf sd;                 // its columns as int16 offsets from the row (instead of sci) when they fit
     DevBuf sperm;              // SELL position -> row when rows are length-sorted
     DevBuf sv64;               // level 0 in FP32 modes: FP64 values in the same SELL layout (outer PCG)
     int64_t sell_entries = 0;
+    int sell_c = 32;
     int32_t max_row = 0;       // longest row of the relaxed operator (kernel choice)
     SellCopy psell, rsell;     // SELL copies of P and R (cycle precision) when they win the trial
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
@@ -170,7 +172,8 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
     else vals = V.hv16.as<VT>();
     CycMat<VT> m = make_mat<VT>(M, vals);
     if (V.sv.ptr) {
-        m.nslices = (M.nrows + 31) / 32;
+        m.sell_c = V.sell_c;
+        m.nslices = (M.nrows + V.sell_c - 1) / V.sell_c;
         m.soff = V.soff.as<int32_t>();
         m.sw = V.sw.as<int32_t>();
         m.sci = V.sci.ptr ? V.sci.as<int32_t>() : nullptr;
@@ -185,7 +188,8 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
 
 template <typename VT> inline void attach_sell(CycMat<VT> &m, const SellCopy &S) {
     if (!S.sv.ptr) return;
-    m.nslices = (m.nrows + 31) / 32;
+    m.sell_c = S.c;
+    m.nslices = (m.nrows + S.c - 1) / S.c;
     m.soff = S.soff.as<int32_t>();
     m.sw = S.sw.as<int32_t>();
     m.sci = S.sci.as<int32_t>();

@@ -93,7 +93,7 @@ def test_option_defaults_without_gpu(libpath):
     assert (o.theta, o.max_size, o.max_levels, o.method, o.precision) == (0.25, 100, 25, amg.METHOD_SPARSE, 0)
     assert (o.lump, o.krylov, o.restart) == (amg.LUMP_DIAG, amg.KRYLOV_CG, 30)
     assert (o.k_check, o.s_levels, o.gamma_min, o.rho_max) == (3, 1, 0.01, 0.5)
-    assert o.div_factor == 1e3
+    assert o.div_factor == 1e3 and o.transfer_variant == amg.SPMV_AUTO
     so = amg.ServerOpts()
     amg.lib().amg_server_opts_default(ctypes.byref(so))
     assert (so.max_batch, so.hbm_budget, so.max_queue, so.max_it, so.stage_budget) == (32, 0, 4096, 500, 0)
@@ -123,7 +123,8 @@ def test_server_options_rejected_before_any_cuda_call(libpath, field, value):
     (0.25, dict(check_every=0), None, "check_every"), (0.25, dict(lump=4), None, "lump"),
     (0.25, dict(krylov=3), None, "krylov"), (0.25, dict(restart=0), None, "restart"),
     (0.25, dict(restart=513), None, "restart"), (0.25, dict(div_factor=0.5), None, "div_factor"),
-    (0.25, dict(div_factor=float("inf")), None, "div_factor"),
+    (0.25, dict(div_factor=float("inf")), None, "div_factor"), (0.25, dict(spmv_variant=10), None, "spmv_variant"),
+    (0.25, dict(transfer_variant=10), None, "transfer_variant"),
     (0.25, {}, [0.5, 0.1], "level 0 is never sparsified"), (0.25, {}, [0.0, float("nan")], "finite"),
     (0.25, {}, [0.0, -0.1], ">= 0"),
 ])

@@ -201,13 +201,49 @@ def test_sparsify_on_oracle_galerkin(amg, gamma):
         assert st["nnz_operator"] == ref.matrix(l, "Ahat").nnz
 
 
-@pytest.mark.parametrize("variant", [-1, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [-1, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("gamma", [0.0, 0.1])
 def test_vcycle_matches_oracle(amg, variant, gamma):
     A = gen.poisson3d_7pt(23)  # n = 12167: ragged against 32-row slices and 256-thread blocks
     ref = oracle.Hierarchy(A)
     ref.sparsify([0.0, gamma])
     h = _assemble_oracle(amg, ref, gamma=[0.0, gamma], spmv_variant=variant)
+    for seed in (5, 6):
+        r = gen.rhs_uniform(A.n, seed)
+        z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        h.precond_apply(torch.from_numpy(r).cuda(), z)
+        zr = ref.vcycle(r)
+        np.testing.assert_allclose(z.cpu().numpy(), zr, rtol=1e-12, atol=1e-12 * np.abs(zr).max())
+
+
+@pytest.mark.parametrize("relax,transfer", [(8, 8), (9, 9), (8, 9), (9, 8), (6, 8), (6, 9), (2, 9)])
+@pytest.mark.parametrize("case", ["3d7_23", "3d27_13", "fv7_18"])
+def test_vcycle_sell_lanes_matches_oracle(amg, relax, transfer, case):
+    """SELL-16 / SELL-8 (two or four lanes per row, rows summed in another
+    order than sequentially) for the relaxation and, forced, for the transfers
+    P and R, on sizes ragged against every slice height."""
+    A = {"3d7_23": lambda: gen.poisson3d_7pt(23), "3d27_13": lambda: gen.poisson3d_27pt(13),
+         "fv7_18": lambda: gen.fv7_lognormal(18, seed=3)}[case]()
+    ref = oracle.Hierarchy(A)
+    ref.sparsify([0.0, 0.1])
+    h = _assemble_oracle(amg, ref, gamma=[0.0, 0.1], spmv_variant=relax, transfer_variant=transfer)
+    for l in range(h.num_levels - 1):
+        st = h.level_stats(l)
+        assert (st["spmv_variant"], st["spmv_variant_p"], st["spmv_variant_r"]) == (relax, transfer, transfer)
+    for seed in (5, 6):
+        r = gen.rhs_uniform(A.n, seed)
+        z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        h.precond_apply(torch.from_numpy(r).cuda(), z)
+        zr = ref.vcycle(r)
+        np.testing.assert_allclose(z.cpu().numpy(), zr, rtol=1e-12, atol=1e-12 * np.abs(zr).max())
+    # the FP32 / BF16 instantiations of the same kernels, inside flexible CG
+    b = gen.rhs_uniform(A.n, 1)
+    xr, ir = ref.pcg(b, tol=1e-8)
+    for prec in (1, 2):
+        h2 = amg.Hierarchy.setup(A, gamma=[0.0, 0.1], precision=prec, spmv_variant=relax, transfer_variant=transfer)
+        x, info = h2.solve(b, tol=1e-8)
+        assert info.status == 0 and info.final_relres <= 1e-8
+        assert np.linalg.norm(x - xr) <= 1e-6 * np.linalg.norm(xr)
     for seed in (5, 6):
         r = gen.rhs_uniform(A.n, seed)
         z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
