@@ -321,6 +321,62 @@ const char *amg_last_error(void);
 amg_status amg_residual_noalloc(const amg_hierarchy *h, const double *b, const double *x, double *r,
                                 double *rnorm, void *stream);
 
+/*
+ * Row-partitioned execution (the paper's parallel SpMV, Section 2, and its
+ * communication model, Section 4).  Each level's rows are split into `parts`
+ * contiguous blocks, one per process of a distributed solve: the finest
+ * level in blocks of n / parts rows, every coarser level so that each block
+ * keeps its own C points (coarse point c belongs to the block of the fine
+ * point it came from).  A block's columns split into the ones it owns (the
+ * diagonal block) and ghosts owned by other blocks (the off-diagonal block),
+ * whose values it receives before each product; a message is one ordered
+ * pair of blocks that exchange at least one value.
+ *
+ * amg_halo_plan -- the plan of one operator, on the host (no GPU): rows
+ * [row0[p], row0[p+1]) form block p, which owns columns [col0[p], col0[p+1]).
+ * Caller-allocated outputs: cext[nnz] (each entry's column in its block's
+ * numbering: owned columns j - col0[p], then ghost g as (col0[p+1] - col0[p])
+ * + g), goff[parts + 1] (block p's ghosts are gcol[goff[p] .. goff[p+1]),
+ * increasing), gcol[nnz] (room for the worst case), recv[parts * parts]
+ * (values block p receives from block q, at p * parts + q).  1 <= parts <= 64.
+ * AMG_ERR_INVALID for inconsistent bounds or columns out of range.
+ */
+amg_status amg_halo_plan(int64_t nrows, int64_t ncols, const int32_t *rowptr, const int32_t *col, int parts,
+                         const int64_t *row0, const int64_t *col0, int32_t *cext, int64_t *goff,
+                         int32_t *gcol, int64_t *recv);
+
+/*
+ * amg_partition -- split every level of h into `parts` blocks (1 <= parts <=
+ * 64; 1 removes the split) and plan each operator of the solve: the relaxed
+ * operator Ahat_l (A_0 on level 0), P_l and R_l; the Galerkin A_l is planned
+ * for its statistics.  Solves (amg_solve, CG or GMRES, FP64 precision only;
+ * AMG_ERR_INVALID otherwise) then run block by block on this GPU: before each
+ * product every block gathers its ghost values -- the exchange a distributed
+ * run performs by messages -- and multiplies its rows by its own columns and
+ * its ghosts.  Rows are summed in stored order, so a partitioned solve equals
+ * an unpartitioned one whose relaxation and transfers run one lane per row
+ * (spmv_variant = transfer_variant = AMG_SPMV_CSR1) bit for bit.  amg_sparsify
+ * and amg_reintroduce re-plan the levels they change.  Batched and served
+ * solves ignore the split.
+ */
+amg_status amg_partition(amg_hierarchy *h, int parts);
+
+/* Communication of one level per product (SpMV) under the current split. */
+typedef struct {
+    int parts;
+    int64_t messages;           /* ordered block pairs exchanging values, relaxed operator */
+    int64_t halo_values;        /* ghost values received, summed over blocks */
+    int64_t max_messages;       /* most messages one block receives */
+    int64_t max_halo;           /* most ghost values one block receives */
+    int64_t messages_galerkin;  /* the same two for the Galerkin A_l */
+    int64_t halo_galerkin;
+    int64_t messages_p, halo_p; /* interpolation x += P x_c (0 on the coarsest level) */
+    int64_t messages_r, halo_r; /* restriction b_c = R r */
+} amg_comm_info;
+amg_status amg_comm_stats(const amg_hierarchy *h, int level, amg_comm_info *out);
+/* row0[0 .. parts]: the block boundaries of level `level` (parts + 1 values). */
+amg_status amg_partition_rows(const amg_hierarchy *h, int level, int64_t *row0);
+
 /* Number of CUDA kernels this process has launched through the library so
  * far (a diagnostic counter, e.g. to count the launches of one solve). */
 int64_t amg_kernel_launches(void);

@@ -16,7 +16,7 @@ _os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 from .amg import (  # noqa: F401,E402
     OK, ERR_INVALID, ERR_OOM, ERR_CUDA, NOT_CONVERGED, DIVERGED, BREAKDOWN, TIMEOUT, REJECTED,
     AmgError, Hierarchy, Matrix, Server, SolveInfo, default_options, device_bytes, kernel_launches, lib,
-    debug_fail_allocation,
+    debug_fail_allocation, halo_plan,
     METHOD_SPARSE, METHOD_HYBRID, METHOD_NONGALERKIN, LUMP_DIAG, LUMP_STRONG, KRYLOV_CG, KRYLOV_GMRES,
     PREC_FP64, PREC_FP32, PREC_FP32_BF16,
     SPMV_AUTO, SPMV_CSR2, SPMV_CSR4, SPMV_CSR8, SPMV_CSR16, SPMV_CSR32, SPMV_SELL32, SPMV_SELL16, SPMV_SELL8,

@@ -75,6 +75,16 @@ class LevelInfo(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class CommInfo(C.Structure):
+    _fields_ = [("parts", C.c_int), ("messages", C.c_int64), ("halo_values", C.c_int64),
+                ("max_messages", C.c_int64), ("max_halo", C.c_int64), ("messages_galerkin", C.c_int64),
+                ("halo_galerkin", C.c_int64), ("messages_p", C.c_int64), ("halo_p", C.c_int64),
+                ("messages_r", C.c_int64), ("halo_r", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ServerOpts(C.Structure):
     _fields_ = [("max_batch", C.c_int), ("hbm_budget", C.c_int64), ("max_queue", C.c_int),
                 ("max_it", C.c_int), ("stage_budget", C.c_int64), ("wait_limit_ms", C.c_int64)]
@@ -112,6 +122,10 @@ SIGNATURES = {
     "amg_kernel_launches": (_i64, []),
     "amg_debug_fail_allocation": (None, [_i64]),
     "amg_residual_noalloc": (_i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "amg_halo_plan": (_i, [_i64, _i64, _vp, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "amg_partition": (_i, [_vp, _i]),
+    "amg_comm_stats": (_i, [_vp, _i, C.POINTER(CommInfo)]),
+    "amg_partition_rows": (_i, [_vp, _i, _vp]),
     "amg_server_opts_default": (None, [C.POINTER(ServerOpts)]),
     "amg_server_create": (_i, [C.POINTER(ServerOpts), C.POINTER(_vp)]),
     "amg_server_register": (_i, [_vp, _vp, C.POINTER(_i)]),
@@ -386,6 +400,22 @@ class Hierarchy:
         _check(self._lib.amg_level_array(self._h, level, code, _ptr(out), C.byref(cnt)), "amg_level_array")
         return out[: cnt.value]
 
+    def partition(self, parts: int):
+        """Split every level into `parts` row blocks (1 removes the split)."""
+        _check(self._lib.amg_partition(self._h, parts), "amg_partition")
+        self._parts = parts
+
+    def comm_stats(self, level: int) -> dict:
+        ci = CommInfo()
+        _check(self._lib.amg_comm_stats(self._h, level, C.byref(ci)), "amg_comm_stats")
+        return ci.as_dict()
+
+    def partition_rows(self, level: int) -> np.ndarray:
+        parts = getattr(self, "_parts", 1)
+        out = np.zeros(max(parts, 1) + 1, dtype=np.int64)
+        _check(self._lib.amg_partition_rows(self._h, level, _ptr(out)), "amg_partition_rows")
+        return out
+
     def timing_enable(self, on: bool = True):
         _check(self._lib.amg_timing_enable(self._h, 1 if on else 0), "amg_timing_enable")
 
@@ -406,6 +436,25 @@ def device_bytes() -> int:
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return lib().amg_kernel_launches()
+
+
+def halo_plan(rowptr, col, ncols: int, row0, col0):
+    """Host-side halo plan of a row-partitioned CSR operator (amg_halo_plan;
+    needs no GPU).  Returns (cext, goff, gcol, recv) with recv as a
+    parts x parts array (values block p receives from block q)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    row0 = np.ascontiguousarray(row0, dtype=np.int64)
+    col0 = np.ascontiguousarray(col0, dtype=np.int64)
+    parts = len(row0) - 1
+    nnz = int(rowptr[-1])
+    cext = np.zeros(max(nnz, 1), dtype=np.int32)
+    goff = np.zeros(parts + 1, dtype=np.int64)
+    gcol = np.zeros(max(nnz, 1), dtype=np.int32)
+    recv = np.zeros(parts * parts, dtype=np.int64)
+    _check(lib().amg_halo_plan(len(rowptr) - 1, ncols, _ptr(rowptr), _ptr(col), parts, _ptr(row0), _ptr(col0),
+                               _ptr(cext), _ptr(goff), _ptr(gcol), _ptr(recv)), "amg_halo_plan")
+    return cext[:nnz], goff, gcol[: goff[-1]], recv.reshape(parts, parts)
 
 
 def debug_fail_allocation(after: int) -> None:

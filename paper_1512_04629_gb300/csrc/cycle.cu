@@ -15,6 +15,8 @@
 // the last block to arrive sums them in block order.
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "cycle_ops.cuh"
 
@@ -223,6 +225,100 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-partitioned execution (amg_partition): before each product every block
+// gathers its ghost values from the global vector -- the exchange that a
+// distributed run performs by messages -- then the same CSR kernels run with
+// a gather that reads owned columns from the block's slice of the vector and
+// ghosts from its part of the ghost buffer.  The loops, grids and sums are the
+// unpartitioned kernels', so the results are the same bits.
+// ---------------------------------------------------------------------------
+__global__ void part_exchange_kernel(int64_t nghost, const int32_t *__restrict__ gcol, const double *__restrict__ src,
+                                     const double *__restrict__ scale, double *__restrict__ gbuf) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nghost) return;
+    const int32_t j = __ldg(gcol + k);
+    gbuf[k] = scale ? __ldg(src + j) * __ldg(scale + j) : __ldg(src + j);
+}
+
+// block of row i (rows past the end, which gather nothing, get block 0)
+__device__ __forceinline__ int part_of(const PartView &pv, int32_t i) {
+    int p = 0;
+    while (p + 1 < pv.parts && __ldg(pv.row0 + p + 1) <= i) ++p;
+    return p;
+}
+
+// where row i's gathers read: owned columns from src + col0[p] (times
+// scale + col0[p] when given), ghosts from gbuf + goff[p]
+struct PartRow {
+    const double *xl, *dl, *g;
+    int32_t nloc;
+};
+__device__ __forceinline__ PartRow part_row(const PartView &pv, int32_t i, int32_t n, const double *src,
+                                            const double *scale) {
+    const int p = i < n ? part_of(pv, i) : 0;
+    const int32_t c0 = __ldg(pv.col0 + p);
+    return PartRow{src + c0, scale ? scale + c0 : nullptr, pv.gbuf + __ldg(pv.goff + p), __ldg(pv.col0 + p + 1) - c0};
+}
+
+template <int T, int OP>
+__global__ void __launch_bounds__(kThreads)
+part_op_kernel(int32_t n, const int32_t *__restrict__ rp, PartView pv, const double *__restrict__ v,
+               const double *__restrict__ b, const double *__restrict__ dinv, const double *__restrict__ x,
+               double *__restrict__ o1, double *__restrict__ o2) {
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t i = (int32_t)(g / T);
+    int t = (int)(g % T);
+    int32_t p0 = 0, p1 = 0;
+    if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
+    double s;
+    if (OP == kPre) {
+        const PartRow pr = part_row(pv, i, n, b, dinv);
+        s = csr_row_sum<double, double, T>(p0, p1, t, pv.cext, v, [&](int32_t c) {
+            return c < pr.nloc ? __ldg(pr.xl + c) * __ldg(pr.dl + c) : __ldg(pr.g + (c - pr.nloc));
+        });
+    } else {
+        const PartRow pr = part_row(pv, i, n, x, nullptr);
+        s = csr_row_sum<double, double, T>(p0, p1, t, pv.cext, v, [&](int32_t c) {
+            return c < pr.nloc ? __ldg(pr.xl + c) : __ldg(pr.g + (c - pr.nloc));
+        });
+    }
+    if (i >= n || t != 0) return;
+    if (OP == kPre) {
+        double bi = b[i];
+        o1[i] = bi * dinv[i];
+        o2[i] = bi - s;
+    } else if (OP == kPost) {
+        o1[i] = x[i] + dinv[i] * (b[i] - s);
+    } else if (OP == kSpmv) {
+        o1[i] = s;
+    } else if (OP == kSpmvScale) {
+        o1[i] = s;
+        o2[i] = s * dinv[i];
+    } else if (OP == kResX) {
+        o2[i] = b[i] - s;
+    } else {
+        o1[i] += s;
+    }
+}
+
+// the exchange for an operator whose products gather src (times scale)
+void part_exchange(const PartView &pv, const double *src, const double *scale, cudaStream_t s) {
+    if (pv.nghost == 0) return;
+    { part_exchange_kernel<<<(int)div_up(pv.nghost, (int64_t)kThreads), kThreads, 0, s>>>(pv.nghost, pv.gcol, src, scale, pv.gbuf); ::amg::count_launch(); }
+}
+
+template <int OP>
+void part_op(const CycMat<double> &A, const double *b, const double *dinv, const double *x, double *o1, double *o2,
+             cudaStream_t s) {
+    const int32_t n = A.nrows;
+    if (OP == kPre) part_exchange(A.part, b, dinv, s);
+    else part_exchange(A.part, x, nullptr, s);
+    // one lane per row: the order of the unpartitioned one-lane kernels
+    { part_op_kernel<1, OP><<<(int)div_up((int64_t)n, (int64_t)kThreads), kThreads, 0, s>>>(n, A.rp, A.part, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    AMG_CHECK_LAUNCH();
+}
+
 // SELL-C with C < 32: one warp per slice of C rows, T = 32 / C lanes per
 // row.  Lane l holds row l % C and the entries k = l / C, l / C + T, ... (the
 // slice width is a multiple of T); its part of the row is loaded U entries
@@ -309,6 +405,12 @@ template <typename VT, typename XT, int OP>
 void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, XT *o1, XT *o2, cudaStream_t s) {
     int32_t n = A.nrows;
     if (n == 0) return;
+    if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+        if (A.part.parts) {
+            part_op<OP>(A, b, dinv, x, o1, o2, s);
+            return;
+        }
+    }
     if ((A.variant == AMG_SPMV_SELL16 || A.variant == AMG_SPMV_SELL8) && A.sv && A.sell_c == sell_height(A.variant)) {
         if (A.sell_c == 16) launch_sell_lanes<VT, XT, OP, 16>(A, b, dinv, x, o1, o2, s);
         else launch_sell_lanes<VT, XT, OP, 8>(A, b, dinv, x, o1, o2, s);
@@ -543,10 +645,10 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
 }
 
 // q = A p (vector-CSR, T lanes per row) and p . q
-template <int T>
+template <int T, bool PART = false>
 __global__ void __launch_bounds__(kThreads)
 ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
-          const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc, Reduce red) {
+          const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc, Reduce red, PartView pv = PartView()) {
     block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -555,7 +657,15 @@ ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__
         int t = (int)(g % T);
         int32_t p0 = 0, p1 = 0;
         if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(p + j); });
+        double s;
+        if constexpr (PART) {  // ci: block-local columns
+            const PartRow pr = part_row(pv, i, n, p, nullptr);
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t c) {
+                return c < pr.nloc ? __ldg(pr.xl + c) : __ldg(pr.g + (c - pr.nloc));
+            });
+        } else {
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(p + j); });
+        }
         if (i < n && t == 0) {
             q[i] = s;
             part[0] += p[i] * s;
@@ -602,11 +712,11 @@ rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z,
     block_partials<2>(part, red);
 }
 
-template <int T>
+template <int T, bool PART = false>
 __global__ void __launch_bounds__(kThreads)
 resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
              const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ t_out,
-             PcgScalars *sc, Reduce red) {
+             PcgScalars *sc, Reduce red, PartView pv = PartView()) {
     block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -615,7 +725,15 @@ resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restric
         int t = (int)(g % T);
         int32_t p0 = 0, p1 = 0;
         if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        double s;
+        if constexpr (PART) {
+            const PartRow pr = part_row(pv, i, n, x, nullptr);
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t c) {
+                return c < pr.nloc ? __ldg(pr.xl + c) : __ldg(pr.g + (c - pr.nloc));
+            });
+        } else {
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        }
         if (i < n && t == 0) {
             double e = b[i] - s;
             t_out[i] = e;
@@ -628,11 +746,12 @@ resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restric
 // level-0 post-smoothing z = x + d (b - A x) with r.z (r = b) and, for
 // flexible CG only (ZQ), z.q -- plain CG's beta needs no z.q, so the FP64
 // cycle reads no q and issues one FMA less per row
-template <int T, bool ZQ>
+template <int T, bool ZQ, bool PART = false>
 __global__ void __launch_bounds__(kThreads)
 post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
-                   double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+                   double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red,
+                   PartView pv = PartView()) {
     block_partials_begin();
     double part[ZQ ? 2 : 1];
 #pragma unroll
@@ -644,7 +763,15 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
         const int t = (int)(g % T);
         int32_t p0 = 0, p1 = 0;
         if (i < n) { p0 = __ldg(rp + i); p1 = __ldg(rp + i + 1); }
-        double s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        double s;
+        if constexpr (PART) {
+            const PartRow pr = part_row(pv, i, n, x, nullptr);
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t c) {
+                return c < pr.nloc ? __ldg(pr.xl + c) : __ldg(pr.g + (c - pr.nloc));
+            });
+        } else {
+            s = csr_row_sum<double, double, T>(p0, p1, t, ci, v, [&](int32_t j) { return __ldg(x + j); });
+        }
         if (i < n && t == 0) {
             double bi = b[i];
             double zi = x[i] + dinv[i] * (bi - s);
@@ -906,6 +1033,14 @@ static int launch_ap_sell(const CycMat<double> &A, const double *p, const double
 }
 
 void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
+    if (A.part.parts) {  // row-partitioned: exchange, then the one-lane kernel's loop
+        part_exchange(A.part, p, nullptr, s);
+        const int blocks = reduce_blocks(A.nrows);
+        { ap_kernel<1, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.part.cext, A.v, p, q, sc, red, A.part); ::amg::count_launch(); }
+        launch_finish<1, kFinAp>(blocks, red, sc, s);
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {
         const int blocks = launch_ap_sell<false>(A, p, nullptr, q, sc, red, s);
         launch_finish<1, kFinAp>(blocks, red, sc, s);
@@ -937,6 +1072,14 @@ static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, cons
                                   double *z, const double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     const int32_t n = A.nrows;
     constexpr int NV = ZQ ? 2 : 1;
+    if (A.part.parts) {
+        part_exchange(A.part, x, nullptr, s);
+        const int blocks = reduce_blocks(n);
+        { post_rz_csr_kernel<1, ZQ, true><<<blocks, kThreads, 0, s>>>(n, A.rp, A.part.cext, A.v, x, b, dinv, z, q, sc, red, A.part); ::amg::count_launch(); }
+        launch_finish<NV, kFinRz>(blocks, red, sc, s);
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {
         int blocks = reduce_blocks(n);
         const SellIdx ix{A.sci, A.sd};
@@ -1002,6 +1145,14 @@ void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgSca
 
 void true_residual(const CycMat<double> &A, const double *b, const double *x, double *t, PcgScalars *sc,
                    Reduce red, cudaStream_t s) {
+    if (A.part.parts) {  // row-partitioned: the four-lane kernel's loop, as below
+        part_exchange(A.part, x, nullptr, s);
+        const int blocks = reduce_blocks((int64_t)A.nrows * 4);
+        { resid_kernel<4, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.part.cext, A.v, b, x, t, sc, red, A.part); ::amg::count_launch(); }
+        launch_finish<1, kFinTt>(blocks, red, sc, s);
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     if (A.variant == AMG_SPMV_SELL32 && A.sv && A.sell_c == 32) {  // the operator's tuned SELL copy, as A p uses
         const int blocks = launch_ap_sell<true>(A, x, b, t, sc, red, s);
         launch_finish<1, kFinTt>(blocks, red, sc, s);

@@ -11,6 +11,19 @@ inline int sell_height(int variant) {
     return variant == AMG_SPMV_SELL32 ? 32 : variant == AMG_SPMV_SELL16 ? 16 : variant == AMG_SPMV_SELL8 ? 8 : 0;
 }
 
+// A row-partitioned operator (amg_partition): its columns in block-local
+// numbering, and where each block's ghost values come from.
+struct PartView {
+    int parts = 0;                  // 0: not partitioned
+    const int32_t *cext = nullptr;  // per stored entry: owned column j - col0[p], or nloc + ghost index
+    const int32_t *row0 = nullptr;  // parts + 1: first row of each block
+    const int32_t *col0 = nullptr;  // parts + 1: first owned column of each block
+    const int32_t *goff = nullptr;  // parts + 1: first ghost of each block in gbuf
+    const int32_t *gcol = nullptr;  // global column of each ghost
+    double *gbuf = nullptr;         // ghost values, written by the exchange
+    int64_t nghost = 0;
+};
+
 // A matrix as the cycle kernels read it: CSR in value type VT, plus an
 // optional SELL-C copy (slices of C rows, column-major inside a slice).
 template <typename VT> struct CycMat {
@@ -26,6 +39,7 @@ template <typename VT> struct CycMat {
     int32_t max_row = 0;  // most stored entries of a row (0: not known)
     int variant = AMG_SPMV_CSR4;
     int sell_c = 32;      // slice height of the SELL copy
+    PartView part;        // set when the hierarchy runs row-partitioned (FP64 only)
 };
 
 // Device-side scalars of one PCG run.

@@ -638,6 +638,7 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
     for (int l : levels) {
         timed(h, 14, l, 0.0, s, [&] { prepare_level(h, l, s); });
         if (l == h.nlev() - 1) timed(h, 15, l, 0.0, s, [&] { prepare_coarse(h, s); });
+        if (h.parts > 1) replan_relaxation(h, l, s);
     }
     if (h.opt.transfer_variant != AMG_SPMV_AUTO) {  // forced for P and R
         const int tv = h.opt.transfer_variant, C = sell_height(tv);

@@ -25,6 +25,28 @@ struct SellCopy {
     }
 };
 
+// One operator split into row blocks (amg_partition): the device copy of its
+// halo plan and its ghost buffer; recv (parts x parts, values block p
+// receives from block q) stays on the host for the statistics.
+struct PartOp {
+    DevBuf cext, gcol, bounds, gbuf;  // bounds: int32 row0 | col0 | goff, parts + 1 each
+    int parts = 0;
+    int64_t nghost = 0;
+    std::vector<int64_t> recv;
+    PartView view() const {
+        PartView v;
+        v.parts = parts;
+        v.cext = cext.as<int32_t>();
+        v.row0 = bounds.as<int32_t>();
+        v.col0 = v.row0 + parts + 1;
+        v.goff = v.col0 + parts + 1;
+        v.gcol = gcol.as<int32_t>();
+        v.gbuf = gbuf.as<double>();
+        v.nghost = nghost;
+        return v;
+    }
+};
+
 // One level l of the hierarchy.  A is the retained Galerkin operator
 // (Algorithm 4 keeps it so Algorithm 5 can reintroduce entries); H is the
 // relaxed operator Ahat_l (an alias of A where nothing is dropped).
@@ -57,6 +79,12 @@ struct Level {
     SellCopy psell, rsell;     // SELL copies of P and R (cycle precision) when they win the trial
     int variant = AMG_SPMV_CSR4, variant_p = AMG_SPMV_CSR2, variant_r = AMG_SPMV_CSR8;
     bool pr_tuned = false;  // transfer-operator variants chosen by timed trials
+    // row-partitioned execution (amg_partition): block boundaries of this
+    // level's rows, the plans of the relaxed operator, P and R, and the
+    // receive counts of the Galerkin A_l (statistics only)
+    std::vector<int64_t> prow0;
+    std::unique_ptr<PartOp> part_h, part_p, part_r;
+    std::vector<int64_t> recv_galerkin;
 
     // work vectors in the cycle precision (b, x, r, post-smoothed output)
     DevBuf b, x, r, xo;
@@ -107,6 +135,7 @@ struct Hierarchy {
     IdleRelease idle_release;  // first member: destroyed after every buffer below
     amg_options opt{};
     int device = 0;
+    int parts = 1;  // row blocks of every level (amg_partition); 1 = not partitioned
     std::vector<std::unique_ptr<Level>> lev;
     DevBuf coarse_inv;  // FP64 dense inverse of the coarsest relaxed operator
     int32_t coarse_n = 0;
@@ -183,6 +212,8 @@ template <typename VT> inline CycMat<VT> op_mat(const Level &V) {
     }
     m.max_row = V.max_row;
     m.variant = V.variant;
+    if constexpr (sizeof(VT) == 8)
+        if (V.part_h) m.part = V.part_h->view();
     return m;
 }
 
@@ -204,6 +235,8 @@ template <typename XT> inline CycMat<XT> p_mat(const Level &V) {
     CycMat<XT> m = make_mat<XT>(V.P, vals);
     attach_sell<XT>(m, V.psell);
     m.variant = V.variant_p;
+    if constexpr (sizeof(XT) == 8)
+        if (V.part_p) m.part = V.part_p->view();
     return m;
 }
 
@@ -214,6 +247,8 @@ template <typename XT> inline CycMat<XT> r_mat(const Level &V) {
     CycMat<XT> m = make_mat<XT>(V.R, vals);
     attach_sell<XT>(m, V.rsell);
     m.variant = V.variant_r;
+    if constexpr (sizeof(XT) == 8)
+        if (V.part_r) m.part = V.part_r->view();
     return m;
 }
 
@@ -221,6 +256,10 @@ template <typename XT> inline const XT *dinv_of(const Level &V) {
     if constexpr (sizeof(XT) == 8) return reinterpret_cast<const XT *>(V.dinv.ptr);
     else return V.dinv32.as<XT>();
 }
+
+// row-partitioned execution (partition.cu): re-plan the relaxed operator of
+// level l after it changed (sparsify / reintroduce)
+void replan_relaxation(Hierarchy &h, int l, cudaStream_t s);
 
 // drivers (hierarchy.cu)
 // Algorithm 1; with method AMG_METHOD_NONGALERKIN each new coarse operator is
