@@ -16,6 +16,10 @@ Also reported, all outside the timed region:
   * `arms`: solve-only time to 1e-8 (setup excluded, median of 5) for the
     Galerkin, gamma in {0.01, 0.1, 1} and adaptive hierarchies of the same
     workload, each with an eager per-kernel breakdown of where the time goes;
+  * `communication`: the paper's communication measure -- every level split
+    into 8 and 64 row blocks (amg_partition), messages and ghost values per
+    product for Galerkin and sparsified hierarchies, and the alpha-beta model
+    time of a V-cycle's relaxation products (a model, not a GPU measurement);
   * `legs` (one GPU only): the metric's other configurations, each with its
     own config, CUDA-event timing and sampled clocks -- c3: 27-point 192^3
     FP64 vs FP32 vs FP32 + BF16 time to 1e-8; c4: lognormal FV 160^3 batched
@@ -651,6 +655,44 @@ def run_aniso(args):
     _lumping_arms(args, A, arms, f"aniso: rotated anisotropic Q1 {N}^2 (n={A.n}, theta pi/8, eps 1e-3), GMRES(30)")
 
 
+# the paper's alpha-beta model (Section 4), with its Blue Waters constants
+ALPHA_S, BETA_S_PER_BYTE = 1.8e-6, 1.8e-9
+
+
+def communication(A_dev, parts_list=(8, 64)):
+    """The paper's communication measure for the bench workload: each level
+    split into row blocks (amg_partition), messages and ghost values per
+    product of the relaxed operator (Galerkin vs sparsified), P and R, and
+    the alpha-beta model time of one V(1,1) cycle on the busiest block
+    (2 products with the relaxed operator, 1 with R, 1 with P per level).
+    The model uses the paper's constants: a model of a distributed run, not
+    a measurement on this GPU."""
+    import paper_1512_04629_gb300 as amg
+
+    out = {"model": f"alpha-beta (Section 4), alpha = {ALPHA_S:g} s, beta = {BETA_S_PER_BYTE:g} s/byte, 8-byte values",
+           "by_parts": {}}
+    for parts in parts_list:
+        per = {}
+        for name, g in (("galerkin", 0.0), ("gamma_0.1", 0.1), ("gamma_1.0", 1.0)):
+            h = amg.Hierarchy.setup(A_dev, gamma=[0.0, g] if g else None)
+            h.partition(parts)
+            levels, model = [], 0.0
+            for l in range(h.num_levels):
+                st = h.comm_stats(l)
+                levels.append({"messages": st["messages"], "halo_values": st["halo_values"],
+                               "max_messages": st["max_messages"], "max_halo": st["max_halo"],
+                               "messages_P": st["messages_p"], "halo_P": st["halo_p"],
+                               "messages_R": st["messages_r"], "halo_R": st["halo_r"]})
+                if l + 1 < h.num_levels:  # the coarsest level is a dense solve, not a product
+                    model += 2 * (ALPHA_S * st["max_messages"] + BETA_S_PER_BYTE * 8 * st["max_halo"])
+            per[name] = {"levels": levels, "model_us_per_vcycle_relaxation": round(1e6 * model, 2),
+                         "messages_per_vcycle": 2 * sum(v["messages"] for v in levels[:-1]),
+                         "halo_values_per_vcycle": 2 * sum(v["halo_values"] for v in levels[:-1])}
+            del h
+        out["by_parts"][str(parts)] = per
+    return out
+
+
 def solve_arms(args, A_dev, nnz0, bd, xd, stream, reps=5):
     """Solve-only time to tol (setup excluded) on the bench workload for the
     Galerkin, gamma in {0.01, 0.1, 1} and adaptive (Algorithm 5 from gamma 1)
@@ -933,6 +975,10 @@ def main():
     if not args.no_arms:
         arms = solve_arms(args, A_dev, A.nnz, bd, xd, stream)
 
+    comm = None
+    if not args.no_arms:
+        comm = communication(A_dev)
+
     # the other configurations of the metric, each with its own config and clocks
     legs = None
     if world == 1 and not args.no_legs:
@@ -959,7 +1005,7 @@ def main():
         "iterations": statistics.median(its), "levels": levels,
         "roofline": roofline, "vcycle_GBps": vcycle_bytes / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms else None,
         "top_kernels": kernels, "solve_ms_per_level": per_level_ms, "setup_phases_ms": _median_phases(setup_phases),
-        "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "legs": legs, "clocks": clocks,
+        "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "communication": comm, "legs": legs, "clocks": clocks,
         "gpu_launches": launches,
     }
     print(json.dumps(line))
