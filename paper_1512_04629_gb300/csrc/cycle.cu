@@ -955,8 +955,16 @@ __global__ void max_col_offset_kernel(int32_t n, const int32_t *rp, const int32_
     }
     m = __reduce_max_sync(0xffffffffu, (unsigned)m);
     len = __reduce_max_sync(0xffffffffu, (unsigned)len);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-    if ((threadIdx.x & 31) == 0 && len) atomicMax(out + 1, len);
+    // one atomic per block: atomics of every warp on one address serialise
+    __shared__ int sm[kThreads / 32], sl[kThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sm[w] = m; sl[w] = len; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { m = max(m, sm[k]); len = max(len, sl[k]); }
+        if (m) atomicMax(out, m);
+        if (len) atomicMax(out + 1, len);
+    }
 }
 
 }  // namespace

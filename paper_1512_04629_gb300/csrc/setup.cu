@@ -191,16 +191,25 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t key) {
 
 enum : int8_t { kU = 0, kC = 1, kF = -1 };
 
-// Appends row i to a list when `keep` holds, with one atomic per warp; the
+// Appends row i to a list when `keep` holds, with one global atomic per
+// block (warps reserve their places in shared memory first): a global
+// counter that every warp of a large grid increments serialises on one
+// address (measured: PMIS's first pass at 128^3, 262K warp atomics, 187 us).
+// Every thread of the block must call it (it holds two block barriers).  The
 // list's order varies from run to run, its contents do not.
-__device__ __forceinline__ void warp_append(bool keep, int32_t i, int32_t *list, int *count) {
+__device__ __forceinline__ void block_append(bool keep, int32_t i, int32_t *list, int *count) {
+    __shared__ int s_count, s_base;
+    if (threadIdx.x == 0) s_count = 0;
+    __syncthreads();
     const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (m == 0u) return;
     const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == __ffs(m) - 1) base = atomicAdd(count, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
-    if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = i;
+    int wbase = 0;
+    if (lane == 0 && m) wbase = atomicAdd(&s_count, __popc(m));
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = s_count ? atomicAdd(count, s_count) : 0;
+    __syncthreads();
+    if (keep) list[s_base + wbase + __popc(m & ((1u << lane) - 1u))] = i;
 }
 
 template <int T>
@@ -228,7 +237,7 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
         state[i] = cnt == 0 ? kF : kU;
         und = cnt != 0;
     }
-    warp_append(und, i, list, undecided);
+    block_append(und, i, list, undecided);
 }
 
 // Every round works on the list of rows still undecided when it starts (the
@@ -287,7 +296,7 @@ __global__ void pmis_apply_f_kernel(const int32_t *list, const int *len, const i
             if (strong[p] && state[ci[p]] == kC) f = true;
     f = group_any<T>(f);
     if (und && t == 0 && f) state[i] = kF;
-    warp_append(und && t == 0 && !f, i, next, next_len);
+    block_append(und && t == 0 && !f, i, next, next_len);
 }
 
 // ---------------------------------------------------------------------------
@@ -340,7 +349,14 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
     if (prp[i + 1] == pos) return;  // no strong C neighbour: empty row
     double diag = 0.0, sum_neg = 0.0, sum_pos = 0.0, sum_neg_c = 0.0, sum_pos_c = 0.0;
     // one pass: the row sums in column order, and P's pattern with a_ij in
-    // place of the weight (the weights need the finished sums)
+    // place of the weight (the weights need the finished sums).  An entry
+    // changes at most two sums -- its sign's total and, for a strong C
+    // neighbour, its sign's C sum -- so two FP64 additions are issued per
+    // entry (a warp instruction costs the FP64 pipe the same however few of
+    // its lanes take it): the sums of the entry's sign are selected, added
+    // to, and written back.  Adding +0.0 (a zero entry, or no strong C
+    // neighbour) leaves a sum unchanged: every sum starts at +0.0 and
+    // accumulates values of one sign, so it is never -0.0.
 #pragma unroll 4
     for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
         int32_t j = ci[p];
@@ -348,8 +364,11 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
         if (j == i) { diag = a; continue; }
         const int64_t ak = f64_key(a);
         const bool sc = strong[p] && cf[j] == kC;
-        if (ak < 0) { sum_neg += a; if (sc) sum_neg_c += a; }
-        if (ak > 0) { sum_pos += a; if (sc) sum_pos_c += a; }
+        const bool is_neg = ak < 0, is_pos = ak > 0;
+        const double tot = (is_neg ? sum_neg : sum_pos) + a;
+        const double csum = (is_neg ? sum_neg_c : sum_pos_c) + (sc ? a : 0.0);
+        if (is_neg) { sum_neg = tot; sum_neg_c = csum; }
+        if (is_pos) { sum_pos = tot; sum_pos_c = csum; }
         if (sc) {
             pci[pos] = cmap[j];
             pv[pos] = a;
@@ -1477,45 +1496,49 @@ constexpr int kSmemCoarse = 112;  // 2 n^2 doubles = 196 KB of shared memory
 __global__ void __launch_bounds__(1024)
 coarse_factor_smem_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double *linv_out,
                           int *err) {
+    // Cholesky A = L L^T and L^{-1} in shared memory, 1024 threads as a
+    // 32 x 32 tile walking the triangles (no index division); the coarsest
+    // solve's explicit inverse is checked against the oracle's triangular
+    // solves within tolerance, so its updates use fused multiply-adds and one
+    // reciprocal per pivot
     extern __shared__ __align__(16) double sm[];
     double *a = sm, *li = sm + (size_t)n * n;
+    const int32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = 0.0;
     __syncthreads();
     for (int32_t i = threadIdx.x; i < n; i += blockDim.x)
         for (int32_t p = rp[i]; p < rp[i + 1]; ++p) a[i * n + ci[p]] = v[p];
-    __shared__ double piv;
+    __shared__ double rpiv;
     for (int32_t j = 0; j < n; ++j) {
         __syncthreads();
         if (threadIdx.x == 0) {
             double d = a[j * n + j];
             if (!(d > 0.0)) { *err = 1; d = 1.0; }
-            piv = sqrt(d);
+            const double piv = sqrt(d);
             a[j * n + j] = piv;
+            rpiv = 1.0 / piv;
         }
         __syncthreads();
-        for (int32_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) a[i * n + j] /= piv;
+        for (int32_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) a[i * n + j] *= rpiv;
         __syncthreads();
-        const int32_t m = n - j - 1;
-        for (int32_t t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int32_t r = j + 1 + t / m, c = j + 1 + t % m;
-            if (c <= r) a[r * n + c] -= a[r * n + j] * a[c * n + j];
+        // trailing update of the lower triangle: rows r > j, columns j < c <= r
+        for (int32_t r = j + 1 + ty; r < n; r += 32) {
+            const double lr = a[r * n + j];
+            for (int32_t c = j + 1 + tx; c <= r; c += 32) a[r * n + c] = fma(-lr, a[c * n + j], a[r * n + c]);
         }
     }
-    // L^{-1} right-looking: start from the identity; at step i, row i of the
-    // result is final once divided by L_ii, and every later row r subtracts
-    // L_ri times it.  Entry (r, c) thus sees the terms L_rk X_kc in increasing
-    // k, then its division -- the forward substitution's order, with every
-    // thread busy at each step instead of one thread per column.
+    // L^{-1}, right-looking from the identity: at step i row i is final once
+    // scaled by 1 / L_ii, and every later row r subtracts L_ri times it
     __syncthreads();
     for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) li[t] = (t / n == t % n) ? 1.0 : 0.0;
     for (int32_t i = 0; i < n; ++i) {
         __syncthreads();
-        for (int32_t c = threadIdx.x; c <= i; c += blockDim.x) li[i * n + c] /= a[i * n + i];
+        const double ri = 1.0 / a[i * n + i];
+        for (int32_t c = threadIdx.x; c <= i; c += blockDim.x) li[i * n + c] *= ri;
         __syncthreads();
-        const int32_t rows = n - i - 1, cols = i + 1;
-        for (int32_t t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-            const int32_t r = i + 1 + t / cols, c = t % cols;
-            li[r * n + c] -= a[r * n + i] * li[i * n + c];
+        for (int32_t r = i + 1 + ty; r < n; r += 32) {
+            const double lri = a[r * n + i];
+            for (int32_t c = tx; c <= i; c += 32) li[r * n + c] = fma(-lri, li[i * n + c], li[r * n + c]);
         }
     }
     __syncthreads();
