@@ -1218,31 +1218,68 @@ __global__ void sparsify_guard_kernel(int32_t n, const int32_t *rp, const int32_
     if (live && t == 0) cnt[i] = c;
 }
 
-__global__ void sparsify_compact_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                        const double *v, const int32_t *diagpos,
-                                        const uint8_t *keep, const int32_t *hrp, int32_t *hci,
-                                        double *hv) {
-    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    // one pass in column order: the lumped diagonal starts from a_ii (read
-    // first, from its known position) and takes the dropped entries in
-    // order; kept entries are written as met, the diagonal's value last
-    double d = v[diagpos[i]];
-    int32_t pos = hrp[i], dpos = -1;
-#pragma unroll 4
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        const double a = v[p];
-        if (!keep[p]) {
-            d += a;
-            continue;
-        }
-        const int32_t j = ci[p];
-        hci[pos] = j;
-        hv[pos] = a;
-        if (j == i) dpos = pos;
-        ++pos;
+// The same with a group of T lanes per row: chunks of T consecutive entries
+// are read together (coalesced), a kept entry's output slot is the row's
+// running count plus its place among the chunk's kept entries (ballot), and
+// lane 0 adds the chunk's dropped entries to the lumped diagonal in lane
+// order -- column order, as the one-thread kernel, so the same bits.
+template <int T>
+__global__ void __launch_bounds__(kThreads)
+sparsify_compact_lanes_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v,
+                              const int32_t *diagpos, const uint8_t *keep, const int32_t *hrp, int32_t *hci,
+                              double *hv) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    const bool live = i < n;  // no early exit: ballots and shuffles need every lane
+    const int lane = threadIdx.x & 31;
+    const int first = lane & ~(T - 1);  // the group's first lane in the warp
+    const unsigned gbits = T == 32 ? 0xffffffffu : ((1u << T) - 1u);
+    int32_t p0 = 0, p1 = 0, out = 0;
+    double d = 0.0;
+    if (live) {
+        p0 = rp[i];
+        p1 = rp[i + 1];
+        out = hrp[i];
+        if (t == 0) d = v[diagpos[i]];
     }
-    if (dpos >= 0) hv[dpos] = d;
+    const int32_t nch = (p1 - p0 + T - 1) / T;
+    const int32_t nch_max = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)nch);
+    int32_t dpos = -1;
+    for (int32_t c = 0; c < nch_max; ++c) {
+        const int32_t p = p0 + c * T + t;
+        const bool in = live && p < p1;
+        bool k = false;
+        double a = 0.0;
+        int32_t j = 0;
+        if (in) {
+            a = v[p];
+            k = keep[p] != 0;
+            j = ci[p];
+        }
+        const unsigned kb = (__ballot_sync(0xffffffffu, in && k) >> first) & gbits;
+        const unsigned db = (__ballot_sync(0xffffffffu, in && !k) >> first) & gbits;
+        if (in && k) {
+            const int32_t q = out + __popc(kb & ((1u << t) - 1u));
+            hci[q] = j;
+            hv[q] = a;
+            if (j == i) dpos = q;
+        }
+        out += __popc(kb);
+        const int nd = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(db));
+        unsigned rest = db;  // the same in every lane of the group
+        for (int r = 0; r < nd; ++r) {
+            const int src = rest ? first + __ffs(rest) - 1 : lane;
+            const double x = __shfl_sync(0xffffffffu, a, src);
+            if (rest) {
+                if (t == 0) d += x;
+                rest &= rest - 1u;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) dpos = max(dpos, __shfl_xor_sync(0xffffffffu, dpos, o, T));
+    if (live && t == 0 && dpos >= 0) hv[dpos] = d;  // the diagonal's value last
 }
 
 // ---------------------------------------------------------------------------
@@ -2151,8 +2188,11 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
             compact_values_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), keep, hval.as<double>(), H.rp(), H.ci(),
                                                         H.v());
         } else {
-            sparsify_compact_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(), H.ci(),
-                                                           H.v());
+            with_row_lanes(row_lanes(A), [&](auto tc) {
+                constexpr int L = decltype(tc)::value;
+                sparsify_compact_lanes_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
+                    n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(), H.ci(), H.v());
+            });
         }
         ::amg::count_launch();
         AMG_CHECK_LAUNCH();
