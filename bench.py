@@ -79,6 +79,9 @@ def parse():
                         "aniso: rotated anisotropic Q1 2D 2048^2 (theta pi/8, eps 1e-3), GMRES arms "
                         "(Galerkin, Sparse, Hybrid, non-Galerkin)")
     p.add_argument("--serve-seconds", type=float, default=20.0)
+    p.add_argument("--serve-batch", type=int, default=8,
+                   help="serving: column slots per hierarchy (the server's max_batch); 8 measured best for the "
+                        "200/s stream over 8 hierarchies (p99 272 ms against 462 at 16 and 938 at 32)")
     p.add_argument("--batch-k", type=int, nargs="*", default=None,
                    help="lognormal-batched: the widths to run (default 1 8 32 64)")
     p.add_argument("--lump", default="diag", choices=["diag", "strong"],
@@ -513,7 +516,7 @@ def leg_c5(args, seconds=None):
     pool_per_h = 4
     pool = [[gen.rhs_uniform(ns[hid], 10_000 + pool_per_h * hid + k) for k in range(pool_per_h)]
             for hid in range(len(hs))]
-    srv = amg.Server(max_batch=32)
+    srv = amg.Server(max_batch=args.serve_batch)
     ids = [srv.register(h) for h in hs]
     rng = np.random.default_rng(5)
     rate, T = 200.0, seconds or args.serve_seconds
@@ -559,7 +562,7 @@ def leg_c5(args, seconds=None):
     its = [info.iterations for _, info in results]
     return {"config": {"workload": "serving 8 resident hierarchies (2D 256^2, 512^2, 1024^2, 2048^2; 3D 32^3, 64^3, "
                                    "96^3, 128^3; gamma 0.1, FP32 cycle, FP64 outer CG), uniform hierarchy choice, "
-                                   f"Poisson arrivals at {rate:g}/s for {T:g} s, tol {args.tol:g}, max_batch 32",
+                                   f"Poisson arrivals at {rate:g}/s for {T:g} s, tol {args.tol:g}, max_batch {args.serve_batch}",
                        "timing": "latency = submit to result per request (host clock); solves/s over the wall time "
                                  "from the first arrival to the last result"},
             "requests": len(results), "failed": bad, "solves_per_s": round(len(results) / wall, 2),
