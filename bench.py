@@ -696,6 +696,39 @@ def communication(A_dev, parts_list=(8, 64)):
     return out
 
 
+def setup_roofline(h, phases):
+    """Throughput of the Galerkin products A P and R (A P) per level, from the
+    exported operators: products (the multiply-adds of the row-by-row
+    product, summed over both products) and algorithmic bytes (read A, P, R
+    and A P once, write A P and A_c once; 4-byte indices, 8-byte values),
+    against the measured Galerkin phase time of that level."""
+    import numpy as np
+
+    out, tot_p, tot_b, tot_ms = [], 0, 0.0, 0.0
+    for l in range(h.num_levels - 1):
+        A = h.export(l, "A").to_scipy()
+        P = h.export(l, "P").to_scipy()
+        Ac = h.export(l + 1, "A")
+        AP = (A @ P).tocsr()
+        AP.sort_indices()
+        p_rows = np.diff(P.indptr)
+        ap_rows = np.diff(AP.indptr)
+        prod_ap = int(p_rows[A.indices].sum())  # every a_ik meets row k of P
+        R = P.T.tocsr()
+        prod_rap = int(ap_rows[R.indices].sum())  # every r_ci meets row i of A P
+        nbytes = 12.0 * (A.nnz + 2 * P.nnz + 2 * AP.nnz + Ac.nnz) + 4.0 * (A.shape[0] + 2 * P.shape[0] + 2 * R.shape[0])
+        ms = phases["galerkin_spgemm_by_level"][l]
+        out.append({"level": l, "products": prod_ap + prod_rap, "nnz_AP": int(AP.nnz), "nnz_Ac": int(Ac.nnz),
+                    "ms": ms, "Gproducts_per_s": round((prod_ap + prod_rap) / (ms * 1e-3) / 1e9, 3),
+                    "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1)})
+        tot_p += prod_ap + prod_rap
+        tot_b += nbytes
+        tot_ms += ms
+    return {"what": "Galerkin A P and R (A P): products and algorithmic bytes per measured phase time",
+            "levels": out, "Gproducts_per_s": round(tot_p / (tot_ms * 1e-3) / 1e9, 3),
+            "GBps": round(tot_b / (tot_ms * 1e-3) / 1e9, 1), "ms": round(tot_ms, 3)}
+
+
 def solve_arms(args, A_dev, nnz0, bd, xd, stream, reps=5):
     """Solve-only time to tol (setup excluded) on the bench workload for the
     Galerkin, gamma in {0.01, 0.1, 1} and adaptive (Algorithm 5 from gamma 1)
@@ -981,6 +1014,9 @@ def main():
     comm = None
     if not args.no_arms:
         comm = communication(A_dev)
+    setup_roof = None
+    if setup_phases:
+        setup_roof = setup_roofline(last_h, _median_phases(setup_phases))
 
     # the other configurations of the metric, each with its own config and clocks
     legs = None
@@ -1008,6 +1044,7 @@ def main():
         "iterations": statistics.median(its), "levels": levels,
         "roofline": roofline, "vcycle_GBps": vcycle_bytes / (vcycle_ms * 1e-3) / 1e9 if vcycle_ms else None,
         "top_kernels": kernels, "solve_ms_per_level": per_level_ms, "setup_phases_ms": _median_phases(setup_phases),
+        "setup_roofline": setup_roof,
         "e2e": e2e, "cpu_baseline": cpu, "arms": arms, "communication": comm, "legs": legs, "clocks": clocks,
         "gpu_launches": launches,
     }
