@@ -865,11 +865,14 @@ def main():
         h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0)
         del h
         torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.cudart().cudaProfilerStart()
+        e0.record()
         h = amg.Hierarchy.setup(A_dev, **hopts, gamma=gamma, use_graph=0)
+        e1.record()
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
-        print(json.dumps({"ncu_setup": True, "levels": h.num_levels}))
+        print(json.dumps({"ncu_setup": True, "levels": h.num_levels, "setup_ms": round(e0.elapsed_time(e1), 3)}))
         return
 
     if args.ncu_solve:

@@ -95,9 +95,13 @@ __device__ __forceinline__ bool row_in_bounds(int32_t p0, int32_t p1, int64_t nn
     return p0 >= 0 && p0 <= p1 && (int64_t)p1 <= nnz;
 }
 
-template <int T>
+// With TPOS (square matrices) the same pass also records, for every entry
+// (i, j), the position of (j, i) in row j -- found by binary search in the
+// sorted row, followed only once j and row j's bounds are known to be valid;
+// a missing mirror entry is reported as an asymmetric pattern.
+template <int T, bool TPOS>
 __global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int32_t *rp, const int32_t *ci,
-                                const double *v, int32_t *diagpos, int *err) {
+                                const double *v, int32_t *diagpos, int32_t *tpos, int *err) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(g / T);
     const int t = (int)(g % T);
@@ -116,10 +120,29 @@ __global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int
     if (inb) {
         for (int32_t p = p0 + t; p < p1; p += T) {
             const int32_t j = ci[p];
-            if (j < 0 || j >= ncols) { e |= kBadCol; continue; }
+            if (j < 0 || j >= ncols) {
+                e |= kBadCol;
+                if (TPOS) tpos[p] = p;  // reported, not followed
+                continue;
+            }
             if (p > p0 && ci[p - 1] >= j) e |= kUnsorted;  // strictly increasing columns
             if (!isfinite(v[p])) e |= kNonFinite;
             if (j == i) dp = p;
+            if (TPOS) {
+                const int32_t q0 = rp[j], q1 = rp[j + 1];
+                if (!row_in_bounds(q0, q1, nnz)) {
+                    tpos[p] = p;
+                    e |= kBadRowptr;
+                    continue;
+                }
+                const int32_t q = lower_bound_i32(ci, q0, q1, i);
+                if (q < q1 && ci[q] == i) {
+                    tpos[p] = q;
+                } else {
+                    tpos[p] = p;
+                    e |= kAsym;
+                }
+            }
         }
     }
     dp = (int32_t)group_max_i64<T>((int64_t)dp);  // the diagonal position, if stored (one lane holds it)
@@ -131,26 +154,6 @@ __global__ void validate_kernel(int32_t n, int32_t ncols, int64_t nnz, const int
         diagpos[i] = -1;
     }
     if (e) atomicOr(err, e);
-}
-
-template <int T>
-__global__ void tpos_kernel(int32_t n, int64_t nnz, const int32_t *rp, const int32_t *ci, int32_t *tpos,
-                            int *err) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int32_t i = (int32_t)(g / T);
-    const int t = (int)(g % T);
-    if (i >= n) return;
-    const int32_t p0 = rp[i], p1 = rp[i + 1];
-    if (!row_in_bounds(p0, p1, nnz)) { if (t == 0) atomicOr(err, (int)kBadRowptr); return; }
-    for (int32_t p = p0 + t; p < p1; p += T) {
-        int32_t j = ci[p];
-        if (j < 0 || j >= n) { tpos[p] = p; atomicOr(err, (int)kBadCol); continue; }  // reported, not followed
-        const int32_t q0 = rp[j], q1 = rp[j + 1];
-        if (!row_in_bounds(q0, q1, nnz)) { tpos[p] = p; atomicOr(err, (int)kBadRowptr); continue; }
-        int32_t q = lower_bound_i32(ci, q0, q1, i);
-        if (q < q1 && ci[q] == i) tpos[p] = q;
-        else { tpos[p] = p; atomicOr(err, (int)kAsym); }
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -242,61 +245,76 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
 
 // Every round works on the list of rows still undecided when it starts (the
 // previous round's output, with its length on the device).  Rounds are
-// launched in batches without reading back in between, each grid sized for
-// the batch's first list; a kernel reads the list's actual length first and
-// does nothing once it is zero.
+// launched in batches without reading back in between, on a grid of at most
+// one wave of resident blocks that strides over the list; a kernel reads the
+// list's actual length first and does nothing once it is zero.  Every block
+// takes the same number of strides, so the block barriers of the append are
+// reached by all of its threads.
 template <int T>
 __global__ void pmis_select_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
                                    const uint8_t *sym, const double *w, const int8_t *state, uint8_t *newc) {
     const int m = *len;  // the same for the whole grid
-    if (m == 0) return;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t k = g / T;
-    const int t = (int)(g % T);
-    const bool live = k < m;  // no early exit: the group reduction needs every lane
-    const int32_t i = live ? list[k] : 0;
-    bool lose = false;
-    if (live) {
-        // weights are >= 0: their bit patterns order like the values
-        const int64_t wi = __double_as_longlong(w[i]);
-        for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
-            if (!sym[p]) continue;  // S_i u S^T_i
-            const int32_t j = ci[p];
-            if (state[j] != kU) continue;
-            const int64_t wj = __double_as_longlong(w[j]);
-            if (wj > wi || (wj == wi && j > i)) { lose = true; break; }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x < (int64_t)m * T;
+         g += stride) {
+        const int64_t k = g / T;
+        const int t = (int)(g % T);
+        const bool live = k < m;  // no early exit: the group reduction needs every lane
+        const int32_t i = live ? list[k] : 0;
+        bool lose = false;
+        if (live) {
+            // weights are >= 0: their bit patterns order like the values
+            const int64_t wi = __double_as_longlong(w[i]);
+            for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
+                if (!sym[p]) continue;  // S_i u S^T_i
+                const int32_t j = ci[p];
+                if (state[j] != kU) continue;
+                const int64_t wj = __double_as_longlong(w[j]);
+                if (wj > wi || (wj == wi && j > i)) { lose = true; break; }
+            }
         }
+        lose = group_any<T>(lose);
+        if (live && t == 0) newc[i] = (uint8_t)!lose;
     }
-    lose = group_any<T>(lose);
-    if (live && t == 0) newc[i] = (uint8_t)!lose;
 }
 
-__global__ void pmis_apply_c_kernel(const int32_t *list, const int *len, const uint8_t *newc, int8_t *state) {
-    const int m = *len;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= m) return;
-    const int32_t i = list[k];
-    if (newc[i]) state[i] = kC;
-}
-
+// The round's two steps in one pass: a selected row becomes C; any other row
+// of the list becomes F when one of its strong neighbours j (j in S_i) is C --
+// from an earlier round (state C) or selected in this one (state still U
+// when read, newc[j] set: j is on this round's list, so newc[j] is this
+// round's).  A row's own state is written only by its own group, and a
+// neighbour read before or after its write gives the same answer, so the
+// result does not depend on the order of the groups.  Undecided rows go to
+// the next round's list.
 template <int T>
-__global__ void pmis_apply_f_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
-                                    const uint8_t *strong, int8_t *state, int32_t *next, int *next_len) {
+__global__ void pmis_apply_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
+                                  const uint8_t *strong, const uint8_t *newc, int8_t *state, int32_t *next,
+                                  int *next_len) {
     const int m = *len;  // the same for the whole grid
-    if (m == 0) return;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t k = g / T;
-    const int t = (int)(g % T);
-    const bool live = k < m;
-    const int32_t i = live ? list[k] : 0;
-    const bool und = live && state[i] == kU;
-    bool f = false;
-    if (und)
-        for (int32_t p = rp[i] + t; p < rp[i + 1] && !f; p += T)
-            if (strong[p] && state[ci[p]] == kC) f = true;
-    f = group_any<T>(f);
-    if (und && t == 0 && f) state[i] = kF;
-    block_append(und && t == 0 && !f, i, next, next_len);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x < (int64_t)m * T;
+         g += stride) {
+        const int64_t k = g / T;
+        const int t = (int)(g % T);
+        const bool live = k < m;
+        const int32_t i = live ? list[k] : 0;
+        const bool c = live && newc[i];
+        const bool und = live && !c;
+        bool f = false;
+        if (und)
+            for (int32_t p = rp[i] + t; p < rp[i + 1] && !f; p += T) {
+                if (!strong[p]) continue;
+                const int32_t j = ci[p];
+                const int8_t sj = *(volatile const int8_t *)&state[j];
+                if (sj == kC || (sj == kU && newc[j])) f = true;
+            }
+        f = group_any<T>(f);
+        if (live && t == 0) {
+            if (c) state[i] = kC;
+            else if (f) state[i] = kF;
+        }
+        block_append(und && t == 0 && !f, i, next, next_len);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -357,23 +375,43 @@ __global__ void interp_rows_kernel(int32_t n, const int32_t *rp, const int32_t *
     // to, and written back.  Adding +0.0 (a zero entry, or no strong C
     // neighbour) leaves a sum unchanged: every sum starts at +0.0 and
     // accumulates values of one sign, so it is never -0.0.
-#pragma unroll 4
-    for (int32_t p = rp[i]; p < rp[i + 1]; ++p) {
-        int32_t j = ci[p];
-        double a = v[p];
-        if (j == i) { diag = a; continue; }
-        const int64_t ak = f64_key(a);
-        const bool sc = strong[p] && cf[j] == kC;
-        const bool is_neg = ak < 0, is_pos = ak > 0;
-        const double tot = (is_neg ? sum_neg : sum_pos) + a;
-        const double csum = (is_neg ? sum_neg_c : sum_pos_c) + (sc ? a : 0.0);
-        if (is_neg) { sum_neg = tot; sum_neg_c = csum; }
-        if (is_pos) { sum_pos = tot; sum_pos_c = csum; }
-        if (sc) {
-            pci[pos] = cmap[j];
-            pv[pos] = a;
-            prow[pos] = i;
-            ++pos;
+    // entries in chunks of 8: the chunk's loads, then its C/F gathers, are
+    // issued together before the sums walk it in column order
+    const int32_t pe = rp[i + 1];
+    for (int32_t p0 = rp[i]; p0 < pe; p0 += 8) {
+        int32_t jj[8];
+        double aa[8];
+        bool sc8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int32_t p = p0 + u;
+            const bool in = p < pe;
+            jj[u] = in ? ci[p] : i;
+            aa[u] = in ? v[p] : 0.0;
+            sc8[u] = in && strong[p];  // the diagonal is never strong
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (sc8[u]) sc8[u] = cf[jj[u]] == kC;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (p0 + u >= pe) break;
+            const int32_t j = jj[u];
+            const double a = aa[u];
+            if (j == i) { diag = a; continue; }
+            const int64_t ak = f64_key(a);
+            const bool sc = sc8[u];
+            const bool is_neg = ak < 0, is_pos = ak > 0;
+            const double tot = (is_neg ? sum_neg : sum_pos) + a;
+            const double csum = (is_neg ? sum_neg_c : sum_pos_c) + (sc ? a : 0.0);
+            if (is_neg) { sum_neg = tot; sum_neg_c = csum; }
+            if (is_pos) { sum_pos = tot; sum_pos_c = csum; }
+            if (sc) {
+                pci[pos] = cmap[j];
+                pv[pos] = a;
+                prow[pos] = i;
+                ++pos;
+            }
         }
     }
     double alpha = f64_key(sum_neg_c) != 0 ? sum_neg / sum_neg_c : 0.0;
@@ -1056,8 +1094,13 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
     return u;
 }
 
+// Blocks of the small table kept resident per SM: shared memory admits 7,
+// and 6 leave 40 registers a thread (at 8 the kernel spills).
+#ifndef AMG_ACC_MIN_BLOCKS
+#define AMG_ACC_MIN_BLOCKS 6
+#endif
 template <int U, int WARPS, bool NUMERIC>
-__global__ void __launch_bounds__(WARPS * 32, U <= 128 ? 8 : 1)  // the small table allows a full SM of warps
+__global__ void __launch_bounds__(WARPS * 32, U <= 128 ? AMG_ACC_MIN_BLOCKS : 1)
 spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                   const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
                   int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
@@ -1701,17 +1744,15 @@ void level_maps(const DevCSR &A, int32_t *diagpos, int32_t *tpos, cudaStream_t s
     if (A.nrows > 0) {
         with_row_lanes(row_lanes(A), [&](auto tc) {
             constexpr int L = decltype(tc)::value;
-            validate_kernel<L><<<div_up((int64_t)A.nrows * L, kThreads), kThreads, 0, s>>>(
-                A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(), diagpos, err.as<int>());
+            const int gl = div_up((int64_t)A.nrows * L, kThreads);
+            if (A.nrows == A.ncols)
+                validate_kernel<L, true><<<gl, kThreads, 0, s>>>(A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(),
+                                                                 diagpos, tpos, err.as<int>());
+            else
+                validate_kernel<L, false><<<gl, kThreads, 0, s>>>(A.nrows, A.ncols, A.nnz, A.rp(), A.ci(), A.v(),
+                                                                  diagpos, nullptr, err.as<int>());
             ::amg::count_launch();
         });
-        if (A.nrows == A.ncols)
-            with_row_lanes(row_lanes(A), [&](auto tc) {
-                constexpr int L = decltype(tc)::value;
-                tpos_kernel<L><<<div_up((int64_t)A.nrows * L, kThreads), kThreads, 0, s>>>(
-                    A.nrows, A.nnz, A.rp(), A.ci(), tpos, err.as<int>());
-                ::amg::count_launch();
-            });
     }
     AMG_CHECK_LAUNCH();
     if (!check) return;  // an operator this library formed: sorted, symmetric pattern by construction
@@ -1787,7 +1828,9 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
         AMG_CUDA(cudaMemsetAsync(cmap, 0, sizeof(int32_t), s));
         return 0;
     }
-    constexpr int kBatch = 4, kMaxRounds = 10000;
+    // eight rounds per read-back: the levels of the test problems finish
+    // within one batch, and a round whose list is empty costs one short launch
+    constexpr int kBatch = 8, kMaxRounds = 10000;
     // cnt[0]: undecided after the initial split; cnt[r]: after round r; the
     // undecided rows alternate between two lists
     TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s), sym(A.nnz + 1, s),
@@ -1796,6 +1839,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     int32_t *list[2] = {lists.as<int32_t>(), lists.as<int32_t>() + n};
     int g = div_up(n, kThreads);
     const int T = row_lanes(A, 8);
+    const int64_t nres = ::amg::resident_blocks(kThreads);
     AMG_CUDA(cudaMemsetAsync(cnt.ptr, 0, cnt.bytes, s));
     with_row_lanes(T, [&](auto tc) {
         constexpr int L = decltype(tc)::value;
@@ -1816,15 +1860,12 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
             int32_t *nxt = list[r & 1];
             with_row_lanes(T, [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
-                const int gl = div_up(bound * L, kThreads);
+                const int gl = (int)std::min<int64_t>(div_up(bound * L, kThreads), nres);
                 pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), sym.as<uint8_t>(),
                                                               w.as<double>(), cf, newc.as<uint8_t>());
                 ::amg::count_launch();
-                pmis_apply_c_kernel<<<div_up(bound, kThreads), kThreads, 0, s>>>(cur, dc + r - 1,
-                                                                               newc.as<uint8_t>(), cf);
-                ::amg::count_launch();
-                pmis_apply_f_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), strong, cf, nxt,
-                                                               dc + r);
+                pmis_apply_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), strong,
+                                                             newc.as<uint8_t>(), cf, nxt, dc + r);
                 ::amg::count_launch();
             });
         }
@@ -2188,7 +2229,10 @@ int64_t sparsify(const DevCSR &A, const uint8_t *inM, const int32_t *tpos, const
             compact_values_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), keep, hval.as<double>(), H.rp(), H.ci(),
                                                         H.v());
         } else {
-            with_row_lanes(row_lanes(A), [&](auto tc) {
+            // at most 8 lanes a row: the lumped diagonal's additions are
+            // issued by one lane per row, so a warp of one row would spend a
+            // whole FP64 warp instruction on each dropped entry
+            with_row_lanes(std::min(row_lanes(A), 8), [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
                 sparsify_compact_lanes_kernel<L><<<div_up((int64_t)n * L, kThreads), kThreads, 0, s>>>(
                     n, A.rp(), A.ci(), A.v(), diagpos, keep, H.rp(), H.ci(), H.v());
