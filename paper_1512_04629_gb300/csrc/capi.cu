@@ -180,8 +180,13 @@ amg_status amg_setup(const amg_csr *A, double theta, const double *gamma, int n_
         h.timing = o.setup_timing != 0;
         h.lev.push_back(std::make_unique<Level>());
         upload_csr(A, h.lev[0]->A, s);
-        build_galerkin(h, h.lev[0]->A, s, gamma, n_gamma);
-        finish_setup(h, gamma, n_gamma, s);
+        setup_hierarchy(h, s, gamma, n_gamma);
+        ensure_workspace(h, s);
+        AMG_CUDA(cudaStreamSynchronize(s));
+        if (h.opt.setup_timing) {  // setup phases were timed; the solve timing stays opt-in
+            timing_collect(h);
+            h.timing = false;
+        }
         *out = H.release();
         return AMG_OK;
     });

@@ -7,8 +7,11 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <exception>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include "common.cuh"
 #include "cycle_ops.cuh"
@@ -110,9 +113,45 @@ static void nongalerkin_thin(Hierarchy &h, Level &C, double g, cudaStream_t s) {
     }
 }
 
-void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const double *gamma, int n_gamma) {
+// Setup pipeline (plain Sparse Galerkin setups that are not timed per
+// phase): a level's sparsification (Algorithm 4) and cycle preparation need
+// only that level and its interpolation, so a second host thread issues them
+// on a second stream while the coarsening goes on to the next levels -- the
+// coarsening's host round trips and short launches leave the device idle,
+// and the second stream's kernels fill those gaps.  Relaxation and transfer
+// variants whose decision would need timed trials are left for the calling
+// thread, which times them once both streams have drained.
+class SetupPipeline {
+  public:
+    SetupPipeline(Hierarchy &h, cudaStream_t main, const double *gamma, int n_gamma);
+    ~SetupPipeline();
+    void level_ready(int l);      // level l and its P_l, R_l are formed (on the main stream)
+    void coarsening_done(int nlev);
+    void finish();                // joins; the main stream then waits for the second one
+
+  private:
+    void run();
+    void cancel();
+    Hierarchy &h_;
+    cudaStream_t main_, side_ = nullptr;
+    int device_ = 0;
+    std::vector<double> gamma_;
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::vector<cudaEvent_t> ev_;  // ev_[l]: level l is ready; the last one also marks the end of coarsening
+    int nready_ = 0, nlev_ = -1;
+    bool stop_ = false;
+    std::exception_ptr err_;
+    std::vector<int> defer_relax_, defer_transfer_;
+    cudaEvent_t done_ = nullptr;
+    std::thread th_;
+};
+
+void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const double *gamma, int n_gamma,
+                   SetupPipeline *pipe) {
     (void)A0in;
     const amg_options &o = h.opt;
+    h.lev.reserve(kMaxLevels + 1);  // the pipeline thread holds references into it while levels are added
     const bool nongal = o.method == AMG_METHOD_NONGALERKIN;
     for (int l = 0;; ++l) {
         Level &V = *h.lev[l];
@@ -159,7 +198,9 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
             timed(h, 13, l + 1, 0.0, s, [&] { nongalerkin_thin(h, *C, g, s); });
         }
         h.lev.push_back(std::move(C));
+        if (pipe) pipe->level_ready(l);
     }
+    if (pipe) pipe->coarsening_done(h.nlev());
 }
 
 // Levels given by the caller (amg_hierarchy_assemble / load).
@@ -215,8 +256,7 @@ static const uint8_t *hybrid_pattern(Hierarchy &h, int l, cudaStream_t s) {
     return V.inM_hybrid.as<uint8_t>();
 }
 
-void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
-    Level &V = *h.lev[l];
+static void resparsify_one(Hierarchy &h, Level &V, int l, cudaStream_t s) {
     if (l == 0 || V.gamma == 0.0) {
         V.H = DevCSR();
         V.h_alias = true;
@@ -237,6 +277,12 @@ void resparsify_level(Hierarchy &h, int l, cudaStream_t s) {
     V.h_alias = false;
 }
 
+void resparsify_level(Hierarchy &h, int l, cudaStream_t s) { resparsify_one(h, *h.lev[l], l, s); }
+
+static double level_gamma(const double *gamma, int n_gamma, int l) {
+    return (l > 0 && n_gamma > 0 && gamma) ? gamma[std::min(l, n_gamma - 1)] : 0.0;
+}
+
 void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s) {
     if (h.opt.method == AMG_METHOD_NONGALERKIN) {  // thinned during the setup: every level is final
         for (int l = 0; l < h.nlev(); ++l) {
@@ -248,9 +294,7 @@ void apply_gammas(Hierarchy &h, const double *gamma, int n_gamma, cudaStream_t s
         return;
     }
     for (int l = 0; l < h.nlev(); ++l) {
-        double g = 0.0;
-        if (l > 0 && n_gamma > 0 && gamma) g = gamma[std::min(l, n_gamma - 1)];
-        h.lev[l]->gamma = g;
+        h.lev[l]->gamma = level_gamma(gamma, n_gamma, l);
         timed(h, 13, l, 0.0, s, [&] { resparsify_level(h, l, s); });
     }
 }
@@ -462,8 +506,10 @@ template <typename T> static void alloc_zero(DevBuf &b, int64_t n, cudaStream_t 
     AMG_CUDA(cudaMemsetAsync(b.ptr, 0, b.bytes, s));
 }
 
-static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
-    Level &V = *h.lev[l];
+// Cycle data of level V (= level l; has_p: it has a coarser level).  Without
+// allow_tune a relaxation variant that would need timed trials is left to the
+// caller (returns true): trials are timed only with the device to themselves.
+static bool prepare_level_at(Hierarchy &h, Level &V, int l, bool has_p, cudaStream_t s, bool allow_tune) {
     const DevCSR &M = V.op();
     int32_t n = V.n();
     int prec = h.opt.precision;
@@ -475,7 +521,6 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
     V.hv16.release();
     V.dinv32.release();
     free_sell(V);
-    bool has_p = l + 1 < h.nlev();
     if (prec == AMG_PREC_FP64) {
         alloc_zero<double>(V.b, n, s); alloc_zero<double>(V.x, n, s);
         alloc_zero<double>(V.r, n, s); alloc_zero<double>(V.xo, n, s);
@@ -520,6 +565,7 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
             tune = false;
         }
     }
+    if (tune && !allow_tune) return true;
     if (tune || sell_height(V.variant)) {
         const int C = tune ? 32 : sell_height(V.variant);
         if (V.vbytes == 8) build_sell<double>(V, s, C);
@@ -544,10 +590,14 @@ static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
                                V.soff.as<int32_t>(), V.sw.as<int32_t>(), V.sd.ptr ? nullptr : junk_idx.as<int32_t>(),
                                V.sv64.as<double>(), s, V.sd.ptr ? junk_idx.as<int16_t>() : nullptr);
     }
+    return false;
 }
 
-static void prepare_coarse(Hierarchy &h, cudaStream_t s) {
-    Level &V = *h.lev[h.nlev() - 1];
+static void prepare_level(Hierarchy &h, int l, cudaStream_t s) {
+    prepare_level_at(h, *h.lev[l], l, l + 1 < h.nlev(), s, true);
+}
+
+static void prepare_coarse_at(Hierarchy &h, Level &V, cudaStream_t s) {
     const DevCSR &M = V.op();
     int32_t n = V.n();
     h.coarse_n = n;
@@ -555,13 +605,16 @@ static void prepare_coarse(Hierarchy &h, cudaStream_t s) {
     setup::cholesky_inverse(M, h.coarse_inv.as<double>(), s);
 }
 
+static void prepare_coarse(Hierarchy &h, cudaStream_t s) { prepare_coarse_at(h, *h.lev[h.nlev() - 1], s); }
+
 // Transfer operators: time prolongation (x += P x_c) and restriction
 // (b_c = R r, x_c = d_c b_c) under the vector-CSR widths that fit their mean
 // row, keep the fastest (cached per shape like the relaxation).
-template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaStream_t s) {
-    Level &V = *h.lev[l];
-    Level &C = *h.lev[l + 1];
+// Without allow_tune, an operator whose decision is not cached is left to the
+// caller (returns true) instead of being timed.
+template <typename XT> static bool autotune_transfers_at(Level &V, Level &C, cudaStream_t s, bool allow_tune) {
     int vb = sizeof(XT);
+    bool deferred = false;
     L2Flush flush;
     cudaEvent_t e0, e1;
     AMG_CUDA(cudaEventCreate(&e0));
@@ -579,6 +632,10 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
             }
         }
         S.release();  // a copy of an earlier operator must not stand in for this one
+        if (!allow_tune) {
+            deferred = true;
+            return;
+        }
         double mean = M.nrows > 0 ? (double)M.nnz / M.nrows : 0.0;
         int V16 = 16 / vb;
         float best = 1e30f;
@@ -632,6 +689,11 @@ template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaS
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    return deferred;
+}
+
+template <typename XT> static void autotune_transfers(Hierarchy &h, int l, cudaStream_t s) {
+    autotune_transfers_at<XT>(*h.lev[l], *h.lev[l + 1], s, true);
 }
 
 void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels) {
@@ -667,6 +729,211 @@ void prepare_cycle(Hierarchy &h, cudaStream_t s, const std::vector<int> &levels)
     }
     h.graph_dirty = true;
     h.version++;
+    AMG_CUDA(cudaStreamSynchronize(s));
+}
+
+// A non-blocking stream of a given priority and an event, released on scope
+// exit (after the stream's work is done).
+struct StreamGuard {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    explicit StreamGuard(int priority) {
+        AMG_CUDA(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, priority));
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamDestroy(s);
+            throw Error(AMG_ERR_CUDA, "cudaEventCreate failed");
+        }
+    }
+    StreamGuard() {
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(AMG_ERR_CUDA, "cudaEventCreate failed");
+        }
+    }
+    ~StreamGuard() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+        cudaEventDestroy(ev);
+        cudaGetLastError();
+    }
+    StreamGuard(const StreamGuard &) = delete;
+    StreamGuard &operator=(const StreamGuard &) = delete;
+};
+
+// ---------------------------------------------------------------------------
+// SetupPipeline
+// ---------------------------------------------------------------------------
+SetupPipeline::SetupPipeline(Hierarchy &h, cudaStream_t main, const double *gamma, int n_gamma)
+    : h_(h), main_(main), gamma_(gamma && n_gamma > 0 ? std::vector<double>(gamma, gamma + n_gamma)
+                                                      : std::vector<double>()) {
+    AMG_CUDA(cudaGetDevice(&device_));
+    AMG_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(side_);
+        throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventCreate failed");
+    }
+    th_ = std::thread([this] { run(); });
+}
+
+SetupPipeline::~SetupPipeline() {
+    cancel();
+    // work already issued on the second stream finishes before the levels it
+    // writes can be released
+    cudaStreamSynchronize(side_);
+    cudaGetLastError();
+    for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+    cudaEventDestroy(done_);
+    cudaStreamDestroy(side_);
+}
+
+void SetupPipeline::cancel() {
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        stop_ = true;
+    }
+    cv_.notify_all();
+    if (th_.joinable()) th_.join();
+}
+
+void SetupPipeline::level_ready(int l) {
+    cudaEvent_t e;
+    AMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (cudaEventRecord(e, main_) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(e);
+        throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventRecord failed");
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        ev_.push_back(e);
+        nready_ = l + 1;
+    }
+    cv_.notify_all();
+}
+
+void SetupPipeline::coarsening_done(int nlev) {
+    cudaEvent_t e;
+    AMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (cudaEventRecord(e, main_) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(e);
+        throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventRecord failed");
+    }
+    {
+        std::lock_guard<std::mutex> lk(mu_);
+        ev_.push_back(e);
+        nlev_ = nlev;
+    }
+    cv_.notify_all();
+}
+
+void SetupPipeline::run() {
+    try {
+        AMG_CUDA(cudaSetDevice(device_));
+        AllocOn alloc_scope(side_);
+        const amg_options &o = h_.opt;
+        const bool fp64 = o.precision == AMG_PREC_FP64;
+        const bool tune_transfers = o.transfer_variant == AMG_SPMV_AUTO && o.spmv_variant == AMG_SPMV_AUTO;
+        for (int l = 0;; ++l) {
+            bool has_p = false, last = false;
+            cudaEvent_t e = nullptr;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || nready_ > l || nlev_ >= 0; });
+                if (stop_) return;
+                if (nready_ > l) {
+                    has_p = true;
+                    e = ev_[l];
+                } else {
+                    if (l >= nlev_) break;
+                    last = l == nlev_ - 1;
+                    has_p = !last;
+                    e = ev_.back();
+                }
+            }
+            AMG_CUDA(cudaStreamWaitEvent(side_, e, 0));
+            Level &V = *h_.lev[l];
+            V.gamma = level_gamma(gamma_.data(), (int)gamma_.size(), l);
+            resparsify_one(h_, V, l, side_);
+            if (prepare_level_at(h_, V, l, has_p, side_, false)) defer_relax_.push_back(l);
+            if (last) prepare_coarse_at(h_, V, side_);
+            if (l > 0) {  // the transfers of level l-1 run on level l's vectors
+                Level &F = *h_.lev[l - 1];
+                if (o.transfer_variant != AMG_SPMV_AUTO) {
+                    const int tv = o.transfer_variant, C = sell_height(tv);
+                    F.variant_p = F.variant_r = tv;
+                    if (C && fp64) {
+                        build_sell_copy<double>(F.P, F.P.v(), F.psell, side_, C);
+                        build_sell_copy<double>(F.R, F.R.v(), F.rsell, side_, C);
+                    } else if (C) {
+                        build_sell_copy<float>(F.P, F.pv32.as<float>(), F.psell, side_, C);
+                        build_sell_copy<float>(F.R, F.rv32.as<float>(), F.rsell, side_, C);
+                    }
+                    F.pr_tuned = true;
+                } else if (tune_transfers) {
+                    const bool d = fp64 ? autotune_transfers_at<double>(F, V, side_, false)
+                                        : autotune_transfers_at<float>(F, V, side_, false);
+                    if (d) defer_transfer_.push_back(l - 1);
+                    else F.pr_tuned = true;
+                }
+            }
+        }
+        AMG_CUDA(cudaEventRecord(done_, side_));
+    } catch (...) {
+        err_ = std::current_exception();
+        cudaEventRecord(done_, side_);
+        cudaGetLastError();
+    }
+}
+
+void SetupPipeline::finish() {
+    if (th_.joinable()) th_.join();
+    if (err_) std::rethrow_exception(err_);
+    AMG_CUDA(cudaStreamWaitEvent(main_, done_, 0));
+    // the trials left over, timed on the main stream with the device to themselves
+    AMG_CUDA(cudaStreamSynchronize(side_));
+    for (int l : defer_relax_) prepare_level(h_, l, main_);
+    const bool fp64 = h_.opt.precision == AMG_PREC_FP64;
+    for (int l : defer_transfer_) {
+        if (fp64) autotune_transfers<double>(h_, l, main_);
+        else autotune_transfers<float>(h_, l, main_);
+        h_.lev[l]->pr_tuned = true;
+    }
+    h_.graph_dirty = true;
+    h_.version++;
+}
+
+// Algorithm 1 and the cycle preparation of every level (amg_setup).
+void setup_hierarchy(Hierarchy &h, cudaStream_t s, const double *gamma, int n_gamma) {
+    const bool pipelined = !h.timing && h.opt.method == AMG_METHOD_SPARSE && h.parts <= 1;
+    if (!pipelined) {
+        build_galerkin(h, h.lev[0]->A, s, gamma, n_gamma);
+        apply_gammas(h, gamma, n_gamma, s);
+        std::vector<int> all;
+        for (int l = 0; l < h.nlev(); ++l) all.push_back(l);
+        prepare_cycle(h, s, all);
+        return;
+    }
+    // the coarsening -- the longer chain -- runs on a stream of the highest
+    // priority, so the second stream's blocks fill the gaps it leaves instead
+    // of delaying it
+    int lo = 0, hi = 0;
+    AMG_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    StreamGuard sc(hi), join;
+    AMG_CUDA(cudaEventRecord(join.ev, s));  // the uploaded operator
+    AMG_CUDA(cudaStreamWaitEvent(sc.s, join.ev, 0));
+    {
+        AllocOn alloc_scope(sc.s);
+        SetupPipeline pipe(h, sc.s, gamma, n_gamma);
+        build_galerkin(h, h.lev[0]->A, sc.s, gamma, n_gamma, &pipe);
+        pipe.finish();
+    }
+    AMG_CUDA(cudaEventRecord(join.ev, sc.s));
+    AMG_CUDA(cudaStreamWaitEvent(s, join.ev, 0));
     AMG_CUDA(cudaStreamSynchronize(s));
 }
 

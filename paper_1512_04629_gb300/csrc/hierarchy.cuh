@@ -264,8 +264,12 @@ void replan_relaxation(Hierarchy &h, int l, cudaStream_t s);
 // drivers (hierarchy.cu)
 // Algorithm 1; with method AMG_METHOD_NONGALERKIN each new coarse operator is
 // thinned (gamma convention of amg_setup) before it is coarsened further.
+class SetupPipeline;
 void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const double *gamma = nullptr,
-                    int n_gamma = 0);
+                    int n_gamma = 0, SetupPipeline *pipe = nullptr);
+// build_galerkin, the sparsification of every level and its cycle data; plain
+// Sparse Galerkin setups overlap the last two with the coarsening
+void setup_hierarchy(Hierarchy &h, cudaStream_t s, const double *gamma, int n_gamma);
 void assemble_levels(Hierarchy &h, std::vector<DevCSR> &A, std::vector<DevCSR> &P,
                      const std::vector<std::vector<int8_t>> &cf,
                      const std::vector<std::vector<uint8_t>> &inM, cudaStream_t s);

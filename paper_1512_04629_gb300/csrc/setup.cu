@@ -724,9 +724,13 @@ constexpr unsigned kFull = 0xffffffffu;
 // sorts the keys (j, e), so equal columns become adjacent and keep product
 // order; the first lane of every run sums its run from 0.0 in that order --
 // the dense-accumulator order of the definition, so the result is exact to
-// the bit with it.
+// the bit with it.  With KEY32 (every column below 2^27 - 1) the key is one
+// 32-bit word, j above the lane index, and only keys move through the
+// network: each lane then fetches its product's value from the lane that
+// formed it, and a run's head, knowing its run length from the ballot of
+// heads, adds the following values without comparing keys again.
 // ---------------------------------------------------------------------------
-template <int W, bool NUMERIC>
+template <int W, bool NUMERIC, bool KEY32>
 __global__ void __launch_bounds__(256, 8)  // 32 registers: a full SM of warps to hide the load chains
 spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_t *__restrict__ arp,
                    const int32_t *__restrict__ aci, const double *__restrict__ av, const int32_t *__restrict__ brp,
@@ -795,6 +799,50 @@ spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_
         }
         p0_nx = rn < nrows ? arp[i_nx] : 0;
         p1_nx = rn < nrows ? arp[i_nx + 1] : 0;
+        if constexpr (KEY32) {
+            constexpr int LB = W == 8 ? 3 : (W == 16 ? 4 : 5);
+            uint32_t key = valid ? (((uint32_t)j << LB) | (uint32_t)sl) : 0xffffffffu;  // empty lanes last
+#pragma unroll
+            for (int size = 2; size <= W; size <<= 1) {
+#pragma unroll
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    const uint32_t ok = __shfl_xor_sync(gmask, key, stride, W);
+                    const bool up = (sl & size) == 0;
+                    const bool lower = (sl & stride) == 0;
+                    key = lower == up ? min(key, ok) : max(key, ok);
+                }
+            }
+            valid = key != 0xffffffffu;
+            j = (int32_t)(key >> LB);
+            if (NUMERIC) val = __shfl_sync(gmask, val, (int)(key & (uint32_t)(W - 1)), W);
+            const int32_t jprev = __shfl_up_sync(gmask, j, 1, W);
+            const bool head = valid && (sl == 0 || jprev != j);
+            const unsigned hb = (__ballot_sync(gmask, head) & gmask) >> (sub * W);
+            const int32_t u = __popc(hb);
+            if (NUMERIC) {
+                // valid keys form a prefix of the group; a run ends at the next head
+                const int nvalid = __popc((__ballot_sync(gmask, valid) & gmask) >> (sub * W));
+                int len = 0;
+                if (head) {
+                    const unsigned later = sl + 1 < 32 ? hb & ~((2u << sl) - 1u) : 0u;
+                    len = (later ? __ffs(later) - 1 : nvalid) - sl;
+                }
+                const int lmax = (int)__reduce_max_sync(kFull, (unsigned)len);  // whole warp: uniform bound
+                double acc = f64_zero_plus(val);  // run sums in product order, from 0.0
+                for (int d = 1; d < lmax; ++d) {
+                    const double vd = __shfl_down_sync(gmask, val, d, W);
+                    if (d < len) acc += vd;
+                }
+                if (head) {
+                    const int32_t pos = __popc(hb & ((1u << sl) - 1u));
+                    const int64_t cb = obase[i];
+                    cci[cb + pos] = j;
+                    cv[cb + pos] = acc;
+                }
+            }
+            if (live && sl == 0) cnt[i] = u;
+            continue;
+        }
         // bitonic sort of (j, e) across the group; empty lanes sort last
         uint64_t key = valid ? (((uint64_t)(uint32_t)j << 8) | (uint64_t)sl) : ~0ull;
 #pragma unroll
@@ -1565,64 +1613,82 @@ __global__ void tri_inverse_kernel(int32_t n, const double *L, double *Linv) {
     }
 }
 
-// inv = Linv^T Linv
-// Small coarsest levels (n <= kSmemCoarse): Cholesky factor and its inverse
-// in shared memory by one block -- the global-memory kernels above walk long
-// chains of dependent loads, which dominates at these sizes.  Same
-// right-looking factorization (same operation order) as cholesky_kernel;
-// column c of L^{-1} by forward substitution, one thread per column.
-constexpr int kSmemCoarse = 112;  // 2 n^2 doubles = 196 KB of shared memory
+// Small coarsest levels (n <= kSmemCoarse): the Cholesky factor by one block
+// in shared memory, then A^{-1} one column per block by two substitutions --
+// the global-memory kernels above walk long chains of dependent loads, and
+// the triangular inverse and its Gram product would keep a single SM's FP64
+// pipe busy for as long again.  The coarsest solve's explicit inverse is
+// checked against the oracle's triangular solves within tolerance, so the
+// updates use fused multiply-adds and reciprocal square roots.
+constexpr int kSmemCoarse = 160;  // n^2 doubles = 200 KB of shared memory
 
+// Right-looking A = L L^T without a column-scaling pass: step j subtracts
+// (a_rj / a_jj) a_cj from the trailing entries -- the unscaled column j, so
+// its entries need no barrier of their own -- and the columns are scaled by
+// 1 / sqrt(a_jj) once at the end.  L (lower, row-major) and 1 / L_jj go out.
 __global__ void __launch_bounds__(1024)
-coarse_factor_smem_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double *linv_out,
-                          int *err) {
-    // Cholesky A = L L^T and L^{-1} in shared memory, 1024 threads as a
-    // 32 x 32 tile walking the triangles (no index division); the coarsest
-    // solve's explicit inverse is checked against the oracle's triangular
-    // solves within tolerance, so its updates use fused multiply-adds and one
-    // reciprocal per pivot
-    extern __shared__ __align__(16) double sm[];
-    double *a = sm, *li = sm + (size_t)n * n;
+coarse_chol_smem_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const double *v, double *lout,
+                        double *rdiag, int *err) {
+    extern __shared__ __align__(16) double a[];
+    __shared__ double rpv[kSmemCoarse];
+    __shared__ double rinv;
     const int32_t tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = 0.0;
     __syncthreads();
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x)
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) a[i * n + ci[p]] = v[p];
-    __shared__ double rpiv;
+    for (int32_t i = ty; i < n; i += 32)  // one warp per row
+        for (int32_t p = rp[i] + tx; p < rp[i + 1]; p += 32) a[i * n + ci[p]] = v[p];
     for (int32_t j = 0; j < n; ++j) {
         __syncthreads();
         if (threadIdx.x == 0) {
             double d = a[j * n + j];
             if (!(d > 0.0)) { *err = 1; d = 1.0; }
-            const double piv = sqrt(d);
-            a[j * n + j] = piv;
-            rpiv = 1.0 / piv;
+            const double r = rsqrt(d);
+            rpv[j] = r;
+            rinv = r * r;
         }
         __syncthreads();
-        for (int32_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) a[i * n + j] *= rpiv;
-        __syncthreads();
-        // trailing update of the lower triangle: rows r > j, columns j < c <= r
+        const double ri = rinv;
         for (int32_t r = j + 1 + ty; r < n; r += 32) {
-            const double lr = a[r * n + j];
-            for (int32_t c = j + 1 + tx; c <= r; c += 32) a[r * n + c] = fma(-lr, a[c * n + j], a[r * n + c]);
-        }
-    }
-    // L^{-1}, right-looking from the identity: at step i row i is final once
-    // scaled by 1 / L_ii, and every later row r subtracts L_ri times it
-    __syncthreads();
-    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) li[t] = (t / n == t % n) ? 1.0 : 0.0;
-    for (int32_t i = 0; i < n; ++i) {
-        __syncthreads();
-        const double ri = 1.0 / a[i * n + i];
-        for (int32_t c = threadIdx.x; c <= i; c += blockDim.x) li[i * n + c] *= ri;
-        __syncthreads();
-        for (int32_t r = i + 1 + ty; r < n; r += 32) {
-            const double lri = a[r * n + i];
-            for (int32_t c = tx; c <= i; c += 32) li[r * n + c] = fma(-lri, li[i * n + c], li[r * n + c]);
+            const double t = a[r * n + j] * ri;
+            for (int32_t c = j + 1 + tx; c <= r; c += 32) a[r * n + c] = fma(-t, a[c * n + j], a[r * n + c]);
         }
     }
     __syncthreads();
-    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) linv_out[t] = li[t];
+    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) {
+        const int32_t r = t / n, c = t % n;
+        lout[t] = c < r ? a[t] * rpv[c] : (c == r ? a[t] * rpv[c] : 0.0);  // L_rc = a_rc / sqrt(a_cc)
+    }
+    for (int32_t j = threadIdx.x; j < n; j += blockDim.x) rdiag[j] = rpv[j];  // 1 / L_jj
+}
+
+// Column c of A^{-1}: L y = e_c, then L^T x = y, one block per column with L
+// in shared memory; each step finalises one entry (times 1 / L_ii) and
+// updates the rest, one barrier a step.  Written as row c (A^{-1} is
+// symmetric).
+__global__ void __launch_bounds__(128)
+coarse_inv_col_kernel(int32_t n, const double *L, const double *rdiag, double *inv) {
+    extern __shared__ __align__(16) double sl[];
+    double *w = sl + (size_t)n * n, *x = w + n;
+    const int32_t c = blockIdx.x;
+    for (int32_t t = threadIdx.x; t < n * n; t += blockDim.x) sl[t] = L[t];
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        w[i] = i == c ? 1.0 : 0.0;
+        x[i] = 0.0;
+    }
+    __syncthreads();
+    for (int32_t i = c; i < n; ++i) {  // forward: rows above c stay 0
+        const double yi = w[i] * rdiag[i];
+        if (threadIdx.x == 0) x[i] = yi;
+        for (int32_t r = i + 1 + threadIdx.x; r < n; r += blockDim.x) w[r] = fma(-sl[r * n + i], yi, w[r]);
+        __syncthreads();
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {  // backward into w; L^T's column i is L's row i
+        const double xi = x[i] * rdiag[i];
+        if (threadIdx.x == 0) w[i] = xi;
+        for (int32_t r = threadIdx.x; r < i; r += blockDim.x) x[r] = fma(-sl[i * n + r], xi, x[r]);
+        __syncthreads();
+    }
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) inv[(size_t)c * n + i] = w[i];
 }
 
 __global__ void gram_kernel(int32_t n, const double *Linv, double *inv) {
@@ -2034,6 +2100,7 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         gscr.alloc(per * gblocks, s);
     }
     const int64_t *ubp = ub.as<int64_t>();
+    const bool key32 = B.ncols < (1 << 27) - 1;  // a column and a lane index in one 32-bit sort key
     // launch(numeric, obase, out_cols, out_vals): one pass over the bins
     auto launch = [&](bool numeric, const int64_t *ob, int32_t *cc, double *cvv) {
         int32_t *cp = cnt.as<int32_t>();
@@ -2046,9 +2113,15 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
             else
                 { kern_sym<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv); ::amg::count_launch(); }
         };
-        sort_bin(spgemm_sort_kernel<kSortW0, true>, spgemm_sort_kernel<kSortW0, false>, 0, kSortW0);
-        sort_bin(spgemm_sort_kernel<kSortW1, true>, spgemm_sort_kernel<kSortW1, false>, 1, kSortW1);
-        sort_bin(spgemm_sort_kernel<kSortW2, true>, spgemm_sort_kernel<kSortW2, false>, 2, kSortW2);
+        if (key32) {
+            sort_bin(spgemm_sort_kernel<kSortW0, true, true>, spgemm_sort_kernel<kSortW0, false, true>, 0, kSortW0);
+            sort_bin(spgemm_sort_kernel<kSortW1, true, true>, spgemm_sort_kernel<kSortW1, false, true>, 1, kSortW1);
+            sort_bin(spgemm_sort_kernel<kSortW2, true, true>, spgemm_sort_kernel<kSortW2, false, true>, 2, kSortW2);
+        } else {
+            sort_bin(spgemm_sort_kernel<kSortW0, true, false>, spgemm_sort_kernel<kSortW0, false, false>, 0, kSortW0);
+            sort_bin(spgemm_sort_kernel<kSortW1, true, false>, spgemm_sort_kernel<kSortW1, false, false>, 1, kSortW1);
+            sort_bin(spgemm_sort_kernel<kSortW2, true, false>, spgemm_sort_kernel<kSortW2, false, false>, 2, kSortW2);
+        }
         if (nb[3] > 0) {
             const int blocks = std::min(div_up(nb[3], kAccWarps0), 152 * 16);
             if (numeric)
@@ -2271,17 +2344,22 @@ void cholesky_inverse(const DevCSR &A, double *inv, cudaStream_t s) {
     TmpBuf linv(sizeof(double) * (size_t)n * n, s), err(sizeof(int), s);
     AMG_CUDA(cudaMemsetAsync(err.ptr, 0, sizeof(int), s));
     if (n <= kSmemCoarse) {
-        const size_t smem = 2 * sizeof(double) * (size_t)n * n;
-        AMG_CUDA(cudaFuncSetAttribute(coarse_factor_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(2 * sizeof(double) * kSmemCoarse * kSmemCoarse)));
-        { coarse_factor_smem_kernel<<<1, 1024, smem, s>>>(n, A.rp(), A.ci(), A.v(), linv.as<double>(), err.as<int>()); ::amg::count_launch(); }
+        TmpBuf rdiag(sizeof(double) * (size_t)n, s);
+        const size_t smem_f = sizeof(double) * (size_t)n * n, smem_i = sizeof(double) * ((size_t)n * n + 2 * (size_t)n);
+        AMG_CUDA(cudaFuncSetAttribute(coarse_chol_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * kSmemCoarse * kSmemCoarse)));
+        AMG_CUDA(cudaFuncSetAttribute(coarse_inv_col_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * (kSmemCoarse * kSmemCoarse + 2 * kSmemCoarse))));
+        { coarse_chol_smem_kernel<<<1, 1024, smem_f, s>>>(n, A.rp(), A.ci(), A.v(), linv.as<double>(),
+                                                          rdiag.as<double>(), err.as<int>()); ::amg::count_launch(); }
+        { coarse_inv_col_kernel<<<n, 128, smem_i, s>>>(n, linv.as<double>(), rdiag.as<double>(), inv); ::amg::count_launch(); }
     } else {
         TmpBuf a(sizeof(double) * (size_t)n * n, s);
         { densify_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, A.rp(), A.ci(), A.v(), a.as<double>()); ::amg::count_launch(); }
         { cholesky_kernel<<<1, 1024, 0, s>>>(n, a.as<double>(), err.as<int>()); ::amg::count_launch(); }
         { tri_inverse_kernel<<<div_up(n, 128), 128, 0, s>>>(n, a.as<double>(), linv.as<double>()); ::amg::count_launch(); }
+        { gram_kernel<<<div_up((int64_t)n * n, kThreads), kThreads, 0, s>>>(n, linv.as<double>(), inv); ::amg::count_launch(); }
     }
-    { gram_kernel<<<div_up((int64_t)n * n, kThreads), kThreads, 0, s>>>(n, linv.as<double>(), inv); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
     if (!read_scalar(err.as<int>(), s)) return;
     // not positive definite: Gauss-Jordan with partial pivoting instead

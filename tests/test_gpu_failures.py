@@ -13,6 +13,7 @@
   AMG_TIMEOUT, later submits are refused with AMG_TIMEOUT, and a new server
   works normally.
 """
+import gc
 import numpy as np
 import pytest
 
@@ -44,6 +45,7 @@ def test_setup_survives_every_injected_allocation_failure(amg):
     b = gen.rhs_uniform(A.n, 1)
     gam = [0.0, 0.1]
     x_ref, i_ref = amg.Hierarchy.setup(A, gamma=gam).solve(b, tol=1e-8)
+    gc.collect()  # hierarchies that earlier tests left in reference cycles are freed now, not mid-sweep
     torch.cuda.synchronize()
     base = amg.device_bytes()
     failures = 0
