@@ -182,16 +182,18 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
                                  (int32_t)nc, V.P, s);
             setup::transpose(V.P, V.R, s);
         });
-        DevCSR AP;
+        // A P is read twice (by R (A P) and the minimal pattern) and then
+        // dropped: it stays in the product slots of its one-pass SpGEMM
+        setup::SlotProduct AP;
         auto C = std::make_unique<Level>();
         timed(h, 11, l, 0.0, s, [&] {
-            setup::spgemm(V.A, V.P, AP, s);
-            setup::spgemm(V.R, AP, C->A, s);
+            setup::spgemm_slots(V.A, V.P, AP, s);
+            setup::spgemm(V.R, AP.rows, C->A, s);
         });
         timed(h, 12, l, 0.0, s, [&] {
             init_level_maps(*C, s, false);  // R (A P) of a checked A_l
             C->inM.alloc(C->A.nnz + kPad);
-            setup::minimal_pattern(C->A, AP, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+            setup::minimal_pattern(C->A, AP.rows, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
         });
         if (nongal) {
             const double g = (n_gamma > 0 && gamma) ? gamma[std::min(l + 1, n_gamma - 1)] : 0.0;
@@ -252,7 +254,7 @@ static const uint8_t *hybrid_pattern(Hierarchy &h, int l, cudaStream_t s) {
     DevCSR APh;
     setup::spgemm(F.op(), F.P, APh, s);
     V.inM_hybrid.alloc(V.A.nnz + kPad);
-    setup::minimal_pattern(V.A, APh, F.cpts.as<int32_t>(), V.inM_hybrid.as<uint8_t>(), s);
+    setup::minimal_pattern(V.A, setup::rows_of(APh), F.cpts.as<int32_t>(), V.inM_hybrid.as<uint8_t>(), s);
     return V.inM_hybrid.as<uint8_t>();
 }
 

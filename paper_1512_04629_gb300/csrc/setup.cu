@@ -560,7 +560,7 @@ __device__ __forceinline__ void block_list_sort_warp(int32_t *list, int32_t u, i
 // Inserts every product column of row i; returns the number of distinct columns.
 template <int NT>
 __device__ int32_t row_insert(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
-                              const int32_t *brp, const int32_t *bci, RowTables &t,
+                              const int32_t *bbeg, const int32_t *bend, const int32_t *bci, RowTables &t,
                               int32_t *counter, int64_t ub) {
     t.hs = row_slots(ub, t.umax * 2);
     for (int32_t s = lane; s < t.hs; s += NT) t.keys[s] = -1;
@@ -569,7 +569,7 @@ __device__ int32_t row_insert(int32_t i, int32_t lane, const int32_t *arp, const
     uint32_t mask = (uint32_t)t.hs - 1;
     for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
         int32_t k = aci[p];
-        for (int32_t q = brp[k] + lane; q < brp[k + 1]; q += NT) {
+        for (int32_t q = bbeg[k] + lane; q < bend[k]; q += NT) {
             int32_t j = bci[q];
             uint32_t s = hash32(j) & mask;
             while (true) {
@@ -595,10 +595,10 @@ __device__ __forceinline__ int32_t row_lookup(const RowTables &t, int32_t j) {
 
 template <int NT>
 __device__ int32_t row_numeric(int32_t i, int32_t lane, const int32_t *arp, const int32_t *aci,
-                               const double *av, const int32_t *brp, const int32_t *bci,
+                               const double *av, const int32_t *bbeg, const int32_t *bend, const int32_t *bci,
                                const double *bv, RowTables &t, int32_t *counter,
                                const int64_t *obase, int32_t *cci, double *cv, int64_t ub) {
-    int32_t u = row_insert<NT>(i, lane, arp, aci, brp, bci, t, counter, ub);
+    int32_t u = row_insert<NT>(i, lane, arp, aci, bbeg, bend, bci, t, counter, ub);
     // compact the distinct keys, pad to a power of two, bitonic sort
     if (lane == 0) *counter = 0;
     gsync<NT>();
@@ -648,7 +648,7 @@ __device__ int32_t row_numeric(int32_t i, int32_t lane, const int32_t *arp, cons
     for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
         int32_t k = aci[p];
         double a = av[p];
-        for (int32_t q = brp[k] + lane; q < brp[k + 1]; q += NT) {
+        for (int32_t q = bbeg[k] + lane; q < bend[k]; q += NT) {
             int32_t r = row_lookup(t, bci[q]);
             t.acc[r] += a * bv[q];
         }
@@ -660,13 +660,13 @@ __device__ int32_t row_numeric(int32_t i, int32_t lane, const int32_t *arp, cons
 }
 
 __global__ void spgemm_ub_kernel(int32_t n, const int32_t *arp, const int32_t *aci,
-                                 const int32_t *brp, int64_t *ub) {
+                                 const int32_t *bbeg, const int32_t *bend, int64_t *ub) {
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t s = 0;
     for (int32_t p = arp[i]; p < arp[i + 1]; ++p) {
         int32_t k = aci[p];
-        s += brp[k + 1] - brp[k];
+        s += bend[k] - bbeg[k];
     }
     ub[i] = s;
 }
@@ -733,7 +733,7 @@ constexpr unsigned kFull = 0xffffffffu;
 template <int W, bool NUMERIC, bool KEY32>
 __global__ void __launch_bounds__(256, 8)  // 32 registers: a full SM of warps to hide the load chains
 spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_t *__restrict__ arp,
-                   const int32_t *__restrict__ aci, const double *__restrict__ av, const int32_t *__restrict__ brp,
+                   const int32_t *__restrict__ aci, const double *__restrict__ av, const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
                    const int32_t *__restrict__ bci, const double *__restrict__ bv, int32_t *__restrict__ cnt,
                    const int64_t *__restrict__ obase, int32_t *__restrict__ cci, double *__restrict__ cv) {
     constexpr int G = 32 / W;  // rows per warp
@@ -766,8 +766,8 @@ spgemm_sort_kernel(const int32_t *__restrict__ rows, int32_t nrows, const int32_
             if (idx < nA) {
                 const int32_t k = aci[p0 + idx];
                 if (NUMERIC) a = av[p0 + idx];
-                b0 = brp[k];
-                len = brp[k + 1] - b0;
+                b0 = bbeg[k];
+                len = bend[k] - b0;
             }
             int32_t incl = len;
 #pragma unroll
@@ -976,7 +976,7 @@ __device__ __forceinline__ void warp_emit_sorted(AccTab<U> &t, int32_t u, uint32
 
 template <int U, bool NUMERIC>
 __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
-                                const double *__restrict__ av, const int32_t *__restrict__ brp,
+                                const double *__restrict__ av, const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
                                 const int32_t *__restrict__ bci, const double *__restrict__ bv, AccTab<U> &t,
                                 int64_t ub, const int64_t *__restrict__ obase, int32_t *__restrict__ cci,
                                 double *__restrict__ cv) {
@@ -1000,8 +1000,8 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
         if (idx < nA) {
             const int32_t k = aci[p0 + idx];
             if (NUMERIC) a = av[p0 + idx];
-            b0 = brp[k];
-            len = brp[k + 1] - b0;
+            b0 = bbeg[k];
+            len = bend[k] - b0;
         }
         if (per_k) {
             const int kend = min(32, nA - c0);
@@ -1150,7 +1150,7 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
 template <int U, int WARPS, bool NUMERIC>
 __global__ void __launch_bounds__(WARPS * 32, U <= 128 ? AMG_ACC_MIN_BLOCKS : 1)
 spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
-                  const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
+                  const double *av, const int32_t *bbeg, const int32_t *bend, const int32_t *bci, const double *bv,
                   int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1166,7 +1166,7 @@ spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const 
             i_nx = rows[r + step];
             ub_nx = ub[i_nx];
         }
-        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, brp, bci, bv, t, ubi, obase, cci, cv);
+        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, bbeg, bend, bci, bv, t, ubi, obase, cci, cv);
         if (lane == 0) cnt[i] = u;
     }
 }
@@ -1174,7 +1174,7 @@ spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const 
 template <bool NUMERIC>
 __global__ void __launch_bounds__(kBlockThreads)
 spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
-                    const double *av, const int32_t *brp, const int32_t *bci, const double *bv,
+                    const double *av, const int32_t *bbeg, const int32_t *bend, const int32_t *bci, const double *bv,
                     int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub,
                     unsigned char *gscratch, int32_t ghs, int32_t gumax) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1197,11 +1197,11 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
     for (int32_t r = blockIdx.x; r < nrows; r += gridDim.x) {
         int32_t i = rows[r];
         if (NUMERIC) {
-            int32_t u = row_numeric<kBlockThreads>(i, threadIdx.x, arp, aci, av, brp, bci, bv, t, &counter,
+            int32_t u = row_numeric<kBlockThreads>(i, threadIdx.x, arp, aci, av, bbeg, bend, bci, bv, t, &counter,
                                                    obase, cci, cv, ub[i]);
             if (threadIdx.x == 0) cnt[i] = u;
         } else {
-            int32_t u = row_insert<kBlockThreads>(i, threadIdx.x, arp, aci, brp, bci, t, &counter, ub[i]);
+            int32_t u = row_insert<kBlockThreads>(i, threadIdx.x, arp, aci, bbeg, bend, bci, t, &counter, ub[i]);
             if (threadIdx.x == 0) cnt[i] = u;
         }
     }
@@ -1212,7 +1212,7 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
 // ---------------------------------------------------------------------------
 template <int T>
 __global__ void minimal_pattern_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
-                                       const int32_t *aprp, const int32_t *apci,
+                                       const int32_t *apbeg, const int32_t *apend, const int32_t *apci,
                                        const int32_t *cpts, uint8_t *inM) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t i = (int32_t)(g / T);
@@ -1222,7 +1222,7 @@ __global__ void minimal_pattern_kernel(int32_t n, const int32_t *rp, const int32
     for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
         const int32_t j = ci[p];
         const int32_t fj = cpts[j];
-        const bool m = contains(apci, aprp[fi], aprp[fi + 1], j) || contains(apci, aprp[fj], aprp[fj + 1], i);
+        const bool m = contains(apci, apbeg[fi], apend[fi], j) || contains(apci, apbeg[fj], apend[fj], i);
         inM[p] = (uint8_t)m;
     }
 }
@@ -1764,6 +1764,15 @@ gauss_jordan_kernel(int32_t n, double *a, double *inv, double *fac, int *err) {
 // copy each row's entries from its product-bound slot to the final CSR
 // compaction of the product-bound slots: eight lanes per row
 constexpr int kCompactLanes = 8;
+// row i of a product left in its slots: [obase_i, obase_i + count_i)
+__global__ void slot_bounds_kernel(int32_t n, const int64_t *obase, const int32_t *cnt, int32_t *beg, int32_t *end) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t b = (int32_t)obase[i];
+    beg[i] = b;
+    end[i] = b + cnt[i];
+}
+
 __global__ void spgemm_compact_kernel(int32_t n, const int64_t *obase, const int32_t *crp, const int32_t *tci,
                                       const double *tv, int32_t *cci, double *cv) {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2043,13 +2052,16 @@ static int64_t next_pow2(int64_t x) {
     return p;
 }
 
-void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
+// The shared driver: C = A B into Cm (CSR), or -- with slots given and the
+// one-pass form available -- left in its product slots.
+static void spgemm_impl(const DevCSR &A, const SpRows &B, DevCSR &Cm, SlotProduct *slots, cudaStream_t s) {
     require(A.ncols == B.nrows, "spgemm: inner dimensions differ");
+    if (slots) slots->rows = SpRows{};
     int32_t n = A.nrows;
     Cm.nrows = n;
     Cm.ncols = B.ncols;
-    Cm.rowptr.alloc(sizeof(int32_t) * (n + 1));
     if (n == 0) {
+        Cm.rowptr.alloc(sizeof(int32_t) * (n + 1));
         Cm.nnz = 0;
         AMG_CUDA(cudaMemsetAsync(Cm.rowptr.ptr, 0, sizeof(int32_t), s));
         Cm.col.alloc(sizeof(int32_t) * kPad);
@@ -2060,7 +2072,7 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         dcounts(sizeof(SpgemmCounts), s), cnt(sizeof(int32_t) * (n + 1), s), obase(sizeof(int64_t) * (n + 1), s);
     int g = div_up(n, kThreads);
     SpgemmCounts *dc = dcounts.as<SpgemmCounts>();
-    { spgemm_ub_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), B.rp(), ub.as<int64_t>()); ::amg::count_launch(); }
+    { spgemm_ub_kernel<<<g, kThreads, 0, s>>>(n, A.rp(), A.ci(), B.beg, B.end, ub.as<int64_t>()); ::amg::count_launch(); }
     AMG_CUDA(cudaMemsetAsync(dcounts.ptr, 0, sizeof(SpgemmCounts), s));
     { bin_rows_kernel<<<g, kThreads, 0, s>>>(n, ub.as<int64_t>(), bins.as<int32_t>(), dc); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
@@ -2109,9 +2121,9 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
             const int64_t warps = ((int64_t)nb[b] * W + 31) / 32;
             const int blocks = (int)std::min<int64_t>((warps + 7) / 8, nres);
             if (numeric)
-                { kern_num<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv); ::amg::count_launch(); }
+                { kern_num<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv); ::amg::count_launch(); }
             else
-                { kern_sym<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv); ::amg::count_launch(); }
+                { kern_sym<<<blocks, 256, 0, s>>>(rows_of(b), nb[b], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv); ::amg::count_launch(); }
         };
         if (key32) {
             sort_bin(spgemm_sort_kernel<kSortW0, true, true>, spgemm_sort_kernel<kSortW0, false, true>, 0, kSortW0);
@@ -2126,39 +2138,39 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
             const int blocks = std::min(div_up(nb[3], kAccWarps0), 152 * 16);
             if (numeric)
                 { spgemm_acc_kernel<kAccU0, kAccWarps0, true><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
-                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
             else
                 { spgemm_acc_kernel<kAccU0, kAccWarps0, false><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
-                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[4] > 0) {
             const int blocks = std::min(div_up(nb[4], kAccWarps1), 152 * 16);
             if (numeric)
                 { spgemm_acc_kernel<kAccU1, kAccWarps1, true><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
-                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
             else
                 { spgemm_acc_kernel<kAccU1, kAccWarps1, false><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
-                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
+                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
         if (nb[5] > 0) {
             const int blocks = std::min(nb[5], 152 * 4);
             if (numeric)
                 { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
                     ubp, nullptr, 0, 0); ::amg::count_launch(); }
         }
         if (nb[6] > 0) {
             if (numeric)
                 { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
             else
                 { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.rp(), B.ci(), B.v(), cp, ob, cc, cvv,
+                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
                     ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
         }
         AMG_CHECK_LAUNCH();
@@ -2173,9 +2185,24 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     const char *force = std::getenv("AMG_SPGEMM_TWO_PASS");
     bool one_pass = (double)total_ub * 12.0 < 0.4 * (double)fr && !(force && force[0] == '1');
     int64_t nnz;
+    if (one_pass && slots && total_ub < ((int64_t)1 << 31) - kPad) {
+        // the rows stay where the numeric pass wrote them: no count scan, no compaction
+        SlotProduct &P = *slots;
+        P.ci.alloc(sizeof(int32_t) * (total_ub + kPad), s);
+        P.v.alloc(sizeof(double) * (total_ub + kPad), s);
+        P.beg.alloc(sizeof(int32_t) * (n + 1), s);
+        P.end.alloc(sizeof(int32_t) * (n + 1), s);
+        launch(true, obase.as<int64_t>(), P.ci.as<int32_t>(), P.v.as<double>());
+        { slot_bounds_kernel<<<g, kThreads, 0, s>>>(n, obase.as<int64_t>(), cnt.as<int32_t>(), P.beg.as<int32_t>(),
+                                                   P.end.as<int32_t>()); ::amg::count_launch(); }
+        AMG_CHECK_LAUNCH();
+        P.rows = SpRows{P.beg.as<int32_t>(), P.end.as<int32_t>(), P.ci.as<int32_t>(), P.v.as<double>(), n, B.ncols};
+        return;
+    }
     if (one_pass) {
         TmpBuf tci(sizeof(int32_t) * (total_ub + kPad), s), tv(sizeof(double) * (total_ub + kPad), s);
         launch(true, obase.as<int64_t>(), tci.as<int32_t>(), tv.as<double>());
+        Cm.rowptr.alloc(sizeof(int32_t) * (n + 1));
         nnz = exclusive_scan_i32(cnt.as<int32_t>(), Cm.rp(), n, s);
         require(nnz < ((int64_t)1 << 31), "spgemm: product has 2^31 or more entries");
         Cm.nnz = nnz;
@@ -2188,6 +2215,7 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
         return;  // the temporaries' stream-ordered frees follow the compaction
     }
     launch(false, nullptr, nullptr, nullptr);
+    Cm.rowptr.alloc(sizeof(int32_t) * (n + 1));
     nnz = exclusive_scan_i32(cnt.as<int32_t>(), Cm.rp(), n, s);
     require(nnz < ((int64_t)1 << 31), "spgemm: product has 2^31 or more entries");
     Cm.nnz = nnz;
@@ -2199,13 +2227,19 @@ void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &Cm, cudaStream_t s) {
     launch(true, obase.as<int64_t>(), Cm.ci(), Cm.v());
 }
 
-void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, uint8_t *inM,
-                     cudaStream_t s) {
+void spgemm(const DevCSR &A, const SpRows &B, DevCSR &C, cudaStream_t s) { spgemm_impl(A, B, C, nullptr, s); }
+
+void spgemm_slots(const DevCSR &A, const DevCSR &B, SlotProduct &C, cudaStream_t s) {
+    spgemm_impl(A, rows_of(B), C.csr, &C, s);
+    if (!C.rows.beg) C.rows = rows_of(C.csr);  // formed as CSR (empty, or too large for its slots)
+}
+
+void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s) {
     if (Ac.nrows == 0) return;
     with_row_lanes(row_lanes(Ac), [&](auto tc) {
         constexpr int L = decltype(tc)::value;
         minimal_pattern_kernel<L><<<div_up((int64_t)Ac.nrows * L, kThreads), kThreads, 0, s>>>(
-            Ac.nrows, Ac.rp(), Ac.ci(), AP.rp(), AP.ci(), cpts, inM);
+            Ac.nrows, Ac.rp(), Ac.ci(), AP.beg, AP.end, AP.ci, cpts, inM);
         ::amg::count_launch();
     });
     AMG_CHECK_LAUNCH();

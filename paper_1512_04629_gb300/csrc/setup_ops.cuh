@@ -33,11 +33,30 @@ void direct_interp(const DevCSR &A, const uint8_t *strong, const int8_t *cf, con
                    int32_t nc, DevCSR &P, cudaStream_t s);
 // R = P^T with sorted rows.
 void transpose(const DevCSR &P, DevCSR &R, cudaStream_t s);
+// Rows of a sparse operand: row i holds ci / v[beg[i] .. end[i]), sorted by
+// column; a CSR matrix is beg = rowptr, end = rowptr + 1.
+struct SpRows {
+    const int32_t *beg = nullptr, *end = nullptr, *ci = nullptr;
+    const double *v = nullptr;
+    int32_t nrows = 0, ncols = 0;
+};
+inline SpRows rows_of(const DevCSR &M) { return SpRows{M.rp(), M.rp() + 1, M.ci(), M.v(), M.nrows, M.ncols}; }
+// A product kept where the one-pass SpGEMM wrote it: row i's sorted entries
+// at the start of its slot (sized by the row's product count), with no
+// compaction; when the products would not fit in memory the product is
+// formed as a CSR matrix instead.  `rows` views either form.
+struct SlotProduct {
+    DevCSR csr;
+    TmpBuf ci, v, beg, end;
+    SpRows rows;
+};
 // C = A B (structural, deterministic, sorted rows).
-void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &C, cudaStream_t s);
+void spgemm(const DevCSR &A, const SpRows &B, DevCSR &C, cudaStream_t s);
+inline void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &C, cudaStream_t s) { spgemm(A, rows_of(B), C, s); }
+// A B left in its product slots (for an operand that is read, not kept).
+void spgemm_slots(const DevCSR &A, const DevCSR &B, SlotProduct &C, cudaStream_t s);
 // Minimal-pattern flags of Ac's entries from the C rows of AP.
-void minimal_pattern(const DevCSR &Ac, const DevCSR &AP, const int32_t *cpts, uint8_t *inM,
-                     cudaStream_t s);
+void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s);
 // Hybrid variant: pattern of Phat^T Ahat P (+ transpose) with Ahat the
 // sparsified fine operator.  Recomputes AP from Ahat.
 // Sparsify (Algorithm 3's drop test and symmetric N); fills keep[] and Ahat;
