@@ -193,7 +193,7 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
         timed(h, 12, l, 0.0, s, [&] {
             init_level_maps(*C, s, false);  // R (A P) of a checked A_l
             C->inM.alloc(C->A.nnz + kPad);
-            setup::minimal_pattern(C->A, AP.rows, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s);
+            setup::minimal_pattern(C->A, AP.rows, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s, C->tpos.as<int32_t>());
         });
         if (nongal) {
             const double g = (n_gamma > 0 && gamma) ? gamma[std::min(l + 1, n_gamma - 1)] : 0.0;
@@ -254,7 +254,8 @@ static const uint8_t *hybrid_pattern(Hierarchy &h, int l, cudaStream_t s) {
     DevCSR APh;
     setup::spgemm(F.op(), F.P, APh, s);
     V.inM_hybrid.alloc(V.A.nnz + kPad);
-    setup::minimal_pattern(V.A, setup::rows_of(APh), F.cpts.as<int32_t>(), V.inM_hybrid.as<uint8_t>(), s);
+    setup::minimal_pattern(V.A, setup::rows_of(APh), F.cpts.as<int32_t>(), V.inM_hybrid.as<uint8_t>(), s,
+                           V.tpos.as<int32_t>());
     return V.inM_hybrid.as<uint8_t>();
 }
 

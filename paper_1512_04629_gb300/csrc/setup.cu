@@ -225,10 +225,24 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
     const bool live = i < n;  // no early exit: the group reduction and the append need every lane
     int32_t cnt = 0;  // |S^T_i|: rows j whose strong set holds i
     if (live) {
-        for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
-            const uint8_t st = strong[tpos[p]];
-            cnt += st;
-            sym[p] = (uint8_t)(st | strong[p]);  // j in S_i u S^T_i, read by every round
+        const int32_t p0 = rp[i], p1 = rp[i + 1];
+        for (int32_t pb = p0 + t; pb < p1; pb += T * 4) {  // four entries' loads in flight per lane
+            int32_t tp[4];
+            uint8_t own[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t p = pb + u * T;
+                tp[u] = p < p1 ? tpos[p] : 0;
+                own[u] = p < p1 ? strong[p] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t p = pb + u * T;
+                if (p >= p1) continue;
+                const uint8_t st = strong[tp[u]];
+                cnt += st;
+                sym[p] = (uint8_t)(st | own[u]);  // j in S_i u S^T_i, read by every round
+            }
         }
     }
     cnt = group_sum_i32<T>(cnt);
@@ -250,27 +264,47 @@ __global__ void pmis_init_kernel(int32_t n, const int32_t *rp, const int32_t *tp
 // list's actual length first and does nothing once it is zero.  Every block
 // takes the same number of strides, so the block barriers of the append are
 // reached by all of its threads.
-template <int T>
-__global__ void pmis_select_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
-                                   const uint8_t *sym, const double *w, const int8_t *state, uint8_t *newc) {
-    const int m = *len;  // the same for the whole grid
+constexpr int kPmisChunk = 4;
+
+// DENSE (the first round, when nearly every row is undecided): the rows
+// 0 .. n-1 themselves, the undecided ones taking part -- coalesced, and one
+// dependent load shorter than going through the list.
+template <int T, bool DENSE>
+__global__ void pmis_select_kernel(const int32_t *list, const int *len, int32_t n, const int32_t *rp,
+                                   const int32_t *ci, const uint8_t *sym, const double *w, const int8_t *state,
+                                   uint8_t *newc) {
+    const int m = DENSE ? n : *len;  // the same for the whole grid
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x < (int64_t)m * T;
          g += stride) {
         const int64_t k = g / T;
         const int t = (int)(g % T);
-        const bool live = k < m;  // no early exit: the group reduction needs every lane
-        const int32_t i = live ? list[k] : 0;
+        const int32_t i = k < m ? (DENSE ? (int32_t)k : list[k]) : 0;
+        // the row's bounds, weight and state are independent loads, issued together
+        const int32_t p0 = k < m ? rp[i] : 0, p1 = k < m ? rp[i + 1] : 0;
+        const int64_t wi = k < m ? __double_as_longlong(w[i]) : 0;  // weights >= 0 order like their bits
+        const bool live = k < m && (!DENSE || state[i] == kU);  // no early exit: the group reduction needs every lane
         bool lose = false;
         if (live) {
-            // weights are >= 0: their bit patterns order like the values
-            const int64_t wi = __double_as_longlong(w[i]);
-            for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) {
-                if (!sym[p]) continue;  // S_i u S^T_i
-                const int32_t j = ci[p];
-                if (state[j] != kU) continue;
-                const int64_t wj = __double_as_longlong(w[j]);
-                if (wj > wi || (wj == wi && j > i)) { lose = true; break; }
+            // kPmisChunk entries a lane per step: their flags and columns, then
+            // their neighbours' states and weights, are each in flight together
+            for (int32_t pb = p0 + t; pb < p1; pb += T * kPmisChunk) {
+                int32_t jj[kPmisChunk];
+                bool sy[kPmisChunk];
+#pragma unroll
+                for (int u = 0; u < kPmisChunk; ++u) {
+                    const int32_t p = pb + u * T;
+                    sy[u] = p < p1 && sym[p];  // S_i u S^T_i
+                    jj[u] = p < p1 ? ci[p] : i;
+                }
+#pragma unroll
+                for (int u = 0; u < kPmisChunk; ++u) {
+                    if (!sy[u]) continue;
+                    const int32_t j = jj[u];
+                    const int8_t sj = state[j];
+                    const int64_t wj = __double_as_longlong(w[j]);
+                    if (sj == kU && (wj > wi || (wj == wi && j > i))) lose = true;
+                }
             }
         }
         lose = group_any<T>(lose);
@@ -286,27 +320,40 @@ __global__ void pmis_select_kernel(const int32_t *list, const int *len, const in
 // neighbour read before or after its write gives the same answer, so the
 // result does not depend on the order of the groups.  Undecided rows go to
 // the next round's list.
-template <int T>
-__global__ void pmis_apply_kernel(const int32_t *list, const int *len, const int32_t *rp, const int32_t *ci,
-                                  const uint8_t *strong, const uint8_t *newc, int8_t *state, int32_t *next,
-                                  int *next_len) {
-    const int m = *len;  // the same for the whole grid
+template <int T, bool DENSE>
+__global__ void pmis_apply_kernel(const int32_t *list, const int *len, int32_t n, const int32_t *rp,
+                                  const int32_t *ci, const uint8_t *strong, const uint8_t *newc, int8_t *state,
+                                  int32_t *next, int *next_len) {
+    const int m = DENSE ? n : *len;  // the same for the whole grid
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x < (int64_t)m * T;
          g += stride) {
         const int64_t k = g / T;
         const int t = (int)(g % T);
-        const bool live = k < m;
-        const int32_t i = live ? list[k] : 0;
+        const int32_t i = k < m ? (DENSE ? (int32_t)k : list[k]) : 0;
+        const int32_t p0 = k < m ? rp[i] : 0, p1 = k < m ? rp[i + 1] : 0;
+        const bool live = k < m && (!DENSE || state[i] == kU);  // a row's state is written by its own group only
         const bool c = live && newc[i];
         const bool und = live && !c;
         bool f = false;
         if (und)
-            for (int32_t p = rp[i] + t; p < rp[i + 1] && !f; p += T) {
-                if (!strong[p]) continue;
-                const int32_t j = ci[p];
-                const int8_t sj = *(volatile const int8_t *)&state[j];
-                if (sj == kC || (sj == kU && newc[j])) f = true;
+            for (int32_t pb = p0 + t; pb < p1; pb += T * kPmisChunk) {
+                int32_t jj[kPmisChunk];
+                bool st[kPmisChunk];
+#pragma unroll
+                for (int u = 0; u < kPmisChunk; ++u) {
+                    const int32_t p = pb + u * T;
+                    st[u] = p < p1 && strong[p];
+                    jj[u] = p < p1 ? ci[p] : i;
+                }
+#pragma unroll
+                for (int u = 0; u < kPmisChunk; ++u) {
+                    if (!st[u]) continue;
+                    const int32_t j = jj[u];
+                    const int8_t sj = *(volatile const int8_t *)&state[j];
+                    const bool cj = newc[j] != 0;
+                    if (sj == kC || (sj == kU && cj)) f = true;
+                }
             }
         f = group_any<T>(f);
         if (live && t == 0) {
@@ -1210,6 +1257,28 @@ spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, cons
 // ---------------------------------------------------------------------------
 // minimal pattern: (i,j) in M iff j in AP[cpts[i]] or i in AP[cpts[j]]
 // ---------------------------------------------------------------------------
+// The same through the symmetric pattern of Ac: a first pass flags (i, j)
+// when j is in AP[cpts[i]] -- one search per entry, in the row shared by the
+// lanes of the group -- and the second ORs in the mirrored entry's flag, which
+// is the test "i in AP[cpts[j]]".
+template <int T>
+__global__ void minimal_pattern_rows_kernel(int32_t n, const int32_t *rp, const int32_t *ci, const int32_t *apbeg,
+                                            const int32_t *apend, const int32_t *apci, const int32_t *cpts,
+                                            uint8_t *first) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t i = (int32_t)(g / T);
+    const int t = (int)(g % T);
+    if (i >= n) return;
+    const int32_t fi = cpts[i];
+    const int32_t b = apbeg[fi], e = apend[fi];
+    for (int32_t p = rp[i] + t; p < rp[i + 1]; p += T) first[p] = (uint8_t)contains(apci, b, e, ci[p]);
+}
+
+__global__ void mirror_or_kernel(int64_t nnz, const uint8_t *first, const int32_t *tpos, uint8_t *inM) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < nnz) inM[p] = first[p] | first[tpos[p]];
+}
+
 template <int T>
 __global__ void minimal_pattern_kernel(int32_t n, const int32_t *rp, const int32_t *ci,
                                        const int32_t *apbeg, const int32_t *apend, const int32_t *apci,
@@ -1935,12 +2004,22 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
             int32_t *nxt = list[r & 1];
             with_row_lanes(T, [&](auto tc) {
                 constexpr int L = decltype(tc)::value;
+                if (r == 1) {  // every row, undecided or not (the list holds nearly all of them)
+                    const int gl = (int)std::min<int64_t>(div_up((int64_t)n * L, kThreads), nres);
+                    pmis_select_kernel<L, true><<<gl, kThreads, 0, s>>>(
+                        cur, dc + r - 1, n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(), cf, newc.as<uint8_t>());
+                    ::amg::count_launch();
+                    pmis_apply_kernel<L, true><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, n, A.rp(), A.ci(), strong,
+                                                                       newc.as<uint8_t>(), cf, nxt, dc + r);
+                    ::amg::count_launch();
+                    return;
+                }
                 const int gl = (int)std::min<int64_t>(div_up(bound * L, kThreads), nres);
-                pmis_select_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), sym.as<uint8_t>(),
-                                                              w.as<double>(), cf, newc.as<uint8_t>());
+                pmis_select_kernel<L, false><<<gl, kThreads, 0, s>>>(
+                    cur, dc + r - 1, n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(), cf, newc.as<uint8_t>());
                 ::amg::count_launch();
-                pmis_apply_kernel<L><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, A.rp(), A.ci(), strong,
-                                                             newc.as<uint8_t>(), cf, nxt, dc + r);
+                pmis_apply_kernel<L, false><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, n, A.rp(), A.ci(), strong,
+                                                                    newc.as<uint8_t>(), cf, nxt, dc + r);
                 ::amg::count_launch();
             });
         }
@@ -2234,8 +2313,24 @@ void spgemm_slots(const DevCSR &A, const DevCSR &B, SlotProduct &C, cudaStream_t
     if (!C.rows.beg) C.rows = rows_of(C.csr);  // formed as CSR (empty, or too large for its slots)
 }
 
-void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s) {
+void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s,
+                     const int32_t *tpos) {
     if (Ac.nrows == 0) return;
+    if (tpos) {
+        TmpBuf first(Ac.nnz + 1, s);
+        with_row_lanes(row_lanes(Ac), [&](auto tc) {
+            constexpr int L = decltype(tc)::value;
+            minimal_pattern_rows_kernel<L><<<div_up((int64_t)Ac.nrows * L, kThreads), kThreads, 0, s>>>(
+                Ac.nrows, Ac.rp(), Ac.ci(), AP.beg, AP.end, AP.ci, cpts, first.as<uint8_t>());
+            ::amg::count_launch();
+        });
+        if (Ac.nnz > 0) {
+            mirror_or_kernel<<<div_up(Ac.nnz, kThreads), kThreads, 0, s>>>(Ac.nnz, first.as<uint8_t>(), tpos, inM);
+            ::amg::count_launch();
+        }
+        AMG_CHECK_LAUNCH();
+        return;
+    }
     with_row_lanes(row_lanes(Ac), [&](auto tc) {
         constexpr int L = decltype(tc)::value;
         minimal_pattern_kernel<L><<<div_up((int64_t)Ac.nrows * L, kThreads), kThreads, 0, s>>>(

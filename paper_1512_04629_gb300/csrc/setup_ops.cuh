@@ -55,8 +55,11 @@ void spgemm(const DevCSR &A, const SpRows &B, DevCSR &C, cudaStream_t s);
 inline void spgemm(const DevCSR &A, const DevCSR &B, DevCSR &C, cudaStream_t s) { spgemm(A, rows_of(B), C, s); }
 // A B left in its product slots (for an operand that is read, not kept).
 void spgemm_slots(const DevCSR &A, const DevCSR &B, SlotProduct &C, cudaStream_t s);
-// Minimal-pattern flags of Ac's entries from the C rows of AP.
-void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s);
+// Minimal-pattern flags of Ac's entries from the C rows of AP; tpos (the
+// mirrored-entry positions of Ac's symmetric pattern), when given, lets each
+// entry be tested in its own row only.
+void minimal_pattern(const DevCSR &Ac, const SpRows &AP, const int32_t *cpts, uint8_t *inM, cudaStream_t s,
+                     const int32_t *tpos = nullptr);
 // Hybrid variant: pattern of Phat^T Ahat P (+ transpose) with Ahat the
 // sparsified fine operator.  Recomputes AP from Ahat.
 // Sparsify (Algorithm 3's drop test and symmetric N); fills keep[] and Ahat;
