@@ -15,7 +15,9 @@
 // the last block to arrive sums them in block order.
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <type_traits>
+#include <utility>
 
 #include "common.cuh"
 #include "cycle_ops.cuh"
@@ -24,6 +26,43 @@ namespace amg {
 namespace cyc {
 
 namespace {
+
+// Programmatic dependent launch: the solve-path kernels go out with the
+// stream-serialisation attribute, so the next kernel's blocks are scheduled
+// while the current one runs (its launch latency is hidden), and every such
+// kernel begins with pdl_begin(): it lets its own dependent launch, then
+// waits until the kernel before it has completed and its writes are visible.
+// Without the attribute (or with AMG_PDL=0) both instructions do nothing.
+__device__ __forceinline__ void pdl_begin() {
+    asm volatile("griddepcontrol.launch_dependents;\n\tgriddepcontrol.wait;" ::: "memory");
+}
+
+static bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = std::getenv("AMG_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
+
+template <typename... KArgs, typename... Args>
+static void pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args &&...args) {
+    if (!pdl_enabled()) {
+        kern<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+        return;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    AMG_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
 
 constexpr int kThreads = 256;
 
@@ -163,6 +202,7 @@ __global__ void __launch_bounds__(kThreads)
 csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const VT *__restrict__ v,
               const XT *__restrict__ b, const XT *__restrict__ dinv, const XT *__restrict__ x,
               XT *__restrict__ o1, XT *__restrict__ o2) {
+    pdl_begin();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t i = (int32_t)(g / T);
     int t = (int)(g % T);
@@ -195,6 +235,7 @@ __global__ void __launch_bounds__(kThreads)
 sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
                const XT *__restrict__ dinv, const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
+    pdl_begin();
     int32_t pos = blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= n) return;
     const int32_t i = perm ? __ldg(perm + pos) : pos;
@@ -235,6 +276,7 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
 // ---------------------------------------------------------------------------
 __global__ void part_exchange_kernel(int64_t nghost, const int32_t *__restrict__ gcol, const double *__restrict__ src,
                                      const double *__restrict__ scale, double *__restrict__ gbuf) {
+    pdl_begin();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nghost) return;
     const int32_t j = __ldg(gcol + k);
@@ -266,6 +308,7 @@ __global__ void __launch_bounds__(kThreads)
 part_op_kernel(int32_t n, const int32_t *__restrict__ rp, PartView pv, const double *__restrict__ v,
                const double *__restrict__ b, const double *__restrict__ dinv, const double *__restrict__ x,
                double *__restrict__ o1, double *__restrict__ o2) {
+    pdl_begin();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t i = (int32_t)(g / T);
     int t = (int)(g % T);
@@ -305,7 +348,7 @@ part_op_kernel(int32_t n, const int32_t *__restrict__ rp, PartView pv, const dou
 // the exchange for an operator whose products gather src (times scale)
 void part_exchange(const PartView &pv, const double *src, const double *scale, cudaStream_t s) {
     if (pv.nghost == 0) return;
-    { part_exchange_kernel<<<(int)div_up(pv.nghost, (int64_t)kThreads), kThreads, 0, s>>>(pv.nghost, pv.gcol, src, scale, pv.gbuf); ::amg::count_launch(); }
+    { pdl_launch(part_exchange_kernel, (int)div_up(pv.nghost, (int64_t)kThreads), kThreads, 0, s, pv.nghost, pv.gcol, src, scale, pv.gbuf); ::amg::count_launch(); }
 }
 
 template <int OP>
@@ -315,7 +358,7 @@ void part_op(const CycMat<double> &A, const double *b, const double *dinv, const
     if (OP == kPre) part_exchange(A.part, b, dinv, s);
     else part_exchange(A.part, x, nullptr, s);
     // one lane per row: the order of the unpartitioned one-lane kernels
-    { part_op_kernel<1, OP><<<(int)div_up((int64_t)n, (int64_t)kThreads), kThreads, 0, s>>>(n, A.rp, A.part, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    { pdl_launch(part_op_kernel<1, OP>, (int)div_up((int64_t)n, (int64_t)kThreads), kThreads, 0, s, n, A.rp, A.part, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
@@ -330,6 +373,7 @@ __global__ void __launch_bounds__(kThreads)
 sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
                      const int32_t *__restrict__ sw, SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
                      const XT *__restrict__ dinv, const XT *__restrict__ x, XT *__restrict__ o1, XT *__restrict__ o2) {
+    pdl_begin();
     constexpr int T = 32 / C, U = 4;
     const int32_t slice = (int32_t)(((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31, r = lane % C, t = lane / C;
@@ -396,9 +440,9 @@ void launch_sell_lanes(const CycMat<VT> &A, const XT *b, const XT *dinv, const X
     const int64_t warps = div_up((int64_t)n, (int64_t)C);
     const int g = (int)div_up(warps * 32, (int64_t)kThreads);
     if (A.sd)
-        { sell_lanes_op_kernel<VT, XT, OP, true, C><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, true, C>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
     else
-        { sell_lanes_op_kernel<VT, XT, OP, false, C><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, false, C>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
 }
 
 template <typename VT, typename XT, int OP>
@@ -424,23 +468,23 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
         const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
         const int g = div_up(n, kThreads);
         if (A.sd && sh)
-            { sell_op_kernel<VT, XT, OP, true, true><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            { pdl_launch(sell_op_kernel<VT, XT, OP, true, true>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
         else if (A.sd)
-            { sell_op_kernel<VT, XT, OP, true, false><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            { pdl_launch(sell_op_kernel<VT, XT, OP, true, false>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
         else if (sh)
-            { sell_op_kernel<VT, XT, OP, false, true><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            { pdl_launch(sell_op_kernel<VT, XT, OP, false, true>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
         else
-            { sell_op_kernel<VT, XT, OP, false, false><<<g, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            { pdl_launch(sell_op_kernel<VT, XT, OP, false, false>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
     } else {
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);
         switch (T) {
-            case 1: { csr_op_kernel<VT, XT, 1, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
-            case 2: { csr_op_kernel<VT, XT, 2, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
-            case 4: { csr_op_kernel<VT, XT, 4, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
-            case 8: { csr_op_kernel<VT, XT, 8, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
-            case 16: { csr_op_kernel<VT, XT, 16, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
-            default: { csr_op_kernel<VT, XT, 32, OP><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 1: { pdl_launch(csr_op_kernel<VT, XT, 1, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 2: { pdl_launch(csr_op_kernel<VT, XT, 2, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 4: { pdl_launch(csr_op_kernel<VT, XT, 4, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 8: { pdl_launch(csr_op_kernel<VT, XT, 8, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            case 16: { pdl_launch(csr_op_kernel<VT, XT, 16, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
+            default: { pdl_launch(csr_op_kernel<VT, XT, 32, OP>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, b, dinv, x, o1, o2); ::amg::count_launch(); } break;
         }
     }
     AMG_CHECK_LAUNCH();
@@ -534,6 +578,7 @@ __device__ __forceinline__ void finish_rz(PcgScalars *sc, double rz, double zq) 
 template <int NV, int FIN>
 __global__ void __launch_bounds__(kFinThreads)
 finish_kernel(int nblocks, Reduce red, PcgScalars *sc, cudaGraphConditionalHandle handle, int use_handle) {
+    pdl_begin();
     __shared__ double sh[NV][kFinThreads / 32];
     double t[NV];
 #pragma unroll
@@ -589,7 +634,7 @@ finish_kernel(int nblocks, Reduce red, PcgScalars *sc, cudaGraphConditionalHandl
 template <int NV, int FIN>
 void launch_finish(int nblocks, Reduce red, PcgScalars *sc, cudaStream_t s,
                    cudaGraphConditionalHandle handle = cudaGraphConditionalHandle{}, bool use_handle = false) {
-    { finish_kernel<NV, FIN><<<1, kFinThreads, 0, s>>>(nblocks, red, sc, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
+    { pdl_launch(finish_kernel<NV, FIN>, 1, kFinThreads, 0, s, nblocks, red, sc, handle, use_handle ? 1 : 0); ::amg::count_launch(); }
 }
 
 // Grid of a reducing kernel: at most one resident wave, so every thread
@@ -610,6 +655,7 @@ static_assert(kThreads == 256, "two-level reduction assumes groups of 256 blocks
 // ---------------------------------------------------------------------------
 __global__ void p_update_kernel(int32_t n, const double *__restrict__ z, double *__restrict__ p,
                                 const PcgScalars *sc) {
+    pdl_begin();
     int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     p[i] = z[i] + sc->beta * p[i];
@@ -623,6 +669,7 @@ __global__ void __launch_bounds__(kThreads)
 ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                SellIdx ix, const double *__restrict__ sv, const double *__restrict__ p, const double *__restrict__ b,
                double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    pdl_begin();
     block_partials_begin();
     double part[1] = {0.0};
     const int lane = threadIdx.x & 31;
@@ -649,6 +696,7 @@ template <int T, bool PART = false>
 __global__ void __launch_bounds__(kThreads)
 ap_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
           const double *__restrict__ p, double *__restrict__ q, PcgScalars *sc, Reduce red, PartView pv = PartView()) {
+    pdl_begin();
     block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -678,6 +726,7 @@ __global__ void __launch_bounds__(kThreads)
 xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ x,
                  double *__restrict__ r, const PcgScalars *sc, Reduce red, const double *__restrict__ dinv0,
                  double *__restrict__ x0, double *__restrict__ xs) {
+    pdl_begin();
     block_partials_begin();
     const double alpha = sc->alpha;
     const bool step = alpha != 0.0;  // 0: breakdown -- x and r stay as they are
@@ -701,6 +750,7 @@ xr_update_kernel(int32_t n, const double *__restrict__ p, const double *__restri
 __global__ void __launch_bounds__(kThreads)
 rz_kernel(int32_t n, const double *__restrict__ r, const double *__restrict__ z, const double *__restrict__ q,
           PcgScalars *sc, Reduce red) {
+    pdl_begin();
     block_partials_begin();
     int first = sc->start;
     double part[2] = {0.0, 0.0};
@@ -717,6 +767,7 @@ __global__ void __launch_bounds__(kThreads)
 resid_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
              const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ t_out,
              PcgScalars *sc, Reduce red, PartView pv = PartView()) {
+    pdl_begin();
     block_partials_begin();
     double part[1] = {0.0};
     int64_t stride = (int64_t)gridDim.x * kThreads;
@@ -752,6 +803,7 @@ post_rz_csr_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__r
                    const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                    double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red,
                    PartView pv = PartView()) {
+    pdl_begin();
     block_partials_begin();
     double part[ZQ ? 2 : 1];
 #pragma unroll
@@ -789,6 +841,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
                     const int32_t *__restrict__ sw, SellIdx ix, const double *__restrict__ sv,
                     const double *__restrict__ x, const double *__restrict__ b, const double *__restrict__ dinv,
                     double *__restrict__ z, const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    pdl_begin();
     block_partials_begin();
     double part[ZQ ? 2 : 1];
 #pragma unroll
@@ -812,6 +865,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
 __global__ void __launch_bounds__(kThreads)
 to_f64_rz_kernel(int32_t n, const float *__restrict__ z32, double *__restrict__ z, const double *__restrict__ r,
                  const double *__restrict__ q, PcgScalars *sc, Reduce red) {
+    pdl_begin();
     block_partials_begin();
     double part[2] = {0.0, 0.0};
     for (int32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
@@ -825,12 +879,14 @@ to_f64_rz_kernel(int32_t n, const float *__restrict__ z32, double *__restrict__ 
 
 template <typename XT>
 __global__ void scale_kernel(int64_t n, const XT *__restrict__ a, const XT *__restrict__ d, XT *__restrict__ out) {
+    pdl_begin();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] * d[i];
 }
 
 __global__ void to_f32_scaled_kernel(int64_t n, const double *__restrict__ src, const float *__restrict__ d,
                                      float *__restrict__ dst, float *__restrict__ xdst) {
+    pdl_begin();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float v = (float)src[i];
@@ -843,6 +899,7 @@ __global__ void to_f32_scaled_kernel(int64_t n, const double *__restrict__ src, 
 // ---------------------------------------------------------------------------
 template <typename XT>
 __global__ void coarse_kernel(int32_t n, const double *__restrict__ inv, const XT *__restrict__ b, XT *__restrict__ x) {
+    pdl_begin();
     int lane = threadIdx.x & 31;
     int32_t row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (row >= n) return;
@@ -868,6 +925,7 @@ __global__ void convert_kernel<__nv_bfloat16>(const double *src, __nv_bfloat16 *
 
 template <typename XT>
 __global__ void to_f64_kernel(const XT *src, double *dst, int64_t n) {
+    pdl_begin();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (double)src[i];
 }
@@ -1006,19 +1064,19 @@ void residual_from_x(const CycMat<VT> &A, const XT *b, const XT *x, XT *r, cudaS
 template <typename XT>
 void coarse_solve(int32_t n, const double *inv, const XT *b, XT *x, cudaStream_t s) {
     if (n == 0) return;
-    { coarse_kernel<XT><<<div_up(n, 8), 256, 0, s>>>(n, inv, b, x); ::amg::count_launch(); }
+    { pdl_launch(coarse_kernel<XT>, div_up(n, 8), 256, 0, s, n, inv, b, x); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
 void pcg_p_update(int32_t n, const double *z, double *p, const PcgScalars *sc, cudaStream_t s) {
-    { p_update_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, z, p, sc); ::amg::count_launch(); }
+    { pdl_launch(p_update_kernel, div_up(n, kThreads), kThreads, 0, s, n, z, p, sc); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
 template <int T>
 static void launch_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc, Reduce red, cudaStream_t s) {
     int blocks = reduce_blocks((int64_t)A.nrows * T);
-    { ap_kernel<T><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, p, q, sc, red); ::amg::count_launch(); }
+    { pdl_launch(ap_kernel<T>, blocks, kThreads, 0, s, A.nrows, A.rp, A.ci, A.v, p, q, sc, red, PartView()); ::amg::count_launch(); }
     launch_finish<1, kFinAp>(blocks, red, sc, s);
 }
 
@@ -1030,13 +1088,13 @@ static int launch_ap_sell(const CycMat<double> &A, const double *p, const double
     const SellIdx ix{A.sci, A.sd};
     const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
     if (A.sd && sh)
-        { ap_sell_kernel<true, true, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+        { pdl_launch(ap_sell_kernel<true, true, RESID>, blocks, kThreads, 0, s, A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
     else if (A.sd)
-        { ap_sell_kernel<true, false, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+        { pdl_launch(ap_sell_kernel<true, false, RESID>, blocks, kThreads, 0, s, A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
     else if (sh)
-        { ap_sell_kernel<false, true, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+        { pdl_launch(ap_sell_kernel<false, true, RESID>, blocks, kThreads, 0, s, A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
     else
-        { ap_sell_kernel<false, false, RESID><<<blocks, kThreads, 0, s>>>(A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
+        { pdl_launch(ap_sell_kernel<false, false, RESID>, blocks, kThreads, 0, s, A.nrows, A.perm, A.soff, A.sw, ix, A.sv, p, b, q, sc, red); ::amg::count_launch(); }
     return blocks;
 }
 
@@ -1044,7 +1102,7 @@ void pcg_ap(const CycMat<double> &A, const double *p, double *q, PcgScalars *sc,
     if (A.part.parts) {  // row-partitioned: exchange, then the one-lane kernel's loop
         part_exchange(A.part, p, nullptr, s);
         const int blocks = reduce_blocks(A.nrows);
-        { ap_kernel<1, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.part.cext, A.v, p, q, sc, red, A.part); ::amg::count_launch(); }
+        { pdl_launch(ap_kernel<1, true>, blocks, kThreads, 0, s, A.nrows, A.rp, A.part.cext, A.v, p, q, sc, red, A.part); ::amg::count_launch(); }
         launch_finish<1, kFinAp>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -1070,7 +1128,7 @@ void pcg_xr_update(int32_t n, const double *p, const double *q, double *x, doubl
                    Reduce red, cudaGraphConditionalHandle handle, bool use_handle, const double *dinv0,
                    double *x0, double *xs, cudaStream_t s) {
     int blocks = reduce_blocks(n);
-    { xr_update_kernel<<<blocks, kThreads, 0, s>>>(n, p, q, x, r, sc, red, dinv0, x0, xs); ::amg::count_launch(); }
+    { pdl_launch(xr_update_kernel, blocks, kThreads, 0, s, n, p, q, x, r, sc, red, dinv0, x0, xs); ::amg::count_launch(); }
     launch_finish<1, kFinXr>(blocks, red, sc, s, handle, use_handle);
     AMG_CHECK_LAUNCH();
 }
@@ -1083,7 +1141,7 @@ static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, cons
     if (A.part.parts) {
         part_exchange(A.part, x, nullptr, s);
         const int blocks = reduce_blocks(n);
-        { post_rz_csr_kernel<1, ZQ, true><<<blocks, kThreads, 0, s>>>(n, A.rp, A.part.cext, A.v, x, b, dinv, z, q, sc, red, A.part); ::amg::count_launch(); }
+        { pdl_launch(post_rz_csr_kernel<1, ZQ, true>, blocks, kThreads, 0, s, n, A.rp, A.part.cext, A.v, x, b, dinv, z, q, sc, red, A.part); ::amg::count_launch(); }
         launch_finish<NV, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -1092,9 +1150,9 @@ static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, cons
         int blocks = reduce_blocks(n);
         const SellIdx ix{A.sci, A.sd};
         if (A.sd)
-            { post_rz_sell_kernel<true, ZQ><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+            { pdl_launch(post_rz_sell_kernel<true, ZQ>, blocks, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
         else
-            { post_rz_sell_kernel<false, ZQ><<<blocks, kThreads, 0, s>>>(n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
+            { pdl_launch(post_rz_sell_kernel<false, ZQ>, blocks, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, x, b, dinv, z, q, sc, red); ::amg::count_launch(); }
         launch_finish<NV, kFinRz>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -1102,12 +1160,12 @@ static void post_smooth_rz_launch(const CycMat<double> &A, const double *x, cons
     int T = threads_per_row(A.variant);
     int blocks = reduce_blocks((int64_t)n * T);
     switch (T) {
-        case 1: { post_rz_csr_kernel<1, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 2: { post_rz_csr_kernel<2, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 4: { post_rz_csr_kernel<4, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 8: { post_rz_csr_kernel<8, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        case 16: { post_rz_csr_kernel<16, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
-        default: { post_rz_csr_kernel<32, ZQ><<<blocks, kThreads, 0, s>>>(n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red); ::amg::count_launch(); } break;
+        case 1: { pdl_launch(post_rz_csr_kernel<1, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
+        case 2: { pdl_launch(post_rz_csr_kernel<2, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
+        case 4: { pdl_launch(post_rz_csr_kernel<4, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
+        case 8: { pdl_launch(post_rz_csr_kernel<8, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
+        case 16: { pdl_launch(post_rz_csr_kernel<16, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
+        default: { pdl_launch(post_rz_csr_kernel<32, ZQ>, blocks, kThreads, 0, s, n, A.rp, A.ci, A.v, x, b, dinv, z, q, sc, red, PartView()); ::amg::count_launch(); } break;
     }
     launch_finish<NV, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
@@ -1124,14 +1182,14 @@ bool post_smooth_rz(const CycMat<double> &A, const double *x, const double *b, c
 void to_f64_rz(int32_t n, const float *z32, double *z, const double *r, const double *q, PcgScalars *sc, Reduce red,
                cudaStream_t s) {
     int blocks = reduce_blocks(n);
-    { to_f64_rz_kernel<<<blocks, kThreads, 0, s>>>(n, z32, z, r, q, sc, red); ::amg::count_launch(); }
+    { pdl_launch(to_f64_rz_kernel, blocks, kThreads, 0, s, n, z32, z, r, q, sc, red); ::amg::count_launch(); }
     launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
 
 template <typename XT> void scale(int64_t n, const XT *a, const XT *d, XT *out, cudaStream_t s) {
     if (n <= 0) return;
-    { scale_kernel<XT><<<div_up(n, kThreads), kThreads, 0, s>>>(n, a, d, out); ::amg::count_launch(); }
+    { pdl_launch(scale_kernel<XT>, div_up(n, kThreads), kThreads, 0, s, n, a, d, out); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 template void scale<double>(int64_t, const double *, const double *, double *, cudaStream_t);
@@ -1139,14 +1197,14 @@ template void scale<float>(int64_t, const float *, const float *, float *, cudaS
 
 void to_f32_scaled(int64_t n, const double *src, const float *d, float *dst, float *xdst, cudaStream_t s) {
     if (n <= 0) return;
-    { to_f32_scaled_kernel<<<div_up(n, kThreads), kThreads, 0, s>>>(n, src, d, dst, xdst); ::amg::count_launch(); }
+    { pdl_launch(to_f32_scaled_kernel, div_up(n, kThreads), kThreads, 0, s, n, src, d, dst, xdst); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
 void pcg_rz(int32_t n, const double *r, const double *z, const double *q, PcgScalars *sc, Reduce red,
             cudaStream_t s) {
     int blocks = reduce_blocks(n);
-    { rz_kernel<<<blocks, kThreads, 0, s>>>(n, r, z, q, sc, red); ::amg::count_launch(); }
+    { pdl_launch(rz_kernel, blocks, kThreads, 0, s, n, r, z, q, sc, red); ::amg::count_launch(); }
     launch_finish<2, kFinRz>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
@@ -1156,7 +1214,7 @@ void true_residual(const CycMat<double> &A, const double *b, const double *x, do
     if (A.part.parts) {  // row-partitioned: the four-lane kernel's loop, as below
         part_exchange(A.part, x, nullptr, s);
         const int blocks = reduce_blocks((int64_t)A.nrows * 4);
-        { resid_kernel<4, true><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.part.cext, A.v, b, x, t, sc, red, A.part); ::amg::count_launch(); }
+        { pdl_launch(resid_kernel<4, true>, blocks, kThreads, 0, s, A.nrows, A.rp, A.part.cext, A.v, b, x, t, sc, red, A.part); ::amg::count_launch(); }
         launch_finish<1, kFinTt>(blocks, red, sc, s);
         AMG_CHECK_LAUNCH();
         return;
@@ -1168,7 +1226,7 @@ void true_residual(const CycMat<double> &A, const double *b, const double *x, do
         return;
     }
     int blocks = reduce_blocks((int64_t)A.nrows * 4);
-    { resid_kernel<4><<<blocks, kThreads, 0, s>>>(A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red); ::amg::count_launch(); }
+    { pdl_launch(resid_kernel<4>, blocks, kThreads, 0, s, A.nrows, A.rp, A.ci, A.v, b, x, t, sc, red, PartView()); ::amg::count_launch(); }
     launch_finish<1, kFinTt>(blocks, red, sc, s);
     AMG_CHECK_LAUNCH();
 }
@@ -1183,7 +1241,7 @@ template <typename XT> void convert_vec_from_f64(const double *src, XT *dst, int
 }
 template <typename XT> void convert_vec_to_f64(const XT *src, double *dst, int64_t n, cudaStream_t s) {
     if (n <= 0) return;
-    { to_f64_kernel<XT><<<div_up(n, kThreads), kThreads, 0, s>>>(src, dst, n); ::amg::count_launch(); }
+    { pdl_launch(to_f64_kernel<XT>, div_up(n, kThreads), kThreads, 0, s, src, dst, n); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
 }
 
