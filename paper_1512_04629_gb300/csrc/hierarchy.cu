@@ -128,6 +128,10 @@ class SetupPipeline {
     void level_ready(int l);      // level l and its P_l, R_l are formed (on the main stream)
     void coarsening_done(int nlev);
     void finish();                // joins; the main stream then waits for the second one
+    // R = P^T on a third stream (of the main stream's priority), beside A P
+    // on the main stream; wait_beside() orders the main stream after it
+    void transpose_beside(const DevCSR &P, DevCSR &R);
+    void wait_beside();
 
   private:
     void run();
@@ -144,6 +148,8 @@ class SetupPipeline {
     std::exception_ptr err_;
     std::vector<int> defer_relax_, defer_transfer_;
     cudaEvent_t done_ = nullptr;
+    cudaStream_t aux_ = nullptr;
+    cudaEvent_t ev_p_ = nullptr, ev_r_ = nullptr;
     std::thread th_;
 };
 
@@ -180,7 +186,8 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
         timed(h, 10, l, 0.0, s, [&] {
             setup::direct_interp(V.A, V.strong.as<uint8_t>(), V.cf.as<int8_t>(), V.cmap.as<int32_t>(),
                                  (int32_t)nc, V.P, s);
-            setup::transpose(V.P, V.R, s);
+            if (pipe) pipe->transpose_beside(V.P, V.R);  // R forms while A P does
+            else setup::transpose(V.P, V.R, s);
         });
         // A P is read twice (by R (A P) and the minimal pattern) and then
         // dropped: it stays in the product slots of its one-pass SpGEMM
@@ -188,6 +195,7 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
         auto C = std::make_unique<Level>();
         timed(h, 11, l, 0.0, s, [&] {
             setup::spgemm_slots(V.A, V.P, AP, s);
+            if (pipe) pipe->wait_beside();
             setup::spgemm(V.R, AP.rows, C->A, s);
         });
         timed(h, 12, l, 0.0, s, [&] {
@@ -773,24 +781,56 @@ SetupPipeline::SetupPipeline(Hierarchy &h, cudaStream_t main, const double *gamm
     : h_(h), main_(main), gamma_(gamma && n_gamma > 0 ? std::vector<double>(gamma, gamma + n_gamma)
                                                       : std::vector<double>()) {
     AMG_CUDA(cudaGetDevice(&device_));
+    int prio = 0;
+    AMG_CUDA(cudaStreamGetPriority(main_, &prio));
+    // every handle is released by the destructor, also when a later one fails
+    struct Undo {
+        SetupPipeline *p;
+        bool ok = false;
+        ~Undo() {
+            if (ok) return;
+            if (p->side_) cudaStreamDestroy(p->side_);
+            if (p->aux_) cudaStreamDestroy(p->aux_);
+            if (p->done_) cudaEventDestroy(p->done_);
+            if (p->ev_p_) cudaEventDestroy(p->ev_p_);
+            if (p->ev_r_) cudaEventDestroy(p->ev_r_);
+            cudaGetLastError();
+        }
+    } undo{this};
     AMG_CUDA(cudaStreamCreateWithFlags(&side_, cudaStreamNonBlocking));
-    if (cudaEventCreateWithFlags(&done_, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        cudaStreamDestroy(side_);
-        throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventCreate failed");
-    }
+    AMG_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, prio));
+    AMG_CUDA(cudaEventCreateWithFlags(&done_, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&ev_p_, cudaEventDisableTiming));
+    AMG_CUDA(cudaEventCreateWithFlags(&ev_r_, cudaEventDisableTiming));
     th_ = std::thread([this] { run(); });
+    undo.ok = true;
 }
+
+void SetupPipeline::transpose_beside(const DevCSR &P, DevCSR &R) {
+    AMG_CUDA(cudaEventRecord(ev_p_, main_));
+    AMG_CUDA(cudaStreamWaitEvent(aux_, ev_p_, 0));
+    {
+        AllocOn alloc_scope(aux_);  // R's buffers are ordered on the stream that fills them
+        setup::transpose(P, R, aux_);
+    }
+    AMG_CUDA(cudaEventRecord(ev_r_, aux_));
+}
+
+void SetupPipeline::wait_beside() { AMG_CUDA(cudaStreamWaitEvent(main_, ev_r_, 0)); }
 
 SetupPipeline::~SetupPipeline() {
     cancel();
     // work already issued on the second stream finishes before the levels it
     // writes can be released
     cudaStreamSynchronize(side_);
+    cudaStreamSynchronize(aux_);
     cudaGetLastError();
     for (cudaEvent_t e : ev_) cudaEventDestroy(e);
     cudaEventDestroy(done_);
+    cudaEventDestroy(ev_p_);
+    cudaEventDestroy(ev_r_);
     cudaStreamDestroy(side_);
+    cudaStreamDestroy(aux_);
 }
 
 void SetupPipeline::cancel() {
