@@ -132,6 +132,9 @@ class SetupPipeline {
     // on the main stream; wait_beside() orders the main stream after it
     void transpose_beside(const DevCSR &P, DevCSR &R);
     void wait_beside();
+    // the minimal pattern of the new level C on the third stream; A P's
+    // buffers are released there once it is done
+    void minimal_pattern_beside(Level &C, setup::SlotProduct &AP, const int32_t *cpts);
 
   private:
     void run();
@@ -143,6 +146,7 @@ class SetupPipeline {
     std::mutex mu_;
     std::condition_variable cv_;
     std::vector<cudaEvent_t> ev_;  // ev_[l]: level l is ready; the last one also marks the end of coarsening
+    std::vector<cudaEvent_t> evx_;  // evx_[l]: the third stream's work up to level l's readiness
     int nready_ = 0, nlev_ = -1;
     bool stop_ = false;
     std::exception_ptr err_;
@@ -201,7 +205,12 @@ void build_galerkin(Hierarchy &h, const DevCSR &A0in, cudaStream_t s, const doub
         timed(h, 12, l, 0.0, s, [&] {
             init_level_maps(*C, s, false);  // R (A P) of a checked A_l
             C->inM.alloc(C->A.nnz + kPad);
-            setup::minimal_pattern(C->A, AP.rows, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s, C->tpos.as<int32_t>());
+            if (pipe) {  // only the sparsification reads M: off the coarsening's path, with A P freed there
+                pipe->minimal_pattern_beside(*C, AP, V.cpts.as<int32_t>());
+            } else {
+                setup::minimal_pattern(C->A, AP.rows, V.cpts.as<int32_t>(), C->inM.as<uint8_t>(), s,
+                                       C->tpos.as<int32_t>());
+            }
         });
         if (nongal) {
             const double g = (n_gamma > 0 && gamma) ? gamma[std::min(l + 1, n_gamma - 1)] : 0.0;
@@ -818,6 +827,14 @@ void SetupPipeline::transpose_beside(const DevCSR &P, DevCSR &R) {
 
 void SetupPipeline::wait_beside() { AMG_CUDA(cudaStreamWaitEvent(main_, ev_r_, 0)); }
 
+void SetupPipeline::minimal_pattern_beside(Level &C, setup::SlotProduct &AP, const int32_t *cpts) {
+    AMG_CUDA(cudaEventRecord(ev_p_, main_));  // R (A P), the level maps and M's buffer
+    AMG_CUDA(cudaStreamWaitEvent(aux_, ev_p_, 0));
+    setup::minimal_pattern(C.A, AP.rows, cpts, C.inM.as<uint8_t>(), aux_, C.tpos.as<int32_t>());
+    // A P's slot buffers go back to the pool in the third stream's order, after M has read them
+    for (TmpBuf *b : {&AP.ci, &AP.v, &AP.beg, &AP.end}) b->stream = aux_;
+}
+
 SetupPipeline::~SetupPipeline() {
     cancel();
     // work already issued on the second stream finishes before the levels it
@@ -826,6 +843,7 @@ SetupPipeline::~SetupPipeline() {
     cudaStreamSynchronize(aux_);
     cudaGetLastError();
     for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+    for (cudaEvent_t e : evx_) cudaEventDestroy(e);
     cudaEventDestroy(done_);
     cudaEventDestroy(ev_p_);
     cudaEventDestroy(ev_r_);
@@ -842,33 +860,47 @@ void SetupPipeline::cancel() {
     if (th_.joinable()) th_.join();
 }
 
-void SetupPipeline::level_ready(int l) {
+// An event recorded now on stream s (appended to `to` under the lock by the caller).
+static cudaEvent_t record_now(cudaStream_t s) {
     cudaEvent_t e;
     AMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    if (cudaEventRecord(e, main_) != cudaSuccess) {
+    if (cudaEventRecord(e, s) != cudaSuccess) {
         cudaGetLastError();
         cudaEventDestroy(e);
         throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventRecord failed");
     }
+    return e;
+}
+
+void SetupPipeline::level_ready(int l) {
+    cudaEvent_t e = record_now(main_), x = nullptr;
+    try {
+        x = record_now(aux_);
+    } catch (...) {
+        cudaEventDestroy(e);
+        throw;
+    }
     {
         std::lock_guard<std::mutex> lk(mu_);
         ev_.push_back(e);
+        evx_.push_back(x);
         nready_ = l + 1;
     }
     cv_.notify_all();
 }
 
 void SetupPipeline::coarsening_done(int nlev) {
-    cudaEvent_t e;
-    AMG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    if (cudaEventRecord(e, main_) != cudaSuccess) {
-        cudaGetLastError();
+    cudaEvent_t e = record_now(main_), x = nullptr;
+    try {
+        x = record_now(aux_);
+    } catch (...) {
         cudaEventDestroy(e);
-        throw Error(AMG_ERR_CUDA, "setup pipeline: cudaEventRecord failed");
+        throw;
     }
     {
         std::lock_guard<std::mutex> lk(mu_);
         ev_.push_back(e);
+        evx_.push_back(x);
         nlev_ = nlev;
     }
     cv_.notify_all();
@@ -883,7 +915,7 @@ void SetupPipeline::run() {
         const bool tune_transfers = o.transfer_variant == AMG_SPMV_AUTO && o.spmv_variant == AMG_SPMV_AUTO;
         for (int l = 0;; ++l) {
             bool has_p = false, last = false;
-            cudaEvent_t e = nullptr;
+            cudaEvent_t e = nullptr, x = nullptr;
             {
                 std::unique_lock<std::mutex> lk(mu_);
                 cv_.wait(lk, [&] { return stop_ || nready_ > l || nlev_ >= 0; });
@@ -891,14 +923,17 @@ void SetupPipeline::run() {
                 if (nready_ > l) {
                     has_p = true;
                     e = ev_[l];
+                    x = evx_[l];
                 } else {
                     if (l >= nlev_) break;
                     last = l == nlev_ - 1;
                     has_p = !last;
                     e = ev_.back();
+                    x = evx_.back();
                 }
             }
             AMG_CUDA(cudaStreamWaitEvent(side_, e, 0));
+            AMG_CUDA(cudaStreamWaitEvent(side_, x, 0));  // the level's minimal pattern
             Level &V = *h_.lev[l];
             V.gamma = level_gamma(gamma_.data(), (int)gamma_.size(), l);
             resparsify_one(h_, V, l, side_);
