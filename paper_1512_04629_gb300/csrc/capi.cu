@@ -69,22 +69,20 @@ void upload_csr(const amg_csr *A, DevCSR &M, cudaStream_t s) {
     int64_t nc = A->ncols > 0 ? A->ncols : A->n;
     M.allocate((int32_t)A->n, (int32_t)nc, A->nnz);
     cudaMemcpyKind k = A->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // the row pointers' order, column range and finite values are checked on
-    // the device (level_maps / validate_rect) before any kernel follows them
+    // the row pointers' order and ends (rowptr[0] = 0, rowptr[n] = nnz), the
+    // column range and finite values are checked on the device (level_maps /
+    // validate_rect) before any kernel follows them; host arrays are checked
+    // here as well, for the message
     if (!A->on_device)
         require(A->rowptr[0] == 0 && A->rowptr[A->n] == A->nnz, "rowptr[0] must be 0 and rowptr[n] = nnz");
+    require(A->n > 0 || A->nnz == 0, "a matrix without rows holds no entries (rowptr[n] = nnz)");
     AMG_CUDA(cudaMemcpyAsync(M.rowptr.ptr, A->rowptr, sizeof(int32_t) * (A->n + 1), k, s));
-    AMG_CUDA(cudaMemsetAsync(M.col.ptr, 0, M.col.bytes, s));
-    AMG_CUDA(cudaMemsetAsync(M.val.ptr, 0, M.val.bytes, s));
+    // only the padding past nnz needs zeros: the copies fill the rest
+    AMG_CUDA(cudaMemsetAsync(M.ci() + A->nnz, 0, M.col.bytes - sizeof(int32_t) * A->nnz, s));
+    AMG_CUDA(cudaMemsetAsync(M.v() + A->nnz, 0, M.val.bytes - sizeof(double) * A->nnz, s));
     if (A->nnz > 0) {
         AMG_CUDA(cudaMemcpyAsync(M.col.ptr, A->col, sizeof(int32_t) * A->nnz, k, s));
         AMG_CUDA(cudaMemcpyAsync(M.val.ptr, A->val, sizeof(double) * A->nnz, k, s));
-    }
-    if (A->on_device) {
-        int32_t ends[2];
-        read_back(&ends[0], M.rp(), sizeof(int32_t), s);
-        read_back(&ends[1], M.rp() + A->n, sizeof(int32_t), s);
-        require(ends[0] == 0 && ends[1] == A->nnz, "rowptr[0] must be 0 and rowptr[n] = nnz");
     }
 }
 
