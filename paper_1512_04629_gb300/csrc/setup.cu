@@ -11,6 +11,7 @@
 #include <type_traits>
 #include <climits>
 #include <cstdlib>
+#include <cstring>
 
 #include "common.cuh"
 #include "setup_ops.cuh"
@@ -323,7 +324,7 @@ __global__ void pmis_select_kernel(const int32_t *list, const int *len, int32_t 
 template <int T, bool DENSE>
 __global__ void pmis_apply_kernel(const int32_t *list, const int *len, int32_t n, const int32_t *rp,
                                   const int32_t *ci, const uint8_t *strong, const uint8_t *newc, int8_t *state,
-                                  int32_t *next, int *next_len) {
+                                  int32_t *next, int *next_len, int *ccount) {
     const int m = DENSE ? n : *len;  // the same for the whole grid
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g - threadIdx.x < (int64_t)m * T;
@@ -360,6 +361,8 @@ __global__ void pmis_apply_kernel(const int32_t *list, const int *len, int32_t n
             if (c) state[i] = kC;
             else if (f) state[i] = kF;
         }
+        const int cb = __syncthreads_count(live && t == 0 && c);  // the block's new C points
+        if (threadIdx.x == 0 && cb) atomicAdd(ccount, cb);
         block_append(und && t == 0 && !f, i, next, next_len);
     }
 }
@@ -1975,11 +1978,13 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     // eight rounds per read-back: the levels of the test problems finish
     // within one batch, and a round whose list is empty costs one short launch
     constexpr int kBatch = 8, kMaxRounds = 10000;
-    // cnt[0]: undecided after the initial split; cnt[r]: after round r; the
-    // undecided rows alternate between two lists
-    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 1), s), sym(A.nnz + 1, s),
+    // cnt[0]: C points so far; dc = cnt + 1: dc[0] undecided after the
+    // initial split, dc[r] after round r (the first batch reads the C count
+    // with the round counts); the undecided rows alternate between two lists
+    TmpBuf w(sizeof(double) * n, s), newc(n, s), cnt(sizeof(int) * (kMaxRounds + 2), s), sym(A.nnz + 1, s),
         lists(sizeof(int32_t) * 2 * (size_t)n, s);
-    int *dc = cnt.as<int>();
+    int *ccount = cnt.as<int>();
+    int *dc = ccount + 1;
     int32_t *list[2] = {lists.as<int32_t>(), lists.as<int32_t>() + n};
     int g = div_up(n, kThreads);
     const int T = row_lanes(A, 8);
@@ -1995,6 +2000,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     int done = 0;   // rounds launched
     int last = n;   // bound on the list length at the start of the batch
     bool first = true;
+    int64_t nc = -1;  // C points, when the first batch finished the split
     while (true) {
         if (done + kBatch > kMaxRounds) throw Error(AMG_ERR_CUDA, "PMIS did not terminate");
         const int64_t bound = std::max(last, 1);
@@ -2010,7 +2016,7 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
                         cur, dc + r - 1, n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(), cf, newc.as<uint8_t>());
                     ::amg::count_launch();
                     pmis_apply_kernel<L, true><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, n, A.rp(), A.ci(), strong,
-                                                                       newc.as<uint8_t>(), cf, nxt, dc + r);
+                                                                       newc.as<uint8_t>(), cf, nxt, dc + r, ccount);
                     ::amg::count_launch();
                     return;
                 }
@@ -2019,13 +2025,21 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
                     cur, dc + r - 1, n, A.rp(), A.ci(), sym.as<uint8_t>(), w.as<double>(), cf, newc.as<uint8_t>());
                 ::amg::count_launch();
                 pmis_apply_kernel<L, false><<<gl, kThreads, 0, s>>>(cur, dc + r - 1, n, A.rp(), A.ci(), strong,
-                                                                    newc.as<uint8_t>(), cf, nxt, dc + r);
+                                                                    newc.as<uint8_t>(), cf, nxt, dc + r, ccount);
                 ::amg::count_launch();
             });
         }
         AMG_CHECK_LAUNCH();
         int hc[kBatch + 1];
-        read_back(hc, dc + done, sizeof(hc), s);
+        if (first) {  // the C count comes with the first batch (usually the only one)
+            int hb[kBatch + 2];
+            read_back(hb, ccount, sizeof(hb), s);
+            nc = hb[0];
+            std::memcpy(hc, hb + 1, sizeof(hc));
+        } else {
+            read_back(hc, dc + done, sizeof(hc), s);
+            nc = -1;
+        }
         if (!first && hc[0] != last) throw Error(AMG_ERR_CUDA, "PMIS counters inconsistent");
         // every round that started with undecided points must have decided some
         for (int b = 0; b < kBatch; ++b)
@@ -2038,7 +2052,9 @@ int64_t pmis(const DevCSR &A, const uint8_t *strong, const int32_t *tpos, uint64
     TmpBuf flag(sizeof(int32_t) * n, s);
     { is_c_kernel<<<g, kThreads, 0, s>>>(n, cf, flag.as<int32_t>()); ::amg::count_launch(); }
     AMG_CHECK_LAUNCH();
-    return exclusive_scan_i32(flag.as<int32_t>(), cmap, n, s);
+    if (nc < 0) return exclusive_scan_i32(flag.as<int32_t>(), cmap, n, s);  // more than one batch
+    exclusive_scan_i32_known(flag.as<int32_t>(), cmap, n, s);  // its total is the C count read back
+    return nc;
 }
 
 void coarse_points(const int8_t *cf, int32_t n, int32_t *cmap, int32_t *cpts, cudaStream_t s) {
