@@ -1024,17 +1024,24 @@ __device__ __forceinline__ void warp_emit_sorted(AccTab<U> &t, int32_t u, uint32
     }
 }
 
-template <int U, bool NUMERIC>
+// CAP: a row with more products than the table's distinct capacity U, in
+// the table sized for U; the distinct columns are counted after every round
+// of at most 32 insertions, and a row that passes U (the table, of 2 U
+// slots, then holds at most U + 32 keys, so probing always ends) is given up
+// with -1 for the larger-table kernels.  Rows that fit are formed exactly as
+// by the unbounded path.
+template <int U, bool NUMERIC, bool CAP = false>
 __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__ arp, const int32_t *__restrict__ aci,
                                 const double *__restrict__ av, const int32_t *__restrict__ bbeg, const int32_t *__restrict__ bend,
                                 const int32_t *__restrict__ bci, const double *__restrict__ bv, AccTab<U> &t,
                                 int64_t ub, const int64_t *__restrict__ obase, int32_t *__restrict__ cci,
                                 double *__restrict__ cv) {
-    const int32_t hs = row_slots(ub, AccTab<U>::kSlots);
+    const int32_t hs = CAP ? AccTab<U>::kSlots : row_slots(ub, AccTab<U>::kSlots);
     const uint32_t mask = (uint32_t)hs - 1;
     for (int32_t s = lane; s < hs; s += 32) t.keys[s] = -1;
     __syncwarp();
     const int32_t p0 = arp[i], nA = arp[i + 1] - p0;
+    int32_t tot = 0;  // CAP: distinct columns so far (the same in every lane)
     // Long rows of B (12 or more products per entry of A's row on average):
     // one round per k, the lanes covering B_k -- columns within a round are
     // distinct, so no matching is needed and rounds follow k's order.  Only
@@ -1060,10 +1067,10 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
                 const double ka = __shfl_sync(kFull, a, kk);
                 for (int32_t e0 = 0; e0 < klen; e0 += 32) {
                     const int32_t e = e0 + lane;
+                    bool fresh = false;
                     if (e < klen) {
                         const int32_t j = bci[kb0 + e];
                         uint32_t sl = hash32(j) & mask;
-                        bool fresh = false;
                         while (true) {
                             const int32_t old = atomicCAS(&t.keys[sl], -1, j);
                             if (old == -1) { fresh = true; break; }
@@ -1077,6 +1084,10 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
                         }
                     }
                     __syncwarp();
+                    if (CAP) {
+                        tot += __popc(__ballot_sync(kFull, fresh));
+                        if (tot > U) return -1;
+                    }
                 }
             }
             continue;
@@ -1143,6 +1154,10 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
                 if (leader) t.val[slot] = acc;
             }
             __syncwarp();
+            if (CAP) {
+                tot += __popc(__ballot_sync(kFull, fresh));
+                if (tot > U) return -1;
+            }
         }
     }
 #pragma unroll
@@ -1197,11 +1212,17 @@ __device__ int32_t warp_row_acc(int32_t i, int lane, const int32_t *__restrict__
 #ifndef AMG_ACC_MIN_BLOCKS
 #define AMG_ACC_MIN_BLOCKS 6
 #endif
-template <int U, int WARPS, bool NUMERIC>
+// CAP: rows of more than U products whose distinct columns fit the table;
+// a row that does not fit is appended to `ovf` (count in *novf) for the
+// larger-table kernels.  nrows_dev, when given, holds the row count (a list
+// whose length is known on the device only).
+template <int U, int WARPS, bool NUMERIC, bool CAP = false>
 __global__ void __launch_bounds__(WARPS * 32, U <= 128 ? AMG_ACC_MIN_BLOCKS : 1)
 spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                   const double *av, const int32_t *bbeg, const int32_t *bend, const int32_t *bci, const double *bv,
-                  int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub) {
+                  int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub,
+                  int32_t *ovf = nullptr, int32_t *novf = nullptr, const int32_t *nrows_dev = nullptr) {
+    if (nrows_dev) nrows = *nrows_dev;
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     AccTab<U> t(smem + (size_t)w * AccTab<U>::kBytes);
@@ -1216,8 +1237,11 @@ spgemm_acc_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const 
             i_nx = rows[r + step];
             ub_nx = ub[i_nx];
         }
-        const int32_t u = warp_row_acc<U, NUMERIC>(i, lane, arp, aci, av, bbeg, bend, bci, bv, t, ubi, obase, cci, cv);
-        if (lane == 0) cnt[i] = u;
+        const int32_t u = warp_row_acc<U, NUMERIC, CAP>(i, lane, arp, aci, av, bbeg, bend, bci, bv, t, ubi, obase, cci, cv);
+        if (lane == 0) {
+            if (CAP && u < 0) ovf[atomicAdd(novf, 1)] = i;
+            else cnt[i] = u;
+        }
     }
 }
 
@@ -1226,7 +1250,8 @@ __global__ void __launch_bounds__(kBlockThreads)
 spgemm_block_kernel(const int32_t *rows, int32_t nrows, const int32_t *arp, const int32_t *aci,
                     const double *av, const int32_t *bbeg, const int32_t *bend, const int32_t *bci, const double *bv,
                     int32_t *cnt, const int64_t *obase, int32_t *cci, double *cv, const int64_t *ub,
-                    unsigned char *gscratch, int32_t ghs, int32_t gumax) {
+                    unsigned char *gscratch, int32_t ghs, int32_t gumax, const int32_t *nrows_dev = nullptr) {
+    if (nrows_dev) nrows = *nrows_dev;  // the same for the whole grid
     extern __shared__ __align__(16) unsigned char smem[];
     RowTables t;
     unsigned char *base;
@@ -2189,6 +2214,8 @@ static void spgemm_impl(const DevCSR &A, const SpRows &B, DevCSR &Cm, SlotProduc
     if (dev >= 64 || !attrs[dev].load()) {
         AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
+        AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU0, kAccWarps0, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc0_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU1, kAccWarps1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc1_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_acc_kernel<kAccU1, kAccWarps1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)acc1_smem));
         AMG_CUDA(cudaFuncSetAttribute(spgemm_block_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_smem));
@@ -2238,25 +2265,49 @@ static void spgemm_impl(const DevCSR &A, const SpRows &B, DevCSR &Cm, SlotProduc
                 { spgemm_acc_kernel<kAccU0, kAccWarps0, false><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
                     rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
-        if (nb[4] > 0) {
-            const int blocks = std::min(div_up(nb[4], kAccWarps1), 152 * 16);
-            if (numeric)
-                { spgemm_acc_kernel<kAccU1, kAccWarps1, true><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
-                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
-            else
-                { spgemm_acc_kernel<kAccU1, kAccWarps1, false><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
-                    rows_of(4), nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
-        }
-        if (nb[5] > 0) {
-            const int blocks = std::min(nb[5], 152 * 4);
-            if (numeric)
-                { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
-                    ubp, nullptr, 0, 0); ::amg::count_launch(); }
-            else
-                { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
-                    rows_of(5), nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
-                    ubp, nullptr, 0, 0); ::amg::count_launch(); }
+        // rows of 129..4096 products: first in the small table (a warp per
+        // row, a full SM of warps -- the distinct columns of such rows are
+        // usually far fewer than their products); the rows whose distinct
+        // columns pass 128 go on to their bin's larger table
+        if (nb[4] > 0 || nb[5] > 0) {
+            TmpBuf ovf(sizeof(int32_t) * ((size_t)nb[4] + nb[5] + 1), s), novf(2 * sizeof(int32_t), s);
+            int32_t *ovf4 = ovf.as<int32_t>(), *ovf5 = ovf4 + nb[4], *nov = novf.as<int32_t>();
+            AMG_CUDA(cudaMemsetAsync(nov, 0, 2 * sizeof(int32_t), s));
+            for (int bin : {4, 5}) {
+                if (nb[bin] == 0) continue;
+                int32_t *list = bin == 4 ? ovf4 : ovf5;
+                const int blocks = std::min(div_up(nb[bin], kAccWarps0), 152 * 16);
+                if (numeric)
+                    { spgemm_acc_kernel<kAccU0, kAccWarps0, true, true><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
+                        rows_of(bin), nb[bin], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp,
+                        list, nov + (bin - 4)); ::amg::count_launch(); }
+                else
+                    { spgemm_acc_kernel<kAccU0, kAccWarps0, false, true><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
+                        rows_of(bin), nb[bin], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp,
+                        list, nov + (bin - 4)); ::amg::count_launch(); }
+            }
+            if (nb[4] > 0) {
+                const int blocks = std::min(div_up(nb[4], kAccWarps1), 152 * 16);
+                if (numeric)
+                    { spgemm_acc_kernel<kAccU1, kAccWarps1, true><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
+                        ovf4, nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp,
+                        nullptr, nullptr, nov); ::amg::count_launch(); }
+                else
+                    { spgemm_acc_kernel<kAccU1, kAccWarps1, false><<<blocks, kAccWarps1 * 32, acc1_smem, s>>>(
+                        ovf4, nb[4], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp,
+                        nullptr, nullptr, nov); ::amg::count_launch(); }
+            }
+            if (nb[5] > 0) {
+                const int blocks = std::min(nb[5], 152 * 4);
+                if (numeric)
+                    { spgemm_block_kernel<true><<<blocks, kBlockThreads, block_smem, s>>>(
+                        ovf5, nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
+                        ubp, nullptr, 0, 0, nov + 1); ::amg::count_launch(); }
+                else
+                    { spgemm_block_kernel<false><<<blocks, kBlockThreads, block_smem, s>>>(
+                        ovf5, nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
+                        ubp, nullptr, 0, 0, nov + 1); ::amg::count_launch(); }
+            }
         }
         if (nb[6] > 0) {
             if (numeric)
