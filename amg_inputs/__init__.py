@@ -274,6 +274,50 @@ def rotated_aniso_q1(N: int, theta: float = np.pi / 8, eps: float = 1e-3) -> CSR
     return _assemble(n, cols, vals, f"rotated_aniso_q1_{N}")
 
 
+def _laplacian_from_edges(n: int, ei: np.ndarray, ej: np.ndarray) -> CSR:
+    """Graph Laplacian of an undirected edge list (unit weights, each edge
+    once) shifted by 0.5 on the diagonal: off-diagonals -1, diagonal
+    degree + 0.5 (a strictly diagonally dominant M-matrix)."""
+    r = np.concatenate([ei, ej, np.arange(n)])
+    c = np.concatenate([ej, ei, np.arange(n)])
+    deg = np.bincount(np.concatenate([ei, ej]), minlength=n).astype(np.float64)
+    v = np.concatenate([-np.ones(2 * len(ei)), deg + 0.5])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rowptr[1:])
+    return CSR(n, rowptr.astype(np.int32), c.astype(np.int32), v.astype(np.float64))
+
+
+def hub_graphs() -> CSR:
+    """Block-diagonal union of four shifted graph Laplacians with very long
+    rows, for the product-heavy and column-heavy rows of the setup's sparse
+    products (2598 unknowns): complete bipartite graphs K(50, 100) and
+    K(130, 140), a 40 x 40 grid whose extra hub node links to every 5th grid
+    node, and a 24 x 24 grid whose hub links to every 3rd node."""
+    ei, ej, off = [], [], 0
+
+    def add(a, b):
+        ei.append(np.asarray(a, dtype=np.int64) + off)
+        ej.append(np.asarray(b, dtype=np.int64) + off)
+
+    for s, L in ((50, 100), (130, 140)):
+        a, b = np.meshgrid(np.arange(s), s + np.arange(L), indexing="ij")
+        add(a.ravel(), b.ravel())
+        off += s + L
+    for N, step in ((40, 5), (24, 3)):
+        i = np.arange(N * N)
+        x, y = i % N, i // N
+        add(i[x < N - 1], i[x < N - 1] + 1)
+        add(i[y < N - 1], i[y < N - 1] + N)
+        links = np.arange(0, N * N, step)
+        add(np.full(len(links), N * N), links)
+        off += N * N + 1
+    A = _laplacian_from_edges(off, np.concatenate(ei), np.concatenate(ej))
+    A.name = "hub_graphs"
+    return A
+
+
 def generate(kind: str, N: int, seed: int = 3) -> CSR:
     """Dispatch by stencil name."""
     if kind == "2d5":
@@ -288,4 +332,6 @@ def generate(kind: str, N: int, seed: int = 3) -> CSR:
         return fv7_lognormal(N, seed)
     if kind == "aniso":
         return rotated_aniso_q1(N)
+    if kind == "hubs":
+        return hub_graphs()
     raise ValueError(f"unknown stencil {kind!r}")

@@ -2265,17 +2265,17 @@ static void spgemm_impl(const DevCSR &A, const SpRows &B, DevCSR &Cm, SlotProduc
                 { spgemm_acc_kernel<kAccU0, kAccWarps0, false><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
                     rows_of(3), nb[3], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv, ubp); ::amg::count_launch(); }
         }
-        // rows of 129..4096 products: first in the small table (a warp per
+        // rows of more than 128 products: first in the small table (a warp per
         // row, a full SM of warps -- the distinct columns of such rows are
         // usually far fewer than their products); the rows whose distinct
         // columns pass 128 go on to their bin's larger table
-        if (nb[4] > 0 || nb[5] > 0) {
-            TmpBuf ovf(sizeof(int32_t) * ((size_t)nb[4] + nb[5] + 1), s), novf(2 * sizeof(int32_t), s);
-            int32_t *ovf4 = ovf.as<int32_t>(), *ovf5 = ovf4 + nb[4], *nov = novf.as<int32_t>();
-            AMG_CUDA(cudaMemsetAsync(nov, 0, 2 * sizeof(int32_t), s));
-            for (int bin : {4, 5}) {
+        if (nb[4] > 0 || nb[5] > 0 || nb[6] > 0) {
+            TmpBuf ovf(sizeof(int32_t) * ((size_t)nb[4] + nb[5] + nb[6] + 1), s), novf(3 * sizeof(int32_t), s);
+            int32_t *ovf4 = ovf.as<int32_t>(), *ovf5 = ovf4 + nb[4], *ovf6 = ovf5 + nb[5], *nov = novf.as<int32_t>();
+            AMG_CUDA(cudaMemsetAsync(nov, 0, 3 * sizeof(int32_t), s));
+            for (int bin : {4, 5, 6}) {
                 if (nb[bin] == 0) continue;
-                int32_t *list = bin == 4 ? ovf4 : ovf5;
+                int32_t *list = bin == 4 ? ovf4 : (bin == 5 ? ovf5 : ovf6);
                 const int blocks = std::min(div_up(nb[bin], kAccWarps0), 152 * 16);
                 if (numeric)
                     { spgemm_acc_kernel<kAccU0, kAccWarps0, true, true><<<blocks, kAccWarps0 * 32, acc0_smem, s>>>(
@@ -2308,16 +2308,16 @@ static void spgemm_impl(const DevCSR &A, const SpRows &B, DevCSR &Cm, SlotProduc
                         ovf5, nb[5], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
                         ubp, nullptr, 0, 0, nov + 1); ::amg::count_launch(); }
             }
-        }
-        if (nb[6] > 0) {
-            if (numeric)
-                { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
-                    ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
-            else
-                { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
-                    rows_of(6), nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
-                    ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax); ::amg::count_launch(); }
+            if (nb[6] > 0) {
+                if (numeric)
+                    { spgemm_block_kernel<true><<<gblocks, kBlockThreads, 0, s>>>(
+                        ovf6, nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
+                        ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax, nov + 2); ::amg::count_launch(); }
+                else
+                    { spgemm_block_kernel<false><<<gblocks, kBlockThreads, 0, s>>>(
+                        ovf6, nb[6], A.rp(), A.ci(), A.v(), B.beg, B.end, B.ci, B.v, cp, ob, cc, cvv,
+                        ubp, gscr.as<unsigned char>(), (int32_t)ghs, (int32_t)gumax, nov + 2); ::amg::count_launch(); }
+            }
         }
         AMG_CHECK_LAUNCH();
     };

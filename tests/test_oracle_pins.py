@@ -74,7 +74,7 @@ def test_poisson3d_eigenvalues(N):
 
 def test_generators_structure():
     for A in [gen.poisson2d_5pt(7), gen.poisson3d_7pt(5), gen.poisson3d_27pt(4),
-              gen.fv7_lognormal(5, seed=3), gen.q1_laplace3d(4)]:
+              gen.fv7_lognormal(5, seed=3), gen.q1_laplace3d(4), gen.hub_graphs()]:
         S = A.to_scipy()
         assert abs(S - S.T).max() < 1e-15
         for i in range(A.n):
@@ -87,6 +87,9 @@ def test_generators_structure():
     assert gen.poisson2d_5pt(N).nnz == 5 * N * N - 4 * N
     assert gen.poisson3d_7pt(N).nnz == 7 * N ** 3 - 6 * N ** 2
     assert gen.poisson3d_27pt(4).nnz == (3 * 4 - 2) ** 3
+    # hub graphs: 2 (50*100 + 130*140) bipartite, 2 (2*39*40 + 320) and
+    # 2 (2*23*24 + 192) grid and hub off-diagonals, plus the diagonal
+    assert gen.hub_graphs().nnz == 2 * (5000 + 18200 + 3120 + 320 + 1104 + 192) + 2598
 
 
 def test_spmv_matches_dense():
