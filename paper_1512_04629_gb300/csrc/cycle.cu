@@ -390,6 +390,23 @@ sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t 
     if (valid) {
         const int32_t nk = w / T;  // entries of this lane
         int32_t k = 0;
+        if ((OP == kSpmvAdd || OP == kSpmvScale) && nk <= kShortMax) {
+            // transfers: a lane's part of a row is short, so all of it loads
+            // first (nk is the same for the whole warp), rather than one
+            // load -> gather round trip per entry in the tail loop
+            switch (nk) {
+                case 1: acc = sell_short_sum<1, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 2: acc = sell_short_sum<2, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 3: acc = sell_short_sum<3, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 4: acc = sell_short_sum<4, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 5: acc = sell_short_sum<5, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 6: acc = sell_short_sum<6, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 7: acc = sell_short_sum<7, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 8: acc = sell_short_sum<8, VT, XT, D16>(off, i, ix, sv, gather); break;
+                default: break;
+            }
+            k = nk;
+        }
         for (; k + U <= nk; k += U) {
             VT v[U];
             int32_t c[U];
