@@ -133,10 +133,20 @@ struct SellIdx {
     const int32_t *col;
     const int16_t *delta;
 };
-template <bool D16>
+// a read-only load; CS: with the evict-first (streaming) policy, for the
+// level-0 operators, which are read once per pass and larger than L2, so
+// that they do not push the coarse levels out of it
+template <bool CS, typename T> __device__ __forceinline__ T ld_ro(const T *p) {
+    if constexpr (CS && (std::is_same<T, double>::value || std::is_same<T, float>::value ||
+                         std::is_same<T, int32_t>::value || std::is_same<T, int16_t>::value))
+        return __ldcs(p);
+    else
+        return __ldg(p);
+}
+template <bool D16, bool CS = false>
 __device__ __forceinline__ int32_t sell_col(const SellIdx &ix, int32_t p, int32_t row) {
-    if constexpr (D16) return row + (int32_t)__ldg(ix.delta + p);
-    else return __ldg(ix.col + p);
+    if constexpr (D16) return row + (int32_t)ld_ro<CS>(ix.delta + p);
+    else return ld_ro<CS>(ix.col + p);
 }
 
 constexpr int kShortMax = 8;  // widest slice of the load-first path
@@ -144,15 +154,15 @@ constexpr int kShortMax = 8;  // widest slice of the load-first path
 // a slice of width W (W <= 8): every value and column load first, then every
 // gather, then the products in k order -- short rows (interpolation P,
 // coarse operators) otherwise pay a load -> gather round trip per entry
-template <int W, typename VT, typename XT, bool D16, class G>
+template <int W, typename VT, typename XT, bool D16, class G, bool CS = false>
 __device__ __forceinline__ XT sell_short_sum(int32_t off, int32_t row, const SellIdx &ix,
                                              const VT *__restrict__ sv, G gather) {
     VT v[W];
     int32_t c[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        v[k] = __ldg(sv + off + k * 32);
-        c[k] = sell_col<D16>(ix, off + k * 32, row);
+        v[k] = ld_ro<CS>(sv + off + k * 32);
+        c[k] = sell_col<D16, CS>(ix, off + k * 32, row);
     }
     XT g[W];
 #pragma unroll
@@ -167,7 +177,7 @@ __device__ __forceinline__ XT sell_short_sum(int32_t off, int32_t row, const Sel
 // entries in k order whatever the path; SHORT: slices of width <= 8 take the
 // load-everything-first path (the transfer operators P and R, whose rows are
 // short; the relaxation kernels measured slower with it)
-template <typename VT, typename XT, bool D16, bool SHORT = false, class G>
+template <typename VT, typename XT, bool D16, bool SHORT = false, bool CS = false, class G>
 __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32_t *__restrict__ soff,
                                            const int32_t *__restrict__ sw, const SellIdx &ix,
                                            const VT *__restrict__ sv, G gather) {
@@ -175,14 +185,14 @@ __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32
     int32_t off = __ldg(soff + s) + lane, w = __ldg(sw + s);
     if constexpr (SHORT) {
         switch (w) {  // uniform over the warp (one slice)
-            case 1: return sell_short_sum<1, VT, XT, D16>(off, row, ix, sv, gather);
-            case 2: return sell_short_sum<2, VT, XT, D16>(off, row, ix, sv, gather);
-            case 3: return sell_short_sum<3, VT, XT, D16>(off, row, ix, sv, gather);
-            case 4: return sell_short_sum<4, VT, XT, D16>(off, row, ix, sv, gather);
-            case 5: return sell_short_sum<5, VT, XT, D16>(off, row, ix, sv, gather);
-            case 6: return sell_short_sum<6, VT, XT, D16>(off, row, ix, sv, gather);
-            case 7: return sell_short_sum<7, VT, XT, D16>(off, row, ix, sv, gather);
-            case 8: return sell_short_sum<8, VT, XT, D16>(off, row, ix, sv, gather);
+            case 1: return sell_short_sum<1, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 2: return sell_short_sum<2, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 3: return sell_short_sum<3, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 4: return sell_short_sum<4, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 5: return sell_short_sum<5, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 6: return sell_short_sum<6, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 7: return sell_short_sum<7, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
+            case 8: return sell_short_sum<8, VT, XT, D16, G, CS>(off, row, ix, sv, gather);
             default: break;
         }
     }
@@ -190,7 +200,7 @@ __device__ __forceinline__ XT sell_row_sum(int32_t pos, int32_t row, const int32
 #pragma unroll 4
     for (int32_t k = 0; k < w; ++k) {
         int32_t p = off + k * 32;
-        acc += cvt<VT, XT>(__ldg(sv + p)) * gather(sell_col<D16>(ix, p, row));
+        acc += cvt<VT, XT>(ld_ro<CS>(sv + p)) * gather(sell_col<D16, CS>(ix, p, row));
     }
     return acc;
 }
@@ -246,8 +256,8 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     if (OP == kSpmvAdd) own = o1[i];
     if (OP == kSpmvScale) own = dinv[i];
     XT s;
-    if (OP == kPre) s = sell_row_sum<VT, XT, D16, SHORT || kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT, D16, SHORT || kTransfer>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -695,7 +705,7 @@ ap_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
         const int32_t pos = sl * 32 + lane;
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
-        double s = sell_row_sum<double, double, D16, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
+        double s = sell_row_sum<double, double, D16, SHORT, true>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(p + j); });
         if (RESID) {
             const double e = b[i] - s;
             q[i] = e;
@@ -869,7 +879,7 @@ post_rz_sell_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *
         const int32_t pos = sl * 32 + lane;
         if (pos >= n) continue;
         const int32_t i = perm ? __ldg(perm + pos) : pos;
-        double s = sell_row_sum<double, double, D16>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
+        double s = sell_row_sum<double, double, D16, false, true>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
         double bi = b[i];
         double zi = x[i] + dinv[i] * (bi - s);
         z[i] = zi;
