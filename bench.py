@@ -367,7 +367,7 @@ def collect_setup_timing(h, nlev):
 
 
 # ---------------------------------------------------------------------------
-# other workloads (measured one line each; not the driver's bench line)
+# other workloads (measured one line each; not the default bench line)
 # ---------------------------------------------------------------------------
 def _events_ms(fn, reps=3):
     import torch
