@@ -240,7 +240,7 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
     }
 }
 
-template <typename VT, typename XT, int OP, bool D16, bool SHORT>
+template <typename VT, typename XT, int OP, bool D16, bool SHORT, bool CS>
 __global__ void __launch_bounds__(kThreads)
 sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
                SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
@@ -256,8 +256,8 @@ sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__res
     if (OP == kSpmvAdd) own = o1[i];
     if (OP == kSpmvScale) own = dinv[i];
     XT s;
-    if (OP == kPre) s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
-    else s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, SHORT>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
+    if (OP == kPre) s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, CS>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(b + j) * __ldg(dinv + j); });
+    else s = sell_row_sum<VT, XT, D16, SHORT || kTransfer, CS>(pos, i, soff, sw, ix, sv, [&](int32_t j) { return __ldg(x + j); });
     if (OP == kPre) {
         XT bi = b[i];
         o1[i] = bi * dinv[i];
@@ -378,7 +378,7 @@ void part_op(const CycMat<double> &A, const double *b, const double *dinv, const
 // at a time -- all values and columns, then all gathers, then the products
 // -- and the T parts are added by xor shuffles.  The row's sum therefore
 // runs in another order than a sequential one (not bit-equal to CSR).
-template <typename VT, typename XT, int OP, bool D16, int C>
+template <typename VT, typename XT, int OP, bool D16, int C, bool CS>
 __global__ void __launch_bounds__(kThreads)
 sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
                      const int32_t *__restrict__ sw, SellIdx ix, const VT *__restrict__ sv, const XT *__restrict__ b,
@@ -405,14 +405,14 @@ sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t 
             // first (nk is the same for the whole warp), rather than one
             // load -> gather round trip per entry in the tail loop
             switch (nk) {
-                case 1: acc = sell_short_sum<1, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 2: acc = sell_short_sum<2, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 3: acc = sell_short_sum<3, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 4: acc = sell_short_sum<4, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 5: acc = sell_short_sum<5, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 6: acc = sell_short_sum<6, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 7: acc = sell_short_sum<7, VT, XT, D16>(off, i, ix, sv, gather); break;
-                case 8: acc = sell_short_sum<8, VT, XT, D16>(off, i, ix, sv, gather); break;
+                case 1: acc = sell_short_sum<1, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 2: acc = sell_short_sum<2, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 3: acc = sell_short_sum<3, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 4: acc = sell_short_sum<4, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 5: acc = sell_short_sum<5, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 6: acc = sell_short_sum<6, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 7: acc = sell_short_sum<7, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
+                case 8: acc = sell_short_sum<8, VT, XT, D16, decltype(gather), CS>(off, i, ix, sv, gather); break;
                 default: break;
             }
             k = nk;
@@ -423,8 +423,8 @@ sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t 
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int32_t p = off + (k + u) * 32;
-                v[u] = __ldg(sv + p);
-                c[u] = sell_col<D16>(ix, p, i);
+                v[u] = ld_ro<CS>(sv + p);
+                c[u] = sell_col<D16, CS>(ix, p, i);
             }
             XT g[U];
 #pragma unroll
@@ -434,7 +434,7 @@ sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t 
         }
         for (; k < nk; ++k) {
             const int32_t p = off + k * 32;
-            acc += cvt<VT, XT>(__ldg(sv + p)) * gather(sell_col<D16>(ix, p, i));
+            acc += cvt<VT, XT>(ld_ro<CS>(sv + p)) * gather(sell_col<D16, CS>(ix, p, i));
         }
     }
 #pragma unroll
@@ -466,10 +466,19 @@ void launch_sell_lanes(const CycMat<VT> &A, const XT *b, const XT *dinv, const X
     const SellIdx ix{A.sci, A.sd};
     const int64_t warps = div_up((int64_t)n, (int64_t)C);
     const int g = (int)div_up(warps * 32, (int64_t)kThreads);
-    if (A.sd)
-        { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, true, C>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-    else
-        { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, false, C>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    auto launch = [&](auto cs) {
+        constexpr bool CS = decltype(cs)::value;
+        if (A.sd)
+            { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, true, C, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        else
+            { pdl_launch(sell_lanes_op_kernel<VT, XT, OP, false, C, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+    };
+    if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+        if (A.stream) launch(std::true_type());
+        else launch(std::false_type());
+    } else {
+        launch(std::false_type());
+    }
 }
 
 template <typename VT, typename XT, int OP>
@@ -494,14 +503,24 @@ void dispatch_op(const CycMat<VT> &A, const XT *b, const XT *dinv, const XT *x, 
         // faster at level 0, slower on the longer, irregular coarse rows)
         const bool sh = A.max_row > 0 && A.max_row <= kShortMax;
         const int g = div_up(n, kThreads);
-        if (A.sd && sh)
-            { pdl_launch(sell_op_kernel<VT, XT, OP, true, true>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-        else if (A.sd)
-            { pdl_launch(sell_op_kernel<VT, XT, OP, true, false>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-        else if (sh)
-            { pdl_launch(sell_op_kernel<VT, XT, OP, false, true>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
-        else
-            { pdl_launch(sell_op_kernel<VT, XT, OP, false, false>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        auto launch = [&](auto cs) {
+            constexpr bool CS = decltype(cs)::value;
+            if (A.sd && sh)
+                { pdl_launch(sell_op_kernel<VT, XT, OP, true, true, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            else if (A.sd)
+                { pdl_launch(sell_op_kernel<VT, XT, OP, true, false, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            else if (sh)
+                { pdl_launch(sell_op_kernel<VT, XT, OP, false, true, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+            else
+                { pdl_launch(sell_op_kernel<VT, XT, OP, false, false, CS>, g, kThreads, 0, s, n, A.perm, A.soff, A.sw, ix, A.sv, b, dinv, x, o1, o2); ::amg::count_launch(); }
+        };
+        // the streaming loads only in FP64 (the reduced-precision copies are half the size or less)
+        if constexpr (std::is_same<VT, double>::value && std::is_same<XT, double>::value) {
+            if (A.stream) launch(std::true_type());
+            else launch(std::false_type());
+        } else {
+            launch(std::false_type());
+        }
     } else {
         int T = threads_per_row(A.variant);
         int blocks = div_up((int64_t)n * T, kThreads);

@@ -39,8 +39,12 @@ template <typename VT> struct CycMat {
     int32_t max_row = 0;  // most stored entries of a row (0: not known)
     int variant = AMG_SPMV_CSR4;
     int sell_c = 32;      // slice height of the SELL copy
+    bool stream = false;  // stored entries larger than kStreamBytes: the SELL kernels load them
+                          // with the evict-first policy (read once per pass, they would only
+                          // push the vectors and the smaller levels out of L1 and L2)
     PartView part;        // set when the hierarchy runs row-partitioned (FP64 only)
 };
+constexpr int64_t kStreamBytes = 48ll << 20;
 
 // Device-side scalars of one PCG run.
 struct PcgScalars {

@@ -190,6 +190,7 @@ template <typename VT> inline CycMat<VT> make_mat(const DevCSR &M, const VT *val
     m.rp = M.rp();
     m.ci = M.ci();
     m.v = vals;
+    m.stream = M.nnz * (int64_t)(sizeof(VT) + sizeof(int32_t)) > kStreamBytes;
     return m;
 }
 
