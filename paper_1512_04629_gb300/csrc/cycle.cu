@@ -133,9 +133,10 @@ struct SellIdx {
     const int32_t *col;
     const int16_t *delta;
 };
-// a read-only load; CS: with the evict-first (streaming) policy, for the
-// level-0 operators, which are read once per pass and larger than L2, so
-// that they do not push the coarse levels out of it
+// a read-only load; CS: with the evict-first (streaming) policy, for
+// operators much larger than L2 (the finest level's, always, and any whose
+// stored entries pass kStreamBytes): read once per pass, they would only
+// push the gathered vectors and the smaller levels out of L1 and L2
 template <bool CS, typename T> __device__ __forceinline__ T ld_ro(const T *p) {
     if constexpr (CS && (std::is_same<T, double>::value || std::is_same<T, float>::value ||
                          std::is_same<T, int32_t>::value || std::is_same<T, int16_t>::value))
@@ -240,6 +241,9 @@ csr_op_kernel(int32_t n, const int32_t *__restrict__ rp, const int32_t *__restri
     }
 }
 
+// One lane per row of a SELL-32 operator; SHORT: every slice fits the
+// load-first path; CS: the operator's entries load with the evict-first
+// policy (CycMat::stream)
 template <typename VT, typename XT, int OP, bool D16, bool SHORT, bool CS>
 __global__ void __launch_bounds__(kThreads)
 sell_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff, const int32_t *__restrict__ sw,
@@ -378,6 +382,7 @@ void part_op(const CycMat<double> &A, const double *b, const double *dinv, const
 // at a time -- all values and columns, then all gathers, then the products
 // -- and the T parts are added by xor shuffles.  The row's sum therefore
 // runs in another order than a sequential one (not bit-equal to CSR).
+// CS: the operator's entries load with the evict-first policy.
 template <typename VT, typename XT, int OP, bool D16, int C, bool CS>
 __global__ void __launch_bounds__(kThreads)
 sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t *__restrict__ soff,
