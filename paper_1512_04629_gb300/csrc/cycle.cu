@@ -174,6 +174,25 @@ __device__ __forceinline__ XT sell_short_sum(int32_t off, int32_t row, const Sel
     return acc;
 }
 
+// the same for the last W (< 4) entries of a lane in the SELL-C kernels,
+// added into acc in k order after every load and gather is in flight
+template <int W, typename VT, typename XT, bool D16, bool CS, class G>
+__device__ __forceinline__ void sell_tail_acc(XT &acc, int32_t off, int32_t row, const SellIdx &ix,
+                                              const VT *__restrict__ sv, G gather) {
+    VT v[W];
+    int32_t c[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        v[k] = ld_ro<CS>(sv + off + k * 32);
+        c[k] = sell_col<D16, CS>(ix, off + k * 32, row);
+    }
+    XT g[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) g[k] = gather(c[k]);
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc += cvt<VT, XT>(v[k]) * g[k];
+}
+
 // sum over the row stored at SELL position pos (slice pos / 32, lane pos % 32),
 // entries in k order whatever the path; SHORT: slices of width <= 8 take the
 // load-everything-first path (the transfer operators P and R, whose rows are
@@ -437,9 +456,12 @@ sell_lanes_op_kernel(int32_t n, const int32_t *__restrict__ perm, const int32_t 
 #pragma unroll
             for (int u = 0; u < U; ++u) acc += cvt<VT, XT>(v[u]) * g[u];
         }
-        for (; k < nk; ++k) {
-            const int32_t p = off + k * 32;
-            acc += cvt<VT, XT>(ld_ro<CS>(sv + p)) * gather(sell_col<D16, CS>(ix, p, i));
+        // the last nk - k < U entries, loaded together (a warp-uniform count)
+        switch (nk - k) {
+            case 1: sell_tail_acc<1, VT, XT, D16, CS>(acc, off + k * 32, i, ix, sv, gather); break;
+            case 2: sell_tail_acc<2, VT, XT, D16, CS>(acc, off + k * 32, i, ix, sv, gather); break;
+            case 3: sell_tail_acc<3, VT, XT, D16, CS>(acc, off + k * 32, i, ix, sv, gather); break;
+            default: break;
         }
     }
 #pragma unroll
